@@ -1,0 +1,115 @@
+"""Pins of the oracle's SIPDG operator (Eq. ellipticOp1 / Eq. INS_SD_5)."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from dg_inputs import jittered_grid, manufactured
+from dg_inputs.mesh import rotate_local_vertices, with_all_neumann
+from oracle.sipdg import Sipdg
+
+
+def _mesh(n, seed=0, rotate=None):
+    m = jittered_grid(n, n, jitter=0.1, seed=seed)
+    return rotate_local_vertices(m, rotate) if rotate is not None else m
+
+
+def _sip(m, N):
+    return Sipdg(m.VX, m.VY, m.EToV, m.bc, N)
+
+
+@pytest.mark.parametrize("n,N", [(1, 1), (1, 8), (2, 2), (2, 5), (4, 3), (4, 8)])
+def test_symmetric_positive_definite(n, N):
+    S = _sip(_mesh(n, rotate=3), N)
+    A = S.assemble().toarray()
+    assert np.abs(A - A.T).max() <= 1e-14 * np.abs(A).max() * 10
+    np.linalg.cholesky(0.5 * (A + A.T))
+    assert np.linalg.eigvalsh(0.5 * (A + A.T)).min() > 0
+
+
+@pytest.mark.parametrize("N", [1, 3, 6])
+def test_all_neumann_kills_constants(N):
+    S = _sip(with_all_neumann(_mesh(3, rotate=1)), N)
+    A = S.assemble()
+    one = np.ones(S.K * S.Np)
+    assert np.abs(A @ one).max() < 1e-11 * abs(A).max()
+
+
+@pytest.mark.parametrize("N", range(1, 9))
+@pytest.mark.parametrize("lam", [0.0, 3.5])
+def test_polynomial_exactness_with_dirichlet_data(N, lam):
+    """For a global polynomial p of degree <= N with g = p on the boundary, all
+    jumps vanish and A p + L(p) = M (-lap p + lam p), whatever tau is."""
+    S = _sip(_mesh(3, rotate=N), N)
+    a = N // 2
+    b = N - a
+    x, y = S.x, S.y
+    p = 0.3 + x ** a * y ** b + 0.5 * x ** (N - 1 if N > 1 else 0) * y
+    lap = np.zeros_like(x)
+    if a >= 2:
+        lap += a * (a - 1) * x ** (a - 2) * y ** b
+    if b >= 2:
+        lap += b * (b - 1) * x ** a * y ** (b - 2)
+    if N - 1 >= 2:
+        lap += 0.5 * (N - 1) * (N - 2) * x ** (N - 3) * y
+    lhs = S.apply(p, lam=lam) + S.dirichlet_lift(p)
+    rhs = S.mass_apply(-lap + lam * p)
+    assert np.linalg.norm(lhs - rhs) <= 1e-11 * max(1.0, np.linalg.norm(rhs)) * N
+
+
+def test_helmholtz_large_lambda_tends_to_mass():
+    S = _sip(_mesh(2, rotate=0), 4)
+    lam = 1e9
+    A = S.assemble(lam).toarray() / lam
+    Mref = S.mass_matrix_ref()
+    for e in range(S.K):
+        blk = A[e * S.Np:(e + 1) * S.Np, e * S.Np:(e + 1) * S.Np]
+        assert np.allclose(blk, S.geo.J[e] * Mref, rtol=0, atol=1e-6 * np.abs(Mref).max())
+
+
+@pytest.mark.parametrize("N", [2, 5])
+def test_matrix_free_equals_assembled_and_sampling(N):
+    S = _sip(_mesh(4, rotate=7), N)
+    u = np.random.default_rng(1).uniform(-1, 1, (S.K, S.Np))
+    A = S.assemble(2.0)
+    ref = (A @ u.ravel()).reshape(u.shape)
+    mf = S.apply(u, lam=2.0)
+    assert np.abs(ref - mf).max() < 1e-12 * np.abs(ref).max()
+    elems = np.array([0, 5, 17, S.K - 1])
+    assert np.abs(S.apply(u, lam=2.0, elems=elems) - ref[elems]).max() < 1e-12 * np.abs(ref).max()
+    ub = np.stack([u, 2 * u])
+    assert np.allclose(S.apply(ub, lam=2.0), np.stack([mf, 2 * mf]), rtol=1e-13, atol=1e-12)
+
+
+def test_invariant_under_local_vertex_rotation():
+    """Rotating each element's local vertex list permutes its (symmetric) node
+    set; the operator must be the same up to that permutation."""
+    m = _mesh(3)
+    mr = rotate_local_vertices(m, 11)
+    N = 4
+    S, Sr = _sip(m, N), _sip(mr, N)
+    u = np.random.default_rng(2).uniform(-1, 1, (S.K, S.Np))
+    perm = np.empty((S.K, S.Np), dtype=int)
+    for e in range(S.K):
+        for i in range(S.Np):
+            d = (S.x[e] - Sr.x[e, i]) ** 2 + (S.y[e] - Sr.y[e, i]) ** 2
+            perm[e, i] = int(np.argmin(d))
+            assert d[perm[e, i]] < 1e-24
+    ur = np.take_along_axis(u, perm, axis=1)
+    Au = S.apply(u)
+    Aur = Sr.apply(ur)
+    assert np.abs(np.take_along_axis(Au, perm, axis=1) - Aur).max() < 1e-12 * np.abs(Au).max()
+
+
+@pytest.mark.parametrize("N", [1, 2, 3])
+def test_h_convergence_rate(N):
+    """Manufactured u = sin(pi x) sin(pi y): L2 error ~ h^{N+1} (Section 4.1)."""
+    uex, fex = manufactured("sin_pi_x_sin_pi_y")
+    errs = []
+    for n in (4, 8, 16):
+        S = _sip(_mesh(n), N)
+        A = S.assemble().tocsc()
+        b = S.rhs(fex(S.x, S.y), uex(S.x, S.y))
+        u = spla.spsolve(A, b.ravel()).reshape(S.K, S.Np)
+        errs.append(S.l2_error(u, uex))
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert rates[-1] > N + 1 - 0.35, (errs, rates)
