@@ -1,0 +1,168 @@
+/*
+ * dg.h - C ABI of the GB300 SIPDG pressure-Poisson library.
+ *
+ * The library implements the hot path of the semi-implicit nodal DG
+ * incompressible-flow method of Karakus, Chalmers, Swirydowicz & Warburton
+ * (arXiv:1801.00246): the matrix-free symmetric-interior-penalty (SIPDG)
+ * Laplacian / screened-Poisson operator on affine triangles of degree
+ * N = 1..8 (Section 2.1 Eq. INS_SD_5, Section 5.2 Eq. ellipticOp1-3), and
+ * its solution by preconditioned conjugate gradients with a degree-coarsening
+ * p-multigrid preconditioner (Section 3).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Reference triangle {r, s >= -1, r + s <= 0}, vertices v0=(-1,-1),
+ *    v1=(1,-1), v2=(-1,1). Elements are given counter-clockwise; local face f
+ *    joins local vertices f and (f+1) mod 3.
+ *  - Nodal fields are contiguous arrays [B][K][Np], Np = (N+1)(N+2)/2, the
+ *    nodes being the Warp & Blend nodes (Section 2.1) ordered in rows of
+ *    constant s from s = -1 upward, r increasing within a row.
+ *  - Operator outputs are WEAK coefficient vectors: (A u)_i = a(u, l_i),
+ *    i.e. already multiplied by the mass matrix (Eq. ellipticOp3 carries the
+ *    leading M^e).
+ *  - Boundary tags per face: 0 interior, 1 Dirichlet, 2 Neumann.
+ *    Dirichlet faces use the ghost state u+ = 2g - u-, grad u+ = grad u-
+ *    (homogeneous operator: g = 0); Neumann faces u+ = u-, grad u+ = -grad u-.
+ *    Penalty per face: tau = (N+1)(N+2)/2 * max(1/h-, 1/h+), h = |E|/|face|
+ *    (Eq. PenaltyParameter); boundary faces use h- only.
+ *  - Field pointers marked "device" are caller-owned CUDA device memory; the
+ *    library never frees them. Host pointers are only read during the call.
+ *  - All device work is enqueued on the caller's stream (cudaStream_t passed
+ *    as void*; NULL = legacy default stream). Calls that return results to
+ *    the host (dg_pcg_solve's info) synchronise that stream.
+ *  - Every entry point returns a dg_status; no exception crosses the ABI.
+ *    Arguments are validated before any launch. dg_last_error() returns a
+ *    human-readable message for the last failing call on this thread.
+ */
+#ifndef DG_H
+#define DG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DG_OK = 0,
+  DG_ERR_ARG = 1,            /* invalid argument (null pointer, bad size, N out of range) */
+  DG_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+  DG_ERR_OOM = 3,            /* device allocation failed */
+  DG_ERR_NOT_CONVERGED = 4,  /* max_iter reached; x holds the last iterate */
+  DG_ERR_BREAKDOWN = 5,      /* p^T A p <= 0 or NaN in a Krylov recurrence */
+  DG_ERR_TIMEOUT = 6,        /* a bounded device-side wait gave up */
+  DG_ERR_MESH = 7            /* non-positive Jacobian or non-conforming faces */
+} dg_status;
+
+typedef enum { DG_F64 = 0, DG_F32 = 1 } dg_prec;
+
+typedef struct dg_mesh dg_mesh; /* opaque; owned by the library until dg_mesh_destroy */
+
+/* Preconditioner choices for dg_pcg_solve (Section 3). */
+enum { DG_PREC_NONE = 0, DG_PREC_JACOBI = 1, DG_PREC_INVMASS = 2, DG_PREC_PMG = 3 };
+
+typedef struct {
+  double tol;          /* stop when ||b - A x||_2 / ||b||_2 <= tol (per right-hand side) */
+  int max_iter;        /* outer iteration cap */
+  int precond;         /* DG_PREC_* */
+  int nlevels;         /* p-multigrid: number of degrees in `degrees` (2..8) */
+  int degrees[8];      /* p-multigrid degrees, degrees[0] = mesh degree, strictly decreasing, last >= 1 */
+  int cheb_degree;     /* Chebyshev smoothing degree per pre/post smoothing (>= 1) */
+  double coarse_tol;   /* relative tolerance of the CG solve on the coarsest degree */
+  int coarse_max_iter; /* iteration cap of that coarse CG */
+  int mixed;           /* 1: p-multigrid levels in FP32, outer iteration FP64; 0: all FP64 */
+  int power_steps;     /* power iterations for the Chebyshev bound rho(D^{-1}A) */
+} dg_solver_opts;
+
+#define DG_MAX_BATCH 64
+
+typedef struct {
+  int iters[DG_MAX_BATCH];      /* outer iterations per right-hand side */
+  double relres[DG_MAX_BATCH];  /* final ||b - A x|| / ||b|| from the recurrence residual */
+  int total_iters;              /* iterations of the batched loop (max over the batch) */
+  float ms;                     /* device time of the solve (CUDA events on the stream) */
+} dg_solve_info;
+
+/* Default options: tol 1e-10, max_iter 1000, Jacobi, no multigrid. */
+void dg_solver_opts_default(dg_solver_opts* opts);
+
+/* Build the discretisation of degree N (1..8) on a triangle mesh.
+ * VX, VY: host, Nv vertex coordinates. EToV: host, K x 3 vertex indices,
+ * counter-clockwise. bc: host, K x 3 tags (0 interior, 1 Dirichlet,
+ * 2 Neumann) of face f = (v_f, v_{f+1}); a face with no neighbour must carry
+ * a non-zero tag and a shared face must carry 0.
+ * Computes on the host: nodes, reference operators (Eq. elMass, elStiff,
+ * elLift), geometric factors (Eq. operators2, elementOps), face connectivity;
+ * uploads them with stream-ordered copies. Returns DG_ERR_MESH for a
+ * non-positive Jacobian, a face shared by more than two elements, or tags
+ * that disagree with the connectivity. */
+dg_status dg_mesh_setup(int N, int64_t Nv, const double* VX, const double* VY, int64_t K,
+                        const int32_t* EToV, const int8_t* bc, void* stream, dg_mesh** out);
+dg_status dg_mesh_destroy(dg_mesh* mesh);
+
+/* Degree, element count and nodes per element of a mesh. */
+dg_status dg_mesh_info(const dg_mesh* mesh, int* N, int64_t* K, int* Np);
+
+/* Physical coordinates of the degree-`degree` nodes (1..8; 0 = mesh degree):
+ * x_dev, y_dev device arrays [K][Np(degree)], FP64. */
+dg_status dg_mesh_nodes(const dg_mesh* mesh, int degree, double* x_dev, double* y_dev, void* stream);
+
+/* Poisson operator (Eq. ellipticOp3 with lambda = 0) at the mesh degree:
+ * Au[b] = A u[b] for b < B. u, Au: device [B][K][Np] of FP64 (DG_F64) or
+ * FP32 (DG_F32); FP32 arithmetic accumulates in FP32. u and Au must not alias. */
+dg_status dg_poisson_apply(const dg_mesh* mesh, dg_prec prec, int B, const void* u, void* Au,
+                           void* stream);
+
+/* Screened-Poisson (Helmholtz) operator -L + lambda (Eq. ellipticOp1):
+ * Au = A u + lambda J M u. Same layout rules as dg_poisson_apply. */
+dg_status dg_helmholtz_apply(const dg_mesh* mesh, dg_prec prec, int B, double lambda,
+                             const void* u, void* Au, void* stream);
+
+/* Either operator at any degree 1..8 on the same mesh (p-multigrid levels). */
+dg_status dg_operator_apply(const dg_mesh* mesh, int degree, dg_prec prec, int B, double lambda,
+                            const void* u, void* Au, void* stream);
+
+/* diag(A) of the operator at `degree` (0 = mesh degree) for the given lambda:
+ * diag device [K][Np(degree)] in FP64 or FP32 (Jacobi preconditioner). */
+dg_status dg_operator_diagonal(const dg_mesh* mesh, int degree, dg_prec prec, double lambda, void* diag,
+                               void* stream);
+
+/* Weak right-hand side of the Dirichlet problem -lap u + lambda u = f,
+ * u = g on Dirichlet faces: b = J M f - L(g), L(g)_i = sum over Dirichlet
+ * faces of (n.grad l_i, g) - 2 tau (l_i, g). f, g, b: device FP64 [B][K][Np]
+ * nodal values (only the face-node values of g are used). */
+dg_status dg_rhs(const dg_mesh* mesh, int B, const double* f, const double* g, double* b,
+                 void* stream);
+
+/* Preconditioned conjugate gradients on A(lambda) x = b for B right-hand
+ * sides at once (Section 3). b, x: device FP64 [B][K][Np]; x holds the
+ * initial guess on entry and the solution on exit. With DG_PREC_PMG and
+ * opts->mixed the multigrid levels run in FP32 and the outer iteration is
+ * flexible CG in FP64; otherwise standard PCG. info (host, may be NULL)
+ * receives iterations and residuals after a stream synchronisation.
+ * Workspace is allocated by the library on first use and kept with the mesh.
+ * Returns DG_ERR_NOT_CONVERGED if any right-hand side misses tol within
+ * max_iter (x holds the last iterate), DG_ERR_BREAKDOWN on p^T A p <= 0. */
+dg_status dg_pcg_solve(dg_mesh* mesh, const dg_solver_opts* opts, int B, double lambda,
+                       const double* b, double* x, dg_solve_info* info, void* stream);
+
+/* Host-only: the library's own reference data for degree N (1..8), for
+ * inspection without a GPU. r, s: Np; M, Dr, Ds: Np x Np row-major;
+ * Mf: (N+1) x (N+1); fmask: 3 x (N+1) local node index of face node j of face
+ * f in counter-clockwise order. Any pointer may be NULL. */
+dg_status dg_reference_operators(int N, double* r, double* s, double* M, double* Dr, double* Ds,
+                                 double* Mf, int32_t* fmask);
+
+/* Host-only: p-multigrid interpolation from degree Nc to degree Nf
+ * (Nf > Nc >= 1): P[Np(Nf)][Np(Nc)] row-major, the coarse nodal basis
+ * evaluated at the fine nodes. */
+dg_status dg_interpolation_matrix(int Nf, int Nc, double* P);
+
+const char* dg_status_string(dg_status status);
+const char* dg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DG_H */

@@ -1,0 +1,216 @@
+"""ctypes binding of include/dg.h (argument marshalling only)."""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+DG_F64, DG_F32 = 0, 1
+PREC_NONE, PREC_JACOBI, PREC_INVMASS, PREC_PMG = 0, 1, 2, 3
+DG_MAX_BATCH = 64
+
+_STATUS = {0: "DG_OK", 1: "DG_ERR_ARG", 2: "DG_ERR_CUDA", 3: "DG_ERR_OOM", 4: "DG_ERR_NOT_CONVERGED",
+           5: "DG_ERR_BREAKDOWN", 6: "DG_ERR_TIMEOUT", 7: "DG_ERR_MESH"}
+
+
+class DgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+        self.name = _STATUS.get(status, str(status))
+
+
+class SolverOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precond", ctypes.c_int),
+                ("nlevels", ctypes.c_int), ("degrees", ctypes.c_int * 8), ("cheb_degree", ctypes.c_int),
+                ("coarse_tol", ctypes.c_double), ("coarse_max_iter", ctypes.c_int), ("mixed", ctypes.c_int),
+                ("power_steps", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int * DG_MAX_BATCH), ("relres", ctypes.c_double * DG_MAX_BATCH),
+                ("total_iters", ctypes.c_int), ("ms", ctypes.c_float)]
+
+
+_lib = None
+
+
+def lib_path():
+    return _build.lib_path()
+
+
+def lib():
+    """Load the shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} missing (run __graft_entry__.build())")
+    L = ctypes.CDLL(path)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    pd, pi32 = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)
+    sig = {
+        "dg_mesh_setup": ([i32, i64, pd, pd, i64, pi32, ctypes.POINTER(ctypes.c_int8), vp, ctypes.POINTER(vp)], i32),
+        "dg_mesh_destroy": ([vp], i32),
+        "dg_mesh_info": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i32)], i32),
+        "dg_mesh_nodes": ([vp, i32, vp, vp, vp], i32),
+        "dg_poisson_apply": ([vp, i32, i32, vp, vp, vp], i32),
+        "dg_helmholtz_apply": ([vp, i32, i32, dbl, vp, vp, vp], i32),
+        "dg_operator_apply": ([vp, i32, i32, i32, dbl, vp, vp, vp], i32),
+        "dg_operator_diagonal": ([vp, i32, i32, dbl, vp, vp], i32),
+        "dg_rhs": ([vp, i32, vp, vp, vp, vp], i32),
+        "dg_pcg_solve": ([vp, ctypes.POINTER(SolverOpts), i32, dbl, vp, vp, ctypes.POINTER(SolveInfo), vp], i32),
+        "dg_solver_opts_default": ([ctypes.POINTER(SolverOpts)], None),
+        "dg_reference_operators": ([i32, pd, pd, pd, pd, pd, pd, pi32], i32),
+        "dg_interpolation_matrix": ([i32, i32, pd], i32),
+        "dg_status_string": ([i32], ctypes.c_char_p),
+        "dg_last_error": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def _check(status):
+    if status != 0:
+        raise DgError(status, lib().dg_last_error().decode())
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _tptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def reference_operators(N):
+    """The library's own reference data (host-only call, no GPU needed)."""
+    Np = (N + 1) * (N + 2) // 2
+    Nfp = N + 1
+    r, s = np.zeros(Np), np.zeros(Np)
+    M, Dr, Ds = np.zeros((Np, Np)), np.zeros((Np, Np)), np.zeros((Np, Np))
+    Mf = np.zeros((Nfp, Nfp))
+    fmask = np.zeros((3, Nfp), dtype=np.int32)
+    _check(lib().dg_reference_operators(N, _dptr(r), _dptr(s), _dptr(M), _dptr(Dr), _dptr(Ds), _dptr(Mf),
+                                        fmask.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+    return dict(r=r, s=s, M=M, Dr=Dr, Ds=Ds, Mf=Mf, fmask=fmask)
+
+
+def interpolation_matrix(Nf, Nc):
+    P = np.zeros(((Nf + 1) * (Nf + 2) // 2, (Nc + 1) * (Nc + 2) // 2))
+    _check(lib().dg_interpolation_matrix(Nf, Nc, _dptr(P)))
+    return P
+
+
+def default_opts(**kw):
+    o = SolverOpts()
+    lib().dg_solver_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "degrees":
+            for i, d in enumerate(v):
+                o.degrees[i] = int(d)
+            o.nlevels = len(v)
+        else:
+            setattr(o, k, v)
+    return o
+
+
+class Mesh:
+    """A discretisation of degree N on a triangle mesh (owns a dg_mesh*)."""
+
+    def __init__(self, N, VX, VY, EToV, bc):
+        self.N = int(N)
+        VX = np.ascontiguousarray(VX, dtype=np.float64)
+        VY = np.ascontiguousarray(VY, dtype=np.float64)
+        EToV = np.ascontiguousarray(EToV, dtype=np.int32)
+        bc = np.ascontiguousarray(bc, dtype=np.int8)
+        self.K = int(EToV.shape[0])
+        self.Np = (self.N + 1) * (self.N + 2) // 2
+        h = ctypes.c_void_p()
+        _check(lib().dg_mesh_setup(self.N, VX.size, _dptr(VX), _dptr(VY), self.K,
+                                   EToV.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                   bc.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)), None, ctypes.byref(h)))
+        self._h = h
+
+    @classmethod
+    def from_inputs(cls, mesh, N):
+        return cls(N, mesh.VX, mesh.VY, mesh.EToV, mesh.bc)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().dg_mesh_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def np_of(self, degree):
+        d = self.N if degree in (0, None) else degree
+        return (d + 1) * (d + 2) // 2
+
+    def nodes(self, degree=0):
+        import torch
+        n = self.np_of(degree)
+        x = torch.empty((self.K, n), dtype=torch.float64, device="cuda")
+        y = torch.empty_like(x)
+        _check(lib().dg_mesh_nodes(self._h, int(degree or 0), _tptr(x), _tptr(y), _stream()))
+        return x, y
+
+    def apply(self, u, lam=0.0, degree=0, out=None):
+        """A u for u of shape [B][K][Np] or [K][Np] (float64 -> FP64, float32 -> FP32)."""
+        import torch
+        if not u.is_cuda or not u.is_contiguous():
+            raise ValueError("u must be a contiguous CUDA tensor")
+        prec = {torch.float64: DG_F64, torch.float32: DG_F32}[u.dtype]
+        B = 1 if u.dim() == 2 else u.shape[0]
+        if out is None:
+            out = torch.empty_like(u)
+        _check(lib().dg_operator_apply(self._h, int(degree or 0), prec, B, float(lam), _tptr(u), _tptr(out),
+                                       _stream()))
+        return out
+
+    def diagonal(self, lam=0.0, degree=0, dtype=None):
+        import torch
+        dtype = dtype or torch.float64
+        prec = DG_F64 if dtype == torch.float64 else DG_F32
+        d = torch.empty((self.K, self.np_of(degree)), dtype=dtype, device="cuda")
+        _check(lib().dg_operator_diagonal(self._h, int(degree or 0), prec, float(lam), _tptr(d), _stream()))
+        return d
+
+    def rhs(self, f, g=None):
+        """b = J M f - L(g) (weak right-hand side with Dirichlet data g)."""
+        import torch
+        B = 1 if f.dim() == 2 else f.shape[0]
+        b = torch.empty_like(f)
+        _check(lib().dg_rhs(self._h, B, _tptr(f), _tptr(g) if g is not None else None, _tptr(b), _stream()))
+        return b
+
+    def solve(self, b, x=None, lam=0.0, opts=None, check=True, **kw):
+        """PCG solve A x = b (b, x float64 [B][K][Np] or [K][Np]); returns (x, info, status)."""
+        import torch
+        if x is None:
+            x = torch.zeros_like(b)
+        B = 1 if b.dim() == 2 else b.shape[0]
+        o = opts if opts is not None else default_opts(**kw)
+        info = SolveInfo()
+        st = lib().dg_pcg_solve(self._h, ctypes.byref(o), B, float(lam), _tptr(b), _tptr(x), ctypes.byref(info),
+                                _stream())
+        if check:
+            _check(st)
+        res = dict(iters=list(info.iters[:B]), relres=list(info.relres[:B]), total_iters=info.total_iters,
+                   ms=info.ms, status=_STATUS.get(st, st))
+        return x, res

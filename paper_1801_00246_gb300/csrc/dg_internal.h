@@ -1,0 +1,94 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "dg.h"
+
+namespace dgx {
+
+constexpr int kMaxN = 8;
+
+// Host reference-element data for one degree (FP64, row-major matrices).
+struct RefElem {
+  int N = 0, Np = 0, Nfp = 0;
+  std::vector<double> r, s, Vinv, M, Dr, Ds, Br, Bs, Mf;
+  std::vector<int> fmask;  // 3 x Nfp, counter-clockwise per face
+  // Jacobi-diagonal pieces: S_rr[i][i], (S_rs+S_sr)[i][i], S_ss[i][i], M[i][i]
+  std::vector<double> diag_rr, diag_rs, diag_ss, diag_m;
+  // per face node a of face f: sum_b Mf[a][b] Dr[k_b][k_a] (and Ds)
+  std::vector<double> face_cr, face_cs;
+};
+
+RefElem build_reference(int N);
+std::vector<double> interpolation_matrix(int Nf, int Nc);
+std::vector<double> lobatto_points(int N);
+void gauss_jacobi(int n, double a, double b, std::vector<double>& x, std::vector<double>& w);
+double jacobi_p(double x, double a, double b, int n);
+int face_node(int N, int f, int j);
+std::vector<double> invert(int n, std::vector<double> A);
+
+// Device copy of the reference operators of one degree, in one precision.
+// Layout of the single buffer (all row-major, T = double or float):
+//   Dr[Np*Np] Ds[Np*Np] Br[Np*Np] Bs[Np*Np] M[Np*Np] Mf[Nfp*Nfp]
+//   diag_rr[Np] diag_rs[Np] diag_ss[Np] diag_m[Np] face_cr[3Nfp] face_cs[3Nfp] Minv[Np*Np]
+struct DevOps {
+  void* buf = nullptr;
+  size_t bytes = 0;
+};
+
+size_t ops_count(int N);  // number of T entries in the buffer above
+
+// Per-mesh, per-degree p-multigrid transfer P (Np_f x Np_c), FP64 and FP32.
+struct DevTransfer {
+  double* P64 = nullptr;
+  float* P32 = nullptr;
+};
+
+// Solver workspace kept with the mesh (FP64 outer vectors + multigrid levels).
+struct Workspace;
+
+}  // namespace dgx
+
+// Connectivity word per face: interior  -> (neighbour << 2) | neighbour_face,
+//                             boundary  -> -1 - tag (tag 1 Dirichlet, 2 Neumann).
+struct dg_mesh {
+  int N = 0;
+  int64_t K = 0;
+  int64_t Nv = 0;
+  // host copies
+  std::vector<double> VX, VY;
+  std::vector<int32_t> EToV;
+  std::vector<double> geo_h;  // K x 4: r_x, s_x, r_y, s_y
+  std::vector<int32_t> conn_h;
+  // device
+  double* geo64 = nullptr;   // K x 4
+  float* geo32 = nullptr;    // K x 4
+  int32_t* conn = nullptr;   // K x 3
+  dgx::RefElem ref[dgx::kMaxN + 1];
+  dgx::DevOps ops64[dgx::kMaxN + 1];
+  dgx::DevOps ops32[dgx::kMaxN + 1];
+  std::map<std::pair<int, int>, dgx::DevTransfer> transfer;
+  dgx::Workspace* ws = nullptr;
+};
+
+namespace dgx {
+
+// Launchers (device code in the .cu files). `degree` in 1..8.
+cudaError_t ensure_ops(dg_mesh* m, int degree);
+cudaError_t launch_apply(const dg_mesh* m, int degree, dg_prec prec, int B, double lambda, const void* u,
+                         void* Au, cudaStream_t st);
+cudaError_t launch_rhs(const dg_mesh* m, int B, const double* f, const double* g, double* b, cudaStream_t st);
+cudaError_t launch_diagonal(const dg_mesh* m, int degree, dg_prec prec, double lambda, void* diag,
+                            cudaStream_t st);
+cudaError_t launch_nodes(const dg_mesh* m, int degree, double* x, double* y, cudaStream_t st);
+
+void set_error(const std::string& msg);
+
+}  // namespace dgx

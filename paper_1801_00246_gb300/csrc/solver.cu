@@ -1,0 +1,811 @@
+// Batched preconditioned conjugate gradients with a p-multigrid preconditioner.
+//
+// Section 3: the SIPDG systems are symmetric positive definite and are solved
+// by PCG; the screened-Poisson (velocity) systems with the scaled inverse mass
+// matrix of each element as preconditioner, the pressure system with a
+// multigrid preconditioner that first coarsens the polynomial degree
+// (matrix-free, N -> ... -> 1) and smooths with a degree-2 Chebyshev iteration.
+// Here the degree-1 level is solved by CG to a loose relative tolerance in FP64
+// (in place of the paper's algebraic multigrid tail). With single-precision
+// multigrid levels the preconditioner is not a fixed SPD operator, so the outer
+// iteration is flexible CG (beta = r_{k+1}.(z_{k+1} - z_k) / r_k.z_k).
+//
+// All B right-hand sides advance together; every right-hand side has its own
+// scalars (alpha, beta, r.z, ...) in device memory and freezes (alpha = 0) once
+// it has converged. Inner products use a fixed two-pass reduction, so reruns
+// are bitwise identical.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <type_traits>
+#include <random>
+#include <string>
+#include <vector>
+
+#include "dg_internal.h"
+
+namespace dgx {
+
+constexpr int kRedBlocks = 240;  // partial sums per right-hand side (fixed: deterministic)
+constexpr int kRedThreads = 256;
+constexpr int kNS = 16;          // scalars per right-hand side
+
+// scalar slots
+enum { S_RZ = 0, S_PAP, S_ALPHA, S_RR, S_RZOLD, S_BETA, S_BB, S_ACTIVE, S_ITERS, S_RELRES, S_BREAK, S_TOL2 };
+
+template <typename T>
+struct LevelVecs {
+  T *rhs = nullptr, *x = nullptr, *res = nullptr, *d = nullptr, *Ad = nullptr, *dinv = nullptr;
+};
+
+struct Workspace {
+  int B = 0;
+  int64_t K = 0;
+  int N = 0;
+  // outer FP64 vectors
+  double *r = nullptr, *z = nullptr, *p = nullptr, *Ap = nullptr, *dinv = nullptr;
+  double* scal = nullptr;     // [B][kNS]
+  double* partial = nullptr;  // [B][kRedBlocks][2]
+  double* h_scal = nullptr;   // pinned host mirror
+  // coarse CG (FP64)
+  double *crhs = nullptr, *cx = nullptr, *cr = nullptr, *cp = nullptr, *cAp = nullptr, *cscal = nullptr,
+         *cpartial = nullptr;
+  // multigrid levels (FP32 or FP64 per mode)
+  std::vector<LevelVecs<float>> lv32;
+  std::vector<LevelVecs<double>> lv64;
+  std::vector<void*> allocs;
+  // cached configuration
+  std::string dinv_key, pmg_key;
+  std::vector<double> rho;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+void free_workspace(dg_mesh* m) {
+  Workspace* w = m->ws;
+  if (!w) return;
+  for (void* p : w->allocs) cudaFree(p);
+  if (w->h_scal) cudaFreeHost(w->h_scal);
+  if (w->ev0) cudaEventDestroy(w->ev0);
+  if (w->ev1) cudaEventDestroy(w->ev1);
+  delete w;
+  m->ws = nullptr;
+}
+
+namespace {
+
+template <typename T>
+cudaError_t walloc(Workspace* w, T** p, size_t count) {
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T) + 16);
+  if (e == cudaSuccess) w->allocs.push_back(*p);
+  return e;
+}
+
+inline int npd(int N) { return (N + 1) * (N + 2) / 2; }
+
+// ---------------------------------------------------------------- reductions
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < int(blockDim.x >> 5); ++k) t += sh[k];
+  return t;  // valid in thread 0
+}
+
+// partial[b][blk][0] = sum x.y over the block's slice of right-hand side b
+template <typename TX, typename TY>
+__global__ void k_dot(int64_t n, const TX* __restrict__ x, const TY* __restrict__ y, double* __restrict__ partial) {
+  __shared__ double sh[32];
+  const int b = blockIdx.y;
+  const TX* xb = x + size_t(b) * n;
+  const TY* yb = y + size_t(b) * n;
+  double acc = 0.0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    acc += double(xb[i]) * double(yb[i]);
+  const double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) partial[(size_t(b) * kRedBlocks + blockIdx.x) * 2] = t;
+}
+
+// x += alpha p; r -= alpha Ap; partial: r.r and r.zold (zold may be null)
+__global__ void k_update_xr(int64_t n, const double* __restrict__ scal, double* __restrict__ x,
+                            double* __restrict__ r, const double* __restrict__ p, const double* __restrict__ Ap,
+                            const double* __restrict__ zold, double* __restrict__ partial) {
+  __shared__ double sh[32];
+  const int b = blockIdx.y;
+  const double alpha = scal[b * kNS + S_ALPHA];
+  const size_t off = size_t(b) * n;
+  double rr = 0.0, rz = 0.0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    x[off + i] += alpha * p[off + i];
+    const double ri = r[off + i] - alpha * Ap[off + i];
+    r[off + i] = ri;
+    rr += ri * ri;
+    if (zold) rz += ri * zold[off + i];
+  }
+  double t = block_sum(rr, sh);
+  if (threadIdx.x == 0) partial[(size_t(b) * kRedBlocks + blockIdx.x) * 2] = t;
+  t = block_sum(rz, sh);
+  if (threadIdx.x == 0) partial[(size_t(b) * kRedBlocks + blockIdx.x) * 2 + 1] = t;
+}
+
+enum FinMode { FIN_INIT_BB = 0, FIN_INIT_RZ, FIN_ALPHA, FIN_RR, FIN_BETA, FIN_BETA_FLEX };
+
+// Sums the partials of right-hand side b in a fixed order and updates its scalars.
+__global__ void k_finalize(int mode, double* __restrict__ scal, const double* __restrict__ partial) {
+  __shared__ double sh[32];
+  const int b = blockIdx.x;
+  const double* pb = partial + size_t(b) * kRedBlocks * 2;
+  const double v0 = threadIdx.x < kRedBlocks ? pb[2 * threadIdx.x] : 0.0;
+  const double v1 = threadIdx.x < kRedBlocks ? pb[2 * threadIdx.x + 1] : 0.0;
+  const double s0 = block_sum(v0, sh);
+  const double s1 = (mode == FIN_RR) ? block_sum(v1, sh) : 0.0;
+  if (threadIdx.x != 0) return;
+  double* s = scal + b * kNS;
+  const bool active = s[S_ACTIVE] != 0.0;
+  switch (mode) {
+    case FIN_INIT_BB:
+      s[S_BB] = s0;
+      break;
+    case FIN_INIT_RZ:  // after r = b - A x0 and z = M^{-1} r: s0 = r.z
+      s[S_RZ] = s0;
+      break;
+    case FIN_ALPHA:
+      s[S_PAP] = s0;
+      if (active) {
+        if (!(s0 > 0.0) || !isfinite(s0)) {
+          s[S_BREAK] = 1.0;
+          s[S_ACTIVE] = 0.0;
+          s[S_ALPHA] = 0.0;
+        } else {
+          s[S_ALPHA] = s[S_RZ] / s0;
+        }
+      } else {
+        s[S_ALPHA] = 0.0;
+      }
+      break;
+    case FIN_RR: {
+      s[S_RR] = s0;
+      s[S_RZOLD] = s1;
+      if (active) {
+        s[S_ITERS] += 1.0;
+        s[S_RELRES] = s[S_BB] > 0.0 ? sqrt(s0 / s[S_BB]) : 0.0;
+        if (!isfinite(s0)) {
+          s[S_BREAK] = 1.0;
+          s[S_ACTIVE] = 0.0;
+        } else if (s0 <= s[S_TOL2] * s[S_BB]) {
+          s[S_ACTIVE] = 0.0;
+        }
+      }
+      break;
+    }
+    case FIN_BETA:
+    case FIN_BETA_FLEX:
+      if (active) {
+        const double num = (mode == FIN_BETA_FLEX) ? (s0 - s[S_RZOLD]) : s0;
+        s[S_BETA] = num / s[S_RZ];
+        s[S_RZ] = s0;
+      } else {
+        s[S_BETA] = 0.0;
+      }
+      break;
+  }
+}
+
+__global__ void k_init_scal(int B, double* scal, double tol2) {
+  const int b = threadIdx.x;
+  if (b >= B) return;
+  double* s = scal + b * kNS;
+  for (int k = 0; k < kNS; ++k) s[k] = 0.0;
+  s[S_ACTIVE] = 1.0;
+  s[S_TOL2] = tol2;
+}
+
+// after initial residual: relres and activity from r.r and b.b (slot S_RR given by partial)
+__global__ void k_init_check(double* scal, const double* partial) {
+  __shared__ double sh[32];
+  const int b = blockIdx.x;
+  const double* pb = partial + size_t(b) * kRedBlocks * 2;
+  const double v0 = threadIdx.x < kRedBlocks ? pb[2 * threadIdx.x] : 0.0;
+  const double s0 = block_sum(v0, sh);
+  if (threadIdx.x != 0) return;
+  double* s = scal + b * kNS;
+  s[S_RR] = s0;
+  s[S_RELRES] = s[S_BB] > 0.0 ? sqrt(s0 / s[S_BB]) : 0.0;
+  if (s0 <= s[S_TOL2] * s[S_BB]) s[S_ACTIVE] = 0.0;
+}
+
+// p = z + beta p (per right-hand side); with init: p = z
+__global__ void k_update_p(int64_t n, const double* __restrict__ scal, const double* __restrict__ z,
+                           double* __restrict__ p, int init) {
+  const int b = blockIdx.y;
+  const size_t off = size_t(b) * n;
+  const double beta = init ? 0.0 : scal[b * kNS + S_BETA];
+  if (!init && scal[b * kNS + S_ACTIVE] == 0.0) return;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    p[off + i] = z[off + i] + beta * p[off + i];
+}
+
+// r = b - Ax
+template <typename T>
+__global__ void k_sub(int64_t n, const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ out) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    out[i] = a[i] - b[i];
+}
+
+// z = dinv * r (dinv shared across the batch: index modulo n)
+template <typename T, typename TD>
+__global__ void k_scale(int64_t n, int64_t ntot, const TD* __restrict__ dinv, const T* __restrict__ r, T* __restrict__ z) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < ntot; i += int64_t(gridDim.x) * blockDim.x)
+    z[i] = T(dinv[i % n]) * r[i];
+}
+
+template <typename T>
+__global__ void k_scaled_copy(int64_t n, T s, const T* __restrict__ a, T* __restrict__ out) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    out[i] = s * a[i];
+}
+
+template <typename T>
+__global__ void k_recip(int64_t n, T* d) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    d[i] = T(1) / d[i];
+}
+
+template <typename TO, typename TI>
+__global__ void k_convert(int64_t n, const TI* __restrict__ a, TO* __restrict__ b) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    b[i] = TO(a[i]);
+}
+
+// z_e = (lambda J_e)^{-1} Minv r_e  (scaled inverse-mass block preconditioner)
+__global__ void k_invmass(int Np, int64_t K, int B, const double* __restrict__ geo, const double* __restrict__ Minv,
+                          double lambda, const double* __restrict__ r, double* __restrict__ z) {
+  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= int64_t(B) * K * Np) return;
+  const int64_t be = idx / Np;
+  const int i = int(idx - be * Np);
+  const int64_t e = be % K;
+  const double* g = geo + 4 * e;
+  const double J = 1.0 / (g[0] * g[3] - g[2] * g[1]);
+  const double* re = r + be * Np;
+  double acc = 0.0;
+  for (int j = 0; j < Np; ++j) acc += Minv[size_t(i) * Np + j] * re[j];
+  z[idx] = acc / (lambda * J);
+}
+
+// ------------------------------------------------------------- multigrid pieces
+// Chebyshev first step: if zero_x: res = rhs, d = c0 dinv rhs, x = d;
+//                       else      d = c0 dinv res, x += d.
+template <typename T>
+__global__ void k_cheb_first(int64_t n, int64_t ntot, const T* __restrict__ dinv, const T* __restrict__ rhs,
+                             T* __restrict__ res, T* __restrict__ d, T* __restrict__ x, T c0, int zero_x) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < ntot; i += int64_t(gridDim.x) * blockDim.x) {
+    if (zero_x) {
+      const T ri = rhs[i];
+      res[i] = ri;
+      const T di = c0 * dinv[i % n] * ri;
+      d[i] = di;
+      x[i] = di;
+    } else {
+      const T di = c0 * dinv[i % n] * res[i];
+      d[i] = di;
+      x[i] += di;
+    }
+  }
+}
+
+// res -= Ad; d = c1 d + c2 dinv res; x += d
+template <typename T>
+__global__ void k_cheb_step(int64_t n, int64_t ntot, const T* __restrict__ dinv, const T* __restrict__ Ad,
+                            T* __restrict__ res, T* __restrict__ d, T* __restrict__ x, T c1, T c2) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < ntot; i += int64_t(gridDim.x) * blockDim.x) {
+    const T ri = res[i] - Ad[i];
+    res[i] = ri;
+    const T di = c1 * d[i] + c2 * dinv[i % n] * ri;
+    d[i] = di;
+    x[i] += di;
+  }
+}
+
+// rc[e][j] = sum_i P[i][j] rf[e][i]  (restriction R = P^T)
+template <typename T>
+__global__ void k_restrict(int Npf, int Npc, int64_t nE, const T* __restrict__ P, const T* __restrict__ rf,
+                           T* __restrict__ rc) {
+  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= nE * Npc) return;
+  const int64_t e = idx / Npc;
+  const int j = int(idx - e * Npc);
+  const T* re = rf + e * Npf;
+  T acc = T(0);
+  for (int i = 0; i < Npf; ++i) acc += P[size_t(i) * Npc + j] * re[i];
+  rc[idx] = acc;
+}
+
+// xf[e][i] += sum_j P[i][j] xc[e][j]
+template <typename T>
+__global__ void k_prolong(int Npf, int Npc, int64_t nE, const T* __restrict__ P, const T* __restrict__ xc,
+                          T* __restrict__ xf) {
+  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= nE * Npf) return;
+  const int64_t e = idx / Npf;
+  const int i = int(idx - e * Npf);
+  const T* ce = xc + e * Npc;
+  T acc = T(0);
+  for (int j = 0; j < Npc; ++j) acc += P[size_t(i) * Npc + j] * ce[j];
+  xf[idx] += acc;
+}
+
+// Reductions always run kRedBlocks blocks per right-hand side (blocks past the
+// end of the data write zero partials), so the finalisation reads a fixed set.
+inline dim3 vgrid(int64_t n, int B) {
+  (void)n;
+  return dim3(unsigned(kRedBlocks), unsigned(B));
+}
+inline int egrid(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  return int(b < 1 ? 1 : b);
+}
+
+#define CK(x)                              \
+  do {                                     \
+    cudaError_t e_ = (x);                  \
+    if (e_ != cudaSuccess) return e_;      \
+  } while (0)
+
+struct Ctx {
+  dg_mesh* m;
+  const dg_solver_opts* o;
+  int B;
+  double lambda;
+  cudaStream_t st;
+  Workspace* w;
+};
+
+cudaError_t ensure_transfer(dg_mesh* m, int Nf, int Nc) {
+  auto key = std::make_pair(Nf, Nc);
+  if (m->transfer.count(key)) return cudaSuccess;
+  const std::vector<double> P = interpolation_matrix(Nf, Nc);
+  std::vector<float> Pf(P.begin(), P.end());
+  DevTransfer t;
+  CK(cudaMalloc(&t.P64, P.size() * sizeof(double)));
+  CK(cudaMalloc(&t.P32, P.size() * sizeof(float)));
+  CK(cudaMemcpy(t.P64, P.data(), P.size() * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(t.P32, Pf.data(), Pf.size() * sizeof(float), cudaMemcpyHostToDevice));
+  m->transfer[key] = t;
+  return cudaSuccess;
+}
+
+cudaError_t setup_workspace(Ctx& c) {
+  dg_mesh* m = c.m;
+  const dg_solver_opts* o = c.o;
+  Workspace* w = m->ws;
+  const bool pmg = o->precond == DG_PREC_PMG;
+  std::string key = std::to_string(c.B) + "/" + std::to_string(pmg) + "/" + std::to_string(o->mixed);
+  if (pmg)
+    for (int l = 0; l < o->nlevels; ++l) key += "," + std::to_string(o->degrees[l]);
+  if (w && w->pmg_key == key) return cudaSuccess;
+  free_workspace(m);
+  w = new Workspace();
+  m->ws = w;
+  w->B = c.B;
+  w->K = m->K;
+  w->N = m->N;
+  w->pmg_key = key;
+  const int64_t n = int64_t(m->K) * npd(m->N);
+  const size_t nt = size_t(n) * c.B;
+  CK(walloc(w, &w->r, nt));
+  CK(walloc(w, &w->z, nt));
+  CK(walloc(w, &w->p, nt));
+  CK(walloc(w, &w->Ap, nt));
+  CK(walloc(w, &w->dinv, size_t(n)));
+  CK(walloc(w, &w->scal, size_t(c.B) * kNS));
+  CK(walloc(w, &w->partial, size_t(c.B) * kRedBlocks * 2));
+  CK(cudaMallocHost(&w->h_scal, sizeof(double) * c.B * kNS));
+  CK(cudaEventCreate(&w->ev0));
+  CK(cudaEventCreate(&w->ev1));
+  if (pmg) {
+    const int L = o->nlevels;
+    for (int l = 0; l + 1 < L; ++l) CK(ensure_transfer(m, o->degrees[l], o->degrees[l + 1]));
+    for (int l = 0; l < L; ++l) CK(ensure_ops(m, o->degrees[l]));
+    if (o->mixed) w->lv32.resize(L);
+    else w->lv64.resize(L);
+    for (int l = 0; l < L; ++l) {
+      const size_t nl = size_t(m->K) * npd(o->degrees[l]);
+      if (o->mixed) {
+        LevelVecs<float>& v = w->lv32[l];
+        CK(walloc(w, &v.rhs, nl * c.B));
+        CK(walloc(w, &v.x, nl * c.B));
+        CK(walloc(w, &v.res, nl * c.B));
+        CK(walloc(w, &v.d, nl * c.B));
+        CK(walloc(w, &v.Ad, nl * c.B));
+        CK(walloc(w, &v.dinv, nl));
+      } else {
+        LevelVecs<double>& v = w->lv64[l];
+        CK(walloc(w, &v.rhs, nl * c.B));
+        CK(walloc(w, &v.x, nl * c.B));
+        CK(walloc(w, &v.res, nl * c.B));
+        CK(walloc(w, &v.d, nl * c.B));
+        CK(walloc(w, &v.Ad, nl * c.B));
+        CK(walloc(w, &v.dinv, nl));
+      }
+    }
+    const size_t nc = size_t(m->K) * npd(o->degrees[L - 1]) * c.B;
+    CK(walloc(w, &w->crhs, nc));
+    CK(walloc(w, &w->cx, nc));
+    CK(walloc(w, &w->cr, nc));
+    CK(walloc(w, &w->cp, nc));
+    CK(walloc(w, &w->cAp, nc));
+    CK(walloc(w, &w->cscal, size_t(c.B) * kNS));
+    CK(walloc(w, &w->cpartial, size_t(c.B) * kRedBlocks * 2));
+  }
+  return cudaSuccess;
+}
+
+// Plain CG on the coarsest degree in FP64 to relative tolerance coarse_tol,
+// starting from x = 0. Convergence is checked on the host every `chk` steps;
+// converged right-hand sides are frozen on the device in between.
+cudaError_t coarse_cg(Ctx& c, int degree, const double* rhs, double* x, int& iters_out) {
+  Workspace* w = c.w;
+  const int B = c.B;
+  const int64_t n = int64_t(c.m->K) * npd(degree);
+  const size_t nt = size_t(n) * B;
+  const dim3 g = vgrid(n, B);
+  const double tol = c.o->coarse_tol;
+  CK(cudaMemsetAsync(x, 0, nt * sizeof(double), c.st));
+  CK(cudaMemcpyAsync(w->cr, rhs, nt * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
+  k_init_scal<<<1, 64, 0, c.st>>>(B, w->cscal, tol * tol);
+  k_dot<<<g, kRedThreads, 0, c.st>>>(n, rhs, rhs, w->cpartial);
+  k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_INIT_BB, w->cscal, w->cpartial);
+  k_init_check<<<B, kRedThreads, 0, c.st>>>(w->cscal, w->cpartial);  // r = b: r.r = b.b
+  k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_INIT_RZ, w->cscal, w->cpartial);
+  k_update_p<<<g, kRedThreads, 0, c.st>>>(n, w->cscal, w->cr, w->cp, 1);
+  const int chk = 8;
+  int it = 0;
+  for (; it < c.o->coarse_max_iter;) {
+    CK(launch_apply(c.m, degree, DG_F64, B, c.lambda, w->cp, w->cAp, c.st));
+    k_dot<<<g, kRedThreads, 0, c.st>>>(n, w->cp, w->cAp, w->cpartial);
+    k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_ALPHA, w->cscal, w->cpartial);
+    k_update_xr<<<g, kRedThreads, 0, c.st>>>(n, w->cscal, x, w->cr, w->cp, w->cAp, nullptr, w->cpartial);
+    k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_RR, w->cscal, w->cpartial);
+    k_dot<<<g, kRedThreads, 0, c.st>>>(n, w->cr, w->cr, w->cpartial);
+    k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_BETA, w->cscal, w->cpartial);
+    k_update_p<<<g, kRedThreads, 0, c.st>>>(n, w->cscal, w->cr, w->cp, 0);
+    ++it;
+    if (it % chk == 0 || it == c.o->coarse_max_iter) {
+      CK(cudaMemcpyAsync(w->h_scal, w->cscal, sizeof(double) * B * kNS, cudaMemcpyDeviceToHost, c.st));
+      CK(cudaStreamSynchronize(c.st));
+      bool any = false;
+      for (int b = 0; b < B; ++b) any = any || w->h_scal[b * kNS + S_ACTIVE] != 0.0;
+      if (!any) break;
+    }
+  }
+  iters_out = it;
+  return cudaGetLastError();
+}
+
+template <typename T>
+std::vector<LevelVecs<T>>& levels(Workspace* w);
+template <>
+std::vector<LevelVecs<float>>& levels<float>(Workspace* w) { return w->lv32; }
+template <>
+std::vector<LevelVecs<double>>& levels<double>(Workspace* w) { return w->lv64; }
+
+template <typename T>
+const T* transfer_ptr(dg_mesh* m, int Nf, int Nc);
+template <>
+const float* transfer_ptr<float>(dg_mesh* m, int Nf, int Nc) { return m->transfer[std::make_pair(Nf, Nc)].P32; }
+template <>
+const double* transfer_ptr<double>(dg_mesh* m, int Nf, int Nc) { return m->transfer[std::make_pair(Nf, Nc)].P64; }
+
+template <typename T>
+constexpr dg_prec prec_of() { return std::is_same<T, double>::value ? DG_F64 : DG_F32; }
+
+// Chebyshev smoothing of the given degree on level l.
+template <typename T>
+cudaError_t chebyshev(Ctx& c, int l, bool zero_x) {
+  LevelVecs<T>& v = levels<T>(c.w)[l];
+  const int deg = c.o->degrees[l];
+  const int64_t n = int64_t(c.m->K) * npd(deg);
+  const int64_t nt = n * c.B;
+  const double rho = c.w->rho[l];
+  const double lmin = rho / 10.0, lmax = 1.1 * rho;
+  const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
+  double rk = 1.0 / sigma;
+  if (!zero_x) {
+    CK(launch_apply(c.m, deg, prec_of<T>(), c.B, c.lambda, v.x, v.Ad, c.st));
+    k_sub<T><<<egrid(nt), 256, 0, c.st>>>(nt, v.rhs, v.Ad, v.res);
+  }
+  k_cheb_first<T><<<egrid(nt), 256, 0, c.st>>>(n, nt, v.dinv, v.rhs, v.res, v.d, v.x, T(1.0 / theta), zero_x ? 1 : 0);
+  for (int k = 1; k < c.o->cheb_degree; ++k) {
+    CK(launch_apply(c.m, deg, prec_of<T>(), c.B, c.lambda, v.d, v.Ad, c.st));
+    const double rnew = 1.0 / (2.0 * sigma - rk);
+    k_cheb_step<T><<<egrid(nt), 256, 0, c.st>>>(n, nt, v.dinv, v.Ad, v.res, v.d, v.x, T(rnew * rk), T(2.0 * rnew / delta));
+    rk = rnew;
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t vcycle(Ctx& c, int l, int& coarse_iters) {
+  std::vector<LevelVecs<T>>& lv = levels<T>(c.w);
+  const int L = c.o->nlevels;
+  const int deg = c.o->degrees[l];
+  const int64_t n = int64_t(c.m->K) * npd(deg);
+  const int64_t nt = n * c.B;
+  if (l == L - 1) {
+    // coarsest degree: CG in FP64 whatever the level precision
+    int it = 0;
+    if (std::is_same<T, double>::value) {
+      CK(coarse_cg(c, deg, reinterpret_cast<const double*>(lv[l].rhs), reinterpret_cast<double*>(lv[l].x), it));
+    } else {
+      k_convert<double, T><<<egrid(nt), 256, 0, c.st>>>(nt, lv[l].rhs, c.w->crhs);
+      CK(coarse_cg(c, deg, c.w->crhs, c.w->cx, it));
+      k_convert<T, double><<<egrid(nt), 256, 0, c.st>>>(nt, c.w->cx, lv[l].x);
+    }
+    coarse_iters += it;
+    return cudaGetLastError();
+  }
+  LevelVecs<T>& v = lv[l];
+  // pre-smoothing from x = 0, then res = rhs - A x
+  CK(chebyshev<T>(c, l, true));
+  CK(launch_apply(c.m, deg, prec_of<T>(), c.B, c.lambda, v.d, v.Ad, c.st));
+  k_sub<T><<<egrid(nt), 256, 0, c.st>>>(nt, v.res, v.Ad, v.res);
+  // restrict, recurse, prolong
+  const int degc = c.o->degrees[l + 1];
+  const int Npf = npd(deg), Npc = npd(degc);
+  const int64_t nE = int64_t(c.m->K) * c.B;
+  const T* P = transfer_ptr<T>(c.m, deg, degc);
+  k_restrict<T><<<int((nE * Npc + 255) / 256), 256, 0, c.st>>>(Npf, Npc, nE, P, v.res, lv[l + 1].rhs);
+  CK(vcycle<T>(c, l + 1, coarse_iters));
+  k_prolong<T><<<int((nE * Npf + 255) / 256), 256, 0, c.st>>>(Npf, Npc, nE, P, lv[l + 1].x, v.x);
+  // post-smoothing
+  CK(chebyshev<T>(c, l, false));
+  return cudaGetLastError();
+}
+
+// Largest eigenvalue of D^{-1}A on level l by power iteration from a seeded
+// random start (normalised on the host; setup cost only).
+template <typename T>
+cudaError_t power_rho(Ctx& c, int l, double& rho) {
+  LevelVecs<T>& v = levels<T>(c.w)[l];
+  const int deg = c.o->degrees[l];
+  const int64_t n = int64_t(c.m->K) * npd(deg);
+  std::vector<T> h(n);
+  std::mt19937_64 rng(12345 + deg);
+  std::normal_distribution<double> nd(0.0, 1.0);
+  for (auto& e : h) e = T(nd(rng));
+  CK(cudaMemcpyAsync(v.d, h.data(), n * sizeof(T), cudaMemcpyHostToDevice, c.st));
+  const dim3 g = vgrid(n, 1);
+  std::vector<double> hp(kRedBlocks * 2);
+  auto norm = [&](const T* a, double& out) -> cudaError_t {
+    k_dot<T, T><<<g, kRedThreads, 0, c.st>>>(n, a, a, c.w->partial);
+    CK(cudaMemcpyAsync(hp.data(), c.w->partial, sizeof(double) * kRedBlocks * 2, cudaMemcpyDeviceToHost, c.st));
+    CK(cudaStreamSynchronize(c.st));
+    double s = 0.0;
+    for (unsigned k = 0; k < g.x; ++k) s += hp[2 * k];
+    out = std::sqrt(s);
+    return cudaSuccess;
+  };
+  double nv = 1.0, lam = 0.0;
+  CK(norm(v.d, nv));
+  for (int it = 0; it < c.o->power_steps; ++it) {
+    k_scaled_copy<T><<<egrid(n), 256, 0, c.st>>>(n, T(1.0 / nv), v.d, v.x);  // x = d / ||d||
+    CK(launch_apply(c.m, deg, prec_of<T>(), 1, c.lambda, v.x, v.Ad, c.st));
+    k_scale<T, T><<<egrid(n), 256, 0, c.st>>>(n, n, v.dinv, v.Ad, v.d);    // d = D^{-1} A x
+    CK(norm(v.d, nv));
+    lam = nv;
+  }
+  rho = lam;
+  return cudaGetLastError();
+}
+
+cudaError_t setup_pmg(Ctx& c, std::string& key) {
+  Workspace* w = c.w;
+  const dg_solver_opts* o = c.o;
+  char buf[64];
+  std::snprintf(buf, sizeof buf, "%.17g/%d/%d", c.lambda, o->power_steps, o->mixed);
+  key = buf;
+  if (w->dinv_key == key && !w->rho.empty()) return cudaSuccess;
+  w->rho.assign(o->nlevels, 0.0);
+  for (int l = 0; l < o->nlevels; ++l) {
+    const int deg = o->degrees[l];
+    const int64_t n = int64_t(c.m->K) * npd(deg);
+    if (o->mixed) {
+      CK(launch_diagonal(c.m, deg, DG_F32, c.lambda, w->lv32[l].dinv, c.st));
+      k_recip<float><<<egrid(n), 256, 0, c.st>>>(n, w->lv32[l].dinv);
+      if (l + 1 < o->nlevels) CK(power_rho<float>(c, l, w->rho[l]));
+    } else {
+      CK(launch_diagonal(c.m, deg, DG_F64, c.lambda, w->lv64[l].dinv, c.st));
+      k_recip<double><<<egrid(n), 256, 0, c.st>>>(n, w->lv64[l].dinv);
+      if (l + 1 < o->nlevels) CK(power_rho<double>(c, l, w->rho[l]));
+    }
+  }
+  w->dinv_key = key;
+  return cudaGetLastError();
+}
+
+// z = M^{-1} r for the outer iteration
+cudaError_t precondition(Ctx& c, int& coarse_iters) {
+  Workspace* w = c.w;
+  const int64_t n = int64_t(c.m->K) * npd(c.m->N);
+  const int64_t nt = n * c.B;
+  switch (c.o->precond) {
+    case DG_PREC_NONE:
+      CK(cudaMemcpyAsync(w->z, w->r, nt * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
+      break;
+    case DG_PREC_JACOBI:
+      k_scale<double, double><<<egrid(nt), 256, 0, c.st>>>(n, nt, w->dinv, w->r, w->z);
+      break;
+    case DG_PREC_INVMASS: {
+      const int Np = npd(c.m->N);
+      const double* Minv = reinterpret_cast<const double*>(c.m->ops64[c.m->N].buf) + (ops_count(c.m->N) - size_t(Np) * Np);
+      k_invmass<<<int((nt + 255) / 256), 256, 0, c.st>>>(Np, c.m->K, c.B, c.m->geo64, Minv, c.lambda, w->r, w->z);
+      break;
+    }
+    case DG_PREC_PMG:
+      if (c.o->mixed) {
+        k_convert<float, double><<<egrid(nt), 256, 0, c.st>>>(nt, w->r, w->lv32[0].rhs);
+        CK(vcycle<float>(c, 0, coarse_iters));
+        k_convert<double, float><<<egrid(nt), 256, 0, c.st>>>(nt, w->lv32[0].x, w->z);
+      } else {
+        CK(cudaMemcpyAsync(w->lv64[0].rhs, w->r, nt * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
+        CK(vcycle<double>(c, 0, coarse_iters));
+        CK(cudaMemcpyAsync(w->z, w->lv64[0].x, nt * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
+      }
+      break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// Outer (flexible) PCG. Returns a cudaError_t; solver status in `status`.
+cudaError_t pcg_run(Ctx& c, const double* b, double* x, dg_solve_info* info, dg_status& status) {
+  CK(setup_workspace(c));
+  c.w = c.m->ws;
+  Workspace* w = c.w;
+  const dg_solver_opts* o = c.o;
+  const int B = c.B;
+  const int64_t n = int64_t(c.m->K) * npd(c.m->N);
+  const int64_t nt = n * B;
+  const dim3 g = vgrid(n, B);
+  const bool flexible = o->precond == DG_PREC_PMG;
+  std::string key;
+  if (o->precond == DG_PREC_JACOBI) {
+    char buf[48];
+    std::snprintf(buf, sizeof buf, "jac/%.17g", c.lambda);
+    if (w->dinv_key != buf) {
+      CK(launch_diagonal(c.m, c.m->N, DG_F64, c.lambda, w->dinv, c.st));
+      k_recip<double><<<egrid(n), 256, 0, c.st>>>(n, w->dinv);
+      w->dinv_key = buf;
+    }
+  } else if (o->precond == DG_PREC_PMG) {
+    CK(setup_pmg(c, key));
+  }
+  CK(cudaEventRecord(w->ev0, c.st));
+  int coarse_iters = 0;
+  k_init_scal<<<1, 64, 0, c.st>>>(B, w->scal, o->tol * o->tol);
+  k_dot<<<g, kRedThreads, 0, c.st>>>(n, b, b, w->partial);
+  k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_INIT_BB, w->scal, w->partial);
+  CK(launch_apply(c.m, c.m->N, DG_F64, B, c.lambda, x, w->Ap, c.st));
+  k_sub<double><<<egrid(nt), 256, 0, c.st>>>(nt, b, w->Ap, w->r);
+  k_dot<<<g, kRedThreads, 0, c.st>>>(n, w->r, w->r, w->partial);
+  k_init_check<<<B, kRedThreads, 0, c.st>>>(w->scal, w->partial);
+  CK(precondition(c, coarse_iters));
+  k_dot<<<g, kRedThreads, 0, c.st>>>(n, w->r, w->z, w->partial);
+  k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_INIT_RZ, w->scal, w->partial);
+  k_update_p<<<g, kRedThreads, 0, c.st>>>(n, w->scal, w->z, w->p, 1);
+  CK(cudaMemcpyAsync(w->h_scal, w->scal, sizeof(double) * B * kNS, cudaMemcpyDeviceToHost, c.st));
+  CK(cudaStreamSynchronize(c.st));
+  bool any = false;
+  for (int bb = 0; bb < B; ++bb) any = any || w->h_scal[bb * kNS + S_ACTIVE] != 0.0;
+  int it = 0;
+  const int chk = (o->precond == DG_PREC_PMG) ? 1 : 4;
+  while (any && it < o->max_iter) {
+    CK(launch_apply(c.m, c.m->N, DG_F64, B, c.lambda, w->p, w->Ap, c.st));
+    k_dot<<<g, kRedThreads, 0, c.st>>>(n, w->p, w->Ap, w->partial);
+    k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_ALPHA, w->scal, w->partial);
+    k_update_xr<<<g, kRedThreads, 0, c.st>>>(n, w->scal, x, w->r, w->p, w->Ap, flexible ? w->z : nullptr, w->partial);
+    k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_RR, w->scal, w->partial);
+    ++it;
+    if (it % chk == 0 || it == o->max_iter) {
+      CK(cudaMemcpyAsync(w->h_scal, w->scal, sizeof(double) * B * kNS, cudaMemcpyDeviceToHost, c.st));
+      CK(cudaStreamSynchronize(c.st));
+      any = false;
+      for (int bb = 0; bb < B; ++bb) any = any || w->h_scal[bb * kNS + S_ACTIVE] != 0.0;
+      if (!any) break;
+    }
+    CK(precondition(c, coarse_iters));
+    k_dot<<<g, kRedThreads, 0, c.st>>>(n, w->r, w->z, w->partial);
+    k_finalize<<<B, kRedThreads, 0, c.st>>>(flexible ? FIN_BETA_FLEX : FIN_BETA, w->scal, w->partial);
+    k_update_p<<<g, kRedThreads, 0, c.st>>>(n, w->scal, w->z, w->p, 0);
+  }
+  CK(cudaEventRecord(w->ev1, c.st));
+  CK(cudaMemcpyAsync(w->h_scal, w->scal, sizeof(double) * B * kNS, cudaMemcpyDeviceToHost, c.st));
+  CK(cudaStreamSynchronize(c.st));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, w->ev0, w->ev1));
+  status = DG_OK;
+  for (int bb = 0; bb < B; ++bb) {
+    const double* s = w->h_scal + bb * kNS;
+    if (s[S_BREAK] != 0.0) status = DG_ERR_BREAKDOWN;
+    else if (s[S_ACTIVE] != 0.0 && status == DG_OK) status = DG_ERR_NOT_CONVERGED;
+  }
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    for (int bb = 0; bb < B; ++bb) {
+      info->iters[bb] = int(w->h_scal[bb * kNS + S_ITERS]);
+      info->relres[bb] = w->h_scal[bb * kNS + S_RELRES];
+    }
+    info->total_iters = it;
+    info->ms = ms;
+  }
+  (void)coarse_iters;
+  return cudaSuccess;
+}
+
+}  // namespace dgx
+
+using namespace dgx;
+
+extern "C" {
+
+void dg_solver_opts_default(dg_solver_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->tol = 1e-10;
+  o->max_iter = 1000;
+  o->precond = DG_PREC_JACOBI;
+  o->nlevels = 0;
+  o->cheb_degree = 2;
+  o->coarse_tol = 1e-2;
+  o->coarse_max_iter = 500;
+  o->mixed = 1;
+  o->power_steps = 20;
+}
+
+dg_status dg_pcg_solve(dg_mesh* m, const dg_solver_opts* o, int B, double lambda, const double* b, double* x,
+                       dg_solve_info* info, void* stream) {
+  if (!m || !o || !b || !x) { set_error("NULL argument"); return DG_ERR_ARG; }
+  if (B < 1 || B > DG_MAX_BATCH) { set_error("batch must be in 1..64"); return DG_ERR_ARG; }
+  if (!(o->tol > 0.0) || o->max_iter < 0) { set_error("tol must be > 0 and max_iter >= 0"); return DG_ERR_ARG; }
+  if (!std::isfinite(lambda) || lambda < 0) { set_error("lambda must be finite and >= 0"); return DG_ERR_ARG; }
+  if (o->precond < DG_PREC_NONE || o->precond > DG_PREC_PMG) { set_error("unknown preconditioner"); return DG_ERR_ARG; }
+  if (o->precond == DG_PREC_INVMASS && !(lambda > 0)) { set_error("inverse-mass preconditioner needs lambda > 0"); return DG_ERR_ARG; }
+  if (o->precond == DG_PREC_PMG) {
+    if (o->nlevels < 2 || o->nlevels > 8 || o->degrees[0] != m->N) {
+      set_error("p-multigrid needs 2..8 levels starting at the mesh degree");
+      return DG_ERR_ARG;
+    }
+    for (int l = 1; l < o->nlevels; ++l)
+      if (o->degrees[l] >= o->degrees[l - 1] || o->degrees[l] < 1) {
+        set_error("p-multigrid degrees must strictly decrease to >= 1");
+        return DG_ERR_ARG;
+      }
+    if (o->cheb_degree < 1 || o->power_steps < 1 || !(o->coarse_tol > 0) || o->coarse_max_iter < 1) {
+      set_error("bad multigrid smoother/coarse options");
+      return DG_ERR_ARG;
+    }
+  }
+  try {
+    Ctx c{m, o, B, lambda, (cudaStream_t)stream, m->ws};
+    dg_status st = DG_OK;
+    cudaError_t e = pcg_run(c, b, x, info, st);
+    if (e != cudaSuccess) {
+      set_error(std::string("dg_pcg_solve: ") + cudaGetErrorString(e));
+      return e == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA;
+    }
+    if (st == DG_ERR_NOT_CONVERGED) set_error("dg_pcg_solve: max_iter reached before tol");
+    if (st == DG_ERR_BREAKDOWN) set_error("dg_pcg_solve: non-positive or non-finite p^T A p or residual");
+    return st;
+  } catch (const std::exception& ex) {
+    set_error(ex.what());
+    return DG_ERR_ARG;
+  }
+}
+
+}  // extern "C"

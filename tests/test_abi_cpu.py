@@ -1,0 +1,91 @@
+"""CPU-only checks of the C-ABI library: it loads, exports every declared
+symbol, and its host-side logic (reference element, transfer operators,
+argument and mesh validation) agrees with the oracle. No GPU call is made."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from dg_inputs import jittered_grid
+from oracle import refops
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_1801_00246_gb300 as P
+    from paper_1801_00246_gb300 import build
+    build.build()
+    return P
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(dg_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+def test_library_exports_every_declared_symbol(P):
+    L = P.lib()
+    names = _declared()
+    assert "dg_poisson_apply" in names and "dg_pcg_solve" in names
+    for n in sorted(names):
+        assert hasattr(L, n), n
+
+
+@pytest.mark.parametrize("N", range(1, 9))
+def test_library_reference_element_matches_oracle(P, N):
+    a = P.reference_operators(N)
+    o = refops.reference_operators(N)
+    assert np.abs(a["r"] - o["r"]).max() < 1e-14 and np.abs(a["s"] - o["s"]).max() < 1e-14
+    for k in ("M", "Dr", "Ds", "Mf"):
+        assert np.abs(a[k] - o[k]).max() < 1e-12 * max(1.0, np.abs(o[k]).max()), k
+    assert (a["fmask"] == np.array(o["faces"])).all()
+
+
+@pytest.mark.parametrize("Nf,Nc", [(8, 4), (4, 2), (2, 1), (6, 3), (3, 1), (8, 1)])
+def test_library_interpolation_matches_oracle(P, Nf, Nc):
+    assert np.abs(P.interpolation_matrix(Nf, Nc) - refops.interpolation(Nf, Nc)).max() < 1e-12
+
+
+def test_status_strings_and_argument_errors(P):
+    L = P.lib()
+    assert L.dg_status_string(0) == b"ok"
+    assert L.dg_status_string(4) == b"not converged"
+    m = jittered_grid(2, 2)
+    with pytest.raises(P.DgError) as ei:
+        P.Mesh(0, m.VX, m.VY, m.EToV, m.bc)
+    assert ei.value.name == "DG_ERR_ARG"
+    with pytest.raises(P.DgError) as ei:
+        P.Mesh(9, m.VX, m.VY, m.EToV, m.bc)
+    assert ei.value.name == "DG_ERR_ARG"
+
+
+def test_mesh_validation_rejects_bad_meshes_before_any_device_work(P):
+    m = jittered_grid(2, 2)
+    cw = m.EToV[:, ::-1].copy()          # clockwise elements
+    with pytest.raises(P.DgError) as ei:
+        P.Mesh(2, m.VX, m.VY, cw, m.bc)
+    assert ei.value.name == "DG_ERR_MESH"
+    bad = m.bc.copy()
+    bad[m.bc == 0] = 1                    # interior face tagged Dirichlet
+    with pytest.raises(P.DgError) as ei:
+        P.Mesh(2, m.VX, m.VY, m.EToV, bad)
+    assert ei.value.name == "DG_ERR_MESH"
+    bad = m.bc.copy()
+    bad[m.bc != 0] = 0                    # boundary face without a tag
+    with pytest.raises(P.DgError) as ei:
+        P.Mesh(2, m.VX, m.VY, m.EToV, bad)
+    assert ei.value.name == "DG_ERR_MESH"
+    e = m.EToV.copy()
+    e[0, 0] = 999                          # vertex index out of range
+    with pytest.raises(P.DgError) as ei:
+        P.Mesh(2, m.VX, m.VY, e, m.bc)
+    assert ei.value.name == "DG_ERR_ARG"

@@ -1,0 +1,113 @@
+"""GPU parity of the batched PCG / p-multigrid solves against the oracle.
+
+A GPU solution passes when the oracle's own residual ||b - A x|| / ||b||
+(FP64, assembled or matrix-free) is at most the requested 1e-10, and, where a
+direct solve is affordable, when it matches the direct solution."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from dg_inputs import config_mesh, jittered_grid, manufactured, uniform_field
+from dg_inputs.mesh import rotate_local_vertices
+from tests.gpu_util import cuda, pair, pkg, rel
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle_relres(ora, x, b, lam=0.0):
+    r = b - ora.apply(x, lam=lam)
+    return np.linalg.norm(r) / np.linalg.norm(b)
+
+
+def test_c1_jacobi_pcg_matches_direct_solve():
+    """16x16 jittered grid, N=3, Dirichlet, u = sin(pi x) sin(pi y)."""
+    m, N = config_mesh("c1_poisson_512tri_N3")
+    lib, ora = pair(m, N)
+    uex, fex = manufactured("sin_pi_x_sin_pi_y")
+    x_n, y_n = lib.nodes()
+    f = fex(x_n.cpu().numpy(), y_n.cpu().numpy())
+    g = uex(x_n.cpu().numpy(), y_n.cpu().numpy())
+    b = lib.rhs(cuda(f), cuda(g))
+    bo = ora.rhs(f, g)
+    assert rel(b.cpu().numpy(), bo) <= 1e-12
+    x, info = lib.solve(b, precond=pkg().PREC_JACOBI, tol=1e-10, max_iter=5000)
+    xs = x.cpu().numpy()
+    assert info["relres"][0] <= 1e-10
+    assert _oracle_relres(ora, xs, bo) <= 1e-10 * 1.5
+    xd = spla.spsolve(ora.assemble().tocsc(), bo.ravel()).reshape(xs.shape)
+    assert rel(xs, xd) <= 1e-7
+    assert ora.l2_error(xs, uex) < 1e-3
+
+
+@pytest.mark.parametrize("mixed", [1, 0])
+def test_pmg_fcg_small_mesh(mixed):
+    P = pkg()
+    m = rotate_local_vertices(jittered_grid(12, 12, seed=0), 1)
+    lib, ora = pair(m, 6)
+    uex, fex = manufactured("sin_2pi_x_cos_3pi_y")
+    f, g = fex(ora.x, ora.y), uex(ora.x, ora.y)
+    b = lib.rhs(cuda(f), cuda(g))
+    x, info = lib.solve(b, precond=P.PREC_PMG, degrees=[6, 3, 1], tol=1e-10, max_iter=200, mixed=mixed)
+    assert info["relres"][0] <= 1e-10
+    assert _oracle_relres(ora, x.cpu().numpy(), ora.rhs(f, g)) <= 1.5e-10
+    _, infoj = lib.solve(b, precond=P.PREC_JACOBI, tol=1e-10, max_iter=5000)
+    assert info["iters"][0] * 4 < infoj["iters"][0]
+
+
+def test_batched_solve_matches_individual_solves():
+    P = pkg()
+    m = rotate_local_vertices(jittered_grid(10, 8, seed=2), 5)
+    lib, ora = pair(m, 4)
+    bb = ora.mass_apply(uniform_field((4, m.K, ora.Np), seed=3))
+    xb, info = lib.solve(cuda(bb), precond=P.PREC_JACOBI, tol=1e-10, max_iter=5000)
+    for k in range(4):
+        xk, ik = lib.solve(cuda(bb[k]), precond=P.PREC_JACOBI, tol=1e-10, max_iter=5000)
+        assert ik["iters"][0] == info["iters"][k]
+        assert np.array_equal(xk.cpu().numpy(), xb[k].cpu().numpy())
+        assert _oracle_relres(ora, xb[k].cpu().numpy(), bb[k]) <= 1.5e-10
+
+
+def test_helmholtz_inverse_mass_batched():
+    """Two velocity components at once, lambda = 3/(2 nu dt) (Eq. INS_TD_3_2)."""
+    P = pkg()
+    m = rotate_local_vertices(jittered_grid(8, 8, seed=1), 2)
+    lib, ora = pair(m, 8)
+    lam = 3.0 / (2 * 0.025 * 0.01)
+    bb = ora.mass_apply(uniform_field((2, m.K, ora.Np), seed=4))
+    x, info = lib.solve(cuda(bb), lam=lam, precond=P.PREC_INVMASS, tol=1e-10, max_iter=500)
+    for k in range(2):
+        assert _oracle_relres(ora, x[k].cpu().numpy(), bb[k], lam=lam) <= 1.5e-10
+
+
+def test_not_converged_status_and_last_iterate():
+    P = pkg()
+    m = jittered_grid(6, 6, seed=0)
+    lib, ora = pair(m, 3)
+    b = cuda(ora.mass_apply(uniform_field((m.K, ora.Np), seed=1)))
+    x, info = lib.solve(b, precond=P.PREC_JACOBI, tol=1e-10, max_iter=3, check=False)
+    assert info["status"] == "DG_ERR_NOT_CONVERGED"
+    assert 0 < info["relres"][0] < 1.0
+    with pytest.raises(P.DgError) as ei:
+        lib.solve(b, precond=P.PREC_JACOBI, tol=1e-10, max_iter=3)
+    assert ei.value.name == "DG_ERR_NOT_CONVERGED"
+
+
+@pytest.mark.parametrize("mixed", [1, 0])
+def test_c2_pmg_32768tri_N6(mixed):
+    """128x128 jittered grid, N=6, V-cycle 6->3->1, 2 Chebyshev-Jacobi smooths,
+    degree-1 CG to 1e-2; u = sin(2 pi x) cos(3 pi y); tolerance 1e-10."""
+    P = pkg()
+    m, N = config_mesh("c2_pmg_32768tri_N6")
+    lib, ora = pair(m, N)
+    uex, fex = manufactured("sin_2pi_x_cos_3pi_y")
+    x_n, y_n = lib.nodes()
+    xn, yn = x_n.cpu().numpy(), y_n.cpu().numpy()
+    f, g = cuda(fex(xn, yn)), cuda(uex(xn, yn))
+    b = lib.rhs(f, g)
+    x, info = lib.solve(b, precond=P.PREC_PMG, degrees=[6, 3, 1], tol=1e-10, max_iter=300, mixed=mixed)
+    assert info["relres"][0] <= 1e-10
+    bo = ora.rhs(f.cpu().numpy(), g.cpu().numpy())
+    assert rel(b.cpu().numpy(), bo) <= 1e-12
+    xs = x.cpu().numpy()
+    assert _oracle_relres(ora, xs, bo) <= 1.5e-10
+    assert ora.l2_error(xs, uex) < 1e-6
