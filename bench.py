@@ -1,0 +1,352 @@
+"""Benchmark of the SIPDG pressure-Poisson hot path on one GB300.
+
+Workload (the headline configuration): 512x512 jittered grid split into
+524,288 triangles, degree N=8 (Np=45, 23.6M nodes), Dirichlet boundary.
+One step = one pass of the hot path over this input:
+  * Poisson apply A u in FP64 and in FP32 (U(-1,1) input, seed 1)
+  * Helmholtz apply (lambda = 1) in FP64 and in FP32
+  * a p-multigrid flexible-CG pressure solve to 1e-10 (V-cycle 8->4->2->1,
+    degree-2 Chebyshev-Jacobi smoothing, degree-1 CG to 1e-2), mixed precision
+    (FP32 multigrid levels, FP64 outer iteration)
+  * the same solve in plain FP64 (FP64 multigrid levels)
+`value` is the FP64 Poisson apply throughput (GDOF/s = K*Np / apply time);
+the other pieces are reported beside it. L2 (135 MB) is flushed by writing a
+256 MB buffer before every timed launch; all timing is CUDA events on the
+launching stream.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+`--impl reference` times the FP64 CPU oracle (the method written plainly in
+numpy) on a bounded sample of the same workload, on the host cores.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MESH_NAME = "c5_sweep_524288tri_N8"
+METRIC = "Poisson Ax GDOF/s & PCG solve ms (N=8, 524k tri), mixed vs FP64, % HBM roof"
+PMG_DEGREES = [8, 4, 2, 1]
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    hbm = 6800.0
+    src = "fallback"
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        hbm = float(d.get("hbm_gbs", hbm))
+        src = "measured"
+    # FP64 CUDA-core peak: the nominal 1.25 TFLOP/s of GB300 (no measured copy in the peaks file)
+    return dict(hbm_gbs=hbm, hbm_src=src, fp64_gflops=1250.0, fp32_gflops=2 * 152 * 128 * 2.07)
+
+
+def algo_per_element(N, word):
+    """Algorithmic bytes and flops per element of one apply (B = 1).
+
+    bytes: read u and write A u (2 Np words) + 4 geometry words + 3 int32
+    neighbour words; flops: 10 Np^2 + 24 Np Nfp (gradient, lift of jumps,
+    divergence, neighbour normal derivatives, lift of the flux, mass)."""
+    Np = (N + 1) * (N + 2) // 2
+    Nfp = N + 1
+    return 2 * Np * word + 4 * word + 12, 10 * Np * Np + 24 * Np * Nfp
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    def __init__(self, index):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks.csv") if os.path.isdir(
+            os.path.join(ROOT, "gpurun_out")) else "/tmp/dg_clocks.csv"
+        self.index = index
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        hi = [s for s in sm if s > 0.5 * max(sm)]
+        return {"sm_mhz": float(np.median(hi)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def cpu_oracle_sample(N, n_elems, reps=1, seed=1):
+    """Time the FP64 oracle apply on a bounded sample of the workload."""
+    from dg_inputs import config_mesh, uniform_field
+    from oracle.sipdg import Sipdg
+    m, _ = config_mesh(MESH_NAME)
+    ora = Sipdg(m.VX, m.VY, m.EToV, m.bc, N)
+    u = uniform_field((m.K, ora.Np), seed=seed)
+    elems = np.linspace(0, m.K - 1, n_elems).astype(np.int64)
+    ora.apply(u, elems=elems[:64])  # warm caches
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        ora.apply(u, elems=elems)
+        times.append(time.perf_counter() - t0)
+    return ora, times
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    N = 8
+    n_elems = 3072
+    ora, _ = cpu_oracle_sample(N, 64, reps=1)
+    from dg_inputs import config_mesh, uniform_field
+    m, _ = config_mesh(MESH_NAME)
+    u = uniform_field((m.K, ora.Np), seed=1)
+    elems = np.linspace(0, m.K - 1, n_elems).astype(np.int64)
+    for _ in range(args.warmup):
+        ora.apply(u, elems=elems[:256])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ora.apply(u, elems=elems)
+    dt = (time.perf_counter() - t0) / args.steps
+    val = n_elems * ora.Np / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "GDOF/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "512x512 jittered grid, 524288 triangles, N=8, Poisson apply (oracle sample)",
+                   "sample_elements": n_elems},
+        "cpu_baseline": {"value": val, "unit": "GDOF/s", "cores": 1, "kind": "oracle",
+                         "sample": f"FP64 oracle Poisson apply on {n_elems} of 524288 elements per step"},
+        "e2e": {"value": val, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    import paper_1801_00246_gb300 as P
+    from paper_1801_00246_gb300 import build
+    from dg_inputs import config_mesh, manufactured, uniform_field
+
+    torch.cuda.set_device(local)
+    if rank == 0:
+        build.build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    L = P.lib()
+    N = 8
+    m, _ = config_mesh(MESH_NAME)
+    mesh = P.Mesh.from_inputs(m, N)
+    K, Np = mesh.K, mesh.Np
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    u64 = torch.from_numpy(uniform_field((K, Np), seed=1)).to(dev)
+    u32 = u64.float()
+    out64 = torch.empty_like(u64)
+    out32 = torch.empty_like(u32)
+    xn, yn = mesh.nodes()
+    uex, fex = manufactured("sin_2pi_x_cos_3pi_y")
+    xh, yh = xn.cpu().numpy(), yn.cpu().numpy()
+    b = mesh.rhs(torch.from_numpy(fex(xh, yh)).to(dev), torch.from_numpy(uex(xh, yh)).to(dev))
+    flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    opts_mixed = P._binding.default_opts(precond=P.PREC_PMG, degrees=PMG_DEGREES, tol=1e-10, max_iter=200,
+                                         mixed=1, cheb_degree=2, coarse_tol=1e-2, coarse_max_iter=500)
+    opts_fp64 = P._binding.default_opts(precond=P.PREC_PMG, degrees=PMG_DEGREES, tol=1e-10, max_iter=200,
+                                        mixed=0, cheb_degree=2, coarse_tol=1e-2, coarse_max_iter=500)
+
+    def flush():
+        flush_buf.fill_(1.0)
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        flush()
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        return e0, e1, r
+
+    def step(record):
+        ev = {}
+        ev["poisson_f64"] = timed(lambda: mesh.apply(u64, out=out64))
+        ev["poisson_f32"] = timed(lambda: mesh.apply(u32, out=out32))
+        ev["helmholtz_f64"] = timed(lambda: mesh.apply(u64, lam=1.0, out=out64))
+        ev["helmholtz_f32"] = timed(lambda: mesh.apply(u32, lam=1.0, out=out32))
+        x_m = torch.zeros_like(b)
+        ev["solve_mixed"] = timed(lambda: mesh.solve(b, x_m, opts=opts_mixed))
+        x_d = torch.zeros_like(b)
+        ev["solve_fp64"] = timed(lambda: mesh.solve(b, x_d, opts=opts_fp64))
+        if record is not None:
+            torch.cuda.synchronize()
+            for k, (e0, e1, r) in ev.items():
+                record.setdefault(k, []).append(e0.elapsed_time(e1))
+                if k.startswith("solve"):
+                    record.setdefault(k + "_iters", []).append(r[1]["iters"][0])
+                    record.setdefault(k + "_relres", []).append(r[1]["relres"][0])
+
+    for _ in range(args.warmup):
+        step(None)
+    torch.cuda.synchronize()
+    rec = {}
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    n0 = L.dg_launch_count()
+    with Clocks(local) as clk:
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(args.steps):
+            step(rec)
+        s1.record(stream)
+        torch.cuda.synchronize()
+    launches = int(L.dg_launch_count() - n0)
+    total_ms = s0.elapsed_time(s1)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms, float(np.mean(rec["poisson_f64"]))], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms, ax_ms_max = float(t[0]), float(t[1])
+    else:
+        ax_ms_max = float(np.mean(rec["poisson_f64"]))
+    clocks = clk.summary()
+
+    # end to end through the public API from pinned host buffers
+    uh = torch.from_numpy(uniform_field((K, Np), seed=1)).pin_memory()
+    oh = torch.empty_like(uh).pin_memory()
+    e2e_ms = []
+    for it in range(args.warmup + args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        flush()
+        e0.record(stream)
+        ud = uh.to(dev, non_blocking=True)
+        r = mesh.apply(ud)
+        oh.copy_(r, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+
+    pk = peaks()
+    bytes64, flops = algo_per_element(N, 8)
+    bytes32, _ = algo_per_element(N, 4)
+    ax = {}
+    for k in ("poisson_f64", "poisson_f32", "helmholtz_f64", "helmholtz_f32"):
+        ms = float(np.mean(rec[k]))
+        bpe = bytes64 if k.endswith("f64") else bytes32
+        fl = flops + (2 * Np * Np if k.startswith("helmholtz") else 0)
+        ax[k] = {"ms": ms, "gdofs": K * Np / (ms * 1e-3) / 1e9,
+                 "hbm_frac": K * bpe / (ms * 1e-3) / 1e9 / pk["hbm_gbs"],
+                 "gflops": K * fl / (ms * 1e-3) / 1e9}
+    value = world * K * Np / (ax_ms_max * 1e-3) / 1e9
+    fp64_ms = ax["poisson_f64"]["ms"]
+    achieved = K * flops / (fp64_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "512x512 jittered grid (jitter 0.1h, seed 0), 524288 triangles, N=8 (Np=45), "
+                               "Dirichlet; Poisson apply FP64 (value), FP32, Helmholtz, pMG-FCG solves",
+                   "K": K, "N": N, "Np": Np, "batch": 1, "pmg_degrees": PMG_DEGREES,
+                   "l2": "256 MB buffer written before every timed launch",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "ax": ax,
+        "pcg_solve_ms": {"mixed": float(np.mean(rec["solve_mixed"])), "fp64": float(np.mean(rec["solve_fp64"])),
+                         "iters_mixed": int(rec["solve_mixed_iters"][-1]),
+                         "iters_fp64": int(rec["solve_fp64_iters"][-1]),
+                         "relres_mixed": float(rec["solve_mixed_relres"][-1]),
+                         "relres_fp64": float(rec["solve_fp64_relres"][-1])},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": pk["fp64_gflops"], "unit": "GFLOP/s",
+                     "frac": achieved / pk["fp64_gflops"], "traffic": None,
+                     "kernel": "sipdg_apply_kernel<8,double> (FP64 Poisson apply)",
+                     "peak_src": "nominal GB300 FP64 1.25 TFLOP/s"},
+        "e2e": {"value": K * Np / (float(np.mean(e2e_ms)) * 1e-3) / 1e9, "unit": "GDOF/s",
+                "h2d_bytes_per_step": int(uh.numel() * 8), "d2h_bytes_per_step": int(oh.numel() * 8)},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        _, times = cpu_oracle_sample(N, 2048, reps=3)
+        cv = 2048 * Np / float(np.min(times)) / 1e9
+        line["cpu_baseline"] = {"value": cv, "unit": "GDOF/s", "cores": 1, "kind": "oracle",
+                                "sample": "FP64 oracle Poisson apply on 2048 of the 524288 elements (numpy, one core)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

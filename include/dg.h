@@ -158,6 +158,10 @@ dg_status dg_reference_operators(int N, double* r, double* s, double* M, double*
  * evaluated at the fine nodes. */
 dg_status dg_interpolation_matrix(int Nf, int Nc, double* P);
 
+/* Number of kernels this library has launched since it was loaded (all
+ * devices and threads); a diagnostic for counting launches in a timed region. */
+uint64_t dg_launch_count(void);
+
 const char* dg_status_string(dg_status status);
 const char* dg_last_error(void);
 

@@ -67,6 +67,7 @@ def lib():
         "dg_interpolation_matrix": ([i32, i32, pd], i32),
         "dg_status_string": ([i32], ctypes.c_char_p),
         "dg_last_error": ([], ctypes.c_char_p),
+        "dg_launch_count": ([], ctypes.c_uint64),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)

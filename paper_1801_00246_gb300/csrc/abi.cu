@@ -187,12 +187,14 @@ cudaError_t launch_diagonal(const dg_mesh* m, int degree, dg_prec prec, double l
   const int64_t n = m->K * Np;
   const int blocks = int((n + 255) / 256);
   const OpsLayout L(degree);
-  if (prec == DG_F64)
+  if (prec == DG_F64) {
     diagonal_kernel<double><<<blocks, 256, 0, st>>>(degree, m->K, m->geo64, m->conn,
                                                      (const double*)m->ops64[degree].buf, L, lambda, (double*)diag);
-  else
+  } else {
     diagonal_kernel<float><<<blocks, 256, 0, st>>>(degree, m->K, m->geo32, m->conn,
                                                     (const float*)m->ops32[degree].buf, L, float(lambda), (float*)diag);
+  }
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -201,7 +203,7 @@ cudaError_t launch_rhs(const dg_mesh* m, int B, const double* f, const double* g
   const int64_t n = int64_t(B) * m->K * Np;
   const OpsLayout L(m->N);
   rhs_kernel<<<int((n + 255) / 256), 256, 0, st>>>(m->N, m->K, B, m->geo64, m->conn, (const double*)m->ops64[m->N].buf,
-                                                   L, f, g, b);
+                                                   L, f, g, b); note_launch();
   return cudaGetLastError();
 }
 
@@ -227,6 +229,8 @@ static dg_status cuda_fail(cudaError_t err, const char* what) {
 }
 
 extern "C" {
+
+uint64_t dg_launch_count(void) { return launch_count(); }
 
 const char* dg_status_string(dg_status s) {
   switch (s) {
@@ -337,14 +341,15 @@ dg_status dg_mesh_nodes(const dg_mesh* mc, int degree, double* x, double* y, voi
 
 dg_status dg_operator_apply(const dg_mesh* mc, int degree, dg_prec prec, int B, double lambda, const void* u, void* Au,
                             void* stream) {
-  if (!mc || !u || !Au) { set_error("NULL argument"); return DG_ERR_ARG; }
+  if (!mc) { set_error("mesh is NULL"); return DG_ERR_ARG; }
+  if (B == 0) return DG_OK;  // empty batch: nothing to read or write
+  if (!u || !Au) { set_error("NULL argument"); return DG_ERR_ARG; }
   if (degree == 0) degree = mc->N;
   if (degree < 1 || degree > kMaxN) { set_error("degree must be in 1..8"); return DG_ERR_ARG; }
   if (prec != DG_F64 && prec != DG_F32) { set_error("bad precision"); return DG_ERR_ARG; }
   if (B < 0) { set_error("negative batch"); return DG_ERR_ARG; }
   if (u == Au) { set_error("u and Au must not alias"); return DG_ERR_ARG; }
   if (!std::isfinite(lambda) || lambda < 0) { set_error("lambda must be finite and >= 0"); return DG_ERR_ARG; }
-  if (B == 0) return DG_OK;
   DG_TRY_BEGIN
   dg_mesh* m = const_cast<dg_mesh*>(mc);
   cudaError_t ce = ensure_ops(m, degree);
@@ -378,9 +383,10 @@ dg_status dg_operator_diagonal(const dg_mesh* mc, int degree, dg_prec prec, doub
 }
 
 dg_status dg_rhs(const dg_mesh* m, int B, const double* f, const double* g, double* b, void* stream) {
-  if (!m || !f || !b) { set_error("NULL argument"); return DG_ERR_ARG; }
+  if (!m) { set_error("mesh is NULL"); return DG_ERR_ARG; }
   if (B < 0) { set_error("negative batch"); return DG_ERR_ARG; }
   if (B == 0) return DG_OK;
+  if (!f || !b) { set_error("NULL argument"); return DG_ERR_ARG; }
   cudaError_t ce = launch_rhs(m, B, f, g, b, (cudaStream_t)stream);
   if (ce != cudaSuccess) return cuda_fail(ce, "dg_rhs");
   return DG_OK;

@@ -356,7 +356,7 @@ cudaError_t launch_t(const dg_mesh* m, int B, double lambda, const void* u, void
                                                  : reinterpret_cast<const T*>(m->geo32);
   const T* ops = reinterpret_cast<const T*>(std::is_same<T, double>::value ? m->ops64[N].buf : m->ops32[N].buf);
   kern<<<grid, kThreads, c.smem, st>>>(m->K, B, geo, m->conn, ops, T(lambda), reinterpret_cast<const T*>(u),
-                                       reinterpret_cast<T*>(Au));
+                                       reinterpret_cast<T*>(Au)); note_launch();
   return cudaGetLastError();
 }
 

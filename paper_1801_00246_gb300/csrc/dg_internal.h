@@ -91,4 +91,8 @@ cudaError_t launch_nodes(const dg_mesh* m, int degree, double* x, double* y, cud
 
 void set_error(const std::string& msg);
 
+// Running count of kernels this library has launched (all devices, all threads).
+void note_launch();
+uint64_t launch_count();
+
 }  // namespace dgx

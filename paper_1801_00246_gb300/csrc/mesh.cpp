@@ -1,6 +1,7 @@
 // Host-side mesh setup: affine geometric factors (Section 5.2, Eq. operators2,
 // elementOps), face connectivity, and the checks that guard every later launch.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -12,6 +13,9 @@
 namespace dgx {
 
 static thread_local std::string g_last_error;
+static std::atomic<uint64_t> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+uint64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 void set_error(const std::string& msg) { g_last_error = msg; }
 const char* last_error() { return g_last_error.c_str(); }
 

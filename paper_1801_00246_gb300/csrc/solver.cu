@@ -457,23 +457,23 @@ cudaError_t coarse_cg(Ctx& c, int degree, const double* rhs, double* x, int& ite
   const double tol = c.o->coarse_tol;
   CK(cudaMemsetAsync(x, 0, nt * sizeof(double), c.st));
   CK(cudaMemcpyAsync(w->cr, rhs, nt * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
-  k_init_scal<<<1, 64, 0, c.st>>>(B, w->cscal, tol * tol);
-  k_dot<<<g, kRedThreads, 0, c.st>>>(n, rhs, rhs, w->cpartial);
-  k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_INIT_BB, w->cscal, w->cpartial);
-  k_init_check<<<B, kRedThreads, 0, c.st>>>(w->cscal, w->cpartial);  // r = b: r.r = b.b
-  k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_INIT_RZ, w->cscal, w->cpartial);
-  k_update_p<<<g, kRedThreads, 0, c.st>>>(n, w->cscal, w->cr, w->cp, 1);
+  k_init_scal<<<1, 64, 0, c.st>>>(B, w->cscal, tol * tol); note_launch();
+  k_dot<<<g, kRedThreads, 0, c.st>>>(n, rhs, rhs, w->cpartial); note_launch();
+  k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_INIT_BB, w->cscal, w->cpartial); note_launch();
+  k_init_check<<<B, kRedThreads, 0, c.st>>>(w->cscal, w->cpartial); note_launch();  // r = b: r.r = b.b
+  k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_INIT_RZ, w->cscal, w->cpartial); note_launch();
+  k_update_p<<<g, kRedThreads, 0, c.st>>>(n, w->cscal, w->cr, w->cp, 1); note_launch();
   const int chk = 8;
   int it = 0;
   for (; it < c.o->coarse_max_iter;) {
     CK(launch_apply(c.m, degree, DG_F64, B, c.lambda, w->cp, w->cAp, c.st));
-    k_dot<<<g, kRedThreads, 0, c.st>>>(n, w->cp, w->cAp, w->cpartial);
-    k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_ALPHA, w->cscal, w->cpartial);
-    k_update_xr<<<g, kRedThreads, 0, c.st>>>(n, w->cscal, x, w->cr, w->cp, w->cAp, nullptr, w->cpartial);
-    k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_RR, w->cscal, w->cpartial);
-    k_dot<<<g, kRedThreads, 0, c.st>>>(n, w->cr, w->cr, w->cpartial);
-    k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_BETA, w->cscal, w->cpartial);
-    k_update_p<<<g, kRedThreads, 0, c.st>>>(n, w->cscal, w->cr, w->cp, 0);
+    k_dot<<<g, kRedThreads, 0, c.st>>>(n, w->cp, w->cAp, w->cpartial); note_launch();
+    k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_ALPHA, w->cscal, w->cpartial); note_launch();
+    k_update_xr<<<g, kRedThreads, 0, c.st>>>(n, w->cscal, x, w->cr, w->cp, w->cAp, nullptr, w->cpartial); note_launch();
+    k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_RR, w->cscal, w->cpartial); note_launch();
+    k_dot<<<g, kRedThreads, 0, c.st>>>(n, w->cr, w->cr, w->cpartial); note_launch();
+    k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_BETA, w->cscal, w->cpartial); note_launch();
+    k_update_p<<<g, kRedThreads, 0, c.st>>>(n, w->cscal, w->cr, w->cp, 0); note_launch();
     ++it;
     if (it % chk == 0 || it == c.o->coarse_max_iter) {
       CK(cudaMemcpyAsync(w->h_scal, w->cscal, sizeof(double) * B * kNS, cudaMemcpyDeviceToHost, c.st));
@@ -517,13 +517,13 @@ cudaError_t chebyshev(Ctx& c, int l, bool zero_x) {
   double rk = 1.0 / sigma;
   if (!zero_x) {
     CK(launch_apply(c.m, deg, prec_of<T>(), c.B, c.lambda, v.x, v.Ad, c.st));
-    k_sub<T><<<egrid(nt), 256, 0, c.st>>>(nt, v.rhs, v.Ad, v.res);
+    k_sub<T><<<egrid(nt), 256, 0, c.st>>>(nt, v.rhs, v.Ad, v.res); note_launch();
   }
-  k_cheb_first<T><<<egrid(nt), 256, 0, c.st>>>(n, nt, v.dinv, v.rhs, v.res, v.d, v.x, T(1.0 / theta), zero_x ? 1 : 0);
+  k_cheb_first<T><<<egrid(nt), 256, 0, c.st>>>(n, nt, v.dinv, v.rhs, v.res, v.d, v.x, T(1.0 / theta), zero_x ? 1 : 0); note_launch();
   for (int k = 1; k < c.o->cheb_degree; ++k) {
     CK(launch_apply(c.m, deg, prec_of<T>(), c.B, c.lambda, v.d, v.Ad, c.st));
     const double rnew = 1.0 / (2.0 * sigma - rk);
-    k_cheb_step<T><<<egrid(nt), 256, 0, c.st>>>(n, nt, v.dinv, v.Ad, v.res, v.d, v.x, T(rnew * rk), T(2.0 * rnew / delta));
+    k_cheb_step<T><<<egrid(nt), 256, 0, c.st>>>(n, nt, v.dinv, v.Ad, v.res, v.d, v.x, T(rnew * rk), T(2.0 * rnew / delta)); note_launch();
     rk = rnew;
   }
   return cudaGetLastError();
@@ -542,9 +542,9 @@ cudaError_t vcycle(Ctx& c, int l, int& coarse_iters) {
     if (std::is_same<T, double>::value) {
       CK(coarse_cg(c, deg, reinterpret_cast<const double*>(lv[l].rhs), reinterpret_cast<double*>(lv[l].x), it));
     } else {
-      k_convert<double, T><<<egrid(nt), 256, 0, c.st>>>(nt, lv[l].rhs, c.w->crhs);
+      k_convert<double, T><<<egrid(nt), 256, 0, c.st>>>(nt, lv[l].rhs, c.w->crhs); note_launch();
       CK(coarse_cg(c, deg, c.w->crhs, c.w->cx, it));
-      k_convert<T, double><<<egrid(nt), 256, 0, c.st>>>(nt, c.w->cx, lv[l].x);
+      k_convert<T, double><<<egrid(nt), 256, 0, c.st>>>(nt, c.w->cx, lv[l].x); note_launch();
     }
     coarse_iters += it;
     return cudaGetLastError();
@@ -553,15 +553,15 @@ cudaError_t vcycle(Ctx& c, int l, int& coarse_iters) {
   // pre-smoothing from x = 0, then res = rhs - A x
   CK(chebyshev<T>(c, l, true));
   CK(launch_apply(c.m, deg, prec_of<T>(), c.B, c.lambda, v.d, v.Ad, c.st));
-  k_sub<T><<<egrid(nt), 256, 0, c.st>>>(nt, v.res, v.Ad, v.res);
+  k_sub<T><<<egrid(nt), 256, 0, c.st>>>(nt, v.res, v.Ad, v.res); note_launch();
   // restrict, recurse, prolong
   const int degc = c.o->degrees[l + 1];
   const int Npf = npd(deg), Npc = npd(degc);
   const int64_t nE = int64_t(c.m->K) * c.B;
   const T* P = transfer_ptr<T>(c.m, deg, degc);
-  k_restrict<T><<<int((nE * Npc + 255) / 256), 256, 0, c.st>>>(Npf, Npc, nE, P, v.res, lv[l + 1].rhs);
+  k_restrict<T><<<int((nE * Npc + 255) / 256), 256, 0, c.st>>>(Npf, Npc, nE, P, v.res, lv[l + 1].rhs); note_launch();
   CK(vcycle<T>(c, l + 1, coarse_iters));
-  k_prolong<T><<<int((nE * Npf + 255) / 256), 256, 0, c.st>>>(Npf, Npc, nE, P, lv[l + 1].x, v.x);
+  k_prolong<T><<<int((nE * Npf + 255) / 256), 256, 0, c.st>>>(Npf, Npc, nE, P, lv[l + 1].x, v.x); note_launch();
   // post-smoothing
   CK(chebyshev<T>(c, l, false));
   return cudaGetLastError();
@@ -582,7 +582,7 @@ cudaError_t power_rho(Ctx& c, int l, double& rho) {
   const dim3 g = vgrid(n, 1);
   std::vector<double> hp(kRedBlocks * 2);
   auto norm = [&](const T* a, double& out) -> cudaError_t {
-    k_dot<T, T><<<g, kRedThreads, 0, c.st>>>(n, a, a, c.w->partial);
+    k_dot<T, T><<<g, kRedThreads, 0, c.st>>>(n, a, a, c.w->partial); note_launch();
     CK(cudaMemcpyAsync(hp.data(), c.w->partial, sizeof(double) * kRedBlocks * 2, cudaMemcpyDeviceToHost, c.st));
     CK(cudaStreamSynchronize(c.st));
     double s = 0.0;
@@ -593,9 +593,9 @@ cudaError_t power_rho(Ctx& c, int l, double& rho) {
   double nv = 1.0, lam = 0.0;
   CK(norm(v.d, nv));
   for (int it = 0; it < c.o->power_steps; ++it) {
-    k_scaled_copy<T><<<egrid(n), 256, 0, c.st>>>(n, T(1.0 / nv), v.d, v.x);  // x = d / ||d||
+    k_scaled_copy<T><<<egrid(n), 256, 0, c.st>>>(n, T(1.0 / nv), v.d, v.x); note_launch();  // x = d / ||d||
     CK(launch_apply(c.m, deg, prec_of<T>(), 1, c.lambda, v.x, v.Ad, c.st));
-    k_scale<T, T><<<egrid(n), 256, 0, c.st>>>(n, n, v.dinv, v.Ad, v.d);    // d = D^{-1} A x
+    k_scale<T, T><<<egrid(n), 256, 0, c.st>>>(n, n, v.dinv, v.Ad, v.d); note_launch();    // d = D^{-1} A x
     CK(norm(v.d, nv));
     lam = nv;
   }
@@ -616,11 +616,11 @@ cudaError_t setup_pmg(Ctx& c, std::string& key) {
     const int64_t n = int64_t(c.m->K) * npd(deg);
     if (o->mixed) {
       CK(launch_diagonal(c.m, deg, DG_F32, c.lambda, w->lv32[l].dinv, c.st));
-      k_recip<float><<<egrid(n), 256, 0, c.st>>>(n, w->lv32[l].dinv);
+      k_recip<float><<<egrid(n), 256, 0, c.st>>>(n, w->lv32[l].dinv); note_launch();
       if (l + 1 < o->nlevels) CK(power_rho<float>(c, l, w->rho[l]));
     } else {
       CK(launch_diagonal(c.m, deg, DG_F64, c.lambda, w->lv64[l].dinv, c.st));
-      k_recip<double><<<egrid(n), 256, 0, c.st>>>(n, w->lv64[l].dinv);
+      k_recip<double><<<egrid(n), 256, 0, c.st>>>(n, w->lv64[l].dinv); note_launch();
       if (l + 1 < o->nlevels) CK(power_rho<double>(c, l, w->rho[l]));
     }
   }
@@ -638,19 +638,19 @@ cudaError_t precondition(Ctx& c, int& coarse_iters) {
       CK(cudaMemcpyAsync(w->z, w->r, nt * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
       break;
     case DG_PREC_JACOBI:
-      k_scale<double, double><<<egrid(nt), 256, 0, c.st>>>(n, nt, w->dinv, w->r, w->z);
+      k_scale<double, double><<<egrid(nt), 256, 0, c.st>>>(n, nt, w->dinv, w->r, w->z); note_launch();
       break;
     case DG_PREC_INVMASS: {
       const int Np = npd(c.m->N);
       const double* Minv = reinterpret_cast<const double*>(c.m->ops64[c.m->N].buf) + (ops_count(c.m->N) - size_t(Np) * Np);
-      k_invmass<<<int((nt + 255) / 256), 256, 0, c.st>>>(Np, c.m->K, c.B, c.m->geo64, Minv, c.lambda, w->r, w->z);
+      k_invmass<<<int((nt + 255) / 256), 256, 0, c.st>>>(Np, c.m->K, c.B, c.m->geo64, Minv, c.lambda, w->r, w->z); note_launch();
       break;
     }
     case DG_PREC_PMG:
       if (c.o->mixed) {
-        k_convert<float, double><<<egrid(nt), 256, 0, c.st>>>(nt, w->r, w->lv32[0].rhs);
+        k_convert<float, double><<<egrid(nt), 256, 0, c.st>>>(nt, w->r, w->lv32[0].rhs); note_launch();
         CK(vcycle<float>(c, 0, coarse_iters));
-        k_convert<double, float><<<egrid(nt), 256, 0, c.st>>>(nt, w->lv32[0].x, w->z);
+        k_convert<double, float><<<egrid(nt), 256, 0, c.st>>>(nt, w->lv32[0].x, w->z); note_launch();
       } else {
         CK(cudaMemcpyAsync(w->lv64[0].rhs, w->r, nt * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
         CK(vcycle<double>(c, 0, coarse_iters));
@@ -680,7 +680,7 @@ cudaError_t pcg_run(Ctx& c, const double* b, double* x, dg_solve_info* info, dg_
     std::snprintf(buf, sizeof buf, "jac/%.17g", c.lambda);
     if (w->dinv_key != buf) {
       CK(launch_diagonal(c.m, c.m->N, DG_F64, c.lambda, w->dinv, c.st));
-      k_recip<double><<<egrid(n), 256, 0, c.st>>>(n, w->dinv);
+      k_recip<double><<<egrid(n), 256, 0, c.st>>>(n, w->dinv); note_launch();
       w->dinv_key = buf;
     }
   } else if (o->precond == DG_PREC_PMG) {
@@ -688,17 +688,17 @@ cudaError_t pcg_run(Ctx& c, const double* b, double* x, dg_solve_info* info, dg_
   }
   CK(cudaEventRecord(w->ev0, c.st));
   int coarse_iters = 0;
-  k_init_scal<<<1, 64, 0, c.st>>>(B, w->scal, o->tol * o->tol);
-  k_dot<<<g, kRedThreads, 0, c.st>>>(n, b, b, w->partial);
-  k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_INIT_BB, w->scal, w->partial);
+  k_init_scal<<<1, 64, 0, c.st>>>(B, w->scal, o->tol * o->tol); note_launch();
+  k_dot<<<g, kRedThreads, 0, c.st>>>(n, b, b, w->partial); note_launch();
+  k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_INIT_BB, w->scal, w->partial); note_launch();
   CK(launch_apply(c.m, c.m->N, DG_F64, B, c.lambda, x, w->Ap, c.st));
-  k_sub<double><<<egrid(nt), 256, 0, c.st>>>(nt, b, w->Ap, w->r);
-  k_dot<<<g, kRedThreads, 0, c.st>>>(n, w->r, w->r, w->partial);
-  k_init_check<<<B, kRedThreads, 0, c.st>>>(w->scal, w->partial);
+  k_sub<double><<<egrid(nt), 256, 0, c.st>>>(nt, b, w->Ap, w->r); note_launch();
+  k_dot<<<g, kRedThreads, 0, c.st>>>(n, w->r, w->r, w->partial); note_launch();
+  k_init_check<<<B, kRedThreads, 0, c.st>>>(w->scal, w->partial); note_launch();
   CK(precondition(c, coarse_iters));
-  k_dot<<<g, kRedThreads, 0, c.st>>>(n, w->r, w->z, w->partial);
-  k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_INIT_RZ, w->scal, w->partial);
-  k_update_p<<<g, kRedThreads, 0, c.st>>>(n, w->scal, w->z, w->p, 1);
+  k_dot<<<g, kRedThreads, 0, c.st>>>(n, w->r, w->z, w->partial); note_launch();
+  k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_INIT_RZ, w->scal, w->partial); note_launch();
+  k_update_p<<<g, kRedThreads, 0, c.st>>>(n, w->scal, w->z, w->p, 1); note_launch();
   CK(cudaMemcpyAsync(w->h_scal, w->scal, sizeof(double) * B * kNS, cudaMemcpyDeviceToHost, c.st));
   CK(cudaStreamSynchronize(c.st));
   bool any = false;
@@ -707,10 +707,10 @@ cudaError_t pcg_run(Ctx& c, const double* b, double* x, dg_solve_info* info, dg_
   const int chk = (o->precond == DG_PREC_PMG) ? 1 : 4;
   while (any && it < o->max_iter) {
     CK(launch_apply(c.m, c.m->N, DG_F64, B, c.lambda, w->p, w->Ap, c.st));
-    k_dot<<<g, kRedThreads, 0, c.st>>>(n, w->p, w->Ap, w->partial);
-    k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_ALPHA, w->scal, w->partial);
-    k_update_xr<<<g, kRedThreads, 0, c.st>>>(n, w->scal, x, w->r, w->p, w->Ap, flexible ? w->z : nullptr, w->partial);
-    k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_RR, w->scal, w->partial);
+    k_dot<<<g, kRedThreads, 0, c.st>>>(n, w->p, w->Ap, w->partial); note_launch();
+    k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_ALPHA, w->scal, w->partial); note_launch();
+    k_update_xr<<<g, kRedThreads, 0, c.st>>>(n, w->scal, x, w->r, w->p, w->Ap, flexible ? w->z : nullptr, w->partial); note_launch();
+    k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_RR, w->scal, w->partial); note_launch();
     ++it;
     if (it % chk == 0 || it == o->max_iter) {
       CK(cudaMemcpyAsync(w->h_scal, w->scal, sizeof(double) * B * kNS, cudaMemcpyDeviceToHost, c.st));
@@ -720,9 +720,9 @@ cudaError_t pcg_run(Ctx& c, const double* b, double* x, dg_solve_info* info, dg_
       if (!any) break;
     }
     CK(precondition(c, coarse_iters));
-    k_dot<<<g, kRedThreads, 0, c.st>>>(n, w->r, w->z, w->partial);
-    k_finalize<<<B, kRedThreads, 0, c.st>>>(flexible ? FIN_BETA_FLEX : FIN_BETA, w->scal, w->partial);
-    k_update_p<<<g, kRedThreads, 0, c.st>>>(n, w->scal, w->z, w->p, 0);
+    k_dot<<<g, kRedThreads, 0, c.st>>>(n, w->r, w->z, w->partial); note_launch();
+    k_finalize<<<B, kRedThreads, 0, c.st>>>(flexible ? FIN_BETA_FLEX : FIN_BETA, w->scal, w->partial); note_launch();
+    k_update_p<<<g, kRedThreads, 0, c.st>>>(n, w->scal, w->z, w->p, 0); note_launch();
   }
   CK(cudaEventRecord(w->ev1, c.st));
   CK(cudaMemcpyAsync(w->h_scal, w->scal, sizeof(double) * B * kNS, cudaMemcpyDeviceToHost, c.st));
