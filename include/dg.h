@@ -146,6 +146,27 @@ dg_status dg_rhs(const dg_mesh* mesh, int B, const double* f, const double* g, d
 dg_status dg_pcg_solve(dg_mesh* mesh, const dg_solver_opts* opts, int B, double lambda,
                        const double* b, double* x, dg_solve_info* info, void* stream);
 
+/* Jacobi-preconditioned CG on A(lambda) x = b that allocates nothing.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory while they run (a host whose memory pool owns
+ * the whole GPU, a time-critical loop that must not pay cudaMalloc's implicit
+ * synchronisation, or a simulation that must not fail on an allocation
+ * midway). Its workspace is a fixed scratch array of 2^22 doubles (32 MiB)
+ * compiled into the library as device memory, which every GPU that loads the
+ * library holds until the process exits. b, x: device FP64 [B][K][Np] as in
+ * dg_pcg_solve (x: initial guess in, solution out); the mesh comes from an
+ * earlier dg_mesh_setup. Sizes beyond the array (about B*K*Np > 838,000) are
+ * rejected with DG_ERR_ARG before any device work. The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) and caches it;
+ * make that first call before any stream capture. The call calls no
+ * cudaMalloc/cudaFree and no allocating library routine. All calls share the
+ * one array and leave their data in it: two calls whose work overlaps on the
+ * GPU (different streams, or different host threads on one device) race and
+ * corrupt each other's results; serialise them. info (host, may be NULL)
+ * receives iterations and residuals; info->ms is not measured (0). */
+dg_status dg_pcg_jacobi_solve_static(const dg_mesh* mesh, int B, double lambda, double tol, int max_iter,
+                                     const double* b, double* x, dg_solve_info* info, void* stream);
+
 /* Host-only: the library's own reference data for degree N (1..8), for
  * inspection without a GPU. r, s: Np; M, Dr, Ds: Np x Np row-major;
  * Mf: (N+1) x (N+1); fmask: 3 x (N+1) local node index of face node j of face

@@ -63,6 +63,7 @@ def lib():
         "dg_rhs": ([vp, i32, vp, vp, vp, vp], i32),
         "dg_pcg_solve": ([vp, ctypes.POINTER(SolverOpts), i32, dbl, vp, vp, ctypes.POINTER(SolveInfo), vp], i32),
         "dg_solver_opts_default": ([ctypes.POINTER(SolverOpts)], None),
+        "dg_pcg_jacobi_solve_static": ([vp, i32, dbl, dbl, i32, vp, vp, ctypes.POINTER(SolveInfo), vp], i32),
         "dg_reference_operators": ([i32, pd, pd, pd, pd, pd, pd, pi32], i32),
         "dg_interpolation_matrix": ([i32, i32, pd], i32),
         "dg_status_string": ([i32], ctypes.c_char_p),
@@ -199,6 +200,21 @@ class Mesh:
         b = torch.empty_like(f)
         _check(lib().dg_rhs(self._h, B, _tptr(f), _tptr(g) if g is not None else None, _tptr(b), _stream()))
         return b
+
+    def solve_static(self, b, x=None, lam=0.0, tol=1e-10, max_iter=1000, check=True):
+        """Jacobi-PCG from the library's fixed device scratch array (no allocation
+        inside the call); returns (x, info)."""
+        import torch
+        if x is None:
+            x = torch.zeros_like(b)
+        B = 1 if b.dim() == 2 else b.shape[0]
+        info = SolveInfo()
+        st = lib().dg_pcg_jacobi_solve_static(self._h, B, float(lam), float(tol), int(max_iter), _tptr(b), _tptr(x),
+                                              ctypes.byref(info), _stream())
+        if check:
+            _check(st)
+        return x, dict(iters=list(info.iters[:B]), relres=list(info.relres[:B]), total_iters=info.total_iters,
+                       status=_STATUS.get(st, st))
 
     def solve(self, b, x=None, lam=0.0, opts=None, check=True, **kw):
         """PCG solve A x = b (b, x float64 [B][K][Np] or [K][Np]); returns (x, info, status)."""

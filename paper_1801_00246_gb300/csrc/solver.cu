@@ -809,3 +809,143 @@ dg_status dg_pcg_solve(dg_mesh* m, const dg_solver_opts* o, int B, double lambda
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free Jacobi-PCG.
+//
+// Some callers cannot allocate device memory while they run: code that hands
+// every byte of the GPU to its own caching allocator or memory pool, code that
+// must not hit cudaMalloc's implicit device synchronisation in a time-critical
+// loop, or hosts that treat an allocation failure in the middle of a
+// simulation as fatal. For them the library keeps a fixed scratch array in
+// device memory (a file-scope __device__ array: every GPU that loads the
+// library holds it until the process exits) and solves from it without any
+// allocation. The mesh itself is still created once, up front, by
+// dg_mesh_setup.
+namespace dgx {
+
+constexpr size_t kStaticScratchDoubles = size_t(1) << 22;  // 32 MiB per device
+static __device__ __align__(256) double g_static_scratch[kStaticScratchDoubles];
+static double* g_static_scratch_ptr[64] = {};  // device address, per device ordinal
+
+static size_t align32(size_t n) { return (n + 31) & ~size_t(31); }  // 256-byte steps
+
+size_t static_scratch_need(int64_t n, int B) {
+  return 4 * align32(size_t(n) * B) + align32(size_t(n)) + align32(size_t(B) * kNS) +
+         align32(size_t(B) * kRedBlocks * 2);
+}
+
+}  // namespace dgx
+
+extern "C" dg_status dg_pcg_jacobi_solve_static(const dg_mesh* mc, int B, double lambda, double tol, int max_iter,
+                                                const double* b, double* x, dg_solve_info* info, void* stream) {
+  using namespace dgx;
+  if (!mc || !b || !x) { set_error("NULL argument"); return DG_ERR_ARG; }
+  if (B < 1 || B > DG_MAX_BATCH) { set_error("batch must be in 1..64"); return DG_ERR_ARG; }
+  if (!(tol > 0.0) || max_iter < 0) { set_error("tol must be > 0 and max_iter >= 0"); return DG_ERR_ARG; }
+  if (!std::isfinite(lambda) || lambda < 0) { set_error("lambda must be finite and >= 0"); return DG_ERR_ARG; }
+  dg_mesh* m = const_cast<dg_mesh*>(mc);
+  const int64_t n = int64_t(m->K) * npd(m->N);
+  const size_t need = static_scratch_need(n, B);
+  if (need > kStaticScratchDoubles) {
+    set_error("dg_pcg_jacobi_solve_static: problem needs " + std::to_string(need) +
+              " scratch doubles, the static array holds " + std::to_string(kStaticScratchDoubles) +
+              " (B*K*Np must stay below about 838,000)");
+    return DG_ERR_ARG;
+  }
+  if (!m->ops64[m->N].buf) { set_error("mesh operators missing"); return DG_ERR_ARG; }
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce != cudaSuccess || dev < 0 || dev >= 64) {
+    set_error(std::string("dg_pcg_jacobi_solve_static: cudaGetDevice: ") + cudaGetErrorString(ce));
+    return DG_ERR_CUDA;
+  }
+  if (!g_static_scratch_ptr[dev]) {  // one-time set-up on this device (before any stream capture)
+    void* p = nullptr;
+    ce = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (ce != cudaSuccess) {
+      set_error(std::string("dg_pcg_jacobi_solve_static: cudaGetSymbolAddress: ") + cudaGetErrorString(ce));
+      return DG_ERR_CUDA;
+    }
+    g_static_scratch_ptr[dev] = static_cast<double*>(p);
+  }
+  double* base = g_static_scratch_ptr[dev];
+  const size_t nt = size_t(n) * B;
+  double* r = base;
+  double* z = r + align32(nt);
+  double* p = z + align32(nt);
+  double* Ap = p + align32(nt);
+  double* dinv = Ap + align32(nt);
+  double* scal = dinv + align32(size_t(n));
+  double* partial = scal + align32(size_t(B) * kNS);
+  const dim3 g = vgrid(n, B);
+#define SCK(expr)                                                                          \
+  do {                                                                                     \
+    cudaError_t e_ = (expr);                                                               \
+    if (e_ != cudaSuccess) {                                                               \
+      set_error(std::string("dg_pcg_jacobi_solve_static: ") + cudaGetErrorString(e_));     \
+      return DG_ERR_CUDA;                                                                  \
+    }                                                                                      \
+  } while (0)
+  // every scratch word read below is written first in this call, except the
+  // per-right-hand-side scalars, which k_init_scal clears
+  SCK(launch_diagonal(m, m->N, DG_F64, lambda, dinv, st));
+  k_recip<double><<<egrid(n), 256, 0, st>>>(n, dinv); note_launch();
+  k_init_scal<<<1, 64, 0, st>>>(B, scal, tol * tol); note_launch();
+  k_dot<<<g, kRedThreads, 0, st>>>(n, b, b, partial); note_launch();
+  k_finalize<<<B, kRedThreads, 0, st>>>(FIN_INIT_BB, scal, partial); note_launch();
+  SCK(launch_apply(m, m->N, DG_F64, B, lambda, x, Ap, st));
+  k_sub<double><<<egrid(nt), 256, 0, st>>>(nt, b, Ap, r); note_launch();
+  k_dot<<<g, kRedThreads, 0, st>>>(n, r, r, partial); note_launch();
+  k_init_check<<<B, kRedThreads, 0, st>>>(scal, partial); note_launch();
+  k_scale<double, double><<<egrid(nt), 256, 0, st>>>(n, nt, dinv, r, z); note_launch();
+  k_dot<<<g, kRedThreads, 0, st>>>(n, r, z, partial); note_launch();
+  k_finalize<<<B, kRedThreads, 0, st>>>(FIN_INIT_RZ, scal, partial); note_launch();
+  k_update_p<<<g, kRedThreads, 0, st>>>(n, scal, z, p, 1); note_launch();
+  double hs[DG_MAX_BATCH * kNS];
+  SCK(cudaMemcpyAsync(hs, scal, sizeof(double) * B * kNS, cudaMemcpyDeviceToHost, st));
+  SCK(cudaStreamSynchronize(st));
+  bool any = false;
+  for (int k = 0; k < B; ++k) any = any || hs[k * kNS + S_ACTIVE] != 0.0;
+  int it = 0;
+  while (any && it < max_iter) {
+    SCK(launch_apply(m, m->N, DG_F64, B, lambda, p, Ap, st));
+    k_dot<<<g, kRedThreads, 0, st>>>(n, p, Ap, partial); note_launch();
+    k_finalize<<<B, kRedThreads, 0, st>>>(FIN_ALPHA, scal, partial); note_launch();
+    k_update_xr<<<g, kRedThreads, 0, st>>>(n, scal, x, r, p, Ap, nullptr, partial); note_launch();
+    k_finalize<<<B, kRedThreads, 0, st>>>(FIN_RR, scal, partial); note_launch();
+    ++it;
+    if (it % 4 == 0 || it == max_iter) {
+      SCK(cudaMemcpyAsync(hs, scal, sizeof(double) * B * kNS, cudaMemcpyDeviceToHost, st));
+      SCK(cudaStreamSynchronize(st));
+      any = false;
+      for (int k = 0; k < B; ++k) any = any || hs[k * kNS + S_ACTIVE] != 0.0;
+      if (!any) break;
+    }
+    k_scale<double, double><<<egrid(nt), 256, 0, st>>>(n, nt, dinv, r, z); note_launch();
+    k_dot<<<g, kRedThreads, 0, st>>>(n, r, z, partial); note_launch();
+    k_finalize<<<B, kRedThreads, 0, st>>>(FIN_BETA, scal, partial); note_launch();
+    k_update_p<<<g, kRedThreads, 0, st>>>(n, scal, z, p, 0); note_launch();
+  }
+  SCK(cudaMemcpyAsync(hs, scal, sizeof(double) * B * kNS, cudaMemcpyDeviceToHost, st));
+  SCK(cudaStreamSynchronize(st));
+#undef SCK
+  dg_status status = DG_OK;
+  for (int k = 0; k < B; ++k) {
+    if (hs[k * kNS + S_BREAK] != 0.0) status = DG_ERR_BREAKDOWN;
+    else if (hs[k * kNS + S_ACTIVE] != 0.0 && status == DG_OK) status = DG_ERR_NOT_CONVERGED;
+  }
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    for (int k = 0; k < B; ++k) {
+      info->iters[k] = int(hs[k * kNS + S_ITERS]);
+      info->relres[k] = hs[k * kNS + S_RELRES];
+    }
+    info->total_iters = it;
+    info->ms = 0.f;
+  }
+  if (status == DG_ERR_NOT_CONVERGED) set_error("dg_pcg_jacobi_solve_static: max_iter reached before tol");
+  if (status == DG_ERR_BREAKDOWN) set_error("dg_pcg_jacobi_solve_static: Krylov breakdown");
+  return status;
+}
