@@ -38,3 +38,15 @@ def manufactured(name):
     else:
         raise KeyError(name)
     return u, f
+
+
+def kovasznay(Re=40.0):
+    """Kovasznay's steady closed-form Navier-Stokes solution (Kovasznay 1948):
+    nu = 1/Re, l = Re/2 - sqrt(Re^2/4 + 4 pi^2),
+    u = 1 - e^{l x} cos 2 pi y, v = l/(2 pi) e^{l x} sin 2 pi y, p = (1 - e^{2 l x})/2.
+    Returns (nu, u, v, p) with u, v, p callables of (x, y)."""
+    lam = Re / 2.0 - np.sqrt(Re * Re / 4.0 + 4.0 * np.pi ** 2)
+    u = lambda x, y: 1.0 - np.exp(lam * x) * np.cos(2 * np.pi * y)
+    v = lambda x, y: lam / (2 * np.pi) * np.exp(lam * x) * np.sin(2 * np.pi * y)
+    p = lambda x, y: 0.5 * (1.0 - np.exp(2 * lam * x))
+    return 1.0 / Re, u, v, p

@@ -92,8 +92,9 @@ CONFIG_MESHES = {
     "c1_poisson_512tri_N3": (16, 16, (0.0, 1.0, 0.0, 1.0), 0.1, 0, (1, 1, 1, 1), 3),
     # 128x128 on the unit square, N=6, Dirichlet everywhere
     "c2_pmg_32768tri_N6": (128, 128, (0.0, 1.0, 0.0, 1.0), 0.1, 0, (1, 1, 1, 1), 6),
-    # 64x64 on [-0.5,1]x[-0.5,1.5], N=8; velocity Dirichlet except the x=1 outflow
-    "c3_ins_8192tri_N8": (64, 64, (-0.5, 1.0, -0.5, 1.5), 0.0, 0, (1, 2, 1, 1), 8),
+    # 64x64 on [-0.5,1]x[-0.5,1.5], N=8; velocity Dirichlet on every side (the
+    # pressure-increment tags come from ins_pressure_tags)
+    "c3_ins_8192tri_N8": (64, 64, (-0.5, 1.0, -0.5, 1.5), 0.0, 0, (1, 1, 1, 1), 8),
     # c2 mesh, batch of 64 right-hand sides
     "c4_adjoint_32768tri_N6": (128, 128, (0.0, 1.0, 0.0, 1.0), 0.1, 0, (1, 1, 1, 1), 6),
     # 512x512 on the unit square, N=8 headline (N=1..8 swept)
@@ -123,3 +124,22 @@ def with_all_neumann(mesh):
     bc = np.where(mesh.bc != INTERIOR, NEUMANN, INTERIOR).astype(np.int8)
     return Mesh(VX=mesh.VX, VY=mesh.VY, EToV=mesh.EToV, bc=bc, nx=mesh.nx, ny=mesh.ny,
                 box=mesh.box, meta=dict(mesh.meta, all_neumann=True))
+
+
+def ins_pressure_tags(mesh, dirichlet_sides=(1,)):
+    """Copy of a velocity mesh whose boundary tags are those of the pressure
+    increment: Dirichlet on the listed sides (0: x0, 1: x1, 2: y0, 3: y1),
+    Neumann on the others."""
+    x0, x1, y0, y1 = mesh.box
+    bc = mesh.bc.copy()
+    for f in range(3):
+        va = mesh.EToV[:, f]
+        vb = mesh.EToV[:, (f + 1) % 3]
+        bnd = mesh.bc[:, f] != INTERIOR
+        bc[bnd, f] = NEUMANN
+        for side, (arr, val) in enumerate(((mesh.VX, x0), (mesh.VX, x1), (mesh.VY, y0), (mesh.VY, y1))):
+            if side in dirichlet_sides:
+                on = bnd & np.isclose(arr[va], val) & np.isclose(arr[vb], val)
+                bc[on, f] = DIRICHLET
+    return Mesh(VX=mesh.VX, VY=mesh.VY, EToV=mesh.EToV, bc=bc, nx=mesh.nx, ny=mesh.ny, box=mesh.box,
+                meta=dict(mesh.meta, pressure_tags=tuple(dirichlet_sides)))

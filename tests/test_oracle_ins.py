@@ -1,0 +1,105 @@
+"""Pins of the oracle's INS pieces (Sections 2.1-2.3)."""
+import numpy as np
+import pytest
+
+from dg_inputs import jittered_grid
+from dg_inputs.fields import kovasznay
+from dg_inputs.mesh import ins_pressure_tags, rotate_local_vertices
+from oracle.ins import LSERK_A, LSERK_B, LSERK_C, InsOracle, lserk_integrate
+from oracle.sipdg import Sipdg
+
+
+def _ins(n, N, rotate=None, box=(-0.5, 1.0, -0.5, 1.5)):
+    m = jittered_grid(n, n, box=box, jitter=0.1, seed=0, bc_sides=(1, 1, 1, 1))
+    if rotate is not None:
+        m = rotate_local_vertices(m, rotate)
+    mp = ins_pressure_tags(m, dirichlet_sides=(1,))
+    Su = Sipdg(m.VX, m.VY, m.EToV, m.bc, N)
+    Sp = Sipdg(mp.VX, mp.VY, mp.EToV, mp.bc, N)
+    return InsOracle(Su, Sp)
+
+
+def test_lserk_fourth_order():
+    """y' = i w y: the global error falls by ~2^4 per halving of the step."""
+    w = 3.0
+    errs = []
+    for nsteps in (20, 40, 80):
+        y = lserk_integrate(lambda t, y: 1j * w * y, np.array([1.0 + 0j]), 0.0, 2.0 / nsteps, nsteps)
+        errs.append(abs(y[0] - np.exp(2j * w)))
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(rates > 3.8), rates
+    assert LSERK_C[0] == 0.0 and np.all(np.diff(LSERK_C) > 0) and LSERK_C[-1] < 1.0
+    # quadrature conditions: y' = t^k integrates exactly for k <= 3 in one step
+    h = 0.5
+    for k in range(4):
+        y = lserk_integrate(lambda t, y: np.full_like(y, t ** k), np.zeros(1), 0.0, h, 1)
+        assert abs(y[0] - h ** (k + 1) / (k + 1)) < 1e-15, k
+    # y' = y: one step reproduces exp(h) through the h^4 term (error ~ h^5)
+    y = lserk_integrate(lambda t, y: y, np.ones(1), 0.0, 0.1, 1)
+    assert abs(y[0] - np.exp(0.1)) < 2e-7
+    assert len(LSERK_A) == len(LSERK_B) == 5
+
+
+def _poly(N, seed):
+    """Random polynomial of total degree N with its x and y derivatives."""
+    c = np.random.default_rng(seed).standard_normal((N + 1, N + 1))
+    terms = [(a, b) for a in range(N + 1) for b in range(N + 1 - a)]
+    f = lambda x, y: sum(c[a, b] * x ** a * y ** b for a, b in terms)
+    fx = lambda x, y: sum(c[a, b] * a * x ** (a - 1) * y ** b for a, b in terms if a > 0)
+    fy = lambda x, y: sum(c[a, b] * b * x ** a * y ** (b - 1) for a, b in terms if b > 0)
+    return f, fx, fy
+
+
+@pytest.mark.parametrize("N", [2, 4, 6])
+def test_gradient_and_divergence_exact_on_polynomials(N):
+    """For continuous polynomials with matching boundary data every jump
+    vanishes, so G p = grad p and D.U = div U at the nodes."""
+    O = _ins(3, N, rotate=N)
+    x, y = O.Su.x, O.Su.y
+    f, fx, fy = _poly(N, 1)
+    p = f(x, y)
+    G = O.to_strong(O.weak_grad(p, p))
+    scale = max(1.0, np.abs(fx(x, y)).max())
+    assert np.abs(G[0] - fx(x, y)).max() < 1e-11 * scale * N ** 2
+    assert np.abs(G[1] - fy(x, y)).max() < 1e-11 * scale * N ** 2
+    g, gx, gy = _poly(N, 2)
+    U = np.stack([f(x, y), g(x, y)])
+    D = O.to_strong(O.weak_div(U, U))
+    assert np.abs(D - (fx(x, y) + gy(x, y))).max() < 1e-11 * scale * N ** 2
+
+
+@pytest.mark.parametrize("N", [1, 3, 5])
+def test_advection_exact_on_continuous_linear_field(N):
+    """For a continuous linear velocity with matching boundary data the LLF
+    jumps vanish and N~(U, U)_c = div(U U_c) exactly (degree <= 1 <= N)."""
+    O = _ins(3, N, rotate=2)
+    x, y = O.Su.x, O.Su.y
+    U = np.stack([1.0 + x + 2 * y, 3.0 - y + 0.5 * x])
+    u, v = U
+    # div(U u) = u_x u + u u_x ... written out: d(u u)/dx + d(v u)/dy
+    div_uu = 2 * u * 1.0 + (v * 2.0 + u * (-1.0))
+    # d(u v)/dx + d(v v)/dy = u_x v + u v_x + 2 v v_y
+    div_uv = 1.0 * v + u * 0.5 + 2 * v * (-1.0)
+    rhs = O.advection(U, U, U)
+    assert np.abs(-rhs[0] - div_uu).max() < 1e-10 * 50
+    assert np.abs(-rhs[1] - div_uv).max() < 1e-10 * 50
+
+
+def test_kovasznay_step_stays_near_exact():
+    """One split step from the exact Kovasznay state (nu = 1/40, dt = 0.01,
+    4 substeps) stays at the discretisation-error level and keeps D.U small."""
+    O = _ins(8, 4, rotate=1)
+    nu, fu, fv, fp = kovasznay(40.0)
+    x, y = O.Su.x, O.Su.y
+    U0 = np.stack([fu(x, y), fv(x, y)])
+    P0 = fp(x, y)
+    st = dict(U=U0.copy(), Uold=U0.copy(), P=P0.copy(), n=0)
+    st, mid = O.step(st, 0.01, nu, 4, U0, P0)
+    st, mid = O.step(st, 0.01, nu, 4, U0, P0)
+    err_u = np.abs(st["U"] - U0).max() / np.abs(U0).max()
+    err_p = np.abs(st["P"] - P0).max()
+    assert err_u < 5e-3, err_u
+    assert err_p < 5e-2, err_p
+    div = np.linalg.norm(O.to_strong(O.weak_div(st["U"], U0)))
+    div0 = np.linalg.norm(O.to_strong(O.weak_div(U0 + 0.01, U0)))
+    assert div < div0
