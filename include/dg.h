@@ -146,6 +146,46 @@ dg_status dg_rhs(const dg_mesh* mesh, int B, const double* f, const double* g, d
 dg_status dg_pcg_solve(dg_mesh* mesh, const dg_solver_opts* opts, int B, double lambda,
                        const double* b, double* x, dg_solve_info* info, void* stream);
 
+/* State of the semi-implicit incompressible Navier-Stokes stepper
+ * (Section 2.2 Eq. INS_TD_3, Section 2.3 subcycling). All field pointers are
+ * caller-owned device FP64 arrays; the caller checkpoints by saving them. */
+typedef struct {
+  double nu;              /* kinematic viscosity */
+  double dt;              /* macro time step */
+  int Ns;                 /* LSERK(5,4) advection substeps per macro step (dt_s = dt / Ns) */
+  int step;               /* completed steps; 0 selects the BDF1/EXT1 start-up step; incremented */
+  double* U;              /* [2][K][Np] velocity U^n on entry, U^{n+1} on exit */
+  double* Uold;           /* [2][K][Np] U^{n-1} on entry (unused when step == 0), U^n on exit */
+  double* P;              /* [K][Np] pressure P^n on entry, P^{n+1} on exit */
+  const double* gU;       /* [2][K][Np] steady velocity data on velocity-Dirichlet faces (face nodes used) */
+  const double* gP;       /* [K][Np] steady pressure data on pressure-Dirichlet faces (face nodes used) */
+  dg_solver_opts vel_opts;   /* the two batched velocity Helmholtz solves (B = 2) */
+  dg_solver_opts pr_opts;    /* the pressure-increment Poisson solve */
+  int vel_iters[2];       /* out: iterations of the last step's velocity solves */
+  int pr_iters;           /* out: iterations of the last step's pressure solve */
+  float ms;               /* out: device time of the last call */
+} dg_ins_state;
+
+/* Advance nsteps macro steps of the algebraic splitting scheme with
+ * second-order BDF/EXT coefficients (gamma = 3/2, beta = 2, -1/2; the first
+ * step uses BDF1) and a first-order pressure increment:
+ *   (i)   U^  = sum_i beta_i U~^{n-i}, each U^{n-i} advected to t^{n+1} by
+ *         LSERK(5,4) substeps of the DG advection operator with cubature and
+ *         the local Lax-Friedrichs flux (Eq. INS_CUB_N), advecting velocity
+ *         the linear extrapolant through U^n, U^{n-1};
+ *   (ii)  (-L + gamma/(nu dt)) U^^ = U^/(nu dt) - (1/nu) G P^n, both
+ *         components in one batched PCG (vel_opts, lambda = gamma/(nu dt));
+ *   (iii) -L dP = -(gamma/dt) D.U^^ (pr_opts);
+ *   (iv)  U^{n+1} = U^^ - (dt/gamma) G dP, P^{n+1} = P^n + dP.
+ * mesh_u and mesh_p are the same triangulation and degree carrying the
+ * velocity and the pressure-increment boundary tags. G uses central fluxes
+ * with p* = gP on pressure-Dirichlet faces and p* = p- on the others; D uses
+ * u* = gU on velocity-Dirichlet faces and u* = u- on velocity-Neumann faces
+ * (Eq. INS_SD_4_1, INS_SD_4_2). Boundary data are steady; the pressure
+ * increment is zero on pressure-Dirichlet faces. Workspace is allocated on the
+ * first call and kept with mesh_u. Returns the status of a failing solve. */
+dg_status dg_ins_step(dg_mesh* mesh_u, dg_mesh* mesh_p, dg_ins_state* state, int nsteps, void* stream);
+
 /* Jacobi-preconditioned CG on A(lambda) x = b that allocates nothing.
  * The paper has no counterpart: this entry point exists for callers that
  * cannot allocate device memory while they run (a host whose memory pool owns

@@ -33,6 +33,14 @@ class SolveInfo(ctypes.Structure):
                 ("total_iters", ctypes.c_int), ("ms", ctypes.c_float)]
 
 
+class InsState(ctypes.Structure):
+    _fields_ = [("nu", ctypes.c_double), ("dt", ctypes.c_double), ("Ns", ctypes.c_int), ("step", ctypes.c_int),
+                ("U", ctypes.c_void_p), ("Uold", ctypes.c_void_p), ("P", ctypes.c_void_p),
+                ("gU", ctypes.c_void_p), ("gP", ctypes.c_void_p), ("vel_opts", SolverOpts),
+                ("pr_opts", SolverOpts), ("vel_iters", ctypes.c_int * 2), ("pr_iters", ctypes.c_int),
+                ("ms", ctypes.c_float)]
+
+
 _lib = None
 
 
@@ -63,6 +71,7 @@ def lib():
         "dg_rhs": ([vp, i32, vp, vp, vp, vp], i32),
         "dg_pcg_solve": ([vp, ctypes.POINTER(SolverOpts), i32, dbl, vp, vp, ctypes.POINTER(SolveInfo), vp], i32),
         "dg_solver_opts_default": ([ctypes.POINTER(SolverOpts)], None),
+        "dg_ins_step": ([vp, vp, ctypes.POINTER(InsState), i32, vp], i32),
         "dg_pcg_jacobi_solve_static": ([vp, i32, dbl, dbl, i32, vp, vp, ctypes.POINTER(SolveInfo), vp], i32),
         "dg_reference_operators": ([i32, pd, pd, pd, pd, pd, pd, pi32], i32),
         "dg_interpolation_matrix": ([i32, i32, pd], i32),
@@ -231,3 +240,31 @@ class Mesh:
         res = dict(iters=list(info.iters[:B]), relres=list(info.relres[:B]), total_iters=info.total_iters,
                    ms=info.ms, status=_STATUS.get(st, st))
         return x, res
+
+
+class InsStepper:
+    """Semi-implicit INS time stepper (dg_ins_step) on a velocity-tagged and a
+    pressure-tagged mesh of the same triangulation. U, Uold: float64 CUDA
+    [2][K][Np]; P: [K][Np]; gU, gP: steady boundary data as nodal fields."""
+
+    def __init__(self, mesh_u, mesh_p, nu, dt, Ns, U, P, gU, gP, vel_opts=None, pr_opts=None, Uold=None):
+        import torch
+        self.mesh_u, self.mesh_p = mesh_u, mesh_p
+        self.U = U.contiguous()
+        self.Uold = (Uold if Uold is not None else U.clone()).contiguous()
+        self.P = P.contiguous()
+        self.gU = gU.contiguous()
+        self.gP = gP.contiguous()
+        self.st = InsState()
+        self.st.nu, self.st.dt, self.st.Ns, self.st.step = float(nu), float(dt), int(Ns), 0
+        for name in ("U", "Uold", "P", "gU", "gP"):
+            setattr(self.st, name, getattr(self, name).data_ptr())
+        self.st.vel_opts = vel_opts if vel_opts is not None else default_opts(precond=PREC_INVMASS, tol=1e-10)
+        self.st.pr_opts = pr_opts if pr_opts is not None else default_opts(precond=PREC_JACOBI, tol=1e-10,
+                                                                           max_iter=20000)
+        del torch
+
+    def step(self, n=1):
+        _check(lib().dg_ins_step(self.mesh_u._h, self.mesh_p._h, ctypes.byref(self.st), int(n), _stream()))
+        return dict(step=self.st.step, vel_iters=list(self.st.vel_iters), pr_iters=self.st.pr_iters,
+                    ms=self.st.ms)

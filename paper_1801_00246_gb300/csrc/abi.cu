@@ -17,6 +17,7 @@ bool check_face_matching(const dg_mesh* m, std::string& err);
 void node_coordinates(const dg_mesh* m, int degree, std::vector<double>& x, std::vector<double>& y);
 const char* last_error();
 void free_workspace(dg_mesh* m);
+void free_ins_workspace(dg_mesh* m);
 
 size_t ops_count(int N) {
   const size_t Np = size_t(N + 1) * (N + 2) / 2, Nfp = N + 1;
@@ -298,6 +299,7 @@ dg_status dg_mesh_setup(int N, int64_t Nv, const double* VX, const double* VY, i
 dg_status dg_mesh_destroy(dg_mesh* m) {
   if (!m) return DG_OK;
   free_workspace(m);
+  free_ins_workspace(m);
   cudaFree(m->geo64);
   cudaFree(m->geo32);
   cudaFree(m->conn);

@@ -33,6 +33,10 @@ void gauss_jacobi(int n, double a, double b, std::vector<double>& x, std::vector
 double jacobi_p(double x, double a, double b, int n);
 int face_node(int N, int f, int j);
 std::vector<double> invert(int n, std::vector<double> A);
+void vandermonde2d(int N, const std::vector<double>& r, const std::vector<double>& s, std::vector<double>& V,
+                   std::vector<double>* Vr, std::vector<double>* Vs);
+struct InsWorkspace;
+void free_ins_workspace(dg_mesh* m);
 
 // Device copy of the reference operators of one degree, in one precision.
 // Layout of the single buffer (all row-major, T = double or float):
@@ -76,6 +80,7 @@ struct dg_mesh {
   dgx::DevOps ops32[dgx::kMaxN + 1];
   std::map<std::pair<int, int>, dgx::DevTransfer> transfer;
   dgx::Workspace* ws = nullptr;
+  dgx::InsWorkspace* ins = nullptr;
 };
 
 namespace dgx {
