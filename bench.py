@@ -328,6 +328,35 @@ def run_ours(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_apply_only(args):
+    """Only the N=8 Poisson applies (FP64 then FP32), for profiler captures."""
+    import torch
+    import paper_1801_00246_gb300 as P
+    from paper_1801_00246_gb300 import build
+    from dg_inputs import config_mesh, uniform_field
+    build.build()
+    m, _ = config_mesh(MESH_NAME)
+    N = args.degree
+    mesh = P.Mesh.from_inputs(m, N)
+    u64 = torch.from_numpy(uniform_field((mesh.K, mesh.Np), seed=1)).cuda()
+    u32 = u64.float()
+    o64, o32 = torch.empty_like(u64), torch.empty_like(u32)
+    flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    ms = {"f64": [], "f32": []}
+    for it in range(args.warmup + args.steps):
+        for key, u, o in (("f64", u64, o64), ("f32", u32, o32)):
+            flush_buf.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            mesh.apply(u, out=o)
+            e1.record()
+            torch.cuda.synchronize()
+            if it >= args.warmup:
+                ms[key].append(e0.elapsed_time(e1))
+    print(json.dumps({"apply_only": True, "N": N, "K": mesh.K, "ms_f64": float(np.mean(ms["f64"])),
+                      "ms_f32": float(np.mean(ms["f32"]))}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -335,9 +364,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--apply-only", action="store_true", help="only the Poisson applies (profiling)")
+    ap.add_argument("--degree", type=int, default=8, help="degree for --apply-only")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.apply_only:
+        run_apply_only(args)
+        return
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
