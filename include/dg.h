@@ -109,7 +109,10 @@ dg_status dg_mesh_nodes(const dg_mesh* mesh, int degree, double* x_dev, double* 
 
 /* Poisson operator (Eq. ellipticOp3 with lambda = 0) at the mesh degree:
  * Au[b] = A u[b] for b < B. u, Au: device [B][K][Np] of FP64 (DG_F64) or
- * FP32 (DG_F32); FP32 arithmetic accumulates in FP32. u and Au must not alias. */
+ * FP32 (DG_F32); FP32 arithmetic accumulates in FP32. u and Au must not alias.
+ * The FP32 path keeps a face-data scratch buffer with the mesh (allocated or
+ * grown on first use), so FP32 applies on one mesh must not overlap on the GPU
+ * (issue them on one stream, or use one mesh per stream). */
 dg_status dg_poisson_apply(const dg_mesh* mesh, dg_prec prec, int B, const void* u, void* Au,
                            void* stream);
 

@@ -1,6 +1,7 @@
 // C ABI entry points: mesh setup, operator applies, right-hand side, nodes,
 // and the small per-element kernels they need (Jacobi diagonal, Dirichlet
 // right-hand side).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <exception>
@@ -286,6 +287,27 @@ dg_status dg_mesh_setup(int N, int64_t Nv, const double* VX, const double* VY, i
   if (ce == cudaSuccess) ce = cudaMemcpy(m->geo64, m->geo_h.data(), sizeof(double) * 4 * K, cudaMemcpyHostToDevice);
   if (ce == cudaSuccess) ce = cudaMemcpy(m->geo32, g32.data(), sizeof(float) * 4 * K, cudaMemcpyHostToDevice);
   if (ce == cudaSuccess) ce = cudaMemcpy(m->conn, m->conn_h.data(), sizeof(int32_t) * 3 * K, cudaMemcpyHostToDevice);
+  if (ce == cudaSuccess) {
+    // 1/h = |grad of the face's reference coordinate| for affine triangles
+    auto inv_h = [&](int64_t e, int f) {
+      const double* g = &m->geo_h[4 * e];
+      double gx, gy;
+      if (f == 0) { gx = -g[1]; gy = -g[3]; }
+      else if (f == 1) { gx = g[0] + g[1]; gy = g[2] + g[3]; }
+      else { gx = -g[0]; gy = -g[2]; }
+      return std::sqrt(gx * gx + gy * gy);
+    };
+    std::vector<float> ih(size_t(3) * K);
+    for (int64_t e = 0; e < K; ++e)
+      for (int f = 0; f < 3; ++f) {
+        const int32_t c = m->conn_h[3 * e + f];
+        double v = inv_h(e, f);
+        if (c >= 0) v = std::max(v, inv_h(c >> 2, c & 3));
+        ih[3 * e + f] = float(v);
+      }
+    ce = cudaMalloc(&m->ih32, sizeof(float) * 3 * K);
+    if (ce == cudaSuccess) ce = cudaMemcpy(m->ih32, ih.data(), sizeof(float) * 3 * K, cudaMemcpyHostToDevice);
+  }
   if (ce == cudaSuccess) ce = ensure_ops(m, N);
   if (ce != cudaSuccess) {
     dg_mesh_destroy(m);
@@ -300,6 +322,8 @@ dg_status dg_mesh_destroy(dg_mesh* m) {
   if (!m) return DG_OK;
   free_workspace(m);
   free_ins_workspace(m);
+  cudaFree(m->face32);
+  cudaFree(m->ih32);
   cudaFree(m->geo64);
   cudaFree(m->geo32);
   cudaFree(m->conn);

@@ -370,17 +370,51 @@ cudaError_t launch_n(const dg_mesh* m, dg_prec prec, int B, double lambda, const
 
 }  // namespace
 
-cudaError_t launch_apply(const dg_mesh* m, int degree, dg_prec prec, int B, double lambda, const void* u, void* Au,
+#define DG_TE_DECL(n)                                                                                       \
+  cudaError_t launch_apply_f32_n##n(const dg_mesh* m, int B, double lambda, const float* u, float* Au, float2* face, \
+                                   cudaStream_t st);
+DG_TE_DECL(1) DG_TE_DECL(2) DG_TE_DECL(3) DG_TE_DECL(4) DG_TE_DECL(5) DG_TE_DECL(6) DG_TE_DECL(7) DG_TE_DECL(8)
+#undef DG_TE_DECL
+
+// FP32: register-blocked GEMM kernels (apply_gemm.cuh) with the mesh face scratch;
+// FP64: the tile kernel above.
+cudaError_t launch_apply(const dg_mesh* mc, int degree, dg_prec prec, int B, double lambda, const void* u, void* Au,
                          cudaStream_t st) {
+  if (prec == DG_F32) {
+    dg_mesh* m = const_cast<dg_mesh*>(mc);
+    const int dmax = degree > m->N ? degree : m->N;
+    const size_t need = size_t(B) * size_t(m->K) * 3 * size_t(dmax + 1);
+    if (m->face32_cap < need) {
+      cudaFree(m->face32);
+      m->face32 = nullptr;
+      m->face32_cap = 0;
+      cudaError_t e = cudaMalloc(&m->face32, need * sizeof(float2));
+      if (e != cudaSuccess) return e;
+      m->face32_cap = need;
+    }
+    const float* uf = reinterpret_cast<const float*>(u);
+    float* of = reinterpret_cast<float*>(Au);
+    switch (degree) {
+      case 1: return launch_apply_f32_n1(m, B, lambda, uf, of, m->face32, st);
+      case 2: return launch_apply_f32_n2(m, B, lambda, uf, of, m->face32, st);
+      case 3: return launch_apply_f32_n3(m, B, lambda, uf, of, m->face32, st);
+      case 4: return launch_apply_f32_n4(m, B, lambda, uf, of, m->face32, st);
+      case 5: return launch_apply_f32_n5(m, B, lambda, uf, of, m->face32, st);
+      case 6: return launch_apply_f32_n6(m, B, lambda, uf, of, m->face32, st);
+      case 7: return launch_apply_f32_n7(m, B, lambda, uf, of, m->face32, st);
+      case 8: return launch_apply_f32_n8(m, B, lambda, uf, of, m->face32, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (degree) {
-    case 1: return launch_n<1>(m, prec, B, lambda, u, Au, st);
-    case 2: return launch_n<2>(m, prec, B, lambda, u, Au, st);
-    case 3: return launch_n<3>(m, prec, B, lambda, u, Au, st);
-    case 4: return launch_n<4>(m, prec, B, lambda, u, Au, st);
-    case 5: return launch_n<5>(m, prec, B, lambda, u, Au, st);
-    case 6: return launch_n<6>(m, prec, B, lambda, u, Au, st);
-    case 7: return launch_n<7>(m, prec, B, lambda, u, Au, st);
-    case 8: return launch_n<8>(m, prec, B, lambda, u, Au, st);
+    case 1: return launch_n<1>(mc, prec, B, lambda, u, Au, st);
+    case 2: return launch_n<2>(mc, prec, B, lambda, u, Au, st);
+    case 3: return launch_n<3>(mc, prec, B, lambda, u, Au, st);
+    case 4: return launch_n<4>(mc, prec, B, lambda, u, Au, st);
+    case 5: return launch_n<5>(mc, prec, B, lambda, u, Au, st);
+    case 6: return launch_n<6>(mc, prec, B, lambda, u, Au, st);
+    case 7: return launch_n<7>(mc, prec, B, lambda, u, Au, st);
+    case 8: return launch_n<8>(mc, prec, B, lambda, u, Au, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -1,0 +1,11 @@
+// FP32 SIPDG apply as register-blocked GEMMs, degree N = 1.
+#define GA_N 1
+#define GA_NS ga1
+#include "apply_gemm.cuh"
+
+namespace dgx {
+cudaError_t launch_apply_f32_n1(const dg_mesh* m, int B, double lambda, const float* u, float* Au, float2* face,
+                                cudaStream_t st) {
+  return ga1::launch(m, B, lambda, u, Au, face, st);
+}
+}  // namespace dgx

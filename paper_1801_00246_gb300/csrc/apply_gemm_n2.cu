@@ -1,0 +1,11 @@
+// FP32 SIPDG apply as register-blocked GEMMs, degree N = 2.
+#define GA_N 2
+#define GA_NS ga2
+#include "apply_gemm.cuh"
+
+namespace dgx {
+cudaError_t launch_apply_f32_n2(const dg_mesh* m, int B, double lambda, const float* u, float* Au, float2* face,
+                                cudaStream_t st) {
+  return ga2::launch(m, B, lambda, u, Au, face, st);
+}
+}  // namespace dgx

@@ -1,0 +1,11 @@
+// FP32 SIPDG apply as register-blocked GEMMs, degree N = 8.
+#define GA_N 8
+#define GA_NS ga8
+#include "apply_gemm.cuh"
+
+namespace dgx {
+cudaError_t launch_apply_f32_n8(const dg_mesh* m, int B, double lambda, const float* u, float* Au, float2* face,
+                                cudaStream_t st) {
+  return ga8::launch(m, B, lambda, u, Au, face, st);
+}
+}  // namespace dgx

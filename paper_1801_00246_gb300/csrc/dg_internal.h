@@ -75,12 +75,19 @@ struct dg_mesh {
   double* geo64 = nullptr;   // K x 4
   float* geo32 = nullptr;    // K x 4
   int32_t* conn = nullptr;   // K x 3
+  // per face: max(1/h-, 1/h+) (1/h- on boundary faces); the penalty of a
+  // degree-d operator is (d+1)(d+2)/2 times this
+  float* ih32 = nullptr;     // K x 3
   dgx::RefElem ref[dgx::kMaxN + 1];
   dgx::DevOps ops64[dgx::kMaxN + 1];
   dgx::DevOps ops32[dgx::kMaxN + 1];
   std::map<std::pair<int, int>, dgx::DevTransfer> transfer;
   dgx::Workspace* ws = nullptr;
   dgx::InsWorkspace* ins = nullptr;
+  // FP32 apply scratch: every element's face traces and outward normal
+  // derivatives, [B][K][3][N+1] float2 (grown on demand)
+  float2* face32 = nullptr;
+  size_t face32_cap = 0;
 };
 
 namespace dgx {
