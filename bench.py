@@ -6,7 +6,8 @@ One step = one pass of the hot path over this input:
   * Poisson apply A u in FP64 and in FP32 (U(-1,1) input, seed 1)
   * Helmholtz apply (lambda = 1) in FP64 and in FP32
   * a p-multigrid flexible-CG pressure solve to 1e-10 (V-cycle 8->4->2->1,
-    degree-2 Chebyshev-Jacobi smoothing, degree-1 CG to 1e-2), mixed precision
+    degree-2 Chebyshev-Jacobi smoothing, degree-1 CG to 1e-2 preconditioned by
+    an algebraic-multigrid V-cycle), mixed precision
     (FP32 multigrid levels, FP64 outer iteration)
   * the same solve in plain FP64 (FP64 multigrid levels)
 `value` is the FP64 Poisson apply throughput (GDOF/s = K*Np / apply time);
@@ -202,9 +203,11 @@ def run_ours(args, world, rank, local):
     b = mesh.rhs(torch.from_numpy(fex(xh, yh)).to(dev), torch.from_numpy(uex(xh, yh)).to(dev))
     flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     opts_mixed = P._binding.default_opts(precond=P.PREC_PMG, degrees=PMG_DEGREES, tol=1e-10, max_iter=200,
-                                         mixed=1, cheb_degree=2, coarse_tol=1e-2, coarse_max_iter=500)
+                                         mixed=1, cheb_degree=2, coarse_tol=1e-2, coarse_max_iter=500,
+                                         coarse_amg=1)
     opts_fp64 = P._binding.default_opts(precond=P.PREC_PMG, degrees=PMG_DEGREES, tol=1e-10, max_iter=200,
-                                        mixed=0, cheb_degree=2, coarse_tol=1e-2, coarse_max_iter=500)
+                                        mixed=0, cheb_degree=2, coarse_tol=1e-2, coarse_max_iter=500,
+                                        coarse_amg=1)
 
     def flush():
         flush_buf.fill_(1.0)

@@ -72,6 +72,8 @@ typedef struct {
   int coarse_max_iter; /* iteration cap of that coarse CG */
   int mixed;           /* 1: p-multigrid levels in FP32, outer iteration FP64; 0: all FP64 */
   int power_steps;     /* power iterations for the Chebyshev bound rho(D^{-1}A) */
+  int coarse_amg;      /* 1: the coarsest-degree CG is preconditioned by an algebraic-multigrid
+                          V-cycle (smoothed aggregation on the probed coarsest matrix, FP64) */
 } dg_solver_opts;
 
 #define DG_MAX_BATCH 64
@@ -81,6 +83,7 @@ typedef struct {
   double relres[DG_MAX_BATCH];  /* final ||b - A x|| / ||b|| from the recurrence residual */
   int total_iters;              /* iterations of the batched loop (max over the batch) */
   float ms;                     /* device time of the solve (CUDA events on the stream) */
+  int coarse_iters;             /* coarsest-degree CG iterations summed over the solve */
 } dg_solve_info;
 
 /* Default options: tol 1e-10, max_iter 1000, Jacobi, no multigrid. */

@@ -25,12 +25,12 @@ class SolverOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precond", ctypes.c_int),
                 ("nlevels", ctypes.c_int), ("degrees", ctypes.c_int * 8), ("cheb_degree", ctypes.c_int),
                 ("coarse_tol", ctypes.c_double), ("coarse_max_iter", ctypes.c_int), ("mixed", ctypes.c_int),
-                ("power_steps", ctypes.c_int)]
+                ("power_steps", ctypes.c_int), ("coarse_amg", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int * DG_MAX_BATCH), ("relres", ctypes.c_double * DG_MAX_BATCH),
-                ("total_iters", ctypes.c_int), ("ms", ctypes.c_float)]
+                ("total_iters", ctypes.c_int), ("ms", ctypes.c_float), ("coarse_iters", ctypes.c_int)]
 
 
 class InsState(ctypes.Structure):
@@ -238,7 +238,7 @@ class Mesh:
         if check:
             _check(st)
         res = dict(iters=list(info.iters[:B]), relres=list(info.relres[:B]), total_iters=info.total_iters,
-                   ms=info.ms, status=_STATUS.get(st, st))
+                   ms=info.ms, coarse_iters=info.coarse_iters, status=_STATUS.get(st, st))
         return x, res
 
 

@@ -36,6 +36,12 @@ std::vector<double> invert(int n, std::vector<double> A);
 void vandermonde2d(int N, const std::vector<double>& r, const std::vector<double>& s, std::vector<double>& V,
                    std::vector<double>* Vr, std::vector<double>* Vs);
 struct InsWorkspace;
+struct Amg;
+cudaError_t amg_build(dg_mesh* m, int degree, double lambda, int B, Amg** out, cudaStream_t st);
+cudaError_t amg_vcycle(Amg* a, const double* b, double* x, cudaStream_t st);
+void amg_free(Amg* a);
+int amg_levels(const Amg* a);
+cudaError_t amg_apply_fine(Amg* a, const double* x, double* y, cudaStream_t st);
 void free_ins_workspace(dg_mesh* m);
 
 // Device copy of the reference operators of one degree, in one precision.
@@ -82,7 +88,8 @@ struct dg_mesh {
   dgx::DevOps ops64[dgx::kMaxN + 1];
   dgx::DevOps ops32[dgx::kMaxN + 1];
   std::map<std::pair<int, int>, dgx::DevTransfer> transfer;
-  dgx::Workspace* ws = nullptr;
+  dgx::Workspace* ws = nullptr;  // most recently used solver workspace
+  std::map<std::string, dgx::Workspace*> ws_cache;  // all workspaces, by configuration
   dgx::InsWorkspace* ins = nullptr;
   // FP32 apply scratch: every element's face traces and outward normal
   // derivatives, [B][K][3][N+1] float2 (grown on demand)

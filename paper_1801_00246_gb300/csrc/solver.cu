@@ -58,16 +58,25 @@ struct Workspace {
   std::string dinv_key, pmg_key;
   std::vector<double> rho;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // algebraic multigrid for the coarsest degree, keyed by (degree, lambda, B)
+  Amg* amg = nullptr;
+  std::string amg_key;
+  double* cz = nullptr;  // coarse preconditioned residual
 };
 
-void free_workspace(dg_mesh* m) {
-  Workspace* w = m->ws;
+static void free_one(Workspace* w) {
   if (!w) return;
   for (void* p : w->allocs) cudaFree(p);
+  amg_free(w->amg);
   if (w->h_scal) cudaFreeHost(w->h_scal);
   if (w->ev0) cudaEventDestroy(w->ev0);
   if (w->ev1) cudaEventDestroy(w->ev1);
   delete w;
+}
+
+void free_workspace(dg_mesh* m) {
+  for (auto& kv : m->ws_cache) free_one(kv.second);
+  m->ws_cache.clear();
   m->ws = nullptr;
 }
 
@@ -387,9 +396,13 @@ cudaError_t setup_workspace(Ctx& c) {
   std::string key = std::to_string(c.B) + "/" + std::to_string(pmg) + "/" + std::to_string(o->mixed);
   if (pmg)
     for (int l = 0; l < o->nlevels; ++l) key += "," + std::to_string(o->degrees[l]);
-  if (w && w->pmg_key == key) return cudaSuccess;
-  free_workspace(m);
+  auto it = m->ws_cache.find(key);
+  if (it != m->ws_cache.end()) {
+    m->ws = it->second;
+    return cudaSuccess;
+  }
   w = new Workspace();
+  m->ws_cache[key] = w;
   m->ws = w;
   w->B = c.B;
   w->K = m->K;
@@ -439,6 +452,7 @@ cudaError_t setup_workspace(Ctx& c) {
     CK(walloc(w, &w->cr, nc));
     CK(walloc(w, &w->cp, nc));
     CK(walloc(w, &w->cAp, nc));
+    CK(walloc(w, &w->cz, nc));
     CK(walloc(w, &w->cscal, size_t(c.B) * kNS));
     CK(walloc(w, &w->cpartial, size_t(c.B) * kRedBlocks * 2));
   }
@@ -482,6 +496,55 @@ cudaError_t coarse_cg(Ctx& c, int degree, const double* rhs, double* x, int& ite
       for (int b = 0; b < B; ++b) any = any || w->h_scal[b * kNS + S_ACTIVE] != 0.0;
       if (!any) break;
     }
+  }
+  iters_out = it;
+  return cudaGetLastError();
+}
+
+// CG on the coarsest degree preconditioned by one AMG V-cycle per iteration,
+// to relative tolerance coarse_tol from x = 0 (host check every iteration).
+cudaError_t coarse_pcg_amg(Ctx& c, int degree, const double* rhs, double* x, int& iters_out) {
+  Workspace* w = c.w;
+  const int B = c.B;
+  char key[96];
+  std::snprintf(key, sizeof key, "%d/%.17g/%d", degree, c.lambda, B);
+  if (!w->amg || w->amg_key != key) {
+    amg_free(w->amg);
+    w->amg = nullptr;
+    CK(amg_build(c.m, degree, c.lambda, B, &w->amg, c.st));
+    w->amg_key = key;
+  }
+  const int64_t n = int64_t(c.m->K) * npd(degree);
+  const size_t nt = size_t(n) * B;
+  const dim3 g = vgrid(n, B);
+  CK(cudaMemsetAsync(x, 0, nt * sizeof(double), c.st));
+  CK(cudaMemcpyAsync(w->cr, rhs, nt * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
+  k_init_scal<<<1, 64, 0, c.st>>>(B, w->cscal, c.o->coarse_tol * c.o->coarse_tol); note_launch();
+  k_dot<<<g, kRedThreads, 0, c.st>>>(n, rhs, rhs, w->cpartial); note_launch();
+  k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_INIT_BB, w->cscal, w->cpartial); note_launch();
+  k_init_check<<<B, kRedThreads, 0, c.st>>>(w->cscal, w->cpartial); note_launch();
+  CK(amg_vcycle(w->amg, w->cr, w->cz, c.st));
+  k_dot<<<g, kRedThreads, 0, c.st>>>(n, w->cr, w->cz, w->cpartial); note_launch();
+  k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_INIT_RZ, w->cscal, w->cpartial); note_launch();
+  k_update_p<<<g, kRedThreads, 0, c.st>>>(n, w->cscal, w->cz, w->cp, 1); note_launch();
+  int it = 0;
+  for (; it < c.o->coarse_max_iter;) {
+    CK(amg_apply_fine(w->amg, w->cp, w->cAp, c.st));  // the probed matrix is this degree's operator
+    k_dot<<<g, kRedThreads, 0, c.st>>>(n, w->cp, w->cAp, w->cpartial); note_launch();
+    k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_ALPHA, w->cscal, w->cpartial); note_launch();
+    k_update_xr<<<g, kRedThreads, 0, c.st>>>(n, w->cscal, x, w->cr, w->cp, w->cAp, nullptr, w->cpartial);
+    note_launch();
+    k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_RR, w->cscal, w->cpartial); note_launch();
+    ++it;
+    CK(cudaMemcpyAsync(w->h_scal, w->cscal, sizeof(double) * B * kNS, cudaMemcpyDeviceToHost, c.st));
+    CK(cudaStreamSynchronize(c.st));
+    bool any = false;
+    for (int b = 0; b < B; ++b) any = any || w->h_scal[b * kNS + S_ACTIVE] != 0.0;
+    if (!any) break;
+    CK(amg_vcycle(w->amg, w->cr, w->cz, c.st));
+    k_dot<<<g, kRedThreads, 0, c.st>>>(n, w->cr, w->cz, w->cpartial); note_launch();
+    k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_BETA, w->cscal, w->cpartial); note_launch();
+    k_update_p<<<g, kRedThreads, 0, c.st>>>(n, w->cscal, w->cz, w->cp, 0); note_launch();
   }
   iters_out = it;
   return cudaGetLastError();
@@ -539,11 +602,14 @@ cudaError_t vcycle(Ctx& c, int l, int& coarse_iters) {
   if (l == L - 1) {
     // coarsest degree: CG in FP64 whatever the level precision
     int it = 0;
+    auto solve = [&](const double* r, double* xo) {
+      return c.o->coarse_amg ? coarse_pcg_amg(c, deg, r, xo, it) : coarse_cg(c, deg, r, xo, it);
+    };
     if (std::is_same<T, double>::value) {
-      CK(coarse_cg(c, deg, reinterpret_cast<const double*>(lv[l].rhs), reinterpret_cast<double*>(lv[l].x), it));
+      CK(solve(reinterpret_cast<const double*>(lv[l].rhs), reinterpret_cast<double*>(lv[l].x)));
     } else {
       k_convert<double, T><<<egrid(nt), 256, 0, c.st>>>(nt, lv[l].rhs, c.w->crhs); note_launch();
-      CK(coarse_cg(c, deg, c.w->crhs, c.w->cx, it));
+      CK(solve(c.w->crhs, c.w->cx));
       k_convert<T, double><<<egrid(nt), 256, 0, c.st>>>(nt, c.w->cx, lv[l].x); note_launch();
     }
     coarse_iters += it;
@@ -743,8 +809,8 @@ cudaError_t pcg_run(Ctx& c, const double* b, double* x, dg_solve_info* info, dg_
     }
     info->total_iters = it;
     info->ms = ms;
+    info->coarse_iters = coarse_iters;
   }
-  (void)coarse_iters;
   return cudaSuccess;
 }
 
@@ -766,6 +832,7 @@ void dg_solver_opts_default(dg_solver_opts* o) {
   o->coarse_max_iter = 500;
   o->mixed = 1;
   o->power_steps = 20;
+  o->coarse_amg = 0;
 }
 
 dg_status dg_pcg_solve(dg_mesh* m, const dg_solver_opts* o, int B, double lambda, const double* b, double* x,

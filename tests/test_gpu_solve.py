@@ -92,8 +92,8 @@ def test_not_converged_status_and_last_iterate():
     assert ei.value.name == "DG_ERR_NOT_CONVERGED"
 
 
-@pytest.mark.parametrize("mixed", [1, 0])
-def test_c2_pmg_32768tri_N6(mixed):
+@pytest.mark.parametrize("mixed,amg", [(1, 0), (0, 0), (1, 1), (0, 1)])
+def test_c2_pmg_32768tri_N6(mixed, amg):
     """128x128 jittered grid, N=6, V-cycle 6->3->1, 2 Chebyshev-Jacobi smooths,
     degree-1 CG to 1e-2; u = sin(2 pi x) cos(3 pi y); tolerance 1e-10."""
     P = pkg()
@@ -104,10 +104,24 @@ def test_c2_pmg_32768tri_N6(mixed):
     xn, yn = x_n.cpu().numpy(), y_n.cpu().numpy()
     f, g = cuda(fex(xn, yn)), cuda(uex(xn, yn))
     b = lib.rhs(f, g)
-    x, info = lib.solve(b, precond=P.PREC_PMG, degrees=[6, 3, 1], tol=1e-10, max_iter=300, mixed=mixed)
+    x, info = lib.solve(b, precond=P.PREC_PMG, degrees=[6, 3, 1], tol=1e-10, max_iter=300, mixed=mixed,
+                        coarse_amg=amg)
+    print("c2 pmg mixed=%d amg=%d: %d iterations, %.1f ms" % (mixed, amg, info["iters"][0], info["ms"]))
     assert info["relres"][0] <= 1e-10
     bo = ora.rhs(f.cpu().numpy(), g.cpu().numpy())
     assert rel(b.cpu().numpy(), bo) <= 1e-12
     xs = x.cpu().numpy()
     assert _oracle_relres(ora, xs, bo) <= 1.5e-10
     assert ora.l2_error(xs, uex) < 1e-6
+
+
+def test_amg_coarse_solve_small_and_batched():
+    """AMG-preconditioned coarse CG inside p-multigrid, batched right-hand sides."""
+    P = pkg()
+    m = rotate_local_vertices(jittered_grid(20, 20, seed=3), 4)
+    lib, ora = pair(m, 4)
+    bb = ora.mass_apply(uniform_field((3, m.K, ora.Np), seed=8))
+    x, info = lib.solve(cuda(bb), precond=P.PREC_PMG, degrees=[4, 2, 1], tol=1e-10, max_iter=200, mixed=1,
+                        coarse_amg=1)
+    for k in range(3):
+        assert _oracle_relres(ora, x[k].cpu().numpy(), bb[k]) <= 1.5e-10
