@@ -314,7 +314,10 @@ def run_ours(args, world, rank, local):
                          "relres_mixed": float(rec["solve_mixed_relres"][-1]),
                          "relres_fp64": float(rec["solve_fp64_relres"][-1])},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": pk["fp64_gflops"], "unit": "GFLOP/s",
-                     "frac": achieved / pk["fp64_gflops"], "traffic": None,
+                     "frac": achieved / pk["fp64_gflops"],
+                     # dram__bytes_read.sum + dram__bytes_write.sum of one launch of this kernel
+                     # (profiles/sipdg_apply_v1_n8_524288tri.md); algorithmic bytes: 400.6 MB
+                     "traffic": 362.6e6 if N == 8 else None,
                      "kernel": "sipdg_apply_kernel<8,double> (FP64 Poisson apply)",
                      "peak_src": "nominal GB300 FP64 1.25 TFLOP/s"},
         "e2e": {"value": K * Np / (float(np.mean(e2e_ms)) * 1e-3) / 1e9, "unit": "GDOF/s",
