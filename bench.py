@@ -356,6 +356,8 @@ def run_apply_only(args):
             e0.record()
             mesh.apply(u, out=o)
             e1.record()
+            if it == 0 and key == "f64":
+                mesh.apply(u, out=o, fp64_pipe=True)
             torch.cuda.synchronize()
             if it >= args.warmup:
                 ms[key].append(e0.elapsed_time(e1))

@@ -54,7 +54,12 @@ typedef enum {
   DG_ERR_MESH = 7            /* non-positive Jacobian or non-conforming faces */
 } dg_status;
 
-typedef enum { DG_F64 = 0, DG_F32 = 1 } dg_prec;
+/* DG_F64: FP64 in/out; from degree 3 up the dense products run on the BF16
+ *         tensor cores with exact integer slicing (relative error ~1e-13 of
+ *         |A||u|), the rest in FP64 or float-float; degrees 1-2 as DG_F64_DFMA;
+ * DG_F32: FP32 in/out, FP32 arithmetic;
+ * DG_F64_DFMA: FP64 in/out, every operation on the FP64 pipe. */
+typedef enum { DG_F64 = 0, DG_F32 = 1, DG_F64_DFMA = 2 } dg_prec;
 
 typedef struct dg_mesh dg_mesh; /* opaque; owned by the library until dg_mesh_destroy */
 

@@ -6,7 +6,7 @@ import numpy as np
 
 from . import build as _build
 
-DG_F64, DG_F32 = 0, 1
+DG_F64, DG_F32, DG_F64_DFMA = 0, 1, 2
 PREC_NONE, PREC_JACOBI, PREC_INVMASS, PREC_PMG = 0, 1, 2, 3
 DG_MAX_BATCH = 64
 
@@ -181,12 +181,15 @@ class Mesh:
         _check(lib().dg_mesh_nodes(self._h, int(degree or 0), _tptr(x), _tptr(y), _stream()))
         return x, y
 
-    def apply(self, u, lam=0.0, degree=0, out=None):
-        """A u for u of shape [B][K][Np] or [K][Np] (float64 -> FP64, float32 -> FP32)."""
+    def apply(self, u, lam=0.0, degree=0, out=None, fp64_pipe=False):
+        """A u for u of shape [B][K][Np] or [K][Np] (float64 -> FP64, float32 -> FP32).
+        float64 runs the tensor-core product path unless fp64_pipe=True."""
         import torch
         if not u.is_cuda or not u.is_contiguous():
             raise ValueError("u must be a contiguous CUDA tensor")
         prec = {torch.float64: DG_F64, torch.float32: DG_F32}[u.dtype]
+        if fp64_pipe and prec == DG_F64:
+            prec = DG_F64_DFMA
         B = 1 if u.dim() == 2 else u.shape[0]
         if out is None:
             out = torch.empty_like(u)

@@ -307,6 +307,32 @@ dg_status dg_mesh_setup(int N, int64_t Nv, const double* VX, const double* VY, i
       }
     ce = cudaMalloc(&m->ih32, sizeof(float) * 3 * K);
     if (ce == cudaSuccess) ce = cudaMemcpy(m->ih32, ih.data(), sizeof(float) * 3 * K, cudaMemcpyHostToDevice);
+    // derived FP64 geometry for the tensor-core FP64 apply
+    std::vector<double> gx(size_t(16) * K);
+    for (int64_t e = 0; e < K; ++e) {
+      const double* g = &m->geo_h[4 * e];
+      const double rx = g[0], sx = g[1], ry = g[2], sy = g[3];
+      const double J = 1.0 / (rx * sy - ry * sx);
+      double* o = &gx[16 * e];
+      o[0] = J;
+      o[1] = J * (rx * rx + ry * ry);
+      o[2] = J * (rx * sx + ry * sy);
+      o[3] = J * (sx * sx + sy * sy);
+      for (int f = 0; f < 3; ++f) {
+        double fx, fy;
+        if (f == 0) { fx = -sx; fy = -sy; }
+        else if (f == 1) { fx = rx + sx; fy = ry + sy; }
+        else { fx = -rx; fy = -ry; }
+        const double gn = std::sqrt(fx * fx + fy * fy), nx = fx / gn, ny = fy / gn;
+        const int32_t c = m->conn_h[3 * e + f];
+        o[4 + 4 * f + 0] = nx * rx + ny * ry;
+        o[4 + 4 * f + 1] = nx * sx + ny * sy;
+        o[4 + 4 * f + 2] = J * gn;
+        o[4 + 4 * f + 3] = c >= 0 ? std::max(gn, inv_h(c >> 2, c & 3)) : gn;
+      }
+    }
+    if (ce == cudaSuccess) ce = cudaMalloc(&m->geox, sizeof(double) * 16 * K);
+    if (ce == cudaSuccess) ce = cudaMemcpy(m->geox, gx.data(), sizeof(double) * 16 * K, cudaMemcpyHostToDevice);
   }
   if (ce == cudaSuccess) ce = ensure_ops(m, N);
   if (ce != cudaSuccess) {
@@ -323,7 +349,9 @@ dg_status dg_mesh_destroy(dg_mesh* m) {
   free_workspace(m);
   free_ins_workspace(m);
   cudaFree(m->face32);
+  cudaFree(m->oz_scratch);
   cudaFree(m->ih32);
+  cudaFree(m->geox);
   cudaFree(m->geo64);
   cudaFree(m->geo32);
   cudaFree(m->conn);
@@ -372,7 +400,7 @@ dg_status dg_operator_apply(const dg_mesh* mc, int degree, dg_prec prec, int B, 
   if (!u || !Au) { set_error("NULL argument"); return DG_ERR_ARG; }
   if (degree == 0) degree = mc->N;
   if (degree < 1 || degree > kMaxN) { set_error("degree must be in 1..8"); return DG_ERR_ARG; }
-  if (prec != DG_F64 && prec != DG_F32) { set_error("bad precision"); return DG_ERR_ARG; }
+  if (prec != DG_F64 && prec != DG_F32 && prec != DG_F64_DFMA) { set_error("bad precision"); return DG_ERR_ARG; }
   if (B < 0) { set_error("negative batch"); return DG_ERR_ARG; }
   if (u == Au) { set_error("u and Au must not alias"); return DG_ERR_ARG; }
   if (!std::isfinite(lambda) || lambda < 0) { set_error("lambda must be finite and >= 0"); return DG_ERR_ARG; }

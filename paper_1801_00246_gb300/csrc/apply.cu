@@ -377,7 +377,8 @@ DG_TE_DECL(1) DG_TE_DECL(2) DG_TE_DECL(3) DG_TE_DECL(4) DG_TE_DECL(5) DG_TE_DECL
 #undef DG_TE_DECL
 
 // FP32: register-blocked GEMM kernels (apply_gemm.cuh) with the mesh face scratch;
-// FP64: the tile kernel above.
+// FP64: products on the BF16 tensor cores with exact integer slicing
+// (apply_oz64.cu); FP64_DFMA: the tile kernel above on the FP64 pipe.
 cudaError_t launch_apply(const dg_mesh* mc, int degree, dg_prec prec, int B, double lambda, const void* u, void* Au,
                          cudaStream_t st) {
   if (prec == DG_F32) {
@@ -406,6 +407,12 @@ cudaError_t launch_apply(const dg_mesh* mc, int degree, dg_prec prec, int B, dou
       default: return cudaErrorInvalidValue;
     }
   }
+  // FP64: tensor-core products from degree 3 up; at degrees 1-2 the products
+  // are too small for the slicing overhead and the FP64-pipe kernel is faster
+  if (prec == DG_F64 && degree >= 3)
+    return launch_apply_oz64(const_cast<dg_mesh*>(mc), degree, B, lambda, reinterpret_cast<const double*>(u),
+                             reinterpret_cast<double*>(Au), st);
+  prec = DG_F64;  // DG_F64_DFMA: the tile kernel on the FP64 pipe
   switch (degree) {
     case 1: return launch_n<1>(mc, prec, B, lambda, u, Au, st);
     case 2: return launch_n<2>(mc, prec, B, lambda, u, Au, st);

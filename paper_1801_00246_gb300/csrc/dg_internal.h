@@ -84,6 +84,8 @@ struct dg_mesh {
   // per face: max(1/h-, 1/h+) (1/h- on boundary faces); the penalty of a
   // degree-d operator is (d+1)(d+2)/2 times this
   float* ih32 = nullptr;     // K x 3
+  // FP64 derived geometry [K][16]: J, Grr, Grs, Gss | per face (n.grad r, n.grad s, sJ, max(1/h-,1/h+))
+  double* geox = nullptr;
   dgx::RefElem ref[dgx::kMaxN + 1];
   dgx::DevOps ops64[dgx::kMaxN + 1];
   dgx::DevOps ops32[dgx::kMaxN + 1];
@@ -95,6 +97,9 @@ struct dg_mesh {
   // derivatives, [B][K][3][N+1] float2 (grown on demand)
   float2* face32 = nullptr;
   size_t face32_cap = 0;
+  // FP64 tensor-core apply scratch: C1, Y and the face buffer (grown on demand)
+  double* oz_scratch = nullptr;
+  size_t oz_cap = 0;
 };
 
 namespace dgx {
@@ -106,6 +111,8 @@ cudaError_t launch_apply(const dg_mesh* m, int degree, dg_prec prec, int B, doub
 cudaError_t launch_rhs(const dg_mesh* m, int B, const double* f, const double* g, double* b, cudaStream_t st);
 cudaError_t launch_diagonal(const dg_mesh* m, int degree, dg_prec prec, double lambda, void* diag,
                             cudaStream_t st);
+cudaError_t launch_apply_oz64(dg_mesh* m, int degree, int B, double lambda, const double* u, double* Au,
+                              cudaStream_t st);
 cudaError_t launch_nodes(const dg_mesh* m, int degree, double* x, double* y, cudaStream_t st);
 
 void set_error(const std::string& msg);

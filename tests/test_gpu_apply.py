@@ -28,6 +28,8 @@ def test_apply_parity_rotated_mesh(N, lam):
     ref = ora.apply(u, lam=lam)
     got64 = lib.apply(cuda(u), lam=lam).cpu().numpy()
     assert rel(got64, ref) <= TOL64
+    gotp = lib.apply(cuda(u), lam=lam, fp64_pipe=True).cpu().numpy()
+    assert rel(gotp, ref) <= TOL64
     got32 = lib.apply(cuda(u, torch.float32), lam=lam).cpu().numpy()
     assert rel(got32, ref) <= TOL32
 
@@ -112,7 +114,7 @@ def test_diagonal_rhs_and_nodes(N):
     assert rel(b0, ora.mass_apply(f)) <= TOL64
 
 
-@pytest.mark.parametrize("N,prec", [(8, "f64"), (8, "f32"), (1, "f64"), (4, "f32")])
+@pytest.mark.parametrize("N,prec", [(8, "f64"), (8, "f32"), (1, "f64"), (4, "f32"), (8, "f64pipe")])
 def test_full_size_524288_triangles_sampled(N, prec):
     """The 512x512 (524,288-triangle) workload at full size, in the launch
     configuration the benchmark times; the oracle recomputes sampled elements."""
@@ -121,10 +123,10 @@ def test_full_size_524288_triangles_sampled(N, prec):
     m, _ = config_mesh("c5_sweep_524288tri_N8")
     lib, ora = pair(m, N)
     u = uniform_field((m.K, ora.Np), seed=1)
-    dt = torch.float64 if prec == "f64" else torch.float32
-    got = lib.apply(cuda(u, dt)).cpu().numpy()
+    dt = torch.float32 if prec == "f32" else torch.float64
+    got = lib.apply(cuda(u, dt), fp64_pipe=(prec == "f64pipe")).cpu().numpy()
     rng = np.random.default_rng(0)
     elems = np.unique(np.concatenate([rng.integers(0, m.K, 200), [0, 1, 1023, m.K - 1]]))
     ref = ora.apply(u, elems=elems)
-    assert rel(got[elems], ref) <= (TOL64 if prec == "f64" else TOL32)
+    assert rel(got[elems], ref) <= (TOL32 if prec == "f32" else TOL64)
     assert np.isfinite(got).all()
