@@ -47,7 +47,10 @@ def peaks():
         hbm = float(d.get("hbm_gbs", hbm))
         src = "measured"
     # FP64 CUDA-core peak: the nominal 1.25 TFLOP/s of GB300 (no measured copy in the peaks file)
-    return dict(hbm_gbs=hbm, hbm_src=src, fp64_gflops=1250.0, fp32_gflops=2 * 152 * 128 * 2.07)
+    bf16 = 1895.5
+    if os.path.exists(p):
+        bf16 = float(d.get("bf16_tflops", bf16))
+    return dict(hbm_gbs=hbm, hbm_src=src, fp64_gflops=1250.0, fp32_gflops=2 * 152 * 128 * 2.07, bf16_tflops=bf16)
 
 
 def algo_per_element(N, word):
@@ -298,6 +301,9 @@ def run_ours(args, world, rank, local):
     value = world * K * Np / (ax_ms_max * 1e-3) / 1e9
     fp64_ms = ax["poisson_f64"]["ms"]
     achieved = K * flops / (fp64_ms * 1e-3) / 1e9
+    # BF16 MMA flops the tensor-core FP64 apply issues per launch at N=8 (Poisson):
+    # 36 slice products x 2 flops x padded (rows x depth) of its two products
+    tc_flops = 36 * 2 * (96 * 48 + 48 * 176) * K
     line = {
         "metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -313,13 +319,16 @@ def run_ours(args, world, rank, local):
                          "iters_fp64": int(rec["solve_fp64_iters"][-1]),
                          "relres_mixed": float(rec["solve_mixed_relres"][-1]),
                          "relres_fp64": float(rec["solve_fp64_relres"][-1])},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": pk["fp64_gflops"], "unit": "GFLOP/s",
-                     "frac": achieved / pk["fp64_gflops"],
-                     # dram__bytes_read.sum + dram__bytes_write.sum of one launch of this kernel
-                     # (profiles/sipdg_apply_v1_n8_524288tri.md); algorithmic bytes: 400.6 MB
-                     "traffic": 362.6e6 if N == 8 else None,
-                     "kernel": "sipdg_apply_kernel<8,double> (FP64 Poisson apply)",
-                     "peak_src": "nominal GB300 FP64 1.25 TFLOP/s"},
+        "roofline": {"bound": "tensor", "achieved": tc_flops / (fp64_ms * 1e-3) / 1e12,
+                     "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+                     "frac": tc_flops / (fp64_ms * 1e-3) / 1e12 / pk["bf16_tflops"],
+                     "traffic": None,
+                     "kernel": "FP64 Poisson apply (oz_gemm x2 + oz_face + oz_build_y): BF16 tensor-core products "
+                               "with exact 7-bit slicing, 36 slice products per FP64 product",
+                     "peak_src": "measured cuBLAS bf16 (MEASURED_PEAKS.json); mma.sync m16n8k16 measured "
+                                 "603 TFLOP/s on this GPU",
+                     "fp64_equiv_tflops": achieved / 1e3,
+                     "fp64_pipe_peak_tflops": pk["fp64_gflops"] / 1e3},
         "e2e": {"value": K * Np / (float(np.mean(e2e_ms)) * 1e-3) / 1e9, "unit": "GDOF/s",
                 "h2d_bytes_per_step": int(uh.numel() * 8), "d2h_bytes_per_step": int(oh.numel() * 8)},
         "gpu_launches": launches,
