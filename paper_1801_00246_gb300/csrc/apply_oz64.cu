@@ -22,8 +22,8 @@
 //   OB = [Br Bs | Dr_f^T Mf  Ds_f^T Mf | E_f Mf | M],
 // so the pointwise stage between the two products only forms
 //   Y = [wr; ws; 1/2 nr sJ [u]; 1/2 ns sJ [u]; -sJ ({n.grad u} + tau [u]); lambda J u].
-// Neighbour coupling goes through a face buffer of each element's face-node
-// values and outward normal derivatives (taken from C1), as in the FP32 path.
+// The neighbour's trace and normal derivative at a shared face node are read
+// from its nodal values and its rows of C1.
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -38,8 +38,7 @@ constexpr int kSliceBits = 7;
 constexpr int kGroups = 8;        // i + j = 2..9 -> 8 accumulators
 constexpr int OE = 32;            // elements per CTA tile
 constexpr int ONT = OE / 8;       // n-tiles (8 elements each)
-constexpr int OWARPS = 8;
-constexpr int OTHREADS = OWARPS * 32;
+
 
 // ---------------------------------------------------------------- host side
 // Slices of one FP64 value relative to 2^{scale_exp} (|v| < 2^{scale_exp}):
@@ -153,8 +152,8 @@ __device__ __forceinline__ void slice_dev(double v, int sc, uint16_t (&s)[kSlice
 
 // out[e][r] = sum_k A[r][k] X[e][k] for e < nE, r < M (FP64 in and out).
 // X rows have Kd entries at stride ldx; out rows stride ldo.
-template <int MAXF>
-__global__ void __launch_bounds__(OTHREADS) oz_gemm(int64_t nE, int M, int Kd, int Mt, int Kt,
+template <int MAXF, int OWARPS>
+__global__ void __launch_bounds__(OWARPS * 32) oz_gemm(int64_t nE, int M, int Kd, int Mt, int Kt,
                                                     const uint4* __restrict__ Af, const int* __restrict__ ea,
                                                     const double* __restrict__ X, int64_t ldx,
                                                     double* __restrict__ out, int64_t ldo) {
@@ -164,6 +163,7 @@ __global__ void __launch_bounds__(OTHREADS) oz_gemm(int64_t nE, int M, int Kd, i
   int* exs = reinterpret_cast<int*>(osm + size_t(kSlices) * OE * KP);  // [OE]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
+  constexpr int OTHREADS = OWARPS * 32;
   const int64_t ntiles = (nE + OE - 1) / OE;
   const int nfrag = Mt * ONT;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -244,28 +244,11 @@ __device__ __forceinline__ int fnode_rt(int N, int f, int j) {
   return f == 0 ? j : (f == 1 ? rs(j) + (N - j) : rs(N - j));
 }
 
-// face buffer: per element and face node, (u, n.grad u) from C1 = (ur; us)
-__global__ void oz_face(int N, int64_t K, int B, const double* __restrict__ gx, const double* __restrict__ u,
-                        const double* __restrict__ C1, double2* __restrict__ face) {
-  const int Np = (N + 1) * (N + 2) / 2, Nfp = N + 1, NFN = 3 * Nfp;
-  const int64_t total = int64_t(B) * K * NFN;
-  for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
-       idx += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t be = idx / NFN;
-    const int q = int(idx - be * NFN), f = q / Nfp, j = q - f * Nfp;
-    const int64_t e = be % K;
-    const double* g = gx + 16 * e + 4 + 4 * f;
-    const int k = fnode_rt(N, f, j);
-    const double* c = C1 + be * (2 * Np);
-    face[idx] = make_double2(u[be * Np + k], g[0] * c[k] + g[1] * c[Np + k]);
-  }
-}
-
 // Y rows per element: wr, ws (Np each) | 1/2 nr sJ [u], 1/2 ns sJ [u] (NFN each) |
 // -sJ ({n.grad u} + tau [u]) (NFN) | lambda J u (Np, Helmholtz only)
 __global__ void oz_build_y(int N, int64_t K, int B, int ldy, const double* __restrict__ gx,
                            const int32_t* __restrict__ conn, const double* __restrict__ u,
-                           const double* __restrict__ C1, const double2* __restrict__ face, double lambda,
+                           const double* __restrict__ C1, double lambda,
                            double* __restrict__ Y) {
   const int Np = (N + 1) * (N + 2) / 2, Nfp = N + 1, NFN = 3 * Nfp;
   const double cpen = double((N + 1) * (N + 2)) / 2.0;
@@ -295,9 +278,17 @@ __global__ void oz_build_y(int N, int64_t K, int B, int ldy, const double* __res
       const int code = conn[3 * e + f];
       double jm = 0.0, av = 0.0;
       if (code >= 0) {
-        const double2 p = face[(boff + (code >> 2)) * NFN + (code & 3) * Nfp + (Nfp - 1 - j)];
-        jm = p.x - um;
-        av = 0.5 * (dnm - p.y);
+        // neighbour's trace and its own outward normal derivative at the shared node,
+        // straight from its nodal values and gradient rows (C1)
+        const int64_t nb = code >> 2;
+        const int fn = code & 3;
+        const int kn = fnode_rt(N, fn, Nfp - 1 - j);
+        const double* gn = gx + 16 * nb + 4 + 4 * fn;
+        const double* cn = C1 + (boff + nb) * (2 * Np);
+        const double up = u[(boff + nb) * Np + kn];
+        const double dnp = gn[0] * cn[kn] + gn[1] * cn[Np + kn];
+        jm = up - um;
+        av = 0.5 * (dnm - dnp);
       } else if (code == -2) {
         jm = -2.0 * um;
         av = dnm;
@@ -372,45 +363,53 @@ cudaError_t build_oz_ops(const RefElem& R, OzOps& o) {
   return up(o.ea2h, e2h);
 }
 
-template <int MAXF>
+template <int MAXF, int OWARPS>
 cudaError_t launch_gemm(int64_t nE, int M, int Kd, int Mt, int Kt, const uint4* Af, const int* ea, const double* X,
                         int64_t ldx, double* out, int64_t ldo, cudaStream_t st) {
+  constexpr int OTHREADS = OWARPS * 32;
   const size_t smem = size_t(kSlices) * OE * (Kt * 16 + 8) * sizeof(uint16_t) + OE * sizeof(int);
   static int configured[64][16] = {};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (!configured[dev & 63][Kt & 15]) {
-    e = cudaFuncSetAttribute(oz_gemm<MAXF>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    e = cudaFuncSetAttribute(oz_gemm<MAXF, OWARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     configured[dev & 63][Kt & 15] = 1;
   }
   int sms = 0, per = 0;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, oz_gemm<MAXF>, OTHREADS, smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, oz_gemm<MAXF, OWARPS>, OTHREADS, smem);
   if (e != cudaSuccess) return e;
   const int64_t tiles = (nE + OE - 1) / OE;
   int64_t grid = int64_t(sms) * (per > 0 ? per : 1);
   if (grid > tiles) grid = tiles;
-  oz_gemm<MAXF><<<unsigned(grid), OTHREADS, smem, st>>>(nE, M, Kd, Mt, Kt, Af, ea, X, ldx, out, ldo);
+  oz_gemm<MAXF, OWARPS><<<unsigned(grid), OTHREADS, smem, st>>>(nE, M, Kd, Mt, Kt, Af, ea, X, ldx, out, ldo);
   note_launch();
   return cudaGetLastError();
 }
 
-template <int MAXF>
-cudaError_t gemm_dispatch(int Mt, int64_t nE, int M, int Kd, int Kt, const uint4* Af, const int* ea,
-                          const double* X, int64_t ldx, double* out, int64_t ldo, cudaStream_t st) {
-  return launch_gemm<MAXF>(nE, M, Kd, Mt, Kt, Af, ea, X, ldx, out, ldo, st);
-}
-
+// warps per CTA chosen so every warp gets the same number of fragments
 cudaError_t gemm(int Mt, int64_t nE, int M, int Kd, int Kt, const uint4* Af, const int* ea, const double* X,
                  int64_t ldx, double* out, int64_t ldo, cudaStream_t st) {
   const int nfrag = Mt * ONT;
-  const int maxf = (nfrag + OWARPS - 1) / OWARPS;
-  if (maxf <= 1) return gemm_dispatch<1>(Mt, nE, M, Kd, Kt, Af, ea, X, ldx, out, ldo, st);
-  if (maxf <= 2) return gemm_dispatch<2>(Mt, nE, M, Kd, Kt, Af, ea, X, ldx, out, ldo, st);
-  if (maxf <= 3) return gemm_dispatch<3>(Mt, nE, M, Kd, Kt, Af, ea, X, ldx, out, ldo, st);
-  return gemm_dispatch<4>(Mt, nE, M, Kd, Kt, Af, ea, X, ldx, out, ldo, st);
+  if (nfrag % 8 == 0) {
+    const int f = nfrag / 8;
+    if (f == 1) return launch_gemm<1, 8>(nE, M, Kd, Mt, Kt, Af, ea, X, ldx, out, ldo, st);
+    if (f == 2) return launch_gemm<2, 8>(nE, M, Kd, Mt, Kt, Af, ea, X, ldx, out, ldo, st);
+    if (f == 3) return launch_gemm<3, 8>(nE, M, Kd, Mt, Kt, Af, ea, X, ldx, out, ldo, st);
+  }
+  if (nfrag % 6 == 0 && nfrag / 6 <= 3) {
+    const int f = nfrag / 6;
+    if (f == 1) return launch_gemm<1, 6>(nE, M, Kd, Mt, Kt, Af, ea, X, ldx, out, ldo, st);
+    if (f == 2) return launch_gemm<2, 6>(nE, M, Kd, Mt, Kt, Af, ea, X, ldx, out, ldo, st);
+    return launch_gemm<3, 6>(nE, M, Kd, Mt, Kt, Af, ea, X, ldx, out, ldo, st);
+  }
+  if (nfrag <= 4) return launch_gemm<1, 4>(nE, M, Kd, Mt, Kt, Af, ea, X, ldx, out, ldo, st);
+  const int maxf = (nfrag + 7) / 8;
+  if (maxf <= 2) return launch_gemm<2, 8>(nE, M, Kd, Mt, Kt, Af, ea, X, ldx, out, ldo, st);
+  if (maxf <= 3) return launch_gemm<3, 8>(nE, M, Kd, Mt, Kt, Af, ea, X, ldx, out, ldo, st);
+  return launch_gemm<4, 8>(nE, M, Kd, Mt, Kt, Af, ea, X, ldx, out, ldo, st);
 }
 
 inline int egrid(int64_t n) {
@@ -439,7 +438,7 @@ cudaError_t launch_apply_oz64(dg_mesh* m, int degree, int B, double lambda, cons
   const bool helm = lambda != 0.0;
   const int KY = 2 * Np + 3 * NFN + (helm ? Np : 0);
   const int64_t nE = int64_t(B) * m->K;
-  const size_t need = size_t(nE) * (2 * Np + KY + 2 * NFN);  // doubles: C1, Y, face
+  const size_t need = size_t(nE) * (2 * Np + KY);  // doubles: C1, Y
   if (m->oz_cap < need) {
     cudaFree(m->oz_scratch);
     m->oz_scratch = nullptr;
@@ -450,12 +449,9 @@ cudaError_t launch_apply_oz64(dg_mesh* m, int degree, int B, double lambda, cons
   }
   double* C1 = m->oz_scratch;
   double* Y = C1 + size_t(nE) * 2 * Np;
-  double2* face = reinterpret_cast<double2*>(Y + size_t(nE) * KY);
   e = gemm(o.Mt1, nE, 2 * Np, Np, o.Kt1, o.A1, o.ea1, u, Np, C1, 2 * Np, st);
   if (e != cudaSuccess) return e;
-  oz_face<<<egrid(nE * NFN), 256, 0, st>>>(N, m->K, B, m->geox, u, C1, face);
-  note_launch();
-  oz_build_y<<<egrid(nE * (Np + NFN)), 256, 0, st>>>(N, m->K, B, KY, m->geox, m->conn, u, C1, face, lambda, Y);
+  oz_build_y<<<egrid(nE * (Np + NFN)), 256, 0, st>>>(N, m->K, B, KY, m->geox, m->conn, u, C1, lambda, Y);
   note_launch();
   if (helm)
     e = gemm(o.Mt2, nE, Np, KY, o.Kt2h, o.A2h, o.ea2h, Y, KY, Au, Np, st);
