@@ -10,12 +10,15 @@ One step = one pass of the hot path over this input:
     an algebraic-multigrid V-cycle), mixed precision
     (FP32 multigrid levels, FP64 outer iteration)
   * the same solve in plain FP64 (FP64 multigrid levels)
+  * the mixed solve once more with the host-driven loop (the two solves above
+    run as one CUDA graph each, loops on the device)
 `value` is the FP64 Poisson apply throughput (GDOF/s = K*Np / apply time);
 the other pieces are reported beside it. L2 (135 MB) is flushed by writing a
 256 MB buffer before every timed launch; all timing is CUDA events on the
 launching stream.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --sweep     # applies for N = 1..8, FP64/FP32, batch 1/4/16
 
 `--impl reference` times the FP64 CPU oracle (the method written plainly in
 numpy) on a bounded sample of the same workload, on the host cores.
@@ -208,6 +211,9 @@ def run_ours(args, world, rank, local):
     opts_mixed = P._binding.default_opts(precond=P.PREC_PMG, degrees=PMG_DEGREES, tol=1e-10, max_iter=200,
                                          mixed=1, cheb_degree=2, coarse_tol=1e-2, coarse_max_iter=500,
                                          coarse_amg=1)
+    opts_mixed_host = P._binding.default_opts(precond=P.PREC_PMG, degrees=PMG_DEGREES, tol=1e-10, max_iter=200,
+                                              mixed=1, cheb_degree=2, coarse_tol=1e-2, coarse_max_iter=500,
+                                              coarse_amg=1, graph=0)
     opts_fp64 = P._binding.default_opts(precond=P.PREC_PMG, degrees=PMG_DEGREES, tol=1e-10, max_iter=200,
                                         mixed=0, cheb_degree=2, coarse_tol=1e-2, coarse_max_iter=500,
                                         coarse_amg=1)
@@ -234,6 +240,8 @@ def run_ours(args, world, rank, local):
         ev["solve_mixed"] = timed(lambda: mesh.solve(b, x_m, opts=opts_mixed))
         x_d = torch.zeros_like(b)
         ev["solve_fp64"] = timed(lambda: mesh.solve(b, x_d, opts=opts_fp64))
+        x_h = torch.zeros_like(b)
+        ev["solve_mixed_host_loop"] = timed(lambda: mesh.solve(b, x_h, opts=opts_mixed_host))
         if record is not None:
             torch.cuda.synchronize()
             for k, (e0, e1, r) in ev.items():
@@ -241,6 +249,7 @@ def run_ours(args, world, rank, local):
                 if k.startswith("solve"):
                     record.setdefault(k + "_iters", []).append(r[1]["iters"][0])
                     record.setdefault(k + "_relres", []).append(r[1]["relres"][0])
+                    record.setdefault(k + "_coarse", []).append(r[1]["coarse_iters"])
 
     for _ in range(args.warmup):
         step(None)
@@ -315,15 +324,19 @@ def run_ours(args, world, rank, local):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "ax": ax,
         "pcg_solve_ms": {"mixed": float(np.mean(rec["solve_mixed"])), "fp64": float(np.mean(rec["solve_fp64"])),
+                         "mixed_host_loop": float(np.mean(rec["solve_mixed_host_loop"])),
+                         "graph": "whole solve as one CUDA graph with device-side loops (host loop beside it)",
                          "iters_mixed": int(rec["solve_mixed_iters"][-1]),
                          "iters_fp64": int(rec["solve_fp64_iters"][-1]),
+                         "coarse_iters_mixed": int(rec["solve_mixed_coarse"][-1]),
+                         "coarse_iters_fp64": int(rec["solve_fp64_coarse"][-1]),
                          "relres_mixed": float(rec["solve_mixed_relres"][-1]),
                          "relres_fp64": float(rec["solve_fp64_relres"][-1])},
         "roofline": {"bound": "tensor", "achieved": tc_flops / (fp64_ms * 1e-3) / 1e12,
                      "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
                      "frac": tc_flops / (fp64_ms * 1e-3) / 1e12 / pk["bf16_tflops"],
                      "traffic": None,
-                     "kernel": "FP64 Poisson apply (oz_gemm x2 + oz_face + oz_build_y): BF16 tensor-core products "
+                     "kernel": "FP64 Poisson apply (oz_gemm x2 + oz_build_y): BF16 tensor-core products "
                                "with exact 7-bit slicing, 36 slice products per FP64 product",
                      "peak_src": "measured cuBLAS bf16 (MEASURED_PEAKS.json); mma.sync m16n8k16 measured "
                                  "603 TFLOP/s on this GPU",
@@ -374,6 +387,62 @@ def run_apply_only(args):
                       "ms_f32": float(np.mean(ms["f32"]))}), flush=True)
 
 
+def run_sweep(args):
+    """Throughput sweep of the applies: N = 1..8, Poisson and Helmholtz
+    (lambda = 1), FP64 (tensor-core products from N = 3; the FP64-pipe kernel
+    beside it at B = 1) and FP32, batches 1/4/16. One JSON line per case."""
+    import torch
+    import paper_1801_00246_gb300 as P
+    from paper_1801_00246_gb300 import build
+    from dg_inputs import config_mesh, uniform_field
+    build.build()
+    m, _ = config_mesh(MESH_NAME)
+    pk = peaks()
+    flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    degrees = [int(d) for d in args.sweep_degrees.split(",")]
+    batches = [int(b) for b in args.sweep_batches.split(",")]
+    for N in degrees:
+        mesh = P.Mesh.from_inputs(m, N)
+        K, Np = mesh.K, mesh.Np
+        for B in batches:
+            u64 = torch.from_numpy(uniform_field((B, K, Np), seed=1)).cuda()
+            u32 = u64.float()
+            o64, o32 = torch.empty_like(u64), torch.empty_like(u32)
+            cases = [("f64", u64, o64, False), ("f32", u32, o32, False)]
+            if B == 1:
+                cases.append(("f64_pipe", u64, o64, True))
+            for lam in (0.0, 1.0):
+                for key, u, o, pipe in cases:
+                    ms = []
+                    for it in range(args.warmup + args.steps):
+                        flush_buf.fill_(1.0)
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record()
+                        mesh.apply(u, lam=lam, out=o, fp64_pipe=pipe)
+                        e1.record()
+                        torch.cuda.synchronize()
+                        if it >= args.warmup:
+                            ms.append(e0.elapsed_time(e1))
+                    t = float(np.median(ms)) * 1e-3
+                    word = 4 if key == "f32" else 8
+                    bpe, fpe = algo_per_element(N, word)
+                    fpe += 2 * Np * Np if lam else 0
+                    geo = 4 * word + 12
+                    nbytes = K * (B * (bpe - geo) + geo)
+                    pipe_peak = pk["fp32_gflops"] if key == "f32" else pk["fp64_gflops"]
+                    print(json.dumps({
+                        "sweep": True, "N": N, "Np": Np, "K": K, "B": B, "op": "helmholtz" if lam else "poisson",
+                        "prec": key, "ms": t * 1e3, "gdofs": B * K * Np / t / 1e9,
+                        "hbm_gbs": nbytes / t / 1e9, "hbm_frac": nbytes / t / 1e9 / pk["hbm_gbs"],
+                        "gflops": B * K * fpe / t / 1e9,
+                        "pipe_frac": B * K * fpe / t / 1e9 / pipe_peak,
+                        "t_hbm_ms": nbytes / (pk["hbm_gbs"] * 1e9) * 1e3,
+                        "t_pipe_ms": B * K * fpe / (pipe_peak * 1e9) * 1e3}), flush=True)
+            del u64, u32, o64, o32
+        del mesh
+        torch.cuda.empty_cache()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -383,11 +452,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--apply-only", action="store_true", help="only the Poisson applies (profiling)")
     ap.add_argument("--degree", type=int, default=8, help="degree for --apply-only")
+    ap.add_argument("--sweep", action="store_true", help="apply throughput for N=1..8, FP64/FP32, B=1/4/16")
+    ap.add_argument("--sweep-degrees", default="1,2,3,4,5,6,7,8")
+    ap.add_argument("--sweep-batches", default="1,4,16")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.apply_only:
         run_apply_only(args)
+        return
+    if args.sweep:
+        run_sweep(args)
         return
     world, rank, local = dist_setup(args)
     if args.impl == "reference":

@@ -79,6 +79,11 @@ typedef struct {
   int power_steps;     /* power iterations for the Chebyshev bound rho(D^{-1}A) */
   int coarse_amg;      /* 1: the coarsest-degree CG is preconditioned by an algebraic-multigrid
                           V-cycle (smoothed aggregation on the probed coarsest matrix, FP64) */
+  int graph;           /* 1 (default): the whole solve runs as one CUDA graph whose iteration
+                          loops are device-side conditional WHILE nodes (no host round trip
+                          per iteration); it is captured on the first solve of a configuration
+                          (batch, lambda, options) and replayed afterwards. 0: host-driven
+                          loop. Both give bit-identical results. */
 } dg_solver_opts;
 
 #define DG_MAX_BATCH 64

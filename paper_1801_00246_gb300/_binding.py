@@ -25,7 +25,8 @@ class SolverOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precond", ctypes.c_int),
                 ("nlevels", ctypes.c_int), ("degrees", ctypes.c_int * 8), ("cheb_degree", ctypes.c_int),
                 ("coarse_tol", ctypes.c_double), ("coarse_max_iter", ctypes.c_int), ("mixed", ctypes.c_int),
-                ("power_steps", ctypes.c_int), ("coarse_amg", ctypes.c_int)]
+                ("power_steps", ctypes.c_int), ("coarse_amg", ctypes.c_int),
+                ("graph", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):

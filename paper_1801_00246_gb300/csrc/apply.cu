@@ -392,6 +392,7 @@ cudaError_t launch_apply(const dg_mesh* mc, int degree, dg_prec prec, int B, dou
       cudaError_t e = cudaMalloc(&m->face32, need * sizeof(float2));
       if (e != cudaSuccess) return e;
       m->face32_cap = need;
+      ++m->scratch_gen;
     }
     const float* uf = reinterpret_cast<const float*>(u);
     float* of = reinterpret_cast<float*>(Au);

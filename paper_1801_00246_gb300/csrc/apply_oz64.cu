@@ -368,14 +368,14 @@ cudaError_t launch_gemm(int64_t nE, int M, int Kd, int Mt, int Kt, const uint4* 
                         int64_t ldx, double* out, int64_t ldo, cudaStream_t st) {
   constexpr int OTHREADS = OWARPS * 32;
   const size_t smem = size_t(kSlices) * OE * (Kt * 16 + 8) * sizeof(uint16_t) + OE * sizeof(int);
-  static int configured[64][16] = {};
+  static size_t configured[64] = {};  // per device: the largest dynamic shared memory set for this instantiation
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (!configured[dev & 63][Kt & 15]) {
+  if (configured[dev & 63] < smem) {
     e = cudaFuncSetAttribute(oz_gemm<MAXF, OWARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    configured[dev & 63][Kt & 15] = 1;
+    configured[dev & 63] = smem;
   }
   int sms = 0, per = 0;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -446,6 +446,7 @@ cudaError_t launch_apply_oz64(dg_mesh* m, int degree, int B, double lambda, cons
     e = cudaMalloc(&m->oz_scratch, need * sizeof(double));
     if (e != cudaSuccess) return e;
     m->oz_cap = need;
+    ++m->scratch_gen;
   }
   double* C1 = m->oz_scratch;
   double* Y = C1 + size_t(nE) * 2 * Np;

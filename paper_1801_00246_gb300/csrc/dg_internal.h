@@ -100,6 +100,7 @@ struct dg_mesh {
   // FP64 tensor-core apply scratch: C1, Y and the face buffer (grown on demand)
   double* oz_scratch = nullptr;
   size_t oz_cap = 0;
+  uint64_t scratch_gen = 0;  // bumped whenever face32 or oz_scratch is reallocated
 };
 
 namespace dgx {
@@ -120,5 +121,6 @@ void set_error(const std::string& msg);
 // Running count of kernels this library has launched (all devices, all threads).
 void note_launch();
 uint64_t launch_count();
+void add_launches(int64_t n);
 
 }  // namespace dgx

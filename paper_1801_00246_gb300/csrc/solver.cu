@@ -5,8 +5,9 @@
 // matrix of each element as preconditioner, the pressure system with a
 // multigrid preconditioner that first coarsens the polynomial degree
 // (matrix-free, N -> ... -> 1) and smooths with a degree-2 Chebyshev iteration.
-// Here the degree-1 level is solved by CG to a loose relative tolerance in FP64
-// (in place of the paper's algebraic multigrid tail). With single-precision
+// The coarsest degree is solved in FP64 by CG to a loose relative tolerance,
+// plain or preconditioned by an algebraic-multigrid V-cycle (amg.cu; the
+// paper's pMG-AMG combination). With single-precision
 // multigrid levels the preconditioner is not a fixed SPD operator, so the outer
 // iteration is flexible CG (beta = r_{k+1}.(z_{k+1} - z_k) / r_k.z_k).
 //
@@ -14,6 +15,11 @@
 // scalars (alpha, beta, r.z, ...) in device memory and freezes (alpha = 0) once
 // it has converged. Inner products use a fixed two-pass reduction, so reruns
 // are bitwise identical.
+//
+// By default a solve runs as one CUDA graph: every loop whose trip count the
+// residual decides (the outer iteration, the coarse CG) is a conditional WHILE
+// node, closed by a one-thread kernel that reads the activity flags and sets
+// the node's condition, so no iteration waits on the host.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -32,6 +38,11 @@ constexpr int kNS = 16;          // scalars per right-hand side
 
 // scalar slots
 enum { S_RZ = 0, S_PAP, S_ALPHA, S_RR, S_RZOLD, S_BETA, S_BB, S_ACTIVE, S_ITERS, S_RELRES, S_BREAK, S_TOL2 };
+// graph counters: kernels run inside loop bodies, outer passes, coarse passes
+// (whole solve), coarse passes of the current coarse solve
+enum { G_KERNELS = 0, G_OUTER, G_COARSE_TOTAL, G_COARSE, G_NCTR };
+// capture streams: the top level, outer WHILE, its IF, coarse WHILE, its IF
+constexpr int kCapDepth = 5;
 
 template <typename T>
 struct LevelVecs {
@@ -61,7 +72,16 @@ struct Workspace {
   // algebraic multigrid for the coarsest degree, keyed by (degree, lambda, B)
   Amg* amg = nullptr;
   std::string amg_key;
+  uint64_t amg_gen = 0;  // bumped on every AMG (re)build
   double* cz = nullptr;  // coarse preconditioned residual
+  // whole-solve CUDA graph
+  double *gb = nullptr, *gx = nullptr;  // staged right-hand side and iterate (the graph's fixed addresses)
+  unsigned long long* gctr = nullptr;   // device counters, slots G_*
+  unsigned long long* h_gctr = nullptr; // pinned mirror
+  cudaStream_t cap[kCapDepth] = {};     // capture streams, one per loop nesting depth
+  cudaGraphExec_t gexec = nullptr;
+  std::string gkey;
+  uint64_t g_top = 0;                   // kernels of the graph outside any loop body
 };
 
 static void free_one(Workspace* w) {
@@ -71,6 +91,10 @@ static void free_one(Workspace* w) {
   if (w->h_scal) cudaFreeHost(w->h_scal);
   if (w->ev0) cudaEventDestroy(w->ev0);
   if (w->ev1) cudaEventDestroy(w->ev1);
+  if (w->gexec) cudaGraphExecDestroy(w->gexec);
+  for (cudaStream_t c : w->cap)
+    if (c) cudaStreamDestroy(c);
+  if (w->h_gctr) cudaFreeHost(w->h_gctr);
   delete w;
 }
 
@@ -237,6 +261,41 @@ __global__ void k_update_p(int64_t n, const double* __restrict__ scal, const dou
     p[off + i] = z[off + i] + beta * p[off + i];
 }
 
+// ------------------------------------------------- device-side loop control
+__device__ __forceinline__ bool any_active(const double* scal, int B) {
+  bool any = false;
+  for (int b = 0; b < B; ++b) any = any || scal[b * kNS + S_ACTIVE] != 0.0;
+  return any;
+}
+
+// Before a loop's first pass: reset its pass count, enter if any right-hand
+// side is active and the cap allows a pass.
+__global__ void k_loop_head(const double* __restrict__ scal, int B, unsigned long long* __restrict__ ctr, int slot,
+                            int max_iter, cudaGraphConditionalHandle hw) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  ctr[slot] = 0;
+  cudaGraphSetConditional(hw, (max_iter > 0 && any_active(scal, B)) ? 1u : 0u);
+}
+
+// End of a loop body: count the pass (and the body's kernels), continue while
+// a right-hand side is active and the cap is not reached; `hi` (if has_if)
+// guards the rest of the pass, which runs while any right-hand side is active.
+__global__ void k_loop_tail(const double* __restrict__ scal, int B, unsigned long long* __restrict__ ctr, int slot,
+                            int total_slot, int max_iter, unsigned long long kernels, cudaGraphConditionalHandle hw,
+                            cudaGraphConditionalHandle hi, int has_if) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const bool any = any_active(scal, B);
+  const unsigned long long it = ++ctr[slot];
+  if (total_slot >= 0) ++ctr[total_slot];
+  ctr[G_KERNELS] += kernels;
+  cudaGraphSetConditional(hw, (any && it < (unsigned long long)max_iter) ? 1u : 0u);
+  if (has_if) cudaGraphSetConditional(hi, any ? 1u : 0u);
+}
+
+__global__ void k_count(unsigned long long* __restrict__ ctr, unsigned long long kernels) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) ctr[G_KERNELS] += kernels;
+}
+
 // r = b - Ax
 template <typename T>
 __global__ void k_sub(int64_t n, const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ out) {
@@ -359,11 +418,20 @@ inline int egrid(int64_t n) {
   return int(b < 1 ? 1 : b);
 }
 
-#define CK(x)                              \
-  do {                                     \
-    cudaError_t e_ = (x);                  \
-    if (e_ != cudaSuccess) return e_;      \
+// the first failing call of a solve, for the error message
+thread_local char g_fail_where[160] = "";
+inline cudaError_t note_fail(cudaError_t e, const char* what, int line) {
+  if (g_fail_where[0] == 0) std::snprintf(g_fail_where, sizeof g_fail_where, "%.120s (solver.cu:%d)", what, line);
+  return e;
+}
+
+#define CK(x)                                                 \
+  do {                                                        \
+    cudaError_t e_ = (x);                                     \
+    if (e_ != cudaSuccess) return note_fail(e_, #x, __LINE__); \
   } while (0)
+
+struct GraphState;
 
 struct Ctx {
   dg_mesh* m;
@@ -372,7 +440,77 @@ struct Ctx {
   double lambda;
   cudaStream_t st;
   Workspace* w;
+  GraphState* g = nullptr;  // non-null while the solve is being captured
 };
+
+// Capture bookkeeping: the stream of each open loop body, and the kernel count
+// at its start (so each body's closing kernel can count its own kernels).
+struct Frame {
+  cudaStream_t outer;
+  uint64_t n0;
+  uint64_t nested;  // kernels captured in bodies nested inside this one
+};
+struct GraphState {
+  int depth = 0;
+  std::vector<Frame> frames;
+  uint64_t root_nested = 0;
+};
+
+// Creates a condition handle in the graph being captured on c.st.
+cudaError_t cond_handle(Ctx& c, cudaGraphConditionalHandle* h) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamGetCaptureInfo(c.st, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+  if (cs != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+  return cudaGraphConditionalHandleCreate(h, g, 0, 0);
+}
+
+// Appends a conditional node after the work captured so far on c.st and
+// redirects c.st into its body until cond_close.
+cudaError_t cond_open(Ctx& c, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type) {
+  GraphState* G = c.g;
+  if (G->depth + 1 >= kCapDepth) return cudaErrorNotSupported;
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  CK(cudaStreamGetCaptureInfo(c.st, &cs, nullptr, &g, &deps, nullptr, &nd));
+  if (cs != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+  cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+  p.conditional.handle = h;
+  p.conditional.type = type;
+  p.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  CK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &p));
+  CK(cudaStreamUpdateCaptureDependencies(c.st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  cudaStream_t body = c.w->cap[G->depth + 1];
+  CK(cudaStreamBeginCaptureToGraph(body, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                   cudaStreamCaptureModeRelaxed));
+  G->frames.push_back({c.st, launch_count(), 0});
+  ++G->depth;
+  c.st = body;
+  return cudaSuccess;
+}
+
+// kernels captured so far in the innermost open body, plus one for the kernel about to close it
+uint64_t body_kernels(Ctx& c) {
+  const Frame& f = c.g->frames.back();
+  return launch_count() - f.n0 - f.nested + 1;
+}
+
+cudaError_t cond_close(Ctx& c) {
+  GraphState* G = c.g;
+  const Frame f = G->frames.back();
+  G->frames.pop_back();
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c.st, &g);
+  c.st = f.outer;
+  --G->depth;
+  const uint64_t total = launch_count() - f.n0;
+  if (G->frames.empty()) G->root_nested += total;
+  else G->frames.back().nested += total;
+  return e;
+}
 
 cudaError_t ensure_transfer(dg_mesh* m, int Nf, int Nc) {
   auto key = std::make_pair(Nf, Nc);
@@ -460,8 +598,9 @@ cudaError_t setup_workspace(Ctx& c) {
 }
 
 // Plain CG on the coarsest degree in FP64 to relative tolerance coarse_tol,
-// starting from x = 0. Convergence is checked on the host every `chk` steps;
-// converged right-hand sides are frozen on the device in between.
+// starting from x = 0. Host-driven, convergence is checked every `chk` steps
+// and converged right-hand sides stay frozen on the device in between; in a
+// captured solve the loop is a device-side WHILE node checked every pass.
 cudaError_t coarse_cg(Ctx& c, int degree, const double* rhs, double* x, int& iters_out) {
   Workspace* w = c.w;
   const int B = c.B;
@@ -477,9 +616,7 @@ cudaError_t coarse_cg(Ctx& c, int degree, const double* rhs, double* x, int& ite
   k_init_check<<<B, kRedThreads, 0, c.st>>>(w->cscal, w->cpartial); note_launch();  // r = b: r.r = b.b
   k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_INIT_RZ, w->cscal, w->cpartial); note_launch();
   k_update_p<<<g, kRedThreads, 0, c.st>>>(n, w->cscal, w->cr, w->cp, 1); note_launch();
-  const int chk = 8;
-  int it = 0;
-  for (; it < c.o->coarse_max_iter;) {
+  auto pass = [&]() -> cudaError_t {
     CK(launch_apply(c.m, degree, DG_F64, B, c.lambda, w->cp, w->cAp, c.st));
     k_dot<<<g, kRedThreads, 0, c.st>>>(n, w->cp, w->cAp, w->cpartial); note_launch();
     k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_ALPHA, w->cscal, w->cpartial); note_launch();
@@ -488,6 +625,24 @@ cudaError_t coarse_cg(Ctx& c, int degree, const double* rhs, double* x, int& ite
     k_dot<<<g, kRedThreads, 0, c.st>>>(n, w->cr, w->cr, w->cpartial); note_launch();
     k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_BETA, w->cscal, w->cpartial); note_launch();
     k_update_p<<<g, kRedThreads, 0, c.st>>>(n, w->cscal, w->cr, w->cp, 0); note_launch();
+    return cudaSuccess;
+  };
+  if (c.g) {
+    cudaGraphConditionalHandle hw = 0;
+    CK(cond_handle(c, &hw));
+    k_loop_head<<<1, 32, 0, c.st>>>(w->cscal, B, w->gctr, G_COARSE, c.o->coarse_max_iter, hw); note_launch();
+    CK(cond_open(c, hw, cudaGraphCondTypeWhile));
+    CK(pass());
+    k_loop_tail<<<1, 32, 0, c.st>>>(w->cscal, B, w->gctr, G_COARSE, G_COARSE_TOTAL, c.o->coarse_max_iter,
+                                    body_kernels(c), hw, 0, 0); note_launch();
+    CK(cond_close(c));
+    iters_out = 0;  // counted on the device
+    return cudaGetLastError();
+  }
+  const int chk = 8;
+  int it = 0;
+  for (; it < c.o->coarse_max_iter;) {
+    CK(pass());
     ++it;
     if (it % chk == 0 || it == c.o->coarse_max_iter) {
       CK(cudaMemcpyAsync(w->h_scal, w->cscal, sizeof(double) * B * kNS, cudaMemcpyDeviceToHost, c.st));
@@ -501,19 +656,29 @@ cudaError_t coarse_cg(Ctx& c, int degree, const double* rhs, double* x, int& ite
   return cudaGetLastError();
 }
 
+// The algebraic multigrid of the coarsest degree for this batch and lambda
+// (built on the host from the probed matrix; never while a solve is captured).
+cudaError_t ensure_amg(Ctx& c, int degree) {
+  Workspace* w = c.w;
+  char key[96];
+  std::snprintf(key, sizeof key, "%d/%.17g/%d", degree, c.lambda, c.B);
+  if (w->amg && w->amg_key == key) return cudaSuccess;
+  if (c.g) return cudaErrorStreamCaptureUnsupported;
+  amg_free(w->amg);
+  w->amg = nullptr;
+  CK(amg_build(c.m, degree, c.lambda, c.B, &w->amg, c.st));
+  w->amg_key = key;
+  ++w->amg_gen;
+  return cudaSuccess;
+}
+
 // CG on the coarsest degree preconditioned by one AMG V-cycle per iteration,
-// to relative tolerance coarse_tol from x = 0 (host check every iteration).
+// to relative tolerance coarse_tol from x = 0 (host check every iteration, or
+// a device-side WHILE node in a captured solve).
 cudaError_t coarse_pcg_amg(Ctx& c, int degree, const double* rhs, double* x, int& iters_out) {
   Workspace* w = c.w;
   const int B = c.B;
-  char key[96];
-  std::snprintf(key, sizeof key, "%d/%.17g/%d", degree, c.lambda, B);
-  if (!w->amg || w->amg_key != key) {
-    amg_free(w->amg);
-    w->amg = nullptr;
-    CK(amg_build(c.m, degree, c.lambda, B, &w->amg, c.st));
-    w->amg_key = key;
-  }
+  CK(ensure_amg(c, degree));
   const int64_t n = int64_t(c.m->K) * npd(degree);
   const size_t nt = size_t(n) * B;
   const dim3 g = vgrid(n, B);
@@ -527,24 +692,49 @@ cudaError_t coarse_pcg_amg(Ctx& c, int degree, const double* rhs, double* x, int
   k_dot<<<g, kRedThreads, 0, c.st>>>(n, w->cr, w->cz, w->cpartial); note_launch();
   k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_INIT_RZ, w->cscal, w->cpartial); note_launch();
   k_update_p<<<g, kRedThreads, 0, c.st>>>(n, w->cscal, w->cz, w->cp, 1); note_launch();
-  int it = 0;
-  for (; it < c.o->coarse_max_iter;) {
+  auto half1 = [&]() -> cudaError_t {
     CK(amg_apply_fine(w->amg, w->cp, w->cAp, c.st));  // the probed matrix is this degree's operator
     k_dot<<<g, kRedThreads, 0, c.st>>>(n, w->cp, w->cAp, w->cpartial); note_launch();
     k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_ALPHA, w->cscal, w->cpartial); note_launch();
     k_update_xr<<<g, kRedThreads, 0, c.st>>>(n, w->cscal, x, w->cr, w->cp, w->cAp, nullptr, w->cpartial);
     note_launch();
     k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_RR, w->cscal, w->cpartial); note_launch();
+    return cudaSuccess;
+  };
+  auto half2 = [&]() -> cudaError_t {
+    CK(amg_vcycle(w->amg, w->cr, w->cz, c.st));
+    k_dot<<<g, kRedThreads, 0, c.st>>>(n, w->cr, w->cz, w->cpartial); note_launch();
+    k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_BETA, w->cscal, w->cpartial); note_launch();
+    k_update_p<<<g, kRedThreads, 0, c.st>>>(n, w->cscal, w->cz, w->cp, 0); note_launch();
+    return cudaSuccess;
+  };
+  if (c.g) {
+    cudaGraphConditionalHandle hw = 0, hi = 0;
+    CK(cond_handle(c, &hw));
+    k_loop_head<<<1, 32, 0, c.st>>>(w->cscal, B, w->gctr, G_COARSE, c.o->coarse_max_iter, hw); note_launch();
+    CK(cond_open(c, hw, cudaGraphCondTypeWhile));
+    CK(half1());
+    CK(cond_handle(c, &hi));
+    k_loop_tail<<<1, 32, 0, c.st>>>(w->cscal, B, w->gctr, G_COARSE, G_COARSE_TOTAL, c.o->coarse_max_iter,
+                                    body_kernels(c), hw, hi, 1); note_launch();
+    CK(cond_open(c, hi, cudaGraphCondTypeIf));
+    CK(half2());
+    k_count<<<1, 32, 0, c.st>>>(w->gctr, body_kernels(c)); note_launch();
+    CK(cond_close(c));
+    CK(cond_close(c));
+    iters_out = 0;
+    return cudaGetLastError();
+  }
+  int it = 0;
+  for (; it < c.o->coarse_max_iter;) {
+    CK(half1());
     ++it;
     CK(cudaMemcpyAsync(w->h_scal, w->cscal, sizeof(double) * B * kNS, cudaMemcpyDeviceToHost, c.st));
     CK(cudaStreamSynchronize(c.st));
     bool any = false;
     for (int b = 0; b < B; ++b) any = any || w->h_scal[b * kNS + S_ACTIVE] != 0.0;
     if (!any) break;
-    CK(amg_vcycle(w->amg, w->cr, w->cz, c.st));
-    k_dot<<<g, kRedThreads, 0, c.st>>>(n, w->cr, w->cz, w->cpartial); note_launch();
-    k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_BETA, w->cscal, w->cpartial); note_launch();
-    k_update_p<<<g, kRedThreads, 0, c.st>>>(n, w->cscal, w->cz, w->cp, 0); note_launch();
+    CK(half2());
   }
   iters_out = it;
   return cudaGetLastError();
@@ -729,6 +919,222 @@ cudaError_t precondition(Ctx& c, int& coarse_iters) {
 
 }  // namespace
 
+// ------------------------------------------------------------ outer iteration
+// Start: scalars, r = b - A x, z = M^{-1} r, r.z, p = z.
+cudaError_t pcg_start(Ctx& c, const double* b, double* x, int& coarse_iters) {
+  Workspace* w = c.w;
+  const int B = c.B;
+  const int64_t n = int64_t(c.m->K) * npd(c.m->N);
+  const int64_t nt = n * B;
+  const dim3 g = vgrid(n, B);
+  k_init_scal<<<1, 64, 0, c.st>>>(B, w->scal, c.o->tol * c.o->tol); note_launch();
+  k_dot<<<g, kRedThreads, 0, c.st>>>(n, b, b, w->partial); note_launch();
+  k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_INIT_BB, w->scal, w->partial); note_launch();
+  CK(launch_apply(c.m, c.m->N, DG_F64, B, c.lambda, x, w->Ap, c.st));
+  k_sub<double><<<egrid(nt), 256, 0, c.st>>>(nt, b, w->Ap, w->r); note_launch();
+  k_dot<<<g, kRedThreads, 0, c.st>>>(n, w->r, w->r, w->partial); note_launch();
+  k_init_check<<<B, kRedThreads, 0, c.st>>>(w->scal, w->partial); note_launch();
+  CK(precondition(c, coarse_iters));
+  k_dot<<<g, kRedThreads, 0, c.st>>>(n, w->r, w->z, w->partial); note_launch();
+  k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_INIT_RZ, w->scal, w->partial); note_launch();
+  k_update_p<<<g, kRedThreads, 0, c.st>>>(n, w->scal, w->z, w->p, 1); note_launch();
+  return cudaGetLastError();
+}
+
+// First half of a pass: A p, alpha, x += alpha p, r -= alpha A p, r.r (convergence).
+cudaError_t pcg_half1(Ctx& c, double* x, bool flexible) {
+  Workspace* w = c.w;
+  const int B = c.B;
+  const int64_t n = int64_t(c.m->K) * npd(c.m->N);
+  const dim3 g = vgrid(n, B);
+  CK(launch_apply(c.m, c.m->N, DG_F64, B, c.lambda, w->p, w->Ap, c.st));
+  k_dot<<<g, kRedThreads, 0, c.st>>>(n, w->p, w->Ap, w->partial); note_launch();
+  k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_ALPHA, w->scal, w->partial); note_launch();
+  k_update_xr<<<g, kRedThreads, 0, c.st>>>(n, w->scal, x, w->r, w->p, w->Ap, flexible ? w->z : nullptr, w->partial); note_launch();
+  k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_RR, w->scal, w->partial); note_launch();
+  return cudaGetLastError();
+}
+
+// Second half: z = M^{-1} r, beta, p = z + beta p.
+cudaError_t pcg_half2(Ctx& c, bool flexible, int& coarse_iters) {
+  Workspace* w = c.w;
+  const int B = c.B;
+  const int64_t n = int64_t(c.m->K) * npd(c.m->N);
+  const dim3 g = vgrid(n, B);
+  CK(precondition(c, coarse_iters));
+  k_dot<<<g, kRedThreads, 0, c.st>>>(n, w->r, w->z, w->partial); note_launch();
+  k_finalize<<<B, kRedThreads, 0, c.st>>>(flexible ? FIN_BETA_FLEX : FIN_BETA, w->scal, w->partial); note_launch();
+  k_update_p<<<g, kRedThreads, 0, c.st>>>(n, w->scal, w->z, w->p, 0); note_launch();
+  return cudaGetLastError();
+}
+
+// Host-driven loop: the residual check reads the scalars back every `chk` passes.
+cudaError_t pcg_eager(Ctx& c, const double* b, double* x, int& it, int& coarse_iters) {
+  Workspace* w = c.w;
+  const dg_solver_opts* o = c.o;
+  const int B = c.B;
+  const bool flexible = o->precond == DG_PREC_PMG;
+  CK(cudaEventRecord(w->ev0, c.st));
+  CK(pcg_start(c, b, x, coarse_iters));
+  CK(cudaMemcpyAsync(w->h_scal, w->scal, sizeof(double) * B * kNS, cudaMemcpyDeviceToHost, c.st));
+  CK(cudaStreamSynchronize(c.st));
+  bool any = false;
+  for (int bb = 0; bb < B; ++bb) any = any || w->h_scal[bb * kNS + S_ACTIVE] != 0.0;
+  it = 0;
+  const int chk = flexible ? 1 : 4;
+  while (any && it < o->max_iter) {
+    CK(pcg_half1(c, x, flexible));
+    ++it;
+    if (it % chk == 0 || it == o->max_iter) {
+      CK(cudaMemcpyAsync(w->h_scal, w->scal, sizeof(double) * B * kNS, cudaMemcpyDeviceToHost, c.st));
+      CK(cudaStreamSynchronize(c.st));
+      any = false;
+      for (int bb = 0; bb < B; ++bb) any = any || w->h_scal[bb * kNS + S_ACTIVE] != 0.0;
+      if (!any) break;
+    }
+    CK(pcg_half2(c, flexible, coarse_iters));
+  }
+  CK(cudaEventRecord(w->ev1, c.st));
+  return cudaSuccess;
+}
+
+// Every (degree, precision) the solve applies, once on zeroed scratch, so that
+// all lazily sized buffers and uploaded operators exist before the capture
+// (allocations are not captured).
+cudaError_t warm_applies(Ctx& c) {
+  Workspace* w = c.w;
+  const dg_solver_opts* o = c.o;
+  const size_t nt = size_t(c.m->K) * npd(c.m->N) * c.B;
+  CK(cudaMemsetAsync(w->p, 0, nt * sizeof(double), c.st));
+  CK(launch_apply(c.m, c.m->N, DG_F64, c.B, c.lambda, w->p, w->Ap, c.st));
+  if (o->precond != DG_PREC_PMG) return cudaGetLastError();
+  const int L = o->nlevels;
+  for (int l = 0; l + 1 < L; ++l) {
+    const size_t nl = size_t(c.m->K) * npd(o->degrees[l]) * c.B;
+    if (o->mixed) {
+      CK(cudaMemsetAsync(w->lv32[l].d, 0, nl * sizeof(float), c.st));
+      CK(launch_apply(c.m, o->degrees[l], DG_F32, c.B, c.lambda, w->lv32[l].d, w->lv32[l].Ad, c.st));
+    } else {
+      CK(cudaMemsetAsync(w->lv64[l].d, 0, nl * sizeof(double), c.st));
+      CK(launch_apply(c.m, o->degrees[l], DG_F64, c.B, c.lambda, w->lv64[l].d, w->lv64[l].Ad, c.st));
+    }
+  }
+  if (!o->coarse_amg) {
+    const size_t nc = size_t(c.m->K) * npd(o->degrees[L - 1]) * c.B;
+    CK(cudaMemsetAsync(w->cp, 0, nc * sizeof(double), c.st));
+    CK(launch_apply(c.m, o->degrees[L - 1], DG_F64, c.B, c.lambda, w->cp, w->cAp, c.st));
+  }
+  return cudaGetLastError();
+}
+
+// Everything a captured graph has baked in: batch, lambda, options, the
+// scratch and AMG buffers it addresses, and the smoother bounds.
+std::string graph_key(const Ctx& c) {
+  const dg_solver_opts* o = c.o;
+  char buf[400];
+  std::snprintf(buf, sizeof buf, "%d|%.17g|%.17g|%d|%d|%d|%d|%.17g|%d|%d|%d|%d|%llu|%llu|%s|", c.B, c.lambda, o->tol,
+                o->max_iter, o->precond, o->nlevels, o->cheb_degree, o->coarse_tol, o->coarse_max_iter, o->mixed,
+                o->power_steps, o->coarse_amg, (unsigned long long)c.m->scratch_gen,
+                (unsigned long long)c.w->amg_gen, c.w->dinv_key.c_str());
+  std::string k = buf;
+  for (int l = 0; l < o->nlevels && l < 8; ++l) k += std::to_string(o->degrees[l]) + ",";
+  return k;
+}
+
+// The captured solve: counters reset, start, then
+//   WHILE (active and passes < max_iter) { first half; tail; IF (active) { second half } }
+cudaError_t capture_body(Ctx& c) {
+  Workspace* w = c.w;
+  const bool flexible = c.o->precond == DG_PREC_PMG;
+  int unused = 0;
+  CK(cudaMemsetAsync(w->gctr, 0, sizeof(unsigned long long) * G_NCTR, c.st));
+  CK(pcg_start(c, w->gb, w->gx, unused));
+  cudaGraphConditionalHandle hw = 0, hi = 0;
+  CK(cond_handle(c, &hw));
+  k_loop_head<<<1, 32, 0, c.st>>>(w->scal, c.B, w->gctr, G_OUTER, c.o->max_iter, hw); note_launch();
+  CK(cond_open(c, hw, cudaGraphCondTypeWhile));
+  CK(pcg_half1(c, w->gx, flexible));
+  CK(cond_handle(c, &hi));
+  k_loop_tail<<<1, 32, 0, c.st>>>(w->scal, c.B, w->gctr, G_OUTER, -1, c.o->max_iter, body_kernels(c), hw, hi, 1);
+  note_launch();
+  CK(cond_open(c, hi, cudaGraphCondTypeIf));
+  CK(pcg_half2(c, flexible, unused));
+  k_count<<<1, 32, 0, c.st>>>(w->gctr, body_kernels(c)); note_launch();
+  CK(cond_close(c));
+  CK(cond_close(c));
+  return cudaGetLastError();
+}
+
+cudaError_t capture_solve(Ctx& c, const std::string& key) {
+  Workspace* w = c.w;
+  if (w->gexec) {
+    cudaGraphExecDestroy(w->gexec);
+    w->gexec = nullptr;
+    w->gkey.clear();
+  }
+  GraphState G;
+  Ctx cc = c;
+  cc.g = &G;
+  cc.st = w->cap[0];
+  const uint64_t n0 = launch_count();
+  CK(cudaStreamBeginCapture(cc.st, cudaStreamCaptureModeRelaxed));
+  cudaError_t e = capture_body(cc);
+  // close whatever a failure left open, innermost first
+  while (!G.frames.empty()) {
+    cudaGraph_t dummy = nullptr;
+    cudaStreamEndCapture(cc.st, &dummy);
+    cc.st = G.frames.back().outer;
+    G.frames.pop_back();
+  }
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(cc.st, &graph);
+  const uint64_t total = launch_count() - n0;
+  add_launches(-int64_t(total));  // counted when they run
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) {
+    w->g_top = total - G.root_nested;
+    e = cudaGraphInstantiate(&w->gexec, graph, 0);
+  }
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    w->gexec = nullptr;
+    return e;
+  }
+  w->gkey = key;
+  return cudaSuccess;
+}
+
+// Captured loop: stage b and x, replay the graph, read the scalars back once.
+cudaError_t pcg_graph(Ctx& c, const double* b, double* x, int& it, int& coarse_iters) {
+  Workspace* w = c.w;
+  const size_t nt = size_t(c.m->K) * npd(c.m->N) * c.B;
+  if (!w->gb) {
+    CK(walloc(w, &w->gb, nt));
+    CK(walloc(w, &w->gx, nt));
+    CK(walloc(w, &w->gctr, size_t(G_NCTR)));
+    CK(cudaMallocHost(&w->h_gctr, sizeof(unsigned long long) * G_NCTR));
+    for (cudaStream_t& s : w->cap) CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  }
+  if (!w->gexec || w->gkey != graph_key(c)) {
+    CK(warm_applies(c));
+    CK(cudaStreamSynchronize(c.st));
+    CK(capture_solve(c, graph_key(c)));
+  }
+  CK(cudaEventRecord(w->ev0, c.st));
+  CK(cudaMemcpyAsync(w->gb, b, nt * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
+  CK(cudaMemcpyAsync(w->gx, x, nt * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
+  CK(cudaGraphLaunch(w->gexec, c.st));
+  CK(cudaMemcpyAsync(x, w->gx, nt * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
+  CK(cudaEventRecord(w->ev1, c.st));
+  add_launches(int64_t(w->g_top));
+  CK(cudaMemcpyAsync(w->h_gctr, w->gctr, sizeof(unsigned long long) * G_NCTR, cudaMemcpyDeviceToHost, c.st));
+  CK(cudaStreamSynchronize(c.st));
+  add_launches(int64_t(w->h_gctr[G_KERNELS]));
+  it = int(w->h_gctr[G_OUTER]);
+  coarse_iters = int(w->h_gctr[G_COARSE_TOTAL]);
+  return cudaSuccess;
+}
+
 // Outer (flexible) PCG. Returns a cudaError_t; solver status in `status`.
 cudaError_t pcg_run(Ctx& c, const double* b, double* x, dg_solve_info* info, dg_status& status) {
   CK(setup_workspace(c));
@@ -737,9 +1143,6 @@ cudaError_t pcg_run(Ctx& c, const double* b, double* x, dg_solve_info* info, dg_
   const dg_solver_opts* o = c.o;
   const int B = c.B;
   const int64_t n = int64_t(c.m->K) * npd(c.m->N);
-  const int64_t nt = n * B;
-  const dim3 g = vgrid(n, B);
-  const bool flexible = o->precond == DG_PREC_PMG;
   std::string key;
   if (o->precond == DG_PREC_JACOBI) {
     char buf[48];
@@ -751,46 +1154,11 @@ cudaError_t pcg_run(Ctx& c, const double* b, double* x, dg_solve_info* info, dg_
     }
   } else if (o->precond == DG_PREC_PMG) {
     CK(setup_pmg(c, key));
+    if (o->coarse_amg) CK(ensure_amg(c, o->degrees[o->nlevels - 1]));
   }
-  CK(cudaEventRecord(w->ev0, c.st));
-  int coarse_iters = 0;
-  k_init_scal<<<1, 64, 0, c.st>>>(B, w->scal, o->tol * o->tol); note_launch();
-  k_dot<<<g, kRedThreads, 0, c.st>>>(n, b, b, w->partial); note_launch();
-  k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_INIT_BB, w->scal, w->partial); note_launch();
-  CK(launch_apply(c.m, c.m->N, DG_F64, B, c.lambda, x, w->Ap, c.st));
-  k_sub<double><<<egrid(nt), 256, 0, c.st>>>(nt, b, w->Ap, w->r); note_launch();
-  k_dot<<<g, kRedThreads, 0, c.st>>>(n, w->r, w->r, w->partial); note_launch();
-  k_init_check<<<B, kRedThreads, 0, c.st>>>(w->scal, w->partial); note_launch();
-  CK(precondition(c, coarse_iters));
-  k_dot<<<g, kRedThreads, 0, c.st>>>(n, w->r, w->z, w->partial); note_launch();
-  k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_INIT_RZ, w->scal, w->partial); note_launch();
-  k_update_p<<<g, kRedThreads, 0, c.st>>>(n, w->scal, w->z, w->p, 1); note_launch();
-  CK(cudaMemcpyAsync(w->h_scal, w->scal, sizeof(double) * B * kNS, cudaMemcpyDeviceToHost, c.st));
-  CK(cudaStreamSynchronize(c.st));
-  bool any = false;
-  for (int bb = 0; bb < B; ++bb) any = any || w->h_scal[bb * kNS + S_ACTIVE] != 0.0;
-  int it = 0;
-  const int chk = (o->precond == DG_PREC_PMG) ? 1 : 4;
-  while (any && it < o->max_iter) {
-    CK(launch_apply(c.m, c.m->N, DG_F64, B, c.lambda, w->p, w->Ap, c.st));
-    k_dot<<<g, kRedThreads, 0, c.st>>>(n, w->p, w->Ap, w->partial); note_launch();
-    k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_ALPHA, w->scal, w->partial); note_launch();
-    k_update_xr<<<g, kRedThreads, 0, c.st>>>(n, w->scal, x, w->r, w->p, w->Ap, flexible ? w->z : nullptr, w->partial); note_launch();
-    k_finalize<<<B, kRedThreads, 0, c.st>>>(FIN_RR, w->scal, w->partial); note_launch();
-    ++it;
-    if (it % chk == 0 || it == o->max_iter) {
-      CK(cudaMemcpyAsync(w->h_scal, w->scal, sizeof(double) * B * kNS, cudaMemcpyDeviceToHost, c.st));
-      CK(cudaStreamSynchronize(c.st));
-      any = false;
-      for (int bb = 0; bb < B; ++bb) any = any || w->h_scal[bb * kNS + S_ACTIVE] != 0.0;
-      if (!any) break;
-    }
-    CK(precondition(c, coarse_iters));
-    k_dot<<<g, kRedThreads, 0, c.st>>>(n, w->r, w->z, w->partial); note_launch();
-    k_finalize<<<B, kRedThreads, 0, c.st>>>(flexible ? FIN_BETA_FLEX : FIN_BETA, w->scal, w->partial); note_launch();
-    k_update_p<<<g, kRedThreads, 0, c.st>>>(n, w->scal, w->z, w->p, 0); note_launch();
-  }
-  CK(cudaEventRecord(w->ev1, c.st));
+  int it = 0, coarse_iters = 0;
+  if (o->graph) CK(pcg_graph(c, b, x, it, coarse_iters));
+  else CK(pcg_eager(c, b, x, it, coarse_iters));
   CK(cudaMemcpyAsync(w->h_scal, w->scal, sizeof(double) * B * kNS, cudaMemcpyDeviceToHost, c.st));
   CK(cudaStreamSynchronize(c.st));
   float ms = 0.f;
@@ -833,6 +1201,7 @@ void dg_solver_opts_default(dg_solver_opts* o) {
   o->mixed = 1;
   o->power_steps = 20;
   o->coarse_amg = 0;
+  o->graph = 1;
 }
 
 dg_status dg_pcg_solve(dg_mesh* m, const dg_solver_opts* o, int B, double lambda, const double* b, double* x,
@@ -861,9 +1230,10 @@ dg_status dg_pcg_solve(dg_mesh* m, const dg_solver_opts* o, int B, double lambda
   try {
     Ctx c{m, o, B, lambda, (cudaStream_t)stream, m->ws};
     dg_status st = DG_OK;
+    g_fail_where[0] = 0;
     cudaError_t e = pcg_run(c, b, x, info, st);
     if (e != cudaSuccess) {
-      set_error(std::string("dg_pcg_solve: ") + cudaGetErrorString(e));
+      set_error(std::string("dg_pcg_solve: ") + cudaGetErrorString(e) + " at " + g_fail_where);
       return e == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA;
     }
     if (st == DG_ERR_NOT_CONVERGED) set_error("dg_pcg_solve: max_iter reached before tol");
