@@ -389,8 +389,9 @@ def run_apply_only(args):
 
 def run_sweep(args):
     """Throughput sweep of the applies: N = 1..8, Poisson and Helmholtz
-    (lambda = 1), FP64 (tensor-core products from N = 3; the FP64-pipe kernel
-    beside it at B = 1) and FP32, batches 1/4/16. One JSON line per case."""
+    (lambda = 1), FP64 and FP32, batches 1/4/16, every available kernel
+    (tile, FP32 GEMM, tensor-core FP64, element per thread). One JSON line per
+    case; `default` marks the kernel the library picks without tuning."""
     import torch
     import paper_1801_00246_gb300 as P
     from paper_1801_00246_gb300 import build
@@ -401,6 +402,7 @@ def run_sweep(args):
     flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     degrees = [int(d) for d in args.sweep_degrees.split(",")]
     batches = [int(b) for b in args.sweep_batches.split(",")]
+    names = {P.KERNEL_TILE: "tile", P.KERNEL_GEMM: "gemm", P.KERNEL_TENSOR: "tensor", P.KERNEL_EPT: "ept"}
     for N in degrees:
         mesh = P.Mesh.from_inputs(m, N)
         K, Np = mesh.K, mesh.Np
@@ -408,36 +410,41 @@ def run_sweep(args):
             u64 = torch.from_numpy(uniform_field((B, K, Np), seed=1)).cuda()
             u32 = u64.float()
             o64, o32 = torch.empty_like(u64), torch.empty_like(u32)
-            cases = [("f64", u64, o64, False), ("f32", u32, o32, False)]
-            if B == 1:
-                cases.append(("f64_pipe", u64, o64, True))
             for lam in (0.0, 1.0):
-                for key, u, o, pipe in cases:
-                    ms = []
-                    for it in range(args.warmup + args.steps):
-                        flush_buf.fill_(1.0)
-                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                        e0.record()
-                        mesh.apply(u, lam=lam, out=o, fp64_pipe=pipe)
-                        e1.record()
-                        torch.cuda.synchronize()
-                        if it >= args.warmup:
-                            ms.append(e0.elapsed_time(e1))
-                    t = float(np.median(ms)) * 1e-3
-                    word = 4 if key == "f32" else 8
-                    bpe, fpe = algo_per_element(N, word)
-                    fpe += 2 * Np * Np if lam else 0
-                    geo = 4 * word + 12
-                    nbytes = K * (B * (bpe - geo) + geo)
-                    pipe_peak = pk["fp32_gflops"] if key == "f32" else pk["fp64_gflops"]
-                    print(json.dumps({
-                        "sweep": True, "N": N, "Np": Np, "K": K, "B": B, "op": "helmholtz" if lam else "poisson",
-                        "prec": key, "ms": t * 1e3, "gdofs": B * K * Np / t / 1e9,
-                        "hbm_gbs": nbytes / t / 1e9, "hbm_frac": nbytes / t / 1e9 / pk["hbm_gbs"],
-                        "gflops": B * K * fpe / t / 1e9,
-                        "pipe_frac": B * K * fpe / t / 1e9 / pipe_peak,
-                        "t_hbm_ms": nbytes / (pk["hbm_gbs"] * 1e9) * 1e3,
-                        "t_pipe_ms": B * K * fpe / (pipe_peak * 1e9) * 1e3}), flush=True)
+                for key, prec, u, o in (("f64", P.DG_F64, u64, o64), ("f32", P.DG_F32, u32, o32)):
+                    default = mesh.kernel(N, prec, lam != 0.0)
+                    ks = [P.KERNEL_TILE, P.KERNEL_TENSOR if key == "f64" else P.KERNEL_GEMM]
+                    if N <= 3:
+                        ks.append(P.KERNEL_EPT)
+                    for k in ks:
+                        mesh.set_kernel(N, prec, lam != 0.0, k)
+                        ms = []
+                        for it in range(args.warmup + args.steps):
+                            flush_buf.fill_(1.0)
+                            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                            e0.record()
+                            mesh.apply(u, lam=lam, out=o)
+                            e1.record()
+                            torch.cuda.synchronize()
+                            if it >= args.warmup:
+                                ms.append(e0.elapsed_time(e1))
+                        t = float(np.median(ms)) * 1e-3
+                        word = 4 if key == "f32" else 8
+                        bpe, fpe = algo_per_element(N, word)
+                        fpe += 2 * Np * Np if lam else 0
+                        geo = 4 * word + 12
+                        nbytes = K * (B * (bpe - geo) + geo)
+                        pipe_peak = pk["fp32_gflops"] if key == "f32" else pk["fp64_gflops"]
+                        print(json.dumps({
+                            "sweep": True, "N": N, "Np": Np, "K": K, "B": B,
+                            "op": "helmholtz" if lam else "poisson", "prec": key, "kernel": names[k],
+                            "default": k == default, "ms": t * 1e3, "gdofs": B * K * Np / t / 1e9,
+                            "hbm_gbs": nbytes / t / 1e9, "hbm_frac": nbytes / t / 1e9 / pk["hbm_gbs"],
+                            "gflops": B * K * fpe / t / 1e9,
+                            "pipe_frac": B * K * fpe / t / 1e9 / pipe_peak,
+                            "t_hbm_ms": nbytes / (pk["hbm_gbs"] * 1e9) * 1e3,
+                            "t_pipe_ms": B * K * fpe / (pipe_peak * 1e9) * 1e3}), flush=True)
+                    mesh.set_kernel(N, prec, lam != 0.0, P.KERNEL_AUTO)
             del u64, u32, o64, o32
         del mesh
         torch.cuda.empty_cache()

@@ -54,14 +54,26 @@ typedef enum {
   DG_ERR_MESH = 7            /* non-positive Jacobian or non-conforming faces */
 } dg_status;
 
-/* DG_F64: FP64 in/out; from degree 3 up the dense products run on the BF16
- *         tensor cores with exact integer slicing (relative error ~1e-13 of
- *         |A||u|), the rest in FP64 or float-float; degrees 1-2 as DG_F64_DFMA;
- * DG_F32: FP32 in/out, FP32 arithmetic;
- * DG_F64_DFMA: FP64 in/out, every operation on the FP64 pipe. */
+/* DG_F64: FP64 in/out with the mesh's FP64 kernel (DG_KERNEL_* below; built-in:
+ *         from degree 3 up the dense products run on the BF16 tensor cores with
+ *         exact integer slicing, relative error ~1e-13 of |A||u|);
+ * DG_F32: FP32 in/out, FP32 arithmetic, with the mesh's FP32 kernel;
+ * DG_F64_DFMA: FP64 in/out, the tile kernel, every operation on the FP64 pipe. */
 typedef enum { DG_F64 = 0, DG_F32 = 1, DG_F64_DFMA = 2 } dg_prec;
 
 typedef struct dg_mesh dg_mesh; /* opaque; owned by the library until dg_mesh_destroy */
+
+/* Apply kernels. Every one evaluates the same operator (Eq. ellipticOp3);
+ * they differ in how the work maps to the GPU, and results agree to rounding.
+ *   DG_KERNEL_AUTO:   the mesh's current choice (built-in per degree, or set
+ *                     by dg_autotune / dg_set_apply_kernel)
+ *   DG_KERNEL_TILE:   element tiles in shared memory, one thread per node
+ *                     (FP64 on the FP64 pipe, or FP32); all degrees
+ *   DG_KERNEL_GEMM:   FP32 only: register-blocked small GEMMs over element tiles; all degrees
+ *   DG_KERNEL_TENSOR: FP64 only: dense products on the BF16 tensor cores with
+ *                     exact integer slicing; all degrees
+ *   DG_KERNEL_EPT:    one element per thread, operators in constant memory; degrees 1-3 */
+enum { DG_KERNEL_AUTO = 0, DG_KERNEL_TILE = 1, DG_KERNEL_GEMM = 2, DG_KERNEL_TENSOR = 3, DG_KERNEL_EPT = 4 };
 
 /* Preconditioner choices for dg_pcg_solve (Section 3). */
 enum { DG_PREC_NONE = 0, DG_PREC_JACOBI = 1, DG_PREC_INVMASS = 2, DG_PREC_PMG = 3 };
@@ -137,6 +149,28 @@ dg_status dg_helmholtz_apply(const dg_mesh* mesh, dg_prec prec, int B, double la
 /* Either operator at any degree 1..8 on the same mesh (p-multigrid levels). */
 dg_status dg_operator_apply(const dg_mesh* mesh, int degree, dg_prec prec, int B, double lambda,
                             const void* u, void* Au, void* stream);
+
+/* The mesh's kernel table: which DG_KERNEL_* the applies (and every solve's
+ * applies) of `degree` in `prec` (DG_F64 or DG_F32), Poisson (helmholtz = 0) or
+ * Helmholtz (1), use. DG_KERNEL_AUTO restores the built-in choice. A kernel
+ * not available for the degree and precision is rejected (DG_ERR_ARG). Not
+ * thread-safe against applies in flight on the same mesh from other threads. */
+dg_status dg_set_apply_kernel(dg_mesh* mesh, int degree, dg_prec prec, int helmholtz, int kernel);
+/* The kernel in use (never DG_KERNEL_AUTO); -1 for bad arguments. */
+int dg_get_apply_kernel(const dg_mesh* mesh, int degree, dg_prec prec, int helmholtz);
+
+/* Autotuner: for each degree in [degree_lo, degree_hi] and both precisions,
+ * times every available kernel on this mesh with B random right-hand sides
+ * (256 MB L2 flush before each of three timed launches, best kept), for the
+ * Poisson form and, if lambda > 0, the Helmholtz form (with lambda = 0 the
+ * Helmholtz entry takes the Poisson winner), and stores the fastest in the
+ * kernel table. times (host, may be NULL): float[9][2][2][5] milliseconds
+ * indexed [degree][0: FP64, 1: FP32][helmholtz][kernel], 0 where not timed.
+ * Allocates and frees its own scratch (4 fields of B*K*Np(degree_hi) values
+ * plus 256 MB); synchronises `stream`. Solves captured as CUDA graphs before
+ * the call are re-captured on their next use. */
+dg_status dg_autotune(dg_mesh* mesh, int B, double lambda, int degree_lo, int degree_hi, float* times,
+                      void* stream);
 
 /* diag(A) of the operator at `degree` (0 = mesh degree) for the given lambda:
  * diag device [K][Np(degree)] in FP64 or FP32 (Jacobi preconditioner). */

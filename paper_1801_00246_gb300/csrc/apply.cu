@@ -376,13 +376,47 @@ cudaError_t launch_n(const dg_mesh* m, dg_prec prec, int B, double lambda, const
 DG_TE_DECL(1) DG_TE_DECL(2) DG_TE_DECL(3) DG_TE_DECL(4) DG_TE_DECL(5) DG_TE_DECL(6) DG_TE_DECL(7) DG_TE_DECL(8)
 #undef DG_TE_DECL
 
-// FP32: register-blocked GEMM kernels (apply_gemm.cuh) with the mesh face scratch;
-// FP64: products on the BF16 tensor cores with exact integer slicing
-// (apply_oz64.cu); FP64_DFMA: the tile kernel above on the FP64 pipe.
+// Kernel choice: the tile kernel above (FP64 or FP32), register-blocked FP32
+// GEMMs (apply_gemm.cuh, with the mesh face scratch), FP64 products on the BF16
+// tensor cores with exact integer slicing (apply_oz64.cu), or one element per
+// thread (apply_ept.cu). DG_F64_DFMA forces the tile kernel in FP64.
+
+// Built-in kernel per degree and precision (the measured winners on the
+// 524,288-triangle workload; dg_autotune replaces them per mesh).
+int default_kernel(int degree, bool f64) {
+  if (f64) return degree >= 3 ? DG_KERNEL_TENSOR : DG_KERNEL_EPT;
+  return degree <= 3 ? DG_KERNEL_EPT : DG_KERNEL_GEMM;
+}
+
+bool kernel_valid(int kernel, int degree, bool f64) {
+  switch (kernel) {
+    case DG_KERNEL_TILE: return true;
+    case DG_KERNEL_GEMM: return !f64;
+    case DG_KERNEL_TENSOR: return f64;
+    case DG_KERNEL_EPT: return ept_supported(degree);
+    default: return false;
+  }
+}
+
 cudaError_t launch_apply(const dg_mesh* mc, int degree, dg_prec prec, int B, double lambda, const void* u, void* Au,
                          cudaStream_t st) {
-  if (prec == DG_F32) {
-    dg_mesh* m = const_cast<dg_mesh*>(mc);
+  dg_mesh* m = const_cast<dg_mesh*>(mc);
+  const bool helm = lambda != 0.0;
+  int k;
+  if (prec == DG_F64_DFMA) {  // the tile kernel on the FP64 pipe, whatever the table says
+    k = DG_KERNEL_TILE;
+    prec = DG_F64;
+  } else {
+    k = m->kern[degree][prec == DG_F32 ? 1 : 0][helm ? 1 : 0];
+    if (k == DG_KERNEL_AUTO) k = default_kernel(degree, prec == DG_F64);
+  }
+  const bool f64 = prec == DG_F64;
+  if (!kernel_valid(k, degree, f64)) return cudaErrorInvalidValue;
+  if (k == DG_KERNEL_EPT) return launch_apply_ept(m, degree, f64, B, lambda, u, Au, st);
+  if (k == DG_KERNEL_TENSOR)
+    return launch_apply_oz64(m, degree, B, lambda, reinterpret_cast<const double*>(u), reinterpret_cast<double*>(Au),
+                             st);
+  if (k == DG_KERNEL_GEMM) {
     const int dmax = degree > m->N ? degree : m->N;
     const size_t need = size_t(B) * size_t(m->K) * 3 * size_t(dmax + 1);
     if (m->face32_cap < need) {
@@ -408,13 +442,7 @@ cudaError_t launch_apply(const dg_mesh* mc, int degree, dg_prec prec, int B, dou
       default: return cudaErrorInvalidValue;
     }
   }
-  // FP64: tensor-core products from degree 3 up; at degrees 1-2 the products
-  // are too small for the slicing overhead and the FP64-pipe kernel is faster
-  if (prec == DG_F64 && degree >= 3)
-    return launch_apply_oz64(const_cast<dg_mesh*>(mc), degree, B, lambda, reinterpret_cast<const double*>(u),
-                             reinterpret_cast<double*>(Au), st);
-  prec = DG_F64;  // DG_F64_DFMA: the tile kernel on the FP64 pipe
-  switch (degree) {
+  switch (degree) {  // DG_KERNEL_TILE, FP64 or FP32
     case 1: return launch_n<1>(mc, prec, B, lambda, u, Au, st);
     case 2: return launch_n<2>(mc, prec, B, lambda, u, Au, st);
     case 3: return launch_n<3>(mc, prec, B, lambda, u, Au, st);

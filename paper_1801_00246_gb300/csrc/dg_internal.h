@@ -101,6 +101,9 @@ struct dg_mesh {
   double* oz_scratch = nullptr;
   size_t oz_cap = 0;
   uint64_t scratch_gen = 0;  // bumped whenever face32 or oz_scratch is reallocated
+  // apply kernel per [degree][0: FP64, 1: FP32][Helmholtz]; DG_KERNEL_AUTO = built-in choice
+  int8_t kern[dgx::kMaxN + 1][2][2] = {};
+  uint64_t kern_gen = 0;  // bumped whenever the table changes
 };
 
 namespace dgx {
@@ -112,6 +115,11 @@ cudaError_t launch_apply(const dg_mesh* m, int degree, dg_prec prec, int B, doub
 cudaError_t launch_rhs(const dg_mesh* m, int B, const double* f, const double* g, double* b, cudaStream_t st);
 cudaError_t launch_diagonal(const dg_mesh* m, int degree, dg_prec prec, double lambda, void* diag,
                             cudaStream_t st);
+int default_kernel(int degree, bool f64);
+bool kernel_valid(int kernel, int degree, bool f64);
+bool ept_supported(int degree);
+cudaError_t launch_apply_ept(dg_mesh* m, int degree, bool f64, int B, double lambda, const void* u, void* Au,
+                             cudaStream_t st);
 cudaError_t launch_apply_oz64(dg_mesh* m, int degree, int B, double lambda, const double* u, double* Au,
                               cudaStream_t st);
 cudaError_t launch_nodes(const dg_mesh* m, int degree, double* x, double* y, cudaStream_t st);

@@ -1028,14 +1028,15 @@ cudaError_t warm_applies(Ctx& c) {
 }
 
 // Everything a captured graph has baked in: batch, lambda, options, the
-// scratch and AMG buffers it addresses, and the smoother bounds.
+// scratch and AMG buffers it addresses, the apply kernels chosen, and the
+// smoother bounds.
 std::string graph_key(const Ctx& c) {
   const dg_solver_opts* o = c.o;
   char buf[400];
-  std::snprintf(buf, sizeof buf, "%d|%.17g|%.17g|%d|%d|%d|%d|%.17g|%d|%d|%d|%d|%llu|%llu|%s|", c.B, c.lambda, o->tol,
-                o->max_iter, o->precond, o->nlevels, o->cheb_degree, o->coarse_tol, o->coarse_max_iter, o->mixed,
-                o->power_steps, o->coarse_amg, (unsigned long long)c.m->scratch_gen,
-                (unsigned long long)c.w->amg_gen, c.w->dinv_key.c_str());
+  std::snprintf(buf, sizeof buf, "%d|%.17g|%.17g|%d|%d|%d|%d|%.17g|%d|%d|%d|%d|%llu|%llu|%llu|%s|", c.B, c.lambda,
+                o->tol, o->max_iter, o->precond, o->nlevels, o->cheb_degree, o->coarse_tol, o->coarse_max_iter,
+                o->mixed, o->power_steps, o->coarse_amg, (unsigned long long)c.m->scratch_gen,
+                (unsigned long long)c.m->kern_gen, (unsigned long long)c.w->amg_gen, c.w->dinv_key.c_str());
   std::string k = buf;
   for (int l = 0; l < o->nlevels && l < 8; ++l) k += std::to_string(o->degrees[l]) + ",";
   return k;
