@@ -450,6 +450,33 @@ def run_sweep(args):
         torch.cuda.empty_cache()
 
 
+def run_solve_only(args):
+    """One mixed-precision pMG-FCG solve on the N=8 workload inside an NVTX
+    range "timed_solve" (after a set-up solve), for per-kernel launch lists."""
+    import torch
+    import paper_1801_00246_gb300 as P
+    from paper_1801_00246_gb300 import build
+    from dg_inputs import config_mesh, manufactured
+    build.build()
+    m, _ = config_mesh(MESH_NAME)
+    mesh = P.Mesh.from_inputs(m, 8)
+    xn, yn = mesh.nodes()
+    uex, fex = manufactured("sin_2pi_x_cos_3pi_y")
+    xh, yh = xn.cpu().numpy(), yn.cpu().numpy()
+    dev = xn.device
+    b = mesh.rhs(torch.from_numpy(fex(xh, yh)).to(dev), torch.from_numpy(uex(xh, yh)).to(dev))
+    opts = P._binding.default_opts(precond=P.PREC_PMG, degrees=PMG_DEGREES, tol=1e-10, max_iter=200,
+                                   mixed=0 if args.fp64 else 1, coarse_amg=1, graph=args.graph)
+    mesh.solve(b, torch.zeros_like(b), opts=opts)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("timed_solve")
+    _, info = mesh.solve(b, torch.zeros_like(b), opts=opts)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"solve_only": True, "mixed": not args.fp64, "graph": args.graph, "ms": info["ms"],
+                      "iters": info["iters"][0], "coarse_iters": info["coarse_iters"]}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -460,6 +487,9 @@ def main():
     ap.add_argument("--apply-only", action="store_true", help="only the Poisson applies (profiling)")
     ap.add_argument("--degree", type=int, default=8, help="degree for --apply-only")
     ap.add_argument("--sweep", action="store_true", help="apply throughput for N=1..8, FP64/FP32, B=1/4/16")
+    ap.add_argument("--solve-only", action="store_true", help="one N=8 pMG-FCG solve in an NVTX range (profiling)")
+    ap.add_argument("--graph", type=int, default=1, help="--solve-only: 1 = CUDA-graph solve, 0 = host loop")
+    ap.add_argument("--fp64", action="store_true", help="--solve-only: FP64 multigrid levels")
     ap.add_argument("--sweep-degrees", default="1,2,3,4,5,6,7,8")
     ap.add_argument("--sweep-batches", default="1,4,16")
     args = ap.parse_args()
@@ -470,6 +500,9 @@ def main():
         return
     if args.sweep:
         run_sweep(args)
+        return
+    if args.solve_only:
+        run_solve_only(args)
         return
     world, rank, local = dist_setup(args)
     if args.impl == "reference":

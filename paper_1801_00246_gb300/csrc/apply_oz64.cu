@@ -22,8 +22,10 @@
 //   OB = [Br Bs | Dr_f^T Mf  Ds_f^T Mf | E_f Mf | M],
 // so the pointwise stage between the two products only forms
 //   Y = [wr; ws; 1/2 nr sJ [u]; 1/2 ns sJ [u]; -sJ ({n.grad u} + tau [u]); lambda J u].
-// The neighbour's trace and normal derivative at a shared face node are read
-// from its nodal values and its rows of C1.
+// The pointwise stage runs inside the output product's slicing phase (Y is
+// built in shared memory, never in HBM); the neighbour's trace and normal
+// derivative at a shared face node are read from its nodal values and its
+// rows of C1.
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -150,6 +152,64 @@ __device__ __forceinline__ void slice_dev(double v, int sc, uint16_t (&s)[kSlice
   }
 }
 
+// The product phase of a tile: out[e0 + n][r] = sum_k A[r][k] X[n][k] from the
+// data slices Xs (per element n: scale exponent exs[n]) and the operator's
+// fragment-ordered slices Af (row exponents ea). Warp w takes fragments
+// w, w + OWARPS, ... (a fragment: 16 operator rows x 8 elements).
+template <int MAXF, int OWARPS>
+__device__ __forceinline__ void oz_mma_tile(const uint16_t* __restrict__ Xs, const int* __restrict__ exs, int KP,
+                                            int M, int Mt, int Kt, int ne, int64_t e0,
+                                            const uint4* __restrict__ Af, const int* __restrict__ ea,
+                                            double* __restrict__ out, int64_t ldo) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int nfrag = Mt * ONT;
+#pragma unroll 1
+  for (int q = 0; q < MAXF; ++q) {
+    const int f = warp + OWARPS * q;
+    if (f >= nfrag) break;
+    const int mt = f / ONT, nt = f - mt * ONT;
+    float acc[kGroups][4];
+#pragma unroll
+    for (int s = 0; s < kGroups; ++s) acc[s][0] = acc[s][1] = acc[s][2] = acc[s][3] = 0.f;
+    for (int kt = 0; kt < Kt; ++kt) {
+      uint32_t b0[kSlices], b1[kSlices];
+#pragma unroll
+      for (int j = 0; j < kSlices; ++j) {
+        const uint16_t* col = Xs + (size_t(j) * OE + nt * 8 + g) * KP + kt * 16 + 2 * t;
+        b0[j] = *reinterpret_cast<const uint32_t*>(col);
+        b1[j] = *reinterpret_cast<const uint32_t*>(col + 8);
+      }
+#pragma unroll
+      for (int i = 0; i < kSlices; ++i) {
+        const uint4 a = __ldg(Af + ((size_t(i) * Mt + mt) * Kt + kt) * 32 + lane);
+#pragma unroll
+        for (int j = 0; j < kSlices - i; ++j) mma_bf16(acc[i + j], a, b0[j], b1[j]);
+      }
+    }
+    // recombine: value = 2^{ea_r + ex_e - 14} sum_s acc[s] 2^{-7 s}
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float h = acc[kGroups - 1][c], l = 0.f;
+#pragma unroll
+      for (int s = kGroups - 2; s >= 0; --s) {
+        const float hs = h * 0.0078125f, ls = l * 0.0078125f;  // exact scaling by 2^-7
+        const float sum = acc[s][c] + hs;
+        const float bb = sum - acc[s][c];
+        const float err = (acc[s][c] - (sum - bb)) + (hs - bb);
+        h = sum;
+        l = ls + err;
+      }
+      const int r = mt * 16 + g + ((c & 2) ? 8 : 0);
+      const int n = nt * 8 + 2 * t + (c & 1);
+      if (r < M && n < ne) {
+        const int sc = ea[r] + exs[n] - 14;
+        out[(e0 + n) * ldo + r] = f2d_scaled(h, sc) + f2d_scaled(l, sc);
+      }
+    }
+  }
+}
+
 // out[e][r] = sum_k A[r][k] X[e][k] for e < nE, r < M (FP64 in and out).
 // X rows have Kd entries at stride ldx; out rows stride ldo.
 template <int MAXF, int OWARPS>
@@ -161,11 +221,8 @@ __global__ void __launch_bounds__(OWARPS * 32) oz_gemm(int64_t nE, int M, int Kd
   const int KP = Kt * 16 + 8;                 // row stride (bf16) of a slice; +8 breaks bank alignment
   uint16_t* Xs = osm;                         // [kSlices][OE][KP]
   int* exs = reinterpret_cast<int*>(osm + size_t(kSlices) * OE * KP);  // [OE]
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int g = lane >> 2, t = lane & 3;
   constexpr int OTHREADS = OWARPS * 32;
   const int64_t ntiles = (nE + OE - 1) / OE;
-  const int nfrag = Mt * ONT;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t e0 = tile * OE;
     const int ne = int((nE - e0) < OE ? (nE - e0) : OE);
@@ -192,50 +249,7 @@ __global__ void __launch_bounds__(OWARPS * 32) oz_gemm(int64_t nE, int M, int Kd
       for (int j = 0; j < kSlices; ++j) Xs[(size_t(j) * OE + e) * KP + k] = s[j];
     }
     __syncthreads();
-#pragma unroll 1
-    for (int q = 0; q < MAXF; ++q) {
-      const int f = warp + OWARPS * q;
-      if (f >= nfrag) break;
-      const int mt = f / ONT, nt = f - mt * ONT;
-      float acc[kGroups][4];
-#pragma unroll
-      for (int s = 0; s < kGroups; ++s) acc[s][0] = acc[s][1] = acc[s][2] = acc[s][3] = 0.f;
-      for (int kt = 0; kt < Kt; ++kt) {
-        uint32_t b0[kSlices], b1[kSlices];
-#pragma unroll
-        for (int j = 0; j < kSlices; ++j) {
-          const uint16_t* col = Xs + (size_t(j) * OE + nt * 8 + g) * KP + kt * 16 + 2 * t;
-          b0[j] = *reinterpret_cast<const uint32_t*>(col);
-          b1[j] = *reinterpret_cast<const uint32_t*>(col + 8);
-        }
-#pragma unroll
-        for (int i = 0; i < kSlices; ++i) {
-          const uint4 a = __ldg(Af + ((size_t(i) * Mt + mt) * Kt + kt) * 32 + lane);
-#pragma unroll
-          for (int j = 0; j < kSlices - i; ++j) mma_bf16(acc[i + j], a, b0[j], b1[j]);
-        }
-      }
-      // recombine: value = 2^{ea_r + ex_e - 14} sum_s acc[s] 2^{-7 s}
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        float h = acc[kGroups - 1][c], l = 0.f;
-#pragma unroll
-        for (int s = kGroups - 2; s >= 0; --s) {
-          const float hs = h * 0.0078125f, ls = l * 0.0078125f;  // exact scaling by 2^-7
-          const float sum = acc[s][c] + hs;
-          const float bb = sum - acc[s][c];
-          const float err = (acc[s][c] - (sum - bb)) + (hs - bb);
-          h = sum;
-          l = ls + err;
-        }
-        const int r = mt * 16 + g + ((c & 2) ? 8 : 0);
-        const int n = nt * 8 + 2 * t + (c & 1);
-        if (r < M && n < ne) {
-          const int sc = ea[r] + exs[n] - 14;
-          out[(e0 + n) * ldo + r] = f2d_scaled(h, sc) + f2d_scaled(l, sc);
-        }
-      }
-    }
+    oz_mma_tile<MAXF, OWARPS>(Xs, exs, KP, M, Mt, Kt, ne, e0, Af, ea, out, ldo);
   }
 }
 
@@ -244,62 +258,127 @@ __device__ __forceinline__ int fnode_rt(int N, int f, int j) {
   return f == 0 ? j : (f == 1 ? rs(j) + (N - j) : rs(N - j));
 }
 
-// Y rows per element: wr, ws (Np each) | 1/2 nr sJ [u], 1/2 ns sJ [u] (NFN each) |
-// -sJ ({n.grad u} + tau [u]) (NFN) | lambda J u (Np, Helmholtz only)
-__global__ void oz_build_y(int N, int64_t K, int B, int ldy, const double* __restrict__ gx,
-                           const int32_t* __restrict__ conn, const double* __restrict__ u,
-                           const double* __restrict__ C1, double lambda,
-                           double* __restrict__ Y) {
+// Y row of an element (the output product's input), columns:
+//   wr, ws (Np each) | 1/2 nr sJ [u], 1/2 ns sJ [u] (NFN each) |
+//   -sJ ({n.grad u} + tau [u]) (NFN) | lambda J u (Np, Helmholtz only)
+// The output product with the pointwise stage fused into its slicing phase:
+// warp w builds the Y row of element n (the columns listed above, from C1, u,
+// the geometry and the neighbours' C1 and u rows) in registers, takes the
+// row's scale exponent as a warp maximum and writes the 8 slices straight to
+// shared memory, so Y never touches HBM.
+template <int MAXF, int OWARPS>
+__global__ void __launch_bounds__(OWARPS * 32) oz_out(int N, int64_t K, int64_t nE, int Kd, int Mt, int Kt,
+                                                   const double* __restrict__ gx, const int32_t* __restrict__ conn,
+                                                   const double* __restrict__ u, const double* __restrict__ C1,
+                                                   double lambda, const uint4* __restrict__ Af,
+                                                   const int* __restrict__ ea, double* __restrict__ out) {
+  extern __shared__ __align__(16) uint16_t osm[];
+  const int KP = Kt * 16 + 8;
+  uint16_t* Xs = osm;
+  int* exs = reinterpret_cast<int*>(osm + size_t(kSlices) * OE * KP);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int Np = (N + 1) * (N + 2) / 2, Nfp = N + 1, NFN = 3 * Nfp;
   const double cpen = double((N + 1) * (N + 2)) / 2.0;
-  const int per = Np + NFN;  // work items per element
-  const int64_t total = int64_t(B) * K * per;
-  for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
-       idx += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t be = idx / per;
-    const int w = int(idx - be * per);
-    const int64_t e = be % K;
-    const int64_t boff = be - e;  // b * K
-    const double* g = gx + 16 * e;
-    const double* c = C1 + be * (2 * Np);
-    double* y = Y + be * ldy;
-    if (w < Np) {
-      const int i = w;
-      const double ur = c[i], us = c[Np + i];
-      y[i] = g[1] * ur + g[2] * us;
-      y[Np + i] = g[2] * ur + g[3] * us;
-      if (lambda != 0.0) y[2 * Np + 3 * NFN + i] = lambda * g[0] * u[be * Np + i];
-    } else {
-      const int q = w - Np, f = q / Nfp, j = q - f * Nfp;
-      const double nr = g[4 + 4 * f], ns = g[5 + 4 * f], sJ = g[6 + 4 * f], tau = cpen * g[7 + 4 * f];
-      const int k = fnode_rt(N, f, j);
-      const double um = u[be * Np + k];
-      const double dnm = nr * c[k] + ns * c[Np + k];
-      const int code = conn[3 * e + f];
-      double jm = 0.0, av = 0.0;
-      if (code >= 0) {
-        // neighbour's trace and its own outward normal derivative at the shared node,
-        // straight from its nodal values and gradient rows (C1)
-        const int64_t nb = code >> 2;
-        const int fn = code & 3;
-        const int kn = fnode_rt(N, fn, Nfp - 1 - j);
-        const double* gn = gx + 16 * nb + 4 + 4 * fn;
-        const double* cn = C1 + (boff + nb) * (2 * Np);
-        const double up = u[(boff + nb) * Np + kn];
-        const double dnp = gn[0] * cn[kn] + gn[1] * cn[Np + kn];
-        jm = up - um;
-        av = 0.5 * (dnm - dnp);
-      } else if (code == -2) {
-        jm = -2.0 * um;
-        av = dnm;
+  const int64_t ntiles = (nE + OE - 1) / OE;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t e0 = tile * OE;
+    const int ne = int((nE - e0) < OE ? (nE - e0) : OE);
+    __syncthreads();
+    for (int n = warp; n < OE; n += OWARPS) {
+      // slots: 0-2 volume node lane (wr, ws, lambda J u), 3-5 node lane + 32, 6-8 face node lane
+      double v[9];
+      int col[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        v[k] = 0.0;
+        col[k] = -1;
       }
-      const double hs = 0.5 * sJ * jm;
-      y[2 * Np + q] = nr * hs;
-      y[2 * Np + NFN + q] = ns * hs;
-      y[2 * Np + 2 * NFN + q] = -sJ * (av + tau * jm);
+      if (n < ne) {
+        const int64_t be = e0 + n;
+        const int64_t e = be % K;
+        const int64_t boff = be - e;
+        const double* g = gx + 16 * e;
+        const double* c = C1 + be * (2 * Np);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int i = lane + 32 * h;
+          if (i < Np) {
+            const double ur = c[i], us = c[Np + i];
+            v[3 * h] = g[1] * ur + g[2] * us;
+            col[3 * h] = i;
+            v[3 * h + 1] = g[2] * ur + g[3] * us;
+            col[3 * h + 1] = Np + i;
+            if (lambda != 0.0) {
+              v[3 * h + 2] = lambda * g[0] * u[be * Np + i];
+              col[3 * h + 2] = 2 * Np + 3 * NFN + i;
+            }
+          }
+        }
+        if (lane < NFN) {
+          const int q = lane, f = q / Nfp, j = q - f * Nfp;
+          const double nr = g[4 + 4 * f], ns = g[5 + 4 * f], sJ = g[6 + 4 * f], tau = cpen * g[7 + 4 * f];
+          const int k = fnode_rt(N, f, j);
+          const double um = u[be * Np + k];
+          const double dnm = nr * c[k] + ns * c[Np + k];
+          const int code = conn[3 * e + f];
+          double jm = 0.0, av = 0.0;
+          if (code >= 0) {
+            const int64_t nb = code >> 2;
+            const int fn = code & 3;
+            const int kn = fnode_rt(N, fn, Nfp - 1 - j);
+            const double* gn = gx + 16 * nb + 4 + 4 * fn;
+            const double* cn = C1 + (boff + nb) * (2 * Np);
+            const double up = u[(boff + nb) * Np + kn];
+            const double dnp = gn[0] * cn[kn] + gn[1] * cn[Np + kn];
+            jm = up - um;
+            av = 0.5 * (dnm - dnp);
+          } else if (code == -2) {
+            jm = -2.0 * um;
+            av = dnm;
+          }
+          const double hs = 0.5 * sJ * jm;
+          v[6] = nr * hs;
+          col[6] = 2 * Np + q;
+          v[7] = ns * hs;
+          col[7] = 2 * Np + NFN + q;
+          v[8] = -sJ * (av + tau * jm);
+          col[8] = 2 * Np + 2 * NFN + q;
+        }
+      }
+      int emax = -1100;
+#pragma unroll
+      for (int k = 0; k < 9; ++k)
+        if (col[k] >= 0) emax = max(emax, exp_bound(v[k]));
+      emax = __reduce_max_sync(0xffffffffu, emax);
+      if (lane == 0) exs[n] = emax;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        if (col[k] < 0) continue;
+        uint16_t sl[kSlices];
+        slice_dev(v[k], emax, sl);
+#pragma unroll
+        for (int jj = 0; jj < kSlices; ++jj) Xs[(size_t(jj) * OE + n) * KP + col[k]] = sl[jj];
+      }
+      // zero padding: the columns past Kd, or the whole row past the tile's end
+      for (int k = (n < ne ? Kd : 0) + lane; k < Kt * 16; k += 32)
+#pragma unroll
+        for (int jj = 0; jj < kSlices; ++jj) Xs[(size_t(jj) * OE + n) * KP + k] = 0;
     }
+    __syncthreads();
+    oz_mma_tile<MAXF, OWARPS>(Xs, exs, KP, Np, Mt, Kt, ne, e0, Af, ea, out, Np);
   }
 }
+
+// arguments of the fused output product (null: plain product from X)
+struct FusedArgs {
+  int N;
+  int64_t K;
+  const double* gx;
+  const int32_t* conn;
+  const double* u;
+  const double* C1;
+  double lambda;
+};
 
 struct OzOps {
   int Mt1 = 0, Kt1 = 0, Mt2 = 0, Kt2p = 0, Kt2h = 0;
@@ -365,58 +444,61 @@ cudaError_t build_oz_ops(const RefElem& R, OzOps& o) {
 
 template <int MAXF, int OWARPS>
 cudaError_t launch_gemm(int64_t nE, int M, int Kd, int Mt, int Kt, const uint4* Af, const int* ea, const double* X,
-                        int64_t ldx, double* out, int64_t ldo, cudaStream_t st) {
+                        int64_t ldx, double* out, int64_t ldo, const FusedArgs* fa, cudaStream_t st) {
   constexpr int OTHREADS = OWARPS * 32;
   const size_t smem = size_t(kSlices) * OE * (Kt * 16 + 8) * sizeof(uint16_t) + OE * sizeof(int);
-  static size_t configured[64] = {};  // per device: the largest dynamic shared memory set for this instantiation
+  static size_t configured[64][2] = {};  // per device and variant: the largest dynamic shared memory set
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (configured[dev & 63] < smem) {
-    e = cudaFuncSetAttribute(oz_gemm<MAXF, OWARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  const void* kern = fa ? reinterpret_cast<const void*>(oz_out<MAXF, OWARPS>)
+                        : reinterpret_cast<const void*>(oz_gemm<MAXF, OWARPS>);
+  if (configured[dev & 63][fa ? 1 : 0] < smem) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    configured[dev & 63] = smem;
+    configured[dev & 63][fa ? 1 : 0] = smem;
   }
   int sms = 0, per = 0;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, oz_gemm<MAXF, OWARPS>, OTHREADS, smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, OTHREADS, smem);
   if (e != cudaSuccess) return e;
   const int64_t tiles = (nE + OE - 1) / OE;
   int64_t grid = int64_t(sms) * (per > 0 ? per : 1);
   if (grid > tiles) grid = tiles;
-  oz_gemm<MAXF, OWARPS><<<unsigned(grid), OTHREADS, smem, st>>>(nE, M, Kd, Mt, Kt, Af, ea, X, ldx, out, ldo);
+  if (fa)
+    oz_out<MAXF, OWARPS><<<unsigned(grid), OTHREADS, smem, st>>>(fa->N, fa->K, nE, Kd, Mt, Kt, fa->gx, fa->conn, fa->u,
+                                                                fa->C1, fa->lambda, Af, ea, out);
+  else
+    oz_gemm<MAXF, OWARPS><<<unsigned(grid), OTHREADS, smem, st>>>(nE, M, Kd, Mt, Kt, Af, ea, X, ldx, out, ldo);
   note_launch();
   return cudaGetLastError();
 }
 
 // warps per CTA chosen so every warp gets the same number of fragments
 cudaError_t gemm(int Mt, int64_t nE, int M, int Kd, int Kt, const uint4* Af, const int* ea, const double* X,
-                 int64_t ldx, double* out, int64_t ldo, cudaStream_t st) {
+                 int64_t ldx, double* out, int64_t ldo, const FusedArgs* fa, cudaStream_t st) {
   const int nfrag = Mt * ONT;
+#define OZ_L(F, W) return launch_gemm<F, W>(nE, M, Kd, Mt, Kt, Af, ea, X, ldx, out, ldo, fa, st)
   if (nfrag % 8 == 0) {
     const int f = nfrag / 8;
-    if (f == 1) return launch_gemm<1, 8>(nE, M, Kd, Mt, Kt, Af, ea, X, ldx, out, ldo, st);
-    if (f == 2) return launch_gemm<2, 8>(nE, M, Kd, Mt, Kt, Af, ea, X, ldx, out, ldo, st);
-    if (f == 3) return launch_gemm<3, 8>(nE, M, Kd, Mt, Kt, Af, ea, X, ldx, out, ldo, st);
+    if (f == 1) OZ_L(1, 8);
+    if (f == 2) OZ_L(2, 8);
+    if (f == 3) OZ_L(3, 8);
   }
   if (nfrag % 6 == 0 && nfrag / 6 <= 3) {
     const int f = nfrag / 6;
-    if (f == 1) return launch_gemm<1, 6>(nE, M, Kd, Mt, Kt, Af, ea, X, ldx, out, ldo, st);
-    if (f == 2) return launch_gemm<2, 6>(nE, M, Kd, Mt, Kt, Af, ea, X, ldx, out, ldo, st);
-    return launch_gemm<3, 6>(nE, M, Kd, Mt, Kt, Af, ea, X, ldx, out, ldo, st);
+    if (f == 1) OZ_L(1, 6);
+    if (f == 2) OZ_L(2, 6);
+    OZ_L(3, 6);
   }
-  if (nfrag <= 4) return launch_gemm<1, 4>(nE, M, Kd, Mt, Kt, Af, ea, X, ldx, out, ldo, st);
+  if (nfrag <= 4) OZ_L(1, 4);
   const int maxf = (nfrag + 7) / 8;
-  if (maxf <= 2) return launch_gemm<2, 8>(nE, M, Kd, Mt, Kt, Af, ea, X, ldx, out, ldo, st);
-  if (maxf <= 3) return launch_gemm<3, 8>(nE, M, Kd, Mt, Kt, Af, ea, X, ldx, out, ldo, st);
-  return launch_gemm<4, 8>(nE, M, Kd, Mt, Kt, Af, ea, X, ldx, out, ldo, st);
+  if (maxf <= 2) OZ_L(2, 8);
+  if (maxf <= 3) OZ_L(3, 8);
+  OZ_L(4, 8);
+#undef OZ_L
 }
 
-inline int egrid(int64_t n) {
-  int64_t b = (n + 255) / 256;
-  if (b > 152 * 16) b = 152 * 16;
-  return int(b < 1 ? 1 : b);
-}
 
 }  // namespace
 
@@ -438,7 +520,7 @@ cudaError_t launch_apply_oz64(dg_mesh* m, int degree, int B, double lambda, cons
   const bool helm = lambda != 0.0;
   const int KY = 2 * Np + 3 * NFN + (helm ? Np : 0);
   const int64_t nE = int64_t(B) * m->K;
-  const size_t need = size_t(nE) * (2 * Np + KY);  // doubles: C1, Y
+  const size_t need = size_t(nE) * (2 * Np);  // doubles: C1 (Y is built in shared memory)
   if (m->oz_cap < need) {
     cudaFree(m->oz_scratch);
     m->oz_scratch = nullptr;
@@ -449,16 +531,11 @@ cudaError_t launch_apply_oz64(dg_mesh* m, int degree, int B, double lambda, cons
     ++m->scratch_gen;
   }
   double* C1 = m->oz_scratch;
-  double* Y = C1 + size_t(nE) * 2 * Np;
-  e = gemm(o.Mt1, nE, 2 * Np, Np, o.Kt1, o.A1, o.ea1, u, Np, C1, 2 * Np, st);
+  e = gemm(o.Mt1, nE, 2 * Np, Np, o.Kt1, o.A1, o.ea1, u, Np, C1, 2 * Np, nullptr, st);
   if (e != cudaSuccess) return e;
-  oz_build_y<<<egrid(nE * (Np + NFN)), 256, 0, st>>>(N, m->K, B, KY, m->geox, m->conn, u, C1, lambda, Y);
-  note_launch();
-  if (helm)
-    e = gemm(o.Mt2, nE, Np, KY, o.Kt2h, o.A2h, o.ea2h, Y, KY, Au, Np, st);
-  else
-    e = gemm(o.Mt2, nE, Np, KY, o.Kt2p, o.A2p, o.ea2p, Y, KY, Au, Np, st);
-  return e;
+  const FusedArgs fa{N, m->K, m->geox, m->conn, u, C1, lambda};
+  if (helm) return gemm(o.Mt2, nE, Np, KY, o.Kt2h, o.A2h, o.ea2h, nullptr, 0, Au, Np, &fa, st);
+  return gemm(o.Mt2, nE, Np, KY, o.Kt2p, o.A2p, o.ea2p, nullptr, 0, Au, Np, &fa, st);
 }
 
 }  // namespace dgx
