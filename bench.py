@@ -6,8 +6,8 @@ One step = one pass of the hot path over this input:
   * Poisson apply A u in FP64 and in FP32 (U(-1,1) input, seed 1)
   * Helmholtz apply (lambda = 1) in FP64 and in FP32
   * a p-multigrid flexible-CG pressure solve to 1e-10 (V-cycle 8->4->2->1,
-    degree-2 Chebyshev-Jacobi smoothing, degree-1 CG to 1e-2 preconditioned by
-    an algebraic-multigrid V-cycle), mixed precision
+    degree-3 Chebyshev-Jacobi smoothing, degree-1 coarse solve by one
+    CG pass preconditioned by an algebraic-multigrid V-cycle), mixed precision
     (FP32 multigrid levels, FP64 outer iteration)
   * the same solve in plain FP64 (FP64 multigrid levels)
   * the mixed solve once more with the host-driven loop (the two solves above
@@ -38,6 +38,8 @@ sys.path.insert(0, ROOT)
 MESH_NAME = "c5_sweep_524288tri_N8"
 METRIC = "Poisson Ax GDOF/s & PCG solve ms (N=8, 524k tri), mixed vs FP64, % HBM roof"
 PMG_DEGREES = [8, 4, 2, 1]
+CHEB = 3           # Chebyshev-Jacobi smoothing degree per pre/post smoothing
+COARSE_PASSES = 1  # degree-1 coarse solve: one AMG-preconditioned CG pass (a scaled AMG V-cycle)
 
 
 def peaks():
@@ -209,13 +211,13 @@ def run_ours(args, world, rank, local):
     b = mesh.rhs(torch.from_numpy(fex(xh, yh)).to(dev), torch.from_numpy(uex(xh, yh)).to(dev))
     flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     opts_mixed = P._binding.default_opts(precond=P.PREC_PMG, degrees=PMG_DEGREES, tol=1e-10, max_iter=200,
-                                         mixed=1, cheb_degree=2, coarse_tol=1e-2, coarse_max_iter=500,
+                                         mixed=1, cheb_degree=CHEB, coarse_tol=1e-2, coarse_max_iter=COARSE_PASSES,
                                          coarse_amg=1)
     opts_mixed_host = P._binding.default_opts(precond=P.PREC_PMG, degrees=PMG_DEGREES, tol=1e-10, max_iter=200,
-                                              mixed=1, cheb_degree=2, coarse_tol=1e-2, coarse_max_iter=500,
+                                              mixed=1, cheb_degree=CHEB, coarse_tol=1e-2, coarse_max_iter=COARSE_PASSES,
                                               coarse_amg=1, graph=0)
     opts_fp64 = P._binding.default_opts(precond=P.PREC_PMG, degrees=PMG_DEGREES, tol=1e-10, max_iter=200,
-                                        mixed=0, cheb_degree=2, coarse_tol=1e-2, coarse_max_iter=500,
+                                        mixed=0, cheb_degree=CHEB, coarse_tol=1e-2, coarse_max_iter=COARSE_PASSES,
                                         coarse_amg=1)
 
     def flush():
@@ -413,7 +415,7 @@ def run_sweep(args):
             for lam in (0.0, 1.0):
                 for key, prec, u, o in (("f64", P.DG_F64, u64, o64), ("f32", P.DG_F32, u32, o32)):
                     default = mesh.kernel(N, prec, lam != 0.0)
-                    ks = [P.KERNEL_TILE, P.KERNEL_TENSOR if key == "f64" else P.KERNEL_GEMM]
+                    ks = [P.KERNEL_TILE, P.KERNEL_TENSOR] + ([] if key == "f64" else [P.KERNEL_GEMM])
                     if N <= 3:
                         ks.append(P.KERNEL_EPT)
                     for k in ks:
@@ -466,7 +468,8 @@ def run_solve_only(args):
     dev = xn.device
     b = mesh.rhs(torch.from_numpy(fex(xh, yh)).to(dev), torch.from_numpy(uex(xh, yh)).to(dev))
     opts = P._binding.default_opts(precond=P.PREC_PMG, degrees=PMG_DEGREES, tol=1e-10, max_iter=200,
-                                   mixed=0 if args.fp64 else 1, coarse_amg=1, graph=args.graph)
+                                   mixed=0 if args.fp64 else 1, cheb_degree=CHEB, coarse_max_iter=COARSE_PASSES,
+                                   coarse_amg=1, graph=args.graph)
     mesh.solve(b, torch.zeros_like(b), opts=opts)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_push("timed_solve")

@@ -70,8 +70,8 @@ typedef struct dg_mesh dg_mesh; /* opaque; owned by the library until dg_mesh_de
  *   DG_KERNEL_TILE:   element tiles in shared memory, one thread per node
  *                     (FP64 on the FP64 pipe, or FP32); all degrees
  *   DG_KERNEL_GEMM:   FP32 only: register-blocked small GEMMs over element tiles; all degrees
- *   DG_KERNEL_TENSOR: FP64 only: dense products on the BF16 tensor cores with
- *                     exact integer slicing; all degrees
+ *   DG_KERNEL_TENSOR: dense products on the BF16 tensor cores with exact integer
+ *                     slicing (FP64: 8 slices, FP32: 3 slices); all degrees
  *   DG_KERNEL_EPT:    one element per thread, operators in constant memory; degrees 1-3 */
 enum { DG_KERNEL_AUTO = 0, DG_KERNEL_TILE = 1, DG_KERNEL_GEMM = 2, DG_KERNEL_TENSOR = 3, DG_KERNEL_EPT = 4 };
 

@@ -307,7 +307,7 @@ dg_status dg_mesh_setup(int N, int64_t Nv, const double* VX, const double* VY, i
       }
     ce = cudaMalloc(&m->ih32, sizeof(float) * 3 * K);
     if (ce == cudaSuccess) ce = cudaMemcpy(m->ih32, ih.data(), sizeof(float) * 3 * K, cudaMemcpyHostToDevice);
-    // derived FP64 geometry for the tensor-core FP64 apply
+    // derived geometry for the tensor-core applies (FP64 and an FP32 copy)
     std::vector<double> gx(size_t(16) * K);
     for (int64_t e = 0; e < K; ++e) {
       const double* g = &m->geo_h[4 * e];
@@ -333,6 +333,9 @@ dg_status dg_mesh_setup(int N, int64_t Nv, const double* VX, const double* VY, i
     }
     if (ce == cudaSuccess) ce = cudaMalloc(&m->geox, sizeof(double) * 16 * K);
     if (ce == cudaSuccess) ce = cudaMemcpy(m->geox, gx.data(), sizeof(double) * 16 * K, cudaMemcpyHostToDevice);
+    const std::vector<float> gx32(gx.begin(), gx.end());
+    if (ce == cudaSuccess) ce = cudaMalloc(&m->geox32, sizeof(float) * 16 * K);
+    if (ce == cudaSuccess) ce = cudaMemcpy(m->geox32, gx32.data(), sizeof(float) * 16 * K, cudaMemcpyHostToDevice);
   }
   if (ce == cudaSuccess) ce = ensure_ops(m, N);
   if (ce != cudaSuccess) {
@@ -352,6 +355,7 @@ dg_status dg_mesh_destroy(dg_mesh* m) {
   cudaFree(m->oz_scratch);
   cudaFree(m->ih32);
   cudaFree(m->geox);
+  cudaFree(m->geox32);
   cudaFree(m->geo64);
   cudaFree(m->geo32);
   cudaFree(m->conn);

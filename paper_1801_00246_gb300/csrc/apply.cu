@@ -378,7 +378,7 @@ DG_TE_DECL(1) DG_TE_DECL(2) DG_TE_DECL(3) DG_TE_DECL(4) DG_TE_DECL(5) DG_TE_DECL
 
 // Kernel choice: the tile kernel above (FP64 or FP32), register-blocked FP32
 // GEMMs (apply_gemm.cuh, with the mesh face scratch), FP64 products on the BF16
-// tensor cores with exact integer slicing (apply_oz64.cu), or one element per
+// tensor cores with exact integer slicing (apply_tensor.cu; FP64 and FP32), or one element per
 // thread (apply_ept.cu). DG_F64_DFMA forces the tile kernel in FP64.
 
 // Built-in kernel per degree and precision (the measured winners on the
@@ -392,7 +392,7 @@ bool kernel_valid(int kernel, int degree, bool f64) {
   switch (kernel) {
     case DG_KERNEL_TILE: return true;
     case DG_KERNEL_GEMM: return !f64;
-    case DG_KERNEL_TENSOR: return f64;
+    case DG_KERNEL_TENSOR: return true;
     case DG_KERNEL_EPT: return ept_supported(degree);
     default: return false;
   }
@@ -413,9 +413,7 @@ cudaError_t launch_apply(const dg_mesh* mc, int degree, dg_prec prec, int B, dou
   const bool f64 = prec == DG_F64;
   if (!kernel_valid(k, degree, f64)) return cudaErrorInvalidValue;
   if (k == DG_KERNEL_EPT) return launch_apply_ept(m, degree, f64, B, lambda, u, Au, st);
-  if (k == DG_KERNEL_TENSOR)
-    return launch_apply_oz64(m, degree, B, lambda, reinterpret_cast<const double*>(u), reinterpret_cast<double*>(Au),
-                             st);
+  if (k == DG_KERNEL_TENSOR) return launch_apply_tensor(m, degree, f64, B, lambda, u, Au, st);
   if (k == DG_KERNEL_GEMM) {
     const int dmax = degree > m->N ? degree : m->N;
     const size_t need = size_t(B) * size_t(m->K) * 3 * size_t(dmax + 1);

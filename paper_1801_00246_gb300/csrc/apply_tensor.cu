@@ -1,31 +1,32 @@
-// FP64-accurate SIPDG apply with its dense products on the BF16 tensor cores.
+// SIPDG apply with its dense products on the BF16 tensor cores, in FP64 or FP32.
 //
-// GB300 executes FP64 at 1/62 of its FP32 rate, so the FP64 tile kernel
-// (apply.cu) is bound by the FP64 pipe. Here the two dense products of the
-// operator (Eq. ellipticOp3 written as in apply_gemm.cuh),
+// The two dense products of the operator (Eq. ellipticOp3 written as in
+// apply_gemm.cuh),
 //   C1 = [Dr; Ds] U   and   Au = OB Y,
-// are evaluated exactly enough for FP64 with integer-sliced BF16 products
-// (the error-free splitting of Ozaki et al., "Error-free transformations of
-// matrix multiplication by using fast routines of matrix multiplication and
-// its applications", Numer. Algorithms 59, 2012):
+// are evaluated exactly enough for the working precision with integer-sliced
+// BF16 products (the error-free splitting of Ozaki et al., "Error-free
+// transformations of matrix multiplication by using fast routines of matrix
+// multiplication and its applications", Numer. Algorithms 59, 2012):
 //   * every operator row r is scaled by a power of two 2^{ea_r} and written as
-//     sum_i a_i 2^{-7i}, i = 1..8, a_i signed integers |a_i| <= 127 (host);
+//     sum_i a_i 2^{-7i}, i = 1..KS, with signed integers |a_i| <= 127 (host);
 //   * every element's data column is scaled by 2^{ex_e} and sliced the same way
-//     on the fly from the FP64 bit pattern (integer shifts, no FP64 work);
-//   * a_i x_j products summed over K <= 176 are integers below 2^22, exact in the
+//     on the fly from the value's bit pattern (integer shifts only);
+//   * a_i x_j products summed over K <= 224 are integers below 2^22, exact in the
 //     FP32 accumulators of mma.sync m16n8k16; products with the same i + j share
-//     an accumulator (exact up to the 2^-49 level), i + j <= 9 (36 products),
-//     which leaves a relative error near 2^-44 of |A||x|;
-//   * the 8 accumulators are combined by Horner's rule in float-float
-//     arithmetic and converted to FP64 once.
+//     an accumulator (exact for FP32 up to 4 products per group: 4 x 127^2 x 224
+//     < 2^24), and only i + j <= KS + 1 is formed;
+//   * the KS accumulators are combined by Horner's rule (float-float for FP64)
+//     and scaled back by building the exponent bits.
+// FP64 takes KS = 8 slices (56 bits, 36 products; relative error near 2^-44 of
+// |A||x|), FP32 KS = 4 (28 bits, 10 products; near 2^-26 of |A||x|).
+//
 // The face mass is folded into the output operator
 //   OB = [Br Bs | Dr_f^T Mf  Ds_f^T Mf | E_f Mf | M],
 // so the pointwise stage between the two products only forms
 //   Y = [wr; ws; 1/2 nr sJ [u]; 1/2 ns sJ [u]; -sJ ({n.grad u} + tau [u]); lambda J u].
-// The pointwise stage runs inside the output product's slicing phase (Y is
-// built in shared memory, never in HBM); the neighbour's trace and normal
-// derivative at a shared face node are read from its nodal values and its
-// rows of C1.
+// That stage runs inside the output product's slicing phase (Y is built in
+// shared memory, never in HBM); the neighbour's trace and normal derivative at
+// a shared face node are read from its nodal values and its rows of C1.
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -35,27 +36,35 @@
 namespace dgx {
 namespace {
 
-constexpr int kSlices = 8;        // 7-bit slices per operand: 56 bits
 constexpr int kSliceBits = 7;
-constexpr int kGroups = 8;        // i + j = 2..9 -> 8 accumulators
-constexpr int OE = 32;            // elements per CTA tile
-constexpr int ONT = OE / 8;       // n-tiles (8 elements each)
+constexpr int OE = 32;       // elements per CTA tile
+constexpr int ONT = OE / 8;  // n-tiles (8 elements each)
 
+template <typename T>
+struct Slices;
+template <>
+struct Slices<double> {
+  static constexpr int KS = 8;  // 56 bits
+};
+template <>
+struct Slices<float> {
+  static constexpr int KS = 4;  // 28 bits (3 slices, 21 bits, miss the FP32 tolerance where Au cancels)
+};
 
 // ---------------------------------------------------------------- host side
-// Slices of one FP64 value relative to 2^{scale_exp} (|v| < 2^{scale_exp}):
-// floor(|v| 2^{56 - scale_exp}) cut into 8 chunks of 7 bits, sign applied.
-void slice_host(double v, int scale_exp, int out[kSlices]) {
-  for (int j = 0; j < kSlices; ++j) out[j] = 0;
+// KS slices of v relative to 2^{scale_exp} (|v| < 2^{scale_exp}):
+// floor(|v| 2^{7 KS - scale_exp}) cut into KS chunks of 7 bits, sign applied.
+void slice_host(double v, int scale_exp, int KS, int* out) {
+  const int bits = kSliceBits * KS;
+  for (int j = 0; j < KS; ++j) out[j] = 0;
   if (v == 0.0 || !std::isfinite(v)) return;
   int e = 0;
   const double fr = std::frexp(std::fabs(v), &e);  // |v| = fr 2^e, fr in [0.5, 1)
-  // |v| 2^{56 - scale_exp} = fr 2^{e + 56 - scale_exp}
-  const int sh = e + 56 - scale_exp;
+  const int sh = e + bits - scale_exp;
   if (sh <= 0) return;
   const unsigned long long I = (unsigned long long)std::ldexp(fr, sh);  // exact for sh <= 53, truncated beyond
   const int sgn = v < 0 ? -1 : 1;
-  for (int j = 0; j < kSlices; ++j) out[j] = sgn * int((I >> (56 - kSliceBits * (j + 1))) & 127ull);
+  for (int j = 0; j < KS; ++j) out[j] = sgn * int((I >> (bits - kSliceBits * (j + 1))) & 127ull);
 }
 
 int row_scale_exp(const double* row, int K) {
@@ -74,21 +83,21 @@ inline uint16_t bf16_of_int(int x) {  // exact for |x| <= 256
   return uint16_t(u >> 16);
 }
 
-// A (M x K, row-major FP64) -> fragment-ordered slices [8][Mt][Kt][32 lanes] of
+// A (M x K, row-major FP64) -> fragment-ordered slices [KS][Mt][Kt][32 lanes] of
 // 4 uint32 (2 bf16 each) for mma.m16n8k16 row-major A, plus row exponents.
-void slice_operator(const std::vector<double>& A, int M, int K, int& Mt, int& Kt, std::vector<uint32_t>& frag,
+void slice_operator(const std::vector<double>& A, int M, int K, int KS, int& Mt, int& Kt, std::vector<uint32_t>& frag,
                     std::vector<int>& ea) {
   Mt = (M + 15) / 16;
   Kt = (K + 15) / 16;
   ea.assign(Mt * 16, 0);
-  std::vector<int> sl(size_t(Mt) * 16 * Kt * 16 * kSlices, 0);  // [row][k][slice]
+  std::vector<int> sl(size_t(Mt) * 16 * Kt * 16 * KS, 0);  // [row][k][slice]
   for (int r = 0; r < M; ++r) {
     ea[r] = row_scale_exp(&A[size_t(r) * K], K);
-    for (int k = 0; k < K; ++k) slice_host(A[size_t(r) * K + k], ea[r], &sl[(size_t(r) * Kt * 16 + k) * kSlices]);
+    for (int k = 0; k < K; ++k) slice_host(A[size_t(r) * K + k], ea[r], KS, &sl[(size_t(r) * Kt * 16 + k) * KS]);
   }
-  auto S = [&](int r, int k, int i) { return sl[(size_t(r) * Kt * 16 + k) * kSlices + i]; };
-  frag.assign(size_t(kSlices) * Mt * Kt * 32 * 4, 0);
-  for (int i = 0; i < kSlices; ++i)
+  auto S = [&](int r, int k, int i) { return sl[(size_t(r) * Kt * 16 + k) * KS + i]; };
+  frag.assign(size_t(KS) * Mt * Kt * 32 * 4, 0);
+  for (int i = 0; i < KS; ++i)
     for (int mt = 0; mt < Mt; ++mt)
       for (int kt = 0; kt < Kt; ++kt)
         for (int lane = 0; lane < 32; ++lane) {
@@ -126,29 +135,64 @@ __device__ __forceinline__ double f2d_scaled(float f, int sc) {
   return __longlong_as_double((long long)(s | e | m));
 }
 
-// unbiased exponent e such that |v| < 2^e (0 for v = 0)
-__device__ __forceinline__ int exp_bound(double v) {
-  const long long b = __double_as_longlong(v);
-  const int E = int((b >> 52) & 0x7ff);
-  return E == 0 ? -1100 : E - 1022;
+// f * 2^sc in float from the exponent bits (results below the normal range flush to zero)
+__device__ __forceinline__ float f2f_scaled(float f, int sc) {
+  const unsigned int u = __float_as_uint(f);
+  const int ef = int((u >> 23) & 0xffu);
+  if (ef == 0) return 0.f;
+  const int ne = ef + sc;
+  if (ne <= 0) return 0.f;
+  if (ne >= 255) return __uint_as_float((u & 0x80000000u) | 0x7f800000u);
+  return __uint_as_float((u & 0x807fffffu) | (unsigned(ne) << 23));
 }
 
-// 8 signed 7-bit slices of v relative to 2^{sc} (|v| < 2^{sc}), as packed bf16 bits
-__device__ __forceinline__ void slice_dev(double v, int sc, uint16_t (&s)[kSlices]) {
+// unbiased exponent e such that |v| < 2^e (a very negative value for zero)
+__device__ __forceinline__ int exp_bound(double v) {
+  const int E = int((__double_as_longlong(v) >> 52) & 0x7ff);
+  return E == 0 ? -1100 : E - 1022;
+}
+__device__ __forceinline__ int exp_bound(float v) {
+  const int E = int((__float_as_uint(v) >> 23) & 0xff);
+  return E == 0 ? -1100 : E - 126;
+}
+
+// KS signed 7-bit slices of v relative to 2^{sc} (|v| < 2^{sc}), as packed bf16 bits
+template <int KS>
+__device__ __forceinline__ void slice_dev(double v, int sc, uint16_t (&s)[KS]) {
+  constexpr int bits = kSliceBits * KS;
   const long long b = __double_as_longlong(v);
   const int E = int((b >> 52) & 0x7ff);
   const unsigned long long m = (unsigned long long)(b & 0xfffffffffffffull) | (E ? (1ull << 52) : 0ull);
-  // |v| = m 2^{E-1075};  I = floor(|v| 2^{56 - sc}) = m 2^{E - 1075 + 56 - sc}
-  const int sh = (E ? E : 1) - 1019 - sc;
+  // |v| = m 2^{E-1075};  I = floor(|v| 2^{bits - sc})
+  const int sh = (E ? E : 1) - 1075 + bits - sc;
   unsigned long long I = 0;
-  if (sh >= 0) I = sh < 11 ? (m << sh) : 0ull;  // sh <= 3 whenever |v| < 2^sc
+  if (sh >= 0) I = sh < 11 ? (m << sh) : 0ull;  // I < 2^bits <= 2^56 whenever |v| < 2^sc
   else if (sh > -63) I = m >> (-sh);
   const uint16_t sgn = (b < 0) ? 0x8000 : 0;
 #pragma unroll
-  for (int j = 0; j < kSlices; ++j) {
-    const int x = int((I >> (56 - kSliceBits * (j + 1))) & 127ull);
-    const uint16_t bits = uint16_t(__float_as_uint(float(x)) >> 16);
-    s[j] = x ? (bits | sgn) : 0;
+  for (int j = 0; j < KS; ++j) {
+    const int x = int((I >> (bits - kSliceBits * (j + 1))) & 127ull);
+    const uint16_t hb = uint16_t(__float_as_uint(float(x)) >> 16);
+    s[j] = x ? (hb | sgn) : 0;
+  }
+}
+template <int KS>
+__device__ __forceinline__ void slice_dev(float v, int sc, uint16_t (&s)[KS]) {
+  constexpr int bits = kSliceBits * KS;
+  const unsigned int b = __float_as_uint(v);
+  const int E = int((b >> 23) & 0xff);
+  const unsigned int m = (b & 0x7fffffu) | (E ? 0x800000u : 0u);
+  // |v| = m 2^{E-150};  I = floor(|v| 2^{bits - sc})
+  const int sh = (E ? E : 1) - 150 + bits - sc;
+  unsigned int I = 0;
+  if (sh >= 0) I = sh < 8 ? (m << sh) : 0u;
+  else if (sh > -32) I = m >> (-sh);
+  const uint16_t sgn = (b >> 31) ? 0x8000 : 0;
+#pragma unroll
+  for (int j = 0; j < KS; ++j) {
+    const int x = int((I >> (bits - kSliceBits * (j + 1))) & 127u);
+    const uint16_t hb = uint16_t(__float_as_uint(float(x)) >> 16);
+    s[j] = x ? (hb | sgn) : 0;
   }
 }
 
@@ -156,11 +200,12 @@ __device__ __forceinline__ void slice_dev(double v, int sc, uint16_t (&s)[kSlice
 // data slices Xs (per element n: scale exponent exs[n]) and the operator's
 // fragment-ordered slices Af (row exponents ea). Warp w takes fragments
 // w, w + OWARPS, ... (a fragment: 16 operator rows x 8 elements).
-template <int MAXF, int OWARPS>
+template <int MAXF, int OWARPS, typename T>
 __device__ __forceinline__ void oz_mma_tile(const uint16_t* __restrict__ Xs, const int* __restrict__ exs, int KP,
                                             int M, int Mt, int Kt, int ne, int64_t e0,
                                             const uint4* __restrict__ Af, const int* __restrict__ ea,
-                                            double* __restrict__ out, int64_t ldo) {
+                                            T* __restrict__ out, int64_t ldo) {
+  constexpr int KS = Slices<T>::KS;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
   const int nfrag = Mt * ONT;
@@ -169,58 +214,63 @@ __device__ __forceinline__ void oz_mma_tile(const uint16_t* __restrict__ Xs, con
     const int f = warp + OWARPS * q;
     if (f >= nfrag) break;
     const int mt = f / ONT, nt = f - mt * ONT;
-    float acc[kGroups][4];
+    float acc[KS][4];
 #pragma unroll
-    for (int s = 0; s < kGroups; ++s) acc[s][0] = acc[s][1] = acc[s][2] = acc[s][3] = 0.f;
+    for (int s = 0; s < KS; ++s) acc[s][0] = acc[s][1] = acc[s][2] = acc[s][3] = 0.f;
     for (int kt = 0; kt < Kt; ++kt) {
-      uint32_t b0[kSlices], b1[kSlices];
+      uint32_t b0[KS], b1[KS];
 #pragma unroll
-      for (int j = 0; j < kSlices; ++j) {
+      for (int j = 0; j < KS; ++j) {
         const uint16_t* col = Xs + (size_t(j) * OE + nt * 8 + g) * KP + kt * 16 + 2 * t;
         b0[j] = *reinterpret_cast<const uint32_t*>(col);
         b1[j] = *reinterpret_cast<const uint32_t*>(col + 8);
       }
 #pragma unroll
-      for (int i = 0; i < kSlices; ++i) {
+      for (int i = 0; i < KS; ++i) {
         const uint4 a = __ldg(Af + ((size_t(i) * Mt + mt) * Kt + kt) * 32 + lane);
 #pragma unroll
-        for (int j = 0; j < kSlices - i; ++j) mma_bf16(acc[i + j], a, b0[j], b1[j]);
+        for (int j = 0; j < KS - i; ++j) mma_bf16(acc[i + j], a, b0[j], b1[j]);
       }
     }
     // recombine: value = 2^{ea_r + ex_e - 14} sum_s acc[s] 2^{-7 s}
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      float h = acc[kGroups - 1][c], l = 0.f;
-#pragma unroll
-      for (int s = kGroups - 2; s >= 0; --s) {
-        const float hs = h * 0.0078125f, ls = l * 0.0078125f;  // exact scaling by 2^-7
-        const float sum = acc[s][c] + hs;
-        const float bb = sum - acc[s][c];
-        const float err = (acc[s][c] - (sum - bb)) + (hs - bb);
-        h = sum;
-        l = ls + err;
-      }
       const int r = mt * 16 + g + ((c & 2) ? 8 : 0);
       const int n = nt * 8 + 2 * t + (c & 1);
-      if (r < M && n < ne) {
-        const int sc = ea[r] + exs[n] - 14;
-        out[(e0 + n) * ldo + r] = f2d_scaled(h, sc) + f2d_scaled(l, sc);
+      if constexpr (sizeof(T) == 8) {
+        float h = acc[KS - 1][c], l = 0.f;
+#pragma unroll
+        for (int s = KS - 2; s >= 0; --s) {
+          const float hs = h * 0.0078125f, ls = l * 0.0078125f;  // exact scaling by 2^-7
+          const float sum = acc[s][c] + hs;
+          const float bb = sum - acc[s][c];
+          const float err = (acc[s][c] - (sum - bb)) + (hs - bb);
+          h = sum;
+          l = ls + err;
+        }
+        if (r < M && n < ne) out[(e0 + n) * ldo + r] = f2d_scaled(h, ea[r] + exs[n] - 14) + f2d_scaled(l, ea[r] + exs[n] - 14);
+      } else {
+        float h = acc[KS - 1][c];
+#pragma unroll
+        for (int s = KS - 2; s >= 0; --s) h = acc[s][c] + h * 0.0078125f;
+        if (r < M && n < ne) out[(e0 + n) * ldo + r] = f2f_scaled(h, ea[r] + exs[n] - 14);
       }
     }
   }
 }
 
-// out[e][r] = sum_k A[r][k] X[e][k] for e < nE, r < M (FP64 in and out).
+// out[e][r] = sum_k A[r][k] X[e][k] for e < nE, r < M.
 // X rows have Kd entries at stride ldx; out rows stride ldo.
-template <int MAXF, int OWARPS>
+template <int MAXF, int OWARPS, typename T>
 __global__ void __launch_bounds__(OWARPS * 32) oz_gemm(int64_t nE, int M, int Kd, int Mt, int Kt,
                                                     const uint4* __restrict__ Af, const int* __restrict__ ea,
-                                                    const double* __restrict__ X, int64_t ldx,
-                                                    double* __restrict__ out, int64_t ldo) {
+                                                    const T* __restrict__ X, int64_t ldx, T* __restrict__ out,
+                                                    int64_t ldo) {
+  constexpr int KS = Slices<T>::KS;
   extern __shared__ __align__(16) uint16_t osm[];
   const int KP = Kt * 16 + 8;                 // row stride (bf16) of a slice; +8 breaks bank alignment
-  uint16_t* Xs = osm;                         // [kSlices][OE][KP]
-  int* exs = reinterpret_cast<int*>(osm + size_t(kSlices) * OE * KP);  // [OE]
+  uint16_t* Xs = osm;                         // [KS][OE][KP]
+  int* exs = reinterpret_cast<int*>(osm + size_t(KS) * OE * KP);  // [OE]
   constexpr int OTHREADS = OWARPS * 32;
   const int64_t ntiles = (nE + OE - 1) / OE;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -238,18 +288,18 @@ __global__ void __launch_bounds__(OWARPS * 32) oz_gemm(int64_t nE, int M, int Kd
     // slices, zero-padded in k and e
     for (int idx = threadIdx.x; idx < OE * Kt * 16; idx += OTHREADS) {
       const int e = idx / (Kt * 16), k = idx - e * (Kt * 16);
-      uint16_t s[kSlices];
+      uint16_t s[KS];
       if (e < ne && k < Kd) {
-        slice_dev(__ldg(X + (e0 + e) * ldx + k), exs[e], s);
+        slice_dev<KS>(__ldg(X + (e0 + e) * ldx + k), exs[e], s);
       } else {
 #pragma unroll
-        for (int j = 0; j < kSlices; ++j) s[j] = 0;
+        for (int j = 0; j < KS; ++j) s[j] = 0;
       }
 #pragma unroll
-      for (int j = 0; j < kSlices; ++j) Xs[(size_t(j) * OE + e) * KP + k] = s[j];
+      for (int j = 0; j < KS; ++j) Xs[(size_t(j) * OE + e) * KP + k] = s[j];
     }
     __syncthreads();
-    oz_mma_tile<MAXF, OWARPS>(Xs, exs, KP, M, Mt, Kt, ne, e0, Af, ea, out, ldo);
+    oz_mma_tile<MAXF, OWARPS, T>(Xs, exs, KP, M, Mt, Kt, ne, e0, Af, ea, out, ldo);
   }
 }
 
@@ -258,27 +308,27 @@ __device__ __forceinline__ int fnode_rt(int N, int f, int j) {
   return f == 0 ? j : (f == 1 ? rs(j) + (N - j) : rs(N - j));
 }
 
-// Y row of an element (the output product's input), columns:
-//   wr, ws (Np each) | 1/2 nr sJ [u], 1/2 ns sJ [u] (NFN each) |
-//   -sJ ({n.grad u} + tau [u]) (NFN) | lambda J u (Np, Helmholtz only)
 // The output product with the pointwise stage fused into its slicing phase:
-// warp w builds the Y row of element n (the columns listed above, from C1, u,
-// the geometry and the neighbours' C1 and u rows) in registers, takes the
-// row's scale exponent as a warp maximum and writes the 8 slices straight to
-// shared memory, so Y never touches HBM.
-template <int MAXF, int OWARPS>
+// warp w builds the Y row of element n (columns: wr, ws (Np each) |
+// 1/2 nr sJ [u], 1/2 ns sJ [u] (NFN each) | -sJ ({n.grad u} + tau [u]) (NFN) |
+// lambda J u (Np, Helmholtz only)) in registers, from C1, u, the geometry
+// gx (16 words per element: J, Grr, Grs, Gss | per face nr, ns, sJ, ihmax) and
+// the neighbours' C1 and u rows; takes the row's scale exponent as a warp
+// maximum and writes the slices straight to shared memory.
+template <int MAXF, int OWARPS, typename T>
 __global__ void __launch_bounds__(OWARPS * 32) oz_out(int N, int64_t K, int64_t nE, int Kd, int Mt, int Kt,
-                                                   const double* __restrict__ gx, const int32_t* __restrict__ conn,
-                                                   const double* __restrict__ u, const double* __restrict__ C1,
-                                                   double lambda, const uint4* __restrict__ Af,
-                                                   const int* __restrict__ ea, double* __restrict__ out) {
+                                                   const T* __restrict__ gx, const int32_t* __restrict__ conn,
+                                                   const T* __restrict__ u, const T* __restrict__ C1, T lambda,
+                                                   const uint4* __restrict__ Af, const int* __restrict__ ea,
+                                                   T* __restrict__ out) {
+  constexpr int KS = Slices<T>::KS;
   extern __shared__ __align__(16) uint16_t osm[];
   const int KP = Kt * 16 + 8;
   uint16_t* Xs = osm;
-  int* exs = reinterpret_cast<int*>(osm + size_t(kSlices) * OE * KP);
+  int* exs = reinterpret_cast<int*>(osm + size_t(KS) * OE * KP);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int Np = (N + 1) * (N + 2) / 2, Nfp = N + 1, NFN = 3 * Nfp;
-  const double cpen = double((N + 1) * (N + 2)) / 2.0;
+  const T cpen = T((N + 1) * (N + 2)) / T(2);
   const int64_t ntiles = (nE + OE - 1) / OE;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t e0 = tile * OE;
@@ -286,29 +336,29 @@ __global__ void __launch_bounds__(OWARPS * 32) oz_out(int N, int64_t K, int64_t 
     __syncthreads();
     for (int n = warp; n < OE; n += OWARPS) {
       // slots: 0-2 volume node lane (wr, ws, lambda J u), 3-5 node lane + 32, 6-8 face node lane
-      double v[9];
+      T v[9];
       int col[9];
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
-        v[k] = 0.0;
+        v[k] = T(0);
         col[k] = -1;
       }
       if (n < ne) {
         const int64_t be = e0 + n;
         const int64_t e = be % K;
         const int64_t boff = be - e;
-        const double* g = gx + 16 * e;
-        const double* c = C1 + be * (2 * Np);
+        const T* g = gx + 16 * e;
+        const T* c = C1 + be * (2 * Np);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int i = lane + 32 * h;
           if (i < Np) {
-            const double ur = c[i], us = c[Np + i];
+            const T ur = c[i], us = c[Np + i];
             v[3 * h] = g[1] * ur + g[2] * us;
             col[3 * h] = i;
             v[3 * h + 1] = g[2] * ur + g[3] * us;
             col[3 * h + 1] = Np + i;
-            if (lambda != 0.0) {
+            if (lambda != T(0)) {
               v[3 * h + 2] = lambda * g[0] * u[be * Np + i];
               col[3 * h + 2] = 2 * Np + 3 * NFN + i;
             }
@@ -316,27 +366,27 @@ __global__ void __launch_bounds__(OWARPS * 32) oz_out(int N, int64_t K, int64_t 
         }
         if (lane < NFN) {
           const int q = lane, f = q / Nfp, j = q - f * Nfp;
-          const double nr = g[4 + 4 * f], ns = g[5 + 4 * f], sJ = g[6 + 4 * f], tau = cpen * g[7 + 4 * f];
+          const T nr = g[4 + 4 * f], ns = g[5 + 4 * f], sJ = g[6 + 4 * f], tau = cpen * g[7 + 4 * f];
           const int k = fnode_rt(N, f, j);
-          const double um = u[be * Np + k];
-          const double dnm = nr * c[k] + ns * c[Np + k];
+          const T um = u[be * Np + k];
+          const T dnm = nr * c[k] + ns * c[Np + k];
           const int code = conn[3 * e + f];
-          double jm = 0.0, av = 0.0;
+          T jm = T(0), av = T(0);
           if (code >= 0) {
             const int64_t nb = code >> 2;
             const int fn = code & 3;
             const int kn = fnode_rt(N, fn, Nfp - 1 - j);
-            const double* gn = gx + 16 * nb + 4 + 4 * fn;
-            const double* cn = C1 + (boff + nb) * (2 * Np);
-            const double up = u[(boff + nb) * Np + kn];
-            const double dnp = gn[0] * cn[kn] + gn[1] * cn[Np + kn];
+            const T* gn = gx + 16 * nb + 4 + 4 * fn;
+            const T* cn = C1 + (boff + nb) * (2 * Np);
+            const T up = u[(boff + nb) * Np + kn];
+            const T dnp = gn[0] * cn[kn] + gn[1] * cn[Np + kn];
             jm = up - um;
-            av = 0.5 * (dnm - dnp);
+            av = T(0.5) * (dnm - dnp);
           } else if (code == -2) {
-            jm = -2.0 * um;
+            jm = T(-2) * um;
             av = dnm;
           }
-          const double hs = 0.5 * sJ * jm;
+          const T hs = T(0.5) * sJ * jm;
           v[6] = nr * hs;
           col[6] = 2 * Np + q;
           v[7] = ns * hs;
@@ -354,30 +404,31 @@ __global__ void __launch_bounds__(OWARPS * 32) oz_out(int N, int64_t K, int64_t 
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
         if (col[k] < 0) continue;
-        uint16_t sl[kSlices];
-        slice_dev(v[k], emax, sl);
+        uint16_t sl[KS];
+        slice_dev<KS>(v[k], emax, sl);
 #pragma unroll
-        for (int jj = 0; jj < kSlices; ++jj) Xs[(size_t(jj) * OE + n) * KP + col[k]] = sl[jj];
+        for (int jj = 0; jj < KS; ++jj) Xs[(size_t(jj) * OE + n) * KP + col[k]] = sl[jj];
       }
       // zero padding: the columns past Kd, or the whole row past the tile's end
       for (int k = (n < ne ? Kd : 0) + lane; k < Kt * 16; k += 32)
 #pragma unroll
-        for (int jj = 0; jj < kSlices; ++jj) Xs[(size_t(jj) * OE + n) * KP + k] = 0;
+        for (int jj = 0; jj < KS; ++jj) Xs[(size_t(jj) * OE + n) * KP + k] = 0;
     }
     __syncthreads();
-    oz_mma_tile<MAXF, OWARPS>(Xs, exs, KP, Np, Mt, Kt, ne, e0, Af, ea, out, Np);
+    oz_mma_tile<MAXF, OWARPS, T>(Xs, exs, KP, Np, Mt, Kt, ne, e0, Af, ea, out, Np);
   }
 }
 
 // arguments of the fused output product (null: plain product from X)
+template <typename T>
 struct FusedArgs {
   int N;
   int64_t K;
-  const double* gx;
+  const T* gx;
   const int32_t* conn;
-  const double* u;
-  const double* C1;
-  double lambda;
+  const T* u;
+  const T* C1;
+  T lambda;
 };
 
 struct OzOps {
@@ -386,7 +437,7 @@ struct OzOps {
   int *ea1 = nullptr, *ea2p = nullptr, *ea2h = nullptr;
 };
 
-cudaError_t build_oz_ops(const RefElem& R, OzOps& o) {
+cudaError_t build_oz_ops(const RefElem& R, int KS, OzOps& o) {
   const int N = R.N, Np = R.Np, Nfp = R.Nfp, NFN = 3 * Nfp;
   // [Dr; Ds]: 2Np x Np
   std::vector<double> A1(size_t(2 * Np) * Np);
@@ -425,9 +476,9 @@ cudaError_t build_oz_ops(const RefElem& R, OzOps& o) {
   std::vector<uint32_t> f1, f2p, f2h;
   std::vector<int> e1, e2p, e2h;
   int Mt2h = 0;
-  slice_operator(A1, 2 * Np, Np, o.Mt1, o.Kt1, f1, e1);
-  slice_operator(build_ob(KPo), Np, KPo, o.Mt2, o.Kt2p, f2p, e2p);
-  slice_operator(build_ob(KHo), Np, KHo, Mt2h, o.Kt2h, f2h, e2h);
+  slice_operator(A1, 2 * Np, Np, KS, o.Mt1, o.Kt1, f1, e1);
+  slice_operator(build_ob(KPo), Np, KPo, KS, o.Mt2, o.Kt2p, f2p, e2p);
+  slice_operator(build_ob(KHo), Np, KHo, KS, Mt2h, o.Kt2h, f2h, e2h);
   auto up = [](auto& dst, const auto& v) -> cudaError_t {
     cudaError_t e = cudaMalloc(&dst, v.size() * sizeof(v[0]));
     if (e != cudaSuccess) return e;
@@ -442,17 +493,17 @@ cudaError_t build_oz_ops(const RefElem& R, OzOps& o) {
   return up(o.ea2h, e2h);
 }
 
-template <int MAXF, int OWARPS>
-cudaError_t launch_gemm(int64_t nE, int M, int Kd, int Mt, int Kt, const uint4* Af, const int* ea, const double* X,
-                        int64_t ldx, double* out, int64_t ldo, const FusedArgs* fa, cudaStream_t st) {
+template <int MAXF, int OWARPS, typename T>
+cudaError_t launch_gemm(int64_t nE, int M, int Kd, int Mt, int Kt, const uint4* Af, const int* ea, const T* X,
+                        int64_t ldx, T* out, int64_t ldo, const FusedArgs<T>* fa, cudaStream_t st) {
   constexpr int OTHREADS = OWARPS * 32;
-  const size_t smem = size_t(kSlices) * OE * (Kt * 16 + 8) * sizeof(uint16_t) + OE * sizeof(int);
+  const size_t smem = size_t(Slices<T>::KS) * OE * (Kt * 16 + 8) * sizeof(uint16_t) + OE * sizeof(int);
   static size_t configured[64][2] = {};  // per device and variant: the largest dynamic shared memory set
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  const void* kern = fa ? reinterpret_cast<const void*>(oz_out<MAXF, OWARPS>)
-                        : reinterpret_cast<const void*>(oz_gemm<MAXF, OWARPS>);
+  const void* kern = fa ? reinterpret_cast<const void*>(oz_out<MAXF, OWARPS, T>)
+                        : reinterpret_cast<const void*>(oz_gemm<MAXF, OWARPS, T>);
   if (configured[dev & 63][fa ? 1 : 0] < smem) {
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
@@ -466,19 +517,20 @@ cudaError_t launch_gemm(int64_t nE, int M, int Kd, int Mt, int Kt, const uint4* 
   int64_t grid = int64_t(sms) * (per > 0 ? per : 1);
   if (grid > tiles) grid = tiles;
   if (fa)
-    oz_out<MAXF, OWARPS><<<unsigned(grid), OTHREADS, smem, st>>>(fa->N, fa->K, nE, Kd, Mt, Kt, fa->gx, fa->conn, fa->u,
-                                                                fa->C1, fa->lambda, Af, ea, out);
+    oz_out<MAXF, OWARPS, T><<<unsigned(grid), OTHREADS, smem, st>>>(fa->N, fa->K, nE, Kd, Mt, Kt, fa->gx, fa->conn,
+                                                                   fa->u, fa->C1, fa->lambda, Af, ea, out);
   else
-    oz_gemm<MAXF, OWARPS><<<unsigned(grid), OTHREADS, smem, st>>>(nE, M, Kd, Mt, Kt, Af, ea, X, ldx, out, ldo);
+    oz_gemm<MAXF, OWARPS, T><<<unsigned(grid), OTHREADS, smem, st>>>(nE, M, Kd, Mt, Kt, Af, ea, X, ldx, out, ldo);
   note_launch();
   return cudaGetLastError();
 }
 
 // warps per CTA chosen so every warp gets the same number of fragments
-cudaError_t gemm(int Mt, int64_t nE, int M, int Kd, int Kt, const uint4* Af, const int* ea, const double* X,
-                 int64_t ldx, double* out, int64_t ldo, const FusedArgs* fa, cudaStream_t st) {
+template <typename T>
+cudaError_t gemm(int Mt, int64_t nE, int M, int Kd, int Kt, const uint4* Af, const int* ea, const T* X, int64_t ldx,
+                 T* out, int64_t ldo, const FusedArgs<T>* fa, cudaStream_t st) {
   const int nfrag = Mt * ONT;
-#define OZ_L(F, W) return launch_gemm<F, W>(nE, M, Kd, Mt, Kt, Af, ea, X, ldx, out, ldo, fa, st)
+#define OZ_L(F, W) return launch_gemm<F, W, T>(nE, M, Kd, Mt, Kt, Af, ea, X, ldx, out, ldo, fa, st)
   if (nfrag % 8 == 0) {
     const int f = nfrag / 8;
     if (f == 1) OZ_L(1, 8);
@@ -499,43 +551,51 @@ cudaError_t gemm(int Mt, int64_t nE, int M, int Kd, int Kt, const uint4* Af, con
 #undef OZ_L
 }
 
+OzOps g_oz[2][64][kMaxN + 1];  // [0: FP64, 1: FP32][device][degree]
 
-}  // namespace
-
-// Per-degree operator slices (device, built once per process and device).
-static OzOps g_oz[64][kMaxN + 1];
-
-cudaError_t launch_apply_oz64(dg_mesh* m, int degree, int B, double lambda, const double* u, double* Au,
-                              cudaStream_t st) {
+template <typename T>
+cudaError_t apply_tensor(dg_mesh* m, int degree, int B, double lambda, const T* u, T* Au, cudaStream_t st) {
+  constexpr bool f64 = sizeof(T) == 8;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  OzOps& o = g_oz[dev & 63][degree];
+  OzOps& o = g_oz[f64 ? 0 : 1][dev & 63][degree];
   if (!o.A1) {
     if (m->ref[degree].N == 0) m->ref[degree] = build_reference(degree);
-    e = build_oz_ops(m->ref[degree], o);
+    e = build_oz_ops(m->ref[degree], Slices<T>::KS, o);
     if (e != cudaSuccess) return e;
   }
   const int N = degree, Np = (N + 1) * (N + 2) / 2, NFN = 3 * (N + 1);
   const bool helm = lambda != 0.0;
   const int KY = 2 * Np + 3 * NFN + (helm ? Np : 0);
   const int64_t nE = int64_t(B) * m->K;
-  const size_t need = size_t(nE) * (2 * Np);  // doubles: C1 (Y is built in shared memory)
-  if (m->oz_cap < need) {
+  const size_t need = size_t(nE) * (2 * Np);  // C1 (Y is built in shared memory)
+  if (m->oz_cap < need * sizeof(T) / sizeof(double) + 1) {
     cudaFree(m->oz_scratch);
     m->oz_scratch = nullptr;
     m->oz_cap = 0;
-    e = cudaMalloc(&m->oz_scratch, need * sizeof(double));
+    const size_t words = need * sizeof(T) / sizeof(double) + 1;
+    e = cudaMalloc(&m->oz_scratch, words * sizeof(double));
     if (e != cudaSuccess) return e;
-    m->oz_cap = need;
+    m->oz_cap = words;
     ++m->scratch_gen;
   }
-  double* C1 = m->oz_scratch;
-  e = gemm(o.Mt1, nE, 2 * Np, Np, o.Kt1, o.A1, o.ea1, u, Np, C1, 2 * Np, nullptr, st);
+  T* C1 = reinterpret_cast<T*>(m->oz_scratch);
+  const T* gx = f64 ? reinterpret_cast<const T*>(m->geox) : reinterpret_cast<const T*>(m->geox32);
+  e = gemm<T>(o.Mt1, nE, 2 * Np, Np, o.Kt1, o.A1, o.ea1, u, Np, C1, 2 * Np, nullptr, st);
   if (e != cudaSuccess) return e;
-  const FusedArgs fa{N, m->K, m->geox, m->conn, u, C1, lambda};
-  if (helm) return gemm(o.Mt2, nE, Np, KY, o.Kt2h, o.A2h, o.ea2h, nullptr, 0, Au, Np, &fa, st);
-  return gemm(o.Mt2, nE, Np, KY, o.Kt2p, o.A2p, o.ea2p, nullptr, 0, Au, Np, &fa, st);
+  const FusedArgs<T> fa{N, m->K, gx, m->conn, u, C1, T(lambda)};
+  if (helm) return gemm<T>(o.Mt2, nE, Np, KY, o.Kt2h, o.A2h, o.ea2h, nullptr, 0, Au, Np, &fa, st);
+  return gemm<T>(o.Mt2, nE, Np, KY, o.Kt2p, o.A2p, o.ea2p, nullptr, 0, Au, Np, &fa, st);
+}
+
+}  // namespace
+
+cudaError_t launch_apply_tensor(dg_mesh* m, int degree, bool f64, int B, double lambda, const void* u, void* Au,
+                                cudaStream_t st) {
+  if (f64)
+    return apply_tensor<double>(m, degree, B, lambda, static_cast<const double*>(u), static_cast<double*>(Au), st);
+  return apply_tensor<float>(m, degree, B, lambda, static_cast<const float*>(u), static_cast<float*>(Au), st);
 }
 
 }  // namespace dgx

@@ -86,6 +86,7 @@ struct dg_mesh {
   float* ih32 = nullptr;     // K x 3
   // FP64 derived geometry [K][16]: J, Grr, Grs, Gss | per face (n.grad r, n.grad s, sJ, max(1/h-,1/h+))
   double* geox = nullptr;
+  float* geox32 = nullptr;  // the same 16 words per element in FP32
   dgx::RefElem ref[dgx::kMaxN + 1];
   dgx::DevOps ops64[dgx::kMaxN + 1];
   dgx::DevOps ops32[dgx::kMaxN + 1];
@@ -120,8 +121,8 @@ bool kernel_valid(int kernel, int degree, bool f64);
 bool ept_supported(int degree);
 cudaError_t launch_apply_ept(dg_mesh* m, int degree, bool f64, int B, double lambda, const void* u, void* Au,
                              cudaStream_t st);
-cudaError_t launch_apply_oz64(dg_mesh* m, int degree, int B, double lambda, const double* u, double* Au,
-                              cudaStream_t st);
+cudaError_t launch_apply_tensor(dg_mesh* m, int degree, bool f64, int B, double lambda, const void* u, void* Au,
+                                cudaStream_t st);
 cudaError_t launch_nodes(const dg_mesh* m, int degree, double* x, double* y, cudaStream_t st);
 
 void set_error(const std::string& msg);
