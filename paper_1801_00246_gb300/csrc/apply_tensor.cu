@@ -200,11 +200,13 @@ __device__ __forceinline__ void slice_dev(float v, int sc, uint16_t (&s)[KS]) {
 // data slices Xs (per element n: scale exponent exs[n]) and the operator's
 // fragment-ordered slices Af (row exponents ea). Warp w takes fragments
 // w, w + OWARPS, ... (a fragment: 16 operator rows x 8 elements).
+// With `add` set, out[e0 + n][r] += addsc[n] * add[(e0 + n) * ldadd + r].
 template <int MAXF, int OWARPS, typename T>
 __device__ __forceinline__ void oz_mma_tile(const uint16_t* __restrict__ Xs, const int* __restrict__ exs, int KP,
                                             int M, int Mt, int Kt, int ne, int64_t e0,
                                             const uint4* __restrict__ Af, const int* __restrict__ ea,
-                                            T* __restrict__ out, int64_t ldo) {
+                                            T* __restrict__ out, int64_t ldo, const T* __restrict__ add = nullptr,
+                                            int64_t ldadd = 0, const T* __restrict__ addsc = nullptr) {
   constexpr int KS = Slices<T>::KS;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
@@ -248,12 +250,20 @@ __device__ __forceinline__ void oz_mma_tile(const uint16_t* __restrict__ Xs, con
           h = sum;
           l = ls + err;
         }
-        if (r < M && n < ne) out[(e0 + n) * ldo + r] = f2d_scaled(h, ea[r] + exs[n] - 14) + f2d_scaled(l, ea[r] + exs[n] - 14);
+        if (r < M && n < ne) {
+          T o = f2d_scaled(h, ea[r] + exs[n] - 14) + f2d_scaled(l, ea[r] + exs[n] - 14);
+          if (add) o += addsc[n] * add[(e0 + n) * ldadd + r];
+          out[(e0 + n) * ldo + r] = o;
+        }
       } else {
         float h = acc[KS - 1][c];
 #pragma unroll
         for (int s = KS - 2; s >= 0; --s) h = acc[s][c] + h * 0.0078125f;
-        if (r < M && n < ne) out[(e0 + n) * ldo + r] = f2f_scaled(h, ea[r] + exs[n] - 14);
+        if (r < M && n < ne) {
+          T o = f2f_scaled(h, ea[r] + exs[n] - 14);
+          if (add) o += addsc[n] * add[(e0 + n) * ldadd + r];
+          out[(e0 + n) * ldo + r] = o;
+        }
       }
     }
   }
@@ -310,22 +320,26 @@ __device__ __forceinline__ int fnode_rt(int N, int f, int j) {
 
 // The output product with the pointwise stage fused into its slicing phase:
 // warp w builds the Y row of element n (columns: wr, ws (Np each) |
-// 1/2 nr sJ [u], 1/2 ns sJ [u] (NFN each) | -sJ ({n.grad u} + tau [u]) (NFN) |
-// lambda J u (Np, Helmholtz only)) in registers, from C1, u, the geometry
+// 1/2 nr sJ [u], 1/2 ns sJ [u] (NFN each) | -sJ ({n.grad u} + tau [u]) (NFN))
+// in registers, from C1, u, the geometry
 // gx (16 words per element: J, Grr, Grs, Gss | per face nr, ns, sJ, ihmax) and
 // the neighbours' C1 and u rows; takes the row's scale exponent as a warp
-// maximum and writes the slices straight to shared memory.
+// maximum and writes the slices straight to shared memory. For the Helmholtz
+// form C1 carries a third block M u (rows 2Np..3Np of the first product) and
+// the epilogue adds lambda J (M u), which keeps the output product as narrow as
+// the Poisson one.
 template <int MAXF, int OWARPS, typename T>
 __global__ void __launch_bounds__(OWARPS * 32) oz_out(int N, int64_t K, int64_t nE, int Kd, int Mt, int Kt,
                                                    const T* __restrict__ gx, const int32_t* __restrict__ conn,
-                                                   const T* __restrict__ u, const T* __restrict__ C1, T lambda,
-                                                   const uint4* __restrict__ Af, const int* __restrict__ ea,
-                                                   T* __restrict__ out) {
+                                                   const T* __restrict__ u, const T* __restrict__ C1, int ldc,
+                                                   T lambda, const uint4* __restrict__ Af,
+                                                   const int* __restrict__ ea, T* __restrict__ out) {
   constexpr int KS = Slices<T>::KS;
   extern __shared__ __align__(16) uint16_t osm[];
   const int KP = Kt * 16 + 8;
   uint16_t* Xs = osm;
   int* exs = reinterpret_cast<int*>(osm + size_t(KS) * OE * KP);
+  T* addsc = reinterpret_cast<T*>(exs + OE);  // [OE]: lambda J per element (Helmholtz)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int Np = (N + 1) * (N + 2) / 2, Nfp = N + 1, NFN = 3 * Nfp;
   const T cpen = T((N + 1) * (N + 2)) / T(2);
@@ -348,7 +362,8 @@ __global__ void __launch_bounds__(OWARPS * 32) oz_out(int N, int64_t K, int64_t 
         const int64_t e = be % K;
         const int64_t boff = be - e;
         const T* g = gx + 16 * e;
-        const T* c = C1 + be * (2 * Np);
+        const T* c = C1 + be * ldc;
+        if (lane == 0) addsc[n] = lambda * g[0];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int i = lane + 32 * h;
@@ -358,10 +373,6 @@ __global__ void __launch_bounds__(OWARPS * 32) oz_out(int N, int64_t K, int64_t 
             col[3 * h] = i;
             v[3 * h + 1] = g[2] * ur + g[3] * us;
             col[3 * h + 1] = Np + i;
-            if (lambda != T(0)) {
-              v[3 * h + 2] = lambda * g[0] * u[be * Np + i];
-              col[3 * h + 2] = 2 * Np + 3 * NFN + i;
-            }
           }
         }
         if (lane < NFN) {
@@ -377,7 +388,7 @@ __global__ void __launch_bounds__(OWARPS * 32) oz_out(int N, int64_t K, int64_t 
             const int fn = code & 3;
             const int kn = fnode_rt(N, fn, Nfp - 1 - j);
             const T* gn = gx + 16 * nb + 4 + 4 * fn;
-            const T* cn = C1 + (boff + nb) * (2 * Np);
+            const T* cn = C1 + (boff + nb) * ldc;
             const T up = u[(boff + nb) * Np + kn];
             const T dnp = gn[0] * cn[kn] + gn[1] * cn[Np + kn];
             jm = up - um;
@@ -415,7 +426,10 @@ __global__ void __launch_bounds__(OWARPS * 32) oz_out(int N, int64_t K, int64_t 
         for (int jj = 0; jj < KS; ++jj) Xs[(size_t(jj) * OE + n) * KP + k] = 0;
     }
     __syncthreads();
-    oz_mma_tile<MAXF, OWARPS, T>(Xs, exs, KP, Np, Mt, Kt, ne, e0, Af, ea, out, Np);
+    if (lambda != T(0))  // + lambda J (M u), M u being C1's third block
+      oz_mma_tile<MAXF, OWARPS, T>(Xs, exs, KP, Np, Mt, Kt, ne, e0, Af, ea, out, Np, C1 + 2 * Np, ldc, addsc);
+    else
+      oz_mma_tile<MAXF, OWARPS, T>(Xs, exs, KP, Np, Mt, Kt, ne, e0, Af, ea, out, Np);
   }
 }
 
@@ -428,57 +442,56 @@ struct FusedArgs {
   const int32_t* conn;
   const T* u;
   const T* C1;
+  int ldc;
   T lambda;
 };
 
 struct OzOps {
-  int Mt1 = 0, Kt1 = 0, Mt2 = 0, Kt2p = 0, Kt2h = 0;
-  uint4 *A1 = nullptr, *A2p = nullptr, *A2h = nullptr;
-  int *ea1 = nullptr, *ea2p = nullptr, *ea2h = nullptr;
+  int Mt1 = 0, Kt1 = 0, Mt1h = 0, Mt2 = 0, Kt2 = 0;
+  uint4 *A1 = nullptr, *A1h = nullptr, *A2 = nullptr;  // [Dr; Ds], [Dr; Ds; M], OB
+  int *ea1 = nullptr, *ea1h = nullptr, *ea2 = nullptr;
 };
 
 cudaError_t build_oz_ops(const RefElem& R, int KS, OzOps& o) {
   const int N = R.N, Np = R.Np, Nfp = R.Nfp, NFN = 3 * Nfp;
-  // [Dr; Ds]: 2Np x Np
-  std::vector<double> A1(size_t(2 * Np) * Np);
+  // [Dr; Ds; M]: 3Np x Np (the Poisson form uses the first 2Np rows)
+  std::vector<double> A1(size_t(3 * Np) * Np);
   for (int i = 0; i < Np; ++i)
     for (int m = 0; m < Np; ++m) {
       A1[size_t(i) * Np + m] = R.Dr[size_t(i) * Np + m];
       A1[size_t(Np + i) * Np + m] = R.Ds[size_t(i) * Np + m];
+      A1[size_t(2 * Np + i) * Np + m] = R.M[size_t(i) * Np + m];
     }
-  // OB: Np x (2Np + 3NFN [+ Np])
-  const int KPo = 2 * Np + 3 * NFN, KHo = KPo + Np;
-  auto build_ob = [&](int Kc) {
-    std::vector<double> B(size_t(Np) * Kc, 0.0);
-    for (int i = 0; i < Np; ++i) {
-      for (int m = 0; m < Np; ++m) {
-        B[size_t(i) * Kc + m] = R.Br[size_t(i) * Np + m];
-        B[size_t(i) * Kc + Np + m] = R.Bs[size_t(i) * Np + m];
-        if (Kc == KHo) B[size_t(i) * Kc + KPo + m] = R.M[size_t(i) * Np + m];
-      }
-      for (int f = 0; f < 3; ++f)
-        for (int l = 0; l < Nfp; ++l) {
-          double dr = 0.0, ds = 0.0, ef = 0.0;
-          for (int j = 0; j < Nfp; ++j) {
-            const int k = face_node(N, f, j);
-            const double mf = R.Mf[size_t(j) * Nfp + l];
-            dr += R.Dr[size_t(k) * Np + i] * mf;
-            ds += R.Ds[size_t(k) * Np + i] * mf;
-            if (k == i) ef += mf;
-          }
-          B[size_t(i) * Kc + 2 * Np + f * Nfp + l] = dr;
-          B[size_t(i) * Kc + 2 * Np + NFN + f * Nfp + l] = ds;
-          B[size_t(i) * Kc + 2 * Np + 2 * NFN + f * Nfp + l] = ef;
+  // OB: Np x (2Np + 3NFN)
+  const int Kc = 2 * Np + 3 * NFN;
+  std::vector<double> B(size_t(Np) * Kc, 0.0);
+  for (int i = 0; i < Np; ++i) {
+    for (int m = 0; m < Np; ++m) {
+      B[size_t(i) * Kc + m] = R.Br[size_t(i) * Np + m];
+      B[size_t(i) * Kc + Np + m] = R.Bs[size_t(i) * Np + m];
+    }
+    for (int f = 0; f < 3; ++f)
+      for (int l = 0; l < Nfp; ++l) {
+        double dr = 0.0, ds = 0.0, ef = 0.0;
+        for (int j = 0; j < Nfp; ++j) {
+          const int k = face_node(N, f, j);
+          const double mf = R.Mf[size_t(j) * Nfp + l];
+          dr += R.Dr[size_t(k) * Np + i] * mf;
+          ds += R.Ds[size_t(k) * Np + i] * mf;
+          if (k == i) ef += mf;
         }
-    }
-    return B;
-  };
-  std::vector<uint32_t> f1, f2p, f2h;
-  std::vector<int> e1, e2p, e2h;
-  int Mt2h = 0;
-  slice_operator(A1, 2 * Np, Np, KS, o.Mt1, o.Kt1, f1, e1);
-  slice_operator(build_ob(KPo), Np, KPo, KS, o.Mt2, o.Kt2p, f2p, e2p);
-  slice_operator(build_ob(KHo), Np, KHo, KS, Mt2h, o.Kt2h, f2h, e2h);
+        B[size_t(i) * Kc + 2 * Np + f * Nfp + l] = dr;
+        B[size_t(i) * Kc + 2 * Np + NFN + f * Nfp + l] = ds;
+        B[size_t(i) * Kc + 2 * Np + 2 * NFN + f * Nfp + l] = ef;
+      }
+  }
+  std::vector<uint32_t> f1, f1h, f2;
+  std::vector<int> e1, e1h, e2;
+  int Kt1h = 0;
+  slice_operator(std::vector<double>(A1.begin(), A1.begin() + size_t(2 * Np) * Np), 2 * Np, Np, KS, o.Mt1, o.Kt1, f1,
+                 e1);
+  slice_operator(A1, 3 * Np, Np, KS, o.Mt1h, Kt1h, f1h, e1h);
+  slice_operator(B, Np, Kc, KS, o.Mt2, o.Kt2, f2, e2);
   auto up = [](auto& dst, const auto& v) -> cudaError_t {
     cudaError_t e = cudaMalloc(&dst, v.size() * sizeof(v[0]));
     if (e != cudaSuccess) return e;
@@ -486,18 +499,19 @@ cudaError_t build_oz_ops(const RefElem& R, int KS, OzOps& o) {
   };
   cudaError_t e;
   if ((e = up(o.A1, f1)) != cudaSuccess) return e;
-  if ((e = up(o.A2p, f2p)) != cudaSuccess) return e;
-  if ((e = up(o.A2h, f2h)) != cudaSuccess) return e;
+  if ((e = up(o.A1h, f1h)) != cudaSuccess) return e;
+  if ((e = up(o.A2, f2)) != cudaSuccess) return e;
   if ((e = up(o.ea1, e1)) != cudaSuccess) return e;
-  if ((e = up(o.ea2p, e2p)) != cudaSuccess) return e;
-  return up(o.ea2h, e2h);
+  if ((e = up(o.ea1h, e1h)) != cudaSuccess) return e;
+  return up(o.ea2, e2);
 }
 
 template <int MAXF, int OWARPS, typename T>
 cudaError_t launch_gemm(int64_t nE, int M, int Kd, int Mt, int Kt, const uint4* Af, const int* ea, const T* X,
                         int64_t ldx, T* out, int64_t ldo, const FusedArgs<T>* fa, cudaStream_t st) {
   constexpr int OTHREADS = OWARPS * 32;
-  const size_t smem = size_t(Slices<T>::KS) * OE * (Kt * 16 + 8) * sizeof(uint16_t) + OE * sizeof(int);
+  const size_t smem = size_t(Slices<T>::KS) * OE * (Kt * 16 + 8) * sizeof(uint16_t) + OE * sizeof(int) +
+                      OE * sizeof(T);
   static size_t configured[64][2] = {};  // per device and variant: the largest dynamic shared memory set
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -518,37 +532,37 @@ cudaError_t launch_gemm(int64_t nE, int M, int Kd, int Mt, int Kt, const uint4* 
   if (grid > tiles) grid = tiles;
   if (fa)
     oz_out<MAXF, OWARPS, T><<<unsigned(grid), OTHREADS, smem, st>>>(fa->N, fa->K, nE, Kd, Mt, Kt, fa->gx, fa->conn,
-                                                                   fa->u, fa->C1, fa->lambda, Af, ea, out);
+                                                                   fa->u, fa->C1, fa->ldc, fa->lambda, Af, ea, out);
   else
     oz_gemm<MAXF, OWARPS, T><<<unsigned(grid), OTHREADS, smem, st>>>(nE, M, Kd, Mt, Kt, Af, ea, X, ldx, out, ldo);
   note_launch();
   return cudaGetLastError();
 }
 
-// warps per CTA chosen so every warp gets the same number of fragments
+// warps per CTA chosen so every warp gets the same number of fragments where
+// possible; every fragment must be covered (MAXF x OWARPS >= fragments)
 template <typename T>
 cudaError_t gemm(int Mt, int64_t nE, int M, int Kd, int Kt, const uint4* Af, const int* ea, const T* X, int64_t ldx,
                  T* out, int64_t ldo, const FusedArgs<T>* fa, cudaStream_t st) {
   const int nfrag = Mt * ONT;
 #define OZ_L(F, W) return launch_gemm<F, W, T>(nE, M, Kd, Mt, Kt, Af, ea, X, ldx, out, ldo, fa, st)
-  if (nfrag % 8 == 0) {
-    const int f = nfrag / 8;
-    if (f == 1) OZ_L(1, 8);
-    if (f == 2) OZ_L(2, 8);
-    if (f == 3) OZ_L(3, 8);
-  }
-  if (nfrag % 6 == 0 && nfrag / 6 <= 3) {
-    const int f = nfrag / 6;
-    if (f == 1) OZ_L(1, 6);
-    if (f == 2) OZ_L(2, 6);
-    OZ_L(3, 6);
+#define OZ_BY(W, f)              \
+  switch (f) {                   \
+    case 1: OZ_L(1, W);          \
+    case 2: OZ_L(2, W);          \
+    case 3: OZ_L(3, W);          \
+    case 4: OZ_L(4, W);          \
+    case 5: OZ_L(5, W);          \
+    case 6: OZ_L(6, W);          \
+    default: break;              \
   }
   if (nfrag <= 4) OZ_L(1, 4);
-  const int maxf = (nfrag + 7) / 8;
-  if (maxf <= 2) OZ_L(2, 8);
-  if (maxf <= 3) OZ_L(3, 8);
-  OZ_L(4, 8);
+  if (nfrag % 8 == 0) OZ_BY(8, nfrag / 8)
+  if (nfrag % 6 == 0) OZ_BY(6, nfrag / 6)
+  OZ_BY(8, (nfrag + 7) / 8)
+#undef OZ_BY
 #undef OZ_L
+  return cudaErrorInvalidValue;  // more fragments than any instantiation covers
 }
 
 OzOps g_oz[2][64][kMaxN + 1];  // [0: FP64, 1: FP32][device][degree]
@@ -567,14 +581,14 @@ cudaError_t apply_tensor(dg_mesh* m, int degree, int B, double lambda, const T* 
   }
   const int N = degree, Np = (N + 1) * (N + 2) / 2, NFN = 3 * (N + 1);
   const bool helm = lambda != 0.0;
-  const int KY = 2 * Np + 3 * NFN + (helm ? Np : 0);
+  const int KY = 2 * Np + 3 * NFN;
+  const int ldc = helm ? 3 * Np : 2 * Np;  // C1 rows: ur, us (+ M u)
   const int64_t nE = int64_t(B) * m->K;
-  const size_t need = size_t(nE) * (2 * Np);  // C1 (Y is built in shared memory)
-  if (m->oz_cap < need * sizeof(T) / sizeof(double) + 1) {
+  const size_t words = size_t(nE) * ldc * sizeof(T) / sizeof(double) + 1;
+  if (m->oz_cap < words) {
     cudaFree(m->oz_scratch);
     m->oz_scratch = nullptr;
     m->oz_cap = 0;
-    const size_t words = need * sizeof(T) / sizeof(double) + 1;
     e = cudaMalloc(&m->oz_scratch, words * sizeof(double));
     if (e != cudaSuccess) return e;
     m->oz_cap = words;
@@ -582,11 +596,11 @@ cudaError_t apply_tensor(dg_mesh* m, int degree, int B, double lambda, const T* 
   }
   T* C1 = reinterpret_cast<T*>(m->oz_scratch);
   const T* gx = f64 ? reinterpret_cast<const T*>(m->geox) : reinterpret_cast<const T*>(m->geox32);
-  e = gemm<T>(o.Mt1, nE, 2 * Np, Np, o.Kt1, o.A1, o.ea1, u, Np, C1, 2 * Np, nullptr, st);
+  if (helm) e = gemm<T>(o.Mt1h, nE, 3 * Np, Np, o.Kt1, o.A1h, o.ea1h, u, Np, C1, ldc, nullptr, st);
+  else e = gemm<T>(o.Mt1, nE, 2 * Np, Np, o.Kt1, o.A1, o.ea1, u, Np, C1, ldc, nullptr, st);
   if (e != cudaSuccess) return e;
-  const FusedArgs<T> fa{N, m->K, gx, m->conn, u, C1, T(lambda)};
-  if (helm) return gemm<T>(o.Mt2, nE, Np, KY, o.Kt2h, o.A2h, o.ea2h, nullptr, 0, Au, Np, &fa, st);
-  return gemm<T>(o.Mt2, nE, Np, KY, o.Kt2p, o.A2p, o.ea2p, nullptr, 0, Au, Np, &fa, st);
+  const FusedArgs<T> fa{N, m->K, gx, m->conn, u, C1, ldc, T(lambda)};
+  return gemm<T>(o.Mt2, nE, Np, KY, o.Kt2, o.A2, o.ea2, nullptr, 0, Au, Np, &fa, st);
 }
 
 }  // namespace
