@@ -17,8 +17,12 @@
 //     < 2^24), and only i + j <= KS + 1 is formed;
 //   * the KS accumulators are combined by Horner's rule (float-float for FP64)
 //     and scaled back by building the exponent bits.
-// FP64 takes KS = 8 slices (56 bits, 36 products; relative error near 2^-44 of
-// |A||x|), FP32 KS = 4 (28 bits, 10 products; near 2^-26 of |A||x|).
+// That is the FP64 scheme: KS = 8 slices (56 bits, 36 products; relative error
+// near 2^-44 of |A||x|). FP32 needs no exactness, only FP32-level accuracy, so
+// it splits operands by round-to-nearest into three BF16 pieces (hi, mid, lo:
+// x - hi - mid - lo is below 2^-24 |x|), forms the 6 products with
+// i + j <= 2 into a single FP32 accumulator and needs no exponents, scaling or
+// integer extraction at all.
 //
 // The face mass is folded into the output operator
 //   OB = [Br Bs | Dr_f^T Mf  Ds_f^T Mf | E_f Mf | M],
@@ -27,6 +31,8 @@
 // That stage runs inside the output product's slicing phase (Y is built in
 // shared memory, never in HBM); the neighbour's trace and normal derivative at
 // a shared face node are read from its nodal values and its rows of C1.
+#include <cuda_bf16.h>
+
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -48,7 +54,7 @@ struct Slices<double> {
 };
 template <>
 struct Slices<float> {
-  static constexpr int KS = 4;  // 28 bits (3 slices, 21 bits, miss the FP32 tolerance where Au cancels)
+  static constexpr int KS = 3;  // round-to-nearest BF16 pieces hi, mid, lo
 };
 
 // ---------------------------------------------------------------- host side
@@ -76,6 +82,31 @@ int row_scale_exp(const double* row, int K) {
   return e;
 }
 
+// round-to-nearest-even BF16 bits of a float
+inline uint16_t bf16_rne(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  if ((u & 0x7f800000u) == 0x7f800000u) return uint16_t(u >> 16);
+  u += 0x7fffu + ((u >> 16) & 1u);
+  return uint16_t(u >> 16);
+}
+inline double bf16_value(uint16_t b) {
+  const uint32_t u = uint32_t(b) << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return double(f);
+}
+
+// v = hi + mid + lo + (a remainder below 2^-24 |v|), each piece BF16
+void split_host(double v, int KS, int* out) {
+  double r = v;
+  for (int j = 0; j < KS; ++j) {
+    const uint16_t b = bf16_rne(float(r));
+    out[j] = int(b);
+    r -= bf16_value(b);
+  }
+}
+
 inline uint16_t bf16_of_int(int x) {  // exact for |x| <= 256
   const float f = float(x);
   uint32_t u;
@@ -85,15 +116,20 @@ inline uint16_t bf16_of_int(int x) {  // exact for |x| <= 256
 
 // A (M x K, row-major FP64) -> fragment-ordered slices [KS][Mt][Kt][32 lanes] of
 // 4 uint32 (2 bf16 each) for mma.m16n8k16 row-major A, plus row exponents.
-void slice_operator(const std::vector<double>& A, int M, int K, int KS, int& Mt, int& Kt, std::vector<uint32_t>& frag,
-                    std::vector<int>& ea) {
+// split = true: round-to-nearest BF16 pieces (already BF16 bit patterns), no exponents.
+void slice_operator(const std::vector<double>& A, int M, int K, int KS, bool split, int& Mt, int& Kt,
+                    std::vector<uint32_t>& frag, std::vector<int>& ea) {
   Mt = (M + 15) / 16;
   Kt = (K + 15) / 16;
   ea.assign(Mt * 16, 0);
   std::vector<int> sl(size_t(Mt) * 16 * Kt * 16 * KS, 0);  // [row][k][slice]
   for (int r = 0; r < M; ++r) {
-    ea[r] = row_scale_exp(&A[size_t(r) * K], K);
-    for (int k = 0; k < K; ++k) slice_host(A[size_t(r) * K + k], ea[r], KS, &sl[(size_t(r) * Kt * 16 + k) * KS]);
+    if (!split) ea[r] = row_scale_exp(&A[size_t(r) * K], K);
+    for (int k = 0; k < K; ++k) {
+      int* o = &sl[(size_t(r) * Kt * 16 + k) * KS];
+      if (split) split_host(A[size_t(r) * K + k], KS, o);
+      else slice_host(A[size_t(r) * K + k], ea[r], KS, o);
+    }
   }
   auto S = [&](int r, int k, int i) { return sl[(size_t(r) * Kt * 16 + k) * KS + i]; };
   frag.assign(size_t(KS) * Mt * Kt * 32 * 4, 0);
@@ -103,9 +139,8 @@ void slice_operator(const std::vector<double>& A, int M, int K, int KS, int& Mt,
         for (int lane = 0; lane < 32; ++lane) {
           const int g = lane >> 2, t = lane & 3;
           const int r0 = mt * 16 + g, r1 = r0 + 8, c0 = kt * 16 + 2 * t, c1 = c0 + 8;
-          auto pack = [&](int r, int c) {
-            return uint32_t(bf16_of_int(S(r, c, i))) | (uint32_t(bf16_of_int(S(r, c + 1, i))) << 16);
-          };
+          auto bits = [&](int r, int c) { return split ? uint16_t(S(r, c, i)) : bf16_of_int(S(r, c, i)); };
+          auto pack = [&](int r, int c) { return uint32_t(bits(r, c)) | (uint32_t(bits(r, c + 1)) << 16); };
           uint32_t* q = &frag[((((size_t(i) * Mt + mt) * Kt + kt) * 32) + lane) * 4];
           q[0] = pack(r0, c0);
           q[1] = pack(r1, c0);
@@ -135,25 +170,10 @@ __device__ __forceinline__ double f2d_scaled(float f, int sc) {
   return __longlong_as_double((long long)(s | e | m));
 }
 
-// f * 2^sc in float from the exponent bits (results below the normal range flush to zero)
-__device__ __forceinline__ float f2f_scaled(float f, int sc) {
-  const unsigned int u = __float_as_uint(f);
-  const int ef = int((u >> 23) & 0xffu);
-  if (ef == 0) return 0.f;
-  const int ne = ef + sc;
-  if (ne <= 0) return 0.f;
-  if (ne >= 255) return __uint_as_float((u & 0x80000000u) | 0x7f800000u);
-  return __uint_as_float((u & 0x807fffffu) | (unsigned(ne) << 23));
-}
-
 // unbiased exponent e such that |v| < 2^e (a very negative value for zero)
 __device__ __forceinline__ int exp_bound(double v) {
   const int E = int((__double_as_longlong(v) >> 52) & 0x7ff);
   return E == 0 ? -1100 : E - 1022;
-}
-__device__ __forceinline__ int exp_bound(float v) {
-  const int E = int((__float_as_uint(v) >> 23) & 0xff);
-  return E == 0 ? -1100 : E - 126;
 }
 
 // KS signed 7-bit slices of v relative to 2^{sc} (|v| < 2^{sc}), as packed bf16 bits
@@ -176,25 +196,23 @@ __device__ __forceinline__ void slice_dev(double v, int sc, uint16_t (&s)[KS]) {
     s[j] = x ? (hb | sgn) : 0;
   }
 }
-template <int KS>
-__device__ __forceinline__ void slice_dev(float v, int sc, uint16_t (&s)[KS]) {
-  constexpr int bits = kSliceBits * KS;
-  const unsigned int b = __float_as_uint(v);
-  const int E = int((b >> 23) & 0xff);
-  const unsigned int m = (b & 0x7fffffu) | (E ? 0x800000u : 0u);
-  // |v| = m 2^{E-150};  I = floor(|v| 2^{bits - sc})
-  const int sh = (E ? E : 1) - 150 + bits - sc;
-  unsigned int I = 0;
-  if (sh >= 0) I = sh < 8 ? (m << sh) : 0u;
-  else if (sh > -32) I = m >> (-sh);
-  const uint16_t sgn = (b >> 31) ? 0x8000 : 0;
-#pragma unroll
-  for (int j = 0; j < KS; ++j) {
-    const int x = int((I >> (bits - kSliceBits * (j + 1))) & 127u);
-    const uint16_t hb = uint16_t(__float_as_uint(float(x)) >> 16);
-    s[j] = x ? (hb | sgn) : 0;
-  }
+
+// round-to-nearest BF16 pieces of an FP32 value (hi, mid, lo)
+__device__ __forceinline__ void split_dev(float v, uint16_t (&s)[3]) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  const float r1 = v - __bfloat162float(h);
+  const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+  const __nv_bfloat16 l = __float2bfloat16_rn(r1 - __bfloat162float(m));
+  s[0] = __bfloat16_as_ushort(h);
+  s[1] = __bfloat16_as_ushort(m);
+  s[2] = __bfloat16_as_ushort(l);
 }
+
+// value -> stored pieces: exponent-scaled integer slices (FP64) or BF16 split (FP32)
+template <int KS>
+__device__ __forceinline__ void pieces(double v, int sc, uint16_t (&s)[KS]) { slice_dev<KS>(v, sc, s); }
+template <int KS>
+__device__ __forceinline__ void pieces(float v, int, uint16_t (&s)[KS]) { split_dev(v, s); }
 
 // The product phase of a tile: out[e0 + n][r] = sum_k A[r][k] X[n][k] from the
 // data slices Xs (per element n: scale exponent exs[n]) and the operator's
@@ -216,9 +234,11 @@ __device__ __forceinline__ void oz_mma_tile(const uint16_t* __restrict__ Xs, con
     const int f = warp + OWARPS * q;
     if (f >= nfrag) break;
     const int mt = f / ONT, nt = f - mt * ONT;
-    float acc[KS][4];
+    // FP64: one accumulator per slice-exponent sum i + j; FP32: all products in one
+    constexpr int NACC = sizeof(T) == 8 ? KS : 1;
+    float acc[NACC][4];
 #pragma unroll
-    for (int s = 0; s < KS; ++s) acc[s][0] = acc[s][1] = acc[s][2] = acc[s][3] = 0.f;
+    for (int s = 0; s < NACC; ++s) acc[s][0] = acc[s][1] = acc[s][2] = acc[s][3] = 0.f;
     for (int kt = 0; kt < Kt; ++kt) {
       uint32_t b0[KS], b1[KS];
 #pragma unroll
@@ -231,7 +251,7 @@ __device__ __forceinline__ void oz_mma_tile(const uint16_t* __restrict__ Xs, con
       for (int i = 0; i < KS; ++i) {
         const uint4 a = __ldg(Af + ((size_t(i) * Mt + mt) * Kt + kt) * 32 + lane);
 #pragma unroll
-        for (int j = 0; j < KS - i; ++j) mma_bf16(acc[i + j], a, b0[j], b1[j]);
+        for (int j = KS - 1 - i; j >= 0; --j) mma_bf16(acc[NACC == 1 ? 0 : i + j], a, b0[j], b1[j]);
       }
     }
     // recombine: value = 2^{ea_r + ex_e - 14} sum_s acc[s] 2^{-7 s}
@@ -240,9 +260,9 @@ __device__ __forceinline__ void oz_mma_tile(const uint16_t* __restrict__ Xs, con
       const int r = mt * 16 + g + ((c & 2) ? 8 : 0);
       const int n = nt * 8 + 2 * t + (c & 1);
       if constexpr (sizeof(T) == 8) {
-        float h = acc[KS - 1][c], l = 0.f;
+        float h = acc[NACC - 1][c], l = 0.f;
 #pragma unroll
-        for (int s = KS - 2; s >= 0; --s) {
+        for (int s = NACC - 2; s >= 0; --s) {
           const float hs = h * 0.0078125f, ls = l * 0.0078125f;  // exact scaling by 2^-7
           const float sum = acc[s][c] + hs;
           const float bb = sum - acc[s][c];
@@ -256,11 +276,8 @@ __device__ __forceinline__ void oz_mma_tile(const uint16_t* __restrict__ Xs, con
           out[(e0 + n) * ldo + r] = o;
         }
       } else {
-        float h = acc[KS - 1][c];
-#pragma unroll
-        for (int s = KS - 2; s >= 0; --s) h = acc[s][c] + h * 0.0078125f;
         if (r < M && n < ne) {
-          T o = f2f_scaled(h, ea[r] + exs[n] - 14);
+          T o = acc[0][c];
           if (add) o += addsc[n] * add[(e0 + n) * ldadd + r];
           out[(e0 + n) * ldo + r] = o;
         }
@@ -287,20 +304,21 @@ __global__ void __launch_bounds__(OWARPS * 32) oz_gemm(int64_t nE, int M, int Kd
     const int64_t e0 = tile * OE;
     const int ne = int((nE - e0) < OE ? (nE - e0) : OE);
     __syncthreads();
-    // per-element scale exponents
-    for (int e = threadIdx.x; e < OE; e += OTHREADS) exs[e] = -1100;
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < ne * Kd; idx += OTHREADS) {
-      const int e = idx / Kd, k = idx - e * Kd;
-      atomicMax(&exs[e], exp_bound(__ldg(X + (e0 + e) * ldx + k)));
+    if constexpr (sizeof(T) == 8) {  // per-element scale exponents
+      for (int e = threadIdx.x; e < OE; e += OTHREADS) exs[e] = -1100;
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < ne * Kd; idx += OTHREADS) {
+        const int e = idx / Kd, k = idx - e * Kd;
+        atomicMax(&exs[e], exp_bound(__ldg(X + (e0 + e) * ldx + k)));
+      }
+      __syncthreads();
     }
-    __syncthreads();
     // slices, zero-padded in k and e
     for (int idx = threadIdx.x; idx < OE * Kt * 16; idx += OTHREADS) {
       const int e = idx / (Kt * 16), k = idx - e * (Kt * 16);
       uint16_t s[KS];
       if (e < ne && k < Kd) {
-        slice_dev<KS>(__ldg(X + (e0 + e) * ldx + k), exs[e], s);
+        pieces<KS>(__ldg(X + (e0 + e) * ldx + k), sizeof(T) == 8 ? exs[e] : 0, s);
       } else {
 #pragma unroll
         for (int j = 0; j < KS; ++j) s[j] = 0;
@@ -407,16 +425,18 @@ __global__ void __launch_bounds__(OWARPS * 32) oz_out(int N, int64_t K, int64_t 
         }
       }
       int emax = -1100;
+      if constexpr (sizeof(T) == 8) {
 #pragma unroll
-      for (int k = 0; k < 9; ++k)
-        if (col[k] >= 0) emax = max(emax, exp_bound(v[k]));
-      emax = __reduce_max_sync(0xffffffffu, emax);
-      if (lane == 0) exs[n] = emax;
+        for (int k = 0; k < 9; ++k)
+          if (col[k] >= 0) emax = max(emax, exp_bound(v[k]));
+        emax = __reduce_max_sync(0xffffffffu, emax);
+        if (lane == 0) exs[n] = emax;
+      }
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
         if (col[k] < 0) continue;
         uint16_t sl[KS];
-        slice_dev<KS>(v[k], emax, sl);
+        pieces<KS>(v[k], emax, sl);
 #pragma unroll
         for (int jj = 0; jj < KS; ++jj) Xs[(size_t(jj) * OE + n) * KP + col[k]] = sl[jj];
       }
@@ -452,7 +472,7 @@ struct OzOps {
   int *ea1 = nullptr, *ea1h = nullptr, *ea2 = nullptr;
 };
 
-cudaError_t build_oz_ops(const RefElem& R, int KS, OzOps& o) {
+cudaError_t build_oz_ops(const RefElem& R, int KS, bool split, OzOps& o) {
   const int N = R.N, Np = R.Np, Nfp = R.Nfp, NFN = 3 * Nfp;
   // [Dr; Ds; M]: 3Np x Np (the Poisson form uses the first 2Np rows)
   std::vector<double> A1(size_t(3 * Np) * Np);
@@ -488,10 +508,10 @@ cudaError_t build_oz_ops(const RefElem& R, int KS, OzOps& o) {
   std::vector<uint32_t> f1, f1h, f2;
   std::vector<int> e1, e1h, e2;
   int Kt1h = 0;
-  slice_operator(std::vector<double>(A1.begin(), A1.begin() + size_t(2 * Np) * Np), 2 * Np, Np, KS, o.Mt1, o.Kt1, f1,
-                 e1);
-  slice_operator(A1, 3 * Np, Np, KS, o.Mt1h, Kt1h, f1h, e1h);
-  slice_operator(B, Np, Kc, KS, o.Mt2, o.Kt2, f2, e2);
+  slice_operator(std::vector<double>(A1.begin(), A1.begin() + size_t(2 * Np) * Np), 2 * Np, Np, KS, split, o.Mt1,
+                 o.Kt1, f1, e1);
+  slice_operator(A1, 3 * Np, Np, KS, split, o.Mt1h, Kt1h, f1h, e1h);
+  slice_operator(B, Np, Kc, KS, split, o.Mt2, o.Kt2, f2, e2);
   auto up = [](auto& dst, const auto& v) -> cudaError_t {
     cudaError_t e = cudaMalloc(&dst, v.size() * sizeof(v[0]));
     if (e != cudaSuccess) return e;
@@ -539,28 +559,24 @@ cudaError_t launch_gemm(int64_t nE, int M, int Kd, int Mt, int Kt, const uint4* 
   return cudaGetLastError();
 }
 
-// warps per CTA chosen so every warp gets the same number of fragments where
-// possible; every fragment must be covered (MAXF x OWARPS >= fragments)
+// 8 warps per CTA (the fill phase, one warp per element, wants them even where
+// the product phase leaves some idle: measured faster than 6 at 12 fragments),
+// except for products of at most 4 fragments (small degrees), where 4 warps
+// per CTA measured faster. Every fragment must be covered (MAXF x warps >= fragments).
 template <typename T>
 cudaError_t gemm(int Mt, int64_t nE, int M, int Kd, int Kt, const uint4* Af, const int* ea, const T* X, int64_t ldx,
                  T* out, int64_t ldo, const FusedArgs<T>* fa, cudaStream_t st) {
   const int nfrag = Mt * ONT;
-#define OZ_L(F, W) return launch_gemm<F, W, T>(nE, M, Kd, Mt, Kt, Af, ea, X, ldx, out, ldo, fa, st)
-#define OZ_BY(W, f)              \
-  switch (f) {                   \
-    case 1: OZ_L(1, W);          \
-    case 2: OZ_L(2, W);          \
-    case 3: OZ_L(3, W);          \
-    case 4: OZ_L(4, W);          \
-    case 5: OZ_L(5, W);          \
-    case 6: OZ_L(6, W);          \
-    default: break;              \
+  if (nfrag <= 4) return launch_gemm<1, 4, T>(nE, M, Kd, Mt, Kt, Af, ea, X, ldx, out, ldo, fa, st);
+#define OZ_L(F) return launch_gemm<F, 8, T>(nE, M, Kd, Mt, Kt, Af, ea, X, ldx, out, ldo, fa, st)
+  switch ((nfrag + 7) / 8) {
+    case 1: OZ_L(1);
+    case 2: OZ_L(2);
+    case 3: OZ_L(3);
+    case 4: OZ_L(4);
+    case 5: OZ_L(5);
+    default: break;
   }
-  if (nfrag <= 4) OZ_L(1, 4);
-  if (nfrag % 8 == 0) OZ_BY(8, nfrag / 8)
-  if (nfrag % 6 == 0) OZ_BY(6, nfrag / 6)
-  OZ_BY(8, (nfrag + 7) / 8)
-#undef OZ_BY
 #undef OZ_L
   return cudaErrorInvalidValue;  // more fragments than any instantiation covers
 }
@@ -576,7 +592,7 @@ cudaError_t apply_tensor(dg_mesh* m, int degree, int B, double lambda, const T* 
   OzOps& o = g_oz[f64 ? 0 : 1][dev & 63][degree];
   if (!o.A1) {
     if (m->ref[degree].N == 0) m->ref[degree] = build_reference(degree);
-    e = build_oz_ops(m->ref[degree], Slices<T>::KS, o);
+    e = build_oz_ops(m->ref[degree], Slices<T>::KS, !f64, o);
     if (e != cudaSuccess) return e;
   }
   const int N = degree, Np = (N + 1) * (N + 2) / 2, NFN = 3 * (N + 1);
