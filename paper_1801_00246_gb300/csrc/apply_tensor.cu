@@ -176,24 +176,29 @@ __device__ __forceinline__ int exp_bound(double v) {
   return E == 0 ? -1100 : E - 1022;
 }
 
-// KS signed 7-bit slices of v relative to 2^{sc} (|v| < 2^{sc}), as packed bf16 bits
+// 8 signed 7-bit slices of v relative to 2^{sc} (|v| < 2^{sc}), as bf16 bits.
+// I = floor(|v| 2^{56 - sc}) is formed as two 28-bit halves; each slice is a
+// bit-field of one half, turned into a float exactly by OR-ing it into the
+// mantissa of 2^23 and subtracting 2^23 (no integer-to-float conversion), whose
+// top 16 bits are its bf16 pattern. A zero slice gives +-0, which adds nothing.
 template <int KS>
 __device__ __forceinline__ void slice_dev(double v, int sc, uint16_t (&s)[KS]) {
-  constexpr int bits = kSliceBits * KS;
-  const long long b = __double_as_longlong(v);
-  const int E = int((b >> 52) & 0x7ff);
-  const unsigned long long m = (unsigned long long)(b & 0xfffffffffffffull) | (E ? (1ull << 52) : 0ull);
-  // |v| = m 2^{E-1075};  I = floor(|v| 2^{bits - sc})
-  const int sh = (E ? E : 1) - 1075 + bits - sc;
+  static_assert(KS == 8, "FP64 slicing: 8 slices of 7 bits");
+  const unsigned int hi = unsigned(__double2hiint(v)), lo = unsigned(__double2loint(v));
+  const int E = int((hi >> 20) & 0x7ffu);
+  const unsigned long long m = ((unsigned long long)((hi & 0xfffffu) | (E ? 0x100000u : 0u)) << 32) | lo;
+  // |v| = m 2^{E-1075};  I = m 2^{sh}
+  const int sh = (E ? E : 1) - 1075 + 56 - sc;
   unsigned long long I = 0;
-  if (sh >= 0) I = sh < 11 ? (m << sh) : 0ull;  // I < 2^bits <= 2^56 whenever |v| < 2^sc
+  if (sh >= 0) I = sh < 11 ? (m << sh) : 0ull;  // I < 2^56 whenever |v| < 2^sc
   else if (sh > -63) I = m >> (-sh);
-  const uint16_t sgn = (b < 0) ? 0x8000 : 0;
+  const unsigned int H = unsigned(I >> 28), L = unsigned(I) & 0xfffffffu;
+  const unsigned int sgn = (hi >> 31) << 15;
 #pragma unroll
-  for (int j = 0; j < KS; ++j) {
-    const int x = int((I >> (bits - kSliceBits * (j + 1))) & 127ull);
-    const uint16_t hb = uint16_t(__float_as_uint(float(x)) >> 16);
-    s[j] = x ? (hb | sgn) : 0;
+  for (int j = 0; j < 8; ++j) {
+    const unsigned int x = ((j < 4 ? H : L) >> (21 - 7 * (j & 3))) & 127u;
+    const float f = __uint_as_float(0x4B000000u | x) - 8388608.0f;  // exactly x
+    s[j] = uint16_t((__float_as_uint(f) >> 16) | sgn);
   }
 }
 
@@ -298,33 +303,33 @@ __global__ void __launch_bounds__(OWARPS * 32) oz_gemm(int64_t nE, int M, int Kd
   const int KP = Kt * 16 + 8;                 // row stride (bf16) of a slice; +8 breaks bank alignment
   uint16_t* Xs = osm;                         // [KS][OE][KP]
   int* exs = reinterpret_cast<int*>(osm + size_t(KS) * OE * KP);  // [OE]
-  constexpr int OTHREADS = OWARPS * 32;
   const int64_t ntiles = (nE + OE - 1) / OE;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t e0 = tile * OE;
     const int ne = int((nE - e0) < OE ? (nE - e0) : OE);
     __syncthreads();
-    if constexpr (sizeof(T) == 8) {  // per-element scale exponents
-      for (int e = threadIdx.x; e < OE; e += OTHREADS) exs[e] = -1100;
-      __syncthreads();
-      for (int idx = threadIdx.x; idx < ne * Kd; idx += OTHREADS) {
-        const int e = idx / Kd, k = idx - e * Kd;
-        atomicMax(&exs[e], exp_bound(__ldg(X + (e0 + e) * ldx + k)));
+    // one warp per element row: scale exponent as a warp maximum (FP64), then
+    // the row's pieces; padding columns and rows past the tile's end are zero
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int e = warp; e < OE; e += OWARPS) {
+      const T* xr = X + (e0 + e) * ldx;
+      int emax = -1100;
+      if (sizeof(T) == 8 && e < ne) {
+        for (int k = lane; k < Kd; k += 32) emax = max(emax, exp_bound(__ldg(xr + k)));
+        emax = __reduce_max_sync(0xffffffffu, emax);
+        if (lane == 0) exs[e] = emax;
       }
-      __syncthreads();
-    }
-    // slices, zero-padded in k and e
-    for (int idx = threadIdx.x; idx < OE * Kt * 16; idx += OTHREADS) {
-      const int e = idx / (Kt * 16), k = idx - e * (Kt * 16);
-      uint16_t s[KS];
-      if (e < ne && k < Kd) {
-        pieces<KS>(__ldg(X + (e0 + e) * ldx + k), sizeof(T) == 8 ? exs[e] : 0, s);
-      } else {
+      for (int k = lane; k < Kt * 16; k += 32) {
+        uint16_t s[KS];
+        if (e < ne && k < Kd) {
+          pieces<KS>(__ldg(xr + k), emax, s);
+        } else {
 #pragma unroll
-        for (int j = 0; j < KS; ++j) s[j] = 0;
+          for (int j = 0; j < KS; ++j) s[j] = 0;
+        }
+#pragma unroll
+        for (int j = 0; j < KS; ++j) Xs[(size_t(j) * OE + e) * KP + k] = s[j];
       }
-#pragma unroll
-      for (int j = 0; j < KS; ++j) Xs[(size_t(j) * OE + e) * KP + k] = s[j];
     }
     __syncthreads();
     oz_mma_tile<MAXF, OWARPS, T>(Xs, exs, KP, M, Mt, Kt, ne, e0, Af, ea, out, ldo);
