@@ -370,6 +370,8 @@ cudaError_t probe_matrix(dg_mesh* m, int degree, double lambda, Csr& A, cudaStre
   double *v = nullptr, *w = nullptr;
   ACK(cudaMalloc(&v, sizeof(double) * n1 * chunk));
   ACK(cudaMalloc(&w, sizeof(double) * n1 * chunk));
+  ACK(poison(v, sizeof(double) * n1 * chunk, POISON_AMG));
+  ACK(poison(w, sizeof(double) * n1 * chunk, POISON_AMG));
   std::vector<double> res(size_t(chunk) * n1);
   ACK(ensure_ops(m, degree));
   for (int p0 = 0; p0 < nprobe; p0 += chunk) {
@@ -424,8 +426,10 @@ cudaError_t amg_build(dg_mesh* m, int degree, double lambda, int B, Amg** out, c
       a->allocs.push_back(a->cinv);
       ACK(cudaMemcpy(a->cinv, inv.data(), sizeof(double) * n * n, cudaMemcpyHostToDevice));
       ACK(cudaMalloc(&a->cb, sizeof(double) * n * B));
+      ACK(poison(a->cb, sizeof(double) * n * B, POISON_AMG));
       a->allocs.push_back(a->cb);
       ACK(cudaMalloc(&a->cx, sizeof(double) * n * B));
+      ACK(poison(a->cx, sizeof(double) * n * B, POISON_AMG));
       a->allocs.push_back(a->cx);
       break;
     }
@@ -481,6 +485,7 @@ cudaError_t amg_build(dg_mesh* m, int degree, double lambda, int B, Amg** out, c
     ACK(cudaMemcpy(L.dinv, di.data(), sizeof(double) * A.n, cudaMemcpyHostToDevice));
     for (double** p : {&L.x, &L.b, &L.r, &L.d, &L.t}) {
       ACK(cudaMalloc(p, sizeof(double) * A.n * B));
+      ACK(poison(*p, sizeof(double) * A.n * B, POISON_AMG));
       a->allocs.push_back(*p);
     }
     a->L.push_back(L);

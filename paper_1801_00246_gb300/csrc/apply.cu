@@ -422,6 +422,7 @@ cudaError_t launch_apply(const dg_mesh* mc, int degree, dg_prec prec, int B, dou
       m->face32 = nullptr;
       m->face32_cap = 0;
       cudaError_t e = cudaMalloc(&m->face32, need * sizeof(float2));
+      if (e == cudaSuccess) e = poison(m->face32, need * sizeof(float2), POISON_APPLY);
       if (e != cudaSuccess) return e;
       m->face32_cap = need;
       ++m->scratch_gen;

@@ -611,6 +611,7 @@ cudaError_t apply_tensor(dg_mesh* m, int degree, int B, double lambda, const T* 
     m->oz_scratch = nullptr;
     m->oz_cap = 0;
     e = cudaMalloc(&m->oz_scratch, words * sizeof(double));
+    if (e == cudaSuccess) e = poison(m->oz_scratch, words * sizeof(double), POISON_APPLY);
     if (e != cudaSuccess) return e;
     m->oz_cap = words;
     ++m->scratch_gen;

@@ -131,5 +131,7 @@ void set_error(const std::string& msg);
 void note_launch();
 uint64_t launch_count();
 void add_launches(int64_t n);
+cudaError_t poison(void* p, size_t bytes, int group);  // 0xFF fill when DG_POISON_SCRATCH=1 or =group
+enum { POISON_AMG = 2, POISON_SOLVER = 3, POISON_APPLY = 4 };
 
 }  // namespace dgx

@@ -1,5 +1,6 @@
 // Host-side mesh setup: affine geometric factors (Section 5.2, Eq. operators2,
 // elementOps), face connectivity, and the checks that guard every later launch.
+#include <cstdlib>
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -17,6 +18,20 @@ static std::atomic<uint64_t> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 uint64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 void add_launches(int64_t n) { g_launches.fetch_add(uint64_t(n), std::memory_order_relaxed); }
+
+// Debug aid: with DG_POISON_SCRATCH=1 in the environment every scratch buffer
+// the library allocates is filled with 0xFF bytes (NaN in FP32 and FP64), so a
+// read of memory no kernel has written shows up as NaN instead of depending on
+// what the allocator hands back; 2, 3 or 4 poison only the AMG, the solver
+// workspace or the apply scratch.
+cudaError_t poison(void* p, size_t bytes, int group) {
+  static const int mode = [] {
+    const char* v = std::getenv("DG_POISON_SCRATCH");
+    return v ? std::atoi(v) : 0;
+  }();
+  if (mode == 0 || (mode != 1 && mode != group) || !p || bytes == 0) return cudaSuccess;
+  return cudaMemset(p, 0xFF, bytes);
+}
 void set_error(const std::string& msg) { g_last_error = msg; }
 const char* last_error() { return g_last_error.c_str(); }
 

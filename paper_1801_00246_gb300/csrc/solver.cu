@@ -110,6 +110,7 @@ template <typename T>
 cudaError_t walloc(Workspace* w, T** p, size_t count) {
   cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T) + 16);
   if (e == cudaSuccess) w->allocs.push_back(*p);
+  if (e == cudaSuccess) e = poison(*p, count * sizeof(T) + 16, POISON_SOLVER);
   return e;
 }
 
@@ -250,13 +251,19 @@ __global__ void k_init_check(double* scal, const double* partial) {
   if (s0 <= s[S_TOL2] * s[S_BB]) s[S_ACTIVE] = 0.0;
 }
 
-// p = z + beta p (per right-hand side); with init: p = z
+// p = z + beta p (per right-hand side); with init: p = z (p is not read: it may
+// hold anything, and 0 * NaN would not vanish)
 __global__ void k_update_p(int64_t n, const double* __restrict__ scal, const double* __restrict__ z,
                            double* __restrict__ p, int init) {
   const int b = blockIdx.y;
   const size_t off = size_t(b) * n;
-  const double beta = init ? 0.0 : scal[b * kNS + S_BETA];
-  if (!init && scal[b * kNS + S_ACTIVE] == 0.0) return;
+  if (init) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+      p[off + i] = z[off + i];
+    return;
+  }
+  if (scal[b * kNS + S_ACTIVE] == 0.0) return;
+  const double beta = scal[b * kNS + S_BETA];
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
     p[off + i] = z[off + i] + beta * p[off + i];
 }
