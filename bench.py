@@ -40,6 +40,7 @@ METRIC = "Poisson Ax GDOF/s & PCG solve ms (N=8, 524k tri), mixed vs FP64, % HBM
 PMG_DEGREES = [8, 4, 2, 1]
 CHEB = 3           # Chebyshev-Jacobi smoothing degree per pre/post smoothing
 COARSE_PASSES = 1  # degree-1 coarse solve: one AMG-preconditioned CG pass (a scaled AMG V-cycle)
+TENSOR_APPLY_TRAFFIC = None  # bytes per FP64 tensor apply from the latest ncu capture of the current kernels
 
 
 def peaks():
@@ -351,8 +352,8 @@ def run_ours(args, world, rank, local):
                      "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
                      "frac": tc_flops / (fp64_ms * 1e-3) / 1e12 / pk["bf16_tflops"],
                      # DRAM bytes read + written by oz_gemm + oz_out in one ncu capture of an
-                     # N=8 apply of this workload (dram__bytes_read.sum + dram__bytes_write.sum)
-                     "traffic": 1.3232e9,
+                     # N=8 apply of this workload; None while the kernels differ from that capture
+                     "traffic": TENSOR_APPLY_TRAFFIC,
                      "kernel": "FP64 Poisson apply (oz_gemm: C1 = [Dr;Ds]U, then oz_out: pointwise stage fused "
                                "into Au = OB Y): BF16 tensor-core products with exact 7-bit slicing, "
                                "36 slice products per FP64 product",

@@ -366,50 +366,53 @@ __global__ void __launch_bounds__(OWARPS * 32) oz_out(int N, int64_t K, int64_t 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int Np = (N + 1) * (N + 2) / 2, Nfp = N + 1, NFN = 3 * Nfp;
   const T cpen = T((N + 1) * (N + 2)) / T(2);
+  // per-lane constants (the same for every element): volume nodes lane and
+  // lane + 32, face node q = lane (face f, position j, local node k), and the
+  // neighbour's matching node for each of its three possible faces
+  const bool vol0 = lane < Np, vol1 = lane + 32 < Np, fq = lane < NFN;
+  const int f = fq ? lane / Nfp : 0, jf = fq ? lane - f * Nfp : 0;
+  const int kf = fnode_rt(N, f, jf);
+  const int kn0 = fnode_rt(N, 0, Nfp - 1 - jf), kn1 = fnode_rt(N, 1, Nfp - 1 - jf),
+            kn2 = fnode_rt(N, 2, Nfp - 1 - jf);
   const int64_t ntiles = (nE + OE - 1) / OE;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t e0 = tile * OE;
     const int ne = int((nE - e0) < OE ? (nE - e0) : OE);
     __syncthreads();
     for (int n = warp; n < OE; n += OWARPS) {
-      // slots: 0-2 volume node lane (wr, ws, lambda J u), 3-5 node lane + 32, 6-8 face node lane
-      T v[9];
-      int col[9];
+      // slots: 0-1 (wr, ws) at node lane, 2-3 at node lane + 32, 4-6 at face node lane
+      T v[7];
 #pragma unroll
-      for (int k = 0; k < 9; ++k) {
-        v[k] = T(0);
-        col[k] = -1;
-      }
-      if (n < ne) {
+      for (int k = 0; k < 7; ++k) v[k] = T(0);
+      const bool live = n < ne;
+      if (live) {
         const int64_t be = e0 + n;
-        const int64_t e = be % K;
+        const int64_t e = be < K ? be : be % K;  // first right-hand side: no division
         const int64_t boff = be - e;
         const T* g = gx + 16 * e;
         const T* c = C1 + be * ldc;
         if (lane == 0) addsc[n] = lambda * g[0];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int i = lane + 32 * h;
-          if (i < Np) {
-            const T ur = c[i], us = c[Np + i];
-            v[3 * h] = g[1] * ur + g[2] * us;
-            col[3 * h] = i;
-            v[3 * h + 1] = g[2] * ur + g[3] * us;
-            col[3 * h + 1] = Np + i;
-          }
+        const T g1 = g[1], g2 = g[2], g3 = g[3];
+        if (vol0) {
+          const T ur = c[lane], us = c[Np + lane];
+          v[0] = g1 * ur + g2 * us;
+          v[1] = g2 * ur + g3 * us;
         }
-        if (lane < NFN) {
-          const int q = lane, f = q / Nfp, j = q - f * Nfp;
+        if (vol1) {
+          const T ur = c[lane + 32], us = c[Np + lane + 32];
+          v[2] = g1 * ur + g2 * us;
+          v[3] = g2 * ur + g3 * us;
+        }
+        if (fq) {
           const T nr = g[4 + 4 * f], ns = g[5 + 4 * f], sJ = g[6 + 4 * f], tau = cpen * g[7 + 4 * f];
-          const int k = fnode_rt(N, f, j);
-          const T um = u[be * Np + k];
-          const T dnm = nr * c[k] + ns * c[Np + k];
+          const T um = u[be * Np + kf];
+          const T dnm = nr * c[kf] + ns * c[Np + kf];
           const int code = conn[3 * e + f];
           T jm = T(0), av = T(0);
           if (code >= 0) {
             const int64_t nb = code >> 2;
             const int fn = code & 3;
-            const int kn = fnode_rt(N, fn, Nfp - 1 - j);
+            const int kn = fn == 0 ? kn0 : (fn == 1 ? kn1 : kn2);
             const T* gn = gx + 16 * nb + 4 + 4 * fn;
             const T* cn = C1 + (boff + nb) * ldc;
             const T up = u[(boff + nb) * Np + kn];
@@ -421,34 +424,44 @@ __global__ void __launch_bounds__(OWARPS * 32) oz_out(int N, int64_t K, int64_t 
             av = dnm;
           }
           const T hs = T(0.5) * sJ * jm;
-          v[6] = nr * hs;
-          col[6] = 2 * Np + q;
-          v[7] = ns * hs;
-          col[7] = 2 * Np + NFN + q;
-          v[8] = -sJ * (av + tau * jm);
-          col[8] = 2 * Np + 2 * NFN + q;
+          v[4] = nr * hs;
+          v[5] = ns * hs;
+          v[6] = -sJ * (av + tau * jm);
         }
       }
+      const bool w0 = live && vol0, w1 = live && vol1, wf = live && fq;
       int emax = -1100;
       if constexpr (sizeof(T) == 8) {
-#pragma unroll
-        for (int k = 0; k < 9; ++k)
-          if (col[k] >= 0) emax = max(emax, exp_bound(v[k]));
+        if (w0) emax = max(emax, max(exp_bound(v[0]), exp_bound(v[1])));
+        if (w1) emax = max(emax, max(exp_bound(v[2]), exp_bound(v[3])));
+        if (wf) emax = max(emax, max(exp_bound(v[4]), max(exp_bound(v[5]), exp_bound(v[6]))));
         emax = __reduce_max_sync(0xffffffffu, emax);
         if (lane == 0) exs[n] = emax;
       }
-#pragma unroll
-      for (int k = 0; k < 9; ++k) {
-        if (col[k] < 0) continue;
+      uint16_t* row = Xs + size_t(n) * KP;  // slice jj of this row at row + jj * OE * KP
+      auto put = [&](T val, int colx) {
         uint16_t sl[KS];
-        pieces<KS>(v[k], emax, sl);
+        pieces<KS>(val, emax, sl);
 #pragma unroll
-        for (int jj = 0; jj < KS; ++jj) Xs[(size_t(jj) * OE + n) * KP + col[k]] = sl[jj];
+        for (int jj = 0; jj < KS; ++jj) row[size_t(jj) * OE * KP + colx] = sl[jj];
+      };
+      if (w0) {
+        put(v[0], lane);
+        put(v[1], Np + lane);
+      }
+      if (w1) {
+        put(v[2], lane + 32);
+        put(v[3], Np + lane + 32);
+      }
+      if (wf) {
+        put(v[4], 2 * Np + lane);
+        put(v[5], 2 * Np + NFN + lane);
+        put(v[6], 2 * Np + 2 * NFN + lane);
       }
       // zero padding: the columns past Kd, or the whole row past the tile's end
-      for (int k = (n < ne ? Kd : 0) + lane; k < Kt * 16; k += 32)
+      for (int k = (live ? Kd : 0) + lane; k < Kt * 16; k += 32)
 #pragma unroll
-        for (int jj = 0; jj < KS; ++jj) Xs[(size_t(jj) * OE + n) * KP + k] = 0;
+        for (int jj = 0; jj < KS; ++jj) row[size_t(jj) * OE * KP + k] = 0;
     }
     __syncthreads();
     if (lambda != T(0))  // + lambda J (M u), M u being C1's third block
