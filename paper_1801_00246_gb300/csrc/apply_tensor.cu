@@ -158,6 +158,21 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint4& a, uint32_t
       : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
 }
 
+// ldmatrix: 8x8 b16 matrices from shared memory, one 16-byte row address per
+// lane (lanes 0-7 matrix 0, 8-15 matrix 1, ...); lane (g, t) receives row g,
+// columns 2t, 2t+1 of each matrix: the B-fragment layout of mma m16n8k16 when
+// rows are elements and columns the k index.
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void* p) {
+  const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(p));
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x2(uint32_t (&r)[2], const void* p) {
+  const unsigned a = static_cast<unsigned>(__cvta_generic_to_shared(p));
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r[0]), "=r"(r[1]) : "r"(a));
+}
+
 // (double) f * 2^sc built from the float's bits (exact; f normal or zero,
 // result within the double range)
 __device__ __forceinline__ double f2d_scaled(float f, int sc) {
@@ -244,13 +259,26 @@ __device__ __forceinline__ void oz_mma_tile(const uint16_t* __restrict__ Xs, con
     float acc[NACC][4];
 #pragma unroll
     for (int s = 0; s < NACC; ++s) acc[s][0] = acc[s][1] = acc[s][2] = acc[s][3] = 0.f;
+    // ldmatrix row addresses: matrix m = lane >> 3 takes slice pair member m >> 1,
+    // k half m & 1; row = element nt * 8 + (lane & 7)
+    const int lrow = lane & 7, lmat = lane >> 3;
+    const uint16_t* xrow = Xs + (size_t(nt) * 8 + lrow) * KP + 8 * (lmat & 1);
     for (int kt = 0; kt < Kt; ++kt) {
       uint32_t b0[KS], b1[KS];
 #pragma unroll
-      for (int j = 0; j < KS; ++j) {
-        const uint16_t* col = Xs + (size_t(j) * OE + nt * 8 + g) * KP + kt * 16 + 2 * t;
-        b0[j] = *reinterpret_cast<const uint32_t*>(col);
-        b1[j] = *reinterpret_cast<const uint32_t*>(col + 8);
+      for (int j = 0; j + 1 < KS; j += 2) {
+        uint32_t r[4];
+        ldsm_x4(r, xrow + size_t(j + (lmat >> 1)) * OE * KP + kt * 16);
+        b0[j] = r[0];
+        b1[j] = r[1];
+        b0[j + 1] = r[2];
+        b1[j + 1] = r[3];
+      }
+      if (KS & 1) {  // the last slice: matrices 0 and 1 only
+        uint32_t r[2];
+        ldsm_x2(r, xrow + size_t(KS - 1) * OE * KP + kt * 16);
+        b0[KS - 1] = r[0];
+        b1[KS - 1] = r[1];
       }
 #pragma unroll
       for (int i = 0; i < KS; ++i) {
