@@ -57,7 +57,9 @@ typedef enum {
 /* DG_F64: FP64 in/out with the mesh's FP64 kernel (DG_KERNEL_* below; built-in:
  *         from degree 3 up the dense products run on the BF16 tensor cores with
  *         exact integer slicing, relative error ~1e-13 of |A||u|);
- * DG_F32: FP32 in/out, FP32 arithmetic, with the mesh's FP32 kernel;
+ * DG_F32: FP32 in/out with FP32-level accuracy (relative error <= 1e-5), with the
+ *         mesh's FP32 kernel: FP32 arithmetic, or on the tensor cores three
+ *         round-to-nearest BF16 pieces per operand with FP32 accumulation;
  * DG_F64_DFMA: FP64 in/out, the tile kernel, every operation on the FP64 pipe. */
 typedef enum { DG_F64 = 0, DG_F32 = 1, DG_F64_DFMA = 2 } dg_prec;
 
@@ -150,7 +152,11 @@ dg_status dg_helmholtz_apply(const dg_mesh* mesh, dg_prec prec, int B, double la
 dg_status dg_operator_apply(const dg_mesh* mesh, int degree, dg_prec prec, int B, double lambda,
                             const void* u, void* Au, void* stream);
 
-/* The mesh's kernel table: which DG_KERNEL_* the applies (and every solve's
+/* Kernel selection has no counterpart in the paper, which tunes its kernels
+ * per degree by hand (Section 5.2); it changes how the operator of
+ * Eq. ellipticOp3 is computed, never what.
+ *
+ * The mesh's kernel table: which DG_KERNEL_* the applies (and every solve's
  * applies) of `degree` in `prec` (DG_F64 or DG_F32), Poisson (helmholtz = 0) or
  * Helmholtz (1), use. DG_KERNEL_AUTO restores the built-in choice. A kernel
  * not available for the degree and precision is rejected (DG_ERR_ARG). Not

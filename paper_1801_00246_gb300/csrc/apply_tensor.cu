@@ -340,21 +340,20 @@ __global__ void __launch_bounds__(OWARPS * 32) oz_gemm(int64_t nE, int M, int Kd
     // the row's pieces; padding columns and rows past the tile's end are zero
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int e = warp; e < OE; e += OWARPS) {
+      // the row (Kd <= 64 entries) is read once into two registers per lane
       const T* xr = X + (e0 + e) * ldx;
+      const bool live = e < ne;
+      const T x0 = (live && lane < Kd) ? __ldg(xr + lane) : T(0);
+      const T x1 = (live && lane + 32 < Kd) ? __ldg(xr + lane + 32) : T(0);
       int emax = -1100;
-      if (sizeof(T) == 8 && e < ne) {
-        for (int k = lane; k < Kd; k += 32) emax = max(emax, exp_bound(__ldg(xr + k)));
+      if (sizeof(T) == 8 && live) {
+        emax = max(exp_bound(x0), exp_bound(x1));
         emax = __reduce_max_sync(0xffffffffu, emax);
         if (lane == 0) exs[e] = emax;
       }
       for (int k = lane; k < Kt * 16; k += 32) {
         uint16_t s[KS];
-        if (e < ne && k < Kd) {
-          pieces<KS>(__ldg(xr + k), emax, s);
-        } else {
-#pragma unroll
-          for (int j = 0; j < KS; ++j) s[j] = 0;
-        }
+        pieces<KS>(k < 32 ? x0 : x1, emax, s);  // zero (and padding) slices to zero
 #pragma unroll
         for (int j = 0; j < KS; ++j) Xs[(size_t(j) * OE + e) * KP + k] = s[j];
       }
@@ -593,6 +592,7 @@ cudaError_t launch_gemm(int64_t nE, int M, int Kd, int Mt, int Kt, const uint4* 
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, OTHREADS, smem);
   if (e != cudaSuccess) return e;
+  if (!fa && Kd > 64) return cudaErrorInvalidValue;  // the plain product holds a row in two registers per lane
   const int64_t tiles = (nE + OE - 1) / OE;
   int64_t grid = int64_t(sms) * (per > 0 ? per : 1);
   if (grid > tiles) grid = tiles;
