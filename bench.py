@@ -421,7 +421,8 @@ def run_sweep(args):
     flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     degrees = [int(d) for d in args.sweep_degrees.split(",")]
     batches = [int(b) for b in args.sweep_batches.split(",")]
-    names = {P.KERNEL_TILE: "tile", P.KERNEL_GEMM: "gemm", P.KERNEL_TENSOR: "tensor", P.KERNEL_EPT: "ept"}
+    names = {P.KERNEL_TILE: "tile", P.KERNEL_GEMM: "gemm", P.KERNEL_TENSOR: "tensor", P.KERNEL_EPT: "ept",
+             P.KERNEL_TENSOR_PIPE: "tensor_pipe"}
     for N in degrees:
         mesh = P.Mesh.from_inputs(m, N)
         K, Np = mesh.K, mesh.Np
@@ -432,7 +433,7 @@ def run_sweep(args):
             for lam in (0.0, 1.0):
                 for key, prec, u, o in (("f64", P.DG_F64, u64, o64), ("f32", P.DG_F32, u32, o32)):
                     default = mesh.kernel(N, prec, lam != 0.0)
-                    ks = [P.KERNEL_TILE, P.KERNEL_TENSOR] + ([] if key == "f64" else [P.KERNEL_GEMM])
+                    ks = [P.KERNEL_TILE, P.KERNEL_TENSOR, P.KERNEL_TENSOR_PIPE] + ([] if key == "f64" else [P.KERNEL_GEMM])
                     if N <= 3:
                         ks.append(P.KERNEL_EPT)
                     for k in ks:

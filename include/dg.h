@@ -74,8 +74,12 @@ typedef struct dg_mesh dg_mesh; /* opaque; owned by the library until dg_mesh_de
  *   DG_KERNEL_GEMM:   FP32 only: register-blocked small GEMMs over element tiles; all degrees
  *   DG_KERNEL_TENSOR: dense products on the BF16 tensor cores with exact integer
  *                     slicing (FP64: 8 slices, FP32: 3 slices); all degrees
- *   DG_KERNEL_EPT:    one element per thread, operators in constant memory; degrees 1-3 */
-enum { DG_KERNEL_AUTO = 0, DG_KERNEL_TILE = 1, DG_KERNEL_GEMM = 2, DG_KERNEL_TENSOR = 3, DG_KERNEL_EPT = 4 };
+ *   DG_KERNEL_EPT:    one element per thread, operators in constant memory; degrees 1-3
+ *   DG_KERNEL_TENSOR_PIPE: DG_KERNEL_TENSOR with the output product's fill and product
+ *                     phases on separate warps, double-buffered through shared memory
+ *                     (mbarrier hand-off with bounded waits; see dg_tensor_timeouts) */
+enum { DG_KERNEL_AUTO = 0, DG_KERNEL_TILE = 1, DG_KERNEL_GEMM = 2, DG_KERNEL_TENSOR = 3, DG_KERNEL_EPT = 4,
+       DG_KERNEL_TENSOR_PIPE = 5 };
 
 /* Preconditioner choices for dg_pcg_solve (Section 3). */
 enum { DG_PREC_NONE = 0, DG_PREC_JACOBI = 1, DG_PREC_INVMASS = 2, DG_PREC_PMG = 3 };
@@ -170,7 +174,7 @@ int dg_get_apply_kernel(const dg_mesh* mesh, int degree, dg_prec prec, int helmh
  * (256 MB L2 flush before each of three timed launches, best kept), for the
  * Poisson form and, if lambda > 0, the Helmholtz form (with lambda = 0 the
  * Helmholtz entry takes the Poisson winner), and stores the fastest in the
- * kernel table. times (host, may be NULL): float[9][2][2][5] milliseconds
+ * kernel table. times (host, may be NULL): float[9][2][2][6] milliseconds
  * indexed [degree][0: FP64, 1: FP32][helmholtz][kernel], 0 where not timed.
  * Allocates and frees its own scratch (4 fields of B*K*Np(degree_hi) values
  * plus 256 MB); synchronises `stream`. Solves captured as CUDA graphs before
@@ -274,6 +278,12 @@ dg_status dg_reference_operators(int N, double* r, double* s, double* M, double*
  * (Nf > Nc >= 1): P[Np(Nf)][Np(Nc)] row-major, the coarse nodal basis
  * evaluated at the fine nodes. */
 dg_status dg_interpolation_matrix(int Nf, int Nc, double* P);
+
+/* Waits of the pipelined tensor kernel that gave up (a broken producer/consumer
+ * hand-off: the affected apply's output is invalid) since the last call, summed
+ * over the current device; reading clears it. Synchronises the device. Returns
+ * -1 if the device could not be queried. No counterpart in the paper. */
+int dg_tensor_timeouts(void);
 
 /* Number of kernels this library has launched since it was loaded (all
  * devices and threads); a diagnostic for counting launches in a timed region. */

@@ -393,6 +393,7 @@ bool kernel_valid(int kernel, int degree, bool f64) {
     case DG_KERNEL_TILE: return true;
     case DG_KERNEL_GEMM: return !f64;
     case DG_KERNEL_TENSOR: return true;
+    case DG_KERNEL_TENSOR_PIPE: return true;
     case DG_KERNEL_EPT: return ept_supported(degree);
     default: return false;
   }
@@ -413,7 +414,8 @@ cudaError_t launch_apply(const dg_mesh* mc, int degree, dg_prec prec, int B, dou
   const bool f64 = prec == DG_F64;
   if (!kernel_valid(k, degree, f64)) return cudaErrorInvalidValue;
   if (k == DG_KERNEL_EPT) return launch_apply_ept(m, degree, f64, B, lambda, u, Au, st);
-  if (k == DG_KERNEL_TENSOR) return launch_apply_tensor(m, degree, f64, B, lambda, u, Au, st);
+  if (k == DG_KERNEL_TENSOR || k == DG_KERNEL_TENSOR_PIPE)
+    return launch_apply_tensor(m, degree, f64, B, lambda, u, Au, k == DG_KERNEL_TENSOR_PIPE, st);
   if (k == DG_KERNEL_GEMM) {
     const int dmax = degree > m->N ? degree : m->N;
     const size_t need = size_t(B) * size_t(m->K) * 3 * size_t(dmax + 1);

@@ -378,6 +378,132 @@ __device__ __forceinline__ int fnode_rt(int N, int f, int j) {
 // form C1 carries a third block M u (rows 2Np..3Np of the first product) and
 // the epilogue adds lambda J (M u), which keeps the output product as narrow as
 // the Poisson one.
+// Per-lane constants of the fused fill (the same for every element): volume
+// nodes lane and lane + 32, face node q = lane (face f, position jf, local node
+// kf), and the neighbour's matching node for each of its three possible faces.
+struct LaneNodes {
+  bool vol0, vol1, fq;
+  int f, jf, kf, kn0, kn1, kn2;
+};
+__device__ __forceinline__ LaneNodes lane_nodes(int N, int lane) {
+  const int Np = (N + 1) * (N + 2) / 2, Nfp = N + 1, NFN = 3 * Nfp;
+  LaneNodes L;
+  L.vol0 = lane < Np;
+  L.vol1 = lane + 32 < Np;
+  L.fq = lane < NFN;
+  L.f = L.fq ? lane / Nfp : 0;
+  L.jf = L.fq ? lane - L.f * Nfp : 0;
+  L.kf = fnode_rt(N, L.f, L.jf);
+  L.kn0 = fnode_rt(N, 0, Nfp - 1 - L.jf);
+  L.kn1 = fnode_rt(N, 1, Nfp - 1 - L.jf);
+  L.kn2 = fnode_rt(N, 2, Nfp - 1 - L.jf);
+  return L;
+}
+
+// The fused fill of one tile by the warps fw, fw + nfw, ... (one element row
+// per warp at a time): the Y row of element n (columns: wr, ws (Np each) |
+// 1/2 nr sJ [u], 1/2 ns sJ [u] (NFN each) | -sJ ({n.grad u} + tau [u]) (NFN))
+// from C1, u, the geometry gx (16 words per element: J, Grr, Grs, Gss | per
+// face nr, ns, sJ, ihmax) and the neighbours' C1 and u rows; the row's scale
+// exponent as a warp maximum (FP64); the slices into Xs; lambda J into addsc.
+template <typename T>
+__device__ __forceinline__ void oz_fill(int fw, int nfw, int lane, const LaneNodes& Ln, int N, int64_t K, int Kd,
+                                        int Kt, int KP, int64_t e0, int ne, const T* __restrict__ gx,
+                                        const int32_t* __restrict__ conn, const T* __restrict__ u,
+                                        const T* __restrict__ C1, int ldc, T lambda, uint16_t* Xs, int* exs,
+                                        T* addsc) {
+  constexpr int KS = Slices<T>::KS;
+  const int Np = (N + 1) * (N + 2) / 2, Nfp = N + 1, NFN = 3 * Nfp;
+  const T cpen = T((N + 1) * (N + 2)) / T(2);
+  const bool vol0 = Ln.vol0, vol1 = Ln.vol1, fq = Ln.fq;
+  const int f = Ln.f, kf = Ln.kf, kn0 = Ln.kn0, kn1 = Ln.kn1, kn2 = Ln.kn2;
+  (void)Nfp;
+  for (int n = fw; n < OE; n += nfw) {
+    // slots: 0-1 (wr, ws) at node lane, 2-3 at node lane + 32, 4-6 at face node lane
+    T v[7];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) v[k] = T(0);
+    const bool live = n < ne;
+    if (live) {
+      const int64_t be = e0 + n;
+      const int64_t e = be < K ? be : be % K;  // first right-hand side: no division
+      const int64_t boff = be - e;
+      const T* g = gx + 16 * e;
+      const T* c = C1 + be * ldc;
+      if (lane == 0) addsc[n] = lambda * g[0];
+      const T g1 = g[1], g2 = g[2], g3 = g[3];
+      if (vol0) {
+        const T ur = c[lane], us = c[Np + lane];
+        v[0] = g1 * ur + g2 * us;
+        v[1] = g2 * ur + g3 * us;
+      }
+      if (vol1) {
+        const T ur = c[lane + 32], us = c[Np + lane + 32];
+        v[2] = g1 * ur + g2 * us;
+        v[3] = g2 * ur + g3 * us;
+      }
+      if (fq) {
+        const T nr = g[4 + 4 * f], ns = g[5 + 4 * f], sJ = g[6 + 4 * f], tau = cpen * g[7 + 4 * f];
+        const T um = u[be * Np + kf];
+        const T dnm = nr * c[kf] + ns * c[Np + kf];
+        const int code = conn[3 * e + f];
+        T jm = T(0), av = T(0);
+        if (code >= 0) {
+          const int64_t nb = code >> 2;
+          const int fn = code & 3;
+          const int kn = fn == 0 ? kn0 : (fn == 1 ? kn1 : kn2);
+          const T* gn = gx + 16 * nb + 4 + 4 * fn;
+          const T* cn = C1 + (boff + nb) * ldc;
+          const T up = u[(boff + nb) * Np + kn];
+          const T dnp = gn[0] * cn[kn] + gn[1] * cn[Np + kn];
+          jm = up - um;
+          av = T(0.5) * (dnm - dnp);
+        } else if (code == -2) {
+          jm = T(-2) * um;
+          av = dnm;
+        }
+        const T hs = T(0.5) * sJ * jm;
+        v[4] = nr * hs;
+        v[5] = ns * hs;
+        v[6] = -sJ * (av + tau * jm);
+      }
+    }
+    const bool w0 = live && vol0, w1 = live && vol1, wf = live && fq;
+    int emax = -1100;
+    if constexpr (sizeof(T) == 8) {
+      if (w0) emax = max(emax, max(exp_bound(v[0]), exp_bound(v[1])));
+      if (w1) emax = max(emax, max(exp_bound(v[2]), exp_bound(v[3])));
+      if (wf) emax = max(emax, max(exp_bound(v[4]), max(exp_bound(v[5]), exp_bound(v[6]))));
+      emax = __reduce_max_sync(0xffffffffu, emax);
+      if (lane == 0) exs[n] = emax;
+    }
+    uint16_t* row = Xs + size_t(n) * KP;  // slice jj of this row at row + jj * OE * KP
+    auto put = [&](T val, int colx) {
+      uint16_t sl[KS];
+      pieces<KS>(val, emax, sl);
+#pragma unroll
+      for (int jj = 0; jj < KS; ++jj) row[size_t(jj) * OE * KP + colx] = sl[jj];
+    };
+    if (w0) {
+      put(v[0], lane);
+      put(v[1], Np + lane);
+    }
+    if (w1) {
+      put(v[2], lane + 32);
+      put(v[3], Np + lane + 32);
+    }
+    if (wf) {
+      put(v[4], 2 * Np + lane);
+      put(v[5], 2 * Np + NFN + lane);
+      put(v[6], 2 * Np + 2 * NFN + lane);
+    }
+    // zero padding: the columns past Kd, or the whole row past the tile's end
+    for (int k = (live ? Kd : 0) + lane; k < Kt * 16; k += 32)
+#pragma unroll
+      for (int jj = 0; jj < KS; ++jj) row[size_t(jj) * OE * KP + k] = 0;
+  }
+}
+
 template <int MAXF, int OWARPS, typename T>
 __global__ void __launch_bounds__(OWARPS * 32) oz_out(int N, int64_t K, int64_t nE, int Kd, int Mt, int Kt,
                                                    const T* __restrict__ gx, const int32_t* __restrict__ conn,
@@ -391,110 +517,118 @@ __global__ void __launch_bounds__(OWARPS * 32) oz_out(int N, int64_t K, int64_t 
   int* exs = reinterpret_cast<int*>(osm + size_t(KS) * OE * KP);
   T* addsc = reinterpret_cast<T*>(exs + OE);  // [OE]: lambda J per element (Helmholtz)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int Np = (N + 1) * (N + 2) / 2, Nfp = N + 1, NFN = 3 * Nfp;
-  const T cpen = T((N + 1) * (N + 2)) / T(2);
-  // per-lane constants (the same for every element): volume nodes lane and
-  // lane + 32, face node q = lane (face f, position j, local node k), and the
-  // neighbour's matching node for each of its three possible faces
-  const bool vol0 = lane < Np, vol1 = lane + 32 < Np, fq = lane < NFN;
-  const int f = fq ? lane / Nfp : 0, jf = fq ? lane - f * Nfp : 0;
-  const int kf = fnode_rt(N, f, jf);
-  const int kn0 = fnode_rt(N, 0, Nfp - 1 - jf), kn1 = fnode_rt(N, 1, Nfp - 1 - jf),
-            kn2 = fnode_rt(N, 2, Nfp - 1 - jf);
+  const int Np = (N + 1) * (N + 2) / 2;
+  const LaneNodes Ln = lane_nodes(N, lane);
   const int64_t ntiles = (nE + OE - 1) / OE;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t e0 = tile * OE;
     const int ne = int((nE - e0) < OE ? (nE - e0) : OE);
     __syncthreads();
-    for (int n = warp; n < OE; n += OWARPS) {
-      // slots: 0-1 (wr, ws) at node lane, 2-3 at node lane + 32, 4-6 at face node lane
-      T v[7];
-#pragma unroll
-      for (int k = 0; k < 7; ++k) v[k] = T(0);
-      const bool live = n < ne;
-      if (live) {
-        const int64_t be = e0 + n;
-        const int64_t e = be < K ? be : be % K;  // first right-hand side: no division
-        const int64_t boff = be - e;
-        const T* g = gx + 16 * e;
-        const T* c = C1 + be * ldc;
-        if (lane == 0) addsc[n] = lambda * g[0];
-        const T g1 = g[1], g2 = g[2], g3 = g[3];
-        if (vol0) {
-          const T ur = c[lane], us = c[Np + lane];
-          v[0] = g1 * ur + g2 * us;
-          v[1] = g2 * ur + g3 * us;
-        }
-        if (vol1) {
-          const T ur = c[lane + 32], us = c[Np + lane + 32];
-          v[2] = g1 * ur + g2 * us;
-          v[3] = g2 * ur + g3 * us;
-        }
-        if (fq) {
-          const T nr = g[4 + 4 * f], ns = g[5 + 4 * f], sJ = g[6 + 4 * f], tau = cpen * g[7 + 4 * f];
-          const T um = u[be * Np + kf];
-          const T dnm = nr * c[kf] + ns * c[Np + kf];
-          const int code = conn[3 * e + f];
-          T jm = T(0), av = T(0);
-          if (code >= 0) {
-            const int64_t nb = code >> 2;
-            const int fn = code & 3;
-            const int kn = fn == 0 ? kn0 : (fn == 1 ? kn1 : kn2);
-            const T* gn = gx + 16 * nb + 4 + 4 * fn;
-            const T* cn = C1 + (boff + nb) * ldc;
-            const T up = u[(boff + nb) * Np + kn];
-            const T dnp = gn[0] * cn[kn] + gn[1] * cn[Np + kn];
-            jm = up - um;
-            av = T(0.5) * (dnm - dnp);
-          } else if (code == -2) {
-            jm = T(-2) * um;
-            av = dnm;
-          }
-          const T hs = T(0.5) * sJ * jm;
-          v[4] = nr * hs;
-          v[5] = ns * hs;
-          v[6] = -sJ * (av + tau * jm);
-        }
-      }
-      const bool w0 = live && vol0, w1 = live && vol1, wf = live && fq;
-      int emax = -1100;
-      if constexpr (sizeof(T) == 8) {
-        if (w0) emax = max(emax, max(exp_bound(v[0]), exp_bound(v[1])));
-        if (w1) emax = max(emax, max(exp_bound(v[2]), exp_bound(v[3])));
-        if (wf) emax = max(emax, max(exp_bound(v[4]), max(exp_bound(v[5]), exp_bound(v[6]))));
-        emax = __reduce_max_sync(0xffffffffu, emax);
-        if (lane == 0) exs[n] = emax;
-      }
-      uint16_t* row = Xs + size_t(n) * KP;  // slice jj of this row at row + jj * OE * KP
-      auto put = [&](T val, int colx) {
-        uint16_t sl[KS];
-        pieces<KS>(val, emax, sl);
-#pragma unroll
-        for (int jj = 0; jj < KS; ++jj) row[size_t(jj) * OE * KP + colx] = sl[jj];
-      };
-      if (w0) {
-        put(v[0], lane);
-        put(v[1], Np + lane);
-      }
-      if (w1) {
-        put(v[2], lane + 32);
-        put(v[3], Np + lane + 32);
-      }
-      if (wf) {
-        put(v[4], 2 * Np + lane);
-        put(v[5], 2 * Np + NFN + lane);
-        put(v[6], 2 * Np + 2 * NFN + lane);
-      }
-      // zero padding: the columns past Kd, or the whole row past the tile's end
-      for (int k = (live ? Kd : 0) + lane; k < Kt * 16; k += 32)
-#pragma unroll
-        for (int jj = 0; jj < KS; ++jj) row[size_t(jj) * OE * KP + k] = 0;
-    }
+    oz_fill<T>(warp, OWARPS, lane, Ln, N, K, Kd, Kt, KP, e0, ne, gx, conn, u, C1, ldc, lambda, Xs, exs, addsc);
     __syncthreads();
     if (lambda != T(0))  // + lambda J (M u), M u being C1's third block
       oz_mma_tile<MAXF, OWARPS, T>(Xs, exs, KP, Np, Mt, Kt, ne, e0, Af, ea, out, Np, C1 + 2 * Np, ldc, addsc);
     else
       oz_mma_tile<MAXF, OWARPS, T>(Xs, exs, KP, Np, Mt, Kt, ne, e0, Af, ea, out, Np);
+  }
+}
+
+// ------------------------------------------------ pipelined output product
+// The same output product with its fill and product phases on separate warps:
+// 8 producer warps fill tile i + 1 into one of two shared-memory stages while
+// 8 consumer warps run the products and epilogue of tile i from the other.
+// The hand-off uses two mbarriers per stage (full: all 256 producer threads
+// arrive after writing; empty: all 256 consumer threads arrive after reading),
+// waited on by phase parity. Every wait gives up after a fixed number of
+// polls, sets g_tensor_err and leaves the loop, so a broken hand-off ends the
+// kernel with an error flag instead of hanging it.
+__device__ int g_tensor_err;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Warp-collective: true once the phase of barrier b with the given parity has
+// completed (seen by every lane), false after kPollCap polls (each poll may
+// suspend the thread briefly). The vote keeps the warp converged, so the
+// aligned ldmatrix / mma / shuffle instructions that follow see all 32 lanes,
+// and a timeout leaves the loop with the whole warp.
+constexpr int kPollCap = 1 << 22;
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity) {
+  for (int it = 0; it < kPollCap; ++it)
+    if (__all_sync(0xffffffffu, mbar_try_wait(b, parity))) return true;
+  return false;
+}
+
+template <int MAXF, typename T>
+__global__ void __launch_bounds__(512, 1) oz_out_pipe(int N, int64_t K, int64_t nE, int Kd, int Mt, int Kt,
+                                                   const T* __restrict__ gx, const int32_t* __restrict__ conn,
+                                                   const T* __restrict__ u, const T* __restrict__ C1, int ldc,
+                                                   T lambda, const uint4* __restrict__ Af,
+                                                   const int* __restrict__ ea, T* __restrict__ out) {
+  constexpr int KS = Slices<T>::KS;
+  constexpr int NW = 8;  // warps per role
+  extern __shared__ __align__(16) uint16_t osm[];
+  const int KP = Kt * 16 + 8;
+  const size_t stage = size_t(KS) * OE * KP;  // bf16 words of one stage's slices
+  int* exs_all = reinterpret_cast<int*>(osm + 2 * stage);  // [2][OE]
+  T* addsc_all = reinterpret_cast<T*>(exs_all + 2 * OE);   // [2][OE]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(addsc_all + 2 * OE);  // full[2], empty[2]
+  if (threadIdx.x == 0) {
+    mbar_init(bar + 0, NW * 32);
+    mbar_init(bar + 1, NW * 32);
+    mbar_init(bar + 2, NW * 32);
+    mbar_init(bar + 3, NW * 32);
+  }
+  __syncthreads();  // the only CTA-wide barrier: before the roles split
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool producer = warp >= NW;
+  const int Np = (N + 1) * (N + 2) / 2;
+  const LaneNodes Ln = lane_nodes(N, lane);
+  const int64_t ntiles = (nE + OE - 1) / OE;
+  unsigned use = 0;  // tile counter of this CTA: stage = use & 1, round = use >> 1
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++use) {
+    const int s = int(use & 1u);
+    const unsigned parity = (use >> 1) & 1u;
+    uint16_t* Xs = osm + s * stage;
+    int* exs = exs_all + s * OE;
+    T* addsc = addsc_all + s * OE;
+    const int64_t e0 = tile * OE;
+    const int ne = int((nE - e0) < OE ? (nE - e0) : OE);
+    if (producer) {
+      // the stage is free once the consumers released its previous round
+      // (the first round waits on the already-complete parity, i.e. not at all)
+      if (!mbar_wait(bar + 2 + s, parity ^ 1u)) {
+        atomicExch(&g_tensor_err, 1);
+        break;
+      }
+      oz_fill<T>(warp - NW, NW, lane, Ln, N, K, Kd, Kt, KP, e0, ne, gx, conn, u, C1, ldc, lambda, Xs, exs, addsc);
+      mbar_arrive(bar + s);
+    } else {
+      if (!mbar_wait(bar + s, parity)) {
+        atomicExch(&g_tensor_err, 1);
+        break;
+      }
+      if (lambda != T(0))
+        oz_mma_tile<MAXF, NW, T>(Xs, exs, KP, Np, Mt, Kt, ne, e0, Af, ea, out, Np, C1 + 2 * Np, ldc, addsc);
+      else
+        oz_mma_tile<MAXF, NW, T>(Xs, exs, KP, Np, Mt, Kt, ne, e0, Af, ea, out, Np);
+      mbar_arrive(bar + 2 + s);
+    }
   }
 }
 
@@ -627,10 +761,51 @@ cudaError_t gemm(int Mt, int64_t nE, int M, int Kd, int Kt, const uint4* Af, con
   return cudaErrorInvalidValue;  // more fragments than any instantiation covers
 }
 
+template <int MAXF, typename T>
+cudaError_t launch_pipe(int64_t nE, int Kd, int Mt, int Kt, const uint4* Af, const int* ea, T* out,
+                        const FusedArgs<T>& fa, cudaStream_t st) {
+  const size_t smem = 2 * (size_t(Slices<T>::KS) * OE * (Kt * 16 + 8) * sizeof(uint16_t) + OE * sizeof(int) +
+                           OE * sizeof(T)) + 4 * sizeof(uint64_t);
+  static size_t configured[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (configured[dev & 63] < smem) {
+    e = cudaFuncSetAttribute(oz_out_pipe<MAXF, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    configured[dev & 63] = smem;
+  }
+  int sms = 0, per = 0;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, oz_out_pipe<MAXF, T>, 512, smem);
+  if (e != cudaSuccess) return e;
+  if (per < 1) return cudaErrorInvalidConfiguration;  // the two stages do not fit
+  const int64_t tiles = (nE + OE - 1) / OE;
+  int64_t grid = int64_t(sms) * per;
+  if (grid > tiles) grid = tiles;
+  oz_out_pipe<MAXF, T><<<unsigned(grid), 512, smem, st>>>(fa.N, fa.K, nE, Kd, Mt, Kt, fa.gx, fa.conn, fa.u, fa.C1,
+                                                          fa.ldc, fa.lambda, Af, ea, out);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// the pipelined output product: 8 consumer warps cover every fragment
+template <typename T>
+cudaError_t gemm_pipe(int Mt, int64_t nE, int Kd, int Kt, const uint4* Af, const int* ea, T* out,
+                      const FusedArgs<T>& fa, cudaStream_t st) {
+  switch ((Mt * ONT + 7) / 8) {
+    case 1: return launch_pipe<1, T>(nE, Kd, Mt, Kt, Af, ea, out, fa, st);
+    case 2: return launch_pipe<2, T>(nE, Kd, Mt, Kt, Af, ea, out, fa, st);
+    case 3: return launch_pipe<3, T>(nE, Kd, Mt, Kt, Af, ea, out, fa, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 OzOps g_oz[2][64][kMaxN + 1];  // [0: FP64, 1: FP32][device][degree]
 
 template <typename T>
-cudaError_t apply_tensor(dg_mesh* m, int degree, int B, double lambda, const T* u, T* Au, cudaStream_t st) {
+cudaError_t apply_tensor(dg_mesh* m, int degree, int B, double lambda, const T* u, T* Au, bool pipe,
+                         cudaStream_t st) {
   constexpr bool f64 = sizeof(T) == 8;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -663,16 +838,26 @@ cudaError_t apply_tensor(dg_mesh* m, int degree, int B, double lambda, const T* 
   else e = gemm<T>(o.Mt1, nE, 2 * Np, Np, o.Kt1, o.A1, o.ea1, u, Np, C1, ldc, nullptr, st);
   if (e != cudaSuccess) return e;
   const FusedArgs<T> fa{N, m->K, gx, m->conn, u, C1, ldc, T(lambda)};
+  if (pipe) return gemm_pipe<T>(o.Mt2, nE, KY, o.Kt2, o.A2, o.ea2, Au, fa, st);
   return gemm<T>(o.Mt2, nE, Np, KY, o.Kt2, o.A2, o.ea2, nullptr, 0, Au, Np, &fa, st);
 }
 
 }  // namespace
 
 cudaError_t launch_apply_tensor(dg_mesh* m, int degree, bool f64, int B, double lambda, const void* u, void* Au,
-                                cudaStream_t st) {
+                                bool pipe, cudaStream_t st) {
   if (f64)
-    return apply_tensor<double>(m, degree, B, lambda, static_cast<const double*>(u), static_cast<double*>(Au), st);
-  return apply_tensor<float>(m, degree, B, lambda, static_cast<const float*>(u), static_cast<float*>(Au), st);
+    return apply_tensor<double>(m, degree, B, lambda, static_cast<const double*>(u), static_cast<double*>(Au), pipe,
+                                st);
+  return apply_tensor<float>(m, degree, B, lambda, static_cast<const float*>(u), static_cast<float*>(Au), pipe, st);
+}
+
+// Reads and clears the pipelined kernels' timeout flag (synchronises the device).
+cudaError_t tensor_pipe_error(int* flag) {
+  int zero = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(flag, g_tensor_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_tensor_err, &zero, sizeof(int));
+  return e;
 }
 
 }  // namespace dgx

@@ -27,7 +27,7 @@ __global__ void k_fill_uniform(int64_t n, uint64_t seed, double* __restrict__ a,
   }
 }
 
-constexpr int kCandidates[] = {DG_KERNEL_TILE, DG_KERNEL_GEMM, DG_KERNEL_TENSOR, DG_KERNEL_EPT};
+constexpr int kCandidates[] = {DG_KERNEL_TILE, DG_KERNEL_GEMM, DG_KERNEL_TENSOR, DG_KERNEL_EPT, DG_KERNEL_TENSOR_PIPE};
 
 struct Scratch {
   void* p[5] = {};
@@ -57,6 +57,11 @@ dg_status dg_set_apply_kernel(dg_mesh* m, int degree, dg_prec prec, int helmholt
   return DG_OK;
 }
 
+int dg_tensor_timeouts(void) {
+  int flag = 0;
+  return tensor_pipe_error(&flag) == cudaSuccess ? flag : -1;
+}
+
 int dg_get_apply_kernel(const dg_mesh* m, int degree, dg_prec prec, int helmholtz) {
   if (!m || degree < 1 || degree > kMaxN || (prec != DG_F64 && prec != DG_F32)) return -1;
   const int k = m->kern[degree][prec == DG_F32 ? 1 : 0][helmholtz ? 1 : 0];
@@ -71,7 +76,7 @@ dg_status dg_autotune(dg_mesh* m, int B, double lambda, int degree_lo, int degre
     return DG_ERR_ARG;
   }
   if (!std::isfinite(lambda) || lambda < 0) { set_error("lambda must be finite and >= 0"); return DG_ERR_ARG; }
-  if (times) std::memset(times, 0, sizeof(float) * (kMaxN + 1) * 2 * 2 * 5);
+  if (times) std::memset(times, 0, sizeof(float) * (kMaxN + 1) * 2 * 2 * 6);
   cudaStream_t st = (cudaStream_t)stream;
   auto fail = [](cudaError_t e) {
     set_error(std::string("dg_autotune: ") + cudaGetErrorString(e));
@@ -120,7 +125,7 @@ dg_status dg_autotune(dg_mesh* m, int B, double lambda, int degree_lo, int degre
               if (e == cudaSuccess && ms < ms_min) ms_min = ms;
             }
             if (e != cudaSuccess) break;
-            if (times) times[((d * 2 + p) * 2 + h) * 5 + k] = ms_min;
+            if (times) times[((d * 2 + p) * 2 + h) * 6 + k] = ms_min;
             if (ms_min < best_ms) {
               best_ms = ms_min;
               best = k;

@@ -122,7 +122,8 @@ bool ept_supported(int degree);
 cudaError_t launch_apply_ept(dg_mesh* m, int degree, bool f64, int B, double lambda, const void* u, void* Au,
                              cudaStream_t st);
 cudaError_t launch_apply_tensor(dg_mesh* m, int degree, bool f64, int B, double lambda, const void* u, void* Au,
-                                cudaStream_t st);
+                                bool pipe, cudaStream_t st);
+cudaError_t tensor_pipe_error(int* flag);
 cudaError_t launch_nodes(const dg_mesh* m, int degree, double* x, double* y, cudaStream_t st);
 
 void set_error(const std::string& msg);

@@ -15,7 +15,7 @@ TOL64, TOL32 = 1e-12, 1e-5
 
 
 def _kernels(P, N, f64):
-    ks = [P.KERNEL_TILE, P.KERNEL_TENSOR] + ([] if f64 else [P.KERNEL_GEMM])
+    ks = [P.KERNEL_TILE, P.KERNEL_TENSOR, P.KERNEL_TENSOR_PIPE] + ([] if f64 else [P.KERNEL_GEMM])
     if N <= 3:
         ks.append(P.KERNEL_EPT)
     return ks
@@ -42,6 +42,7 @@ def test_every_kernel_matches_oracle(N):
                     assert lib.kernel(N, prec, lam != 0.0) == k
                     x = cuda(u) if f64 else cuda(u, torch.float32)
                     got = lib.apply(x, lam=lam).cpu().numpy()
+                    assert P.lib().dg_tensor_timeouts() == 0  # no pipelined hand-off gave up
                     assert np.isfinite(got).all()
                     assert rel(got, ref) <= (TOL64 if f64 else TOL32), (N, f64, k, lam)
                 lib.set_kernel(N, prec, lam != 0.0, P.KERNEL_AUTO)
