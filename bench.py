@@ -523,7 +523,10 @@ def run_ins(args):
                       vel_opts=P._binding.default_opts(**o), pr_opts=P._binding.default_opts(**o))
     st.step(args.warmup)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("ins_steps")
     out = st.step(args.steps)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     err = float((st.U - U0).abs().max())
     print(json.dumps({"ins": True, "workload": "64x64 Kovasznay, 8192 triangles, N=8, dt=0.01, 32 substeps",
                       "steps": args.steps, "ms_per_step": out["ms"] / args.steps, "vel_iters": out["vel_iters"],

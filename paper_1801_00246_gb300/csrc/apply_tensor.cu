@@ -340,22 +340,38 @@ __global__ void __launch_bounds__(OWARPS * 32) oz_gemm(int64_t nE, int M, int Kd
     // the row's pieces; padding columns and rows past the tile's end are zero
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int e = warp; e < OE; e += OWARPS) {
-      // the row (Kd <= 64 entries) is read once into two registers per lane
       const T* xr = X + (e0 + e) * ldx;
       const bool live = e < ne;
-      const T x0 = (live && lane < Kd) ? __ldg(xr + lane) : T(0);
-      const T x1 = (live && lane + 32 < Kd) ? __ldg(xr + lane + 32) : T(0);
-      int emax = -1100;
-      if (sizeof(T) == 8 && live) {
-        emax = max(exp_bound(x0), exp_bound(x1));
-        emax = __reduce_max_sync(0xffffffffu, emax);
-        if (lane == 0) exs[e] = emax;
-      }
-      for (int k = lane; k < Kt * 16; k += 32) {
-        uint16_t s[KS];
-        pieces<KS>(k < 32 ? x0 : x1, emax, s);  // zero (and padding) slices to zero
+      if (Kd <= 64) {
+        // the row is read once into two registers per lane
+        const T x0 = (live && lane < Kd) ? __ldg(xr + lane) : T(0);
+        const T x1 = (live && lane + 32 < Kd) ? __ldg(xr + lane + 32) : T(0);
+        int emax = -1100;
+        if (sizeof(T) == 8 && live) {
+          emax = max(exp_bound(x0), exp_bound(x1));
+          emax = __reduce_max_sync(0xffffffffu, emax);
+          if (lane == 0) exs[e] = emax;
+        }
+        for (int k = lane; k < Kt * 16; k += 32) {
+          uint16_t s[KS];
+          pieces<KS>(k < 32 ? x0 : x1, emax, s);  // zero (and padding) slices to zero
 #pragma unroll
-        for (int j = 0; j < KS; ++j) Xs[(size_t(j) * OE + e) * KP + k] = s[j];
+          for (int j = 0; j < KS; ++j) Xs[(size_t(j) * OE + e) * KP + k] = s[j];
+        }
+      } else {
+        // long rows: a pass for the exponent, a pass for the slices
+        int emax = -1100;
+        if (sizeof(T) == 8 && live) {
+          for (int k = lane; k < Kd; k += 32) emax = max(emax, exp_bound(__ldg(xr + k)));
+          emax = __reduce_max_sync(0xffffffffu, emax);
+          if (lane == 0) exs[e] = emax;
+        }
+        for (int k = lane; k < Kt * 16; k += 32) {
+          uint16_t s[KS];
+          pieces<KS>((live && k < Kd) ? __ldg(xr + k) : T(0), emax, s);
+#pragma unroll
+          for (int j = 0; j < KS; ++j) Xs[(size_t(j) * OE + e) * KP + k] = s[j];
+        }
       }
     }
     __syncthreads();
@@ -726,7 +742,6 @@ cudaError_t launch_gemm(int64_t nE, int M, int Kd, int Mt, int Kt, const uint4* 
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, OTHREADS, smem);
   if (e != cudaSuccess) return e;
-  if (!fa && Kd > 64) return cudaErrorInvalidValue;  // the plain product holds a row in two registers per lane
   const int64_t tiles = (nE + OE - 1) / OE;
   int64_t grid = int64_t(sms) * (per > 0 ? per : 1);
   if (grid > tiles) grid = tiles;
@@ -755,6 +770,7 @@ cudaError_t gemm(int Mt, int64_t nE, int M, int Kd, int Kt, const uint4* Af, con
     case 3: OZ_L(3);
     case 4: OZ_L(4);
     case 5: OZ_L(5);
+    case 6: OZ_L(6);
     default: break;
   }
 #undef OZ_L
@@ -850,6 +866,35 @@ cudaError_t launch_apply_tensor(dg_mesh* m, int degree, bool f64, int B, double 
     return apply_tensor<double>(m, degree, B, lambda, static_cast<const double*>(u), static_cast<double*>(Au), pipe,
                                 st);
   return apply_tensor<float>(m, degree, B, lambda, static_cast<const float*>(u), static_cast<float*>(Au), pipe, st);
+}
+
+// A general FP64 operator for batched row products out[r] = A X[r] (the
+// advection's cubature interpolation and projection): sliced once on the host.
+cudaError_t sliced_op_create(const std::vector<double>& A, int M, int K, SlicedOp* op) {
+  std::vector<uint32_t> frag;
+  std::vector<int> ea;
+  op->M = M;
+  op->K = K;
+  slice_operator(A, M, K, Slices<double>::KS, false, op->Mt, op->Kt, frag, ea);
+  if (op->Mt * ONT > 48 || op->Kt * 16 > 400) return cudaErrorInvalidValue;  // beyond the instantiated shapes
+  cudaError_t e = cudaMalloc(&op->A, frag.size() * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemcpy(op->A, frag.data(), frag.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&op->ea, ea.size() * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpy(op->ea, ea.data(), ea.size() * sizeof(int), cudaMemcpyHostToDevice);
+  return e;
+}
+
+void sliced_op_free(SlicedOp* op) {
+  cudaFree(op->A);
+  cudaFree(op->ea);
+  op->A = nullptr;
+  op->ea = nullptr;
+}
+
+cudaError_t sliced_gemm(const SlicedOp& op, int64_t rows, const double* X, int64_t ldx, double* out, int64_t ldo,
+                        cudaStream_t st) {
+  return gemm<double>(op.Mt, rows, op.M, op.K, op.Kt, reinterpret_cast<const uint4*>(op.A), op.ea, X, ldx, out, ldo,
+                      nullptr, st);
 }
 
 // Reads and clears the pipelined kernels' timeout flag (synchronises the device).

@@ -124,6 +124,16 @@ cudaError_t launch_apply_ept(dg_mesh* m, int degree, bool f64, int B, double lam
 cudaError_t launch_apply_tensor(dg_mesh* m, int degree, bool f64, int B, double lambda, const void* u, void* Au,
                                 bool pipe, cudaStream_t st);
 cudaError_t tensor_pipe_error(int* flag);
+// FP64 operator A (M x K, row-major) sliced for the tensor-core products out[r] = A X[r]
+struct SlicedOp {
+  int M = 0, K = 0, Mt = 0, Kt = 0;
+  uint32_t* A = nullptr;
+  int* ea = nullptr;
+};
+cudaError_t sliced_op_create(const std::vector<double>& A, int M, int K, SlicedOp* op);
+void sliced_op_free(SlicedOp* op);
+cudaError_t sliced_gemm(const SlicedOp& op, int64_t rows, const double* X, int64_t ldx, double* out, int64_t ldo,
+                        cudaStream_t st);
 cudaError_t launch_nodes(const dg_mesh* m, int degree, double* x, double* y, cudaStream_t st);
 
 void set_error(const std::string& msg);

@@ -12,9 +12,12 @@
 //   (ii)  both velocity components in one batched Helmholtz PCG;
 //   (iii) the pressure-increment Poisson PCG;
 //   (iv)  the pressure-gradient correction.
-// One advection kernel computes volume and surface terms together and applies
-// the LSERK stage update, ping-ponging U~ between two buffers so neighbours
-// always read the previous stage.
+// At degrees 1-2 one advection kernel computes volume and surface terms
+// together and applies the LSERK stage update, ping-ponging U~ between two
+// buffers so neighbours always read the previous stage. From degree 3 the
+// stage's two dense contractions (cubature interpolation, projection with the
+// lift) run as exactly sliced FP64 products on the tensor cores, around an
+// FP64 kernel for the fluxes at the cubature points.
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -44,6 +47,13 @@ struct InsWorkspace {
   int N = 0;
   AdvLayout L;
   double* ops = nullptr;
+  // tensor-core advection (degree >= 3): the cubature interpolation Iq and the
+  // projection blocks Pr, Ps, -Lc as sliced FP64 operators, with their row
+  // buffers (the projection is split at its blocks so that every sliced product
+  // sums at most 224 terms, which keeps its FP32 group sums exact)
+  bool tensor = false;
+  SlicedOp opIq, opPr, opPs, opLc;
+  double *X = nullptr, *W = nullptr, *Y = nullptr, *R = nullptr;
   double *Ut0 = nullptr, *Ut1 = nullptr, *res = nullptr, *Uhat = nullptr, *Uhh = nullptr, *bu = nullptr,
          *G = nullptr, *bp = nullptr, *dP = nullptr, *tmp = nullptr;
   std::vector<void*> allocs;
@@ -54,6 +64,10 @@ void free_ins_workspace(dg_mesh* m) {
   InsWorkspace* w = m->ins;
   if (!w) return;
   for (void* p : w->allocs) cudaFree(p);
+  sliced_op_free(&w->opIq);
+  sliced_op_free(&w->opPr);
+  sliced_op_free(&w->opPs);
+  sliced_op_free(&w->opLc);
   if (w->ev0) cudaEventDestroy(w->ev0);
   if (w->ev1) cudaEventDestroy(w->ev1);
   delete w;
@@ -445,6 +459,95 @@ cudaError_t launch_advect(const dg_mesh* m, InsWorkspace* w, const double* Un, c
   }
 }
 
+// ------------------------------------------- tensor-core advection stage
+// The stage of advect_kernel split at its two dense contractions, which run as
+// sliced FP64 products on the tensor cores (sliced_gemm):
+//   X = [Ubar_x; Ubar_y; Ut_x; Ut_y]            rows (c K + e), Np each
+//   W = Iq X                                     rows (c K + e), Nc each
+//   Y = [ G.F at the volume points | (sJ/J) n.F* at the face points ]   rows (c K + e)
+//   R = Pr Y_r + Ps Y_s - Lc Y_F                 rows (c K + e), Np each: the rhs
+//       (three sliced products, summed in FP64 by the update)
+// then the LSERK update. Arithmetic and layout as in advect_kernel.
+__global__ void k_adv_gather(int64_t n1, const double* __restrict__ Un, const double* __restrict__ Unm1, double ca,
+                             double cb, const double* __restrict__ Ut_in, double* __restrict__ X) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < 4 * n1; i += int64_t(gridDim.x) * blockDim.x) {
+    const int c = int(i / n1);
+    const int64_t j = i - c * n1;
+    X[i] = c < 2 ? ca * Un[c * n1 + j] + (cb != 0.0 ? cb * Unm1[c * n1 + j] : 0.0) : Ut_in[(c - 2) * n1 + j];
+  }
+}
+
+// one thread per volume cubature point (e, q) or face cubature point (e, f, k)
+__global__ void k_adv_flux(int N, int64_t K, const double* __restrict__ geo, const int32_t* __restrict__ conn,
+                           const double* __restrict__ I1, const double* __restrict__ X, const double* __restrict__ W,
+                           const double* __restrict__ gU, double* __restrict__ Y) {
+  const int Np = (N + 1) * (N + 2) / 2, Nfp = N + 1, nc = (3 * N + 2) / 2, Nc = nc * nc;
+  const int KY = 2 * Nc + 3 * nc;
+  const int64_t nvol = K * Nc, total = nvol + K * 3 * nc;
+  const size_t fsX = size_t(K) * Np, fsW = size_t(K) * Nc, fsY = size_t(K) * KY;
+  for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
+       idx += int64_t(gridDim.x) * blockDim.x) {
+    if (idx < nvol) {
+      const int64_t e = idx / Nc;
+      const int q = int(idx - e * Nc);
+      const GeoF g = load_geo(geo, e);
+      double w[4];
+      for (int c = 0; c < 4; ++c) w[c] = W[c * fsW + size_t(e) * Nc + q];
+      for (int c = 0; c < 2; ++c) {
+        const double Fx = w[0] * w[2 + c], Fy = w[1] * w[2 + c];
+        Y[c * fsY + size_t(e) * KY + q] = g.rx * Fx + g.ry * Fy;
+        Y[c * fsY + size_t(e) * KY + Nc + q] = g.sx * Fx + g.sy * Fy;
+      }
+    } else {
+      const int64_t r = idx - nvol;
+      const int64_t e = r / (3 * nc);
+      const int q = int(r - e * 3 * nc), f = q / nc, k = q - f * nc;
+      const GeoF g = load_geo(geo, e);
+      const int code = conn[3 * e + f];
+      double m[4] = {0, 0, 0, 0}, p[4] = {0, 0, 0, 0};
+      for (int a2 = 0; a2 < Nfp; ++a2) {
+        const double i1 = I1[size_t(k) * Nfp + a2];
+        const int kl = fnode_i(N, f, a2);
+        double vm[4], vp[4];
+        for (int c = 0; c < 4; ++c) vm[c] = X[c * fsX + size_t(e) * Np + kl];
+        if (code >= 0) {
+          const int64_t nb = code >> 2;
+          const int kn = fnode_i(N, code & 3, Nfp - 1 - a2);
+          for (int c = 0; c < 4; ++c) vp[c] = X[c * fsX + size_t(nb) * Np + kn];
+        } else if (code == -2) {  // velocity Dirichlet: exterior state is the boundary datum
+          const size_t gi = size_t(e) * Np + kl;
+          vp[0] = vp[2] = gU[gi];
+          vp[1] = vp[3] = gU[fsX + gi];
+        } else {                  // Neumann: exterior = interior
+          for (int c = 0; c < 4; ++c) vp[c] = vm[c];
+        }
+        for (int c = 0; c < 4; ++c) {
+          m[c] += i1 * vm[c];
+          p[c] += i1 * vp[c];
+        }
+      }
+      double nx, ny, sjj;
+      face_n(g, f, nx, ny, sjj);
+      const double unm = nx * m[0] + ny * m[1], unp = nx * p[0] + ny * p[1];
+      const double lam = fmax(fabs(unm), fabs(unp));
+      for (int c = 0; c < 2; ++c)
+        Y[c * fsY + size_t(e) * KY + 2 * Nc + q] =
+            sjj * (0.5 * (unm * m[2 + c] + unp * p[2 + c]) + 0.5 * lam * (m[2 + c] - p[2 + c]));
+    }
+  }
+}
+
+// rhs = R_r + R_s + R_lift (the three projection blocks, each n entries);
+// res = a res + dts rhs; Ut_out = Ut_in + b res  (n = 2 K Np)
+__global__ void k_adv_update(int64_t n, const double* __restrict__ R, double a, double dts, double b,
+                             const double* __restrict__ Ut_in, double* __restrict__ res, double* __restrict__ Ut_out) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const double r = a * res[i] + dts * (R[i] + R[n + i] + R[2 * n + i]);
+    res[i] = r;
+    Ut_out[i] = Ut_in[i] + b * r;
+  }
+}
+
 #define ICK(x)                         \
   do {                                 \
     cudaError_t e_ = (x);              \
@@ -478,7 +581,46 @@ cudaError_t setup_ins(dg_mesh* m) {
   ICK(al(&w->tmp, 2 * n1));
   ICK(cudaEventCreate(&w->ev0));
   ICK(cudaEventCreate(&w->ev1));
+  // degree >= 3: the stage's dense contractions on the tensor cores
+  if (m->N >= 3) {
+    const AdvLayout& L = w->L;
+    const int Np = L.Np, Nc = L.Nc, nc = L.nc, KY = 2 * Nc + 3 * nc;
+    const std::vector<double> Iq(h.begin() + L.Iq, h.begin() + L.Iq + size_t(Nc) * Np);
+    const std::vector<double> Pr(h.begin() + L.Pr, h.begin() + L.Pr + size_t(Np) * Nc);
+    const std::vector<double> Ps(h.begin() + L.Ps, h.begin() + L.Ps + size_t(Np) * Nc);
+    std::vector<double> Lc(h.begin() + L.Lc, h.begin() + L.Lc + size_t(Np) * 3 * nc);
+    for (double& v : Lc) v = -v;
+    ICK(sliced_op_create(Iq, Nc, Np, &w->opIq));
+    ICK(sliced_op_create(Pr, Np, Nc, &w->opPr));
+    ICK(sliced_op_create(Ps, Np, Nc, &w->opPs));
+    ICK(sliced_op_create(Lc, Np, 3 * nc, &w->opLc));
+    ICK(al(&w->X, 4 * n1));
+    ICK(al(&w->W, 4 * size_t(m->K) * Nc));
+    ICK(al(&w->Y, 2 * size_t(m->K) * KY));
+    ICK(al(&w->R, 3 * 2 * n1));  // the three projection blocks' results
+    w->tensor = true;
+  }
   return cudaSuccess;
+}
+
+// One LSERK stage of the advection on the tensor cores (see k_adv_gather).
+cudaError_t advect_stage_tensor(const dg_mesh* m, InsWorkspace* w, const double* Un, const double* Unm1, double ca,
+                                double cb, const double* Ut_in, double* Ut_out, const double* gU, double a, double b,
+                                double dts, cudaStream_t st) {
+  const AdvLayout& L = w->L;
+  const int Np = L.Np, Nc = L.Nc, nc = L.nc, KY = 2 * Nc + 3 * nc;
+  const int64_t K = m->K, n1 = K * Np;
+  k_adv_gather<<<eg(4 * n1), 256, 0, st>>>(n1, Un, Unm1, ca, cb, Ut_in, w->X);
+  note_launch();
+  ICK(sliced_gemm(w->opIq, 4 * K, w->X, Np, w->W, Nc, st));
+  k_adv_flux<<<eg(K * (Nc + 3 * nc)), 256, 0, st>>>(m->N, K, m->geo64, m->conn, w->ops + L.I1, w->X, w->W, gU, w->Y);
+  note_launch();
+  ICK(sliced_gemm(w->opPr, 2 * K, w->Y, KY, w->R, Np, st));
+  ICK(sliced_gemm(w->opPs, 2 * K, w->Y + Nc, KY, w->R + 2 * n1, Np, st));
+  ICK(sliced_gemm(w->opLc, 2 * K, w->Y + 2 * Nc, KY, w->R + 4 * n1, Np, st));
+  k_adv_update<<<eg(2 * n1), 256, 0, st>>>(2 * n1, w->R, a, dts, b, Ut_in, w->res, Ut_out);
+  note_launch();
+  return cudaGetLastError();
 }
 
 // Advect U0 (given at t0) to t0 + nsub*dts with LSERK(5,4); result in the
@@ -501,7 +643,10 @@ cudaError_t advect_field(const dg_mesh* m, InsWorkspace* w, const dg_ins_state* 
         ca = 1.0 + th;
         cb = -th;
       }
-      ICK(launch_advect(m, w, s->U, s->Uold, ca, cb, cur, nxt, s->gU, kRkA[stg], kRkB[stg], dts, st));
+      if (w->tensor)
+        ICK(advect_stage_tensor(m, w, s->U, s->Uold, ca, cb, cur, nxt, s->gU, kRkA[stg], kRkB[stg], dts, st));
+      else
+        ICK(launch_advect(m, w, s->U, s->Uold, ca, cb, cur, nxt, s->gU, kRkA[stg], kRkB[stg], dts, st));
       std::swap(cur, nxt);
     }
     t += dts;
