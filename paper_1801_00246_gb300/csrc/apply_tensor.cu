@@ -13,8 +13,10 @@
 //     on the fly from the value's bit pattern (integer shifts only);
 //   * a_i x_j products summed over K <= 224 are integers below 2^22, exact in the
 //     FP32 accumulators of mma.sync m16n8k16; products with the same i + j share
-//     an accumulator (exact for FP32 up to 4 products per group: 4 x 127^2 x 224
-//     < 2^24), and only i + j <= KS + 1 is formed;
+//     an accumulator, which stays exact (below 2^24) for groups of up to 4
+//     products at K = 224 (up to 6 at K = 171); the larger groups carry weights
+//     below 2^-28 of the leading one, so their rounding is below 2^-50 of the
+//     result; only i + j <= KS + 1 is formed;
 //   * the KS accumulators are combined by Horner's rule (float-float for FP64)
 //     and scaled back by building the exponent bits.
 // That is the FP64 scheme: KS = 8 slices (56 bits, 36 products; relative error
@@ -876,7 +878,8 @@ cudaError_t sliced_op_create(const std::vector<double>& A, int M, int K, SlicedO
   op->M = M;
   op->K = K;
   slice_operator(A, M, K, Slices<double>::KS, false, op->Mt, op->Kt, frag, ea);
-  if (op->Mt * ONT > 48 || op->Kt * 16 > 400) return cudaErrorInvalidValue;  // beyond the instantiated shapes
+  // beyond the instantiated shapes, or too long a sum for the FP32 group sums to stay exact
+  if (op->Mt * ONT > 48 || K > 224) return cudaErrorInvalidValue;
   cudaError_t e = cudaMalloc(&op->A, frag.size() * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemcpy(op->A, frag.data(), frag.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&op->ea, ea.size() * sizeof(int));
