@@ -72,3 +72,25 @@ def test_c3_kovasznay_100_steps_8192tri_N8():
     assert err_u < 2e-3        # measured 9.4e-4 (splitting error)
     assert err_p < 5e-2        # measured 3.3e-2 (first-order pressure increment)
     assert max(out["vel_iters"]) < 60 and out["pr_iters"] < 100
+
+
+@pytest.mark.parametrize("N,sides", [(2, (1, 1, 1, 1)), (2, (1, 2, 1, 1)), (3, (1, 2, 1, 1)), (5, (1, 2, 1, 1))])
+def test_ins_parity_outflow_and_both_advection_paths(N, sides):
+    """Degrees 1-2 advect with the fused FP64 kernel, degrees from 3 with the
+    tensor-core stages; an outflow side (velocity Neumann at x = 1 where the
+    pressure is Dirichlet) takes the Neumann branches of the advection flux,
+    the divergence and the velocity Helmholtz operator."""
+    from oracle.ins import InsOracle
+    from oracle.sipdg import Sipdg
+    m = rotate_local_vertices(jittered_grid(5, 5, box=(-0.5, 1.0, -0.5, 1.5), jitter=0.1, seed=2,
+                                            bc_sides=sides), N)
+    stepper, mp, nu, U0, P0, _ = _setup(m, N)
+    O = InsOracle(Sipdg(m.VX, m.VY, m.EToV, m.bc, N), Sipdg(mp.VX, mp.VY, mp.EToV, mp.bc, N))
+    st = dict(U=U0.copy(), Uold=U0.copy(), P=P0.copy(), n=0)
+    for k in range(10):
+        st, _ = O.step(st, 0.01, nu, 4, U0, P0)
+        stepper.step(1)
+        if k in (0, 9):
+            assert rel(stepper.U.cpu().numpy(), st["U"]) <= 1e-9, k
+            assert rel(stepper.Uold.cpu().numpy(), st["Uold"]) <= 1e-9, k
+            assert rel(stepper.P.cpu().numpy(), st["P"]) <= 1e-8, k
