@@ -32,7 +32,10 @@
 
 namespace dgx {
 
-constexpr int kRedBlocks = 240;  // partial sums per right-hand side (fixed: deterministic)
+// Partial sums per right-hand side: 8 resident blocks of 256 threads on each of
+// the 152 SMs, enough loads in flight for the FP64 vector updates to reach HBM
+// bandwidth. Fixed, so every sum is taken in the same order (deterministic).
+constexpr int kRedBlocks = 152 * 8;
 constexpr int kRedThreads = 256;
 constexpr int kNS = 16;          // scalars per right-hand side
 
@@ -167,13 +170,20 @@ __global__ void k_update_xr(int64_t n, const double* __restrict__ scal, double* 
 
 enum FinMode { FIN_INIT_BB = 0, FIN_INIT_RZ, FIN_ALPHA, FIN_RR, FIN_BETA, FIN_BETA_FLEX };
 
+// Thread t's share of one partial slot: blocks t, t + blockDim.x, ... in order.
+__device__ __forceinline__ double partial_share(const double* pb, int slot) {
+  double v = 0.0;
+  for (int k = threadIdx.x; k < kRedBlocks; k += blockDim.x) v += pb[2 * k + slot];
+  return v;
+}
+
 // Sums the partials of right-hand side b in a fixed order and updates its scalars.
 __global__ void k_finalize(int mode, double* __restrict__ scal, const double* __restrict__ partial) {
   __shared__ double sh[32];
   const int b = blockIdx.x;
   const double* pb = partial + size_t(b) * kRedBlocks * 2;
-  const double v0 = threadIdx.x < kRedBlocks ? pb[2 * threadIdx.x] : 0.0;
-  const double v1 = threadIdx.x < kRedBlocks ? pb[2 * threadIdx.x + 1] : 0.0;
+  const double v0 = partial_share(pb, 0);
+  const double v1 = partial_share(pb, 1);
   const double s0 = block_sum(v0, sh);
   const double s1 = (mode == FIN_RR) ? block_sum(v1, sh) : 0.0;
   if (threadIdx.x != 0) return;
@@ -242,8 +252,7 @@ __global__ void k_init_check(double* scal, const double* partial) {
   __shared__ double sh[32];
   const int b = blockIdx.x;
   const double* pb = partial + size_t(b) * kRedBlocks * 2;
-  const double v0 = threadIdx.x < kRedBlocks ? pb[2 * threadIdx.x] : 0.0;
-  const double s0 = block_sum(v0, sh);
+  const double s0 = block_sum(partial_share(pb, 0), sh);
   if (threadIdx.x != 0) return;
   double* s = scal + b * kNS;
   s[S_RR] = s0;
