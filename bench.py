@@ -71,12 +71,12 @@ def algo_per_element(N, word):
 
 
 class Clocks:
-    """nvidia-smi sampler running during the timed region."""
+    """nvidia-smi sampler running during the timed region; the raw samples go to
+    $DG_CLOCKS_CSV (default /tmp/dg_clocks.csv), the summary into the JSON line."""
 
     def __init__(self, index):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks.csv") if os.path.isdir(
-            os.path.join(ROOT, "gpurun_out")) else "/tmp/dg_clocks.csv"
+        self.path = os.environ.get("DG_CLOCKS_CSV", "/tmp/dg_clocks.csv")
         self.index = index
 
     def __enter__(self):
