@@ -72,11 +72,13 @@ def algo_per_element(N, word):
 
 class Clocks:
     """nvidia-smi sampler running during the timed region; the raw samples go to
-    $DG_CLOCKS_CSV (default /tmp/dg_clocks.csv), the summary into the JSON line."""
+    $DG_CLOCKS_CSV (default /tmp/dg_clocks.csv; local rank r > 0 appends ".r"), the
+    summary into the JSON line."""
 
     def __init__(self, index):
         self.proc = None
-        self.path = os.environ.get("DG_CLOCKS_CSV", "/tmp/dg_clocks.csv")
+        base = os.environ.get("DG_CLOCKS_CSV", "/tmp/dg_clocks.csv")
+        self.path = base if index == 0 else "%s.%d" % (base, index)  # one file per local rank
         self.index = index
 
     def __enter__(self):
