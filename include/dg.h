@@ -33,6 +33,12 @@
  *  - Every entry point returns a dg_status; no exception crosses the ABI.
  *    Arguments are validated before any launch. dg_last_error() returns a
  *    human-readable message for the last failing call on this thread.
+ *  - Threads: a mesh and its workspaces belong to one host thread at a time
+ *    (calls on one mesh from several threads must be serialised by the
+ *    caller). The first call that uses a degree and precision on a device
+ *    builds process-wide tables (operator slices, launch configurations,
+ *    constant-memory operators) without a lock: make that first call, e.g.
+ *    one apply per degree, before other threads use the library.
  */
 #ifndef DG_H
 #define DG_H
