@@ -20,6 +20,12 @@ loose relative tolerance):
     levels, inner CG) the outer iteration is flexible CG with
     beta = r_{k+1}^T (z_{k+1} - z_k) / r_k^T z_k.
 The residual norm is ||b - A x||_2 / ||b||_2 on the weak coefficient vector.
+
+Parity unpinned: the iteration counts of the p-multigrid preconditioned solve
+(Section 4 reports them as figures only). What is pinned: the V-cycle's
+symmetry with an exact coarse solve, the Chebyshev error factor against its
+closed form, CG's finite termination, and every solution through its
+residual against the assembled operator.
 """
 import numpy as np
 
