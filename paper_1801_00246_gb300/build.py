@@ -43,7 +43,7 @@ def _stale(out, deps):
 def build(verbose=False, jobs=None):
     nvcc = nvcc_path()
     os.makedirs(os.path.join(OUT_DIR, "obj"), exist_ok=True)
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(INCLUDE, "dg.h"))
     common = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
     objs, cmds = [], []
