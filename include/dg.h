@@ -78,8 +78,9 @@ typedef struct dg_mesh dg_mesh; /* opaque; owned by the library until dg_mesh_de
  *   DG_KERNEL_TILE:   element tiles in shared memory, one thread per node
  *                     (FP64 on the FP64 pipe, or FP32); all degrees
  *   DG_KERNEL_GEMM:   FP32 only: register-blocked small GEMMs over element tiles; all degrees
- *   DG_KERNEL_TENSOR: dense products on the BF16 tensor cores with exact integer
- *                     slicing (FP64: 8 slices, FP32: 3 slices); all degrees
+ *   DG_KERNEL_TENSOR: dense products on the BF16 tensor cores (FP64: exact 7-bit
+ *                     integer slicing, 8 slices; FP32: three round-to-nearest BF16
+ *                     pieces); all degrees
  *   DG_KERNEL_EPT:    one element per thread, operators in constant memory; degrees 1-3
  *   DG_KERNEL_TENSOR_PIPE: DG_KERNEL_TENSOR with the output product's fill and product
  *                     phases on separate warps, double-buffered through shared memory
@@ -147,9 +148,10 @@ dg_status dg_mesh_nodes(const dg_mesh* mesh, int degree, double* x_dev, double* 
 /* Poisson operator (Eq. ellipticOp3 with lambda = 0) at the mesh degree:
  * Au[b] = A u[b] for b < B. u, Au: device [B][K][Np] of FP64 (DG_F64) or
  * FP32 (DG_F32); FP32 arithmetic accumulates in FP32. u and Au must not alias.
- * The FP32 path keeps a face-data scratch buffer with the mesh (allocated or
- * grown on first use), so FP32 applies on one mesh must not overlap on the GPU
- * (issue them on one stream, or use one mesh per stream). */
+ * The apply kernels keep scratch with the mesh (the FP32 GEMM kernel's face
+ * data, the tensor kernels' gradient rows; allocated or grown on first use),
+ * so applies on one mesh must not overlap on the GPU (issue them on one
+ * stream, or use one mesh per stream). */
 dg_status dg_poisson_apply(const dg_mesh* mesh, dg_prec prec, int B, const void* u, void* Au,
                            void* stream);
 
