@@ -9,8 +9,8 @@ from oracle.ins import LSERK_A, LSERK_B, LSERK_C, InsOracle, lserk_integrate
 from oracle.sipdg import Sipdg
 
 
-def _ins(n, N, rotate=None, box=(-0.5, 1.0, -0.5, 1.5)):
-    m = jittered_grid(n, n, box=box, jitter=0.1, seed=0, bc_sides=(1, 1, 1, 1))
+def _ins(n, N, rotate=None, box=(-0.5, 1.0, -0.5, 1.5), sides=(1, 1, 1, 1)):
+    m = jittered_grid(n, n, box=box, jitter=0.1, seed=0, bc_sides=sides)
     if rotate is not None:
         m = rotate_local_vertices(m, rotate)
     mp = ins_pressure_tags(m, dirichlet_sides=(1,))
@@ -50,11 +50,16 @@ def _poly(N, seed):
     return f, fx, fy
 
 
+# velocity Dirichlet everywhere, or Neumann at the outflow x = 1 (u* = u- there)
+SIDES = [(1, 1, 1, 1), (1, 2, 1, 1)]
+
+
+@pytest.mark.parametrize("sides", SIDES)
 @pytest.mark.parametrize("N", [2, 4, 6])
-def test_gradient_and_divergence_exact_on_polynomials(N):
+def test_gradient_and_divergence_exact_on_polynomials(N, sides):
     """For continuous polynomials with matching boundary data every jump
     vanishes, so G p = grad p and D.U = div U at the nodes."""
-    O = _ins(3, N, rotate=N)
+    O = _ins(3, N, rotate=N, sides=sides)
     x, y = O.Su.x, O.Su.y
     f, fx, fy = _poly(N, 1)
     p = f(x, y)
@@ -68,11 +73,12 @@ def test_gradient_and_divergence_exact_on_polynomials(N):
     assert np.abs(D - (fx(x, y) + gy(x, y))).max() < 1e-11 * scale * N ** 2
 
 
+@pytest.mark.parametrize("sides", SIDES)
 @pytest.mark.parametrize("N", [1, 3, 5])
-def test_advection_exact_on_continuous_linear_field(N):
+def test_advection_exact_on_continuous_linear_field(N, sides):
     """For a continuous linear velocity with matching boundary data the LLF
     jumps vanish and N~(U, U)_c = div(U U_c) exactly (degree <= 1 <= N)."""
-    O = _ins(3, N, rotate=2)
+    O = _ins(3, N, rotate=2, sides=sides)
     x, y = O.Su.x, O.Su.y
     U = np.stack([1.0 + x + 2 * y, 3.0 - y + 0.5 * x])
     u, v = U
