@@ -56,6 +56,32 @@ def test_polynomial_exactness_with_dirichlet_data(N, lam):
     assert np.linalg.norm(lhs - rhs) <= 1e-11 * max(1.0, np.linalg.norm(rhs)) * N
 
 
+@pytest.mark.parametrize("N", range(1, 9))
+@pytest.mark.parametrize("lam", [0.0, 3.5])
+def test_polynomial_exactness_with_neumann_sides(N, lam):
+    """Neumann on x = 0 and x = 1, Dirichlet (g = p) on y = 0 and y = 1: for a
+    polynomial with dp/dx = 0 on x = 0, 1 the homogeneous Neumann faces carry
+    exactly the right (zero) flux and no jump, so A p + L(g) = M(-lap p + lam p)
+    again, with data g that equal p on the Dirichlet sides only (g - p = 5 y (1 - y)
+    is not zero on the Neumann sides). A Neumann face that takes a Dirichlet block
+    or boundary data fails."""
+    m = rotate_local_vertices(jittered_grid(3, 3, jitter=0.1, seed=0, bc_sides=(2, 2, 1, 1)), N)
+    S = _sip(m, N)
+    x, y = S.x, S.y
+    p = 0.3 + 0.7 * y ** N
+    lap = 0.7 * N * (N - 1) * y ** (N - 2) if N >= 2 else np.zeros_like(x)
+    if N >= 4:  # x^2 (1 - x)^2 has zero slope at x = 0 and x = 1
+        X = x * x * (1 - x) ** 2
+        Xpp = 2 - 12 * x + 12 * x * x
+        p = p + X * y ** (N - 4)
+        lap = lap + Xpp * y ** (N - 4)
+        if N >= 6:
+            lap = lap + X * (N - 4) * (N - 5) * y ** (N - 6)
+    lhs = S.apply(p, lam=lam) + S.dirichlet_lift(p + 5.0 * y * (1.0 - y))
+    rhs = S.mass_apply(-lap + lam * p)
+    assert np.linalg.norm(lhs - rhs) <= 1e-11 * max(1.0, np.linalg.norm(rhs)) * N
+
+
 def test_helmholtz_large_lambda_tends_to_mass():
     S = _sip(_mesh(2, rotate=0), 4)
     lam = 1e9
