@@ -82,3 +82,31 @@ def test_reference_arm_prints_the_contract_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_clock_summary_reads_nvidia_smi_samples(tmp_path):
+    """The clocks record of the JSON line: median SM clock over the loaded
+    samples (idle samples below half the peak are left out), the maximum clock,
+    and every throttle reason seen Active; malformed lines are skipped."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    path = tmp_path / "clocks.csv"
+    na = "Not Active"
+    lines = ["0, 345, 2070, 120.5, 0x0, %s, %s, %s, %s" % (na, na, na, na),
+             "0, 2070, 2070, 900.1, 0x0, %s, %s, %s, %s" % (na, na, na, na),
+             "0, 1980, 2070, 1390.0, 0x4, %s, %s, %s, Active" % (na, na, na),
+             "0, 2055, 2070, 1200.0, 0x0, %s, %s, %s, %s" % (na, na, na, na),
+             "garbage line",
+             "0, [N/A], 2070, 0, 0x0, %s, %s, %s, %s" % (na, na, na, na)]
+    path.write_text("\n".join(lines) + "\n")
+    c = bench.Clocks(0)
+    c.path = str(path)
+    c.proc = object()  # as if the sampler had run
+    s = c.summary()
+    assert s["sm_mhz"] == 2055.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 4
+    assert s["reasons"] == ["sw_power_cap"]
+    path.write_text("")
+    assert bench.Clocks.summary(c)["reasons"] == ["no samples"]
+    c.proc = None
+    assert c.summary()["reasons"] == ["nvidia-smi unavailable"]
