@@ -89,3 +89,42 @@ def test_mesh_validation_rejects_bad_meshes_before_any_device_work(P):
     with pytest.raises(P.DgError) as ei:
         P.Mesh(2, m.VX, m.VY, e, m.bc)
     assert ei.value.name == "DG_ERR_ARG"
+
+
+C_CONSUMER = r"""
+#include <stdio.h>
+#include "dg.h"
+int main(void) {
+  double r[45], s[45];
+  int32_t fmask[27];
+  dg_solver_opts o;
+  dg_status st = dg_reference_operators(8, r, s, NULL, NULL, NULL, NULL, fmask);
+  dg_solver_opts_default(&o);
+  printf("%d %.17g %.17g %g %d %s\n", (int)st, r[0], s[44], o.tol, o.max_iter,
+         dg_status_string(DG_ERR_BREAKDOWN));
+  return st != DG_OK;
+}
+"""
+
+
+def test_header_is_c_and_a_c_program_links_and_runs(P, tmp_path):
+    """include/dg.h is plain C (C99, -pedantic, no warnings) and a C program
+    links against the library and calls its host-side entry points."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "consumer.c"
+    src.write_text(C_CONSUMER)
+    exe = tmp_path / "consumer"
+    libdir = os.path.dirname(P.lib_path())
+    cmd = [gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I" + os.path.join(ROOT, "include"),
+           str(src), "-o", str(exe), "-L" + libdir, "-ldg_gb300", "-Wl,-rpath," + libdir]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, out.stderr
+    st, r0, s_last, tol, max_iter, name = out.stdout.split(None, 5)
+    assert st == "0" and float(r0) == -1.0 and float(s_last) == 1.0   # vertices v0 and v2 of the reference triangle
+    assert float(tol) == 1e-10 and int(max_iter) == 1000 and name.strip()
