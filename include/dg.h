@@ -62,7 +62,10 @@ typedef enum {
 
 /* DG_F64: FP64 in/out with the mesh's FP64 kernel (DG_KERNEL_* below; built-in:
  *         from degree 3 up the dense products run on the BF16 tensor cores with
- *         exact integer slicing, relative error ~1e-13 of |A||u|);
+ *         exact integer slicing, relative error ~1e-13 of |A||u|; that path scales
+ *         each element's data by a power of two and rebuilds results from their
+ *         exponent bits, so it takes finite fields whose nonzero element
+ *         magnitudes lie between about 1e-290 and 1e290);
  * DG_F32: FP32 in/out with FP32-level accuracy (relative error <= 1e-5), with the
  *         mesh's FP32 kernel: FP32 arithmetic, or on the tensor cores three
  *         round-to-nearest BF16 pieces per operand with FP32 accumulation;
