@@ -65,7 +65,7 @@ typedef enum {
  *         exact integer slicing, relative error ~1e-13 of |A||u|; that path scales
  *         each element's data by a power of two and rebuilds results from their
  *         exponent bits, so it takes finite fields whose nonzero element
- *         magnitudes lie between about 1e-290 and 1e290);
+ *         magnitudes lie between about 1e-250 and 1e250);
  * DG_F32: FP32 in/out with FP32-level accuracy (relative error <= 1e-5), with the
  *         mesh's FP32 kernel: FP32 arithmetic, or on the tensor cores three
  *         round-to-nearest BF16 pieces per operand with FP32 accumulation;
