@@ -23,7 +23,8 @@ ALPHA_OPT = [0.0000, 0.0000, 1.4152, 0.1001, 0.2751, 0.9800, 1.0999, 1.2832,
 
 
 def jacobi_normalized(x, alpha, beta, n):
-    """P_n^{(alpha,beta)}(x) scaled to unit norm w.r.t. (1-x)^alpha (1+x)^beta."""
+    """P_n^{(alpha,beta)}(x) scaled to unit norm w.r.t. (1-x)^alpha (1+x)^beta:
+    the 1-D factors of the orthonormal basis behind the nodal basis of Section 2.1."""
     x = np.asarray(x, dtype=np.float64)
     # squared norm of the classical polynomial
     lh = ((alpha + beta + 1) * np.log(2.0) - np.log(2 * n + alpha + beta + 1)
@@ -33,7 +34,8 @@ def jacobi_normalized(x, alpha, beta, n):
 
 
 def jacobi_normalized_deriv(x, alpha, beta, n):
-    """d/dx of jacobi_normalized, from d/dx P_n^(a,b) = (n+a+b+1)/2 P_{n-1}^(a+1,b+1)."""
+    """d/dx of jacobi_normalized, from d/dx P_n^(a,b) = (n+a+b+1)/2 P_{n-1}^(a+1,b+1)
+    (for the derivative matrices of Section 5.2, Eq. operators1)."""
     x = np.asarray(x, dtype=np.float64)
     if n == 0:
         return np.zeros_like(x)
@@ -41,14 +43,16 @@ def jacobi_normalized_deriv(x, alpha, beta, n):
 
 
 def gauss_legendre(n):
-    """n-point Gauss-Legendre rule on [-1, 1] (exact to degree 2n-1)."""
+    """n-point Gauss-Legendre rule on [-1, 1] (exact to degree 2n-1): the face
+    integrals of Eq. ellipticOp1 and Eq. INS_CUB_N."""
     x, w = roots_jacobi(n, 0.0, 0.0)
     return np.asarray(x), np.asarray(w)
 
 
 def gauss_lobatto(N):
     """N+1 Legendre-Gauss-Lobatto points on [-1, 1]: the endpoints and the
-    zeros of P_N', which are the zeros of P_{N-1}^{(1,1)}."""
+    zeros of P_N', which are the zeros of P_{N-1}^{(1,1)} (the edge nodes of the
+    Warp & Blend set of Section 2.1)."""
     if N == 1:
         return np.array([-1.0, 1.0])
     xi, _ = roots_jacobi(N - 1, 1.0, 1.0)
@@ -57,7 +61,8 @@ def gauss_lobatto(N):
 
 def warp_factor(N, rout):
     """1-D warp: the interpolant (through equispaced points) of the displacement
-    from equispaced to Gauss-Lobatto points, divided by the edge blend 1-r^2."""
+    from equispaced to Gauss-Lobatto points, divided by the edge blend 1-r^2
+    (Warburton 2006, the node construction Section 2.1 cites)."""
     rout = np.asarray(rout, dtype=np.float64)
     r_gl = gauss_lobatto(N)
     r_eq = np.linspace(-1.0, 1.0, N + 1)
@@ -75,7 +80,8 @@ def warp_factor(N, rout):
 
 
 def warp_blend_nodes(N):
-    """Warp & Blend nodes on the bi-unit triangle {r,s >= -1, r+s <= 0}.
+    """Warp & Blend nodes on the bi-unit triangle {r,s >= -1, r+s <= 0}
+    (Section 2.1; Warburton 2006 with its Table 1 blend parameters).
 
     Ordering: rows of constant s from s=-1 upward; within a row r increases.
     Node 0 = (-1,-1), node N = (1,-1), node Np-1 = (-1,1).
@@ -112,7 +118,8 @@ def warp_blend_nodes(N):
 
 def face_node_lists(N):
     """Local node indices of the three faces, each in counter-clockwise order:
-    face 0 v0->v1 (s=-1), face 1 v1->v2 (r+s=0), face 2 v2->v0 (r=-1)."""
+    face 0 v0->v1 (s=-1), face 1 v1->v2 (r+s=0), face 2 v2->v0 (r=-1): the
+    face nodes of Section 2.1 (ordering: a reading, the paper is silent)."""
     rows = []
     k = 0
     for n in range(N + 1):
@@ -125,7 +132,8 @@ def face_node_lists(N):
 
 
 def collapsed(r, s):
-    """Collapsed coordinates a = 2(1+r)/(1-s) - 1, b = s (a = -1 at s = 1)."""
+    """Collapsed coordinates a = 2(1+r)/(1-s) - 1, b = s (a = -1 at s = 1), in
+    which the orthonormal basis of Section 2.1 factors into Jacobi polynomials."""
     r = np.asarray(r, dtype=np.float64)
     s = np.asarray(s, dtype=np.float64)
     top = np.abs(1.0 - s) < 1e-14
@@ -134,18 +142,21 @@ def collapsed(r, s):
 
 
 def simplex_modes(N):
+    """Mode indices (i, j), i + j <= N, of P_N on the triangle (Section 2.1)."""
     return [(i, j) for i in range(N + 1) for j in range(N + 1 - i)]
 
 
 def simplex_basis(r, s, i, j):
-    """Orthonormal (Dubiner) basis function psi_ij on the bi-unit triangle."""
+    """Orthonormal (Dubiner) basis function psi_ij on the bi-unit triangle: the
+    modal basis whose Vandermonde gives M and Dr, Ds (Section 5.2, Eq. operators1)."""
     a, b = collapsed(r, s)
     return (np.sqrt(2.0) * jacobi_normalized(a, 0, 0, i)
             * jacobi_normalized(b, 2 * i + 1, 0, j) * (1.0 - b) ** i)
 
 
 def simplex_basis_grad(r, s, i, j):
-    """(d psi_ij / dr, d psi_ij / ds) by the chain rule through (a, b)."""
+    """(d psi_ij / dr, d psi_ij / ds) by the chain rule through (a, b) (for Dr, Ds of
+    Section 5.2, Eq. operators1)."""
     a, b = collapsed(r, s)
     fa = jacobi_normalized(a, 0, 0, i)
     dfa = jacobi_normalized_deriv(a, 0, 0, i)
@@ -163,17 +174,21 @@ def simplex_basis_grad(r, s, i, j):
 
 
 def vandermonde(N, r, s):
-    """V[q, k] = psi_k(r_q, s_q) over the modes of simplex_modes(N)."""
+    """V[q, k] = psi_k(r_q, s_q) over the modes of simplex_modes(N): the
+    Vandermonde matrix of Section 5.2 (M = (V V^T)^{-1}, Eq. elMass)."""
     return np.stack([simplex_basis(r, s, i, j) for (i, j) in simplex_modes(N)], axis=-1)
 
 
 def vandermonde_grad(N, r, s):
+    """(Vr, Vs): derivatives of the basis at the points, so that Dr = Vr V^{-1}
+    and Ds = Vs V^{-1} (Section 5.2, Eq. operators1)."""
     g = [simplex_basis_grad(r, s, i, j) for (i, j) in simplex_modes(N)]
     return np.stack([t[0] for t in g], axis=-1), np.stack([t[1] for t in g], axis=-1)
 
 
 def triangle_quadrature(n):
-    """Collapsed (Duffy) rule on the bi-unit triangle with n x n points.
+    """Collapsed (Duffy) rule on the bi-unit triangle with n x n points: the
+    volume integrals of Eq. ellipticOp1 and the cubature of Eq. INS_CUB_N.
 
     a: n-point Gauss-Legendre; b: n-point Gauss-Jacobi with weight (1-b);
     dr ds = (1-b)/2 da db. Exact for polynomials of total degree <= 2n-1.

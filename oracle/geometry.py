@@ -14,6 +14,9 @@ REF_VERTS = np.array([[-1.0, -1.0], [1.0, -1.0], [-1.0, 1.0]])
 
 
 class Geometry:
+    """Per-element affine map, its inverse metric G^e and Jacobian J^e, edge
+    normals and lengths, and face neighbours (Section 5.2, Eq. operators2)."""
+
     def __init__(self, VX, VY, EToV):
         self.VX = np.asarray(VX, dtype=np.float64)
         self.VY = np.asarray(VY, dtype=np.float64)
@@ -63,8 +66,8 @@ class Geometry:
         return EToE, EToF
 
     def to_physical(self, elems, r, s):
-        """Physical coordinates of reference points (r, s) in elements `elems`.
-        r, s broadcast against elems[:, None]."""
+        """Physical coordinates of reference points (r, s) in elements `elems`
+        (the affine map of Eq. operators2). r, s broadcast against elems[:, None]."""
         P0 = self.P[elems, 0]
         jac = self.jac[elems]
         rr = np.asarray(r) + 1.0
@@ -75,7 +78,8 @@ class Geometry:
 
     def to_reference(self, elems, x, y):
         """Reference coordinates in elements `elems` of physical points (x, y),
-        arrays of shape (len(elems), n)."""
+        arrays of shape (len(elems), n): the inverse of the map of Eq. operators2,
+        used to evaluate a neighbour's basis at shared face points."""
         P0 = self.P[elems, 0]
         inv = self.inv[elems]
         dx = x - P0[:, 0, None]

@@ -59,7 +59,9 @@ LSERK_C = np.array([0.0,
 
 
 def lserk_integrate(f, y, t, dt, nsteps):
-    """Integrate y' = f(t, y) with LSERK(5,4) (2N-storage form)."""
+    """Integrate y' = f(t, y) with LSERK(5,4) (2N-storage form): the substep
+    integrator of the subcycling of Section 2.3 (Carpenter & Kennedy 1994, which
+    the paper cites)."""
     res = np.zeros_like(y)
     for _ in range(nsteps):
         for s in range(5):
@@ -70,7 +72,8 @@ def lserk_integrate(f, y, t, dt, nsteps):
 
 
 class InsOracle:
-    """Operators of the split scheme on a velocity-tagged and a pressure-tagged
+    """Operators of the split scheme of Section 2.2 (G, D of Eq. INS_SD_4_1-2,
+    the advection of Eq. INS_CUB_N) on a velocity-tagged and a pressure-tagged
     SIPDG discretisation of the same mesh and degree."""
 
     def __init__(self, Su, Sp):
@@ -179,7 +182,8 @@ class InsOracle:
         return out
 
     def to_strong(self, weak):
-        """(J M)^{-1} applied element-wise."""
+        """(J M)^{-1} applied element-wise: weak to nodal values with the element
+        mass matrix of Eq. elMass."""
         return np.einsum("ij,...ej->...ei", self.Minv, weak) / self.geo.J[:, None]
 
     def advection(self, Ubar, Ut, gU):
@@ -218,8 +222,10 @@ class InsOracle:
 
     # -- the split step -------------------------------------------------------
     def step(self, st, dt, nu, Ns, gU, gP, solve=None):
-        """One time step; st = dict(U, Uold, P, n). Returns the new state and
-        the intermediate fields (U^, U^^, dP) for inspection."""
+        """One time step of Eq. INS_TD_3 (steps (i)-(iv) of the module header)
+        with the subcycled advection of Section 2.3; st = dict(U, Uold, P, n).
+        Returns the new state and the intermediate fields (U^, U^^, dP) for
+        inspection."""
         U, Uold, P, n = st["U"], st["Uold"], st["P"], st["n"]
         t = n * dt
         dts = dt / Ns

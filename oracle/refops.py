@@ -16,6 +16,8 @@ from . import basis
 
 
 def reference_operators(N):
+    """Nodes, M, Dr, Ds, the face mass and LIFT of degree N on the reference
+    triangle (Section 5.2, Eq. elMass, Eq. operators1, Eq. elLift)."""
     r, s = basis.warp_blend_nodes(N)
     V = basis.vandermonde(N, r, s)
     Vinv = np.linalg.inv(V)
@@ -39,7 +41,9 @@ def reference_operators(N):
 
 
 def interpolation(Nf, Nc):
-    """P (Np_f x Np_c): values at the degree-Nf nodes of the degree-Nc nodal basis."""
+    """P (Np_f x Np_c): values at the degree-Nf nodes of the degree-Nc nodal basis,
+    the prolongation of the degree-coarsening multigrid of Section 3 (its form is
+    a reading: the paper does not print the transfer operators)."""
     rf, sf = basis.warp_blend_nodes(Nf)
     rc, sc = basis.warp_blend_nodes(Nc)
     Vc = basis.vandermonde(Nc, rc, sc)

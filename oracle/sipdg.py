@@ -39,7 +39,8 @@ INTERIOR, DIRICHLET, NEUMANN = 0, 1, 2
 
 
 class Sipdg:
-    """Reference data plus per-element quadrature for degree N on a mesh."""
+    """Reference data plus per-element quadrature for degree N on a mesh: the
+    SIPDG bilinear form of Eq. ellipticOp1 (Section 5.2; Eq. INS_SD_5 in Section 2.1)."""
 
     def __init__(self, VX, VY, EToV, bc, N):
         self.N = N
@@ -88,7 +89,9 @@ class Sipdg:
                 (Vs @ self.Vinv).reshape(shp + (self.Np,)))
 
     def local_blocks(self, elems, lam=0.0):
-        """Element matrix and face coupling matrices for the listed elements.
+        """Element matrix and face coupling matrices for the listed elements: the
+        volume and face integrals of Eq. ellipticOp1, with the penalty of
+        Eq. PenaltyParameter and the averages and jumps of Eq. AverageJumpScalar.
 
         Returns (Ke, faces) where Ke[e] = volume stiffness + lambda mass and
         faces[f] = (Fm, Fp, nbr, Fb_dir, A1, A2, tau) per face f.
@@ -146,7 +149,8 @@ class Sipdg:
             yield elems[i:i + size]
 
     def apply(self, u, lam=0.0, elems=None):
-        """(A u) on the listed elements (default all). u: (K, Np) or (B, K, Np)."""
+        """(A u) of Eq. ellipticOp1, matrix-free, on the listed elements (default all).
+        u: (K, Np) or (B, K, Np)."""
         u = np.asarray(u, dtype=np.float64)
         batched = u.ndim == 3
         U = u if batched else u[None]
@@ -169,7 +173,8 @@ class Sipdg:
         return out if batched else out[0]
 
     def assemble(self, lam=0.0):
-        """Sparse CSR matrix A with A[(e,i),(e',j)] = a(l_j^{e'}, l_i^e)."""
+        """Sparse CSR matrix A with A[(e,i),(e',j)] = a(l_j^{e'}, l_i^e), a the bilinear
+        form of Eq. ellipticOp1."""
         rows, cols, vals = [], [], []
         Np = self.Np
         ii, jj = np.meshgrid(np.arange(Np), np.arange(Np), indexing="ij")
@@ -194,7 +199,7 @@ class Sipdg:
         return A
 
     def diagonal(self, lam=0.0):
-        """diag(A) as a (K, Np) array (Jacobi preconditioner)."""
+        """diag(A) as a (K, Np) array (the Jacobi preconditioner of Section 3)."""
         out = np.zeros((self.K, self.Np))
         for ch in self._chunks(np.arange(self.K)):
             Ke, faces = self.local_blocks(ch, lam)
@@ -209,17 +214,21 @@ class Sipdg:
         return out
 
     def mass_matrix_ref(self):
-        """Reference mass matrix (l_i, l_j) on the bi-unit triangle, by quadrature."""
+        """Reference mass matrix (l_i, l_j) on the bi-unit triangle, by quadrature
+        (Eq. elMass)."""
         return np.einsum("q,qi,qj->ij", self.wq, self.Lq, self.Lq)
 
     def mass_apply(self, f):
-        """(l_i, f_h)_E for a nodal field f (K, Np) or (B, K, Np)."""
+        """(l_i, f_h)_E = J^e M f_e for a nodal field f (K, Np) or (B, K, Np) (the
+        lambda term of Eq. ellipticOp1, and the load of the right-hand side)."""
         M = self.mass_matrix_ref()
         return np.einsum("ij,...ej->...ei", M, f) * self.geo.J[:, None]
 
     def dirichlet_lift(self, g):
         """L(g)_i = sum over Dirichlet faces of (n.grad l_i, g) - 2 tau (l_i, g),
-        g the nodal trace of a field given at all nodes (K, Np)."""
+        g the nodal trace of a field given at all nodes (K, Np): the data part of
+        the Dirichlet faces of Eq. ellipticOp1 under the ghost state u+ = 2g - u-
+        (a reading: Section 2.1 calls the boundary treatment analogous)."""
         g = np.asarray(g, dtype=np.float64)
         out = np.zeros((self.K, self.Np))
         for ch in self._chunks(np.arange(self.K)):
@@ -232,11 +241,13 @@ class Sipdg:
         return out
 
     def rhs(self, f_nodal, g_nodal):
-        """Weak right-hand side b = M f - L(g) of the Dirichlet problem."""
+        """Weak right-hand side b = M f - L(g) of the Dirichlet problem (Eq. DirichletBC
+        data; f interpolated at the nodes, a reading)."""
         return self.mass_apply(f_nodal) - self.dirichlet_lift(g_nodal)
 
     def l2_error(self, u_nodal, exact):
-        """L2 norm of (u_h - exact) over the mesh, by the volume quadrature."""
+        """L2 norm of (u_h - exact) over the mesh, by the volume quadrature (the error
+        norm of the convergence studies of Section 4)."""
         rq, sq, wq = basis.triangle_quadrature(self.N + 3)
         Lq = basis.vandermonde(self.N, rq, sq) @ self.Vinv
         xq, yq = self.geo.to_physical(np.arange(self.K), rq[None, :], sq[None, :])

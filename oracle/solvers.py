@@ -31,7 +31,8 @@ import numpy as np
 
 
 def cg(apply, b, x0=None, tol=1e-10, maxit=10000, prec=None, flexible=False):
-    """(Flexible) preconditioned CG. Returns (x, iters, relres)."""
+    """(Flexible) preconditioned CG (Section 3; flexible beta with a variable
+    preconditioner, a reading). Returns (x, iters, relres)."""
     b = np.asarray(b, dtype=np.float64)
     x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
     r = b - apply(x)
@@ -89,7 +90,8 @@ def chebyshev(apply, dinv, b, x, lmin, lmax, degree):
 
 def power_rho(apply, dinv, shape, steps=20, seed=12345):
     """Largest eigenvalue of D^{-1} A estimated by `steps` power iterations
-    from a seeded random start."""
+    from a seeded random start: the bound of the Chebyshev smoother of Section 3
+    (its estimate is a reading: the paper does not say how it is obtained)."""
     v = np.random.default_rng(seed).standard_normal(shape)
     v /= np.linalg.norm(v)
     lam = 0.0
@@ -101,7 +103,8 @@ def power_rho(apply, dinv, shape, steps=20, seed=12345):
 
 
 class PMultigrid:
-    """V-cycle over degrees levels[0] > levels[1] > ... > levels[-1].
+    """V-cycle over degrees levels[0] > levels[1] > ... > levels[-1]: the
+    degree-coarsening multigrid preconditioner of Section 3.
 
     ops[l] = (apply, dinv) of the SIPDG operator at degree levels[l] on
     (K, Np_l) arrays; P[l] interpolates level l+1 to level l (Np_l x Np_{l+1}).
@@ -123,6 +126,8 @@ class PMultigrid:
         self.coarse_iters = []
 
     def vcycle(self, r, l=0):
+        """One V-cycle from level l (Section 3): Chebyshev pre-smoothing, residual,
+        restriction by P^T, recursion, prolongation by P, post-smoothing."""
         if l == len(self.ops) - 1:
             apply, _ = self.ops[l]
             if self.coarse_solve is not None:
@@ -147,5 +152,6 @@ def inverse_mass_prec(sip, lam):
     J = sip.geo.J
 
     def prec(r):
+        """z_e = (lam J_e M)^{-1} r_e (Section 3)."""
         return np.einsum("ij,...ej->...ei", Minv, r) / (lam * J[:, None])
     return prec
