@@ -1,6 +1,9 @@
 // C ABI entry points: mesh setup, operator applies, right-hand side, nodes,
 // and the small per-element kernels they need (Jacobi diagonal, Dirichlet
-// right-hand side).
+// right-hand side). The operator is the SIPDG form of Section 5.2
+// (Eq. ellipticOp1, evaluated as Eq. ellipticOp3); the right-hand side carries
+// the Dirichlet data of Eq. DirichletBC; the diagonal feeds the Jacobi
+// preconditioner of Section 3.
 #include <algorithm>
 #include <cmath>
 #include <cstring>

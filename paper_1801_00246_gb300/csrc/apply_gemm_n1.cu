@@ -1,4 +1,5 @@
 // FP32 SIPDG apply as register-blocked GEMMs, degree N = 1.
+// (Eq. ellipticOp3 as two dense products per element tile; see apply_gemm.cuh.)
 #define GA_N 1
 #define GA_NS ga1
 #include "apply_gemm.cuh"

@@ -1,4 +1,5 @@
 // FP32 SIPDG apply as register-blocked GEMMs, degree N = 8.
+// (Eq. ellipticOp3 as two dense products per element tile; see apply_gemm.cuh.)
 #define GA_N 8
 #define GA_NS ga8
 #include "apply_gemm.cuh"
