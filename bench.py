@@ -13,7 +13,10 @@ One step = one pass of the hot path over this input:
   * the mixed solve once more with the host-driven loop (the two solves above
     run as one CUDA graph each, loops on the device)
 `value` is the FP64 Poisson apply throughput (GDOF/s = K*Np / apply time);
-the other pieces are reported beside it. L2 (135 MB) is flushed by writing a
+the other pieces are reported beside it. After the timed steps, outside the
+timed region: the true residuals of the last solves, the same solves with 4
+and 16 right-hand sides in one batched solve, and the split INS step on the
+8,192-triangle Kovasznay workload. L2 (135 MB) is flushed by writing a
 256 MB buffer before every timed launch; all timing is CUDA events on the
 launching stream.
 
@@ -41,6 +44,12 @@ PMG_DEGREES = [8, 4, 2, 1]
 CHEB = 3           # Chebyshev-Jacobi smoothing degree per pre/post smoothing
 COARSE_PASSES = 1  # degree-1 coarse solve: one AMG-preconditioned CG pass (a scaled AMG V-cycle)
 TENSOR_APPLY_TRAFFIC = 1.3250e9  # bytes per FP64 tensor apply from the latest ncu capture of the current kernels
+
+
+# apply kernels by DG_KERNEL_* value
+KERNEL_NAMES = {1: "tile (FP64/FP32 pipe)", 2: "gemm (FP32 register GEMMs)",
+                3: "tensor (mma.sync BF16 slice products: gradient product, then fused fill + output product)",
+                4: "ept (element per thread)", 5: "tensor_pipe"}
 
 
 def peaks():
@@ -276,6 +285,7 @@ def run_ours(args, world, rank, local):
         ev["solve_mixed_host_loop"] = timed(lambda: mesh.solve(b, x_h, opts=opts_mixed_host))
         if record is not None:
             torch.cuda.synchronize()
+            record["x_last"] = {"mixed": x_m, "fp64": x_d}
             for k, (e0, e1, r) in ev.items():
                 record.setdefault(k, []).append(e0.elapsed_time(e1))
                 if k.startswith("solve"):
@@ -325,6 +335,17 @@ def run_ours(args, world, rank, local):
         if it >= args.warmup:
             e2e_ms.append(e0.elapsed_time(e1))
 
+    # true residual ||b - A x|| / ||b|| of the last step's solutions, with the
+    # apply kernel that runs every operation on the FP64 pipe (no slicing; an
+    # operator path independent of the one inside the solves)
+    def true_relres(xx):
+        return float((b - mesh.apply(xx, fp64_pipe=True)).norm() / b.norm())
+
+    relres_true = {k: true_relres(v) for k, v in rec["x_last"].items()}
+    del rec["x_last"]
+    batched = batched_solves(P, m, b, opts_mixed, opts_fp64, stream) if not args.no_extras else {}
+    ins = ins_measure(P, 2, 3) if (not args.no_extras and world == 1) else None
+
     pk = peaks()
     bytes64, flops = algo_per_element(N, 8)
     bytes32, _ = algo_per_element(N, 4)
@@ -342,6 +363,7 @@ def run_ours(args, world, rank, local):
     # BF16 MMA flops the tensor-core FP64 apply issues per launch at N=8 (Poisson):
     # 36 slice products x 2 flops x padded (rows x depth) of its two products
     tc_flops = 36 * 2 * (96 * 48 + 48 * 176) * K
+    algo_gbs = K * bytes64 / (fp64_ms * 1e-3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -349,6 +371,8 @@ def run_ours(args, world, rank, local):
         "config": {"workload": "512x512 jittered grid (jitter 0.1h, seed 0), 524288 triangles, N=8 (Np=45), "
                                "Dirichlet; Poisson apply FP64 (value), FP32, Helmholtz, pMG-FCG solves",
                    "K": K, "N": N, "Np": Np, "batch": 1, "pmg_degrees": PMG_DEGREES,
+                   "fp64_kernel": KERNEL_NAMES.get(mesh.kernel(N, P.DG_F64, 0), "?"),
+                   "fp32_kernel": KERNEL_NAMES.get(mesh.kernel(N, P.DG_F32, 0), "?"),
                    "l2": "256 MB buffer written before every timed launch",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "ax": ax,
@@ -360,20 +384,29 @@ def run_ours(args, world, rank, local):
                          "coarse_iters_mixed": int(rec["solve_mixed_coarse"][-1]),
                          "coarse_iters_fp64": int(rec["solve_fp64_coarse"][-1]),
                          "relres_mixed": float(rec["solve_mixed_relres"][-1]),
-                         "relres_fp64": float(rec["solve_fp64_relres"][-1])},
-        "roofline": {"bound": "tensor", "achieved": tc_flops / (fp64_ms * 1e-3) / 1e12,
-                     "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
-                     "frac": tc_flops / (fp64_ms * 1e-3) / 1e12 / pk["bf16_tflops"],
-                     # DRAM bytes read + written by oz_gemm + oz_out in one ncu capture of an
-                     # N=8 apply of this workload; None while the kernels differ from that capture
+                         "relres_fp64": float(rec["solve_fp64_relres"][-1]),
+                         "relres_true_mixed": relres_true["mixed"],
+                         "relres_true_fp64": relres_true["fp64"],
+                         "relres_true_how": "||b - A x|| / ||b|| with the FP64-pipe tile kernel (DG_F64_DFMA)",
+                         "batched": batched},
+        # the dominant kernel against the metric's own roof: the method's algorithmic
+        # bytes per apply (read u, write A u, 4 geometry words, 3 neighbour ids per
+        # element) over the measured HBM copy bandwidth
+        "roofline": {"bound": "hbm", "achieved": algo_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": algo_gbs / pk["hbm_gbs"],
+                     # DRAM bytes read + written per apply in one ncu capture of the current
+                     # kernels on this workload; None while the kernels differ from that capture
                      "traffic": TENSOR_APPLY_TRAFFIC,
-                     "kernel": "FP64 Poisson apply (oz_gemm: C1 = [Dr;Ds]U, then oz_out: pointwise stage fused "
-                               "into Au = OB Y): BF16 tensor-core products with exact 7-bit slicing, "
-                               "36 slice products per FP64 product",
-                     "peak_src": "measured cuBLAS bf16 (MEASURED_PEAKS.json); mma.sync m16n8k16 measured "
-                                 "603 TFLOP/s on this GPU",
+                     "algorithmic_bytes": K * bytes64,
+                     "kernel": "FP64 Poisson apply, N=8 (default kernel sequence; see config.fp64_kernel)",
+                     "peak_src": pk["hbm_src"] + " HBM copy bandwidth (MEASURED_PEAKS.json)",
                      "fp64_equiv_tflops": achieved / 1e3,
-                     "fp64_pipe_peak_tflops": pk["fp64_gflops"] / 1e3},
+                     "fp64_pipe_peak_tflops": pk["fp64_gflops"] / 1e3,
+                     # the FP64 emulation's own work (BF16 slice products on padded tiles), kept
+                     # apart from frac: it is work the method does not need
+                     "emulation_bf16_tflops": tc_flops / (fp64_ms * 1e-3) / 1e12,
+                     "emulation_bf16_frac": tc_flops / (fp64_ms * 1e-3) / 1e12 / pk["bf16_tflops"]},
+        "ins_step": ins,
         "e2e": {"value": K * Np / (float(np.mean(e2e_ms)) * 1e-3) / 1e9, "unit": "GDOF/s",
                 "h2d_bytes_per_step": int(uh.numel() * 8), "d2h_bytes_per_step": int(oh.numel() * 8)},
         "gpu_launches": launches,
@@ -386,6 +419,76 @@ def run_ours(args, world, rank, local):
                                 "sample": "FP64 oracle Poisson apply on 2048 of the 524288 elements (numpy)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def batched_solves(P, m, b, opts_mixed, opts_fp64, stream, batches=(4, 16)):
+    """The N=8 pressure solve with B right-hand sides in one batched solve
+    (mixed and plain FP64), once to capture the graph and once timed, on a
+    mesh of its own (destroyed after each B, which frees its workspaces); the
+    right-hand sides are b scaled by 1, 1/2, 1/3, ... (every one converges
+    on its own). Per B: ms of the solve, ms per right-hand side, iterations,
+    largest recurrence and true relative residual (FP64-pipe apply)."""
+    import torch
+    out = {}
+    for B in batches:
+        mesh = P.Mesh.from_inputs(m, 8)
+        bb = torch.stack([b / (i + 1) for i in range(B)])
+
+        def true_relres(xx):
+            r = bb - mesh.apply(xx, fp64_pipe=True)
+            return float((r.norm(dim=(1, 2)) / bb.norm(dim=(1, 2))).max())
+
+        for key, opts in (("mixed", opts_mixed), ("fp64", opts_fp64)):
+            x = torch.zeros_like(bb)
+            mesh.solve(bb, x, opts=opts)
+            x.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, info = mesh.solve(bb, x, opts=opts)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            out[f"B{B}_{key}"] = {"ms": ms, "ms_per_rhs": ms / B, "iters": max(info["iters"]),
+                                  "relres": max(info["relres"]), "relres_true": true_relres(x)}
+            del x
+        del bb
+        mesh.close()
+        torch.cuda.empty_cache()
+    return out
+
+
+def ins_measure(P, warmup, steps):
+    """ms per dg_ins_step on the 64x64 Kovasznay workload (8,192 triangles,
+    N=8, Re=40, dt=0.01, 32 LSERK substeps), velocity and pressure solves by
+    mixed-precision pMG-FCG (8->4->1, Chebyshev degree 3, one AMG-preconditioned
+    coarse iteration) to 1e-10; and the velocity's distance from the closed
+    form after the timed steps."""
+    import torch
+    from dg_inputs import config_mesh
+    from dg_inputs.fields import kovasznay
+    from dg_inputs.mesh import ins_pressure_tags
+    m, N = config_mesh("c3_ins_8192tri_N8")
+    mp = ins_pressure_tags(m, dirichlet_sides=(1,))
+    mu_l, mp_l = P.Mesh.from_inputs(m, N), P.Mesh.from_inputs(mp, N)
+    nu, fu, fv, fp = kovasznay(40.0)
+    x, y = mu_l.nodes()
+    xh, yh = x.cpu().numpy(), y.cpu().numpy()
+    U0 = torch.from_numpy(np.stack([fu(xh, yh), fv(xh, yh)])).cuda()
+    P0 = torch.from_numpy(fp(xh, yh)).cuda()
+    o = dict(precond=P.PREC_PMG, degrees=[N, N // 2, 1], cheb_degree=3, coarse_amg=1, coarse_max_iter=1,
+             tol=1e-10, max_iter=500, mixed=1)
+    st = P.InsStepper(mu_l, mp_l, nu, 0.01, 32, U0.clone(), P0.clone(), U0.clone(), P0.clone(),
+                      vel_opts=P._binding.default_opts(**o), pr_opts=P._binding.default_opts(**o))
+    st.step(warmup)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("ins_steps")
+    out = st.step(steps)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    err = float((st.U - U0).abs().max())
+    return {"workload": "64x64 Kovasznay, 8192 triangles, N=8, dt=0.01, 32 substeps", "steps": steps,
+            "ms_per_step": out["ms"] / steps, "vel_iters": out["vel_iters"], "pr_iters": out["pr_iters"],
+            "max_err_u": err}
 
 
 def run_apply_only(args):
@@ -512,40 +615,11 @@ def run_solve_only(args):
 
 
 def run_ins(args):
-    """The split INS step on the 64x64 Kovasznay workload (8,192 triangles,
-    N=8, Re=40, dt=0.01, 32 LSERK substeps): velocity and pressure solves by
-    mixed-precision pMG-FCG (8->4->1, Chebyshev degree 3, one AMG-preconditioned
-    coarse iteration) to 1e-10; ms per dg_ins_step and the
-    velocity's distance from the closed form after the timed steps."""
-    import torch
+    """The split INS step on the 64x64 Kovasznay workload alone (see ins_measure)."""
     import paper_1801_00246_gb300 as P
     from paper_1801_00246_gb300 import build
-    from dg_inputs import config_mesh
-    from dg_inputs.fields import kovasznay
-    from dg_inputs.mesh import ins_pressure_tags
     build.build()
-    m, N = config_mesh("c3_ins_8192tri_N8")
-    mp = ins_pressure_tags(m, dirichlet_sides=(1,))
-    mu_l, mp_l = P.Mesh.from_inputs(m, N), P.Mesh.from_inputs(mp, N)
-    nu, fu, fv, fp = kovasznay(40.0)
-    x, y = mu_l.nodes()
-    xh, yh = x.cpu().numpy(), y.cpu().numpy()
-    U0 = torch.from_numpy(np.stack([fu(xh, yh), fv(xh, yh)])).cuda()
-    P0 = torch.from_numpy(fp(xh, yh)).cuda()
-    o = dict(precond=P.PREC_PMG, degrees=[N, N // 2, 1], cheb_degree=3, coarse_amg=1, coarse_max_iter=1,
-             tol=1e-10, max_iter=500, mixed=1)
-    st = P.InsStepper(mu_l, mp_l, nu, 0.01, 32, U0.clone(), P0.clone(), U0.clone(), P0.clone(),
-                      vel_opts=P._binding.default_opts(**o), pr_opts=P._binding.default_opts(**o))
-    st.step(args.warmup)
-    torch.cuda.synchronize()
-    torch.cuda.nvtx.range_push("ins_steps")
-    out = st.step(args.steps)
-    torch.cuda.synchronize()
-    torch.cuda.nvtx.range_pop()
-    err = float((st.U - U0).abs().max())
-    print(json.dumps({"ins": True, "workload": "64x64 Kovasznay, 8192 triangles, N=8, dt=0.01, 32 substeps",
-                      "steps": args.steps, "ms_per_step": out["ms"] / args.steps, "vel_iters": out["vel_iters"],
-                      "pr_iters": out["pr_iters"], "max_err_u": err}), flush=True)
+    print(json.dumps(dict(ins=True, **ins_measure(P, args.warmup, args.steps))), flush=True)
 
 
 def main():
@@ -555,6 +629,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched solves and the INS step measured after the timed region")
     ap.add_argument("--apply-only", action="store_true", help="only the Poisson applies (profiling)")
     ap.add_argument("--degree", type=int, default=8, help="degree for --apply-only")
     ap.add_argument("--sweep", action="store_true", help="apply throughput for N=1..8, FP64/FP32, B=1/4/16")

@@ -35,10 +35,10 @@
  *    human-readable message for the last failing call on this thread.
  *  - Threads: a mesh and its workspaces belong to one host thread at a time
  *    (calls on one mesh from several threads must be serialised by the
- *    caller). The first call that uses a degree and precision on a device
- *    builds process-wide tables (operator slices, launch configurations,
- *    constant-memory operators) without a lock: make that first call, e.g.
- *    one apply per degree, before other threads use the library.
+ *    caller). Process-wide tables (operator slices, launch configurations,
+ *    constant-memory operators) are built under a library lock on first use
+ *    of a degree and precision on a device, so meshes on different threads
+ *    may meet a new degree at the same time.
  */
 #ifndef DG_H
 #define DG_H
@@ -262,19 +262,25 @@ dg_status dg_ins_step(dg_mesh* mesh_u, dg_mesh* mesh_p, dg_ins_state* state, int
  * cannot allocate device memory while they run (a host whose memory pool owns
  * the whole GPU, a time-critical loop that must not pay cudaMalloc's implicit
  * synchronisation, or a simulation that must not fail on an allocation
- * midway). Its workspace is a fixed scratch array of 2^22 doubles (32 MiB)
- * compiled into the library as device memory, which every GPU that loads the
- * library holds until the process exits. b, x: device FP64 [B][K][Np] as in
+ * midway). Its workspace, including the gradient rows of the tensor-core
+ * apply, is a fixed scratch array of 2^22 doubles (32 MiB) compiled into the
+ * library as device memory, which every GPU that loads the library holds
+ * until the process exits; the apply's operator tables for the mesh degree
+ * are built by dg_mesh_setup. b, x: device FP64 [B][K][Np] as in
  * dg_pcg_solve (x: initial guess in, solution out); the mesh comes from an
- * earlier dg_mesh_setup. Sizes beyond the array (about B*K*Np > 838,000) are
- * rejected with DG_ERR_ARG before any device work. The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress) and caches it;
- * make that first call before any stream capture. The call calls no
- * cudaMalloc/cudaFree and no allocating library routine. All calls share the
- * one array and leave their data in it: two calls whose work overlaps on the
- * GPU (different streams, or different host threads on one device) race and
- * corrupt each other's results; serialise them. info (host, may be NULL)
- * receives iterations and residuals; info->ms is not measured (0). */
+ * earlier dg_mesh_setup on the current device. The array holds
+ * (6 B + 1) K Np words plus a few per right-hand side (7 B + 1 with
+ * lambda != 0): at B = 1 about K*Np <= 599,000 (lambda = 0) or 524,000;
+ * larger problems are rejected with DG_ERR_ARG before any device work. The
+ * first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture. The call calls no cudaMalloc/cudaFree and no allocating
+ * library routine. All calls share the one array and leave their data in it
+ * (every word a call reads is written by that call first): two calls whose
+ * work overlaps on the GPU (different streams, or different host threads on
+ * one device) race and corrupt each other's results; serialise them. info
+ * (host, may be NULL) receives iterations and residuals; info->ms is not
+ * measured (0). */
 dg_status dg_pcg_jacobi_solve_static(const dg_mesh* mesh, int B, double lambda, double tol, int max_iter,
                                      const double* b, double* x, dg_solve_info* info, void* stream);
 

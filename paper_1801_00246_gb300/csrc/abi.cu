@@ -341,6 +341,10 @@ dg_status dg_mesh_setup(int N, int64_t Nv, const double* VX, const double* VY, i
     if (ce == cudaSuccess) ce = cudaMemcpy(m->geox32, gx32.data(), sizeof(float) * 16 * K, cudaMemcpyHostToDevice);
   }
   if (ce == cudaSuccess) ce = ensure_ops(m, N);
+  // the tensor kernels' operator slices of the mesh degree: built here so that
+  // an apply at the mesh degree allocates nothing once the mesh exists
+  if (ce == cudaSuccess) ce = ensure_tensor_ops(m, N, true);
+  if (ce == cudaSuccess) ce = ensure_tensor_ops(m, N, false);
   if (ce != cudaSuccess) {
     dg_mesh_destroy(m);
     return cuda_fail(ce, "dg_mesh_setup");

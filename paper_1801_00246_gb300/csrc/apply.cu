@@ -336,6 +336,7 @@ cudaError_t launch_t(const dg_mesh* m, int B, double lambda, const void* u, void
   if (dev >= 64) return cudaErrorInvalidDevice;
   LaunchCfg& c = cfg[dev];
   auto kern = sipdg_apply_kernel<N, T, HELM>;
+  std::unique_lock<std::mutex> lk(table_mutex());
   if (!c.ready) {
     c.smem = S::bytes;
     err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(c.smem));
@@ -348,6 +349,7 @@ cudaError_t launch_t(const dg_mesh* m, int B, double lambda, const void* u, void
     c.grid = (per_sm > 0 ? per_sm : 1) * sms;
     c.ready = true;
   }
+  lk.unlock();
   const int64_t ntiles = (m->K + S::E - 1) / S::E;
   const int64_t work = ntiles * B;
   const int grid = int(work < c.grid ? work : c.grid);
@@ -400,7 +402,7 @@ bool kernel_valid(int kernel, int degree, bool f64) {
 }
 
 cudaError_t launch_apply(const dg_mesh* mc, int degree, dg_prec prec, int B, double lambda, const void* u, void* Au,
-                         cudaStream_t st) {
+                         cudaStream_t st, double* c1_scratch) {
   dg_mesh* m = const_cast<dg_mesh*>(mc);
   const bool helm = lambda != 0.0;
   int k;
@@ -415,7 +417,7 @@ cudaError_t launch_apply(const dg_mesh* mc, int degree, dg_prec prec, int B, dou
   if (!kernel_valid(k, degree, f64)) return cudaErrorInvalidValue;
   if (k == DG_KERNEL_EPT) return launch_apply_ept(m, degree, f64, B, lambda, u, Au, st);
   if (k == DG_KERNEL_TENSOR || k == DG_KERNEL_TENSOR_PIPE)
-    return launch_apply_tensor(m, degree, f64, B, lambda, u, Au, k == DG_KERNEL_TENSOR_PIPE, st);
+    return launch_apply_tensor(m, degree, f64, B, lambda, u, Au, k == DG_KERNEL_TENSOR_PIPE, st, c1_scratch);
   if (k == DG_KERNEL_GEMM) {
     const int dmax = degree > m->N ? degree : m->N;
     const size_t need = size_t(B) * size_t(m->K) * 3 * size_t(dmax + 1);

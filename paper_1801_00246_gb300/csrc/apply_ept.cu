@@ -308,10 +308,13 @@ cudaError_t launch_apply_ept(dg_mesh* m, int degree, bool f64, int B, double lam
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (!g_uploaded[dev & 63]) {
-    e = upload(m);
-    if (e != cudaSuccess) return e;
-    g_uploaded[dev & 63] = true;
+  {
+    std::lock_guard<std::mutex> lk(table_mutex());
+    if (!g_uploaded[dev & 63]) {
+      e = upload(m);
+      if (e != cudaSuccess) return e;
+      g_uploaded[dev & 63] = true;
+    }
   }
   switch (degree) {
     case 1: return launch_n<1>(m, f64, B, lambda, u, Au, st);

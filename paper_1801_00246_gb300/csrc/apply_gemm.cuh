@@ -442,6 +442,7 @@ cudaError_t launch(const dg_mesh* m, int B, double lambda, const float* u, float
   Cfg& c = cfg[dev];
   constexpr size_t smP = sizeof(float) * nPrep;
   constexpr size_t smA = sizeof(float) * nApply;
+  std::unique_lock<std::mutex> lk(table_mutex());
   if (!c.ops) {
     const RefElem R = m->ref[N].N ? m->ref[N] : build_reference(N);
     const std::vector<float> h = build_ops(R);
@@ -464,6 +465,7 @@ cudaError_t launch(const dg_mesh* m, int B, double lambda, const float* u, float
     c.grid_h = sms * (hh > 0 ? hh : 1);
     c.ops = d;
   }
+  lk.unlock();
   const int64_t work = ((m->K + E - 1) / E) * B;
   auto clampg = [work](int g) { return int(work < g ? work : g); };
   face_prep_g<<<clampg(c.grid_prep), THREADS, smP, st>>>(m->K, B, m->geo32, m->conn, c.ops, u, face);

@@ -735,10 +735,13 @@ cudaError_t launch_gemm(int64_t nE, int M, int Kd, int Mt, int Kt, const uint4* 
   if (e != cudaSuccess) return e;
   const void* kern = fa ? reinterpret_cast<const void*>(oz_out<MAXF, OWARPS, T>)
                         : reinterpret_cast<const void*>(oz_gemm<MAXF, OWARPS, T>);
-  if (configured[dev & 63][fa ? 1 : 0] < smem) {
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
-    configured[dev & 63][fa ? 1 : 0] = smem;
+  {
+    std::lock_guard<std::mutex> lk(table_mutex());
+    if (configured[dev & 63][fa ? 1 : 0] < smem) {
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      if (e != cudaSuccess) return e;
+      configured[dev & 63][fa ? 1 : 0] = smem;
+    }
   }
   int sms = 0, per = 0;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -788,10 +791,13 @@ cudaError_t launch_pipe(int64_t nE, int Kd, int Mt, int Kt, const uint4* Af, con
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (configured[dev & 63] < smem) {
-    e = cudaFuncSetAttribute(oz_out_pipe<MAXF, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
-    configured[dev & 63] = smem;
+  {
+    std::lock_guard<std::mutex> lk(table_mutex());
+    if (configured[dev & 63] < smem) {
+      e = cudaFuncSetAttribute(oz_out_pipe<MAXF, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      if (e != cudaSuccess) return e;
+      configured[dev & 63] = smem;
+    }
   }
   int sms = 0, per = 0;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -821,26 +827,42 @@ cudaError_t gemm_pipe(int Mt, int64_t nE, int Kd, int Kt, const uint4* Af, const
 
 OzOps g_oz[2][64][kMaxN + 1];  // [0: FP64, 1: FP32][device][degree]
 
+// The per-device operator slices of one degree and precision, built on first
+// use (under the table lock; the slices of a built entry never change).
 template <typename T>
-cudaError_t apply_tensor(dg_mesh* m, int degree, int B, double lambda, const T* u, T* Au, bool pipe,
-                         cudaStream_t st) {
+cudaError_t tensor_ops(dg_mesh* m, int degree, const OzOps** out) {
   constexpr bool f64 = sizeof(T) == 8;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(table_mutex());
   OzOps& o = g_oz[f64 ? 0 : 1][dev & 63][degree];
   if (!o.A1) {
-    if (m->ref[degree].N == 0) m->ref[degree] = build_reference(degree);
-    e = build_oz_ops(m->ref[degree], Slices<T>::KS, !f64, o);
+    const RefElem R = m->ref[degree].N ? m->ref[degree] : build_reference(degree);
+    OzOps built;
+    e = build_oz_ops(R, Slices<T>::KS, !f64, built);
     if (e != cudaSuccess) return e;
+    o = built;
   }
+  *out = &o;
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t apply_tensor(dg_mesh* m, int degree, int B, double lambda, const T* u, T* Au, bool pipe,
+                         cudaStream_t st, double* c1_scratch) {
+  constexpr bool f64 = sizeof(T) == 8;
+  const OzOps* op = nullptr;
+  cudaError_t e = tensor_ops<T>(m, degree, &op);
+  if (e != cudaSuccess) return e;
+  const OzOps& o = *op;
   const int N = degree, Np = (N + 1) * (N + 2) / 2, NFN = 3 * (N + 1);
   const bool helm = lambda != 0.0;
   const int KY = 2 * Np + 3 * NFN;
   const int ldc = helm ? 3 * Np : 2 * Np;  // C1 rows: ur, us (+ M u)
   const int64_t nE = int64_t(B) * m->K;
   const size_t words = size_t(nE) * ldc * sizeof(T) / sizeof(double) + 1;
-  if (m->oz_cap < words) {
+  if (!c1_scratch && m->oz_cap < words) {
     cudaFree(m->oz_scratch);
     m->oz_scratch = nullptr;
     m->oz_cap = 0;
@@ -850,7 +872,7 @@ cudaError_t apply_tensor(dg_mesh* m, int degree, int B, double lambda, const T* 
     m->oz_cap = words;
     ++m->scratch_gen;
   }
-  T* C1 = reinterpret_cast<T*>(m->oz_scratch);
+  T* C1 = reinterpret_cast<T*>(c1_scratch ? c1_scratch : m->oz_scratch);
   const T* gx = f64 ? reinterpret_cast<const T*>(m->geox) : reinterpret_cast<const T*>(m->geox32);
   if (helm) e = gemm<T>(o.Mt1h, nE, 3 * Np, Np, o.Kt1, o.A1h, o.ea1h, u, Np, C1, ldc, nullptr, st);
   else e = gemm<T>(o.Mt1, nE, 2 * Np, Np, o.Kt1, o.A1, o.ea1, u, Np, C1, ldc, nullptr, st);
@@ -863,11 +885,24 @@ cudaError_t apply_tensor(dg_mesh* m, int degree, int B, double lambda, const T* 
 }  // namespace
 
 cudaError_t launch_apply_tensor(dg_mesh* m, int degree, bool f64, int B, double lambda, const void* u, void* Au,
-                                bool pipe, cudaStream_t st) {
+                                bool pipe, cudaStream_t st, double* c1_scratch) {
   if (f64)
     return apply_tensor<double>(m, degree, B, lambda, static_cast<const double*>(u), static_cast<double*>(Au), pipe,
-                                st);
-  return apply_tensor<float>(m, degree, B, lambda, static_cast<const float*>(u), static_cast<float*>(Au), pipe, st);
+                                st, c1_scratch);
+  return apply_tensor<float>(m, degree, B, lambda, static_cast<const float*>(u), static_cast<float*>(Au), pipe, st,
+                             c1_scratch);
+}
+
+bool tensor_ops_ready(int degree, bool f64) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  std::lock_guard<std::mutex> lk(table_mutex());
+  return g_oz[f64 ? 0 : 1][dev & 63][degree].A1 != nullptr;
+}
+
+cudaError_t ensure_tensor_ops(dg_mesh* m, int degree, bool f64) {
+  const OzOps* op = nullptr;
+  return f64 ? tensor_ops<double>(m, degree, &op) : tensor_ops<float>(m, degree, &op);
 }
 
 // A general FP64 operator for batched row products out[r] = A X[r] (the

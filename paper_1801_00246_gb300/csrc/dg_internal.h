@@ -6,6 +6,7 @@
 #include <cstdint>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -111,8 +112,11 @@ namespace dgx {
 
 // Launchers (device code in the .cu files). `degree` in 1..8.
 cudaError_t ensure_ops(dg_mesh* m, int degree);
+// c1_scratch (optional): device words for the tensor kernels' gradient rows,
+// at least B*K*Np(degree)*(lambda != 0 ? 3 : 2) + 1 of them (FP64 words; FP32
+// needs half); null uses the scratch kept with the mesh (grown on demand).
 cudaError_t launch_apply(const dg_mesh* m, int degree, dg_prec prec, int B, double lambda, const void* u,
-                         void* Au, cudaStream_t st);
+                         void* Au, cudaStream_t st, double* c1_scratch = nullptr);
 cudaError_t launch_rhs(const dg_mesh* m, int B, const double* f, const double* g, double* b, cudaStream_t st);
 cudaError_t launch_diagonal(const dg_mesh* m, int degree, dg_prec prec, double lambda, void* diag,
                             cudaStream_t st);
@@ -122,7 +126,11 @@ bool ept_supported(int degree);
 cudaError_t launch_apply_ept(dg_mesh* m, int degree, bool f64, int B, double lambda, const void* u, void* Au,
                              cudaStream_t st);
 cudaError_t launch_apply_tensor(dg_mesh* m, int degree, bool f64, int B, double lambda, const void* u, void* Au,
-                                bool pipe, cudaStream_t st);
+                                bool pipe, cudaStream_t st, double* c1_scratch = nullptr);
+// Builds (once per device, degree and precision) the tensor kernels' operator
+// slices on the current device; dg_mesh_setup calls it for the mesh degree.
+cudaError_t ensure_tensor_ops(dg_mesh* m, int degree, bool f64);
+bool tensor_ops_ready(int degree, bool f64);  // built on the current device (no build)
 cudaError_t tensor_pipe_error(int* flag);
 // FP64 operator A (M x K, row-major) sliced for the tensor-core products out[r] = A X[r]
 struct SlicedOp {
@@ -137,6 +145,10 @@ cudaError_t sliced_gemm(const SlicedOp& op, int64_t rows, const double* X, int64
 cudaError_t launch_nodes(const dg_mesh* m, int degree, double* x, double* y, cudaStream_t st);
 
 void set_error(const std::string& msg);
+
+// Guards the process-wide tables built on first use (operator slices, launch
+// configurations, constant-memory operators): every lazy build takes it.
+std::mutex& table_mutex();
 
 // Running count of kernels this library has launched (all devices, all threads).
 void note_launch();

@@ -33,6 +33,10 @@ cudaError_t poison(void* p, size_t bytes, int group) {
   return cudaMemset(p, 0xFF, bytes);
 }
 void set_error(const std::string& msg) { g_last_error = msg; }
+std::mutex& table_mutex() {
+  static std::mutex mu;
+  return mu;
+}
 const char* last_error() { return g_last_error.c_str(); }
 
 // Geometric factors per element: the affine map x = x0 + (x1-x0)(r+1)/2 +

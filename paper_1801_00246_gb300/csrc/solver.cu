@@ -1284,9 +1284,12 @@ static double* g_static_scratch_ptr[64] = {};  // device address, per device ord
 
 static size_t align32(size_t n) { return (n + 31) & ~size_t(31); }  // 256-byte steps
 
-size_t static_scratch_need(int64_t n, int B) {
+// Words of the fixed array one call uses: r, z, p, Ap, the Jacobi inverse, the
+// per-right-hand-side scalars and reduction partials, and the gradient rows of
+// the tensor-core apply (2 Np per element, 3 Np with lambda != 0).
+size_t static_scratch_need(int64_t n, int B, bool helm) {
   return 4 * align32(size_t(n) * B) + align32(size_t(n)) + align32(size_t(B) * kNS) +
-         align32(size_t(B) * kRedBlocks * 2);
+         align32(size_t(B) * kRedBlocks * 2) + align32(size_t(n) * B * (helm ? 3 : 2) + 1);
 }
 
 }  // namespace dgx
@@ -1300,11 +1303,11 @@ extern "C" dg_status dg_pcg_jacobi_solve_static(const dg_mesh* mc, int B, double
   if (!std::isfinite(lambda) || lambda < 0) { set_error("lambda must be finite and >= 0"); return DG_ERR_ARG; }
   dg_mesh* m = const_cast<dg_mesh*>(mc);
   const int64_t n = int64_t(m->K) * npd(m->N);
-  const size_t need = static_scratch_need(n, B);
+  const size_t need = static_scratch_need(n, B, lambda != 0.0);
   if (need > kStaticScratchDoubles) {
     set_error("dg_pcg_jacobi_solve_static: problem needs " + std::to_string(need) +
               " scratch doubles, the static array holds " + std::to_string(kStaticScratchDoubles) +
-              " (B*K*Np must stay below about 838,000)");
+              " (at B = 1, K*Np must stay below about 599,000 for lambda = 0 and 524,000 otherwise)");
     return DG_ERR_ARG;
   }
   if (!m->ops64[m->N].buf) { set_error("mesh operators missing"); return DG_ERR_ARG; }
@@ -1315,16 +1318,30 @@ extern "C" dg_status dg_pcg_jacobi_solve_static(const dg_mesh* mc, int B, double
     set_error(std::string("dg_pcg_jacobi_solve_static: cudaGetDevice: ") + cudaGetErrorString(ce));
     return DG_ERR_CUDA;
   }
-  if (!g_static_scratch_ptr[dev]) {  // one-time set-up on this device (before any stream capture)
-    void* p = nullptr;
-    ce = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (ce != cudaSuccess) {
-      set_error(std::string("dg_pcg_jacobi_solve_static: cudaGetSymbolAddress: ") + cudaGetErrorString(ce));
-      return DG_ERR_CUDA;
+  // the tensor-core apply's operator slices are built by dg_mesh_setup on the
+  // mesh's device; building them here would allocate
+  {
+    int kf = m->kern[m->N][0][lambda != 0.0 ? 1 : 0];
+    if (kf == DG_KERNEL_AUTO) kf = default_kernel(m->N, true);
+    if ((kf == DG_KERNEL_TENSOR || kf == DG_KERNEL_TENSOR_PIPE) && !tensor_ops_ready(m->N, true)) {
+      set_error("dg_pcg_jacobi_solve_static: the current device is not the one the mesh was set up on");
+      return DG_ERR_ARG;
     }
-    g_static_scratch_ptr[dev] = static_cast<double*>(p);
   }
-  double* base = g_static_scratch_ptr[dev];
+  double* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(table_mutex());
+    if (!g_static_scratch_ptr[dev]) {  // one-time set-up on this device (before any stream capture)
+      void* sp = nullptr;
+      ce = cudaGetSymbolAddress(&sp, g_static_scratch);
+      if (ce != cudaSuccess) {
+        set_error(std::string("dg_pcg_jacobi_solve_static: cudaGetSymbolAddress: ") + cudaGetErrorString(ce));
+        return DG_ERR_CUDA;
+      }
+      g_static_scratch_ptr[dev] = static_cast<double*>(sp);
+    }
+    base = g_static_scratch_ptr[dev];
+  }
   const size_t nt = size_t(n) * B;
   double* r = base;
   double* z = r + align32(nt);
@@ -1333,6 +1350,7 @@ extern "C" dg_status dg_pcg_jacobi_solve_static(const dg_mesh* mc, int B, double
   double* dinv = Ap + align32(nt);
   double* scal = dinv + align32(size_t(n));
   double* partial = scal + align32(size_t(B) * kNS);
+  double* c1 = partial + align32(size_t(B) * kRedBlocks * 2);  // the apply's gradient rows
   const dim3 g = vgrid(n, B);
 #define SCK(expr)                                                                          \
   do {                                                                                     \
@@ -1349,7 +1367,7 @@ extern "C" dg_status dg_pcg_jacobi_solve_static(const dg_mesh* mc, int B, double
   k_init_scal<<<1, 64, 0, st>>>(B, scal, tol * tol); note_launch();
   k_dot<<<g, kRedThreads, 0, st>>>(n, b, b, partial); note_launch();
   k_finalize<<<B, kRedThreads, 0, st>>>(FIN_INIT_BB, scal, partial); note_launch();
-  SCK(launch_apply(m, m->N, DG_F64, B, lambda, x, Ap, st));
+  SCK(launch_apply(m, m->N, DG_F64, B, lambda, x, Ap, st, c1));
   k_sub<double><<<egrid(nt), 256, 0, st>>>(nt, b, Ap, r); note_launch();
   k_dot<<<g, kRedThreads, 0, st>>>(n, r, r, partial); note_launch();
   k_init_check<<<B, kRedThreads, 0, st>>>(scal, partial); note_launch();
@@ -1364,7 +1382,7 @@ extern "C" dg_status dg_pcg_jacobi_solve_static(const dg_mesh* mc, int B, double
   for (int k = 0; k < B; ++k) any = any || hs[k * kNS + S_ACTIVE] != 0.0;
   int it = 0;
   while (any && it < max_iter) {
-    SCK(launch_apply(m, m->N, DG_F64, B, lambda, p, Ap, st));
+    SCK(launch_apply(m, m->N, DG_F64, B, lambda, p, Ap, st, c1));
     k_dot<<<g, kRedThreads, 0, st>>>(n, p, Ap, partial); note_launch();
     k_finalize<<<B, kRedThreads, 0, st>>>(FIN_ALPHA, scal, partial); note_launch();
     k_update_xr<<<g, kRedThreads, 0, st>>>(n, scal, x, r, p, Ap, nullptr, partial); note_launch();
