@@ -87,9 +87,14 @@ typedef struct dg_mesh dg_mesh; /* opaque; owned by the library until dg_mesh_de
  *   DG_KERNEL_EPT:    one element per thread, operators in constant memory; degrees 1-3
  *   DG_KERNEL_TENSOR_PIPE: DG_KERNEL_TENSOR with the output product's fill and product
  *                     phases on separate warps, double-buffered through shared memory
- *                     (mbarrier hand-off with bounded waits; see dg_tensor_timeouts) */
+ *                     (mbarrier hand-off with bounded waits; see dg_tensor_timeouts)
+ *   DG_KERNEL_TC05:   FP32 only: both products on the Blackwell tensor cores (tcgen05,
+ *                     operands and accumulators in tensor memory, bulk copies), two FP16
+ *                     pieces per operand scaled by powers of two; all degrees. Needs u and
+ *                     Au 16-byte aligned (otherwise DG_KERNEL_TENSOR runs instead). */
 enum { DG_KERNEL_AUTO = 0, DG_KERNEL_TILE = 1, DG_KERNEL_GEMM = 2, DG_KERNEL_TENSOR = 3, DG_KERNEL_EPT = 4,
-       DG_KERNEL_TENSOR_PIPE = 5 };
+       DG_KERNEL_TENSOR_PIPE = 5, DG_KERNEL_TC05 = 6 };
+#define DG_NUM_KERNELS 7 /* kernel ids 0..6; dg_autotune's times use this many slots per entry */
 
 /* Preconditioner choices for dg_pcg_solve (Section 3). */
 enum { DG_PREC_NONE = 0, DG_PREC_JACOBI = 1, DG_PREC_INVMASS = 2, DG_PREC_PMG = 3 };
@@ -185,7 +190,7 @@ int dg_get_apply_kernel(const dg_mesh* mesh, int degree, dg_prec prec, int helmh
  * (256 MB L2 flush before each of three timed launches, best kept), for the
  * Poisson form and, if lambda > 0, the Helmholtz form (with lambda = 0 the
  * Helmholtz entry takes the Poisson winner), and stores the fastest in the
- * kernel table. times (host, may be NULL): float[9][2][2][6] milliseconds
+ * kernel table. times (host, may be NULL): float[9][2][2][DG_NUM_KERNELS] milliseconds
  * indexed [degree][0: FP64, 1: FP32][helmholtz][kernel], 0 where not timed.
  * Allocates and frees its own scratch (4 fields of B*K*Np(degree_hi) values
  * plus 256 MB); synchronises `stream`. Solves captured as CUDA graphs before

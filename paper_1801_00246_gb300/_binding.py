@@ -8,7 +8,8 @@ from . import build as _build
 
 DG_F64, DG_F32, DG_F64_DFMA = 0, 1, 2
 PREC_NONE, PREC_JACOBI, PREC_INVMASS, PREC_PMG = 0, 1, 2, 3
-KERNEL_AUTO, KERNEL_TILE, KERNEL_GEMM, KERNEL_TENSOR, KERNEL_EPT, KERNEL_TENSOR_PIPE = 0, 1, 2, 3, 4, 5
+KERNEL_AUTO, KERNEL_TILE, KERNEL_GEMM, KERNEL_TENSOR, KERNEL_EPT, KERNEL_TENSOR_PIPE, KERNEL_TC05 = 0, 1, 2, 3, 4, 5, 6
+NUM_KERNELS = 7
 DG_MAX_BATCH = 64
 
 _STATUS = {0: "DG_OK", 1: "DG_ERR_ARG", 2: "DG_ERR_CUDA", 3: "DG_ERR_OOM", 4: "DG_ERR_NOT_CONVERGED",
@@ -215,14 +216,14 @@ class Mesh:
         """Time every available kernel per degree and precision on this mesh and
         keep the fastest; returns {(degree, 'f64'|'f32', helmholtz): {kernel: ms}}."""
         lo, hi = degrees if degrees is not None else (1, self.N)
-        times = (ctypes.c_float * (9 * 2 * 2 * 6))()
+        times = (ctypes.c_float * (9 * 2 * 2 * NUM_KERNELS))()
         _check(lib().dg_autotune(self._h, int(B), float(lam), int(lo), int(hi), times, _stream()))
         out = {}
         for d in range(lo, hi + 1):
             for p, name in ((0, "f64"), (1, "f32")):
                 for h in (0, 1):
-                    row = {k: times[((d * 2 + p) * 2 + h) * 6 + k] for k in range(1, 6)
-                           if times[((d * 2 + p) * 2 + h) * 6 + k] > 0}
+                    base = ((d * 2 + p) * 2 + h) * NUM_KERNELS
+                    row = {k: times[base + k] for k in range(1, NUM_KERNELS) if times[base + k] > 0}
                     if row:
                         out[(d, name, h)] = row
         return out

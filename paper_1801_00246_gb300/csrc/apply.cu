@@ -397,6 +397,7 @@ bool kernel_valid(int kernel, int degree, bool f64) {
     case DG_KERNEL_TENSOR: return true;
     case DG_KERNEL_TENSOR_PIPE: return true;
     case DG_KERNEL_EPT: return ept_supported(degree);
+    case DG_KERNEL_TC05: return !f64;
     default: return false;
   }
 }
@@ -416,6 +417,11 @@ cudaError_t launch_apply(const dg_mesh* mc, int degree, dg_prec prec, int B, dou
   const bool f64 = prec == DG_F64;
   if (!kernel_valid(k, degree, f64)) return cudaErrorInvalidValue;
   if (k == DG_KERNEL_EPT) return launch_apply_ept(m, degree, f64, B, lambda, u, Au, st);
+  if (k == DG_KERNEL_TC05) {
+    if (tc05_usable(u, Au))
+      return launch_apply_tc05(m, degree, B, lambda, static_cast<const float*>(u), static_cast<float*>(Au), st);
+    k = DG_KERNEL_TENSOR;  // unaligned fields: the mma.sync tensor kernel takes them
+  }
   if (k == DG_KERNEL_TENSOR || k == DG_KERNEL_TENSOR_PIPE)
     return launch_apply_tensor(m, degree, f64, B, lambda, u, Au, k == DG_KERNEL_TENSOR_PIPE, st, c1_scratch);
   if (k == DG_KERNEL_GEMM) {

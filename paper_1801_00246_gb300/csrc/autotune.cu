@@ -28,7 +28,8 @@ __global__ void k_fill_uniform(int64_t n, uint64_t seed, double* __restrict__ a,
   }
 }
 
-constexpr int kCandidates[] = {DG_KERNEL_TILE, DG_KERNEL_GEMM, DG_KERNEL_TENSOR, DG_KERNEL_EPT, DG_KERNEL_TENSOR_PIPE};
+constexpr int kCandidates[] = {DG_KERNEL_TILE, DG_KERNEL_GEMM, DG_KERNEL_TENSOR, DG_KERNEL_EPT, DG_KERNEL_TENSOR_PIPE,
+                               DG_KERNEL_TC05};
 
 struct Scratch {
   void* p[5] = {};
@@ -59,8 +60,9 @@ dg_status dg_set_apply_kernel(dg_mesh* m, int degree, dg_prec prec, int helmholt
 }
 
 int dg_tensor_timeouts(void) {
-  int flag = 0;
-  return tensor_pipe_error(&flag) == cudaSuccess ? flag : -1;
+  int flag = 0, flag05 = 0;
+  if (tensor_pipe_error(&flag) != cudaSuccess || tc05_error(&flag05) != cudaSuccess) return -1;
+  return flag + flag05;
 }
 
 int dg_get_apply_kernel(const dg_mesh* m, int degree, dg_prec prec, int helmholtz) {
@@ -126,7 +128,7 @@ dg_status dg_autotune(dg_mesh* m, int B, double lambda, int degree_lo, int degre
               if (e == cudaSuccess && ms < ms_min) ms_min = ms;
             }
             if (e != cudaSuccess) break;
-            if (times) times[((d * 2 + p) * 2 + h) * 6 + k] = ms_min;
+            if (times) times[((d * 2 + p) * 2 + h) * DG_NUM_KERNELS + k] = ms_min;
             if (ms_min < best_ms) {
               best_ms = ms_min;
               best = k;

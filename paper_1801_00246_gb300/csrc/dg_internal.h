@@ -132,6 +132,11 @@ cudaError_t launch_apply_tensor(dg_mesh* m, int degree, bool f64, int B, double 
 cudaError_t ensure_tensor_ops(dg_mesh* m, int degree, bool f64);
 bool tensor_ops_ready(int degree, bool f64);  // built on the current device (no build)
 cudaError_t tensor_pipe_error(int* flag);
+// FP32 apply on the tcgen05 tensor cores (apply_tc05.cu); needs 16-byte aligned u and Au
+bool tc05_usable(const void* u, const void* Au);
+cudaError_t launch_apply_tc05(dg_mesh* m, int degree, int B, double lambda, const float* u, float* Au,
+                              cudaStream_t st);
+cudaError_t tc05_error(int* flag);  // reads and clears the tcgen05 kernels' timeout flag
 // FP64 operator A (M x K, row-major) sliced for the tensor-core products out[r] = A X[r]
 struct SlicedOp {
   int M = 0, K = 0, Mt = 0, Kt = 0;
