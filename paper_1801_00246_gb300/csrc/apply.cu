@@ -387,7 +387,7 @@ DG_TE_DECL(1) DG_TE_DECL(2) DG_TE_DECL(3) DG_TE_DECL(4) DG_TE_DECL(5) DG_TE_DECL
 // 524,288-triangle workload; dg_autotune replaces them per mesh).
 int default_kernel(int degree, bool f64) {
   if (f64) return degree >= 3 ? DG_KERNEL_TENSOR : DG_KERNEL_EPT;
-  return degree <= 3 ? DG_KERNEL_EPT : (degree == 4 ? DG_KERNEL_GEMM : DG_KERNEL_TENSOR);
+  return degree <= 3 ? DG_KERNEL_EPT : DG_KERNEL_TC05;
 }
 
 bool kernel_valid(int kernel, int degree, bool f64) {

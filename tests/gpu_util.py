@@ -35,3 +35,25 @@ def rel(a, b):
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def abs_bound(ora, u, lam=0.0):
+    """(|A| |u|)_i per node: the scale against which a sliced or piecewise
+    product's rounding is bounded entry by entry (small meshes: assembles A)."""
+    A = ora.assemble(lam)
+    A.data = np.abs(A.data)
+    U = np.asarray(u, dtype=np.float64)
+    if U.ndim == 3:
+        return np.stack([(A @ np.abs(Ub).ravel()).reshape(Ub.shape) for Ub in U])
+    return (A @ np.abs(U).ravel()).reshape(U.shape)
+
+
+def max_entry_err(got, ref, bound):
+    """max_i |got_i - ref_i| / bound_i (entries with a zero bound must match exactly)."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    d = np.abs(got - ref)
+    zero = bound == 0
+    if np.any(d[zero] != 0):
+        return float("inf")
+    return float(np.max(d[~zero] / bound[~zero])) if np.any(~zero) else 0.0

@@ -74,12 +74,17 @@ def test_c3_kovasznay_100_steps_8192tri_N8():
     assert max(out["vel_iters"]) < 60 and out["pr_iters"] < 100
 
 
-@pytest.mark.parametrize("N,sides", [(2, (1, 1, 1, 1)), (2, (1, 2, 1, 1)), (3, (1, 2, 1, 1)), (5, (1, 2, 1, 1))])
+@pytest.mark.parametrize("N,sides", [(2, (1, 1, 1, 1)), (2, (1, 2, 1, 1)), (3, (1, 2, 1, 1)), (5, (1, 2, 1, 1)),
+                                     (8, (1, 1, 1, 1)), (8, (1, 2, 1, 1))])
 def test_ins_parity_outflow_and_both_advection_paths(N, sides):
     """Degrees 1-2 advect with the fused FP64 kernel, degrees from 3 with the
-    tensor-core stages; an outflow side (velocity Neumann at x = 1 where the
-    pressure is Dirichlet) takes the Neumann branches of the advection flux,
-    the divergence and the velocity Helmholtz operator."""
+    tensor-core stages (N = 8 is the Kovasznay workload's degree, with its own
+    169-point cubature shapes); an outflow side (velocity Neumann at x = 1 where
+    the pressure is Dirichlet) takes the Neumann branches of the advection flux,
+    the divergence and the velocity Helmholtz operator. Both sides solve to a
+    relative residual of 1e-13; the pressure increment's condition number
+    (about 1e5 on these meshes) leaves differences near 1e-8 in P and 1e-9 in U,
+    which is what the tolerances allow."""
     from oracle.ins import InsOracle
     from oracle.sipdg import Sipdg
     m = rotate_local_vertices(jittered_grid(5, 5, box=(-0.5, 1.0, -0.5, 1.5), jitter=0.1, seed=2,

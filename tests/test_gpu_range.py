@@ -1,0 +1,130 @@
+"""Entry-by-entry parity of every apply kernel, and the magnitude range of the
+scaled products.
+
+The sliced and piecewise products scale each element's data by its own power
+of two; their rounding is bounded, node by node, by a multiple of
+(|A| |u|)_i. These tests assert that bound at every node (beside the 2-norm
+checks of the other files) on fields whose element magnitudes differ by up to
+2^120 between neighbours, with all-zero elements, and (FP64) with elements
+near the documented 1e-250 / 1e250 limits."""
+import numpy as np
+import pytest
+
+from dg_inputs import jittered_grid, uniform_field
+from dg_inputs.mesh import rotate_local_vertices
+from tests.gpu_util import abs_bound, cuda, max_entry_err, pair, pkg, rel
+
+pytestmark = pytest.mark.gpu
+
+# entry-wise bounds: FP64 kernels near 2^-44 of |A||u|, FP32 kernels near 2^-21
+BOUND64, BOUND32 = 1e-12, 1e-5
+
+
+def _kernels(P, N, f64):
+    ks = [P.KERNEL_TILE, P.KERNEL_TENSOR, P.KERNEL_TENSOR_PIPE] + ([] if f64 else [P.KERNEL_GEMM, P.KERNEL_TC05])
+    if N <= 3:
+        ks.append(P.KERNEL_EPT)
+    return ks
+
+
+def _scaled_field(K, Np, seed, exps):
+    """U(-1, 1) values, element e scaled by 2^{exps[e]}."""
+    u = uniform_field((K, Np), seed=seed)
+    return u * np.exp2(np.asarray(exps, dtype=np.float64))[:, None]
+
+
+def _check_all_kernels(lib, ora, u, f64, N, lam):
+    import torch
+    P = pkg()
+    ref = ora.apply(u, lam=lam)
+    bnd = abs_bound(ora, u, lam)
+    prec = P.DG_F64 if f64 else P.DG_F32
+    x = cuda(u) if f64 else cuda(u, torch.float32)
+    out = {}
+    for k in _kernels(P, N, f64):
+        lib.set_kernel(N, prec, lam != 0.0, k)
+        got = lib.apply(x, lam=lam).cpu().numpy()
+        assert P.lib().dg_tensor_timeouts() == 0
+        out[k] = max_entry_err(got, ref, bnd)
+    lib.set_kernel(N, prec, lam != 0.0, P.KERNEL_AUTO)
+    return out
+
+
+@pytest.mark.parametrize("N", range(1, 9))
+def test_entrywise_bound_every_kernel(N):
+    m = rotate_local_vertices(jittered_grid(5, 6, jitter=0.1, seed=7, bc_sides=(1, 2, 1, 2)), N)
+    lib, ora = pair(m, N)
+    u = uniform_field((m.K, ora.Np), seed=40 + N)
+    for lam in (0.0, 2.0):
+        for f64 in (True, False):
+            errs = _check_all_kernels(lib, ora, u, f64, N, lam)
+            assert max(errs.values()) <= (BOUND64 if f64 else BOUND32), (N, lam, f64, errs)
+
+
+@pytest.mark.parametrize("N", [3, 5, 8])
+def test_fp64_neighbours_2_to_the_60_apart_and_zero_elements(N):
+    """Element magnitudes 2^-60, 1 or 2^60 at random, every tenth element zero."""
+    m = rotate_local_vertices(jittered_grid(6, 6, jitter=0.1, seed=3), 2)
+    lib, ora = pair(m, N)
+    rng = np.random.default_rng(N)
+    exps = rng.choice([-60.0, 0.0, 60.0], size=m.K)
+    u = _scaled_field(m.K, ora.Np, 50 + N, exps)
+    u[::10] = 0.0
+    for lam in (0.0, 1.5):
+        errs = _check_all_kernels(lib, ora, u, True, N, lam)
+        assert max(errs.values()) <= BOUND64, (lam, errs)
+
+
+@pytest.mark.parametrize("N", [4, 8])
+def test_fp64_near_the_documented_magnitude_limits(N):
+    """One element near 1e250 and one near 1e-250 among O(1) elements."""
+    m = rotate_local_vertices(jittered_grid(5, 5, jitter=0.1, seed=5), 1)
+    lib, ora = pair(m, N)
+    exps = np.zeros(m.K)
+    exps[7] = np.log2(1e250)
+    exps[31] = np.log2(1e-250)
+    u = _scaled_field(m.K, ora.Np, 60 + N, exps)
+    errs = _check_all_kernels(lib, ora, u, True, N, 0.0)
+    assert max(errs.values()) <= BOUND64, errs
+    # the tiny element's own rows, where its neighbours are O(1): still bounded entry by entry
+    assert np.isfinite(list(errs.values())).all()
+
+
+@pytest.mark.parametrize("N", [2, 5, 8])
+def test_fp32_neighbours_2_to_the_20_apart_and_zero_elements(N):
+    m = rotate_local_vertices(jittered_grid(6, 5, jitter=0.1, seed=4), 3)
+    lib, ora = pair(m, N)
+    rng = np.random.default_rng(100 + N)
+    exps = rng.choice([-20.0, 0.0, 20.0], size=m.K)
+    u = _scaled_field(m.K, ora.Np, 70 + N, exps)
+    u[::9] = 0.0
+    u = u.astype(np.float32).astype(np.float64)  # the FP32 input the kernels see
+    for lam in (0.0, 1.5):
+        errs = _check_all_kernels(lib, ora, u, False, N, lam)
+        assert max(errs.values()) <= BOUND32, (lam, errs)
+
+
+def test_c5_mixed_solve_true_residual_and_sampled_oracle():
+    """The headline solve (524,288 triangles, N=8, p-multigrid 8->4->2->1 in
+    FP32, FP64 outer iteration, as the benchmark runs it): ||b - A x|| / ||b||
+    recomputed with the FP64-pipe tile kernel is at most 1e-10, and that
+    kernel's A x agrees with the oracle on sampled elements."""
+    from dg_inputs import config_mesh, manufactured
+    P = pkg()
+    m, _ = config_mesh("c5_sweep_524288tri_N8")
+    lib, ora = pair(m, 8)
+    uex, fex = manufactured("sin_2pi_x_cos_3pi_y")
+    x_n, y_n = lib.nodes()
+    xh, yh = x_n.cpu().numpy(), y_n.cpu().numpy()
+    b = lib.rhs(cuda(fex(xh, yh)), cuda(uex(xh, yh)))
+    opts = P._binding.default_opts(precond=P.PREC_PMG, degrees=[8, 4, 2, 1], tol=1e-10, max_iter=200, mixed=1,
+                                   cheb_degree=3, coarse_tol=1e-2, coarse_max_iter=1, coarse_amg=1)
+    x, info = lib.solve(b, opts=opts)
+    assert info["relres"][0] <= 1e-10
+    Ax = lib.apply(x, fp64_pipe=True)
+    true_rel = float((b - Ax).norm() / b.norm())
+    assert true_rel <= 1e-10, true_rel
+    rng = np.random.default_rng(3)
+    elems = np.unique(np.concatenate([rng.integers(0, m.K, 150), [0, m.K - 1]]))
+    ref = ora.apply(x.cpu().numpy(), elems=elems)
+    assert rel(Ax.cpu().numpy()[elems], ref) <= 1e-12
