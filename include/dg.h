@@ -307,6 +307,15 @@ dg_status dg_interpolation_matrix(int Nf, int Nc, double* P);
  * -1 if the device could not be queried. No counterpart in the paper. */
 int dg_tensor_timeouts(void);
 
+/* Diagnostic with no counterpart in the paper: launches one kernel whose
+ * warp waits, with the bounded mbarrier wait every tensor-core kernel of the
+ * library uses, on a barrier phase that nothing completes. The wait gives up
+ * after `seconds` (0 < seconds <= 10), the kernel counts one timeout in
+ * dg_tensor_timeouts and returns, and the call returns DG_ERR_TIMEOUT: a
+ * device-side wait that cannot finish ends its kernel instead of hanging the
+ * GPU, and the context stays usable. Synchronises `stream`. */
+dg_status dg_wait_selftest(double seconds, void* stream);
+
 /* Number of kernels this library has launched since it was loaded (all
  * devices and threads); a diagnostic for counting launches in a timed region. */
 uint64_t dg_launch_count(void);

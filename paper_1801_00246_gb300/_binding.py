@@ -85,6 +85,7 @@ def lib():
         "dg_get_apply_kernel": ([vp, i32, i32, i32], i32),
         "dg_autotune": ([vp, i32, dbl, i32, i32, ctypes.POINTER(ctypes.c_float), vp], i32),
         "dg_tensor_timeouts": ([], i32),
+        "dg_wait_selftest": ([dbl, vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)

@@ -83,7 +83,8 @@ struct Tc {
   static constexpr int smA = smA_bar + 8 * 8;
   // shared memory of tc_face
   static constexpr int smF_ut = rup128(opsF);
-  static constexpr int smF_bar = smF_ut + 2 * utile;
+  static constexpr int smF_stg = smF_ut + 2 * utile;       // [kTile][NFN] float2 face data
+  static constexpr int smF_bar = smF_stg + rup128(kTile * NFN * 8);
   static constexpr int smF = smF_bar + 8 * 8;
 };
 
@@ -96,16 +97,23 @@ __device__ __forceinline__ int fnode(int N, int f, int j) {
   return f == 0 ? j : (f == 1 ? rs(j) + (N - j) : rs(N - j));
 }
 
-__device__ __forceinline__ uint32_t h2bits(__half h) { return uint32_t(__half_as_ushort(h)); }
-
 // FP16 pieces of a pair of scaled values: hi = fp16(x), lo = fp16(x - hi);
 // k even in the low half of the 32-bit column, k odd in the high half
 __device__ __forceinline__ void split_pair(float a, float b, uint32_t& hi, uint32_t& lo) {
-  const __half ah = __float2half_rn(a), bh = __float2half_rn(b);
-  const __half al = __float2half_rn(a - __half2float(ah)), bl = __float2half_rn(b - __half2float(bh));
-  hi = h2bits(ah) | (h2bits(bh) << 16);
-  lo = h2bits(al) | (h2bits(bl) << 16);
+  const __half2 h = __floats2half2_rn(a, b);
+  const float2 hf = __half22float2(h);
+  const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
 }
+
+// Scale exponent for a row whose largest magnitude is mx: 2^s mx < 2^14 (and
+// FP16 range). Clamped to 127, so rows below about 1e-34 keep fewer bits.
+__device__ __forceinline__ int scale_exp(float mx) {
+  const int em = tc::exp_of(mx);
+  return em == -200 ? 0 : min(14 - em, 127);
+}
+__device__ __forceinline__ float pow2f(int s) { return __int_as_float((127 + s) << 23); }  // s in [-126, 127]
 
 // one bulk copy of the element rows [e0, e0 + ne) of u into a tile buffer, armed on
 // `bar`; bytes beyond the last multiple of 16 are left to plain loads (fix_tail)
@@ -122,7 +130,8 @@ __device__ __forceinline__ void fix_tail(const float* u, int Np, int64_t e0, int
 
 // -------------------------------------------------------------------------------
 // Face data: FN[be][f][j] = (u, n.grad u) at face node j of face f (counter-clockwise),
-// with the element's own outward normal.
+// with the element's own outward normal. One thread per element; the tile's
+// face data go through shared memory to coalesced stores.
 template <int N>
 __global__ void __launch_bounds__(kTile) tc_face(int64_t K, int64_t nE, const float* __restrict__ gx,
                                                  const float* __restrict__ u, const uint8_t* __restrict__ opsF,
@@ -133,6 +142,7 @@ __global__ void __launch_bounds__(kTile) tc_face(int64_t K, int64_t nE, const fl
   const uint8_t* sBF = sm;
   const float* iscF = reinterpret_cast<const float*>(sm + 2 * S::szBF);
   float* ut = reinterpret_cast<float*>(sm + S::smF_ut);
+  float2* stg = reinterpret_cast<float2*>(sm + S::smF_stg);  // [kTile][NFN]
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + S::smF_bar);  // op, u0, u1, mma
   uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 4);
   int* abort_flag = reinterpret_cast<int*>(slot + 1);
@@ -165,6 +175,16 @@ __global__ void __launch_bounds__(kTile) tc_face(int64_t K, int64_t nE, const fl
     const int64_t e0 = tile * kTile;
     const int ne = tile_len(nE, e0);
     float* cur = ut + buf * (kTile * Np);
+    const int e = tid;
+    const bool live = e < ne;
+    const int64_t el = (e0 + e) % K;
+    // the face normals, loaded while the tile and the products are in flight
+    float nrm[6];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      nrm[2 * f] = live ? __ldg(gx + 16 * el + 4 + 4 * f) : 0.f;
+      nrm[2 * f + 1] = live ? __ldg(gx + 16 * el + 5 + 4 * f) : 0.f;
+    }
     if (!tc::mbar_wait(bars + 1 + buf, (it >> 1) & 1)) *abort_flag = 1;
     if (tid == 0 && tile + gridDim.x < ntiles) {
       const int64_t e1 = (tile + gridDim.x) * kTile;
@@ -173,26 +193,25 @@ __global__ void __launch_bounds__(kTile) tc_face(int64_t K, int64_t nE, const fl
     if (ne < kTile) fix_tail(u, Np, e0, ne, cur);
     __syncthreads();
     if (*abort_flag) break;
-    const int e = tid;
-    const bool live = e < ne;
     const float* urow = cur + e * Np;
     // FP16 pieces of the element's scaled u row into tensor memory
-    int emax = -200;
+    float mx = 0.f;
     if (live)
-      for (int k = 0; k < Np; ++k) emax = max(emax, tc::exp_of(urow[k]));
-    const int s1 = emax == -200 ? 0 : 14 - emax;
+      for (int k = 0; k < Np; ++k) mx = fmaxf(mx, fabsf(urow[k]));
+    const int s1 = scale_exp(mx);
+    const float f1 = pow2f(s1);
 #pragma unroll
     for (int c0 = 0; c0 < K1 / 2; c0 += 8) {
       uint32_t hi[8], lo[8];
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
         const int k = 2 * (c0 + c);
-        const float a = (live && k < Np) ? tc::ldexp2(urow[k], s1) : 0.f;
-        const float b = (live && k + 1 < Np) ? tc::ldexp2(urow[k + 1], s1) : 0.f;
+        const float a = (live && k < Np) ? urow[k] * f1 : 0.f;
+        const float b = (live && k + 1 < Np) ? urow[k + 1] * f1 : 0.f;
         split_pair(a, b, hi[c], lo[c]);
       }
-      tc::tmem_st8(tb + lanebase + S::oA1 + c0, hi);
-      tc::tmem_st8(tb + lanebase + S::oA1 + K1 / 2 + c0, lo);
+      tc::tmem_st8(tb + lanebase + c0, hi);
+      tc::tmem_st8(tb + lanebase + K1 / 2 + c0, lo);
     }
     tc::tmem_wait_st();
     tc::fence_before();
@@ -224,23 +243,32 @@ __global__ void __launch_bounds__(kTile) tc_face(int64_t K, int64_t nE, const fl
       for (int c = 0; c < 8; ++c) d[c0 + c] = v[c];
     }
     tc::tmem_wait_ld();
-    if (live && !*abort_flag) {
-      const int64_t be = e0 + e;
-      const int64_t el = be % K;
-      const float* g = gx + 16 * el;
+    if (live) {
       const float isc = tc::ldexp2(1.0f, -s1);
 #pragma unroll
       for (int f = 0; f < 3; ++f) {
-        const float nr = __ldg(g + 4 + 4 * f), ns = __ldg(g + 5 + 4 * f);
 #pragma unroll
         for (int j = 0; j < Nfp; ++j) {
           const int rr = f * Nfp + j;
           const float dr = __uint_as_float(d[rr]) * iscF[rr];
           const float ds = __uint_as_float(d[NFN + rr]) * iscF[NFN + rr];
-          FN[be * NFN + rr] = make_float2(urow[fnode(N, f, j)], (nr * dr + ns * ds) * isc);
+          stg[e * NFN + rr] = make_float2(urow[fnode(N, f, j)], (nrm[2 * f] * dr + nrm[2 * f + 1] * ds) * isc);
         }
       }
     }
+    __syncthreads();
+    {
+      const int n = ne * NFN;  // float2 entries of the tile, contiguous in FN
+      float2* dst = FN + e0 * NFN;
+      if ((n & 1) == 0 && ((e0 * NFN) & 1) == 0) {
+        const float4* s4 = reinterpret_cast<const float4*>(stg);
+        float4* d4 = reinterpret_cast<float4*>(dst);
+        for (int i = tid; i < n / 2; i += kTile) d4[i] = s4[i];
+      } else {
+        for (int i = tid; i < n; i += kTile) dst[i] = stg[i];
+      }
+    }
+    tc::fence_async_smem();
     tc::fence_before();
     __syncthreads();
   }
@@ -252,6 +280,84 @@ __global__ void __launch_bounds__(kTile) tc_face(int64_t K, int64_t nE, const fl
 }
 
 // -------------------------------------------------------------------------------
+// The face columns of one face f for the element: Y[base + j], Y[base + Nfp + j],
+// Y[base + 2 Nfp + j] from the element's own gradient at the face nodes (dr, ds:
+// tensor-memory words), its trace, and the neighbour's face data p.
+template <int N, int BASE, int YN>
+__device__ __forceinline__ void face_columns(float (&y)[YN], const uint32_t (&dr)[N + 1], const uint32_t (&ds)[N + 1],
+                                             const float2 (&p)[N + 1], int f, int code, const float* g,
+                                             const float* urow, const float* isc1, float iu, float cpen) {
+  constexpr int Np = (N + 1) * (N + 2) / 2, Nfp = N + 1;
+  const float nr = __ldg(g + 4 + 4 * f), ns = __ldg(g + 5 + 4 * f), sJ = __ldg(g + 6 + 4 * f);
+  const float tau = cpen * __ldg(g + 7 + 4 * f);
+#pragma unroll
+  for (int j = 0; j < Nfp; ++j) {
+    const int kf = fnode(N, f, j);
+    const float um = urow[kf];
+    const float dnm = (nr * (__uint_as_float(dr[j]) * isc1[kf]) + ns * (__uint_as_float(ds[j]) * isc1[Np + kf])) * iu;
+    float jm = 0.f, av = 0.f;
+    if (code >= 0) {
+      jm = p[j].x - um;
+      av = 0.5f * (dnm - p[j].y);
+    } else if (code == -2) {  // Dirichlet
+      jm = -2.f * um;
+      av = dnm;
+    }
+    const float hs = 0.5f * sJ * jm;
+    y[BASE + j] = nr * hs;
+    y[BASE + Nfp + j] = ns * hs;
+    y[BASE + 2 * Nfp + j] = -sJ * (av + tau * jm);
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void load_face(uint32_t tb, uint32_t lanebase, int oD1, int f, uint32_t (&dr)[N + 1],
+                                          uint32_t (&ds)[N + 1]) {
+  constexpr int Np = (N + 1) * (N + 2) / 2;
+#pragma unroll
+  for (int j = 0; j <= N; ++j) {
+    const int kf = fnode(N, f, j);
+    tc::tmem_ld1(tb + lanebase + oD1 + kf, dr[j]);
+    tc::tmem_ld1(tb + lanebase + oD1 + Np + kf, ds[j]);
+  }
+}
+
+// neighbour's face data across face f in the element's own node order
+template <int N>
+__device__ __forceinline__ void load_nb(const float2* FN, int64_t boff, int code, bool live, float2 (&p)[N + 1]) {
+  constexpr int Nfp = N + 1, NFN = 3 * Nfp;
+  if (live && code >= 0) {
+    const float2* fnb = FN + (boff + (code >> 2)) * NFN + (code & 3) * Nfp;
+#pragma unroll
+    for (int j = 0; j < Nfp; ++j) p[j] = __ldg(fnb + (Nfp - 1 - j));
+  } else {
+#pragma unroll
+    for (int j = 0; j < Nfp; ++j) p[j] = make_float2(0.f, 0.f);
+  }
+}
+
+// FP16 pieces of Y columns [0, L) of this quarter into tensor memory at
+// column offset c (of piece hi; piece lo KY/2 further)
+template <int L, int YN>
+__device__ __forceinline__ void store_y(const float (&y)[YN], float f2, uint32_t addr, uint32_t lo_off) {
+#pragma unroll
+  for (int c0 = 0; c0 < L / 2; c0 += 8) {
+    uint32_t hi[8], lo[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) split_pair(y[2 * (c0 + c)] * f2, y[2 * (c0 + c) + 1] * f2, hi[c], lo[c]);
+    tc::tmem_st8(addr + c0, hi);
+    tc::tmem_st8(addr + lo_off + c0, lo);
+  }
+}
+
+template <int L, int YN>
+__device__ __forceinline__ float absmax(const float (&y)[YN]) {
+  float m = 0.f;
+#pragma unroll
+  for (int j = 0; j < L; ++j) m = fmaxf(m, fabsf(y[j]));
+  return m;
+}
+
 // The whole apply of one tile per step (see the file comment).
 template <int N, bool HELM>
 __global__ void __launch_bounds__(512, 1) tc_apply(int64_t K, int64_t nE, const float* __restrict__ gx,
@@ -260,16 +366,14 @@ __global__ void __launch_bounds__(512, 1) tc_apply(int64_t K, int64_t nE, const 
                                                    const uint8_t* __restrict__ opsA, float lambda,
                                                    float* __restrict__ out) {
   using S = Tc<N>;
-  constexpr int Np = S::Np, Nfp = S::Nfp, NFN = S::NFN, K1 = S::K1, KY = S::KY, V0 = S::V0, VB = S::VB;
+  constexpr int Np = S::Np, Nfp = S::Nfp, K1 = S::K1, KY = S::KY, V0 = S::V0, VB = S::VB;
   extern __shared__ __align__(128) uint8_t sm[];
   const uint8_t* sB1 = sm;
   const uint8_t* sB2 = sm + 2 * S::szB1;
   const float* isc1 = reinterpret_cast<const float*>(sm + 2 * S::szB1 + 2 * S::szB2);
   const float* isc2 = isc1 + S::N1;
   float* ut = reinterpret_cast<float*>(sm + S::smA_ut);
-  int* pmax = reinterpret_cast<int*>(sm + S::smA_pmax);  // [4][kTile] partial maxima
-  int* sc1 = pmax + 4 * kTile;                           // [kTile] scale exponent of u
-  int* sc2 = sc1 + kTile;                                // [kTile] scale exponent of Y
+  float* pmax = reinterpret_cast<float*>(sm + S::smA_pmax);  // [4][kTile] partial maxima
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + S::smA_bar);  // op, u0, u1, mma1, mma2
   uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 5);
   int* abort_flag = reinterpret_cast<int*>(slot + 1);
@@ -306,6 +410,21 @@ __global__ void __launch_bounds__(512, 1) tc_apply(int64_t K, int64_t nE, const 
     const int64_t e0 = tile * kTile;
     const int ne = tile_len(nE, e0);
     float* cur = ut + buf * (kTile * Np);
+    const bool live = e < ne;
+    const int64_t be = e0 + e;
+    const int64_t el = be % K;  // element of the mesh (first right-hand side: no division)
+    const int64_t boff = be - el;
+    const float* g = gx + 16 * el;
+    // neighbour data of the face quarters, requested before anything waits
+    int code0 = -1, code1 = -1;
+    float2 p0[Nfp], p1[Nfp];
+    if (q >= 2) {
+      const int f0 = q == 2 ? 0 : 2;
+      code0 = live ? __ldg(conn + 3 * el + f0) : -1;
+      if (q == 2) code1 = live ? __ldg(conn + 3 * el + 1) : -1;
+      load_nb<N>(FN, boff, code0, live, p0);
+      load_nb<N>(FN, boff, code1, live && q == 2, p1);
+    }
     if (!tc::mbar_wait(bars + 1 + buf, (it >> 1) & 1)) *abort_flag = 1;
     if (tid == 0 && tile + gridDim.x < ntiles) {
       const int64_t e1 = (tile + gridDim.x) * kTile;
@@ -314,33 +433,28 @@ __global__ void __launch_bounds__(512, 1) tc_apply(int64_t K, int64_t nE, const 
     if (ne < kTile) fix_tail(u, Np, e0, ne, cur);
     __syncthreads();
     if (*abort_flag) break;
-    const bool live = e < ne;
-    const int64_t be = e0 + e;
-    const int64_t el = be % K;  // element of the mesh (first right-hand side: no division)
-    const int64_t boff = be - el;
     const float* urow = cur + e * Np;
-    const float* g = gx + 16 * el;
 
     // ---- FP16 pieces of u (scaled per element) into tensor memory: quarter q
     //      takes k in [16q, 16q + 16)
     float xv[16];
     {
-      int em = -200;
+      float mx = 0.f;
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
         const int k = 16 * q + j;
         xv[j] = (live && k < Np) ? urow[k] : 0.f;
-        em = max(em, tc::exp_of(xv[j]));
+        mx = fmaxf(mx, fabsf(xv[j]));
       }
-      pmax[q * kTile + e] = em;
+      pmax[q * kTile + e] = mx;
     }
     __syncthreads();
-    const int m1 = max(max(pmax[e], pmax[kTile + e]), max(pmax[2 * kTile + e], pmax[3 * kTile + e]));
-    const int s1 = m1 == -200 ? 0 : 14 - m1;
+    const int s1 = scale_exp(fmaxf(fmaxf(pmax[e], pmax[kTile + e]), fmaxf(pmax[2 * kTile + e], pmax[3 * kTile + e])));
     if (16 * q < K1) {
+      const float f1 = pow2f(s1);
       uint32_t hi[8], lo[8];
 #pragma unroll
-      for (int c = 0; c < 8; ++c) split_pair(tc::ldexp2(xv[2 * c], s1), tc::ldexp2(xv[2 * c + 1], s1), hi[c], lo[c]);
+      for (int c = 0; c < 8; ++c) split_pair(xv[2 * c] * f1, xv[2 * c + 1] * f1, hi[c], lo[c]);
       tc::tmem_st8(tb + lanebase + S::oA1 + 8 * q, hi);
       tc::tmem_st8(tb + lanebase + S::oA1 + K1 / 2 + 8 * q, lo);
       tc::tmem_wait_st();
@@ -370,6 +484,7 @@ __global__ void __launch_bounds__(512, 1) tc_apply(int64_t K, int64_t nE, const 
     float y[S::YMAX];
 #pragma unroll
     for (int j = 0; j < S::YMAX; ++j) y[j] = 0.f;
+    float mx;
     if (q < 2) {
       // volume columns of nodes [n0, n0 + len): wr at [0, len), ws at [V0, V0 + len)
       const int n0 = q * V0;
@@ -399,82 +514,44 @@ __global__ void __launch_bounds__(512, 1) tc_apply(int64_t K, int64_t nE, const 
           }
         }
       }
+      mx = absmax<VB>(y);
+    } else if (q == 2) {
+      uint32_t dr0[Nfp], ds0[Nfp], dr1[Nfp], ds1[Nfp];
+      load_face<N>(tb, lanebase, S::oD1, 0, dr0, ds0);
+      load_face<N>(tb, lanebase, S::oD1, 1, dr1, ds1);
+      tc::tmem_wait_ld();
+      if (live) {
+        face_columns<N, 0>(y, dr0, ds0, p0, 0, code0, g, urow, isc1, iu, cpen);
+        face_columns<N, 3 * Nfp>(y, dr1, ds1, p1, 1, code1, g, urow, isc1, iu, cpen);
+      }
+      mx = absmax<S::FB2>(y);
     } else {
-      // face columns: quarter 2 faces 0 and 1, quarter 3 face 2; per face
-      // [1/2 nr sJ [u] | 1/2 ns sJ [u] | -sJ ({n.grad u} + tau [u])] at its nodes
-      constexpr int FMAX = 2;
-      const int nf = q == 2 ? 2 : 1;
-      const int f0 = q == 2 ? 0 : 2;
+      uint32_t dr0[Nfp], ds0[Nfp];
+      load_face<N>(tb, lanebase, S::oD1, 2, dr0, ds0);
+      tc::tmem_wait_ld();
+      if (live) face_columns<N, 0>(y, dr0, ds0, p0, 2, code0, g, urow, isc1, iu, cpen);
+      mx = absmax<S::FB3>(y);
+    }
+    uint32_t mv[S::RQ];  // Helmholtz: M u rows of this quarter's outputs
+    if (HELM) {
 #pragma unroll
-      for (int ff = 0; ff < FMAX; ++ff) {
-        if (ff < nf) {
-          const int f = f0 + ff;
-          // own gradient at the face nodes (tensor-memory columns of the nodes)
-          uint32_t dr[Nfp], ds[Nfp];
+      for (int c0 = 0; c0 < S::RQ; c0 += 4) {
+        uint32_t v[4];
+        tc::tmem_ld4(tb + lanebase + S::oD1 + 2 * Np + q * S::RQ + c0, v);
 #pragma unroll
-          for (int j = 0; j < Nfp; ++j) {
-            const int kf = fnode(N, f, j);
-            tc::tmem_ld1(tb + lanebase + S::oD1 + kf, dr[j]);
-            tc::tmem_ld1(tb + lanebase + S::oD1 + Np + kf, ds[j]);
-          }
-          tc::tmem_wait_ld();
-          if (live) {
-            const float nr = __ldg(g + 4 + 4 * f), ns = __ldg(g + 5 + 4 * f), sJ = __ldg(g + 6 + 4 * f);
-            const float tau = cpen * __ldg(g + 7 + 4 * f);
-            const int code = __ldg(conn + 3 * el + f);
-            const float2* fnb = code >= 0 ? FN + (boff + (code >> 2)) * NFN + (code & 3) * Nfp : FN;
-#pragma unroll
-            for (int j = 0; j < Nfp; ++j) {
-              const int kf = fnode(N, f, j);
-              const float um = urow[kf];
-              const float dnm = (nr * (__uint_as_float(dr[j]) * isc1[kf]) +
-                                 ns * (__uint_as_float(ds[j]) * isc1[Np + kf])) * iu;
-              float jm = 0.f, av = 0.f;
-              if (code >= 0) {
-                const float2 p = __ldg(fnb + (Nfp - 1 - j));
-                jm = p.x - um;
-                av = 0.5f * (dnm - p.y);
-              } else if (code == -2) {  // Dirichlet
-                jm = -2.f * um;
-                av = dnm;
-              }
-              const float hs = 0.5f * sJ * jm;
-              y[ff * 3 * Nfp + j] = nr * hs;
-              y[ff * 3 * Nfp + Nfp + j] = ns * hs;
-              y[ff * 3 * Nfp + 2 * Nfp + j] = -sJ * (av + tau * jm);
-            }
-          }
-        }
+        for (int c = 0; c < 4; ++c) mv[c0 + c] = v[c];
       }
+      tc::tmem_wait_ld();
     }
-    {
-      int em = -200;
-#pragma unroll
-      for (int j = 0; j < S::YMAX; ++j) em = max(em, tc::exp_of(y[j]));
-      pmax[q * kTile + e] = em;
-    }
+    pmax[q * kTile + e] = mx;
     __syncthreads();
-    const int m2 = max(max(pmax[e], pmax[kTile + e]), max(pmax[2 * kTile + e], pmax[3 * kTile + e]));
-    const int s2 = m2 == -200 ? 0 : 14 - m2;
-    if (q == 0) {
-      sc1[e] = s1;
-      sc2[e] = s2;
-    }
+    const int s2 = scale_exp(fmaxf(fmaxf(pmax[e], pmax[kTile + e]), fmaxf(pmax[2 * kTile + e], pmax[3 * kTile + e])));
     {
-      // this quarter's columns of Y: [cq, cq + LQ)
-      const int cq = q < 2 ? q * VB : (q == 2 ? 2 * VB : 2 * VB + S::FB2);
-      const int LQ = q < 2 ? VB : (q == 2 ? S::FB2 : S::FB3);
-#pragma unroll
-      for (int c0 = 0; c0 < S::YMAX / 2; c0 += 8) {
-        if (2 * c0 < LQ) {
-          uint32_t hi[8], lo[8];
-#pragma unroll
-          for (int c = 0; c < 8; ++c)
-            split_pair(tc::ldexp2(y[2 * (c0 + c)], s2), tc::ldexp2(y[2 * (c0 + c) + 1], s2), hi[c], lo[c]);
-          tc::tmem_st8(tb + lanebase + S::oA2 + cq / 2 + c0, hi);
-          tc::tmem_st8(tb + lanebase + S::oA2 + KY / 2 + cq / 2 + c0, lo);
-        }
-      }
+      const float f2 = pow2f(s2);
+      const uint32_t a2 = tb + lanebase + S::oA2;
+      if (q < 2) store_y<VB>(y, f2, a2 + q * (VB / 2), KY / 2);
+      else if (q == 2) store_y<S::FB2>(y, f2, a2 + VB, KY / 2);
+      else store_y<S::FB3>(y, f2, a2 + VB + S::FB2 / 2, KY / 2);
       tc::tmem_wait_st();
     }
     tc::fence_before();
@@ -500,22 +577,17 @@ __global__ void __launch_bounds__(512, 1) tc_apply(int64_t K, int64_t nE, const 
     // ---- epilogue: rows [q RQ, q RQ + RQ) of the element's output
     {
       constexpr int RQ = S::RQ;
-      uint32_t dv[RQ], mv[RQ];
+      uint32_t dv[RQ];
 #pragma unroll
       for (int c0 = 0; c0 < RQ; c0 += 4) {
         uint32_t v[4];
         tc::tmem_ld4(tb + lanebase + S::oD2 + q * RQ + c0, v);
 #pragma unroll
         for (int c = 0; c < 4; ++c) dv[c0 + c] = v[c];
-        if (HELM) {
-          tc::tmem_ld4(tb + lanebase + S::oD1 + 2 * Np + q * RQ + c0, v);
-#pragma unroll
-          for (int c = 0; c < 4; ++c) mv[c0 + c] = v[c];
-        }
       }
       tc::tmem_wait_ld();
-      float* stg = cur;  // the tile's u rows are no longer needed
-      __syncthreads();   // every quarter has finished reading u from the tile buffer
+      float* stg = cur;  // the tile's u rows are no longer needed (every read of them
+                         // precedes the barriers since the pointwise stage)
       if (live) {
         const float iy = tc::ldexp2(1.0f, -s2);
         const float lj = HELM ? lambda * __ldg(g) : 0.f;
@@ -677,12 +749,14 @@ cudaError_t launch_n(dg_mesh* m, int B, double lambda, const float* u, float* Au
         e = cudaFuncSetAttribute(tc_apply<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::smA);
       if (e == cudaSuccess)
         e = cudaFuncSetAttribute(tc_apply<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::smA);
-      int sms = 0, per = 0;
+      int sms = 0, smem_sm = 0;
       if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tc_face<N>, kTile, S::smF);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
       if (e != cudaSuccess) return e;
-      // tensor memory: 128 columns per face CTA (at most 4 per SM), 512 per apply CTA
-      grid_face[dev] = sms * std::max(1, std::min(per, 4));
+      // face CTAs per SM: by shared memory (1 KB reserved per CTA) and tensor
+      // memory (128 of 512 columns each)
+      const int per = std::max(1, std::min(4, smem_sm / (S::smF + 1024)));
+      grid_face[dev] = sms * per;
       grid_apply[dev] = sms;
       o = built;
     }
@@ -734,6 +808,31 @@ cudaError_t launch_apply_tc05(dg_mesh* m, int degree, int B, double lambda, cons
     case 8: return launch_n<8>(m, B, lambda, u, Au, st);
     default: return cudaErrorInvalidValue;
   }
+}
+
+namespace {
+// One warp waits on an mbarrier phase that nothing completes (count 1, no
+// arrival), with the bounded wait of the kernels above; *gave_up = 1 when the
+// wait ran out, and the timeout is counted in g_tc05_err.
+__global__ void wait_selftest(uint64_t limit_ns, int* gave_up) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::mbar_init_fence();
+  }
+  __syncwarp();
+  const bool ok = tc::mbar_wait(&bar, 0, limit_ns);
+  if (threadIdx.x == 0) {
+    *gave_up = ok ? 0 : 1;
+    if (!ok) atomicAdd(&g_tc05_err, 1);
+  }
+}
+}  // namespace
+
+cudaError_t launch_wait_selftest(double seconds, int* gave_up_dev, cudaStream_t st) {
+  wait_selftest<<<1, 32, 0, st>>>(uint64_t(seconds * 1e9), gave_up_dev);
+  note_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t tc05_error(int* flag) {

@@ -40,6 +40,7 @@
 #include <vector>
 
 #include "dg_internal.h"
+#include "tc05.cuh"
 
 namespace dgx {
 namespace {
@@ -581,16 +582,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* b, unsigned parity) {
   return ok != 0;
 }
 // Warp-collective: true once the phase of barrier b with the given parity has
-// completed (seen by every lane), false after kPollCap polls (each poll may
-// suspend the thread briefly). The vote keeps the warp converged, so the
-// aligned ldmatrix / mma / shuffle instructions that follow see all 32 lanes,
-// and a timeout leaves the loop with the whole warp.
-constexpr int kPollCap = 1 << 22;
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity) {
-  for (int it = 0; it < kPollCap; ++it)
-    if (__all_sync(0xffffffffu, mbar_try_wait(b, parity))) return true;
-  return false;
-}
+// completed (seen by every lane), false after one second (the time-bounded
+// wait of tc05.cuh). The vote keeps the warp converged, so the aligned
+// ldmatrix / mma / shuffle instructions that follow see all 32 lanes, and a
+// timeout leaves the loop with the whole warp.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity) { return tc::mbar_wait(b, parity); }
 
 template <int MAXF, typename T>
 __global__ void __launch_bounds__(512, 1) oz_out_pipe(int N, int64_t K, int64_t nE, int Kd, int Mt, int Kt,

@@ -59,6 +59,29 @@ dg_status dg_set_apply_kernel(dg_mesh* m, int degree, dg_prec prec, int helmholt
   return DG_OK;
 }
 
+dg_status dg_wait_selftest(double seconds, void* stream) {
+  if (!(seconds > 0.0) || seconds > 10.0) {
+    set_error("dg_wait_selftest: seconds must be in (0, 10]");
+    return DG_ERR_ARG;
+  }
+  int* flag = nullptr;
+  int host = -1;
+  cudaError_t e = cudaMalloc(&flag, sizeof(int));
+  if (e == cudaSuccess) e = launch_wait_selftest(seconds, flag, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&host, flag, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  cudaFree(flag);
+  if (e != cudaSuccess) {
+    set_error(std::string("dg_wait_selftest: ") + cudaGetErrorString(e));
+    return DG_ERR_CUDA;
+  }
+  if (host == 1) {
+    set_error("dg_wait_selftest: the bounded wait gave up as designed");
+    return DG_ERR_TIMEOUT;
+  }
+  return DG_OK;
+}
+
 int dg_tensor_timeouts(void) {
   int flag = 0, flag05 = 0;
   if (tensor_pipe_error(&flag) != cudaSuccess || tc05_error(&flag05) != cudaSuccess) return -1;

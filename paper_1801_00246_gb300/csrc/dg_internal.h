@@ -137,6 +137,7 @@ bool tc05_usable(const void* u, const void* Au);
 cudaError_t launch_apply_tc05(dg_mesh* m, int degree, int B, double lambda, const float* u, float* Au,
                               cudaStream_t st);
 cudaError_t tc05_error(int* flag);  // reads and clears the tcgen05 kernels' timeout flag
+cudaError_t launch_wait_selftest(double seconds, int* gave_up_dev, cudaStream_t st);
 // FP64 operator A (M x K, row-major) sliced for the tensor-core products out[r] = A X[r]
 struct SlicedOp {
   int M = 0, K = 0, Mt = 0, Kt = 0;

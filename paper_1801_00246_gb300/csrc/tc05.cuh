@@ -99,12 +99,21 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Warp-collective bounded wait for the phase of parity `parity` to complete.
-constexpr int kWaitCap = 1 << 22;
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
-  for (int it = 0; it < kWaitCap; ++it)
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;\n" : "=l"(t));
+  return t;
+}
+// Warp-collective wait for the phase of parity `parity` to complete, bounded
+// in time (default one second, far beyond any tile's work): false if it gave
+// up. The votes keep the warp converged for the aligned instructions after it.
+constexpr uint64_t kWaitLimitNs = 1000000000ull;
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, uint64_t limit_ns = kWaitLimitNs) {
+  const uint64_t t0 = globaltimer_ns();
+  for (;;) {
     if (__all_sync(0xffffffffu, mbar_try(b, parity))) return true;
-  return false;
+    if (__any_sync(0xffffffffu, globaltimer_ns() - t0 > limit_ns)) return false;
+  }
 }
 // arm the barrier for `bytes` of bulk-copy traffic (one arrival)
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {

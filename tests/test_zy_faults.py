@@ -29,3 +29,30 @@ def test_nan_right_hand_side_is_a_breakdown_of_that_entry_only(graph):
         lib.solve(cuda(b[1]), precond=P.PREC_JACOBI, tol=1e-10, max_iter=100, graph=graph)
     x, info = lib.solve(cuda(b[0]), precond=P.PREC_JACOBI, tol=1e-10, max_iter=5000, graph=graph)
     assert info["status"] == "DG_OK" and info["relres"][0] <= 1e-10
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable():
+    """A device-side wait on an mbarrier phase that nothing completes (the wait
+    routine of every tensor-core kernel) gives up after its time limit: the call
+    reports DG_ERR_TIMEOUT, the timeout is counted once in dg_tensor_timeouts,
+    and the next apply on the same device is correct."""
+    import time
+    import torch
+    P = pkg()
+    L = P.lib()
+    assert L.dg_tensor_timeouts() >= 0   # clear
+    t0 = time.perf_counter()
+    st = L.dg_wait_selftest(0.2, None)
+    dt = time.perf_counter() - t0
+    assert st == 6, L.dg_last_error()    # DG_ERR_TIMEOUT
+    assert 0.15 < dt < 10.0
+    assert L.dg_tensor_timeouts() == 1
+    assert L.dg_tensor_timeouts() == 0   # reading clears
+    m, N = config_mesh("c1_poisson_512tri_N3")
+    lib, ora = pair(m, N)
+    u = uniform_field((m.K, ora.Np), seed=9)
+    got = lib.apply(cuda(u)).cpu().numpy()
+    ref = ora.apply(u)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-12
+    got32 = lib.apply(cuda(u, torch.float32)).cpu().numpy()
+    assert np.linalg.norm(got32 - ref) / np.linalg.norm(ref) <= 1e-5
