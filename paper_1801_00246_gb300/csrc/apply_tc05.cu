@@ -60,26 +60,28 @@ struct Tc {
   static constexpr int V0 = (Np + 1) / 2;    // nodes of volume half 0 (half 1 has Np - V0)
   static constexpr int VL = rup8(V0);        // tensor-memory columns loaded per volume half
   static constexpr int VB = rup16(2 * V0);   // Y columns of one volume half (wr at 0.., ws at V0..)
-  static constexpr int FB2 = rup16(6 * Nfp);  // Y columns of faces 0 and 1
-  static constexpr int FB3 = rup16(3 * Nfp);  // Y columns of face 2
-  static constexpr int KY = 2 * VB + FB2 + FB3;
+  static constexpr int E2 = (NFN + 1) / 2;   // face-node entries of face quarter 0 (quarter 1: NFN - E2)
+  static constexpr int FQ = rup16(3 * E2);   // Y columns of one face quarter (3 per entry)
+  static constexpr int KYV = 2 * VB, KYF = 2 * FQ;  // depths of the volume and face output products
   static constexpr int N2 = rup16(Np);  // output rows
   static constexpr int RQ = N2 / 4;     // output rows per thread of an element
-  static constexpr int YMAX = VB > FB2 ? VB : FB2;
+  static constexpr int KQ = K1 / 2;     // u values per volume quarter in the gradient product's input
   // tensor-memory columns of tc_apply
-  static constexpr int oA1 = 0, oD1 = K1, oA2 = oD1 + N1, oD2 = oA2 + KY, TCOLS = oD2 + N2;
+  static constexpr int oA1 = 0, oD1 = K1, oAV = oD1 + N1, oAF = oAV + KYV, oDV = oAF + KYF, oDF = oDV + N2,
+                       TCOLS = oDF + N2;
   static_assert(TCOLS <= 512, "tensor memory");
-  // operator image (bytes): tc_apply part [B1 hi | B1 lo | B2 hi | B2 lo | isc1 | isc2],
-  // tc_face part [BF hi | BF lo | iscF]
-  static constexpr int szB1 = N1 * K1 * 2, szB2 = N2 * KY * 2, szBF = NF * K1 * 2;
-  static constexpr int opsA = 2 * szB1 + 2 * szB2 + 4 * (N1 + N2);  // a multiple of 16
+  static_assert(KQ % 8 == 0 || KQ % 4 == 0, "volume quarter input columns");
+  // operator image (bytes): tc_apply part [B1 hi | B1 lo | BV hi | BV lo | BF2 hi | BF2 lo |
+  // isc1 | iscV | iscF2], tc_face part [BF hi | BF lo | iscF]
+  static constexpr int szB1 = N1 * K1 * 2, szBV = N2 * KYV * 2, szBF2 = N2 * KYF * 2, szBF = NF * K1 * 2;
+  static constexpr int opsA = 2 * szB1 + 2 * szBV + 2 * szBF2 + 4 * (N1 + 2 * N2);  // a multiple of 16
   static constexpr int opsF = 2 * szBF + 4 * NF;
   static_assert(opsA % 16 == 0 && opsF % 16 == 0, "bulk copy sizes");
   static constexpr int utile = kTile * Np * 4;  // bytes of one FP32 u tile
   // shared memory of tc_apply
   static constexpr int smA_ut = rup128(opsA);
   static constexpr int smA_pmax = smA_ut + 2 * utile;
-  static constexpr int smA_bar = smA_pmax + 6 * kTile * 4;
+  static constexpr int smA_bar = smA_pmax + 4 * kTile * 4;
   static constexpr int smA = smA_bar + 8 * 8;
   // shared memory of tc_face
   static constexpr int smF_ut = rup128(opsF);
@@ -280,64 +282,16 @@ __global__ void __launch_bounds__(kTile) tc_face(int64_t K, int64_t nE, const fl
 }
 
 // -------------------------------------------------------------------------------
-// The face columns of one face f for the element: Y[base + j], Y[base + Nfp + j],
-// Y[base + 2 Nfp + j] from the element's own gradient at the face nodes (dr, ds:
-// tensor-memory words), its trace, and the neighbour's face data p.
-template <int N, int BASE, int YN>
-__device__ __forceinline__ void face_columns(float (&y)[YN], const uint32_t (&dr)[N + 1], const uint32_t (&ds)[N + 1],
-                                             const float2 (&p)[N + 1], int f, int code, const float* g,
-                                             const float* urow, const float* isc1, float iu, float cpen) {
-  constexpr int Np = (N + 1) * (N + 2) / 2, Nfp = N + 1;
-  const float nr = __ldg(g + 4 + 4 * f), ns = __ldg(g + 5 + 4 * f), sJ = __ldg(g + 6 + 4 * f);
-  const float tau = cpen * __ldg(g + 7 + 4 * f);
-#pragma unroll
-  for (int j = 0; j < Nfp; ++j) {
-    const int kf = fnode(N, f, j);
-    const float um = urow[kf];
-    const float dnm = (nr * (__uint_as_float(dr[j]) * isc1[kf]) + ns * (__uint_as_float(ds[j]) * isc1[Np + kf])) * iu;
-    float jm = 0.f, av = 0.f;
-    if (code >= 0) {
-      jm = p[j].x - um;
-      av = 0.5f * (dnm - p[j].y);
-    } else if (code == -2) {  // Dirichlet
-      jm = -2.f * um;
-      av = dnm;
-    }
-    const float hs = 0.5f * sJ * jm;
-    y[BASE + j] = nr * hs;
-    y[BASE + Nfp + j] = ns * hs;
-    y[BASE + 2 * Nfp + j] = -sJ * (av + tau * jm);
-  }
+__device__ __forceinline__ void named_sync(int id) { asm volatile("bar.sync %0, 256;\n" ::"r"(id) : "memory"); }
+
+__device__ __forceinline__ void tmem_st4(uint32_t a, uint32_t v0, uint32_t v1, uint32_t v2, uint32_t v3) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};\n" ::"r"(a), "r"(v0), "r"(v1), "r"(v2),
+               "r"(v3)
+               : "memory");
 }
 
-template <int N>
-__device__ __forceinline__ void load_face(uint32_t tb, uint32_t lanebase, int oD1, int f, uint32_t (&dr)[N + 1],
-                                          uint32_t (&ds)[N + 1]) {
-  constexpr int Np = (N + 1) * (N + 2) / 2;
-#pragma unroll
-  for (int j = 0; j <= N; ++j) {
-    const int kf = fnode(N, f, j);
-    tc::tmem_ld1(tb + lanebase + oD1 + kf, dr[j]);
-    tc::tmem_ld1(tb + lanebase + oD1 + Np + kf, ds[j]);
-  }
-}
-
-// neighbour's face data across face f in the element's own node order
-template <int N>
-__device__ __forceinline__ void load_nb(const float2* FN, int64_t boff, int code, bool live, float2 (&p)[N + 1]) {
-  constexpr int Nfp = N + 1, NFN = 3 * Nfp;
-  if (live && code >= 0) {
-    const float2* fnb = FN + (boff + (code >> 2)) * NFN + (code & 3) * Nfp;
-#pragma unroll
-    for (int j = 0; j < Nfp; ++j) p[j] = __ldg(fnb + (Nfp - 1 - j));
-  } else {
-#pragma unroll
-    for (int j = 0; j < Nfp; ++j) p[j] = make_float2(0.f, 0.f);
-  }
-}
-
-// FP16 pieces of Y columns [0, L) of this quarter into tensor memory at
-// column offset c (of piece hi; piece lo KY/2 further)
+// FP16 pieces of Y columns [0, L) (scaled by f2) into tensor memory at column
+// `addr` (piece hi) and addr + lo_off (piece lo)
 template <int L, int YN>
 __device__ __forceinline__ void store_y(const float (&y)[YN], float f2, uint32_t addr, uint32_t lo_off) {
 #pragma unroll
@@ -358,7 +312,61 @@ __device__ __forceinline__ float absmax(const float (&y)[YN]) {
   return m;
 }
 
-// The whole apply of one tile per step (see the file comment).
+// The face columns of the face-node entries [I0, I1) (entry i = f Nfp + j):
+// per entry [1/2 nr sJ [u], 1/2 ns sJ [u], -sJ ({n.grad u} + tau [u])] from the
+// element's own face data (trace, outward normal derivative) and its
+// neighbour's across face f, both read from the face kernel's output.
+template <int N, int I0, int I1, int YN>
+__device__ __forceinline__ void face_quarter(float (&y)[YN], const float2* __restrict__ FN, const float* g,
+                                             const int32_t* __restrict__ conn, int64_t be, int64_t el, int64_t boff,
+                                             float cpen) {
+  constexpr int Nfp = N + 1, NFN = 3 * Nfp;
+  constexpr int FA = I0 / Nfp, FB = (I1 - 1) / Nfp;  // faces the entries touch
+  float nr[3], ns[3], sJ[3], tau[3];
+  int code[3];
+  const float2* nb[3];
+#pragma unroll
+  for (int f = FA; f <= FB; ++f) {
+    nr[f] = __ldg(g + 4 + 4 * f);
+    ns[f] = __ldg(g + 5 + 4 * f);
+    sJ[f] = __ldg(g + 6 + 4 * f);
+    tau[f] = cpen * __ldg(g + 7 + 4 * f);
+    code[f] = __ldg(conn + 3 * el + f);
+    nb[f] = code[f] >= 0 ? FN + (boff + (code[f] >> 2)) * NFN + (code[f] & 3) * Nfp : FN;
+  }
+  float2 own[I1 - I0], oth[I1 - I0];
+#pragma unroll
+  for (int i = I0; i < I1; ++i) {
+    const int f = i / Nfp, j = i - f * Nfp;
+    own[i - I0] = __ldg(FN + be * NFN + i);
+    oth[i - I0] = code[f] >= 0 ? __ldg(nb[f] + (Nfp - 1 - j)) : make_float2(0.f, 0.f);
+  }
+#pragma unroll
+  for (int i = I0; i < I1; ++i) {
+    const int f = i / Nfp;
+    const float um = own[i - I0].x, dnm = own[i - I0].y;
+    float jm = 0.f, av = 0.f;
+    if (code[f] >= 0) {
+      jm = oth[i - I0].x - um;
+      av = 0.5f * (dnm - oth[i - I0].y);
+    } else if (code[f] == -2) {  // Dirichlet
+      jm = -2.f * um;
+      av = dnm;
+    }
+    const float hs = 0.5f * sJ[f] * jm;
+    y[3 * (i - I0)] = nr[f] * hs;
+    y[3 * (i - I0) + 1] = ns[f] * hs;
+    y[3 * (i - I0) + 2] = -sJ[f] * (av + tau[f] * jm);
+  }
+}
+
+// The whole apply of one tile per step (see the file comment). Warps 0-7
+// (volume pair: quarters 0 and 1 of every element) build the gradient
+// product's input, read its result and form the volume columns; warps 8-15
+// (face pair: quarters 2 and 3) form the face columns from the face kernel's
+// output without waiting for the gradient product. The output product is two
+// accumulators, volume and face columns, each with its own scale, so each
+// pair issues its own products as soon as its columns are in tensor memory.
 template <int N, bool HELM>
 __global__ void __launch_bounds__(512, 1) tc_apply(int64_t K, int64_t nE, const float* __restrict__ gx,
                                                    const int32_t* __restrict__ conn,
@@ -366,16 +374,18 @@ __global__ void __launch_bounds__(512, 1) tc_apply(int64_t K, int64_t nE, const 
                                                    const uint8_t* __restrict__ opsA, float lambda,
                                                    float* __restrict__ out) {
   using S = Tc<N>;
-  constexpr int Np = S::Np, Nfp = S::Nfp, K1 = S::K1, KY = S::KY, V0 = S::V0, VB = S::VB;
+  constexpr int Np = S::Np, K1 = S::K1, V0 = S::V0, VB = S::VB, FQ = S::FQ, KQ = S::KQ;
   extern __shared__ __align__(128) uint8_t sm[];
   const uint8_t* sB1 = sm;
-  const uint8_t* sB2 = sm + 2 * S::szB1;
-  const float* isc1 = reinterpret_cast<const float*>(sm + 2 * S::szB1 + 2 * S::szB2);
-  const float* isc2 = isc1 + S::N1;
+  const uint8_t* sBV = sm + 2 * S::szB1;
+  const uint8_t* sBF = sBV + 2 * S::szBV;
+  const float* isc1 = reinterpret_cast<const float*>(sBF + 2 * S::szBF2);
+  const float* iscV = isc1 + S::N1;
+  const float* iscF = iscV + S::N2;
   float* ut = reinterpret_cast<float*>(sm + S::smA_ut);
   float* pmax = reinterpret_cast<float*>(sm + S::smA_pmax);  // [4][kTile] partial maxima
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + S::smA_bar);  // op, u0, u1, mma1, mma2
-  uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 5);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + S::smA_bar);  // op, u0, u1, mma1, mmaV, mmaF
+  uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 6);
   int* abort_flag = reinterpret_cast<int*>(slot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int e = (warp & 3) * 32 + lane;  // element of the tile (tensor-memory lane)
@@ -384,7 +394,7 @@ __global__ void __launch_bounds__(512, 1) tc_apply(int64_t K, int64_t nE, const 
   const int64_t ntiles = (nE + kTile - 1) / kTile;
   const float cpen = float((N + 1) * (N + 2)) * 0.5f;
   if (tid == 0) {
-    for (int i = 0; i < 5; ++i) tc::mbar_init(bars + i, 1);
+    for (int i = 0; i < 6; ++i) tc::mbar_init(bars + i, 1);
     *abort_flag = 0;
     tc::mbar_init_fence();
   }
@@ -415,78 +425,71 @@ __global__ void __launch_bounds__(512, 1) tc_apply(int64_t K, int64_t nE, const 
     const int64_t el = be % K;  // element of the mesh (first right-hand side: no division)
     const int64_t boff = be - el;
     const float* g = gx + 16 * el;
-    // neighbour data of the face quarters, requested before anything waits
-    int code0 = -1, code1 = -1;
-    float2 p0[Nfp], p1[Nfp];
-    if (q >= 2) {
-      const int f0 = q == 2 ? 0 : 2;
-      code0 = live ? __ldg(conn + 3 * el + f0) : -1;
-      if (q == 2) code1 = live ? __ldg(conn + 3 * el + 1) : -1;
-      load_nb<N>(FN, boff, code0, live, p0);
-      load_nb<N>(FN, boff, code1, live && q == 2, p1);
-    }
-    if (!tc::mbar_wait(bars + 1 + buf, (it >> 1) & 1)) *abort_flag = 1;
-    if (tid == 0 && tile + gridDim.x < ntiles) {
-      const int64_t e1 = (tile + gridDim.x) * kTile;
-      issue_tile(u, Np, e1, tile_len(nE, e1), ut + (buf ^ 1) * (kTile * Np), bars + 2 - buf);
-    }
-    if (ne < kTile) fix_tail(u, Np, e0, ne, cur);
-    __syncthreads();
-    if (*abort_flag) break;
-    const float* urow = cur + e * Np;
-
-    // ---- FP16 pieces of u (scaled per element) into tensor memory: quarter q
-    //      takes k in [16q, 16q + 16)
-    float xv[16];
-    {
+    float s_own = 0.f;  // 2^{-s} of this pair's Y scale, for the epilogue
+    float iu_own = 0.f;  // 2^{-s1} of the gradient product's input scale (volume pair)
+    int s1 = 0;
+    if (q < 2) {
+      // ================= volume pair
+      if (!tc::mbar_wait(bars + 1 + buf, (it >> 1) & 1)) *abort_flag = 1;
+      if (tid == 0 && tile + gridDim.x < ntiles) {
+        const int64_t e1 = (tile + gridDim.x) * kTile;
+        issue_tile(u, Np, e1, tile_len(nE, e1), ut + (buf ^ 1) * (kTile * Np), bars + 2 - buf);
+      }
+      if (ne < kTile) {
+        const int n = ne * Np, b = n & ~3;
+        for (int i = b + tid; i < n; i += 256) cur[i] = u[e0 * Np + i];
+      }
+      const float* urow = cur + e * Np;
+      named_sync(1);  // tail of a ragged tile in place
+      // FP16 pieces of u (scaled per element): quarter q takes k in [q KQ, q KQ + KQ)
+      float xv[KQ];
       float mx = 0.f;
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int k = 16 * q + j;
+      for (int j = 0; j < KQ; ++j) {
+        const int k = q * KQ + j;
         xv[j] = (live && k < Np) ? urow[k] : 0.f;
         mx = fmaxf(mx, fabsf(xv[j]));
       }
       pmax[q * kTile + e] = mx;
-    }
-    __syncthreads();
-    const int s1 = scale_exp(fmaxf(fmaxf(pmax[e], pmax[kTile + e]), fmaxf(pmax[2 * kTile + e], pmax[3 * kTile + e])));
-    if (16 * q < K1) {
-      const float f1 = pow2f(s1);
-      uint32_t hi[8], lo[8];
+      named_sync(1);
+      s1 = scale_exp(fmaxf(pmax[e], pmax[kTile + e]));
+      {
+        const float f1 = pow2f(s1);
 #pragma unroll
-      for (int c = 0; c < 8; ++c) split_pair(xv[2 * c] * f1, xv[2 * c + 1] * f1, hi[c], lo[c]);
-      tc::tmem_st8(tb + lanebase + S::oA1 + 8 * q, hi);
-      tc::tmem_st8(tb + lanebase + S::oA1 + K1 / 2 + 8 * q, lo);
-      tc::tmem_wait_st();
-    }
-    tc::fence_before();
-    __syncthreads();
-    if (tid == 0) {
-      tc::fence_after();
-      uint32_t acc = 0;
+        for (int c0 = 0; c0 < KQ / 2; c0 += 4) {
+          uint32_t hi[4], lo[4];
 #pragma unroll
-      for (int ks = 0; ks < K1 / 16; ++ks) {
-#pragma unroll
-        for (int pr = 0; pr < 3; ++pr) {
-          const int pa = pr == 2 ? 1 : 0, pb = pr == 1 ? 1 : 0;
-          const uint64_t bd = tc::smem_desc(tc::smem_addr(sB1) + pb * S::szB1 + ks * 256, 128, (K1 / 8) * 128);
-          tc::mma_ts(tb + S::oD1, tb + S::oA1 + pa * (K1 / 2) + ks * 8, bd, idesc1, acc);
-          acc = 1;
+          for (int c = 0; c < 4; ++c) split_pair(xv[2 * (c0 + c)] * f1, xv[2 * (c0 + c) + 1] * f1, hi[c], lo[c]);
+          tmem_st4(tb + lanebase + S::oA1 + q * (KQ / 2) + c0, hi[0], hi[1], hi[2], hi[3]);
+          tmem_st4(tb + lanebase + S::oA1 + K1 / 2 + q * (KQ / 2) + c0, lo[0], lo[1], lo[2], lo[3]);
         }
+        tc::tmem_wait_st();
       }
-      tc::mma_commit(bars + 3);
-    }
-    if (!tc::mbar_wait(bars + 3, it & 1)) *abort_flag = 1;
-    tc::fence_after();
-    const float iu = tc::ldexp2(1.0f, -s1);  // D1 column c holds C1[c] 2^{s1} / isc1[c]
-
-    // ---- the pointwise stage: this quarter's Y columns in registers
-    float y[S::YMAX];
+      tc::fence_before();
+      named_sync(1);
+      if (tid == 0) {
+        tc::fence_after();
+        uint32_t acc = 0;
 #pragma unroll
-    for (int j = 0; j < S::YMAX; ++j) y[j] = 0.f;
-    float mx;
-    if (q < 2) {
+        for (int ks = 0; ks < K1 / 16; ++ks) {
+#pragma unroll
+          for (int pr = 0; pr < 3; ++pr) {  // (hi, hi), (hi, lo), (lo, hi)
+            const int pa = pr == 2 ? 1 : 0, pb = pr == 1 ? 1 : 0;
+            const uint64_t bd = tc::smem_desc(tc::smem_addr(sB1) + pb * S::szB1 + ks * 256, 128, (K1 / 8) * 128);
+            tc::mma_ts(tb + S::oD1, tb + S::oA1 + pa * (K1 / 2) + ks * 8, bd, idesc1, acc);
+            acc = 1;
+          }
+        }
+        tc::mma_commit(bars + 3);
+      }
+      if (!tc::mbar_wait(bars + 3, it & 1)) *abort_flag = 1;
+      tc::fence_after();
+      const float iu = tc::ldexp2(1.0f, -s1);  // D1 column c holds C1[c] 2^{s1} / isc1[c]
+      iu_own = iu;
       // volume columns of nodes [n0, n0 + len): wr at [0, len), ws at [V0, V0 + len)
+      float y[VB];
+#pragma unroll
+      for (int j = 0; j < VB; ++j) y[j] = 0.f;
       const int n0 = q * V0;
       uint32_t dr[S::VL], ds[S::VL];
 #pragma unroll
@@ -514,88 +517,108 @@ __global__ void __launch_bounds__(512, 1) tc_apply(int64_t K, int64_t nE, const 
           }
         }
       }
-      mx = absmax<VB>(y);
-    } else if (q == 2) {
-      uint32_t dr0[Nfp], ds0[Nfp], dr1[Nfp], ds1[Nfp];
-      load_face<N>(tb, lanebase, S::oD1, 0, dr0, ds0);
-      load_face<N>(tb, lanebase, S::oD1, 1, dr1, ds1);
-      tc::tmem_wait_ld();
-      if (live) {
-        face_columns<N, 0>(y, dr0, ds0, p0, 0, code0, g, urow, isc1, iu, cpen);
-        face_columns<N, 3 * Nfp>(y, dr1, ds1, p1, 1, code1, g, urow, isc1, iu, cpen);
-      }
-      mx = absmax<S::FB2>(y);
-    } else {
-      uint32_t dr0[Nfp], ds0[Nfp];
-      load_face<N>(tb, lanebase, S::oD1, 2, dr0, ds0);
-      tc::tmem_wait_ld();
-      if (live) face_columns<N, 0>(y, dr0, ds0, p0, 2, code0, g, urow, isc1, iu, cpen);
-      mx = absmax<S::FB3>(y);
-    }
-    uint32_t mv[S::RQ];  // Helmholtz: M u rows of this quarter's outputs
-    if (HELM) {
-#pragma unroll
-      for (int c0 = 0; c0 < S::RQ; c0 += 4) {
-        uint32_t v[4];
-        tc::tmem_ld4(tb + lanebase + S::oD1 + 2 * Np + q * S::RQ + c0, v);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) mv[c0 + c] = v[c];
-      }
-      tc::tmem_wait_ld();
-    }
-    pmax[q * kTile + e] = mx;
-    __syncthreads();
-    const int s2 = scale_exp(fmaxf(fmaxf(pmax[e], pmax[kTile + e]), fmaxf(pmax[2 * kTile + e], pmax[3 * kTile + e])));
-    {
-      const float f2 = pow2f(s2);
-      const uint32_t a2 = tb + lanebase + S::oA2;
-      if (q < 2) store_y<VB>(y, f2, a2 + q * (VB / 2), KY / 2);
-      else if (q == 2) store_y<S::FB2>(y, f2, a2 + VB, KY / 2);
-      else store_y<S::FB3>(y, f2, a2 + VB + S::FB2 / 2, KY / 2);
+      pmax[q * kTile + e] = absmax<VB>(y);
+      named_sync(1);
+      const int sv = scale_exp(fmaxf(pmax[e], pmax[kTile + e]));
+      s_own = tc::ldexp2(1.0f, -sv);
+      store_y<VB>(y, pow2f(sv), tb + lanebase + S::oAV + q * (VB / 2), S::KYV / 2);
       tc::tmem_wait_st();
-    }
-    tc::fence_before();
-    __syncthreads();
-    if (tid == 0) {
-      tc::fence_after();
-      uint32_t acc = 0;
-#pragma unroll 1
-      for (int ks = 0; ks < KY / 16; ++ks) {
+      tc::fence_before();
+      named_sync(1);
+      if (tid == 0) {
+        tc::fence_after();
+        uint32_t acc = 0;
 #pragma unroll
-        for (int pr = 0; pr < 3; ++pr) {
-          const int pa = pr == 2 ? 1 : 0, pb = pr == 1 ? 1 : 0;
-          const uint64_t bd = tc::smem_desc(tc::smem_addr(sB2) + pb * S::szB2 + ks * 256, 128, (KY / 8) * 128);
-          tc::mma_ts(tb + S::oD2, tb + S::oA2 + pa * (KY / 2) + ks * 8, bd, idesc2, acc);
-          acc = 1;
+        for (int ks = 0; ks < S::KYV / 16; ++ks) {
+#pragma unroll
+          for (int pr = 0; pr < 3; ++pr) {
+            const int pa = pr == 2 ? 1 : 0, pb = pr == 1 ? 1 : 0;
+            const uint64_t bd =
+                tc::smem_desc(tc::smem_addr(sBV) + pb * S::szBV + ks * 256, 128, (S::KYV / 8) * 128);
+            tc::mma_ts(tb + S::oDV, tb + S::oAV + pa * (S::KYV / 2) + ks * 8, bd, idesc2, acc);
+            acc = 1;
+          }
         }
+        tc::mma_commit(bars + 4);
       }
-      tc::mma_commit(bars + 4);
+    } else {
+      // ================= face pair
+      const int qf = q - 2;
+      float y[FQ];
+#pragma unroll
+      for (int j = 0; j < FQ; ++j) y[j] = 0.f;
+      if (live) {
+        if (qf == 0) face_quarter<N, 0, S::E2>(y, FN, g, conn, be, el, boff, cpen);
+        else face_quarter<N, S::E2, S::NFN>(y, FN, g, conn, be, el, boff, cpen);
+      }
+      pmax[q * kTile + e] = absmax<FQ>(y);
+      named_sync(2);
+      const int sf = scale_exp(fmaxf(pmax[2 * kTile + e], pmax[3 * kTile + e]));
+      s_own = tc::ldexp2(1.0f, -sf);
+      store_y<FQ>(y, pow2f(sf), tb + lanebase + S::oAF + qf * (FQ / 2), S::KYF / 2);
+      tc::tmem_wait_st();
+      tc::fence_before();
+      named_sync(2);
+      if (tid == 256) {
+        tc::fence_after();
+        uint32_t acc = 0;
+#pragma unroll
+        for (int ks = 0; ks < S::KYF / 16; ++ks) {
+#pragma unroll
+          for (int pr = 0; pr < 3; ++pr) {
+            const int pa = pr == 2 ? 1 : 0, pb = pr == 1 ? 1 : 0;
+            const uint64_t bd =
+                tc::smem_desc(tc::smem_addr(sBF) + pb * S::szBF2 + ks * 256, 128, (S::KYF / 8) * 128);
+            tc::mma_ts(tb + S::oDF, tb + S::oAF + pa * (S::KYF / 2) + ks * 8, bd, idesc2, acc);
+            acc = 1;
+          }
+        }
+        tc::mma_commit(bars + 5);
+      }
     }
-    if (!tc::mbar_wait(bars + 4, it & 1)) *abort_flag = 1;
+    // ---- epilogue: both output products done; rows [q RQ, q RQ + RQ)
+    // the other pair's scale comes through shared memory
+    float* sscale = pmax;  // [3][kTile]: the pairs' 2^{-s} and 2^{-s1}; pmax is free again
+    __syncthreads();       // every pair has read its partial maxima
+    if (q == 0) {
+      sscale[e] = s_own;
+      sscale[2 * kTile + e] = iu_own;
+    }
+    if (q == 2) sscale[kTile + e] = s_own;
+    const bool okv = tc::mbar_wait(bars + 4, it & 1);
+    const bool okf = tc::mbar_wait(bars + 5, it & 1);
+    if (!okv || !okf) *abort_flag = 1;
     tc::fence_after();
-
-    // ---- epilogue: rows [q RQ, q RQ + RQ) of the element's output
+    __syncthreads();
     {
       constexpr int RQ = S::RQ;
-      uint32_t dv[RQ];
+      uint32_t dv[RQ], df[RQ], mv[RQ];
 #pragma unroll
       for (int c0 = 0; c0 < RQ; c0 += 4) {
-        uint32_t v[4];
-        tc::tmem_ld4(tb + lanebase + S::oD2 + q * RQ + c0, v);
+        uint32_t v[4], w[4];
+        tc::tmem_ld4(tb + lanebase + S::oDV + q * RQ + c0, v);
+        tc::tmem_ld4(tb + lanebase + S::oDF + q * RQ + c0, w);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) dv[c0 + c] = v[c];
+        for (int c = 0; c < 4; ++c) {
+          dv[c0 + c] = v[c];
+          df[c0 + c] = w[c];
+        }
+        if (HELM) {
+          tc::tmem_ld4(tb + lanebase + S::oD1 + 2 * Np + q * RQ + c0, v);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) mv[c0 + c] = v[c];
+        }
       }
       tc::tmem_wait_ld();
-      float* stg = cur;  // the tile's u rows are no longer needed (every read of them
-                         // precedes the barriers since the pointwise stage)
+      float* stg = cur;  // the tile's u rows are no longer needed
       if (live) {
-        const float iy = tc::ldexp2(1.0f, -s2);
+        const float iyv = sscale[e], iyf = sscale[kTile + e], iu = sscale[2 * kTile + e];
         const float lj = HELM ? lambda * __ldg(g) : 0.f;
 #pragma unroll
         for (int c = 0; c < RQ; ++c) {
           const int r = q * RQ + c;
           if (r < Np) {
-            float o = __uint_as_float(dv[c]) * isc2[r] * iy;
+            float o = __uint_as_float(dv[c]) * iscV[r] * iyv + __uint_as_float(df[c]) * iscF[r] * iyf;
             if (HELM) o += lj * (__uint_as_float(mv[c]) * isc1[2 * Np + r] * iu);
             stg[e * Np + r] = o;
           }
@@ -615,6 +638,7 @@ __global__ void __launch_bounds__(512, 1) tc_apply(int64_t K, int64_t nE, const 
     tc::fence_async_smem();
     tc::fence_before();
     __syncthreads();
+    if (*abort_flag) break;
   }
   if (*abort_flag && tid == 0) atomicExch(&g_tc05_err, 1);
   tc::fence_before();
@@ -678,18 +702,19 @@ cudaError_t build_tc_ops(const RefElem& R, TcOps& o) {
     A1[Np * Np + i] = R.Ds[i];
     A1[2 * Np * Np + i] = R.M[i];
   }
-  // OB in the Y column order of tc_apply
-  std::vector<double> B(size_t(Np) * S::KY, 0.0);
+  // OB split into its volume columns (Y order of the volume pair) and its
+  // face columns (Y order of the face pair: per face-node entry i = f Nfp + l,
+  // [Dr_f^T Mf, Ds_f^T Mf, E_f Mf] column l of face f)
+  std::vector<double> BV(size_t(Np) * S::KYV, 0.0), BF2(size_t(Np) * S::KYF, 0.0);
   for (int i = 0; i < Np; ++i) {
     for (int h = 0; h < 2; ++h) {
       const int n0 = h * S::V0, len = h == 0 ? S::V0 : Np - S::V0;
       for (int j = 0; j < len; ++j) {
-        B[size_t(i) * S::KY + h * S::VB + j] = R.Br[size_t(i) * Np + n0 + j];
-        B[size_t(i) * S::KY + h * S::VB + S::V0 + j] = R.Bs[size_t(i) * Np + n0 + j];
+        BV[size_t(i) * S::KYV + h * S::VB + j] = R.Br[size_t(i) * Np + n0 + j];
+        BV[size_t(i) * S::KYV + h * S::VB + S::V0 + j] = R.Bs[size_t(i) * Np + n0 + j];
       }
     }
-    for (int f = 0; f < 3; ++f) {
-      const int gb = 2 * S::VB + (f < 2 ? f * 3 * Nfp : S::FB2);
+    for (int f = 0; f < 3; ++f)
       for (int l = 0; l < Nfp; ++l) {
         double dr = 0.0, ds = 0.0, ef = 0.0;
         for (int j = 0; j < Nfp; ++j) {
@@ -699,11 +724,12 @@ cudaError_t build_tc_ops(const RefElem& R, TcOps& o) {
           ds += R.Ds[size_t(k) * Np + i] * mf;
           if (k == i) ef += mf;
         }
-        B[size_t(i) * S::KY + gb + l] = dr;
-        B[size_t(i) * S::KY + gb + Nfp + l] = ds;
-        B[size_t(i) * S::KY + gb + 2 * Nfp + l] = ef;
+        const int ent = f * Nfp + l;
+        const int col = ent < S::E2 ? 3 * ent : S::FQ + 3 * (ent - S::E2);
+        BF2[size_t(i) * S::KYF + col] = dr;
+        BF2[size_t(i) * S::KYF + col + 1] = ds;
+        BF2[size_t(i) * S::KYF + col + 2] = ef;
       }
-    }
   }
   // face rows of [Dr; Ds]
   std::vector<double> F(size_t(2 * NFN) * Np);
@@ -716,9 +742,10 @@ cudaError_t build_tc_ops(const RefElem& R, TcOps& o) {
       }
     }
   std::vector<uint8_t> ia(S::opsA, 0), iff(S::opsF, 0);
-  float* isc1 = reinterpret_cast<float*>(ia.data() + 2 * S::szB1 + 2 * S::szB2);
+  float* isc1 = reinterpret_cast<float*>(ia.data() + 2 * S::szB1 + 2 * S::szBV + 2 * S::szBF2);
   put_operator(ia.data(), A1, 3 * Np, Np, S::N1, S::K1, isc1);
-  put_operator(ia.data() + 2 * S::szB1, B, Np, S::KY, S::N2, S::KY, isc1 + S::N1);
+  put_operator(ia.data() + 2 * S::szB1, BV, Np, S::KYV, S::N2, S::KYV, isc1 + S::N1);
+  put_operator(ia.data() + 2 * S::szB1 + 2 * S::szBV, BF2, Np, S::KYF, S::N2, S::KYF, isc1 + S::N1 + S::N2);
   put_operator(iff.data(), F, 2 * NFN, Np, S::NF, S::K1, reinterpret_cast<float*>(iff.data() + 2 * S::szBF));
   cudaError_t e = cudaMalloc(&o.opsA, ia.size());
   if (e == cudaSuccess) e = cudaMemcpy(o.opsA, ia.data(), ia.size(), cudaMemcpyHostToDevice);
