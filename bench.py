@@ -50,7 +50,9 @@ TENSOR_APPLY_TRAFFIC = 1.3250e9  # bytes per FP64 tensor apply from the latest n
 KERNEL_NAMES = {1: "tile (FP64/FP32 pipe)", 2: "gemm (FP32 register GEMMs)",
                 3: "tensor (mma.sync BF16 slice products: gradient product, then fused fill + output product)",
                 4: "ept (element per thread)", 5: "tensor_pipe",
-                6: "tc05 (tcgen05 FP16-piece products, tensor-memory operands: face kernel, then fused apply)"}
+                6: "tc05 (tcgen05 FP16-piece products, tensor-memory operands: face kernel, then fused apply)",
+                7: "tc64 (tcgen05 exactly sliced FP64 products: gradient product, float-float pointwise stage, "
+                   "output product)"}
 
 
 def peaks():
@@ -539,7 +541,7 @@ def run_sweep(args):
     degrees = [int(d) for d in args.sweep_degrees.split(",")]
     batches = [int(b) for b in args.sweep_batches.split(",")]
     names = {P.KERNEL_TILE: "tile", P.KERNEL_GEMM: "gemm", P.KERNEL_TENSOR: "tensor", P.KERNEL_EPT: "ept",
-             P.KERNEL_TENSOR_PIPE: "tensor_pipe", P.KERNEL_TC05: "tc05"}
+             P.KERNEL_TENSOR_PIPE: "tensor_pipe", P.KERNEL_TC05: "tc05", P.KERNEL_TC64: "tc64"}
     for N in degrees:
         mesh = P.Mesh.from_inputs(m, N)
         K, Np = mesh.K, mesh.Np
@@ -550,7 +552,7 @@ def run_sweep(args):
             for lam in (0.0, 1.0):
                 for key, prec, u, o in (("f64", P.DG_F64, u64, o64), ("f32", P.DG_F32, u32, o32)):
                     default = mesh.kernel(N, prec, lam != 0.0)
-                    ks = [P.KERNEL_TILE, P.KERNEL_TENSOR, P.KERNEL_TENSOR_PIPE] + ([] if key == "f64" else [P.KERNEL_GEMM, P.KERNEL_TC05])
+                    ks = [P.KERNEL_TILE, P.KERNEL_TENSOR, P.KERNEL_TENSOR_PIPE] + ([P.KERNEL_TC64] if key == "f64" else [P.KERNEL_GEMM, P.KERNEL_TC05])
                     if N <= 3:
                         ks.append(P.KERNEL_EPT)
                     for k in ks:

@@ -91,10 +91,15 @@ typedef struct dg_mesh dg_mesh; /* opaque; owned by the library until dg_mesh_de
  *   DG_KERNEL_TC05:   FP32 only: both products on the Blackwell tensor cores (tcgen05,
  *                     operands and accumulators in tensor memory, bulk copies), two FP16
  *                     pieces per operand scaled by powers of two; all degrees. Needs u and
- *                     Au 16-byte aligned (otherwise DG_KERNEL_TENSOR runs instead). */
+ *                     Au 16-byte aligned (otherwise DG_KERNEL_TENSOR runs instead).
+ *   DG_KERNEL_TC64:   FP64 only: both products on the Blackwell tensor cores (tcgen05,
+ *                     exact 7-bit integer slicing, 8 slices, accumulators in tensor memory)
+ *                     and the pointwise stage in float-float on the FP32 pipe; degrees 1-8.
+ *                     Handles finite fields whose magnitudes stay within the double range
+ *                     at every stage (about 1e-250..1e250, as DG_KERNEL_TENSOR). */
 enum { DG_KERNEL_AUTO = 0, DG_KERNEL_TILE = 1, DG_KERNEL_GEMM = 2, DG_KERNEL_TENSOR = 3, DG_KERNEL_EPT = 4,
-       DG_KERNEL_TENSOR_PIPE = 5, DG_KERNEL_TC05 = 6 };
-#define DG_NUM_KERNELS 7 /* kernel ids 0..6; dg_autotune's times use this many slots per entry */
+       DG_KERNEL_TENSOR_PIPE = 5, DG_KERNEL_TC05 = 6, DG_KERNEL_TC64 = 7 };
+#define DG_NUM_KERNELS 8 /* kernel ids 0..7; dg_autotune's times use this many slots per entry */
 
 /* Preconditioner choices for dg_pcg_solve (Section 3). */
 enum { DG_PREC_NONE = 0, DG_PREC_JACOBI = 1, DG_PREC_INVMASS = 2, DG_PREC_PMG = 3 };

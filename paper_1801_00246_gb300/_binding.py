@@ -8,8 +8,9 @@ from . import build as _build
 
 DG_F64, DG_F32, DG_F64_DFMA = 0, 1, 2
 PREC_NONE, PREC_JACOBI, PREC_INVMASS, PREC_PMG = 0, 1, 2, 3
-KERNEL_AUTO, KERNEL_TILE, KERNEL_GEMM, KERNEL_TENSOR, KERNEL_EPT, KERNEL_TENSOR_PIPE, KERNEL_TC05 = 0, 1, 2, 3, 4, 5, 6
-NUM_KERNELS = 7
+(KERNEL_AUTO, KERNEL_TILE, KERNEL_GEMM, KERNEL_TENSOR, KERNEL_EPT, KERNEL_TENSOR_PIPE, KERNEL_TC05,
+ KERNEL_TC64) = 0, 1, 2, 3, 4, 5, 6, 7
+NUM_KERNELS = 8
 DG_MAX_BATCH = 64
 
 _STATUS = {0: "DG_OK", 1: "DG_ERR_ARG", 2: "DG_ERR_CUDA", 3: "DG_ERR_OOM", 4: "DG_ERR_NOT_CONVERGED",

@@ -360,6 +360,7 @@ dg_status dg_mesh_destroy(dg_mesh* m) {
   free_ins_workspace(m);
   cudaFree(m->face32);
   cudaFree(m->oz_scratch);
+  cudaFree(m->t64_scratch);
   cudaFree(m->ih32);
   cudaFree(m->geox);
   cudaFree(m->geox32);

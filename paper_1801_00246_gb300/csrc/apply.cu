@@ -398,6 +398,7 @@ bool kernel_valid(int kernel, int degree, bool f64) {
     case DG_KERNEL_TENSOR_PIPE: return true;
     case DG_KERNEL_EPT: return ept_supported(degree);
     case DG_KERNEL_TC05: return !f64;
+    case DG_KERNEL_TC64: return f64 && tc64_supported(degree);
     default: return false;
   }
 }
@@ -417,6 +418,11 @@ cudaError_t launch_apply(const dg_mesh* mc, int degree, dg_prec prec, int B, dou
   const bool f64 = prec == DG_F64;
   if (!kernel_valid(k, degree, f64)) return cudaErrorInvalidValue;
   if (k == DG_KERNEL_EPT) return launch_apply_ept(m, degree, f64, B, lambda, u, Au, st);
+  if (k == DG_KERNEL_TC64) {
+    if (!c1_scratch)
+      return launch_apply_tc64(m, degree, B, lambda, static_cast<const double*>(u), static_cast<double*>(Au), st);
+    k = DG_KERNEL_TENSOR;  // a caller-provided scratch (the allocation-free solve) fits the mma.sync kernel
+  }
   if (k == DG_KERNEL_TC05) {
     if (tc05_usable(u, Au))
       return launch_apply_tc05(m, degree, B, lambda, static_cast<const float*>(u), static_cast<float*>(Au), st);

@@ -29,7 +29,7 @@ __global__ void k_fill_uniform(int64_t n, uint64_t seed, double* __restrict__ a,
 }
 
 constexpr int kCandidates[] = {DG_KERNEL_TILE, DG_KERNEL_GEMM, DG_KERNEL_TENSOR, DG_KERNEL_EPT, DG_KERNEL_TENSOR_PIPE,
-                               DG_KERNEL_TC05};
+                               DG_KERNEL_TC05, DG_KERNEL_TC64};
 
 struct Scratch {
   void* p[5] = {};
@@ -83,9 +83,11 @@ dg_status dg_wait_selftest(double seconds, void* stream) {
 }
 
 int dg_tensor_timeouts(void) {
-  int flag = 0, flag05 = 0;
-  if (tensor_pipe_error(&flag) != cudaSuccess || tc05_error(&flag05) != cudaSuccess) return -1;
-  return flag + flag05;
+  int flag = 0, flag05 = 0, flag64 = 0;
+  if (tensor_pipe_error(&flag) != cudaSuccess || tc05_error(&flag05) != cudaSuccess ||
+      tc64_error(&flag64) != cudaSuccess)
+    return -1;
+  return flag + flag05 + flag64;
 }
 
 int dg_get_apply_kernel(const dg_mesh* m, int degree, dg_prec prec, int helmholtz) {

@@ -102,7 +102,10 @@ struct dg_mesh {
   // FP64 tensor-core apply scratch: C1, Y and the face buffer (grown on demand)
   double* oz_scratch = nullptr;
   size_t oz_cap = 0;
-  uint64_t scratch_gen = 0;  // bumped whenever face32 or oz_scratch is reallocated
+  // FP64 tcgen05 apply scratch: C1, Y and per-element exponents (grown on demand)
+  double* t64_scratch = nullptr;
+  size_t t64_cap = 0;
+  uint64_t scratch_gen = 0;  // bumped whenever face32, oz_scratch or t64_scratch is reallocated
   // apply kernel per [degree][0: FP64, 1: FP32][Helmholtz]; DG_KERNEL_AUTO = built-in choice
   int8_t kern[dgx::kMaxN + 1][2][2] = {};
   uint64_t kern_gen = 0;  // bumped whenever the table changes
@@ -138,6 +141,23 @@ cudaError_t launch_apply_tc05(dg_mesh* m, int degree, int B, double lambda, cons
                               cudaStream_t st);
 cudaError_t tc05_error(int* flag);  // reads and clears the tcgen05 kernels' timeout flag
 cudaError_t launch_wait_selftest(double seconds, int* gave_up_dev, cudaStream_t st);
+// FP64 products on the tcgen05 tensor cores with exact integer slicing (apply_tc64.cu):
+// an operator A (M x K, K <= 224) cut into 8 slices in blocks of 48 rows x 32 columns
+struct Tc64Op {
+  int M = 0, K = 0, NCH = 0, KCH = 0;
+  uint8_t* blocks = nullptr;
+  int* ea = nullptr;
+};
+cudaError_t tc64_op_create(const std::vector<double>& A, int M, int K, Tc64Op* op);
+void tc64_op_free(Tc64Op* op);
+// out[r][c] = sum_k A[c][k] X[r][k]; ex_in / ex_out (optional, per row): the scale
+// exponent of X's row and an exponent bound of the outputs
+cudaError_t tc64_gemm_launch(const Tc64Op& op, int64_t rows, const double* X, int64_t ldx, double* out, int64_t ldo,
+                             int* ex_in, int* ex_out, cudaStream_t st);
+bool tc64_supported(int degree);
+cudaError_t launch_apply_tc64(dg_mesh* m, int degree, int B, double lambda, const double* u, double* Au,
+                              cudaStream_t st);
+cudaError_t tc64_error(int* flag);
 // FP64 operator A (M x K, row-major) sliced for the tensor-core products out[r] = A X[r]
 struct SlicedOp {
   int M = 0, K = 0, Mt = 0, Kt = 0;

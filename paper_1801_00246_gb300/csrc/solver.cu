@@ -1323,7 +1323,8 @@ extern "C" dg_status dg_pcg_jacobi_solve_static(const dg_mesh* mc, int B, double
   {
     int kf = m->kern[m->N][0][lambda != 0.0 ? 1 : 0];
     if (kf == DG_KERNEL_AUTO) kf = default_kernel(m->N, true);
-    if ((kf == DG_KERNEL_TENSOR || kf == DG_KERNEL_TENSOR_PIPE) && !tensor_ops_ready(m->N, true)) {
+    if ((kf == DG_KERNEL_TENSOR || kf == DG_KERNEL_TENSOR_PIPE || kf == DG_KERNEL_TC64) &&
+        !tensor_ops_ready(m->N, true)) {  // (the tcgen05 FP64 kernel is replaced by the mma.sync one here)
       set_error("dg_pcg_jacobi_solve_static: the current device is not the one the mesh was set up on");
       return DG_ERR_ARG;
     }

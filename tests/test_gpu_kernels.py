@@ -15,7 +15,7 @@ TOL64, TOL32 = 1e-12, 1e-5
 
 
 def _kernels(P, N, f64):
-    ks = [P.KERNEL_TILE, P.KERNEL_TENSOR, P.KERNEL_TENSOR_PIPE] + ([] if f64 else [P.KERNEL_GEMM, P.KERNEL_TC05])
+    ks = [P.KERNEL_TILE, P.KERNEL_TENSOR, P.KERNEL_TENSOR_PIPE] + ([P.KERNEL_TC64] if f64 else [P.KERNEL_GEMM, P.KERNEL_TC05])
     if N <= 3:
         ks.append(P.KERNEL_EPT)
     return ks

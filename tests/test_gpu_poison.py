@@ -38,7 +38,7 @@ for N, degs in ((4, [4, 2, 1]), (6, [6, 3, 1])):
                     r = bb[k] - ora.apply(xs[k])
                     assert np.linalg.norm(r) / np.linalg.norm(bb[k]) <= 1.5e-10, (N, amg, mixed, graph)
     for prec, dt in ((P.DG_F64, torch.float64), (P.DG_F32, torch.float32)):
-        for kern in (P.KERNEL_TILE, P.KERNEL_TENSOR, P.KERNEL_GEMM, P.KERNEL_EPT, P.KERNEL_TC05):
+        for kern in (P.KERNEL_TILE, P.KERNEL_TENSOR, P.KERNEL_GEMM, P.KERNEL_EPT, P.KERNEL_TC05, P.KERNEL_TC64):
             lib = P.Mesh.from_inputs(m, N)
             try:
                 lib.set_kernel(N, prec, 1, kern)
