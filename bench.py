@@ -504,6 +504,12 @@ def run_apply_only(args):
     m, _ = config_mesh(MESH_NAME)
     N = args.degree
     mesh = P.Mesh.from_inputs(m, N)
+    kn = {"tile": P.KERNEL_TILE, "gemm": P.KERNEL_GEMM, "tensor": P.KERNEL_TENSOR, "ept": P.KERNEL_EPT,
+          "tensor_pipe": P.KERNEL_TENSOR_PIPE, "tc05": P.KERNEL_TC05, "tc64": P.KERNEL_TC64}
+    if args.kernel64:
+        mesh.set_kernel(N, P.DG_F64, 0, kn[args.kernel64])
+    if args.kernel32:
+        mesh.set_kernel(N, P.DG_F32, 0, kn[args.kernel32])
     u64 = torch.from_numpy(uniform_field((mesh.K, mesh.Np), seed=1)).cuda()
     u32 = u64.float()
     o64, o32 = torch.empty_like(u64), torch.empty_like(u32)
@@ -636,6 +642,8 @@ def main():
                     help="skip the batched solves and the INS step measured after the timed region")
     ap.add_argument("--apply-only", action="store_true", help="only the Poisson applies (profiling)")
     ap.add_argument("--degree", type=int, default=8, help="degree for --apply-only")
+    ap.add_argument("--kernel64", default="", help="--apply-only: FP64 kernel (tile, tensor, tensor_pipe, ept, tc64)")
+    ap.add_argument("--kernel32", default="", help="--apply-only: FP32 kernel (tile, gemm, tensor, tensor_pipe, ept, tc05)")
     ap.add_argument("--sweep", action="store_true", help="apply throughput for N=1..8, FP64/FP32, B=1/4/16")
     ap.add_argument("--solve-only", action="store_true", help="one N=8 pMG-FCG solve in an NVTX range (profiling)")
     ap.add_argument("--graph", type=int, default=1, help="--solve-only: 1 = CUDA-graph solve, 0 = host loop")

@@ -915,6 +915,7 @@ cudaError_t sliced_op_create(const std::vector<double>& A, int M, int K, SlicedO
   if (e == cudaSuccess) e = cudaMemcpy(op->A, frag.data(), frag.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&op->ea, ea.size() * sizeof(int));
   if (e == cudaSuccess) e = cudaMemcpy(op->ea, ea.data(), ea.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = tc64_op_create(A, M, K, &op->t64);
   return e;
 }
 
@@ -923,10 +924,12 @@ void sliced_op_free(SlicedOp* op) {
   cudaFree(op->ea);
   op->A = nullptr;
   op->ea = nullptr;
+  tc64_op_free(&op->t64);
 }
 
 cudaError_t sliced_gemm(const SlicedOp& op, int64_t rows, const double* X, int64_t ldx, double* out, int64_t ldo,
                         cudaStream_t st) {
+  if (op.t64.blocks) return tc64_gemm_launch(op.t64, rows, X, ldx, out, ldo, nullptr, nullptr, st);
   return gemm<double>(op.Mt, rows, op.M, op.K, op.Kt, reinterpret_cast<const uint4*>(op.A), op.ea, X, ldx, out, ldo,
                       nullptr, st);
 }

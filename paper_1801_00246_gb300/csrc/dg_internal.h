@@ -141,13 +141,7 @@ cudaError_t launch_apply_tc05(dg_mesh* m, int degree, int B, double lambda, cons
                               cudaStream_t st);
 cudaError_t tc05_error(int* flag);  // reads and clears the tcgen05 kernels' timeout flag
 cudaError_t launch_wait_selftest(double seconds, int* gave_up_dev, cudaStream_t st);
-// FP64 products on the tcgen05 tensor cores with exact integer slicing (apply_tc64.cu):
-// an operator A (M x K, K <= 224) cut into 8 slices in blocks of 48 rows x 32 columns
-struct Tc64Op {
-  int M = 0, K = 0, NCH = 0, KCH = 0;
-  uint8_t* blocks = nullptr;
-  int* ea = nullptr;
-};
+struct Tc64Op;
 cudaError_t tc64_op_create(const std::vector<double>& A, int M, int K, Tc64Op* op);
 void tc64_op_free(Tc64Op* op);
 // out[r][c] = sum_k A[c][k] X[r][k]; ex_in / ex_out (optional, per row): the scale
@@ -158,11 +152,20 @@ bool tc64_supported(int degree);
 cudaError_t launch_apply_tc64(dg_mesh* m, int degree, int B, double lambda, const double* u, double* Au,
                               cudaStream_t st);
 cudaError_t tc64_error(int* flag);
-// FP64 operator A (M x K, row-major) sliced for the tensor-core products out[r] = A X[r]
+// FP64 products on the tcgen05 tensor cores with exact integer slicing (apply_tc64.cu):
+// an operator A (M x K, K <= 224) cut into 8 slices in blocks of 48 rows x 32 columns
+struct Tc64Op {
+  int M = 0, K = 0, NCH = 0, KCH = 0;
+  uint8_t* blocks = nullptr;
+  int* ea = nullptr;
+};
+// FP64 operator A (M x K, row-major) sliced for the tensor-core products out[r] = A X[r]:
+// the mma.sync fragment layout and the tcgen05 block layout (used when built)
 struct SlicedOp {
   int M = 0, K = 0, Mt = 0, Kt = 0;
   uint32_t* A = nullptr;
   int* ea = nullptr;
+  Tc64Op t64;
 };
 cudaError_t sliced_op_create(const std::vector<double>& A, int M, int K, SlicedOp* op);
 void sliced_op_free(SlicedOp* op);
