@@ -19,11 +19,14 @@
 //    the threads into a double-buffered shared-memory chunk (32 columns) while
 //    the previous chunk's products run; operator blocks (48 rows x 32 columns,
 //    8 slices) arrive by bulk copy.
-//  * tc64_fill: the pointwise stage (metric terms, jumps and averages at face
-//    nodes, penalty) in float-float arithmetic on the FP32 pipe, every input
-//    scaled by the largest exponent among the element and its neighbours;
-//    writes Y in FP64.
-//  * C1 and Au are tc64_gemm launches with [Dr; Ds] and OB.
+//  * the gradient product C1 = [Dr; Ds] u (rows interleaved, so one thread
+//    holds ur and us of a node) with an epilogue that forms the volume columns
+//    of Y (wr, ws), the Helmholtz columns and every element's face data
+//    (u, n.grad u at its face nodes) in float-float on the FP32 pipe;
+//  * tc64_face_fill: the face columns of Y (jumps and averages against the
+//    neighbour's face data, penalty of Eq. PenaltyParameter), float-float,
+//    one thread per face-node entry;
+//  * the output product Au = OB Y, a plain tc64_gemm launch.
 // Accuracy: relative error near 2^-44 of |A||u| (the slicing's), as the mma.sync path.
 #include <cmath>
 #include <cstring>
@@ -147,15 +150,53 @@ __device__ __forceinline__ ff d2ff(double x, int R) {
 }
 
 // ------------------------------------------------------------------ the GEMM
+__device__ __forceinline__ int fnode(int N, int f, int j) {
+  auto rs = [N](int row) { return row * (N + 1) - row * (row - 1) / 2; };
+  return f == 0 ? j : (f == 1 ? rs(j) + (N - j) : rs(N - j));
+}
+
+// Horner's rule over the 8 slice sums of one output column: (h, l) with
+// h + l = sum_s acc_s 2^{-7 s} (float-float)
+__device__ __forceinline__ ff horner8(const uint32_t (&acc)[kSl][4], int c) {
+  float h = __uint_as_float(acc[kSl - 1][c]), l = 0.f;
+#pragma unroll
+  for (int s = kSl - 2; s >= 0; --s) {
+    const float a = __uint_as_float(acc[s][c]);
+    const float hs = h * 0.0078125f, ls = l * 0.0078125f;
+    const float sum = __fadd_rn(a, hs);
+    const float bb = __fsub_rn(sum, a);
+    const float err = __fadd_rn(__fsub_rn(a, __fsub_rn(sum, bb)), __fsub_rn(hs, bb));
+    h = sum;
+    l = __fadd_rn(ls, err);
+  }
+  return ff_renorm(h, l);
+}
+
+// Arguments of the gradient product's epilogue (MODE 1): the rows of A are
+// [Dr; Ds] interleaved (column 2n = ur at node n, 2n + 1 = us), and instead of
+// C1 the epilogue writes the volume columns of Y (wr, ws), the Helmholtz
+// columns lambda J u, and every element's face data FN = (u, n.grad u) at its
+// face nodes (outward normal of the element itself).
+struct GradOut {
+  int N;
+  int64_t K;
+  const double* gx;  // derived geometry, 16 words per element
+  double* Y;
+  int ldy, helm;
+  double lambda;
+  double2* FN;  // [rows][3 (N+1)]
+};
+
 // out[r][c] = sum_k A[c][k] X[r][k] for r < rows, c < M, k < Kd (A sliced in
 // blocks of kNC rows x kKC columns: block (nc, kc) at (nc KCH + kc) kBBytes).
-// ex_in (optional): per row, the scale exponent of X's row; ex_out (optional):
-// per row, an exponent bound of the outputs.
+// With KCH <= 2 the data chunks of a tile stay in shared memory for every
+// output pass; otherwise they stream through the two buffers (one pass). Only
+// warp 0 polls the mbarriers; the other warps meet it at a CTA barrier.
+template <int MODE>
 __global__ void __launch_bounds__(512, 1) tc64_gemm(int64_t rows, int M, int Kd, int NCH, int KCH,
-                                                    const double* __restrict__ X, int64_t ldx,
+                                                    const double* __restrict__ X, int64_t ldx, int vec2,
                                                     const uint8_t* __restrict__ Bops, const int* __restrict__ ea,
-                                                    double* __restrict__ out, int64_t ldo, int* __restrict__ ex_in,
-                                                    int* __restrict__ ex_out) {
+                                                    double* __restrict__ out, int64_t ldo, GradOut go) {
   extern __shared__ __align__(1024) uint8_t sm[];
   uint8_t* sA = sm;                        // [2][8 slices][128 rows][32] canonical
   uint8_t* sB = sm + 2 * kABytes;          // [2][8 slices][48 rows][32] canonical
@@ -168,6 +209,7 @@ __global__ void __launch_bounds__(512, 1) tc64_gemm(int64_t rows, int M, int Kd,
   const int q = warp >> 2;
   const uint32_t lanebase = uint32_t((warp & 3) * 32) << 16;
   const int64_t ntiles = (rows + kT - 1) / kT;
+  const bool resident = KCH <= 2;
   if (tid == 0) {
     for (int i = 0; i < 4; ++i) tc::mbar_init(bars + i, 1);
     *abort_flag = 0;
@@ -179,84 +221,127 @@ __global__ void __launch_bounds__(512, 1) tc64_gemm(int64_t rows, int M, int Kd,
   tc::fence_after();
   const uint32_t tb = *slot;
   constexpr uint32_t idesc = tc::idesc_f16(128, kNC, true);
-  uint32_t cnt = 0;  // data chunks issued by this CTA
+  uint32_t cnt = 0;  // operator blocks (and products) issued by this CTA
+  auto load8 = [&](const double* xr, bool live, int k0, double (&v)[8]) {
+    if (live && vec2 && k0 + 8 <= Kd) {
+      const double2* p2 = reinterpret_cast<const double2*>(xr + k0);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const double2 w = __ldg(p2 + t);
+        v[2 * t] = w.x;
+        v[2 * t + 1] = w.y;
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < 8; ++t) v[t] = (live && k0 + t < Kd) ? __ldg(xr + k0 + t) : 0.0;
+    }
+  };
+  auto slice_chunk = [&](const double (&v)[8], int E, uint32_t buf) {
+    uint64_t I[8];
+    uint32_t sg[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) I[t] = fixed56(v[t], E, sg[t]);
+    uint8_t* dst = sA + buf * kABytes + (e >> 3) * 512 + q * 128 + (e & 7) * 16;
+#pragma unroll
+    for (int j = 0; j < kSl; ++j) {
+      uint4 w;
+      w.x = slice_bits(I[0], j, sg[0]) | (slice_bits(I[1], j, sg[1]) << 16);
+      w.y = slice_bits(I[2], j, sg[2]) | (slice_bits(I[3], j, sg[3]) << 16);
+      w.z = slice_bits(I[4], j, sg[4]) | (slice_bits(I[5], j, sg[5]) << 16);
+      w.w = slice_bits(I[6], j, sg[6]) | (slice_bits(I[7], j, sg[7]) << 16);
+      *reinterpret_cast<uint4*>(dst + j * kASlice) = w;
+    }
+  };
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t row = tile * kT + e;
     const bool live = row < rows;
     const double* xr = X + (live ? row : 0) * ldx;
     // scale exponent of the row: the largest |X[row][k]| < 2^E
+    double v0[8], v1[8];  // resident mode: the thread's values of chunks 0 and 1
     int em = -1100;
-    if (live)
-      for (int kc = 0; kc < KCH; ++kc)
+    if (resident) {
+      load8(xr, live, 8 * q, v0);
+      load8(xr, live, kKC + 8 * q, v1);
 #pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          const int k = kc * kKC + 8 * q + t;
-          if (k < Kd) em = max(em, exp_bound64(__ldg(xr + k)));
-        }
+      for (int t = 0; t < 8; ++t) em = max(em, max(exp_bound64(v0[t]), KCH > 1 ? exp_bound64(v1[t]) : -1100));
+    } else if (live) {
+      for (int kc = 0; kc < KCH; ++kc) {
+        double v[8];
+        load8(xr, live, kc * kKC + 8 * q, v);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) em = max(em, exp_bound64(v[t]));
+      }
+    }
     pmax[q * kT + e] = em;
+    // the previous tile's products are complete (its last drain waited), so
+    // both data buffers are free here
     __syncthreads();
     int E = max(max(pmax[e], pmax[kT + e]), max(pmax[2 * kT + e], pmax[3 * kT + e]));
     if (E == -1100) E = 0;
-    if (ex_in && q == 0 && live) ex_in[row] = E;
-    int out_em = -1100;
+    if (resident) {
+      slice_chunk(v0, E, 0);
+      if (KCH > 1) slice_chunk(v1, E, 1);
+      tc::fence_async_smem();
+    }
+    float gh[6];  // MODE 1: Grr, Grs, Gss as float-float
+    if (MODE == 1) {
+      const int64_t el = (live ? row : 0) % go.K;
+      const double* g = go.gx + 16 * el;
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        const ff gf = d2ff(__ldg(g + 1 + t), 0);
+        gh[2 * t] = gf.h;
+        gh[2 * t + 1] = gf.l;
+      }
+    }
     for (int nc = 0; nc < NCH; ++nc) {
       for (int kc = 0; kc < KCH; ++kc, ++cnt) {
-        const uint32_t ab = cnt & 1u;
-        // the buffers of chunk cnt - 2 are free once its products completed
-        if (cnt >= 2 && !tc::mbar_wait(bars + ab, ((cnt - 2) >> 1) & 1u)) *abort_flag = 1;
-        if (tid == 0) {
-          tc::mbar_expect_tx(bars + 2 + ab, kBBytes);
-          tc::bulk_g2s(sB + ab * kBBytes, Bops + size_t(nc * KCH + kc) * kBBytes, kBBytes, bars + 2 + ab);
-        }
-        // slices of X[row][kc*32 + 8q .. + 8): one 16-byte row of a core matrix per slice
-        {
-          uint64_t I[8];
-          uint32_t sg[8];
-#pragma unroll
-          for (int t = 0; t < 8; ++t) {
-            const int k = kc * kKC + 8 * q + t;
-            const double v = (live && k < Kd) ? __ldg(xr + k) : 0.0;
-            I[t] = fixed56(v, E, sg[t]);
-          }
-          uint8_t* dst = sA + ab * kABytes + (e >> 3) * 512 + q * 128 + (e & 7) * 16;
-#pragma unroll
-          for (int j = 0; j < kSl; ++j) {
-            uint4 w;
-            w.x = slice_bits(I[0], j, sg[0]) | (slice_bits(I[1], j, sg[1]) << 16);
-            w.y = slice_bits(I[2], j, sg[2]) | (slice_bits(I[3], j, sg[3]) << 16);
-            w.z = slice_bits(I[4], j, sg[4]) | (slice_bits(I[5], j, sg[5]) << 16);
-            w.w = slice_bits(I[6], j, sg[6]) | (slice_bits(I[7], j, sg[7]) << 16);
-            *reinterpret_cast<uint4*>(dst + j * kASlice) = w;
-          }
-        }
-        tc::fence_async_smem();
-        tc::fence_before();
+        const uint32_t sb_i = cnt & 1u;
+        // the operator stage (and, streaming, the data buffer) of block cnt - 2 is
+        // free once that block's products completed
+        if (warp == 0 && cnt >= 2 && !tc::mbar_wait(bars + sb_i, ((cnt - 2) >> 1) & 1u)) *abort_flag = 1;
         __syncthreads();
+        if (tid == 0) {
+          tc::mbar_expect_tx(bars + 2 + sb_i, kBBytes);
+          tc::bulk_g2s(sB + sb_i * kBBytes, Bops + size_t(nc * KCH + kc) * kBBytes, kBBytes, bars + 2 + sb_i);
+        }
+        uint32_t abuf = kc;
+        if (!resident) {
+          abuf = sb_i;
+          double v[8];
+          load8(xr, live, kc * kKC + 8 * q, v);
+          slice_chunk(v, E, abuf);
+        }
+        if (!resident) tc::fence_async_smem();
+        tc::fence_before();
+        __syncthreads();  // the data chunk (sliced above, or at the tile's start) is in place
         if (warp == 0) {  // the whole warp waits for the operator block, lane 0 issues
           tc::fence_after();
-          if (!tc::mbar_wait(bars + 2 + ab, (cnt >> 1) & 1u)) *abort_flag = 1;
-        }
-        if (tid == 0) {
-          const uint32_t sa = tc::smem_addr(sA + ab * kABytes), sb = tc::smem_addr(sB + ab * kBBytes);
-          uint32_t started = kc > 0 ? 0xffu : 0u;
+          if (!tc::mbar_wait(bars + 2 + sb_i, (cnt >> 1) & 1u)) *abort_flag = 1;
+          if (lane == 0) {
+            const uint32_t sa = tc::smem_addr(sA + abuf * kABytes), sb = tc::smem_addr(sB + sb_i * kBBytes);
+            uint32_t started = kc > 0 ? 0xffu : 0u;
 #pragma unroll
-          for (int ks = 0; ks < kKC / 16; ++ks)
+            for (int ks = 0; ks < kKC / 16; ++ks)
 #pragma unroll
-            for (int i = 0; i < kSl; ++i)
+              for (int i = 0; i < kSl; ++i)
 #pragma unroll
-              for (int j = 0; j < kSl - i; ++j) {
-                const int s = i + j;
-                const uint64_t ad = tc::smem_desc(sa + j * kASlice + ks * 256, 128, (kKC / 8) * 128);
-                const uint64_t bd = tc::smem_desc(sb + i * kBSlice + ks * 256, 128, (kKC / 8) * 128);
-                tc::mma_ss(tb + s * kNC, ad, bd, idesc, (started >> s) & 1u);
-                started |= 1u << s;
-              }
-          tc::mma_commit(bars + ab);
+                for (int j = 0; j < kSl - i; ++j) {
+                  const int s = i + j;
+                  const uint64_t ad = tc::smem_desc(sa + j * kASlice + ks * 256, 128, (kKC / 8) * 128);
+                  const uint64_t bd = tc::smem_desc(sb + i * kBSlice + ks * 256, 128, (kKC / 8) * 128);
+                  tc::mma_ss(tb + s * kNC, ad, bd, idesc, (started >> s) & 1u);
+                  started |= 1u << s;
+                }
+            tc::mma_commit(bars + sb_i);
+          }
+          __syncwarp();
         }
       }
       // drain: output columns [12q, 12q + 12) of this pass
       const uint32_t last = cnt - 1;
-      if (!tc::mbar_wait(bars + (last & 1u), (last >> 1) & 1u)) *abort_flag = 1;
+      if (warp == 0 && !tc::mbar_wait(bars + (last & 1u), (last >> 1) & 1u)) *abort_flag = 1;
+      __syncthreads();
       tc::fence_after();
 #pragma unroll 1
       for (int p = 0; p < 3; ++p) {
@@ -270,37 +355,67 @@ __global__ void __launch_bounds__(512, 1) tc64_gemm(int64_t rows, int M, int Kd,
           for (int c = 0; c < 4; ++c) acc[s][c] = v[c];
         }
         tc::tmem_wait_ld();
+        if (MODE == 0) {
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const int col = nc * kNC + c0 + c;
-          if (live && col < M) {
-            // value = 2^{ea + E - 14} sum_s acc_s 2^{-7 s}: Horner from the last slice sum
-            float h = __uint_as_float(acc[kSl - 1][c]), l = 0.f;
-#pragma unroll
-            for (int s = kSl - 2; s >= 0; --s) {
-              const float a = __uint_as_float(acc[s][c]);
-              const float hs = h * 0.0078125f, ls = l * 0.0078125f;
-              const float sum = __fadd_rn(a, hs);
-              const float bb = __fsub_rn(sum, a);
-              const float err = __fadd_rn(__fsub_rn(a, __fsub_rn(sum, bb)), __fsub_rn(hs, bb));
-              h = sum;
-              l = __fadd_rn(ls, err);
+          for (int c = 0; c < 4; ++c) {
+            const int col = nc * kNC + c0 + c;
+            if (live && col < M) {
+              // value = 2^{ea + E - 14} sum_s acc_s 2^{-7 s}
+              const ff hl = horner8(acc, c);
+              out[row * ldo + col] = ff_to_double(hl.h, hl.l, __ldg(ea + col) + E - 14);
             }
-            const double o = ff_to_double(h, l, __ldg(ea + col) + E - 14);
-            out[row * ldo + col] = o;
-            out_em = max(out_em, exp_bound64(o));
+          }
+        } else {
+          // nodes n = col / 2: (ur, us) in columns (2n, 2n + 1)
+          const int N = go.N, Np = (N + 1) * (N + 2) / 2, Nfp = N + 1, NFN = 3 * Nfp;
+#pragma unroll
+          for (int c = 0; c < 4; c += 2) {
+            const int n = (nc * kNC + c0 + c) >> 1;
+            if (live && n < Np) {
+              const int er = __ldg(ea + 2 * n), es = __ldg(ea + 2 * n + 1);
+              const int ec = max(er, es);
+              ff ur = horner8(acc, c), us = horner8(acc, c + 1);
+              ur = ff_pow2(ur, __uint_as_float(uint32_t(127 + er - ec) << 23));
+              us = ff_pow2(us, __uint_as_float(uint32_t(127 + es - ec) << 23));
+              const int S = ec + E - 14;  // ur, us, wr, ws, n.grad u all carry 2^S
+              const ff grr{gh[0], gh[1]}, grs{gh[2], gh[3]}, gss{gh[4], gh[5]};
+              const ff wr = ff_add(ff_mul(grr, ur), ff_mul(grs, us));
+              const ff ws = ff_add(ff_mul(grs, ur), ff_mul(gss, us));
+              double* yr = go.Y + row * go.ldy;
+              yr[n] = ff_to_double(wr.h, wr.l, S);
+              yr[Np + n] = ff_to_double(ws.h, ws.l, S);
+              const double un = __ldg(X + row * ldx + n);
+              const int64_t el = row % go.K;
+              const double* g = go.gx + 16 * el;
+              if (go.helm) {
+                const int eu = exp_bound64(un);
+                const ff lj = ff_mul(d2ff(go.lambda, 0), d2ff(__ldg(g), 0));
+                const ff v = ff_mul(lj, d2ff(un, eu));
+                yr[2 * Np + 3 * NFN + n] = ff_to_double(v.h, v.l, eu);
+              }
+              // face data at the face nodes this node is (a corner belongs to two faces)
+              int rrow = 0;
+              while (n >= (rrow + 1) * (N + 1) - (rrow + 1) * rrow / 2) ++rrow;  // n's row of constant s
+              const int rs0 = rrow * (N + 1) - rrow * (rrow - 1) / 2, len = N + 1 - rrow;
+              int fj[2][2], nf = 0;
+              if (rrow == 0) fj[nf][0] = 0, fj[nf][1] = n, ++nf;                    // face 0, j = n
+              if (n == rs0 + len - 1) fj[nf][0] = 1, fj[nf][1] = rrow, ++nf;        // face 1, j = row
+              if (n == rs0 && nf < 2) fj[nf][0] = 2, fj[nf][1] = N - rrow, ++nf;   // face 2, j = N - row
+#pragma unroll
+              for (int t = 0; t < 2; ++t) {
+                if (t < nf) {
+                  const int f = fj[t][0], j = fj[t][1];
+                  const ff nr = d2ff(__ldg(g + 4 + 4 * f), 0), ns = d2ff(__ldg(g + 5 + 4 * f), 0);
+                  const ff dn = ff_add(ff_mul(nr, ur), ff_mul(ns, us));
+                  go.FN[row * NFN + f * Nfp + j] = make_double2(un, ff_to_double(dn.h, dn.l, S));
+                }
+              }
+            }
           }
         }
       }
       tc::fence_before();
       __syncthreads();  // the accumulators are read; the next pass may overwrite them
-    }
-    if (ex_out) {
-      pmax[q * kT + e] = out_em;
-      __syncthreads();
-      if (q == 0 && live)
-        ex_out[row] = max(max(pmax[e], pmax[kT + e]), max(pmax[2 * kT + e], pmax[3 * kT + e]));
-      __syncthreads();
     }
     if (*abort_flag) break;
   }
@@ -311,92 +426,50 @@ __global__ void __launch_bounds__(512, 1) tc64_gemm(int64_t rows, int M, int Kd,
   if (warp == 0) tc::tmem_dealloc(tb, 512);
 }
 
-// ------------------------------------------------------------------ pointwise stage
-__device__ __forceinline__ int fnode(int N, int f, int j) {
-  auto rs = [N](int row) { return row * (N + 1) - row * (row - 1) / 2; };
-  return f == 0 ? j : (f == 1 ? rs(j) + (N - j) : rs(N - j));
-}
-
-// One warp per element: Y[be] = [wr, ws | 1/2 nr sJ [u], 1/2 ns sJ [u],
-// -sJ ({n.grad u} + tau [u]) (| lambda J u)] from C1 = [ur; us] (ldc per
-// element), u, the derived geometry gx (16 FP64 words per element) and the
-// neighbours' rows, in float-float scaled by 2^{-R}, R the largest exponent
-// of the element's and its neighbours' u and C1 rows (exu, exc).
-__global__ void __launch_bounds__(256) tc64_fill(int N, int64_t K, int64_t nE, const double* __restrict__ gx,
-                                                 const int32_t* __restrict__ conn, const double* __restrict__ u,
-                                                 const double* __restrict__ C1, int ldc, const int* __restrict__ exu,
-                                                 const int* __restrict__ exc, double lambda, double* __restrict__ Y,
-                                                 int ldy) {
+// ------------------------------------------------------------------ face columns of Y
+// One thread per (element, face-node entry i = f (N+1) + j): from the element's
+// face data and its neighbour's across face f (FN, written by the gradient
+// product), Y[2Np + i] = 1/2 nr sJ [u], Y[2Np + NFN + i] = 1/2 ns sJ [u],
+// Y[2Np + 2 NFN + i] = -sJ ({n.grad u} + tau [u]), in float-float scaled by
+// the entry's largest input; the row's largest exponent per element
+// (ex_y, atomically) for the output product's slicing.
+__global__ void __launch_bounds__(256) tc64_face_fill(int N, int64_t K, int64_t nE, const double* __restrict__ gx,
+                                                      const int32_t* __restrict__ conn,
+                                                      const double2* __restrict__ FN, double* __restrict__ Y,
+                                                      int ldy) {
   const int Np = (N + 1) * (N + 2) / 2, Nfp = N + 1, NFN = 3 * Nfp;
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
+  const int64_t total = nE * NFN;
   const ff cpen{float((N + 1) * (N + 2)) * 0.5f, 0.f};
-  const ff half{0.5f, 0.f};
-  const ff lam = d2ff(lambda, 0);
-  for (int64_t be = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); be < nE; be += warps) {
+  for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t be = t / NFN;
+    const int i = int(t - be * NFN);
+    const int f = i / Nfp, j = i - f * Nfp;
     const int64_t el = be % K, boff = be - el;
-    // scale: the largest exponent among this element and its neighbours
-    int r = -1100;
-    if (lane < 3) {
-      const int code = __ldg(conn + 3 * el + lane);
-      if (code >= 0) {
-        const int64_t nb = boff + (code >> 2);
-        r = max(__ldg(exu + nb), __ldg(exc + nb));
-      }
-    } else if (lane == 3) {
-      r = max(__ldg(exu + be), __ldg(exc + be));
+    const double* g = gx + 16 * el + 4 + 4 * f;
+    const double2 own = __ldg(FN + t);
+    const int code = __ldg(conn + 3 * el + f);
+    double2 oth = make_double2(0.0, 0.0);
+    if (code >= 0) oth = __ldg(FN + (boff + (code >> 2)) * NFN + (code & 3) * Nfp + (Nfp - 1 - j));
+    const int R = max(max(exp_bound64(own.x), exp_bound64(own.y)), max(exp_bound64(oth.x), exp_bound64(oth.y)));
+    const int Rs = R == -1100 ? 0 : R;
+    const ff um = d2ff(own.x, Rs), dnm = d2ff(own.y, Rs);
+    ff jm{0.f, 0.f}, av{0.f, 0.f};
+    if (code >= 0) {
+      jm = ff_sub(d2ff(oth.x, Rs), um);
+      av = ff_pow2(ff_sub(dnm, d2ff(oth.y, Rs)), 0.5f);
+    } else if (code == -2) {  // Dirichlet
+      jm = ff_pow2(um, -2.0f);
+      av = dnm;
     }
-    int R = __reduce_max_sync(0xffffffffu, r);
-    if (R == -1100) R = 0;
-    const double* g = gx + 16 * el;
-    const double* c = C1 + be * ldc;
-    const double* ue = u + be * Np;
-    double* y = Y + be * ldy;
-    const ff grr = d2ff(__ldg(g + 1), 0), grs = d2ff(__ldg(g + 2), 0), gss = d2ff(__ldg(g + 3), 0);
-    for (int n = lane; n < Np; n += 32) {
-      const ff ur = d2ff(__ldg(c + n), R), us = d2ff(__ldg(c + Np + n), R);
-      const ff wr = ff_add(ff_mul(grr, ur), ff_mul(grs, us));
-      const ff ws = ff_add(ff_mul(grs, ur), ff_mul(gss, us));
-      y[n] = ff_to_double(wr.h, wr.l, R);
-      y[Np + n] = ff_to_double(ws.h, ws.l, R);
-      if (ldy > 2 * Np + 3 * NFN) {  // Helmholtz column lambda J u
-        const ff lj = ff_mul(lam, d2ff(__ldg(g), 0));
-        const ff v = ff_mul(lj, d2ff(__ldg(ue + n), R));
-        y[2 * Np + 3 * NFN + n] = ff_to_double(v.h, v.l, R);
-      }
-    }
-    if (lane < NFN) {
-      const int f = lane / Nfp, j = lane - f * Nfp;
-      const int kf = fnode(N, f, j);
-      const ff nr = d2ff(__ldg(g + 4 + 4 * f), 0), ns = d2ff(__ldg(g + 5 + 4 * f), 0);
-      const ff sJ = d2ff(__ldg(g + 6 + 4 * f), 0);
-      const ff tau = ff_mul(cpen, d2ff(__ldg(g + 7 + 4 * f), 0));
-      const ff um = d2ff(__ldg(ue + kf), R);
-      const ff dnm = ff_add(ff_mul(nr, d2ff(__ldg(c + kf), R)), ff_mul(ns, d2ff(__ldg(c + Np + kf), R)));
-      const int code = __ldg(conn + 3 * el + f);
-      ff jm{0.f, 0.f}, av{0.f, 0.f};
-      if (code >= 0) {
-        const int64_t nb = boff + (code >> 2);
-        const int fn = code & 3;
-        const int kn = fnode(N, fn, Nfp - 1 - j);
-        const double* gn = gx + 16 * (code >> 2) + 4 + 4 * fn;
-        const double* cn = C1 + nb * ldc;
-        const ff up = d2ff(__ldg(u + nb * Np + kn), R);
-        const ff dnp = ff_add(ff_mul(d2ff(__ldg(gn), 0), d2ff(__ldg(cn + kn), R)),
-                              ff_mul(d2ff(__ldg(gn + 1), 0), d2ff(__ldg(cn + Np + kn), R)));
-        jm = ff_sub(up, um);
-        av = ff_pow2(ff_sub(dnm, dnp), 0.5f);
-      } else if (code == -2) {  // Dirichlet
-        jm = ff_pow2(um, -2.0f);
-        av = dnm;
-      }
-      const ff hs = ff_pow2(ff_mul(sJ, jm), 0.5f);
-      const ff a = ff_mul(nr, hs), b = ff_mul(ns, hs);
-      const ff fl = ff_neg(ff_mul(sJ, ff_add(av, ff_mul(tau, jm))));
-      y[2 * Np + f * Nfp + j] = ff_to_double(a.h, a.l, R);
-      y[2 * Np + NFN + f * Nfp + j] = ff_to_double(b.h, b.l, R);
-      y[2 * Np + 2 * NFN + f * Nfp + j] = ff_to_double(fl.h, fl.l, R);
-    }
+    const ff nr = d2ff(__ldg(g), 0), ns = d2ff(__ldg(g + 1), 0), sJ = d2ff(__ldg(g + 2), 0);
+    const ff tau = ff_mul(cpen, d2ff(__ldg(g + 3), 0));
+    const ff hs = ff_pow2(ff_mul(sJ, jm), 0.5f);
+    const ff a = ff_mul(nr, hs), b = ff_mul(ns, hs);
+    const ff fl = ff_neg(ff_mul(sJ, ff_add(av, ff_mul(tau, jm))));
+    double* y = Y + be * ldy + 2 * Np + i;
+    y[0] = ff_to_double(a.h, a.l, Rs);
+    y[NFN] = ff_to_double(b.h, b.l, Rs);
+    y[2 * NFN] = ff_to_double(fl.h, fl.l, Rs);
   }
 }
 
@@ -464,8 +537,10 @@ void tc64_op_free(Tc64Op* op) {
   op->ea = nullptr;
 }
 
-cudaError_t tc64_gemm_launch(const Tc64Op& op, int64_t rows, const double* X, int64_t ldx, double* out, int64_t ldo,
-                             int* ex_in, int* ex_out, cudaStream_t st) {
+namespace {
+template <int MODE>
+cudaError_t gemm_launch(const Tc64Op& op, int64_t rows, const double* X, int64_t ldx, double* out, int64_t ldo,
+                        const GradOut& go, cudaStream_t st) {
   if (rows <= 0) return cudaSuccess;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -474,24 +549,32 @@ cudaError_t tc64_gemm_launch(const Tc64Op& op, int64_t rows, const double* X, in
   {
     std::lock_guard<std::mutex> lk(table_mutex());
     if (!grid[dev & 63]) {
-      e = cudaFuncSetAttribute(tc64_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+      e = cudaFuncSetAttribute(tc64_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(tc64_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
       int sms = 0;
       if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       if (e != cudaSuccess) return e;
       grid[dev & 63] = sms;  // one CTA per SM (all of tensor memory, most of shared memory)
     }
   }
+  const int vec2 = (ldx % 2 == 0 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0) ? 1 : 0;
   const int64_t tiles = (rows + kT - 1) / kT;
   const unsigned g = unsigned(std::min<int64_t>(tiles, grid[dev & 63]));
-  tc64_gemm<<<g, 512, kSmem, st>>>(rows, op.M, op.K, op.NCH, op.KCH, X, ldx, op.blocks, op.ea, out, ldo, ex_in,
-                                   ex_out);
+  tc64_gemm<MODE><<<g, 512, kSmem, st>>>(rows, op.M, op.K, op.NCH, op.KCH, X, ldx, vec2, op.blocks, op.ea, out, ldo,
+                                         go);
   note_launch();
   return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t tc64_gemm_launch(const Tc64Op& op, int64_t rows, const double* X, int64_t ldx, double* out, int64_t ldo,
+                             cudaStream_t st) {
+  return gemm_launch<0>(op, rows, X, ldx, out, ldo, GradOut{}, st);
 }
 
 namespace {
 struct Tc64Apply {
-  Tc64Op grad;      // [Dr; Ds]
+  Tc64Op grad;       // [Dr; Ds] with rows interleaved (Dr row n, Ds row n, ...)
   Tc64Op out, outh;  // OB, [OB | M]
 };
 Tc64Apply g_t64[64][kMaxN + 1];  // [device][degree]
@@ -499,10 +582,11 @@ Tc64Apply g_t64[64][kMaxN + 1];  // [device][degree]
 cudaError_t build_t64(const RefElem& R, Tc64Apply& o) {
   const int N = R.N, Np = R.Np, Nfp = R.Nfp, NFN = 3 * Nfp;
   std::vector<double> A1(size_t(2 * Np) * Np);
-  for (int i = 0; i < Np * Np; ++i) {
-    A1[i] = R.Dr[i];
-    A1[Np * Np + i] = R.Ds[i];
-  }
+  for (int n = 0; n < Np; ++n)
+    for (int m = 0; m < Np; ++m) {
+      A1[size_t(2 * n) * Np + m] = R.Dr[size_t(n) * Np + m];
+      A1[size_t(2 * n + 1) * Np + m] = R.Ds[size_t(n) * Np + m];
+    }
   const int KY = 2 * Np + 3 * NFN, KH = KY + Np;
   std::vector<double> B(size_t(Np) * KY, 0.0), BH(size_t(Np) * KH, 0.0);
   for (int i = 0; i < Np; ++i) {
@@ -561,10 +645,11 @@ cudaError_t launch_apply_tc64(dg_mesh* m, int degree, int B, double lambda, cons
   }
   const int N = degree, Np = (N + 1) * (N + 2) / 2, NFN = 3 * (N + 1);
   const bool helm = lambda != 0.0;
-  const int ldc = 2 * Np, ldy = 2 * Np + 3 * NFN + (helm ? Np : 0);
+  const int KYH = 2 * Np + 3 * NFN + (helm ? Np : 0);
+  const int ldy = (KYH + 1) & ~1;  // even: 16-byte rows for paired loads
   const int64_t nE = int64_t(B) * m->K;
-  // scratch: C1 [nE][2Np], Y [nE][ldy] (FP64), exponents exu, exc [nE]
-  const size_t words = size_t(nE) * (ldc + ldy) + size_t(nE) + 8;
+  // scratch: Y [nE][ldy] and the face data FN [nE][NFN] (u, n.grad u), FP64
+  const size_t words = size_t(nE) * ldy + size_t(nE) * NFN * 2 + 2;
   if (m->t64_cap < words) {
     cudaFree(m->t64_scratch);
     m->t64_scratch = nullptr;
@@ -575,23 +660,23 @@ cudaError_t launch_apply_tc64(dg_mesh* m, int degree, int B, double lambda, cons
     m->t64_cap = words;
     ++m->scratch_gen;
   }
-  double* C1 = m->t64_scratch;
-  double* Y = C1 + size_t(nE) * ldc;
-  int* exu = reinterpret_cast<int*>(Y + size_t(nE) * ldy);
-  int* exc = exu + nE;
-  e = tc64_gemm_launch(ops->grad, nE, u, Np, C1, ldc, exu, exc, st);
+  double* Y = m->t64_scratch;
+  double2* FN = reinterpret_cast<double2*>(Y + size_t(nE) * ldy);
+  GradOut go{N, m->K, m->geox, Y, ldy, helm ? 1 : 0, lambda, FN};
+  e = gemm_launch<1>(ops->grad, nE, u, Np, nullptr, 0, go, st);
   if (e != cudaSuccess) return e;
   {
     int sms = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    const int64_t blocks = std::min<int64_t>((nE + 7) / 8, int64_t(sms) * 8);
-    tc64_fill<<<unsigned(blocks), 256, 0, st>>>(N, m->K, nE, m->geox, m->conn, u, C1, ldc, exu, exc, lambda, Y, ldy);
+    const int64_t total = nE * NFN;
+    const int64_t blocks = std::min<int64_t>((total + 255) / 256, int64_t(sms) * 16);
+    tc64_face_fill<<<unsigned(blocks), 256, 0, st>>>(N, m->K, nE, m->geox, m->conn, FN, Y, ldy);
     note_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  return tc64_gemm_launch(helm ? ops->outh : ops->out, nE, Y, ldy, Au, Np, nullptr, nullptr, st);
+  return tc64_gemm_launch(helm ? ops->outh : ops->out, nE, Y, ldy, Au, Np, st);
 }
 
 cudaError_t tc64_error(int* flag) {

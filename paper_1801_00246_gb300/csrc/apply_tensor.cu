@@ -929,7 +929,7 @@ void sliced_op_free(SlicedOp* op) {
 
 cudaError_t sliced_gemm(const SlicedOp& op, int64_t rows, const double* X, int64_t ldx, double* out, int64_t ldo,
                         cudaStream_t st) {
-  if (op.t64.blocks) return tc64_gemm_launch(op.t64, rows, X, ldx, out, ldo, nullptr, nullptr, st);
+  if (op.t64.blocks) return tc64_gemm_launch(op.t64, rows, X, ldx, out, ldo, st);
   return gemm<double>(op.Mt, rows, op.M, op.K, op.Kt, reinterpret_cast<const uint4*>(op.A), op.ea, X, ldx, out, ldo,
                       nullptr, st);
 }

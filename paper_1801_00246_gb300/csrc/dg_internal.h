@@ -144,10 +144,9 @@ cudaError_t launch_wait_selftest(double seconds, int* gave_up_dev, cudaStream_t 
 struct Tc64Op;
 cudaError_t tc64_op_create(const std::vector<double>& A, int M, int K, Tc64Op* op);
 void tc64_op_free(Tc64Op* op);
-// out[r][c] = sum_k A[c][k] X[r][k]; ex_in / ex_out (optional, per row): the scale
-// exponent of X's row and an exponent bound of the outputs
+// out[r][c] = sum_k A[c][k] X[r][k] (FP64, exact slicing on the tcgen05 tensor cores)
 cudaError_t tc64_gemm_launch(const Tc64Op& op, int64_t rows, const double* X, int64_t ldx, double* out, int64_t ldo,
-                             int* ex_in, int* ex_out, cudaStream_t st);
+                             cudaStream_t st);
 bool tc64_supported(int degree);
 cudaError_t launch_apply_tc64(dg_mesh* m, int degree, int B, double lambda, const double* u, double* Au,
                               cudaStream_t st);
