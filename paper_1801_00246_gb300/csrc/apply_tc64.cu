@@ -45,7 +45,7 @@ constexpr int kSl = 8;                       // slices of 7 bits
 constexpr int kABytes = kSl * kT * kKC * 2;  // one data chunk, 8 slices: 64 KB
 constexpr int kBBytes = kSl * kNC * kKC * 2; // one operator block, 8 slices: 24 KB
 constexpr int kASlice = kT * kKC * 2, kBSlice = kNC * kKC * 2;
-constexpr int kSmem = 2 * kABytes + 2 * kBBytes + 4 * kT * 4 + 8 * 8;
+constexpr int kSmem = 2 * kABytes + 2 * kBBytes + 4 * kT * 4 + 12 * 8;
 
 __device__ int g_tc64_err;
 
@@ -189,29 +189,45 @@ struct GradOut {
 
 // out[r][c] = sum_k A[c][k] X[r][k] for r < rows, c < M, k < Kd (A sliced in
 // blocks of kNC rows x kKC columns: block (nc, kc) at (nc KCH + kc) kBBytes).
-// With KCH <= 2 the data chunks of a tile stay in shared memory for every
-// output pass; otherwise they stream through the two buffers (one pass). Only
-// warp 0 polls the mbarriers; the other warps meet it at a CTA barrier.
+//
+// Warp-specialised pipeline over a stream of data chunks (tile, output pass
+// nc, column chunk kc), chunk g using shared-memory buffer g & 1:
+//  * warps 0-15 (four threads per row of the 128-row tile) find each row's
+//    scale exponent, slice chunk g into buffer g & 1 once the products of
+//    chunk g - 2 have released it (mbarrier `empty`), signal `full`, and after
+//    a pass's last chunk wait for its accumulators (`acc_full`), drain them
+//    (Horner's rule, epilogue) and release them (`acc_empty`);
+//  * warp 16 loads operator block g by bulk copy, waits for `full`, issues the
+//    36 slice products per 16 columns from one lane and commits to `empty`
+//    (and to `acc_full` after a pass's last chunk); before a pass's first
+//    chunk it waits until the previous pass has been drained.
+// No CTA-wide barrier in the steady state; every wait is bounded in time.
+constexpr int kSlicers = 512;  // threads of warps 0-15
 template <int MODE>
-__global__ void __launch_bounds__(512, 1) tc64_gemm(int64_t rows, int M, int Kd, int NCH, int KCH,
-                                                    const double* __restrict__ X, int64_t ldx, int vec2,
-                                                    const uint8_t* __restrict__ Bops, const int* __restrict__ ea,
-                                                    double* __restrict__ out, int64_t ldo, GradOut go) {
+__global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int M, int Kd, int NCH, int KCH,
+                                                              const double* __restrict__ X, int64_t ldx, int vec2,
+                                                              const uint8_t* __restrict__ Bops,
+                                                              const int* __restrict__ ea, double* __restrict__ out,
+                                                              int64_t ldo, GradOut go) {
   extern __shared__ __align__(1024) uint8_t sm[];
   uint8_t* sA = sm;                        // [2][8 slices][128 rows][32] canonical
   uint8_t* sB = sm + 2 * kABytes;          // [2][8 slices][48 rows][32] canonical
   int* pmax = reinterpret_cast<int*>(sB + 2 * kBBytes);  // [4][kT]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(pmax + 4 * kT);  // mma0, mma1, b0, b1
-  uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 4);
+  // full[2], empty[2], bfull[2], acc_full, acc_empty
+  uint64_t* bars = reinterpret_cast<uint64_t*>(pmax + 4 * kT);
+  uint64_t *full = bars, *empty = bars + 2, *bfull = bars + 4, *acc_full = bars + 6, *acc_empty = bars + 7;
+  uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 8);
   int* abort_flag = reinterpret_cast<int*>(slot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int e = (warp & 3) * 32 + lane;
-  const int q = warp >> 2;
-  const uint32_t lanebase = uint32_t((warp & 3) * 32) << 16;
   const int64_t ntiles = (rows + kT - 1) / kT;
-  const bool resident = KCH <= 2;
   if (tid == 0) {
-    for (int i = 0; i < 4; ++i) tc::mbar_init(bars + i, 1);
+    for (int i = 0; i < 2; ++i) {
+      tc::mbar_init(full + i, kSlicers / 32);  // one arrival per slicing warp
+      tc::mbar_init(empty + i, 1);             // the products' commit
+      tc::mbar_init(bfull + i, 1);             // the bulk copy
+    }
+    tc::mbar_init(acc_full, 1);
+    tc::mbar_init(acc_empty, kSlicers / 32);
     *abort_flag = 0;
     tc::mbar_init_fence();
   }
@@ -221,105 +237,31 @@ __global__ void __launch_bounds__(512, 1) tc64_gemm(int64_t rows, int M, int Kd,
   tc::fence_after();
   const uint32_t tb = *slot;
   constexpr uint32_t idesc = tc::idesc_f16(128, kNC, true);
-  uint32_t cnt = 0;  // operator blocks (and products) issued by this CTA
-  auto load8 = [&](const double* xr, bool live, int k0, double (&v)[8]) {
-    if (live && vec2 && k0 + 8 <= Kd) {
-      const double2* p2 = reinterpret_cast<const double2*>(xr + k0);
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const double2 w = __ldg(p2 + t);
-        v[2 * t] = w.x;
-        v[2 * t + 1] = w.y;
-      }
-    } else {
-#pragma unroll
-      for (int t = 0; t < 8; ++t) v[t] = (live && k0 + t < Kd) ? __ldg(xr + k0 + t) : 0.0;
-    }
-  };
-  auto slice_chunk = [&](const double (&v)[8], int E, uint32_t buf) {
-    uint64_t I[8];
-    uint32_t sg[8];
-#pragma unroll
-    for (int t = 0; t < 8; ++t) I[t] = fixed56(v[t], E, sg[t]);
-    uint8_t* dst = sA + buf * kABytes + (e >> 3) * 512 + q * 128 + (e & 7) * 16;
-#pragma unroll
-    for (int j = 0; j < kSl; ++j) {
-      uint4 w;
-      w.x = slice_bits(I[0], j, sg[0]) | (slice_bits(I[1], j, sg[1]) << 16);
-      w.y = slice_bits(I[2], j, sg[2]) | (slice_bits(I[3], j, sg[3]) << 16);
-      w.z = slice_bits(I[4], j, sg[4]) | (slice_bits(I[5], j, sg[5]) << 16);
-      w.w = slice_bits(I[6], j, sg[6]) | (slice_bits(I[7], j, sg[7]) << 16);
-      *reinterpret_cast<uint4*>(dst + j * kASlice) = w;
-    }
-  };
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t row = tile * kT + e;
-    const bool live = row < rows;
-    const double* xr = X + (live ? row : 0) * ldx;
-    // scale exponent of the row: the largest |X[row][k]| < 2^E
-    double v0[8], v1[8];  // resident mode: the thread's values of chunks 0 and 1
-    int em = -1100;
-    if (resident) {
-      load8(xr, live, 8 * q, v0);
-      load8(xr, live, kKC + 8 * q, v1);
-#pragma unroll
-      for (int t = 0; t < 8; ++t) em = max(em, max(exp_bound64(v0[t]), KCH > 1 ? exp_bound64(v1[t]) : -1100));
-    } else if (live) {
-      for (int kc = 0; kc < KCH; ++kc) {
-        double v[8];
-        load8(xr, live, kc * kKC + 8 * q, v);
-#pragma unroll
-        for (int t = 0; t < 8; ++t) em = max(em, exp_bound64(v[t]));
-      }
-    }
-    pmax[q * kT + e] = em;
-    // the previous tile's products are complete (its last drain waited), so
-    // both data buffers are free here
-    __syncthreads();
-    int E = max(max(pmax[e], pmax[kT + e]), max(pmax[2 * kT + e], pmax[3 * kT + e]));
-    if (E == -1100) E = 0;
-    if (resident) {
-      slice_chunk(v0, E, 0);
-      if (KCH > 1) slice_chunk(v1, E, 1);
-      tc::fence_async_smem();
-    }
-    float gh[6];  // MODE 1: Grr, Grs, Gss as float-float
-    if (MODE == 1) {
-      const int64_t el = (live ? row : 0) % go.K;
-      const double* g = go.gx + 16 * el;
-#pragma unroll
-      for (int t = 0; t < 3; ++t) {
-        const ff gf = d2ff(__ldg(g + 1 + t), 0);
-        gh[2 * t] = gf.h;
-        gh[2 * t + 1] = gf.l;
-      }
-    }
-    for (int nc = 0; nc < NCH; ++nc) {
-      for (int kc = 0; kc < KCH; ++kc, ++cnt) {
-        const uint32_t sb_i = cnt & 1u;
-        // the operator stage (and, streaming, the data buffer) of block cnt - 2 is
-        // free once that block's products completed
-        if (warp == 0 && cnt >= 2 && !tc::mbar_wait(bars + sb_i, ((cnt - 2) >> 1) & 1u)) *abort_flag = 1;
-        __syncthreads();
-        if (tid == 0) {
-          tc::mbar_expect_tx(bars + 2 + sb_i, kBBytes);
-          tc::bulk_g2s(sB + sb_i * kBBytes, Bops + size_t(nc * KCH + kc) * kBBytes, kBBytes, bars + 2 + sb_i);
-        }
-        uint32_t abuf = kc;
-        if (!resident) {
-          abuf = sb_i;
-          double v[8];
-          load8(xr, live, kc * kKC + 8 * q, v);
-          slice_chunk(v, E, abuf);
-        }
-        if (!resident) tc::fence_async_smem();
-        tc::fence_before();
-        __syncthreads();  // the data chunk (sliced above, or at the tile's start) is in place
-        if (warp == 0) {  // the whole warp waits for the operator block, lane 0 issues
-          tc::fence_after();
-          if (!tc::mbar_wait(bars + 2 + sb_i, (cnt >> 1) & 1u)) *abort_flag = 1;
+
+  if (warp == kSlicers / 32) {
+    // ================= products
+    uint32_t g = 0, pass = 0;
+    const uint64_t adesc0 = tc::smem_desc(tc::smem_addr(sA), 128, (kKC / 8) * 128);
+    const uint64_t bdesc0 = tc::smem_desc(tc::smem_addr(sB), 128, (kKC / 8) * 128);
+    for (int64_t tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
+      for (int nc = 0; nc < NCH; ++nc, ++pass) {
+        // the accumulators are free once the previous pass has been drained
+        if (pass > 0 && !tc::mbar_wait(acc_empty, (pass - 1) & 1u)) *abort_flag = 1;
+        tc::fence_after();
+        for (int kc = 0; kc < KCH; ++kc, ++g) {
+          const uint32_t b = g & 1u;
+          // the operator stage is free once chunk g - 2's products completed
+          if (g >= 2 && !tc::mbar_wait(empty + b, ((g - 2) >> 1) & 1u)) *abort_flag = 1;
           if (lane == 0) {
-            const uint32_t sa = tc::smem_addr(sA + abuf * kABytes), sb = tc::smem_addr(sB + sb_i * kBBytes);
+            tc::mbar_expect_tx(bfull + b, kBBytes);
+            tc::bulk_g2s(sB + b * kBBytes, Bops + size_t(nc * KCH + kc) * kBBytes, kBBytes, bfull + b);
+          }
+          __syncwarp();
+          if (!tc::mbar_wait(full + b, (g >> 1) & 1u)) *abort_flag = 1;
+          if (!tc::mbar_wait(bfull + b, (g >> 1) & 1u)) *abort_flag = 1;
+          tc::fence_after();
+          if (lane == 0) {
+            const uint64_t ab = adesc0 + ((b * kABytes) >> 4), bb = bdesc0 + ((b * kBBytes) >> 4);
             uint32_t started = kc > 0 ? 0xffu : 0u;
 #pragma unroll
             for (int ks = 0; ks < kKC / 16; ++ks)
@@ -328,96 +270,182 @@ __global__ void __launch_bounds__(512, 1) tc64_gemm(int64_t rows, int M, int Kd,
 #pragma unroll
                 for (int j = 0; j < kSl - i; ++j) {
                   const int s = i + j;
-                  const uint64_t ad = tc::smem_desc(sa + j * kASlice + ks * 256, 128, (kKC / 8) * 128);
-                  const uint64_t bd = tc::smem_desc(sb + i * kBSlice + ks * 256, 128, (kKC / 8) * 128);
-                  tc::mma_ss(tb + s * kNC, ad, bd, idesc, (started >> s) & 1u);
+                  tc::mma_ss(tb + s * kNC, ab + ((j * kASlice + ks * 256) >> 4), bb + ((i * kBSlice + ks * 256) >> 4),
+                             idesc, (started >> s) & 1u);
                   started |= 1u << s;
                 }
-            tc::mma_commit(bars + sb_i);
+            tc::mma_commit(empty + b);
+            if (kc == KCH - 1) tc::mma_commit(acc_full);
           }
           __syncwarp();
         }
       }
-      // drain: output columns [12q, 12q + 12) of this pass
-      const uint32_t last = cnt - 1;
-      if (warp == 0 && !tc::mbar_wait(bars + (last & 1u), (last >> 1) & 1u)) *abort_flag = 1;
-      __syncthreads();
-      tc::fence_after();
-#pragma unroll 1
-      for (int p = 0; p < 3; ++p) {
-        const int c0 = 12 * q + 4 * p;
-        uint32_t acc[kSl][4];
+    }
+  } else {
+    // ================= slicing and epilogue
+    const int e = (warp & 3) * 32 + lane;
+    const int q = warp >> 2;
+    const uint32_t lanebase = uint32_t((warp & 3) * 32) << 16;
+    uint32_t g = 0, pass = 0;
+    auto load8 = [&](const double* xr, bool live, int k0, double (&v)[8]) {
+      if (live && vec2 && k0 + 8 <= Kd) {
+        const double2* p2 = reinterpret_cast<const double2*>(xr + k0);
 #pragma unroll
-        for (int s = 0; s < kSl; ++s) {
-          uint32_t v[4];
-          tc::tmem_ld4(tb + lanebase + s * kNC + c0, v);
-#pragma unroll
-          for (int c = 0; c < 4; ++c) acc[s][c] = v[c];
+        for (int t = 0; t < 4; ++t) {
+          const double2 w = __ldg(p2 + t);
+          v[2 * t] = w.x;
+          v[2 * t + 1] = w.y;
         }
-        tc::tmem_wait_ld();
-        if (MODE == 0) {
+      } else {
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const int col = nc * kNC + c0 + c;
-            if (live && col < M) {
-              // value = 2^{ea + E - 14} sum_s acc_s 2^{-7 s}
-              const ff hl = horner8(acc, c);
-              out[row * ldo + col] = ff_to_double(hl.h, hl.l, __ldg(ea + col) + E - 14);
-            }
+        for (int t = 0; t < 8; ++t) v[t] = (live && k0 + t < Kd) ? __ldg(xr + k0 + t) : 0.0;
+      }
+    };
+    for (int64_t tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
+      const int64_t row = tile * kT + e;
+      const bool live = row < rows;
+      const double* xr = X + (live ? row : 0) * ldx;
+      // scale exponent of the row: the largest |X[row][k]| < 2^E
+      int em = -1100;
+      if (live)
+        for (int kc = 0; kc < KCH; ++kc) {
+          double v[8];
+          load8(xr, live, kc * kKC + 8 * q, v);
+#pragma unroll
+          for (int t = 0; t < 8; ++t) em = max(em, exp_bound64(v[t]));
+        }
+      asm volatile("bar.sync 1, %0;\n" ::"r"(kSlicers) : "memory");  // pmax free (previous tile read it)
+      pmax[q * kT + e] = em;
+      asm volatile("bar.sync 1, %0;\n" ::"r"(kSlicers) : "memory");
+      int E = max(max(pmax[e], pmax[kT + e]), max(pmax[2 * kT + e], pmax[3 * kT + e]));
+      if (E == -1100) E = 0;
+      float gh[6];  // MODE 1: Grr, Grs, Gss as float-float
+      if (MODE == 1) {
+        const int64_t el = (live ? row : 0) % go.K;
+        const double* gg = go.gx + 16 * el;
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+          const ff gf = d2ff(__ldg(gg + 1 + t), 0);
+          gh[2 * t] = gf.h;
+          gh[2 * t + 1] = gf.l;
+        }
+      }
+      for (int nc = 0; nc < NCH; ++nc, ++pass) {
+        for (int kc = 0; kc < KCH; ++kc, ++g) {
+          const uint32_t b = g & 1u;
+          double v[8];
+          load8(xr, live, kc * kKC + 8 * q, v);
+          uint64_t I[8];
+          uint32_t sg[8];
+#pragma unroll
+          for (int t = 0; t < 8; ++t) I[t] = fixed56(v[t], E, sg[t]);
+          // buffer b is free once chunk g - 2's products completed
+          if (g >= 2 && !tc::mbar_wait(empty + b, ((g - 2) >> 1) & 1u)) *abort_flag = 1;
+          uint8_t* dst = sA + b * kABytes + (e >> 3) * 512 + q * 128 + (e & 7) * 16;
+#pragma unroll
+          for (int j = 0; j < kSl; ++j) {
+            uint4 w;
+            w.x = slice_bits(I[0], j, sg[0]) | (slice_bits(I[1], j, sg[1]) << 16);
+            w.y = slice_bits(I[2], j, sg[2]) | (slice_bits(I[3], j, sg[3]) << 16);
+            w.z = slice_bits(I[4], j, sg[4]) | (slice_bits(I[5], j, sg[5]) << 16);
+            w.w = slice_bits(I[6], j, sg[6]) | (slice_bits(I[7], j, sg[7]) << 16);
+            *reinterpret_cast<uint4*>(dst + j * kASlice) = w;
           }
-        } else {
-          // nodes n = col / 2: (ur, us) in columns (2n, 2n + 1)
-          const int N = go.N, Np = (N + 1) * (N + 2) / 2, Nfp = N + 1, NFN = 3 * Nfp;
+          tc::fence_async_smem();
+          __syncwarp();
+          if (lane == 0) asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(
+                                          tc::smem_addr(full + b))
+                                      : "memory");
+        }
+        // drain: output columns [12q, 12q + 12) of this pass
+        if (!tc::mbar_wait(acc_full, pass & 1u)) *abort_flag = 1;
+        tc::fence_after();
+#pragma unroll 1
+        for (int p = 0; p < 3; ++p) {
+          const int c0 = 12 * q + 4 * p;
+          uint32_t acc[kSl][4];
 #pragma unroll
-          for (int c = 0; c < 4; c += 2) {
-            const int n = (nc * kNC + c0 + c) >> 1;
-            if (live && n < Np) {
-              const int er = __ldg(ea + 2 * n), es = __ldg(ea + 2 * n + 1);
-              const int ec = max(er, es);
-              ff ur = horner8(acc, c), us = horner8(acc, c + 1);
-              ur = ff_pow2(ur, __uint_as_float(uint32_t(127 + er - ec) << 23));
-              us = ff_pow2(us, __uint_as_float(uint32_t(127 + es - ec) << 23));
-              const int S = ec + E - 14;  // ur, us, wr, ws, n.grad u all carry 2^S
-              const ff grr{gh[0], gh[1]}, grs{gh[2], gh[3]}, gss{gh[4], gh[5]};
-              const ff wr = ff_add(ff_mul(grr, ur), ff_mul(grs, us));
-              const ff ws = ff_add(ff_mul(grs, ur), ff_mul(gss, us));
-              double* yr = go.Y + row * go.ldy;
-              yr[n] = ff_to_double(wr.h, wr.l, S);
-              yr[Np + n] = ff_to_double(ws.h, ws.l, S);
-              const double un = __ldg(X + row * ldx + n);
-              const int64_t el = row % go.K;
-              const double* g = go.gx + 16 * el;
-              if (go.helm) {
-                const int eu = exp_bound64(un);
-                const ff lj = ff_mul(d2ff(go.lambda, 0), d2ff(__ldg(g), 0));
-                const ff v = ff_mul(lj, d2ff(un, eu));
-                yr[2 * Np + 3 * NFN + n] = ff_to_double(v.h, v.l, eu);
+          for (int s = 0; s < kSl; ++s) {
+            uint32_t vv[4];
+            tc::tmem_ld4(tb + lanebase + s * kNC + c0, vv);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[s][c] = vv[c];
+          }
+          tc::tmem_wait_ld();
+          if (p == 2) {  // the accumulators are read: release them to the next pass
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0) asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(
+                                            tc::smem_addr(acc_empty))
+                                        : "memory");
+          }
+          if (MODE == 0) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              const int col = nc * kNC + c0 + c;
+              if (live && col < M) {
+                // value = 2^{ea + E - 14} sum_s acc_s 2^{-7 s}
+                const ff hl = horner8(acc, c);
+                out[row * ldo + col] = ff_to_double(hl.h, hl.l, __ldg(ea + col) + E - 14);
               }
-              // face data at the face nodes this node is (a corner belongs to two faces)
-              int rrow = 0;
-              while (n >= (rrow + 1) * (N + 1) - (rrow + 1) * rrow / 2) ++rrow;  // n's row of constant s
-              const int rs0 = rrow * (N + 1) - rrow * (rrow - 1) / 2, len = N + 1 - rrow;
-              int fj[2][2], nf = 0;
-              if (rrow == 0) fj[nf][0] = 0, fj[nf][1] = n, ++nf;                    // face 0, j = n
-              if (n == rs0 + len - 1) fj[nf][0] = 1, fj[nf][1] = rrow, ++nf;        // face 1, j = row
-              if (n == rs0 && nf < 2) fj[nf][0] = 2, fj[nf][1] = N - rrow, ++nf;   // face 2, j = N - row
+            }
+          } else {
+            // nodes n = col / 2: (ur, us) in columns (2n, 2n + 1)
+            const int N = go.N, Np = (N + 1) * (N + 2) / 2, Nfp = N + 1, NFN = 3 * Nfp;
 #pragma unroll
-              for (int t = 0; t < 2; ++t) {
-                if (t < nf) {
-                  const int f = fj[t][0], j = fj[t][1];
-                  const ff nr = d2ff(__ldg(g + 4 + 4 * f), 0), ns = d2ff(__ldg(g + 5 + 4 * f), 0);
-                  const ff dn = ff_add(ff_mul(nr, ur), ff_mul(ns, us));
-                  go.FN[row * NFN + f * Nfp + j] = make_double2(un, ff_to_double(dn.h, dn.l, S));
+            for (int c = 0; c < 4; c += 2) {
+              const int n = (nc * kNC + c0 + c) >> 1;
+              if (live && n < Np) {
+                const int er = __ldg(ea + 2 * n), es = __ldg(ea + 2 * n + 1);
+                const int ec = max(er, es);
+                ff ur = horner8(acc, c), us = horner8(acc, c + 1);
+                ur = ff_pow2(ur, __uint_as_float(uint32_t(127 + er - ec) << 23));
+                us = ff_pow2(us, __uint_as_float(uint32_t(127 + es - ec) << 23));
+                const int S = ec + E - 14;  // ur, us, wr, ws, n.grad u all carry 2^S
+                const ff grr{gh[0], gh[1]}, grs{gh[2], gh[3]}, gss{gh[4], gh[5]};
+                const ff wr = ff_add(ff_mul(grr, ur), ff_mul(grs, us));
+                const ff ws = ff_add(ff_mul(grs, ur), ff_mul(gss, us));
+                double* yr = go.Y + row * go.ldy;
+                yr[n] = ff_to_double(wr.h, wr.l, S);
+                yr[Np + n] = ff_to_double(ws.h, ws.l, S);
+                const double un = __ldg(X + row * ldx + n);
+                const int64_t el = row % go.K;
+                const double* gg = go.gx + 16 * el;
+                if (go.helm) {
+                  const int eu = exp_bound64(un);
+                  const ff lj = ff_mul(d2ff(go.lambda, 0), d2ff(__ldg(gg), 0));
+                  const ff vv = ff_mul(lj, d2ff(un, eu));
+                  yr[2 * Np + 3 * NFN + n] = ff_to_double(vv.h, vv.l, eu);
+                }
+                // face data at the face nodes this node is (a corner belongs to two faces)
+                int rrow = 0;
+                while (n >= (rrow + 1) * (N + 1) - (rrow + 1) * rrow / 2) ++rrow;  // n's row of constant s
+                const int rs0 = rrow * (N + 1) - rrow * (rrow - 1) / 2, len = N + 1 - rrow;
+                int fa = -1, ja = 0, fb = -1, jb = 0;
+                if (rrow == 0) fa = 0, ja = n;                         // face 0, j = n
+                if (n == rs0 + len - 1) {                              // face 1, j = row
+                  if (fa < 0) fa = 1, ja = rrow;
+                  else fb = 1, jb = rrow;
+                }
+                if (n == rs0 && fb < 0) {                              // face 2, j = N - row
+                  if (fa < 0) fa = 2, ja = N - rrow;
+                  else fb = 2, jb = N - rrow;
+                }
+#pragma unroll
+                for (int t = 0; t < 2; ++t) {
+                  const int f = t == 0 ? fa : fb, j = t == 0 ? ja : jb;
+                  if (f >= 0) {
+                    const ff nr = d2ff(__ldg(gg + 4 + 4 * f), 0), ns = d2ff(__ldg(gg + 5 + 4 * f), 0);
+                    const ff dn = ff_add(ff_mul(nr, ur), ff_mul(ns, us));
+                    go.FN[row * NFN + f * Nfp + j] = make_double2(un, ff_to_double(dn.h, dn.l, S));
+                  }
                 }
               }
             }
           }
         }
       }
-      tc::fence_before();
-      __syncthreads();  // the accumulators are read; the next pass may overwrite them
     }
-    if (*abort_flag) break;
   }
   if (*abort_flag && tid == 0) atomicExch(&g_tc64_err, 1);
   tc::fence_before();
@@ -560,8 +588,8 @@ cudaError_t gemm_launch(const Tc64Op& op, int64_t rows, const double* X, int64_t
   const int vec2 = (ldx % 2 == 0 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0) ? 1 : 0;
   const int64_t tiles = (rows + kT - 1) / kT;
   const unsigned g = unsigned(std::min<int64_t>(tiles, grid[dev & 63]));
-  tc64_gemm<MODE><<<g, 512, kSmem, st>>>(rows, op.M, op.K, op.NCH, op.KCH, X, ldx, vec2, op.blocks, op.ea, out, ldo,
-                                         go);
+  tc64_gemm<MODE><<<g, kSlicers + 32, kSmem, st>>>(rows, op.M, op.K, op.NCH, op.KCH, X, ldx, vec2, op.blocks, op.ea,
+                                                   out, ldo, go);
   note_launch();
   return cudaGetLastError();
 }
