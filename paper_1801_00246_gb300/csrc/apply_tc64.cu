@@ -185,6 +185,7 @@ struct GradOut {
   int ldy, helm;
   double lambda;
   double2* FN;  // [rows][3 (N+1)]
+  int* exy;     // [rows]: largest exponent of the row's Y values (for the output product)
 };
 
 // out[r][c] = sum_k A[c][k] X[r][k] for r < rows, c < M, k < Kd (A sliced in
@@ -206,6 +207,7 @@ constexpr int kSlicers = 512;  // threads of warps 0-15
 template <int MODE>
 __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int M, int Kd, int NCH, int KCH,
                                                               const double* __restrict__ X, int64_t ldx, int vec2,
+                                                              const int* __restrict__ ex_given,
                                                               const uint8_t* __restrict__ Bops,
                                                               const int* __restrict__ ea, double* __restrict__ out,
                                                               int64_t ldo, GradOut go) {
@@ -305,20 +307,32 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
       const int64_t row = tile * kT + e;
       const bool live = row < rows;
       const double* xr = X + (live ? row : 0) * ldx;
-      // scale exponent of the row: the largest |X[row][k]| < 2^E
-      int em = -1100;
-      if (live)
-        for (int kc = 0; kc < KCH; ++kc) {
-          double v[8];
-          load8(xr, live, kc * kKC + 8 * q, v);
+      // scale exponent of the row: a bound |X[row][k]| < 2^E, given by the producer
+      // of X or found here
+      int E;
+      double vn[8];  // the next chunk's values (loaded one chunk ahead)
+      if (ex_given) {
+        E = live ? __ldg(ex_given + row) : 0;
+        if (E == -1100) E = 0;
+      } else {
+        int em = -1100;
+        if (live) {
+          double v[2][8];
+          for (int kc = 0; kc < KCH; kc += 2) {
+            load8(xr, live, kc * kKC + 8 * q, v[0]);
+            load8(xr, live && kc + 1 < KCH, (kc + 1) * kKC + 8 * q, v[1]);
 #pragma unroll
-          for (int t = 0; t < 8; ++t) em = max(em, exp_bound64(v[t]));
+            for (int t = 0; t < 8; ++t) em = max(em, max(exp_bound64(v[0][t]), exp_bound64(v[1][t])));
+          }
         }
-      asm volatile("bar.sync 1, %0;\n" ::"r"(kSlicers) : "memory");  // pmax free (previous tile read it)
-      pmax[q * kT + e] = em;
-      asm volatile("bar.sync 1, %0;\n" ::"r"(kSlicers) : "memory");
-      int E = max(max(pmax[e], pmax[kT + e]), max(pmax[2 * kT + e], pmax[3 * kT + e]));
-      if (E == -1100) E = 0;
+        asm volatile("bar.sync 1, %0;\n" ::"r"(kSlicers) : "memory");  // pmax free (previous tile read it)
+        pmax[q * kT + e] = em;
+        asm volatile("bar.sync 1, %0;\n" ::"r"(kSlicers) : "memory");
+        E = max(max(pmax[e], pmax[kT + e]), max(pmax[2 * kT + e], pmax[3 * kT + e]));
+        if (E == -1100) E = 0;
+      }
+      load8(xr, live, 8 * q, vn);
+      int ymax = -1100;  // MODE 1: largest exponent of the Y columns this thread writes
       float gh[6];  // MODE 1: Grr, Grs, Gss as float-float
       if (MODE == 1) {
         const int64_t el = (live ? row : 0) % go.K;
@@ -334,7 +348,12 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
         for (int kc = 0; kc < KCH; ++kc, ++g) {
           const uint32_t b = g & 1u;
           double v[8];
-          load8(xr, live, kc * kKC + 8 * q, v);
+#pragma unroll
+          for (int t = 0; t < 8; ++t) v[t] = vn[t];
+          {  // request the next chunk of this row (the next pass starts again at chunk 0)
+            const int kn = kc + 1 < KCH ? kc + 1 : 0;
+            if (kc + 1 < KCH || nc + 1 < NCH) load8(xr, live, kn * kKC + 8 * q, vn);
+          }
           uint64_t I[8];
           uint32_t sg[8];
 #pragma unroll
@@ -406,8 +425,10 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
                 const ff wr = ff_add(ff_mul(grr, ur), ff_mul(grs, us));
                 const ff ws = ff_add(ff_mul(grs, ur), ff_mul(gss, us));
                 double* yr = go.Y + row * go.ldy;
-                yr[n] = ff_to_double(wr.h, wr.l, S);
-                yr[Np + n] = ff_to_double(ws.h, ws.l, S);
+                const double dwr = ff_to_double(wr.h, wr.l, S), dws = ff_to_double(ws.h, ws.l, S);
+                yr[n] = dwr;
+                yr[Np + n] = dws;
+                ymax = max(ymax, max(exp_bound64(dwr), exp_bound64(dws)));
                 const double un = __ldg(X + row * ldx + n);
                 const int64_t el = row % go.K;
                 const double* gg = go.gx + 16 * el;
@@ -415,7 +436,9 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
                   const int eu = exp_bound64(un);
                   const ff lj = ff_mul(d2ff(go.lambda, 0), d2ff(__ldg(gg), 0));
                   const ff vv = ff_mul(lj, d2ff(un, eu));
-                  yr[2 * Np + 3 * NFN + n] = ff_to_double(vv.h, vv.l, eu);
+                  const double dv = ff_to_double(vv.h, vv.l, eu);
+                  yr[2 * Np + 3 * NFN + n] = dv;
+                  ymax = max(ymax, exp_bound64(dv));
                 }
                 // face data at the face nodes this node is (a corner belongs to two faces)
                 int rrow = 0;
@@ -445,6 +468,13 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
           }
         }
       }
+      if (MODE == 1) {  // the row's largest Y exponent so far (the face columns add theirs)
+        asm volatile("bar.sync 1, %0;\n" ::"r"(kSlicers) : "memory");
+        pmax[q * kT + e] = ymax;
+        asm volatile("bar.sync 1, %0;\n" ::"r"(kSlicers) : "memory");
+        if (q == 0 && live)
+          go.exy[row] = max(max(pmax[e], pmax[kT + e]), max(pmax[2 * kT + e], pmax[3 * kT + e]));
+      }
     }
   }
   if (*abort_flag && tid == 0) atomicExch(&g_tc64_err, 1);
@@ -460,11 +490,11 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
 // product), Y[2Np + i] = 1/2 nr sJ [u], Y[2Np + NFN + i] = 1/2 ns sJ [u],
 // Y[2Np + 2 NFN + i] = -sJ ({n.grad u} + tau [u]), in float-float scaled by
 // the entry's largest input; the row's largest exponent per element
-// (ex_y, atomically) for the output product's slicing.
+// (exy, raised atomically) for the output product's slicing.
 __global__ void __launch_bounds__(256) tc64_face_fill(int N, int64_t K, int64_t nE, const double* __restrict__ gx,
                                                       const int32_t* __restrict__ conn,
                                                       const double2* __restrict__ FN, double* __restrict__ Y,
-                                                      int ldy) {
+                                                      int ldy, int* __restrict__ exy) {
   const int Np = (N + 1) * (N + 2) / 2, Nfp = N + 1, NFN = 3 * Nfp;
   const int64_t total = nE * NFN;
   const ff cpen{float((N + 1) * (N + 2)) * 0.5f, 0.f};
@@ -495,9 +525,12 @@ __global__ void __launch_bounds__(256) tc64_face_fill(int N, int64_t K, int64_t 
     const ff a = ff_mul(nr, hs), b = ff_mul(ns, hs);
     const ff fl = ff_neg(ff_mul(sJ, ff_add(av, ff_mul(tau, jm))));
     double* y = Y + be * ldy + 2 * Np + i;
-    y[0] = ff_to_double(a.h, a.l, Rs);
-    y[NFN] = ff_to_double(b.h, b.l, Rs);
-    y[2 * NFN] = ff_to_double(fl.h, fl.l, Rs);
+    const double da = ff_to_double(a.h, a.l, Rs), db = ff_to_double(b.h, b.l, Rs), dc = ff_to_double(fl.h, fl.l, Rs);
+    y[0] = da;
+    y[NFN] = db;
+    y[2 * NFN] = dc;
+    const int ym = max(exp_bound64(da), max(exp_bound64(db), exp_bound64(dc)));
+    if (ym > -1100) atomicMax(exy + be, ym);  // the row's bound: the volume columns' (set before) and these
   }
 }
 
@@ -568,7 +601,7 @@ void tc64_op_free(Tc64Op* op) {
 namespace {
 template <int MODE>
 cudaError_t gemm_launch(const Tc64Op& op, int64_t rows, const double* X, int64_t ldx, double* out, int64_t ldo,
-                        const GradOut& go, cudaStream_t st) {
+                        const int* ex_given, const GradOut& go, cudaStream_t st) {
   if (rows <= 0) return cudaSuccess;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -588,8 +621,8 @@ cudaError_t gemm_launch(const Tc64Op& op, int64_t rows, const double* X, int64_t
   const int vec2 = (ldx % 2 == 0 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0) ? 1 : 0;
   const int64_t tiles = (rows + kT - 1) / kT;
   const unsigned g = unsigned(std::min<int64_t>(tiles, grid[dev & 63]));
-  tc64_gemm<MODE><<<g, kSlicers + 32, kSmem, st>>>(rows, op.M, op.K, op.NCH, op.KCH, X, ldx, vec2, op.blocks, op.ea,
-                                                   out, ldo, go);
+  tc64_gemm<MODE><<<g, kSlicers + 32, kSmem, st>>>(rows, op.M, op.K, op.NCH, op.KCH, X, ldx, vec2, ex_given,
+                                                   op.blocks, op.ea, out, ldo, go);
   note_launch();
   return cudaGetLastError();
 }
@@ -597,7 +630,7 @@ cudaError_t gemm_launch(const Tc64Op& op, int64_t rows, const double* X, int64_t
 
 cudaError_t tc64_gemm_launch(const Tc64Op& op, int64_t rows, const double* X, int64_t ldx, double* out, int64_t ldo,
                              cudaStream_t st) {
-  return gemm_launch<0>(op, rows, X, ldx, out, ldo, GradOut{}, st);
+  return gemm_launch<0>(op, rows, X, ldx, out, ldo, nullptr, GradOut{}, st);
 }
 
 namespace {
@@ -676,8 +709,9 @@ cudaError_t launch_apply_tc64(dg_mesh* m, int degree, int B, double lambda, cons
   const int KYH = 2 * Np + 3 * NFN + (helm ? Np : 0);
   const int ldy = (KYH + 1) & ~1;  // even: 16-byte rows for paired loads
   const int64_t nE = int64_t(B) * m->K;
-  // scratch: Y [nE][ldy] and the face data FN [nE][NFN] (u, n.grad u), FP64
-  const size_t words = size_t(nE) * ldy + size_t(nE) * NFN * 2 + 2;
+  // scratch: Y [nE][ldy], the face data FN [nE][NFN] (u, n.grad u), FP64, and the
+  // rows' largest Y exponents
+  const size_t words = size_t(nE) * ldy + size_t(nE) * NFN * 2 + size_t(nE + 1) / 2 + 2;
   if (m->t64_cap < words) {
     cudaFree(m->t64_scratch);
     m->t64_scratch = nullptr;
@@ -690,8 +724,9 @@ cudaError_t launch_apply_tc64(dg_mesh* m, int degree, int B, double lambda, cons
   }
   double* Y = m->t64_scratch;
   double2* FN = reinterpret_cast<double2*>(Y + size_t(nE) * ldy);
-  GradOut go{N, m->K, m->geox, Y, ldy, helm ? 1 : 0, lambda, FN};
-  e = gemm_launch<1>(ops->grad, nE, u, Np, nullptr, 0, go, st);
+  int* exy = reinterpret_cast<int*>(FN + size_t(nE) * NFN);
+  GradOut go{N, m->K, m->geox, Y, ldy, helm ? 1 : 0, lambda, FN, exy};
+  e = gemm_launch<1>(ops->grad, nE, u, Np, nullptr, 0, nullptr, go, st);
   if (e != cudaSuccess) return e;
   {
     int sms = 0;
@@ -699,12 +734,12 @@ cudaError_t launch_apply_tc64(dg_mesh* m, int degree, int B, double lambda, cons
     if (e != cudaSuccess) return e;
     const int64_t total = nE * NFN;
     const int64_t blocks = std::min<int64_t>((total + 255) / 256, int64_t(sms) * 16);
-    tc64_face_fill<<<unsigned(blocks), 256, 0, st>>>(N, m->K, nE, m->geox, m->conn, FN, Y, ldy);
+    tc64_face_fill<<<unsigned(blocks), 256, 0, st>>>(N, m->K, nE, m->geox, m->conn, FN, Y, ldy, exy);
     note_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  return tc64_gemm_launch(helm ? ops->outh : ops->out, nE, Y, ldy, Au, Np, st);
+  return gemm_launch<0>(helm ? ops->outh : ops->out, nE, Y, ldy, Au, Np, exy, GradOut{}, st);
 }
 
 cudaError_t tc64_error(int* flag) {
