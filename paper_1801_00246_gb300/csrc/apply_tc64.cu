@@ -360,27 +360,68 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
       int E = 0, R = 0;
       int codes[3] = {-1, -1, -1};
       if (MODE == 2) {
-        // inputs scaled by 2^-R (R bounds C1 and the face data of the element and its
-        // neighbours), so every scaled input is below 1 and Y stays below the geometry
-        // bounds; E bounds Y relative to 2^R
+        // inputs scaled by 2^-R, R bounding C1 and the face data of the element and
+        // its neighbours (so scaled values stay in the FP32 range); E from the row's
+        // largest |Y| (relative to 2^R), found by a float pre-pass over this thread's
+        // columns (float estimates within 2^-20 of Y: a margin factor covers them)
         int r = live ? max(__ldg(ap.exc + row), __ldg(ap.exfn + row)) : -1100;
-        float gb = 0.f;
         if (live) {
-          const float grr = fabsf(float(__ldg(gg + 1))), grs = fabsf(float(__ldg(gg + 2))),
-                      gss = fabsf(float(__ldg(gg + 3)));
-          gb = fmaxf(grr + grs, grs + gss);
-          const float cp = float((N + 1) * (N + 2)) * 0.5f;
 #pragma unroll
           for (int f = 0; f < 3; ++f) {
             codes[f] = __ldg(ap.conn + 3 * el + f);
             if (codes[f] >= 0) r = max(r, __ldg(ap.exfn + boff + (codes[f] >> 2)));
-            const float nr = fabsf(float(__ldg(gg + 4 + 4 * f))), ns = fabsf(float(__ldg(gg + 5 + 4 * f)));
-            const float sJ = fabsf(float(__ldg(gg + 6 + 4 * f))), tau = cp * float(__ldg(gg + 7 + 4 * f));
-            gb = fmaxf(gb, fmaxf(sJ * fmaxf(nr, ns), sJ * (1.0f + 2.0f * tau)));
           }
         }
         R = r == -1100 ? 0 : r;
-        E = gb > 0.f ? tc::exp_of(gb) + 2 : 0;  // 2^2 margin for the float rounding of the bound
+        float ymax = 0.f;
+        if (live) {
+          const float grr = d2ff(__ldg(gg + 1), 0).h, grs = d2ff(__ldg(gg + 2), 0).h, gss = d2ff(__ldg(gg + 3), 0).h;
+          const float cp = float((N + 1) * (N + 2)) * 0.5f;
+          for (int kc = 0; kc < KCH; ++kc) {
+            const int c0 = kc * kKC + 8 * q;
+            if (c0 < ap.VK) {
+              double v[8];
+              load8(ap.C1 + row * 2 * Np, live, c0, 2 * Np, v);
+#pragma unroll
+              for (int t = 0; t < 4; ++t) {
+                const float ur = d2ff(v[2 * t], R).h, us = d2ff(v[2 * t + 1], R).h;
+                ymax = fmaxf(ymax, fmaxf(fabsf(grr * ur + grs * us), fabsf(grs * ur + gss * us)));
+              }
+            } else {
+              const int i0 = (c0 - ap.VK) >> 2;
+#pragma unroll
+              for (int t = 0; t < 2; ++t) {
+                const int i = i0 + t;
+                if (i < NFN) {
+                  const int f = i / Nfp, j = i - f * Nfp;
+                  const int code = codes[f];
+                  const double2 own = __ldg(ap.FN + row * NFN + i);
+                  const float um = d2ff(own.x, R).h, dnm = d2ff(own.y, R).h;
+                  float jm = 0.f, av = 0.f;
+                  if (code >= 0) {
+                    const double2 oth = __ldg(ap.FN + (boff + (code >> 2)) * NFN + (code & 3) * Nfp + (Nfp - 1 - j));
+                    jm = d2ff(oth.x, R).h - um;
+                    av = 0.5f * (dnm - d2ff(oth.y, R).h);
+                  } else if (code == -2) {
+                    jm = -2.f * um;
+                    av = dnm;
+                  }
+                  const double* gf = gg + 4 + 4 * f;
+                  const float nr = d2ff(__ldg(gf), 0).h, ns = d2ff(__ldg(gf + 1), 0).h, sJ = d2ff(__ldg(gf + 2), 0).h;
+                  const float tau = cp * d2ff(__ldg(gf + 3), 0).h;
+                  const float hs = 0.5f * sJ * jm;
+                  ymax = fmaxf(ymax, fmaxf(fmaxf(fabsf(nr * hs), fabsf(ns * hs)), fabsf(sJ * (av + tau * jm))));
+                }
+              }
+            }
+          }
+        }
+        asm volatile("bar.sync 1, %0;\n" ::"r"(kSlicers) : "memory");  // pmax free (previous tile read it)
+        reinterpret_cast<float*>(pmax)[q * kT + e] = ymax;
+        asm volatile("bar.sync 1, %0;\n" ::"r"(kSlicers) : "memory");
+        const float* pf = reinterpret_cast<const float*>(pmax);
+        const float mx = fmaxf(fmaxf(pf[e], pf[kT + e]), fmaxf(pf[2 * kT + e], pf[3 * kT + e]));
+        E = mx > 0.f ? tc::exp_of(mx * 1.0001f) : 0;  // |Y| 2^-R < 2^E
       } else {
         int em = -1100;
         if (live) {
