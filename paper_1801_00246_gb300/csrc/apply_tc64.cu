@@ -20,13 +20,13 @@
 //    the previous chunk's products run; operator blocks (48 rows x 32 columns,
 //    8 slices) arrive by bulk copy.
 //  * the gradient product C1 = [Dr; Ds] u (rows interleaved, so one thread
-//    holds ur and us of a node; the rows of M follow for Helmholtz) writes C1,
-//    M u, every element's face data (u, n.grad u at its face nodes) and
-//    exponent bounds per row;
-//  * the output product Au = OB Y (+ lambda J M u) forms each data chunk of Y
-//    while slicing it: the metric terms wr, ws, and the jumps, averages and
-//    penalty of Eq. PenaltyParameter against the neighbours' face data, in
-//    float-float on the FP32 pipe (Y never reaches memory).
+//    holds ur and us of a node) with an epilogue that forms the volume columns
+//    of Y (wr, ws), the Helmholtz columns and every element's face data
+//    (u, n.grad u at its face nodes) in float-float on the FP32 pipe;
+//  * tc64_face_fill: the face columns of Y (jumps and averages against the
+//    neighbour's face data, penalty of Eq. PenaltyParameter), float-float,
+//    one thread per face-node entry;
+//  * the output product Au = OB Y, a plain tc64_gemm launch.
 // Accuracy: relative error near 2^-44 of |A||u| (the slicing's), as the mma.sync path.
 #include <cmath>
 #include <cstring>
@@ -172,43 +172,20 @@ __device__ __forceinline__ ff horner8(const uint32_t (&acc)[kSl][4], int c) {
   return ff_renorm(h, l);
 }
 
-// |x| 2^{56 - E} (x = h + l, a float-float pair with |x| < 2^E) as a 56-bit
-// integer, and the sign of x
-__device__ __forceinline__ uint64_t fixed56_ff(ff x, int E, uint32_t& sgn) {
-  const uint32_t uh = __float_as_uint(x.h), ul = __float_as_uint(x.l);
-  const int eh = int((uh >> 23) & 0xffu), el = int((ul >> 23) & 0xffu);
-  if (eh == 0) {  // h zero (or below the normal range): the value is negligible
-    sgn = 0;
-    return 0ull;
-  }
-  sgn = uh >> 31;
-  auto part = [E](uint32_t u, int eb) -> long long {  // |part| 2^{56 - E}
-    const long long m = (long long)((u & 0x7fffffu) | 0x800000u);
-    const int sh = eb - 150 + 56 - E;
-    if (sh >= 0) return sh < 40 ? (m << sh) : 0ll;
-    return sh > -40 ? (m >> (-sh)) : 0ll;
-  };
-  long long I = part(uh, eh);
-  if (el != 0) {
-    const long long L = part(ul, el);
-    I += ((uh ^ ul) >> 31) ? -L : L;
-  }
-  return I > 0 ? (uint64_t)I : 0ull;
-}
-
-// Arguments of the apply's two products.
-struct ApplyArgs {
+// Arguments of the gradient product's epilogue (MODE 1): the rows of A are
+// [Dr; Ds] interleaved (column 2n = ur at node n, 2n + 1 = us), and instead of
+// C1 the epilogue writes the volume columns of Y (wr, ws), the Helmholtz
+// columns lambda J u, and every element's face data FN = (u, n.grad u) at its
+// face nodes (outward normal of the element itself).
+struct GradOut {
   int N;
   int64_t K;
-  const double* gx;        // derived geometry, 16 FP64 words per element
-  const int32_t* conn;     // face connectivity
-  double* C1;              // [rows][2 Np]: (ur, us) per node, interleaved
-  double* Mu;              // [rows][Np]: M u (Helmholtz), or null
-  double2* FN;             // [rows][3 (N+1)]: (u, n.grad u) at the face nodes
-  int* exc;                // [rows]: exponent bound of the row's C1 values
-  int* exfn;               // [rows]: exponent bound of the row's face data
+  const double* gx;  // derived geometry, 16 words per element
+  double* Y;
+  int ldy, helm;
   double lambda;
-  int VK;                  // columns of the volume part of Y (2 Np rounded up to 32)
+  double2* FN;  // [rows][3 (N+1)]
+  int* exy;     // [rows]: largest exponent of the row's Y values (for the output product)
 };
 
 // out[r][c] = sum_k A[c][k] X[r][k] for r < rows, c < M, k < Kd (A sliced in
@@ -216,34 +193,24 @@ struct ApplyArgs {
 //
 // Warp-specialised pipeline over a stream of data chunks (tile, output pass
 // nc, column chunk kc), chunk g using shared-memory buffer g & 1:
-//  * warps 0-15 (four threads per row of the 128-row tile) fix each row's
+//  * warps 0-15 (four threads per row of the 128-row tile) find each row's
 //    scale exponent, slice chunk g into buffer g & 1 once the products of
 //    chunk g - 2 have released it (mbarrier `empty`), signal `full`, and after
 //    a pass's last chunk wait for its accumulators (`acc_full`), drain them
-//    and release them (`acc_empty`);
+//    (Horner's rule, epilogue) and release them (`acc_empty`);
 //  * warp 16 loads operator block g by bulk copy, waits for `full`, issues the
 //    36 slice products per 16 columns from one lane and commits to `empty`
 //    (and to `acc_full` after a pass's last chunk); before a pass's first
 //    chunk it waits until the previous pass has been drained.
 // No CTA-wide barrier in the steady state; every wait is bounded in time.
-//
-// MODE 0: X is a plain FP64 matrix (rows of length Kd, stride ldx); out FP64.
-// MODE 1 (the apply's gradient product): X = u, A = [Dr; Ds] with rows
-//   interleaved (column 2n = ur at node n, 2n + 1 = us) and, for Helmholtz,
-//   the rows of M after them; the epilogue writes C1, M u, the face data and
-//   the rows' exponent bounds instead of `out`.
-// MODE 2 (the apply's output product): the data row is Y = [wr_n, ws_n per
-//   node | per face-node entry 1/2 nr sJ [u], 1/2 ns sJ [u],
-//   -sJ ({n.grad u} + tau [u]), 0], formed while slicing, in float-float on the
-//   FP32 pipe, from C1, the face data of the element and its neighbours and the
-//   geometry (Y never reaches memory); the epilogue adds lambda J M u.
 constexpr int kSlicers = 512;  // threads of warps 0-15
 template <int MODE>
 __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int M, int Kd, int NCH, int KCH,
                                                               const double* __restrict__ X, int64_t ldx, int vec2,
+                                                              const int* __restrict__ ex_given,
                                                               const uint8_t* __restrict__ Bops,
                                                               const int* __restrict__ ea, double* __restrict__ out,
-                                                              int64_t ldo, ApplyArgs ap) {
+                                                              int64_t ldo, GradOut go) {
   extern __shared__ __align__(1024) uint8_t sm[];
   uint8_t* sA = sm;                        // [2][8 slices][128 rows][32] canonical
   uint8_t* sB = sm + 2 * kABytes;          // [2][8 slices][48 rows][32] canonical
@@ -322,9 +289,8 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
     const int q = warp >> 2;
     const uint32_t lanebase = uint32_t((warp & 3) * 32) << 16;
     uint32_t g = 0, pass = 0;
-    const int N = ap.N, Np = (N + 1) * (N + 2) / 2, Nfp = N + 1, NFN = 3 * Nfp;
-    auto load8 = [&](const double* xr, bool live, int k0, int kd, double (&v)[8]) {
-      if (live && vec2 && k0 + 8 <= kd) {
+    auto load8 = [&](const double* xr, bool live, int k0, double (&v)[8]) {
+      if (live && vec2 && k0 + 8 <= Kd) {
         const double2* p2 = reinterpret_cast<const double2*>(xr + k0);
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
@@ -334,101 +300,27 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
         }
       } else {
 #pragma unroll
-        for (int t = 0; t < 8; ++t) v[t] = (live && k0 + t < kd) ? __ldg(xr + k0 + t) : 0.0;
-      }
-    };
-    auto store_slices = [&](const uint64_t (&I)[8], const uint32_t (&sg)[8], uint32_t b) {
-      uint8_t* dst = sA + b * kABytes + (e >> 3) * 512 + q * 128 + (e & 7) * 16;
-#pragma unroll
-      for (int j = 0; j < kSl; ++j) {
-        uint4 w;
-        w.x = slice_bits(I[0], j, sg[0]) | (slice_bits(I[1], j, sg[1]) << 16);
-        w.y = slice_bits(I[2], j, sg[2]) | (slice_bits(I[3], j, sg[3]) << 16);
-        w.z = slice_bits(I[4], j, sg[4]) | (slice_bits(I[5], j, sg[5]) << 16);
-        w.w = slice_bits(I[6], j, sg[6]) | (slice_bits(I[7], j, sg[7]) << 16);
-        *reinterpret_cast<uint4*>(dst + j * kASlice) = w;
+        for (int t = 0; t < 8; ++t) v[t] = (live && k0 + t < Kd) ? __ldg(xr + k0 + t) : 0.0;
       }
     };
     for (int64_t tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
       const int64_t row = tile * kT + e;
       const bool live = row < rows;
-      const int64_t el = MODE == 0 ? 0 : (live ? row : 0) % ap.K;
-      const int64_t boff = (live ? row : 0) - el;
       const double* xr = X + (live ? row : 0) * ldx;
-      const double* gg = MODE == 0 ? nullptr : ap.gx + 16 * el;
-      // ---- the row's scale exponent E (|data| < 2^E) and, MODE 2, the input reference R
-      int E = 0, R = 0;
-      int codes[3] = {-1, -1, -1};
-      if (MODE == 2) {
-        // inputs scaled by 2^-R, R bounding C1 and the face data of the element and
-        // its neighbours (so scaled values stay in the FP32 range); E from the row's
-        // largest |Y| (relative to 2^R), found by a float pre-pass over this thread's
-        // columns (float estimates within 2^-20 of Y: a margin factor covers them)
-        int r = live ? max(__ldg(ap.exc + row), __ldg(ap.exfn + row)) : -1100;
-        if (live) {
-#pragma unroll
-          for (int f = 0; f < 3; ++f) {
-            codes[f] = __ldg(ap.conn + 3 * el + f);
-            if (codes[f] >= 0) r = max(r, __ldg(ap.exfn + boff + (codes[f] >> 2)));
-          }
-        }
-        R = r == -1100 ? 0 : r;
-        float ymax = 0.f;
-        if (live) {
-          const float grr = d2ff(__ldg(gg + 1), 0).h, grs = d2ff(__ldg(gg + 2), 0).h, gss = d2ff(__ldg(gg + 3), 0).h;
-          const float cp = float((N + 1) * (N + 2)) * 0.5f;
-          for (int kc = 0; kc < KCH; ++kc) {
-            const int c0 = kc * kKC + 8 * q;
-            if (c0 < ap.VK) {
-              double v[8];
-              load8(ap.C1 + row * 2 * Np, live, c0, 2 * Np, v);
-#pragma unroll
-              for (int t = 0; t < 4; ++t) {
-                const float ur = d2ff(v[2 * t], R).h, us = d2ff(v[2 * t + 1], R).h;
-                ymax = fmaxf(ymax, fmaxf(fabsf(grr * ur + grs * us), fabsf(grs * ur + gss * us)));
-              }
-            } else {
-              const int i0 = (c0 - ap.VK) >> 2;
-#pragma unroll
-              for (int t = 0; t < 2; ++t) {
-                const int i = i0 + t;
-                if (i < NFN) {
-                  const int f = i / Nfp, j = i - f * Nfp;
-                  const int code = codes[f];
-                  const double2 own = __ldg(ap.FN + row * NFN + i);
-                  const float um = d2ff(own.x, R).h, dnm = d2ff(own.y, R).h;
-                  float jm = 0.f, av = 0.f;
-                  if (code >= 0) {
-                    const double2 oth = __ldg(ap.FN + (boff + (code >> 2)) * NFN + (code & 3) * Nfp + (Nfp - 1 - j));
-                    jm = d2ff(oth.x, R).h - um;
-                    av = 0.5f * (dnm - d2ff(oth.y, R).h);
-                  } else if (code == -2) {
-                    jm = -2.f * um;
-                    av = dnm;
-                  }
-                  const double* gf = gg + 4 + 4 * f;
-                  const float nr = d2ff(__ldg(gf), 0).h, ns = d2ff(__ldg(gf + 1), 0).h, sJ = d2ff(__ldg(gf + 2), 0).h;
-                  const float tau = cp * d2ff(__ldg(gf + 3), 0).h;
-                  const float hs = 0.5f * sJ * jm;
-                  ymax = fmaxf(ymax, fmaxf(fmaxf(fabsf(nr * hs), fabsf(ns * hs)), fabsf(sJ * (av + tau * jm))));
-                }
-              }
-            }
-          }
-        }
-        asm volatile("bar.sync 1, %0;\n" ::"r"(kSlicers) : "memory");  // pmax free (previous tile read it)
-        reinterpret_cast<float*>(pmax)[q * kT + e] = ymax;
-        asm volatile("bar.sync 1, %0;\n" ::"r"(kSlicers) : "memory");
-        const float* pf = reinterpret_cast<const float*>(pmax);
-        const float mx = fmaxf(fmaxf(pf[e], pf[kT + e]), fmaxf(pf[2 * kT + e], pf[3 * kT + e]));
-        E = mx > 0.f ? tc::exp_of(mx * 1.0001f) : 0;  // |Y| 2^-R < 2^E
+      // scale exponent of the row: a bound |X[row][k]| < 2^E, given by the producer
+      // of X or found here
+      int E;
+      double vn[8];  // the next chunk's values (loaded one chunk ahead)
+      if (ex_given) {
+        E = live ? __ldg(ex_given + row) : 0;
+        if (E == -1100) E = 0;
       } else {
         int em = -1100;
         if (live) {
           double v[2][8];
           for (int kc = 0; kc < KCH; kc += 2) {
-            load8(xr, live, kc * kKC + 8 * q, Kd, v[0]);
-            load8(xr, live && kc + 1 < KCH, (kc + 1) * kKC + 8 * q, Kd, v[1]);
+            load8(xr, live, kc * kKC + 8 * q, v[0]);
+            load8(xr, live && kc + 1 < KCH, (kc + 1) * kKC + 8 * q, v[1]);
 #pragma unroll
             for (int t = 0; t < 8; ++t) em = max(em, max(exp_bound64(v[0][t]), exp_bound64(v[1][t])));
           }
@@ -439,80 +331,45 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
         E = max(max(pmax[e], pmax[kT + e]), max(pmax[2 * kT + e], pmax[3 * kT + e]));
         if (E == -1100) E = 0;
       }
-      ff gmx[3];  // MODE 2: Grr, Grs, Gss as float-float
-      if (MODE == 2) {
+      load8(xr, live, 8 * q, vn);
+      int ymax = -1100;  // MODE 1: largest exponent of the Y columns this thread writes
+      float gh[6];  // MODE 1: Grr, Grs, Gss as float-float
+      if (MODE == 1) {
+        const int64_t el = (live ? row : 0) % go.K;
+        const double* gg = go.gx + 16 * el;
 #pragma unroll
-        for (int t = 0; t < 3; ++t) gmx[t] = live ? d2ff(__ldg(gg + 1 + t), 0) : ff{0.f, 0.f};
+        for (int t = 0; t < 3; ++t) {
+          const ff gf = d2ff(__ldg(gg + 1 + t), 0);
+          gh[2 * t] = gf.h;
+          gh[2 * t + 1] = gf.l;
+        }
       }
-      double vn[8];  // MODE 0/1: the next chunk's values, loaded one chunk ahead
-      if (MODE != 2) load8(xr, live, 8 * q, Kd, vn);
-      int mexc = -1100, mexf = -1100;  // MODE 1: exponent bounds of the C1 values and face data written
       for (int nc = 0; nc < NCH; ++nc, ++pass) {
         for (int kc = 0; kc < KCH; ++kc, ++g) {
           const uint32_t b = g & 1u;
+          double v[8];
+#pragma unroll
+          for (int t = 0; t < 8; ++t) v[t] = vn[t];
+          {  // request the next chunk of this row (the next pass starts again at chunk 0)
+            const int kn = kc + 1 < KCH ? kc + 1 : 0;
+            if (kc + 1 < KCH || nc + 1 < NCH) load8(xr, live, kn * kKC + 8 * q, vn);
+          }
           uint64_t I[8];
           uint32_t sg[8];
-          const int c0 = kc * kKC + 8 * q;  // this thread's 8 data columns
-          if (MODE != 2) {
-            double v[8];
 #pragma unroll
-            for (int t = 0; t < 8; ++t) v[t] = vn[t];
-            {  // request the next chunk of this row (the next pass starts again at chunk 0)
-              const int kn = kc + 1 < KCH ? kc + 1 : 0;
-              if (kc + 1 < KCH || nc + 1 < NCH) load8(xr, live, kn * kKC + 8 * q, Kd, vn);
-            }
-#pragma unroll
-            for (int t = 0; t < 8; ++t) I[t] = fixed56(v[t], E, sg[t]);
-          } else {
-            ff y[8];
-#pragma unroll
-            for (int t = 0; t < 8; ++t) y[t] = ff{0.f, 0.f};
-            if (live && c0 < ap.VK) {
-              // volume: nodes c0/2 .. c0/2 + 3, (wr, ws) each
-              double v[8];
-              load8(ap.C1 + row * 2 * Np, live, c0, 2 * Np, v);
-#pragma unroll
-              for (int t = 0; t < 4; ++t) {
-                const ff ur = d2ff(v[2 * t], R), us = d2ff(v[2 * t + 1], R);
-                y[2 * t] = ff_add(ff_mul(gmx[0], ur), ff_mul(gmx[1], us));
-                y[2 * t + 1] = ff_add(ff_mul(gmx[1], ur), ff_mul(gmx[2], us));
-              }
-            } else if (live) {
-              // faces: entries i0, i0 + 1 (four columns each: a, b, c, 0)
-              const int i0 = (c0 - ap.VK) >> 2;
-#pragma unroll
-              for (int t = 0; t < 2; ++t) {
-                const int i = i0 + t;
-                if (i < NFN) {
-                  const int f = i / Nfp, j = i - f * Nfp;
-                  const int code = codes[f];
-                  const double2 own = __ldg(ap.FN + row * NFN + i);
-                  const ff um = d2ff(own.x, R), dnm = d2ff(own.y, R);
-                  ff jm{0.f, 0.f}, av{0.f, 0.f};
-                  if (code >= 0) {
-                    const double2 oth = __ldg(ap.FN + (boff + (code >> 2)) * NFN + (code & 3) * Nfp + (Nfp - 1 - j));
-                    jm = ff_sub(d2ff(oth.x, R), um);
-                    av = ff_pow2(ff_sub(dnm, d2ff(oth.y, R)), 0.5f);
-                  } else if (code == -2) {  // Dirichlet
-                    jm = ff_pow2(um, -2.0f);
-                    av = dnm;
-                  }
-                  const double* gf = gg + 4 + 4 * f;
-                  const ff nr = d2ff(__ldg(gf), 0), ns = d2ff(__ldg(gf + 1), 0), sJ = d2ff(__ldg(gf + 2), 0);
-                  const ff tau = ff_mul(ff{float((N + 1) * (N + 2)) * 0.5f, 0.f}, d2ff(__ldg(gf + 3), 0));
-                  const ff hs = ff_pow2(ff_mul(sJ, jm), 0.5f);
-                  y[4 * t] = ff_mul(nr, hs);
-                  y[4 * t + 1] = ff_mul(ns, hs);
-                  y[4 * t + 2] = ff_neg(ff_mul(sJ, ff_add(av, ff_mul(tau, jm))));
-                }
-              }
-            }
-#pragma unroll
-            for (int t = 0; t < 8; ++t) I[t] = fixed56_ff(y[t], E, sg[t]);
-          }
+          for (int t = 0; t < 8; ++t) I[t] = fixed56(v[t], E, sg[t]);
           // buffer b is free once chunk g - 2's products completed
           if (g >= 2 && !tc::mbar_wait(empty + b, ((g - 2) >> 1) & 1u)) *abort_flag = 1;
-          store_slices(I, sg, b);
+          uint8_t* dst = sA + b * kABytes + (e >> 3) * 512 + q * 128 + (e & 7) * 16;
+#pragma unroll
+          for (int j = 0; j < kSl; ++j) {
+            uint4 w;
+            w.x = slice_bits(I[0], j, sg[0]) | (slice_bits(I[1], j, sg[1]) << 16);
+            w.y = slice_bits(I[2], j, sg[2]) | (slice_bits(I[3], j, sg[3]) << 16);
+            w.z = slice_bits(I[4], j, sg[4]) | (slice_bits(I[5], j, sg[5]) << 16);
+            w.w = slice_bits(I[6], j, sg[6]) | (slice_bits(I[7], j, sg[7]) << 16);
+            *reinterpret_cast<uint4*>(dst + j * kASlice) = w;
+          }
           tc::fence_async_smem();
           __syncwarp();
           if (lane == 0) asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(
@@ -524,12 +381,12 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
         tc::fence_after();
 #pragma unroll 1
         for (int p = 0; p < 3; ++p) {
-          const int cl = 12 * q + 4 * p;
+          const int c0 = 12 * q + 4 * p;
           uint32_t acc[kSl][4];
 #pragma unroll
           for (int s = 0; s < kSl; ++s) {
             uint32_t vv[4];
-            tc::tmem_ld4(tb + lanebase + s * kNC + cl, vv);
+            tc::tmem_ld4(tb + lanebase + s * kNC + c0, vv);
 #pragma unroll
             for (int c = 0; c < 4; ++c) acc[s][c] = vv[c];
           }
@@ -541,86 +398,69 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
                                             tc::smem_addr(acc_empty))
                                         : "memory");
           }
-          if (MODE == 0 || MODE == 2) {
-            const int Eo = MODE == 2 ? E + R : E;  // the data row's scale
-            float lj_h = 0.f, lj_l = 0.f;
-            if (MODE == 2 && ap.Mu && live) {
-              const ff lj = ff_mul(d2ff(ap.lambda, 0), d2ff(__ldg(gg), 0));
-              lj_h = lj.h;
-              lj_l = lj.l;
-            }
+          if (MODE == 0) {
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-              const int col = nc * kNC + cl + c;
+              const int col = nc * kNC + c0 + c;
               if (live && col < M) {
                 // value = 2^{ea + E - 14} sum_s acc_s 2^{-7 s}
                 const ff hl = horner8(acc, c);
-                const int sc = __ldg(ea + col) + Eo - 14;
-                double o;
-                if (MODE == 2 && ap.Mu) {  // + lambda J (M u) in float-float at the product's scale
-                  const double mu = __ldg(ap.Mu + row * Np + col);
-                  const ff t = ff_mul(ff{lj_h, lj_l}, d2ff(mu, sc));
-                  const ff sum = ff_add(hl, t);
-                  o = ff_to_double(sum.h, sum.l, sc);
-                } else {
-                  o = ff_to_double(hl.h, hl.l, sc);
-                }
-                out[row * ldo + col] = o;
+                out[row * ldo + col] = ff_to_double(hl.h, hl.l, __ldg(ea + col) + E - 14);
               }
             }
           } else {
-            // MODE 1: columns (2n, 2n + 1) = (ur, us) of node n; columns from 2 Np: M u
+            // nodes n = col / 2: (ur, us) in columns (2n, 2n + 1)
+            const int N = go.N, Np = (N + 1) * (N + 2) / 2, Nfp = N + 1, NFN = 3 * Nfp;
 #pragma unroll
             for (int c = 0; c < 4; c += 2) {
-              const int col = nc * kNC + cl + c;
-              if (!live || col >= M) continue;
-              if (col >= 2 * Np) {  // Helmholtz rows: M u
-#pragma unroll
-                for (int t = 0; t < 2; ++t) {
-                  if (col + t < M) {
-                    const ff hl = horner8(acc, c + t);
-                    ap.Mu[row * Np + col + t - 2 * Np] = ff_to_double(hl.h, hl.l, __ldg(ea + col + t) + E - 14);
-                  }
-                }
-                continue;
-              }
-              const int n = col >> 1;
-              const int er = __ldg(ea + col), es = __ldg(ea + col + 1);
-              const int ec = max(er, es);
-              ff ur = horner8(acc, c), us = horner8(acc, c + 1);
-              const double dur = ff_to_double(ur.h, ur.l, er + E - 14), dus = ff_to_double(us.h, us.l, es + E - 14);
-              ap.C1[row * 2 * Np + col] = dur;
-              ap.C1[row * 2 * Np + col + 1] = dus;
-              mexc = max(mexc, max(exp_bound64(dur), exp_bound64(dus)));
-              // face data at the face nodes this node is (a corner belongs to two faces)
-              int rrow = 0;
-              while (n >= (rrow + 1) * (N + 1) - (rrow + 1) * rrow / 2) ++rrow;  // n's row of constant s
-              const int rs0 = rrow * (N + 1) - rrow * (rrow - 1) / 2, len = N + 1 - rrow;
-              int fa = -1, ja = 0, fb = -1, jb = 0;
-              if (rrow == 0) fa = 0, ja = n;                  // face 0, j = n
-              if (n == rs0 + len - 1) {                       // face 1, j = row
-                if (fa < 0) fa = 1, ja = rrow;
-                else fb = 1, jb = rrow;
-              }
-              if (n == rs0 && fb < 0) {                       // face 2, j = N - row
-                if (fa < 0) fa = 2, ja = N - rrow;
-                else fb = 2, jb = N - rrow;
-              }
-              if (fa >= 0) {
+              const int n = (nc * kNC + c0 + c) >> 1;
+              if (live && n < Np) {
+                const int er = __ldg(ea + 2 * n), es = __ldg(ea + 2 * n + 1);
+                const int ec = max(er, es);
+                ff ur = horner8(acc, c), us = horner8(acc, c + 1);
                 ur = ff_pow2(ur, __uint_as_float(uint32_t(127 + er - ec) << 23));
                 us = ff_pow2(us, __uint_as_float(uint32_t(127 + es - ec) << 23));
-                const int S = ec + E - 14;
+                const int S = ec + E - 14;  // ur, us, wr, ws, n.grad u all carry 2^S
+                const ff grr{gh[0], gh[1]}, grs{gh[2], gh[3]}, gss{gh[4], gh[5]};
+                const ff wr = ff_add(ff_mul(grr, ur), ff_mul(grs, us));
+                const ff ws = ff_add(ff_mul(grs, ur), ff_mul(gss, us));
+                double* yr = go.Y + row * go.ldy;
+                const double dwr = ff_to_double(wr.h, wr.l, S), dws = ff_to_double(ws.h, ws.l, S);
+                yr[n] = dwr;
+                yr[Np + n] = dws;
+                ymax = max(ymax, max(exp_bound64(dwr), exp_bound64(dws)));
                 const double un = __ldg(X + row * ldx + n);
-                const double* g2 = ap.gx + 16 * (row % ap.K);
+                const int64_t el = row % go.K;
+                const double* gg = go.gx + 16 * el;
+                if (go.helm) {
+                  const int eu = exp_bound64(un);
+                  const ff lj = ff_mul(d2ff(go.lambda, 0), d2ff(__ldg(gg), 0));
+                  const ff vv = ff_mul(lj, d2ff(un, eu));
+                  const double dv = ff_to_double(vv.h, vv.l, eu);
+                  yr[2 * Np + 3 * NFN + n] = dv;
+                  ymax = max(ymax, exp_bound64(dv));
+                }
+                // face data at the face nodes this node is (a corner belongs to two faces)
+                int rrow = 0;
+                while (n >= (rrow + 1) * (N + 1) - (rrow + 1) * rrow / 2) ++rrow;  // n's row of constant s
+                const int rs0 = rrow * (N + 1) - rrow * (rrow - 1) / 2, len = N + 1 - rrow;
+                int fa = -1, ja = 0, fb = -1, jb = 0;
+                if (rrow == 0) fa = 0, ja = n;                         // face 0, j = n
+                if (n == rs0 + len - 1) {                              // face 1, j = row
+                  if (fa < 0) fa = 1, ja = rrow;
+                  else fb = 1, jb = rrow;
+                }
+                if (n == rs0 && fb < 0) {                              // face 2, j = N - row
+                  if (fa < 0) fa = 2, ja = N - rrow;
+                  else fb = 2, jb = N - rrow;
+                }
 #pragma unroll
                 for (int t = 0; t < 2; ++t) {
                   const int f = t == 0 ? fa : fb, j = t == 0 ? ja : jb;
                   if (f >= 0) {
-                    const ff nr = d2ff(__ldg(g2 + 4 + 4 * f), 0), ns = d2ff(__ldg(g2 + 5 + 4 * f), 0);
+                    const ff nr = d2ff(__ldg(gg + 4 + 4 * f), 0), ns = d2ff(__ldg(gg + 5 + 4 * f), 0);
                     const ff dn = ff_add(ff_mul(nr, ur), ff_mul(ns, us));
-                    const double ddn = ff_to_double(dn.h, dn.l, S);
-                    ap.FN[row * NFN + f * Nfp + j] = make_double2(un, ddn);
-                    mexf = max(mexf, max(exp_bound64(un), exp_bound64(ddn)));
+                    go.FN[row * NFN + f * Nfp + j] = make_double2(un, ff_to_double(dn.h, dn.l, S));
                   }
                 }
               }
@@ -628,19 +468,12 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
           }
         }
       }
-      if (MODE == 1) {  // the rows' exponent bounds of C1 and of the face data
+      if (MODE == 1) {  // the row's largest Y exponent so far (the face columns add theirs)
         asm volatile("bar.sync 1, %0;\n" ::"r"(kSlicers) : "memory");
-        pmax[q * kT + e] = mexc;
+        pmax[q * kT + e] = ymax;
         asm volatile("bar.sync 1, %0;\n" ::"r"(kSlicers) : "memory");
-        const int xc = max(max(pmax[e], pmax[kT + e]), max(pmax[2 * kT + e], pmax[3 * kT + e]));
-        asm volatile("bar.sync 1, %0;\n" ::"r"(kSlicers) : "memory");
-        pmax[q * kT + e] = mexf;
-        asm volatile("bar.sync 1, %0;\n" ::"r"(kSlicers) : "memory");
-        const int xf = max(max(pmax[e], pmax[kT + e]), max(pmax[2 * kT + e], pmax[3 * kT + e]));
-        if (q == 0 && live) {
-          ap.exc[row] = xc;
-          ap.exfn[row] = xf;
-        }
+        if (q == 0 && live)
+          go.exy[row] = max(max(pmax[e], pmax[kT + e]), max(pmax[2 * kT + e], pmax[3 * kT + e]));
       }
     }
   }
@@ -649,6 +482,56 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
   __syncthreads();
   tc::fence_after();
   if (warp == 0) tc::tmem_dealloc(tb, 512);
+}
+
+// ------------------------------------------------------------------ face columns of Y
+// One thread per (element, face-node entry i = f (N+1) + j): from the element's
+// face data and its neighbour's across face f (FN, written by the gradient
+// product), Y[2Np + i] = 1/2 nr sJ [u], Y[2Np + NFN + i] = 1/2 ns sJ [u],
+// Y[2Np + 2 NFN + i] = -sJ ({n.grad u} + tau [u]), in float-float scaled by
+// the entry's largest input; the row's largest exponent per element
+// (exy, raised atomically) for the output product's slicing.
+__global__ void __launch_bounds__(256) tc64_face_fill(int N, int64_t K, int64_t nE, const double* __restrict__ gx,
+                                                      const int32_t* __restrict__ conn,
+                                                      const double2* __restrict__ FN, double* __restrict__ Y,
+                                                      int ldy, int* __restrict__ exy) {
+  const int Np = (N + 1) * (N + 2) / 2, Nfp = N + 1, NFN = 3 * Nfp;
+  const int64_t total = nE * NFN;
+  const ff cpen{float((N + 1) * (N + 2)) * 0.5f, 0.f};
+  for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t be = t / NFN;
+    const int i = int(t - be * NFN);
+    const int f = i / Nfp, j = i - f * Nfp;
+    const int64_t el = be % K, boff = be - el;
+    const double* g = gx + 16 * el + 4 + 4 * f;
+    const double2 own = __ldg(FN + t);
+    const int code = __ldg(conn + 3 * el + f);
+    double2 oth = make_double2(0.0, 0.0);
+    if (code >= 0) oth = __ldg(FN + (boff + (code >> 2)) * NFN + (code & 3) * Nfp + (Nfp - 1 - j));
+    const int R = max(max(exp_bound64(own.x), exp_bound64(own.y)), max(exp_bound64(oth.x), exp_bound64(oth.y)));
+    const int Rs = R == -1100 ? 0 : R;
+    const ff um = d2ff(own.x, Rs), dnm = d2ff(own.y, Rs);
+    ff jm{0.f, 0.f}, av{0.f, 0.f};
+    if (code >= 0) {
+      jm = ff_sub(d2ff(oth.x, Rs), um);
+      av = ff_pow2(ff_sub(dnm, d2ff(oth.y, Rs)), 0.5f);
+    } else if (code == -2) {  // Dirichlet
+      jm = ff_pow2(um, -2.0f);
+      av = dnm;
+    }
+    const ff nr = d2ff(__ldg(g), 0), ns = d2ff(__ldg(g + 1), 0), sJ = d2ff(__ldg(g + 2), 0);
+    const ff tau = ff_mul(cpen, d2ff(__ldg(g + 3), 0));
+    const ff hs = ff_pow2(ff_mul(sJ, jm), 0.5f);
+    const ff a = ff_mul(nr, hs), b = ff_mul(ns, hs);
+    const ff fl = ff_neg(ff_mul(sJ, ff_add(av, ff_mul(tau, jm))));
+    double* y = Y + be * ldy + 2 * Np + i;
+    const double da = ff_to_double(a.h, a.l, Rs), db = ff_to_double(b.h, b.l, Rs), dc = ff_to_double(fl.h, fl.l, Rs);
+    y[0] = da;
+    y[NFN] = db;
+    y[2 * NFN] = dc;
+    const int ym = max(exp_bound64(da), max(exp_bound64(db), exp_bound64(dc)));
+    if (ym > -1100) atomicMax(exy + be, ym);  // the row's bound: the volume columns' (set before) and these
+  }
 }
 
 // ------------------------------------------------------------------ host side
@@ -718,7 +601,7 @@ void tc64_op_free(Tc64Op* op) {
 namespace {
 template <int MODE>
 cudaError_t gemm_launch(const Tc64Op& op, int64_t rows, const double* X, int64_t ldx, double* out, int64_t ldo,
-                        const ApplyArgs& ap, cudaStream_t st) {
+                        const int* ex_given, const GradOut& go, cudaStream_t st) {
   if (rows <= 0) return cudaSuccess;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -729,20 +612,17 @@ cudaError_t gemm_launch(const Tc64Op& op, int64_t rows, const double* X, int64_t
     if (!grid[dev & 63]) {
       e = cudaFuncSetAttribute(tc64_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
       if (e == cudaSuccess) e = cudaFuncSetAttribute(tc64_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-      if (e == cudaSuccess) e = cudaFuncSetAttribute(tc64_gemm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
       int sms = 0;
       if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       if (e != cudaSuccess) return e;
       grid[dev & 63] = sms;  // one CTA per SM (all of tensor memory, most of shared memory)
     }
   }
-  const double* vx = MODE == 2 ? ap.C1 : X;  // the rows read with paired loads
-  const int64_t vld = MODE == 2 ? 2 * ((ap.N + 1) * (ap.N + 2) / 2) : ldx;
-  const int vec2 = (vld % 2 == 0 && (reinterpret_cast<uintptr_t>(vx) & 15u) == 0) ? 1 : 0;
+  const int vec2 = (ldx % 2 == 0 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0) ? 1 : 0;
   const int64_t tiles = (rows + kT - 1) / kT;
   const unsigned g = unsigned(std::min<int64_t>(tiles, grid[dev & 63]));
-  tc64_gemm<MODE><<<g, kSlicers + 32, kSmem, st>>>(rows, op.M, op.K, op.NCH, op.KCH, X, ldx, vec2, op.blocks, op.ea, out,
-                                                   ldo, ap);
+  tc64_gemm<MODE><<<g, kSlicers + 32, kSmem, st>>>(rows, op.M, op.K, op.NCH, op.KCH, X, ldx, vec2, ex_given,
+                                                   op.blocks, op.ea, out, ldo, go);
   note_launch();
   return cudaGetLastError();
 }
@@ -750,33 +630,30 @@ cudaError_t gemm_launch(const Tc64Op& op, int64_t rows, const double* X, int64_t
 
 cudaError_t tc64_gemm_launch(const Tc64Op& op, int64_t rows, const double* X, int64_t ldx, double* out, int64_t ldo,
                              cudaStream_t st) {
-  return gemm_launch<0>(op, rows, X, ldx, out, ldo, ApplyArgs{}, st);
+  return gemm_launch<0>(op, rows, X, ldx, out, ldo, nullptr, GradOut{}, st);
 }
 
 namespace {
 struct Tc64Apply {
-  Tc64Op grad, gradh;  // [Dr; Ds] with rows interleaved (Dr row n, Ds row n, ...), then M for Helmholtz
-  Tc64Op out;          // OB in the column order of Y: (Br, Bs) per node, then 4 per face-node entry
+  Tc64Op grad;       // [Dr; Ds] with rows interleaved (Dr row n, Ds row n, ...)
+  Tc64Op out, outh;  // OB, [OB | M]
 };
 Tc64Apply g_t64[64][kMaxN + 1];  // [device][degree]
 
-int vol_cols(int Np) { return (2 * Np + 31) / 32 * 32; }
-
 cudaError_t build_t64(const RefElem& R, Tc64Apply& o) {
   const int N = R.N, Np = R.Np, Nfp = R.Nfp, NFN = 3 * Nfp;
-  std::vector<double> A1(size_t(3 * Np) * Np);
+  std::vector<double> A1(size_t(2 * Np) * Np);
   for (int n = 0; n < Np; ++n)
     for (int m = 0; m < Np; ++m) {
       A1[size_t(2 * n) * Np + m] = R.Dr[size_t(n) * Np + m];
       A1[size_t(2 * n + 1) * Np + m] = R.Ds[size_t(n) * Np + m];
-      A1[size_t(2 * Np + n) * Np + m] = R.M[size_t(n) * Np + m];
     }
-  const int VK = vol_cols(Np), KK = VK + 4 * NFN;
-  std::vector<double> B(size_t(Np) * KK, 0.0);
+  const int KY = 2 * Np + 3 * NFN, KH = KY + Np;
+  std::vector<double> B(size_t(Np) * KY, 0.0), BH(size_t(Np) * KH, 0.0);
   for (int i = 0; i < Np; ++i) {
-    for (int n = 0; n < Np; ++n) {
-      B[size_t(i) * KK + 2 * n] = R.Br[size_t(i) * Np + n];
-      B[size_t(i) * KK + 2 * n + 1] = R.Bs[size_t(i) * Np + n];
+    for (int m = 0; m < Np; ++m) {
+      B[size_t(i) * KY + m] = R.Br[size_t(i) * Np + m];
+      B[size_t(i) * KY + Np + m] = R.Bs[size_t(i) * Np + m];
     }
     for (int f = 0; f < 3; ++f)
       for (int l = 0; l < Nfp; ++l) {
@@ -788,23 +665,23 @@ cudaError_t build_t64(const RefElem& R, Tc64Apply& o) {
           ds += R.Ds[size_t(k) * Np + i] * mf;
           if (k == i) ef += mf;
         }
-        const int c = VK + 4 * (f * Nfp + l);
-        B[size_t(i) * KK + c] = dr;
-        B[size_t(i) * KK + c + 1] = ds;
-        B[size_t(i) * KK + c + 2] = ef;
+        B[size_t(i) * KY + 2 * Np + f * Nfp + l] = dr;
+        B[size_t(i) * KY + 2 * Np + NFN + f * Nfp + l] = ds;
+        B[size_t(i) * KY + 2 * Np + 2 * NFN + f * Nfp + l] = ef;
       }
+    for (int k = 0; k < KY; ++k) BH[size_t(i) * KH + k] = B[size_t(i) * KY + k];
+    for (int m = 0; m < Np; ++m) BH[size_t(i) * KH + KY + m] = R.M[size_t(i) * Np + m];
   }
-  cudaError_t e = tc64_op_create(std::vector<double>(A1.begin(), A1.begin() + size_t(2 * Np) * Np), 2 * Np, Np,
-                                 &o.grad);
-  if (e == cudaSuccess) e = tc64_op_create(A1, 3 * Np, Np, &o.gradh);
-  if (e == cudaSuccess) e = tc64_op_create(B, Np, KK, &o.out);
+  cudaError_t e = tc64_op_create(A1, 2 * Np, Np, &o.grad);
+  if (e == cudaSuccess) e = tc64_op_create(B, Np, KY, &o.out);
+  if (e == cudaSuccess) e = tc64_op_create(BH, Np, KH, &o.outh);
   return e;
 }
 }  // namespace
 
 bool tc64_supported(int degree) {
   const int Np = (degree + 1) * (degree + 2) / 2, NFN = 3 * (degree + 1);
-  return vol_cols(Np) + 4 * NFN <= 224;
+  return 2 * Np + 3 * NFN + Np <= 224;
 }
 
 cudaError_t launch_apply_tc64(dg_mesh* m, int degree, int B, double lambda, const double* u, double* Au,
@@ -829,10 +706,12 @@ cudaError_t launch_apply_tc64(dg_mesh* m, int degree, int B, double lambda, cons
   }
   const int N = degree, Np = (N + 1) * (N + 2) / 2, NFN = 3 * (N + 1);
   const bool helm = lambda != 0.0;
+  const int KYH = 2 * Np + 3 * NFN + (helm ? Np : 0);
+  const int ldy = (KYH + 1) & ~1;  // even: 16-byte rows for paired loads
   const int64_t nE = int64_t(B) * m->K;
-  // scratch: C1 [nE][2 Np], M u [nE][Np] (Helmholtz), the face data [nE][NFN] (u, n.grad u),
-  // FP64, and two exponent bounds per row
-  const size_t words = size_t(nE) * (2 * Np + (helm ? Np : 0) + 2 * NFN) + size_t(nE) + 4;
+  // scratch: Y [nE][ldy], the face data FN [nE][NFN] (u, n.grad u), FP64, and the
+  // rows' largest Y exponents
+  const size_t words = size_t(nE) * ldy + size_t(nE) * NFN * 2 + size_t(nE + 1) / 2 + 2;
   if (m->t64_cap < words) {
     cudaFree(m->t64_scratch);
     m->t64_scratch = nullptr;
@@ -843,15 +722,24 @@ cudaError_t launch_apply_tc64(dg_mesh* m, int degree, int B, double lambda, cons
     m->t64_cap = words;
     ++m->scratch_gen;
   }
-  double* C1 = m->t64_scratch;
-  double* Mu = helm ? C1 + size_t(nE) * 2 * Np : nullptr;
-  double2* FN = reinterpret_cast<double2*>(C1 + size_t(nE) * (2 * Np + (helm ? Np : 0)));
-  int* exc = reinterpret_cast<int*>(FN + size_t(nE) * NFN);
-  int* exfn = exc + nE;
-  const ApplyArgs ap{N, m->K, m->geox, m->conn, C1, Mu, FN, exc, exfn, lambda, vol_cols(Np)};
-  e = gemm_launch<1>(helm ? ops->gradh : ops->grad, nE, u, Np, nullptr, 0, ap, st);
+  double* Y = m->t64_scratch;
+  double2* FN = reinterpret_cast<double2*>(Y + size_t(nE) * ldy);
+  int* exy = reinterpret_cast<int*>(FN + size_t(nE) * NFN);
+  GradOut go{N, m->K, m->geox, Y, ldy, helm ? 1 : 0, lambda, FN, exy};
+  e = gemm_launch<1>(ops->grad, nE, u, Np, nullptr, 0, nullptr, go, st);
   if (e != cudaSuccess) return e;
-  return gemm_launch<2>(ops->out, nE, nullptr, 0, Au, Np, ap, st);
+  {
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int64_t total = nE * NFN;
+    const int64_t blocks = std::min<int64_t>((total + 255) / 256, int64_t(sms) * 16);
+    tc64_face_fill<<<unsigned(blocks), 256, 0, st>>>(N, m->K, nE, m->geox, m->conn, FN, Y, ldy, exy);
+    note_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return gemm_launch<0>(helm ? ops->outh : ops->out, nE, Y, ldy, Au, Np, exy, GradOut{}, st);
 }
 
 cudaError_t tc64_error(int* flag) {
