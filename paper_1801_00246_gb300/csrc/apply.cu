@@ -386,7 +386,7 @@ DG_TE_DECL(1) DG_TE_DECL(2) DG_TE_DECL(3) DG_TE_DECL(4) DG_TE_DECL(5) DG_TE_DECL
 // Built-in kernel per degree and precision (the measured winners on the
 // 524,288-triangle workload; dg_autotune replaces them per mesh).
 int default_kernel(int degree, bool f64) {
-  if (f64) return degree >= 3 ? DG_KERNEL_TENSOR : DG_KERNEL_EPT;
+  if (f64) return degree >= 3 ? DG_KERNEL_TC64 : DG_KERNEL_EPT;
   return degree <= 3 ? DG_KERNEL_EPT : DG_KERNEL_TC05;
 }
 
