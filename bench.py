@@ -43,7 +43,9 @@ METRIC = "Poisson Ax GDOF/s & PCG solve ms (N=8, 524k tri), mixed vs FP64, % HBM
 PMG_DEGREES = [8, 4, 2, 1]
 CHEB = 3           # Chebyshev-Jacobi smoothing degree per pre/post smoothing
 COARSE_PASSES = 1  # degree-1 coarse solve: one AMG-preconditioned CG pass (a scaled AMG V-cycle)
-TENSOR_APPLY_TRAFFIC = 1.3250e9  # bytes per FP64 tensor apply from the latest ncu capture of the current kernels
+# DRAM bytes per FP64 apply at N=8 from the latest ncu capture of the current
+# default kernels; None until the kernels that changed have been captured again
+TENSOR_APPLY_TRAFFIC = None
 
 
 # apply kernels by DG_KERNEL_* value
@@ -364,8 +366,10 @@ def run_ours(args, world, rank, local):
     fp64_ms = ax["poisson_f64"]["ms"]
     achieved = K * flops / (fp64_ms * 1e-3) / 1e9
     # BF16 MMA flops the tensor-core FP64 apply issues per launch at N=8 (Poisson):
-    # 36 slice products x 2 flops x padded (rows x depth) of its two products
-    tc_flops = 36 * 2 * (96 * 48 + 48 * 176) * K
+    # 36 slice products x 2 flops x padded (rows x depth) of its two products (the
+    # tcgen05 kernel pads the depth to 32-column chunks, the mma.sync one to 16)
+    k64 = mesh.kernel(N, P.DG_F64, 0)
+    tc_flops = 36 * 2 * ((96 * 64 + 48 * 192) if k64 == P.KERNEL_TC64 else (96 * 48 + 48 * 176)) * K
     algo_gbs = K * bytes64 / (fp64_ms * 1e-3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world, "steps": args.steps,

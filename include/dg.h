@@ -272,16 +272,21 @@ dg_status dg_ins_step(dg_mesh* mesh_u, dg_mesh* mesh_p, dg_ins_state* state, int
  * cannot allocate device memory while they run (a host whose memory pool owns
  * the whole GPU, a time-critical loop that must not pay cudaMalloc's implicit
  * synchronisation, or a simulation that must not fail on an allocation
- * midway). Its workspace, including the gradient rows of the tensor-core
- * apply, is a fixed scratch array of 2^22 doubles (32 MiB) compiled into the
- * library as device memory, which every GPU that loads the library holds
- * until the process exits; the apply's operator tables for the mesh degree
- * are built by dg_mesh_setup. b, x: device FP64 [B][K][Np] as in
- * dg_pcg_solve (x: initial guess in, solution out); the mesh comes from an
- * earlier dg_mesh_setup on the current device. The array holds
- * (6 B + 1) K Np words plus a few per right-hand side (7 B + 1 with
- * lambda != 0): at B = 1 about K*Np <= 599,000 (lambda = 0) or 524,000;
- * larger problems are rejected with DG_ERR_ARG before any device work. The
+ * midway). Its workspace, including the scratch of the tensor-core apply, is
+ * a fixed scratch array of 2^22 doubles (32 MiB) compiled into the library as
+ * device memory, which every GPU that loads the library holds until the
+ * process exits; the apply's operator tables for the mesh degree are built by
+ * dg_mesh_setup. The apply is the kernel dg_pcg_solve would use (the mesh's
+ * FP64 kernel choice), so both give the same iterates. b, x: device FP64
+ * [B][K][Np] as in dg_pcg_solve (x: initial guess in, solution out); the mesh
+ * comes from an earlier dg_mesh_setup on the current device. A call needs
+ * (4 B + 1) K Np words for the CG vectors and the Jacobi inverse, a few per
+ * right-hand side, and the apply's scratch: B K (2 Np + 15 (N + 1)) words
+ * (B K (3 Np + 15 (N + 1)) with lambda != 0) for the tcgen05 FP64 kernel,
+ * the default from degree 3, or 2 B K Np (3 B K Np) for the mma.sync ones.
+ * At B = 1 and N = 8 that is about K <= 9,200 triangles (lambda = 0) or
+ * 8,400; larger problems are rejected with DG_ERR_ARG before any device
+ * work. The
  * first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) and caches it; make that first call before any
  * stream capture. The call calls no cudaMalloc/cudaFree and no allocating

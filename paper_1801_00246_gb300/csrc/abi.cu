@@ -345,6 +345,7 @@ dg_status dg_mesh_setup(int N, int64_t Nv, const double* VX, const double* VY, i
   // an apply at the mesh degree allocates nothing once the mesh exists
   if (ce == cudaSuccess) ce = ensure_tensor_ops(m, N, true);
   if (ce == cudaSuccess) ce = ensure_tensor_ops(m, N, false);
+  if (ce == cudaSuccess) ce = ensure_tc64_ops(m, N);
   if (ce != cudaSuccess) {
     dg_mesh_destroy(m);
     return cuda_fail(ce, "dg_mesh_setup");

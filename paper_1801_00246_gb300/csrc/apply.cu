@@ -419,9 +419,8 @@ cudaError_t launch_apply(const dg_mesh* mc, int degree, dg_prec prec, int B, dou
   if (!kernel_valid(k, degree, f64)) return cudaErrorInvalidValue;
   if (k == DG_KERNEL_EPT) return launch_apply_ept(m, degree, f64, B, lambda, u, Au, st);
   if (k == DG_KERNEL_TC64) {
-    if (!c1_scratch)
-      return launch_apply_tc64(m, degree, B, lambda, static_cast<const double*>(u), static_cast<double*>(Au), st);
-    k = DG_KERNEL_TENSOR;  // a caller-provided scratch (the allocation-free solve) fits the mma.sync kernel
+    return launch_apply_tc64(m, degree, B, lambda, static_cast<const double*>(u), static_cast<double*>(Au), st,
+                             c1_scratch);
   }
   if (k == DG_KERNEL_TC05) {
     if (tc05_usable(u, Au))

@@ -684,35 +684,74 @@ bool tc64_supported(int degree) {
   return 2 * Np + 3 * NFN + Np <= 224;
 }
 
-cudaError_t launch_apply_tc64(dg_mesh* m, int degree, int B, double lambda, const double* u, double* Au,
-                              cudaStream_t st) {
-  if (B < 1) return cudaSuccess;
-  if (!tc64_supported(degree)) return cudaErrorInvalidValue;
+namespace {
+// The degree's sliced operators on the current device, built on first use
+// when `build` is set (null if not built, or if building failed: *err says why).
+const Tc64Apply* t64_ops(dg_mesh* m, int degree, bool build, cudaError_t* err) {
+  *err = cudaSuccess;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  const Tc64Apply* ops = nullptr;
-  {
-    std::lock_guard<std::mutex> lk(table_mutex());
-    Tc64Apply& o = g_t64[dev & 63][degree];
-    if (!o.grad.blocks) {
-      const RefElem R = m->ref[degree].N ? m->ref[degree] : build_reference(degree);
-      Tc64Apply built;
-      e = build_t64(R, built);
-      if (e != cudaSuccess) return e;
-      o = built;
-    }
-    ops = &o;
+  if (e != cudaSuccess) {
+    *err = e;
+    return nullptr;
   }
+  std::lock_guard<std::mutex> lk(table_mutex());
+  Tc64Apply& o = g_t64[dev & 63][degree];
+  if (!o.grad.blocks) {
+    if (!build) return nullptr;
+    const RefElem R = m->ref[degree].N ? m->ref[degree] : build_reference(degree);
+    Tc64Apply built;
+    e = build_t64(R, built);
+    if (e != cudaSuccess) {
+      *err = e;
+      return nullptr;
+    }
+    o = built;
+  }
+  return &o;
+}
+int t64_ldy(int degree, bool helm) {
+  const int Np = (degree + 1) * (degree + 2) / 2, NFN = 3 * (degree + 1);
+  return (2 * Np + 3 * NFN + (helm ? Np : 0) + 1) & ~1;  // even: 16-byte rows for paired loads
+}
+}  // namespace
+
+size_t tc64_scratch_words(int degree, int64_t nE, bool helm) {
+  const int NFN = 3 * (degree + 1);
+  return size_t(nE) * t64_ldy(degree, helm) + size_t(nE) * NFN * 2 + size_t(nE + 1) / 2 + 2;
+}
+
+cudaError_t ensure_tc64_ops(dg_mesh* m, int degree) {
+  if (!tc64_supported(degree)) return cudaSuccess;
+  cudaError_t e;
+  t64_ops(m, degree, true, &e);
+  return e;
+}
+
+bool tc64_ops_ready(int degree) {
+  if (!tc64_supported(degree)) return false;
+  cudaError_t e;
+  return t64_ops(nullptr, degree, false, &e) != nullptr;
+}
+
+cudaError_t launch_apply_tc64(dg_mesh* m, int degree, int B, double lambda, const double* u, double* Au,
+                              cudaStream_t st, double* scratch) {
+  if (B < 1) return cudaSuccess;
+  if (!tc64_supported(degree)) return cudaErrorInvalidValue;
+  cudaError_t e;
+  const Tc64Apply* ops = t64_ops(m, degree, scratch == nullptr, &e);
+  if (!ops) return e != cudaSuccess ? e : cudaErrorNotReady;
+  int dev = 0;
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
   const int N = degree, Np = (N + 1) * (N + 2) / 2, NFN = 3 * (N + 1);
   const bool helm = lambda != 0.0;
-  const int KYH = 2 * Np + 3 * NFN + (helm ? Np : 0);
-  const int ldy = (KYH + 1) & ~1;  // even: 16-byte rows for paired loads
+  const int ldy = t64_ldy(N, helm);
   const int64_t nE = int64_t(B) * m->K;
   // scratch: Y [nE][ldy], the face data FN [nE][NFN] (u, n.grad u), FP64, and the
-  // rows' largest Y exponents
-  const size_t words = size_t(nE) * ldy + size_t(nE) * NFN * 2 + size_t(nE + 1) / 2 + 2;
-  if (m->t64_cap < words) {
+  // rows' largest Y exponents; every word read is written first by this call
+  const size_t words = tc64_scratch_words(N, nE, helm);
+  if (!scratch && m->t64_cap < words) {
     cudaFree(m->t64_scratch);
     m->t64_scratch = nullptr;
     m->t64_cap = 0;
@@ -722,7 +761,7 @@ cudaError_t launch_apply_tc64(dg_mesh* m, int degree, int B, double lambda, cons
     m->t64_cap = words;
     ++m->scratch_gen;
   }
-  double* Y = m->t64_scratch;
+  double* Y = scratch ? scratch : m->t64_scratch;
   double2* FN = reinterpret_cast<double2*>(Y + size_t(nE) * ldy);
   int* exy = reinterpret_cast<int*>(FN + size_t(nE) * NFN);
   GradOut go{N, m->K, m->geox, Y, ldy, helm ? 1 : 0, lambda, FN, exy};

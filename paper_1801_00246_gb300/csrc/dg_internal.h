@@ -115,9 +115,10 @@ namespace dgx {
 
 // Launchers (device code in the .cu files). `degree` in 1..8.
 cudaError_t ensure_ops(dg_mesh* m, int degree);
-// c1_scratch (optional): device words for the tensor kernels' gradient rows,
-// at least B*K*Np(degree)*(lambda != 0 ? 3 : 2) + 1 of them (FP64 words; FP32
-// needs half); null uses the scratch kept with the mesh (grown on demand).
+// c1_scratch (optional, FP64 only): device words for the tensor kernels'
+// scratch, at least B*K*Np(degree)*(lambda != 0 ? 3 : 2) + 1 of them for the
+// mma.sync kernels and tc64_scratch_words(degree, B*K, lambda != 0) for the
+// tcgen05 one; null uses the scratch kept with the mesh (grown on demand).
 cudaError_t launch_apply(const dg_mesh* m, int degree, dg_prec prec, int B, double lambda, const void* u,
                          void* Au, cudaStream_t st, double* c1_scratch = nullptr);
 cudaError_t launch_rhs(const dg_mesh* m, int B, const double* f, const double* g, double* b, cudaStream_t st);
@@ -148,8 +149,14 @@ void tc64_op_free(Tc64Op* op);
 cudaError_t tc64_gemm_launch(const Tc64Op& op, int64_t rows, const double* X, int64_t ldx, double* out, int64_t ldo,
                              cudaStream_t st);
 bool tc64_supported(int degree);
+// scratch (optional): tc64_scratch_words(degree, B*K, lambda != 0) device words;
+// null uses the scratch kept with the mesh (grown on demand) and builds the
+// degree's tables on first use, a given scratch needs them built already
 cudaError_t launch_apply_tc64(dg_mesh* m, int degree, int B, double lambda, const double* u, double* Au,
-                              cudaStream_t st);
+                              cudaStream_t st, double* scratch = nullptr);
+size_t tc64_scratch_words(int degree, int64_t nE, bool helm);
+cudaError_t ensure_tc64_ops(dg_mesh* m, int degree);  // dg_mesh_setup builds the mesh degree's tables
+bool tc64_ops_ready(int degree);                      // built on the current device (no build)
 cudaError_t tc64_error(int* flag);
 // FP64 products on the tcgen05 tensor cores with exact integer slicing (apply_tc64.cu):
 // an operator A (M x K, K <= 224) cut into 8 slices in blocks of 48 rows x 32 columns

@@ -1285,11 +1285,15 @@ static double* g_static_scratch_ptr[64] = {};  // device address, per device ord
 static size_t align32(size_t n) { return (n + 31) & ~size_t(31); }  // 256-byte steps
 
 // Words of the fixed array one call uses: r, z, p, Ap, the Jacobi inverse, the
-// per-right-hand-side scalars and reduction partials, and the gradient rows of
-// the tensor-core apply (2 Np per element, 3 Np with lambda != 0).
-size_t static_scratch_need(int64_t n, int B, bool helm) {
+// per-right-hand-side scalars and reduction partials, and the apply kernel's
+// scratch: the gradient rows of the mma.sync tensor kernels (2 Np per element,
+// 3 Np with lambda != 0) or the tcgen05 kernel's rows and face data.
+size_t static_scratch_need(const dg_mesh* m, int kernel, int B, bool helm) {
+  const int64_t n = int64_t(m->K) * npd(m->N);
+  const size_t apply = kernel == DG_KERNEL_TC64 ? tc64_scratch_words(m->N, int64_t(B) * m->K, helm)
+                                                : size_t(n) * B * (helm ? 3 : 2) + 1;
   return 4 * align32(size_t(n) * B) + align32(size_t(n)) + align32(size_t(B) * kNS) +
-         align32(size_t(B) * kRedBlocks * 2) + align32(size_t(n) * B * (helm ? 3 : 2) + 1);
+         align32(size_t(B) * kRedBlocks * 2) + align32(apply);
 }
 
 }  // namespace dgx
@@ -1303,11 +1307,14 @@ extern "C" dg_status dg_pcg_jacobi_solve_static(const dg_mesh* mc, int B, double
   if (!std::isfinite(lambda) || lambda < 0) { set_error("lambda must be finite and >= 0"); return DG_ERR_ARG; }
   dg_mesh* m = const_cast<dg_mesh*>(mc);
   const int64_t n = int64_t(m->K) * npd(m->N);
-  const size_t need = static_scratch_need(n, B, lambda != 0.0);
+  int kf = m->kern[m->N][0][lambda != 0.0 ? 1 : 0];
+  if (kf == DG_KERNEL_AUTO) kf = default_kernel(m->N, true);
+  const size_t need = static_scratch_need(m, kf, B, lambda != 0.0);
   if (need > kStaticScratchDoubles) {
     set_error("dg_pcg_jacobi_solve_static: problem needs " + std::to_string(need) +
               " scratch doubles, the static array holds " + std::to_string(kStaticScratchDoubles) +
-              " (at B = 1, K*Np must stay below about 599,000 for lambda = 0 and 524,000 otherwise)");
+              " (at B = 1 and degree 8 with the default kernel, K must stay below about 9,200 triangles "
+              "for lambda = 0 and 8,400 otherwise)");
     return DG_ERR_ARG;
   }
   if (!m->ops64[m->N].buf) { set_error("mesh operators missing"); return DG_ERR_ARG; }
@@ -1320,14 +1327,10 @@ extern "C" dg_status dg_pcg_jacobi_solve_static(const dg_mesh* mc, int B, double
   }
   // the tensor-core apply's operator slices are built by dg_mesh_setup on the
   // mesh's device; building them here would allocate
-  {
-    int kf = m->kern[m->N][0][lambda != 0.0 ? 1 : 0];
-    if (kf == DG_KERNEL_AUTO) kf = default_kernel(m->N, true);
-    if ((kf == DG_KERNEL_TENSOR || kf == DG_KERNEL_TENSOR_PIPE || kf == DG_KERNEL_TC64) &&
-        !tensor_ops_ready(m->N, true)) {  // (the tcgen05 FP64 kernel is replaced by the mma.sync one here)
-      set_error("dg_pcg_jacobi_solve_static: the current device is not the one the mesh was set up on");
-      return DG_ERR_ARG;
-    }
+  if (((kf == DG_KERNEL_TENSOR || kf == DG_KERNEL_TENSOR_PIPE) && !tensor_ops_ready(m->N, true)) ||
+      (kf == DG_KERNEL_TC64 && !tc64_ops_ready(m->N))) {
+    set_error("dg_pcg_jacobi_solve_static: the current device is not the one the mesh was set up on");
+    return DG_ERR_ARG;
   }
   double* base = nullptr;
   {
@@ -1351,7 +1354,7 @@ extern "C" dg_status dg_pcg_jacobi_solve_static(const dg_mesh* mc, int B, double
   double* dinv = Ap + align32(nt);
   double* scal = dinv + align32(size_t(n));
   double* partial = scal + align32(size_t(B) * kNS);
-  double* c1 = partial + align32(size_t(B) * kRedBlocks * 2);  // the apply's gradient rows
+  double* c1 = partial + align32(size_t(B) * kRedBlocks * 2);  // the apply kernel's scratch
   const dim3 g = vgrid(n, B);
 #define SCK(expr)                                                                          \
   do {                                                                                     \
