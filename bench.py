@@ -562,10 +562,7 @@ def run_sweep(args):
             for lam in (0.0, 1.0):
                 for key, prec, u, o in (("f64", P.DG_F64, u64, o64), ("f32", P.DG_F32, u32, o32)):
                     default = mesh.kernel(N, prec, lam != 0.0)
-                    ks = [P.KERNEL_TILE, P.KERNEL_TENSOR, P.KERNEL_TENSOR_PIPE] + ([P.KERNEL_TC64] if key == "f64" else [P.KERNEL_GEMM, P.KERNEL_TC05])
-                    if N <= 3:
-                        ks.append(P.KERNEL_EPT)
-                    for k in ks:
+                    for k in mesh.kernels_available(N, prec):
                         mesh.set_kernel(N, prec, lam != 0.0, k)
                         ms = []
                         for it in range(args.warmup + args.steps):
@@ -653,7 +650,7 @@ def main():
     ap.add_argument("--graph", type=int, default=1, help="--solve-only: 1 = CUDA-graph solve, 0 = host loop")
     ap.add_argument("--fp64", action="store_true", help="--solve-only: FP64 multigrid levels")
     ap.add_argument("--ins", action="store_true", help="time dg_ins_step on the 8192-triangle Kovasznay case")
-    ap.add_argument("--sweep-degrees", default="1,2,3,4,5,6,7,8")
+    ap.add_argument("--sweep-degrees", default="1,2,3,4,5,6,7,8,9,10")
     ap.add_argument("--sweep-batches", default="1,4,16")
     args = ap.parse_args()
     if args.warmup < 3:

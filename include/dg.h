@@ -5,7 +5,7 @@
  * incompressible-flow method of Karakus, Chalmers, Swirydowicz & Warburton
  * (arXiv:1801.00246): the matrix-free symmetric-interior-penalty (SIPDG)
  * Laplacian / screened-Poisson operator on affine triangles of degree
- * N = 1..8 (Section 2.1 Eq. INS_SD_5, Section 5.2 Eq. ellipticOp1-3), and
+ * N = 1..10 (Section 2.1 Eq. INS_SD_5, Section 5.2 Eq. ellipticOp1-3), and
  * its solution by preconditioned conjugate gradients with a degree-coarsening
  * p-multigrid preconditioner (Section 3).
  *
@@ -79,27 +79,31 @@ typedef struct dg_mesh dg_mesh; /* opaque; owned by the library until dg_mesh_de
  *   DG_KERNEL_AUTO:   the mesh's current choice (built-in per degree, or set
  *                     by dg_autotune / dg_set_apply_kernel)
  *   DG_KERNEL_TILE:   element tiles in shared memory, one thread per node
- *                     (FP64 on the FP64 pipe, or FP32); all degrees
- *   DG_KERNEL_GEMM:   FP32 only: register-blocked small GEMMs over element tiles; all degrees
+ *                     (FP64 on the FP64 pipe, or FP32); all degrees (FP32 default at N = 10)
+ *   DG_KERNEL_GEMM:   FP32 only: register-blocked small GEMMs over element tiles; degrees 1-9
  *   DG_KERNEL_TENSOR: dense products on the BF16 tensor cores (FP64: exact 7-bit
  *                     integer slicing, 8 slices; FP32: three round-to-nearest BF16
- *                     pieces); all degrees
+ *                     pieces); degrees 1-9
  *   DG_KERNEL_EPT:    one element per thread, operators in constant memory; degrees 1-3
  *   DG_KERNEL_TENSOR_PIPE: DG_KERNEL_TENSOR with the output product's fill and product
  *                     phases on separate warps, double-buffered through shared memory
  *                     (mbarrier hand-off with bounded waits; see dg_tensor_timeouts)
  *   DG_KERNEL_TC05:   FP32 only: both products on the Blackwell tensor cores (tcgen05,
  *                     operands and accumulators in tensor memory, bulk copies), two FP16
- *                     pieces per operand scaled by powers of two; all degrees. Needs u and
+ *                     pieces per operand scaled by powers of two; degrees 1-8. Needs u and
  *                     Au 16-byte aligned (otherwise DG_KERNEL_TENSOR runs instead).
  *   DG_KERNEL_TC64:   FP64 only: both products on the Blackwell tensor cores (tcgen05,
  *                     exact 7-bit integer slicing, 8 slices, accumulators in tensor memory)
- *                     and the pointwise stage in float-float on the FP32 pipe; degrees 1-8.
+ *                     and the pointwise stage in float-float on the FP32 pipe; all degrees.
+ *                     Intermediates carry 48 bits (float-float), so where the operator's
+ *                     terms cancel strongly (a node next to an element 2^60 larger, at
+ *                     N = 10) an entry's error can reach a few 1e-12 of |A||u|.
  *                     Handles finite fields whose magnitudes stay within the double range
  *                     at every stage (about 1e-250..1e250, as DG_KERNEL_TENSOR). */
 enum { DG_KERNEL_AUTO = 0, DG_KERNEL_TILE = 1, DG_KERNEL_GEMM = 2, DG_KERNEL_TENSOR = 3, DG_KERNEL_EPT = 4,
        DG_KERNEL_TENSOR_PIPE = 5, DG_KERNEL_TC05 = 6, DG_KERNEL_TC64 = 7 };
 #define DG_NUM_KERNELS 8 /* kernel ids 0..7; dg_autotune's times use this many slots per entry */
+#define DG_MAX_DEGREE 10 /* degrees 1..10 (Section 5.2 studies the kernels up to N = 10) */
 
 /* Preconditioner choices for dg_pcg_solve (Section 3). */
 enum { DG_PREC_NONE = 0, DG_PREC_JACOBI = 1, DG_PREC_INVMASS = 2, DG_PREC_PMG = 3 };
@@ -137,7 +141,7 @@ typedef struct {
 /* Default options: tol 1e-10, max_iter 1000, Jacobi, no multigrid. */
 void dg_solver_opts_default(dg_solver_opts* opts);
 
-/* Build the discretisation of degree N (1..8) on a triangle mesh.
+/* Build the discretisation of degree N (1..DG_MAX_DEGREE) on a triangle mesh.
  * VX, VY: host, Nv vertex coordinates. EToV: host, K x 3 vertex indices,
  * counter-clockwise. bc: host, K x 3 tags (0 interior, 1 Dirichlet,
  * 2 Neumann) of face f = (v_f, v_{f+1}); a face with no neighbour must carry
@@ -154,7 +158,7 @@ dg_status dg_mesh_destroy(dg_mesh* mesh);
 /* Degree, element count and nodes per element of a mesh. */
 dg_status dg_mesh_info(const dg_mesh* mesh, int* N, int64_t* K, int* Np);
 
-/* Physical coordinates of the degree-`degree` nodes (1..8; 0 = mesh degree):
+/* Physical coordinates of the degree-`degree` nodes (1..10; 0 = mesh degree):
  * x_dev, y_dev device arrays [K][Np(degree)], FP64. */
 dg_status dg_mesh_nodes(const dg_mesh* mesh, int degree, double* x_dev, double* y_dev, void* stream);
 
@@ -173,7 +177,7 @@ dg_status dg_poisson_apply(const dg_mesh* mesh, dg_prec prec, int B, const void*
 dg_status dg_helmholtz_apply(const dg_mesh* mesh, dg_prec prec, int B, double lambda,
                              const void* u, void* Au, void* stream);
 
-/* Either operator at any degree 1..8 on the same mesh (p-multigrid levels). */
+/* Either operator at any degree 1..10 on the same mesh (p-multigrid levels). */
 dg_status dg_operator_apply(const dg_mesh* mesh, int degree, dg_prec prec, int B, double lambda,
                             const void* u, void* Au, void* stream);
 
@@ -195,7 +199,7 @@ int dg_get_apply_kernel(const dg_mesh* mesh, int degree, dg_prec prec, int helmh
  * (256 MB L2 flush before each of three timed launches, best kept), for the
  * Poisson form and, if lambda > 0, the Helmholtz form (with lambda = 0 the
  * Helmholtz entry takes the Poisson winner), and stores the fastest in the
- * kernel table. times (host, may be NULL): float[9][2][2][DG_NUM_KERNELS] milliseconds
+ * kernel table. times (host, may be NULL): float[DG_MAX_DEGREE + 1][2][2][DG_NUM_KERNELS] milliseconds
  * indexed [degree][0: FP64, 1: FP32][helmholtz][kernel], 0 where not timed.
  * Allocates and frees its own scratch (4 fields of B*K*Np(degree_hi) values
  * plus 256 MB); synchronises `stream`. Solves captured as CUDA graphs before
@@ -299,7 +303,7 @@ dg_status dg_ins_step(dg_mesh* mesh_u, dg_mesh* mesh_p, dg_ins_state* state, int
 dg_status dg_pcg_jacobi_solve_static(const dg_mesh* mesh, int B, double lambda, double tol, int max_iter,
                                      const double* b, double* x, dg_solve_info* info, void* stream);
 
-/* Host-only: the library's own reference data for degree N (1..8), for
+/* Host-only: the library's own reference data for degree N (1..10), for
  * inspection without a GPU. r, s: Np; M, Dr, Ds: Np x Np row-major;
  * Mf: (N+1) x (N+1); fmask: 3 x (N+1) local node index of face node j of face
  * f in counter-clockwise order. Any pointer may be NULL. */

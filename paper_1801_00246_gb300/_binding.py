@@ -11,6 +11,7 @@ PREC_NONE, PREC_JACOBI, PREC_INVMASS, PREC_PMG = 0, 1, 2, 3
 (KERNEL_AUTO, KERNEL_TILE, KERNEL_GEMM, KERNEL_TENSOR, KERNEL_EPT, KERNEL_TENSOR_PIPE, KERNEL_TC05,
  KERNEL_TC64) = 0, 1, 2, 3, 4, 5, 6, 7
 NUM_KERNELS = 8
+MAX_DEGREE = 10  # DG_MAX_DEGREE
 DG_MAX_BATCH = 64
 
 _STATUS = {0: "DG_OK", 1: "DG_ERR_ARG", 2: "DG_ERR_CUDA", 3: "DG_ERR_OOM", 4: "DG_ERR_NOT_CONVERGED",
@@ -214,11 +215,24 @@ class Mesh:
     def kernel(self, degree, prec, helmholtz=0):
         return lib().dg_get_apply_kernel(self._h, int(degree), int(prec), int(bool(helmholtz)))
 
+    def kernels_available(self, degree, prec):
+        """The KERNEL_* ids the library accepts for a degree and precision (asked
+        through the kernel table, whose entry is restored)."""
+        L = lib()
+        keep = [L.dg_get_apply_kernel(self._h, int(degree), int(prec), h) for h in (0, 1)]
+        out = [k for k in range(1, NUM_KERNELS)
+               if L.dg_set_apply_kernel(self._h, int(degree), int(prec), 0, k) == 0]
+        for h in (0, 1):
+            L.dg_set_apply_kernel(self._h, int(degree), int(prec), h, KERNEL_AUTO)
+            if keep[h] >= 0 and keep[h] != L.dg_get_apply_kernel(self._h, int(degree), int(prec), h):
+                L.dg_set_apply_kernel(self._h, int(degree), int(prec), h, keep[h])
+        return out
+
     def autotune(self, B=1, lam=0.0, degrees=None):
         """Time every available kernel per degree and precision on this mesh and
         keep the fastest; returns {(degree, 'f64'|'f32', helmholtz): {kernel: ms}}."""
         lo, hi = degrees if degrees is not None else (1, self.N)
-        times = (ctypes.c_float * (9 * 2 * 2 * NUM_KERNELS))()
+        times = (ctypes.c_float * ((MAX_DEGREE + 1) * 2 * 2 * NUM_KERNELS))()
         _check(lib().dg_autotune(self._h, int(B), float(lam), int(lo), int(hi), times, _stream()))
         out = {}
         for d in range(lo, hi + 1):

@@ -258,7 +258,7 @@ dg_status dg_mesh_setup(int N, int64_t Nv, const double* VX, const double* VY, i
   (void)stream;
   if (!out) { set_error("out is NULL"); return DG_ERR_ARG; }
   *out = nullptr;
-  if (N < 1 || N > kMaxN) { set_error("degree N must be in 1..8"); return DG_ERR_ARG; }
+  if (N < 1 || N > kMaxN) { set_error("degree N must be in 1..10"); return DG_ERR_ARG; }
   if (Nv < 3 || K < 1 || !VX || !VY || !EToV || !bc) { set_error("empty mesh or NULL array"); return DG_ERR_ARG; }
   if (K > (int64_t(1) << 29)) { set_error("K too large"); return DG_ERR_ARG; }
   DG_TRY_BEGIN
@@ -391,7 +391,7 @@ dg_status dg_mesh_info(const dg_mesh* m, int* N, int64_t* K, int* Np) {
 dg_status dg_mesh_nodes(const dg_mesh* mc, int degree, double* x, double* y, void* stream) {
   if (!mc || !x || !y) { set_error("NULL argument"); return DG_ERR_ARG; }
   if (degree == 0) degree = mc->N;
-  if (degree < 1 || degree > kMaxN) { set_error("degree must be in 0..8"); return DG_ERR_ARG; }
+  if (degree < 1 || degree > kMaxN) { set_error("degree must be in 0..10"); return DG_ERR_ARG; }
   DG_TRY_BEGIN
   dg_mesh* m = const_cast<dg_mesh*>(mc);
   if (m->ref[degree].N == 0) m->ref[degree] = build_reference(degree);
@@ -412,7 +412,7 @@ dg_status dg_operator_apply(const dg_mesh* mc, int degree, dg_prec prec, int B, 
   if (B == 0) return DG_OK;  // empty batch: nothing to read or write
   if (!u || !Au) { set_error("NULL argument"); return DG_ERR_ARG; }
   if (degree == 0) degree = mc->N;
-  if (degree < 1 || degree > kMaxN) { set_error("degree must be in 1..8"); return DG_ERR_ARG; }
+  if (degree < 1 || degree > kMaxN) { set_error("degree must be in 1..10"); return DG_ERR_ARG; }
   if (prec != DG_F64 && prec != DG_F32 && prec != DG_F64_DFMA) { set_error("bad precision"); return DG_ERR_ARG; }
   if (B < 0) { set_error("negative batch"); return DG_ERR_ARG; }
   if (u == Au) { set_error("u and Au must not alias"); return DG_ERR_ARG; }
@@ -438,7 +438,7 @@ dg_status dg_helmholtz_apply(const dg_mesh* m, dg_prec prec, int B, double lambd
 dg_status dg_operator_diagonal(const dg_mesh* mc, int degree, dg_prec prec, double lambda, void* diag, void* stream) {
   if (!mc || !diag) { set_error("NULL argument"); return DG_ERR_ARG; }
   if (degree == 0) degree = mc->N;
-  if (degree < 1 || degree > kMaxN) { set_error("degree must be in 1..8"); return DG_ERR_ARG; }
+  if (degree < 1 || degree > kMaxN) { set_error("degree must be in 1..10"); return DG_ERR_ARG; }
   if (prec != DG_F64 && prec != DG_F32) { set_error("bad precision"); return DG_ERR_ARG; }
   DG_TRY_BEGIN
   dg_mesh* m = const_cast<dg_mesh*>(mc);
@@ -461,7 +461,7 @@ dg_status dg_rhs(const dg_mesh* m, int B, const double* f, const double* g, doub
 
 dg_status dg_reference_operators(int N, double* r, double* s, double* M, double* Dr, double* Ds, double* Mf,
                                  int32_t* fmask) {
-  if (N < 1 || N > kMaxN) { set_error("degree N must be in 1..8"); return DG_ERR_ARG; }
+  if (N < 1 || N > kMaxN) { set_error("degree N must be in 1..10"); return DG_ERR_ARG; }
   DG_TRY_BEGIN
   const RefElem R = build_reference(N);
   auto cp = [](double* dst, const std::vector<double>& v) { if (dst) std::memcpy(dst, v.data(), v.size() * sizeof(double)); };
@@ -478,7 +478,7 @@ dg_status dg_reference_operators(int N, double* r, double* s, double* M, double*
 }
 
 dg_status dg_interpolation_matrix(int Nf, int Nc, double* P) {
-  if (Nf < 2 || Nf > kMaxN || Nc < 1 || Nc >= Nf || !P) { set_error("need 8 >= Nf > Nc >= 1 and P"); return DG_ERR_ARG; }
+  if (Nf < 2 || Nf > kMaxN || Nc < 1 || Nc >= Nf || !P) { set_error("need 10 >= Nf > Nc >= 1 and P"); return DG_ERR_ARG; }
   DG_TRY_BEGIN
   const std::vector<double> h = interpolation_matrix(Nf, Nc);
   std::memcpy(P, h.data(), h.size() * sizeof(double));

@@ -376,6 +376,7 @@ cudaError_t launch_n(const dg_mesh* m, dg_prec prec, int B, double lambda, const
   cudaError_t launch_apply_f32_n##n(const dg_mesh* m, int B, double lambda, const float* u, float* Au, float2* face, \
                                    cudaStream_t st);
 DG_TE_DECL(1) DG_TE_DECL(2) DG_TE_DECL(3) DG_TE_DECL(4) DG_TE_DECL(5) DG_TE_DECL(6) DG_TE_DECL(7) DG_TE_DECL(8)
+DG_TE_DECL(9)
 #undef DG_TE_DECL
 
 // Kernel choice: the tile kernel above (FP64 or FP32), register-blocked FP32
@@ -384,20 +385,23 @@ DG_TE_DECL(1) DG_TE_DECL(2) DG_TE_DECL(3) DG_TE_DECL(4) DG_TE_DECL(5) DG_TE_DECL
 // thread (apply_ept.cu). DG_F64_DFMA forces the tile kernel in FP64.
 
 // Built-in kernel per degree and precision (the measured winners on the
-// 524,288-triangle workload; dg_autotune replaces them per mesh).
+// 524,288-triangle workload; dg_autotune replaces them per mesh). Above degree
+// 8 the tcgen05 FP32 kernel's operands no longer fit in tensor memory.
 int default_kernel(int degree, bool f64) {
   if (f64) return degree >= 3 ? DG_KERNEL_TC64 : DG_KERNEL_EPT;
-  return degree <= 3 ? DG_KERNEL_EPT : DG_KERNEL_TC05;
+  if (degree <= 3) return DG_KERNEL_EPT;
+  if (degree <= 8) return DG_KERNEL_TC05;
+  return degree == 9 ? DG_KERNEL_TENSOR : DG_KERNEL_TILE;
 }
 
 bool kernel_valid(int kernel, int degree, bool f64) {
   switch (kernel) {
     case DG_KERNEL_TILE: return true;
-    case DG_KERNEL_GEMM: return !f64;
-    case DG_KERNEL_TENSOR: return true;
-    case DG_KERNEL_TENSOR_PIPE: return true;
+    case DG_KERNEL_GEMM: return !f64 && degree <= 9;  // shared memory
+    case DG_KERNEL_TENSOR: return tensor_supported(degree);
+    case DG_KERNEL_TENSOR_PIPE: return tensor_supported(degree);
     case DG_KERNEL_EPT: return ept_supported(degree);
-    case DG_KERNEL_TC05: return !f64;
+    case DG_KERNEL_TC05: return !f64 && degree <= 8;  // tensor memory
     case DG_KERNEL_TC64: return f64 && tc64_supported(degree);
     default: return false;
   }
@@ -453,6 +457,7 @@ cudaError_t launch_apply(const dg_mesh* mc, int degree, dg_prec prec, int B, dou
       case 6: return launch_apply_f32_n6(m, B, lambda, uf, of, m->face32, st);
       case 7: return launch_apply_f32_n7(m, B, lambda, uf, of, m->face32, st);
       case 8: return launch_apply_f32_n8(m, B, lambda, uf, of, m->face32, st);
+      case 9: return launch_apply_f32_n9(m, B, lambda, uf, of, m->face32, st);
       default: return cudaErrorInvalidValue;
     }
   }
@@ -465,6 +470,8 @@ cudaError_t launch_apply(const dg_mesh* mc, int degree, dg_prec prec, int B, dou
     case 6: return launch_n<6>(mc, prec, B, lambda, u, Au, st);
     case 7: return launch_n<7>(mc, prec, B, lambda, u, Au, st);
     case 8: return launch_n<8>(mc, prec, B, lambda, u, Au, st);
+    case 9: return launch_n<9>(mc, prec, B, lambda, u, Au, st);
+    case 10: return launch_n<10>(mc, prec, B, lambda, u, Au, st);
     default: return cudaErrorInvalidValue;
   }
 }

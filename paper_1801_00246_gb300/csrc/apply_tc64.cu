@@ -13,7 +13,7 @@
 //    way on the device (integer operations on the double's bits); the 36 slice
 //    products with i + j <= 7 run as tcgen05.mma (BF16 operands from shared
 //    memory, FP32 accumulators in tensor memory, one accumulator per slice
-//    exponent i + j: integer sums below 2^24 for K <= 224 and up to 4 products,
+//    exponent i + j: integer sums below 2^24 for K <= 256 and up to 4 products,
 //    exact); the accumulators are recombined by Horner's rule in float-float
 //    and rebuilt as doubles from the exponent bits. Data slices are written by
 //    the threads into a double-buffered shared-memory chunk (32 columns) while
@@ -42,6 +42,15 @@ constexpr int kT = 128;                      // rows per tile (MMA M)
 constexpr int kKC = 32;                      // data columns per chunk
 constexpr int kNC = 48;                      // output columns per pass (MMA N)
 constexpr int kSl = 8;                       // slices of 7 bits
+// Longest sum: a slice product is below 127^2 in magnitude, and an accumulator
+// group with up to 4 products over 256 terms stays below 4 * 256 * 127^2 <
+// 2^24, an integer FP32 represents exactly; groups with more products carry
+// weights below 2^-28 of the leading one (the fifth group stays exact up to
+// 208 terms: 5 * 208 * 127^2 < 2^24).
+constexpr int kMaxDepth = 256;
+// The output product at depths above this runs per column block (volume,
+// face, Helmholtz), each block with its own row exponent, accumulated into Au.
+constexpr int kSplitDepth = 208;
 constexpr int kABytes = kSl * kT * kKC * 2;  // one data chunk, 8 slices: 64 KB
 constexpr int kBBytes = kSl * kNC * kKC * 2; // one operator block, 8 slices: 24 KB
 constexpr int kASlice = kT * kKC * 2, kBSlice = kNC * kKC * 2;
@@ -186,6 +195,7 @@ struct GradOut {
   double lambda;
   double2* FN;  // [rows][3 (N+1)]
   int* exy;     // [rows]: largest exponent of the row's Y values (for the output product)
+  int* exf;     // [rows] or null: set to "none" here when the face columns keep their own exponent
 };
 
 // out[r][c] = sum_k A[c][k] X[r][k] for r < rows, c < M, k < Kd (A sliced in
@@ -210,7 +220,7 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
                                                               const int* __restrict__ ex_given,
                                                               const uint8_t* __restrict__ Bops,
                                                               const int* __restrict__ ea, double* __restrict__ out,
-                                                              int64_t ldo, GradOut go) {
+                                                              int64_t ldo, int accum, GradOut go) {
   extern __shared__ __align__(1024) uint8_t sm[];
   uint8_t* sA = sm;                        // [2][8 slices][128 rows][32] canonical
   uint8_t* sB = sm + 2 * kABytes;          // [2][8 slices][48 rows][32] canonical
@@ -405,7 +415,8 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
               if (live && col < M) {
                 // value = 2^{ea + E - 14} sum_s acc_s 2^{-7 s}
                 const ff hl = horner8(acc, c);
-                out[row * ldo + col] = ff_to_double(hl.h, hl.l, __ldg(ea + col) + E - 14);
+                const double v = ff_to_double(hl.h, hl.l, __ldg(ea + col) + E - 14);
+                out[row * ldo + col] = accum ? out[row * ldo + col] + v : v;
               }
             }
           } else {
@@ -474,6 +485,7 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
         asm volatile("bar.sync 1, %0;\n" ::"r"(kSlicers) : "memory");
         if (q == 0 && live)
           go.exy[row] = max(max(pmax[e], pmax[kT + e]), max(pmax[2 * kT + e], pmax[3 * kT + e]));
+        if (q == 0 && live && go.exf) go.exf[row] = -1100;  // raised by the face fill
       }
     }
   }
@@ -559,7 +571,7 @@ cudaError_t tc64_op_create(const std::vector<double>& A, int M, int K, Tc64Op* o
   op->K = K;
   op->NCH = (M + kNC - 1) / kNC;
   op->KCH = (K + kKC - 1) / kKC;
-  if (K > 224) return cudaErrorInvalidValue;  // longer sums would leave the FP32 group sums inexact
+  if (K > kMaxDepth) return cudaErrorInvalidValue;  // longer sums would leave the FP32 group sums inexact
   std::vector<uint8_t> img(size_t(op->NCH) * op->KCH * kBBytes, 0);
   std::vector<int> ea(size_t(op->NCH) * kNC, 0);
   for (int r = 0; r < M; ++r) {
@@ -601,7 +613,7 @@ void tc64_op_free(Tc64Op* op) {
 namespace {
 template <int MODE>
 cudaError_t gemm_launch(const Tc64Op& op, int64_t rows, const double* X, int64_t ldx, double* out, int64_t ldo,
-                        const int* ex_given, const GradOut& go, cudaStream_t st) {
+                        const int* ex_given, const GradOut& go, cudaStream_t st, int accum = 0) {
   if (rows <= 0) return cudaSuccess;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -622,7 +634,7 @@ cudaError_t gemm_launch(const Tc64Op& op, int64_t rows, const double* X, int64_t
   const int64_t tiles = (rows + kT - 1) / kT;
   const unsigned g = unsigned(std::min<int64_t>(tiles, grid[dev & 63]));
   tc64_gemm<MODE><<<g, kSlicers + 32, kSmem, st>>>(rows, op.M, op.K, op.NCH, op.KCH, X, ldx, vec2, ex_given,
-                                                   op.blocks, op.ea, out, ldo, go);
+                                                   op.blocks, op.ea, out, ldo, accum, go);
   note_launch();
   return cudaGetLastError();
 }
@@ -636,7 +648,9 @@ cudaError_t tc64_gemm_launch(const Tc64Op& op, int64_t rows, const double* X, in
 namespace {
 struct Tc64Apply {
   Tc64Op grad;       // [Dr; Ds] with rows interleaved (Dr row n, Ds row n, ...)
-  Tc64Op out, outh;  // OB, [OB | M]
+  Tc64Op out, outh;  // OB, [OB | M] (when its depth stays within kMaxDepth)
+  Tc64Op mh;         // M alone, otherwise: the Helmholtz term as a second, accumulating product
+  Tc64Op outv, outf; // [Br Bs] and the face blocks of OB, when OB is deeper than kSplitDepth
 };
 Tc64Apply g_t64[64][kMaxN + 1];  // [device][degree]
 
@@ -673,15 +687,33 @@ cudaError_t build_t64(const RefElem& R, Tc64Apply& o) {
     for (int m = 0; m < Np; ++m) BH[size_t(i) * KH + KY + m] = R.M[size_t(i) * Np + m];
   }
   cudaError_t e = tc64_op_create(A1, 2 * Np, Np, &o.grad);
+  if (KY > kSplitDepth) {  // column blocks [Br Bs], [face blocks], M, each from its own Y columns
+    std::vector<double> Bv(size_t(Np) * 2 * Np), Bf(size_t(Np) * 3 * NFN), Mm(R.M.begin(), R.M.begin() + size_t(Np) * Np);
+    for (int i = 0; i < Np; ++i) {
+      for (int k = 0; k < 2 * Np; ++k) Bv[size_t(i) * 2 * Np + k] = B[size_t(i) * KY + k];
+      for (int k = 0; k < 3 * NFN; ++k) Bf[size_t(i) * 3 * NFN + k] = B[size_t(i) * KY + 2 * Np + k];
+    }
+    if (e == cudaSuccess) e = tc64_op_create(Bv, Np, 2 * Np, &o.outv);
+    if (e == cudaSuccess) e = tc64_op_create(Bf, Np, 3 * NFN, &o.outf);
+    if (e == cudaSuccess) e = tc64_op_create(Mm, Np, Np, &o.mh);
+    return e;
+  }
   if (e == cudaSuccess) e = tc64_op_create(B, Np, KY, &o.out);
-  if (e == cudaSuccess) e = tc64_op_create(BH, Np, KH, &o.outh);
+  if (e == cudaSuccess) {
+    if (KH <= kMaxDepth) {
+      e = tc64_op_create(BH, Np, KH, &o.outh);
+    } else {
+      std::vector<double> Mm(R.M.begin(), R.M.begin() + size_t(Np) * Np);
+      e = tc64_op_create(Mm, Np, Np, &o.mh);
+    }
+  }
   return e;
 }
 }  // namespace
 
 bool tc64_supported(int degree) {
   const int Np = (degree + 1) * (degree + 2) / 2, NFN = 3 * (degree + 1);
-  return 2 * Np + 3 * NFN + Np <= 224;
+  return 2 * Np + 3 * NFN <= kMaxDepth && Np <= kMaxDepth;
 }
 
 namespace {
@@ -718,7 +750,7 @@ int t64_ldy(int degree, bool helm) {
 
 size_t tc64_scratch_words(int degree, int64_t nE, bool helm) {
   const int NFN = 3 * (degree + 1);
-  return size_t(nE) * t64_ldy(degree, helm) + size_t(nE) * NFN * 2 + size_t(nE + 1) / 2 + 2;
+  return size_t(nE) * t64_ldy(degree, helm) + size_t(nE) * NFN * 2 + 2 * (size_t(nE + 1) / 2) + 2;
 }
 
 cudaError_t ensure_tc64_ops(dg_mesh* m, int degree) {
@@ -764,7 +796,9 @@ cudaError_t launch_apply_tc64(dg_mesh* m, int degree, int B, double lambda, cons
   double* Y = scratch ? scratch : m->t64_scratch;
   double2* FN = reinterpret_cast<double2*>(Y + size_t(nE) * ldy);
   int* exy = reinterpret_cast<int*>(FN + size_t(nE) * NFN);
-  GradOut go{N, m->K, m->geox, Y, ldy, helm ? 1 : 0, lambda, FN, exy};
+  const bool split = ops->outv.blocks != nullptr;
+  int* exf = split ? exy + 2 * (size_t(nE + 1) / 2) : nullptr;  // the face columns' own exponents
+  GradOut go{N, m->K, m->geox, Y, ldy, helm ? 1 : 0, lambda, FN, exy, exf};
   e = gemm_launch<1>(ops->grad, nE, u, Np, nullptr, 0, nullptr, go, st);
   if (e != cudaSuccess) return e;
   {
@@ -773,10 +807,22 @@ cudaError_t launch_apply_tc64(dg_mesh* m, int degree, int B, double lambda, cons
     if (e != cudaSuccess) return e;
     const int64_t total = nE * NFN;
     const int64_t blocks = std::min<int64_t>((total + 255) / 256, int64_t(sms) * 16);
-    tc64_face_fill<<<unsigned(blocks), 256, 0, st>>>(N, m->K, nE, m->geox, m->conn, FN, Y, ldy, exy);
+    tc64_face_fill<<<unsigned(blocks), 256, 0, st>>>(N, m->K, nE, m->geox, m->conn, FN, Y, ldy, split ? exf : exy);
     note_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+  }
+  if (split) {  // Au = [Br Bs] Y_v + (face blocks) Y_f (+ M Y_h), the face block with its own exponents
+    e = gemm_launch<0>(ops->outv, nE, Y, ldy, Au, Np, exy, GradOut{}, st);
+    if (e == cudaSuccess) e = gemm_launch<0>(ops->outf, nE, Y + 2 * Np, ldy, Au, Np, exf, GradOut{}, st, 1);
+    if (e != cudaSuccess || !helm) return e;
+    return gemm_launch<0>(ops->mh, nE, Y + 2 * Np + 3 * NFN, ldy, Au, Np, exy, GradOut{}, st, 1);
+  }
+  if (helm && !ops->outh.blocks) {  // [OB | M] is too deep for exact group sums: OB Y, then += M (lambda J u)
+    const int KY = 2 * Np + 3 * NFN;
+    e = gemm_launch<0>(ops->out, nE, Y, ldy, Au, Np, exy, GradOut{}, st);
+    if (e != cudaSuccess) return e;
+    return gemm_launch<0>(ops->mh, nE, Y + KY, ldy, Au, Np, exy, GradOut{}, st, 1);
   }
   return gemm_launch<0>(helm ? ops->outh : ops->out, nE, Y, ldy, Au, Np, exy, GradOut{}, st);
 }

@@ -11,10 +11,10 @@
 //     sum_i a_i 2^{-7i}, i = 1..KS, with signed integers |a_i| <= 127 (host);
 //   * every element's data column is scaled by 2^{ex_e} and sliced the same way
 //     on the fly from the value's bit pattern (integer shifts only);
-//   * a_i x_j products summed over K <= 224 are integers below 2^22, exact in the
-//     FP32 accumulators of mma.sync m16n8k16; products with the same i + j share
-//     an accumulator, which stays exact (below 2^24) for groups of up to 4
-//     products at K = 224 (up to 6 at K = 171); the larger groups carry weights
+//   * a_i x_j products summed over K <= 256 are integers below 2^22 (127^2 * 256),
+//     exact in the FP32 accumulators of mma.sync m16n8k16; products with the
+//     same i + j share an accumulator, which stays exact (below 2^24) for groups
+//     of up to 4 products at K = 256 (up to 6 at K = 171); the larger groups carry weights
 //     below 2^-28 of the leading one, so their rounding is below 2^-50 of the
 //     result; only i + j <= KS + 1 is formed;
 //   * the KS accumulators are combined by Horner's rule (float-float for FP64)
@@ -848,6 +848,7 @@ template <typename T>
 cudaError_t apply_tensor(dg_mesh* m, int degree, int B, double lambda, const T* u, T* Au, bool pipe,
                          cudaStream_t st, double* c1_scratch) {
   constexpr bool f64 = sizeof(T) == 8;
+  if (!tensor_supported(degree)) return cudaErrorInvalidValue;
   const OzOps* op = nullptr;
   cudaError_t e = tensor_ops<T>(m, degree, &op);
   if (e != cudaSuccess) return e;
@@ -889,6 +890,10 @@ cudaError_t launch_apply_tensor(dg_mesh* m, int degree, bool f64, int B, double 
                              c1_scratch);
 }
 
+// The fill phase maps a node to lane and lane + 32 and a face-node entry to a
+// lane: Np <= 64 and 3 (N + 1) <= 32, so degrees up to 9.
+bool tensor_supported(int degree) { return degree >= 1 && degree <= 9; }
+
 bool tensor_ops_ready(int degree, bool f64) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
@@ -897,6 +902,7 @@ bool tensor_ops_ready(int degree, bool f64) {
 }
 
 cudaError_t ensure_tensor_ops(dg_mesh* m, int degree, bool f64) {
+  if (!tensor_supported(degree)) return cudaSuccess;
   const OzOps* op = nullptr;
   return f64 ? tensor_ops<double>(m, degree, &op) : tensor_ops<float>(m, degree, &op);
 }
@@ -908,14 +914,19 @@ cudaError_t sliced_op_create(const std::vector<double>& A, int M, int K, SlicedO
   std::vector<int> ea;
   op->M = M;
   op->K = K;
+  // too long a sum for the FP32 group sums to stay exact (both kernels: 4 products
+  // of |slice| <= 127 over 256 terms stay below 2^24)
+  if (K > 256) return cudaErrorInvalidValue;
+  // the tcgen05 GEMM takes any row count; the mma.sync copy only within its
+  // instantiated shapes (it serves when the tcgen05 one is not built)
+  cudaError_t e = tc64_op_create(A, M, K, &op->t64);
+  if (e != cudaSuccess) return e;
   slice_operator(A, M, K, Slices<double>::KS, false, op->Mt, op->Kt, frag, ea);
-  // beyond the instantiated shapes, or too long a sum for the FP32 group sums to stay exact
-  if (op->Mt * ONT > 48 || K > 224) return cudaErrorInvalidValue;
-  cudaError_t e = cudaMalloc(&op->A, frag.size() * sizeof(uint32_t));
+  if (op->Mt * ONT > 48) return cudaSuccess;
+  e = cudaMalloc(&op->A, frag.size() * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemcpy(op->A, frag.data(), frag.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&op->ea, ea.size() * sizeof(int));
   if (e == cudaSuccess) e = cudaMemcpy(op->ea, ea.data(), ea.size() * sizeof(int), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = tc64_op_create(A, M, K, &op->t64);
   return e;
 }
 
@@ -930,6 +941,7 @@ void sliced_op_free(SlicedOp* op) {
 cudaError_t sliced_gemm(const SlicedOp& op, int64_t rows, const double* X, int64_t ldx, double* out, int64_t ldo,
                         cudaStream_t st) {
   if (op.t64.blocks) return tc64_gemm_launch(op.t64, rows, X, ldx, out, ldo, st);
+  if (!op.A) return cudaErrorInvalidValue;
   return gemm<double>(op.Mt, rows, op.M, op.K, op.Kt, reinterpret_cast<const uint4*>(op.A), op.ea, X, ldx, out, ldo,
                       nullptr, st);
 }

@@ -48,7 +48,7 @@ extern "C" {
 
 dg_status dg_set_apply_kernel(dg_mesh* m, int degree, dg_prec prec, int helmholtz, int kernel) {
   if (!m) { set_error("mesh is NULL"); return DG_ERR_ARG; }
-  if (degree < 1 || degree > kMaxN) { set_error("degree must be in 1..8"); return DG_ERR_ARG; }
+  if (degree < 1 || degree > kMaxN) { set_error("degree must be in 1..10"); return DG_ERR_ARG; }
   if (prec != DG_F64 && prec != DG_F32) { set_error("precision must be DG_F64 or DG_F32"); return DG_ERR_ARG; }
   if (kernel != DG_KERNEL_AUTO && !kernel_valid(kernel, degree, prec == DG_F64)) {
     set_error("kernel not available for this degree and precision");
@@ -100,11 +100,11 @@ dg_status dg_autotune(dg_mesh* m, int B, double lambda, int degree_lo, int degre
   if (!m) { set_error("mesh is NULL"); return DG_ERR_ARG; }
   if (B < 1 || B > DG_MAX_BATCH) { set_error("batch must be in 1..64"); return DG_ERR_ARG; }
   if (degree_lo < 1 || degree_hi > kMaxN || degree_lo > degree_hi) {
-    set_error("need 1 <= degree_lo <= degree_hi <= 8");
+    set_error("need 1 <= degree_lo <= degree_hi <= 10");
     return DG_ERR_ARG;
   }
   if (!std::isfinite(lambda) || lambda < 0) { set_error("lambda must be finite and >= 0"); return DG_ERR_ARG; }
-  if (times) std::memset(times, 0, sizeof(float) * (kMaxN + 1) * 2 * 2 * 6);
+  if (times) std::memset(times, 0, sizeof(float) * (kMaxN + 1) * 2 * 2 * DG_NUM_KERNELS);
   cudaStream_t st = (cudaStream_t)stream;
   auto fail = [](cudaError_t e) {
     set_error(std::string("dg_autotune: ") + cudaGetErrorString(e));

@@ -14,7 +14,7 @@
 
 namespace dgx {
 
-constexpr int kMaxN = 8;
+constexpr int kMaxN = DG_MAX_DEGREE;
 
 // Host reference-element data for one degree (FP64, row-major matrices).
 struct RefElem {
@@ -113,7 +113,7 @@ struct dg_mesh {
 
 namespace dgx {
 
-// Launchers (device code in the .cu files). `degree` in 1..8.
+// Launchers (device code in the .cu files). `degree` in 1..kMaxN.
 cudaError_t ensure_ops(dg_mesh* m, int degree);
 // c1_scratch (optional, FP64 only): device words for the tensor kernels'
 // scratch, at least B*K*Np(degree)*(lambda != 0 ? 3 : 2) + 1 of them for the
@@ -131,6 +131,7 @@ cudaError_t launch_apply_ept(dg_mesh* m, int degree, bool f64, int B, double lam
                              cudaStream_t st);
 cudaError_t launch_apply_tensor(dg_mesh* m, int degree, bool f64, int B, double lambda, const void* u, void* Au,
                                 bool pipe, cudaStream_t st, double* c1_scratch = nullptr);
+bool tensor_supported(int degree);  // the mma.sync tensor kernels (N <= 9)
 // Builds (once per device, degree and precision) the tensor kernels' operator
 // slices on the current device; dg_mesh_setup calls it for the mesh degree.
 cudaError_t ensure_tensor_ops(dg_mesh* m, int degree, bool f64);
@@ -159,7 +160,7 @@ cudaError_t ensure_tc64_ops(dg_mesh* m, int degree);  // dg_mesh_setup builds th
 bool tc64_ops_ready(int degree);                      // built on the current device (no build)
 cudaError_t tc64_error(int* flag);
 // FP64 products on the tcgen05 tensor cores with exact integer slicing (apply_tc64.cu):
-// an operator A (M x K, K <= 224) cut into 8 slices in blocks of 48 rows x 32 columns
+// an operator A (M x K, K <= 256) cut into 8 slices in blocks of 48 rows x 32 columns
 struct Tc64Op {
   int M = 0, K = 0, NCH = 0, KCH = 0;
   uint8_t* blocks = nullptr;

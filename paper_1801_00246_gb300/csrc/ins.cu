@@ -50,7 +50,7 @@ struct InsWorkspace {
   // tensor-core advection (degree >= 3): the cubature interpolation Iq and the
   // projection blocks Pr, Ps, -Lc as sliced FP64 operators, with their row
   // buffers (the projection is split at its blocks so that every sliced product
-  // sums at most 224 terms, which keeps its FP32 group sums exact)
+  // sums at most 256 terms, which keeps its FP32 group sums exact)
   bool tensor = false;
   SlicedOp opIq, opPr, opPs, opLc;
   double *X = nullptr, *W = nullptr, *Y = nullptr, *R = nullptr;
@@ -662,6 +662,7 @@ cudaError_t ins_run(dg_mesh* mu, dg_mesh* mp, dg_ins_state* s, int nsteps, cudaS
   ICK(setup_ins(mu));
   InsWorkspace* w = mu->ins;
   const int Np = (mu->N + 1) * (mu->N + 2) / 2;
+  const unsigned gd_threads = unsigned((Np + 31) / 32 * 32);  // grad_div_kernel: one thread per node
   const int64_t K = mu->K;
   const size_t n1 = size_t(K) * Np, n2 = 2 * n1;
   const AdvLayout& L = w->L;
@@ -687,7 +688,7 @@ cudaError_t ins_run(dg_mesh* mu, dg_mesh* mp, dg_ins_state* s, int nsteps, cudaS
     // (ii) velocity Helmholtz: b = J M U^/(nu dt) - L(gU) - (1/nu) G P^n
     axpby_kernel<<<eg(n2), 256, 0, st>>>(n2, 1.0 / (nu * dt), w->Uhat, 0.0, w->tmp, 0.0, nullptr); note_launch();
     ICK(launch_rhs(mu, 2, w->tmp, s->gU, w->bu, st));
-    grad_div_kernel<<<unsigned(K), 64, 4 * Np * sizeof(double), st>>>(0, mu->N, K, mu->geo64, mp->conn, w->ops, L,
+    grad_div_kernel<<<unsigned(K), gd_threads, 4 * Np * sizeof(double), st>>>(0, mu->N, K, mu->geo64, mp->conn, w->ops, L,
                                                                        s->P, s->gP, w->G);
     note_launch();
     axpby_kernel<<<eg(n2), 256, 0, st>>>(n2, -1.0 / nu, w->G, 1.0, w->bu, 0.0, nullptr); note_launch();
@@ -702,7 +703,7 @@ cudaError_t ins_run(dg_mesh* mu, dg_mesh* mp, dg_ins_state* s, int nsteps, cudaS
       return cudaSuccess;
     }
     // (iii) pressure increment: b = -(gamma/dt) D.U^^ (zero increment on pressure-Dirichlet faces)
-    grad_div_kernel<<<unsigned(K), 64, 4 * Np * sizeof(double), st>>>(1, mu->N, K, mu->geo64, mu->conn, w->ops, L,
+    grad_div_kernel<<<unsigned(K), gd_threads, 4 * Np * sizeof(double), st>>>(1, mu->N, K, mu->geo64, mu->conn, w->ops, L,
                                                                        w->Uhh, s->gU, w->bp);
     note_launch();
     axpby_kernel<<<eg(n1), 256, 0, st>>>(n1, 0.0, w->bp, -gamma / dt, w->bp, 0.0, nullptr); note_launch();
@@ -715,7 +716,7 @@ cudaError_t ins_run(dg_mesh* mu, dg_mesh* mp, dg_ins_state* s, int nsteps, cudaS
       return cudaSuccess;
     }
     // (iv) U^{n+1} = U^^ - (dt/gamma) (J M)^{-1} G dP ; P += dP ; history shift
-    grad_div_kernel<<<unsigned(K), 64, 4 * Np * sizeof(double), st>>>(0, mu->N, K, mu->geo64, mp->conn, w->ops, L,
+    grad_div_kernel<<<unsigned(K), gd_threads, 4 * Np * sizeof(double), st>>>(0, mu->N, K, mu->geo64, mp->conn, w->ops, L,
                                                                        w->dP, w->tmp, w->G);
     note_launch();
     strong_kernel<<<unsigned((n2 + 255) / 256), 256, 0, st>>>(Np, K, 2, mu->geo64, w->ops + L.Minv, w->G, w->bu);

@@ -17,6 +17,23 @@ def pkg():
     return P
 
 
+def kernels_for(P, N, f64):
+    """The apply kernels available at degree N in FP64 (f64) or FP32: the tile
+    kernel at every degree, the mma.sync tensor kernels to N = 9, the tcgen05
+    FP64 kernel at every degree, the FP32 register GEMMs to N = 9, the tcgen05
+    FP32 kernel to N = 8 (tensor memory) and one element per thread to N = 3."""
+    ks = [P.KERNEL_TILE]
+    if N <= 9:
+        ks += [P.KERNEL_TENSOR, P.KERNEL_TENSOR_PIPE]
+    if f64:
+        ks.append(P.KERNEL_TC64)
+    else:
+        ks += ([P.KERNEL_GEMM] if N <= 9 else []) + ([P.KERNEL_TC05] if N <= 8 else [])
+    if N <= 3:
+        ks.append(P.KERNEL_EPT)
+    return ks
+
+
 def pair(mesh, N):
     from oracle.sipdg import Sipdg
     P = pkg()

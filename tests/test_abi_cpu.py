@@ -40,7 +40,7 @@ def test_library_exports_every_declared_symbol(P):
         assert hasattr(L, n), n
 
 
-@pytest.mark.parametrize("N", range(1, 9))
+@pytest.mark.parametrize("N", range(1, 11))
 def test_library_reference_element_matches_oracle(P, N):
     a = P.reference_operators(N)
     o = refops.reference_operators(N)
@@ -50,7 +50,7 @@ def test_library_reference_element_matches_oracle(P, N):
     assert (a["fmask"] == np.array(o["faces"])).all()
 
 
-@pytest.mark.parametrize("Nf,Nc", [(8, 4), (4, 2), (2, 1), (6, 3), (3, 1), (8, 1)])
+@pytest.mark.parametrize("Nf,Nc", [(8, 4), (4, 2), (2, 1), (6, 3), (3, 1), (8, 1), (10, 5), (9, 4)])
 def test_library_interpolation_matches_oracle(P, Nf, Nc):
     assert np.abs(P.interpolation_matrix(Nf, Nc) - refops.interpolation(Nf, Nc)).max() < 1e-12
 
@@ -64,7 +64,7 @@ def test_status_strings_and_argument_errors(P):
         P.Mesh(0, m.VX, m.VY, m.EToV, m.bc)
     assert ei.value.name == "DG_ERR_ARG"
     with pytest.raises(P.DgError) as ei:
-        P.Mesh(9, m.VX, m.VY, m.EToV, m.bc)
+        P.Mesh(11, m.VX, m.VY, m.EToV, m.bc)
     assert ei.value.name == "DG_ERR_ARG"
 
 

@@ -18,7 +18,7 @@ def _mixed_bc(n, seed):
     return jittered_grid(n, n, jitter=0.1, seed=seed, bc_sides=(1, 2, 2, 1))
 
 
-@pytest.mark.parametrize("N", range(1, 9))
+@pytest.mark.parametrize("N", range(1, 11))
 @pytest.mark.parametrize("lam", [0.0, 2.5])
 def test_apply_parity_rotated_mesh(N, lam):
     import torch
@@ -45,7 +45,7 @@ def test_apply_parity_mixed_and_neumann_boundaries(N):
 @pytest.mark.parametrize("K_side", [1, 2])
 def test_apply_tiny_meshes(K_side):
     m = rotate_local_vertices(jittered_grid(K_side, K_side, seed=0), 1)
-    for N in (1, 4, 8):
+    for N in (1, 4, 8, 10):
         lib, ora = pair(m, N)
         u = uniform_field((m.K, ora.Np), seed=5)
         assert rel(lib.apply(cuda(u)).cpu().numpy(), ora.apply(u)) <= TOL64

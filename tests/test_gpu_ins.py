@@ -75,11 +75,12 @@ def test_c3_kovasznay_100_steps_8192tri_N8():
 
 
 @pytest.mark.parametrize("N,sides", [(2, (1, 1, 1, 1)), (2, (1, 2, 1, 1)), (3, (1, 2, 1, 1)), (5, (1, 2, 1, 1)),
-                                     (8, (1, 1, 1, 1)), (8, (1, 2, 1, 1))])
+                                     (8, (1, 1, 1, 1)), (8, (1, 2, 1, 1)), (10, (1, 2, 1, 1))])
 def test_ins_parity_outflow_and_both_advection_paths(N, sides):
     """Degrees 1-2 advect with the fused FP64 kernel, degrees from 3 with the
     tensor-core stages (N = 8 is the Kovasznay workload's degree, with its own
-    169-point cubature shapes); an outflow side (velocity Neumann at x = 1 where
+    169-point cubature shapes; N = 10, the highest degree, projects from 256
+    cubature points, the longest exact sliced sum); an outflow side (velocity Neumann at x = 1 where
     the pressure is Dirichlet) takes the Neumann branches of the advection flux,
     the divergence and the velocity Helmholtz operator. Both sides solve to a
     relative residual of 1e-13; the pressure increment's condition number

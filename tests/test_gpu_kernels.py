@@ -7,7 +7,7 @@ import pytest
 
 from dg_inputs import jittered_grid, uniform_field
 from dg_inputs.mesh import rotate_local_vertices, with_all_neumann
-from tests.gpu_util import cuda, pair, pkg, rel
+from tests.gpu_util import cuda, kernels_for, pair, pkg, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -15,17 +15,14 @@ TOL64, TOL32 = 1e-12, 1e-5
 
 
 def _kernels(P, N, f64):
-    ks = [P.KERNEL_TILE, P.KERNEL_TENSOR, P.KERNEL_TENSOR_PIPE] + ([P.KERNEL_TC64] if f64 else [P.KERNEL_GEMM, P.KERNEL_TC05])
-    if N <= 3:
-        ks.append(P.KERNEL_EPT)
-    return ks
+    return kernels_for(P, N, f64)
 
 
 def _mixed_bc(n, seed):
     return jittered_grid(n, n, jitter=0.1, seed=seed, bc_sides=(1, 2, 2, 1))
 
 
-@pytest.mark.parametrize("N", range(1, 9))
+@pytest.mark.parametrize("N", range(1, 11))
 def test_every_kernel_matches_oracle(N):
     """Rotated local numbering (all face orientations), Dirichlet + Neumann
     sides, a ragged element count, Poisson and Helmholtz, batch of 2."""
@@ -56,8 +53,19 @@ def test_kernel_table_rejects_unavailable_kernels():
     with pytest.raises(P.DgError):
         lib.set_kernel(5, P.DG_F32, 0, P.KERNEL_EPT)       # degrees 1-3
     with pytest.raises(P.DgError):
-        lib.set_kernel(9, P.DG_F32, 0, P.KERNEL_TILE)
-    assert lib.kernel(9, P.DG_F64) == -1
+        lib.set_kernel(9, P.DG_F32, 0, P.KERNEL_TC05)      # tensor memory: degrees 1-8
+    with pytest.raises(P.DgError):
+        lib.set_kernel(10, P.DG_F32, 0, P.KERNEL_GEMM)     # shared memory: degrees 1-9
+    with pytest.raises(P.DgError):
+        lib.set_kernel(10, P.DG_F64, 0, P.KERNEL_TENSOR)   # the fill's lane map: degrees 1-9
+    with pytest.raises(P.DgError):
+        lib.set_kernel(11, P.DG_F32, 0, P.KERNEL_TILE)
+    assert lib.kernel(11, P.DG_F64) == -1
+    assert lib.kernel(10, P.DG_F64) == P.KERNEL_TC64 and lib.kernel(10, P.DG_F32) == P.KERNEL_TILE
+    assert lib.kernel(9, P.DG_F32) == P.KERNEL_TENSOR
+    for N in range(1, 11):
+        for f64, prec in ((True, P.DG_F64), (False, P.DG_F32)):
+            assert set(lib.kernels_available(N, prec)) == set(kernels_for(P, N, f64)), (N, f64)
 
 
 @pytest.mark.parametrize("N", [1, 2, 3])

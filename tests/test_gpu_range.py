@@ -12,7 +12,7 @@ import pytest
 
 from dg_inputs import jittered_grid, uniform_field
 from dg_inputs.mesh import rotate_local_vertices
-from tests.gpu_util import abs_bound, cuda, max_entry_err, pair, pkg, rel
+from tests.gpu_util import abs_bound, cuda, kernels_for, max_entry_err, pair, pkg, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -21,10 +21,7 @@ BOUND64, BOUND32 = 1e-12, 1e-5
 
 
 def _kernels(P, N, f64):
-    ks = [P.KERNEL_TILE, P.KERNEL_TENSOR, P.KERNEL_TENSOR_PIPE] + ([P.KERNEL_TC64] if f64 else [P.KERNEL_GEMM, P.KERNEL_TC05])
-    if N <= 3:
-        ks.append(P.KERNEL_EPT)
-    return ks
+    return kernels_for(P, N, f64)
 
 
 def _scaled_field(K, Np, seed, exps):
@@ -50,7 +47,7 @@ def _check_all_kernels(lib, ora, u, f64, N, lam):
     return out
 
 
-@pytest.mark.parametrize("N", range(1, 9))
+@pytest.mark.parametrize("N", range(1, 11))
 def test_entrywise_bound_every_kernel(N):
     m = rotate_local_vertices(jittered_grid(5, 6, jitter=0.1, seed=7, bc_sides=(1, 2, 1, 2)), N)
     lib, ora = pair(m, N)
@@ -61,9 +58,18 @@ def test_entrywise_bound_every_kernel(N):
             assert max(errs.values()) <= (BOUND64 if f64 else BOUND32), (N, lam, f64, errs)
 
 
-@pytest.mark.parametrize("N", [3, 5, 8])
+@pytest.mark.parametrize("N", [3, 5, 8, 10])
 def test_fp64_neighbours_2_to_the_60_apart_and_zero_elements(N):
-    """Element magnitudes 2^-60, 1 or 2^60 at random, every tenth element zero."""
+    """Element magnitudes 2^-60, 1 or 2^60 at random, every tenth element zero.
+
+    Next to an element 2^60 larger, a node's own |A||u| can sit a few hundred
+    times below the terms its value is summed from (the consistency, symmetry
+    and penalty terms of the huge neighbour cancel there). The tile kernel
+    rounds those terms in FP64 (53 bits); the tcgen05 FP64 kernel carries them
+    in float-float (48 bits), so its entry error is up to ~32x larger: measured
+    3.1e-13 at N = 8 and 2.3e-12 at one node at N = 10 (where the penalty and
+    the derivative rows are largest), against 1.6e-13 for the tile kernel."""
+    P = pkg()
     m = rotate_local_vertices(jittered_grid(6, 6, jitter=0.1, seed=3), 2)
     lib, ora = pair(m, N)
     rng = np.random.default_rng(N)
@@ -72,10 +78,12 @@ def test_fp64_neighbours_2_to_the_60_apart_and_zero_elements(N):
     u[::10] = 0.0
     for lam in (0.0, 1.5):
         errs = _check_all_kernels(lib, ora, u, True, N, lam)
-        assert max(errs.values()) <= BOUND64, (lam, errs)
+        for k, err in errs.items():
+            bound = 4 * BOUND64 if (k == P.KERNEL_TC64 and N >= 10) else BOUND64
+            assert err <= bound, (lam, k, errs)
 
 
-@pytest.mark.parametrize("N", [4, 8])
+@pytest.mark.parametrize("N", [4, 8, 10])
 def test_fp64_near_the_documented_magnitude_limits(N):
     """One element near 1e250 and one near 1e-250 among O(1) elements."""
     m = rotate_local_vertices(jittered_grid(5, 5, jitter=0.1, seed=5), 1)
@@ -90,7 +98,7 @@ def test_fp64_near_the_documented_magnitude_limits(N):
     assert np.isfinite(list(errs.values())).all()
 
 
-@pytest.mark.parametrize("N", [2, 5, 8])
+@pytest.mark.parametrize("N", [2, 5, 8, 9])
 def test_fp32_neighbours_2_to_the_20_apart_and_zero_elements(N):
     m = rotate_local_vertices(jittered_grid(6, 5, jitter=0.1, seed=4), 3)
     lib, ora = pair(m, N)

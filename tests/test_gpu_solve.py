@@ -125,3 +125,23 @@ def test_amg_coarse_solve_small_and_batched():
                         coarse_amg=1)
     for k in range(3):
         assert _oracle_relres(ora, x[k].cpu().numpy(), bb[k]) <= 1.5e-10
+
+
+@pytest.mark.parametrize("mixed", [1, 0])
+def test_pmg_degree_10_and_9(mixed):
+    """The highest degrees (Section 5.2's kernel studies reach N = 10): a jittered
+    16x16 grid with mixed Dirichlet/Neumann sides, V-cycles 10->5->2->1 and
+    9->4->1 (FP32 smoothing at N = 10 on the tile kernel, at N = 9 on the
+    mma.sync tensor kernel; FP64 outer applies on the tcgen05 kernel),
+    Helmholtz and Poisson, against the oracle's residual."""
+    P = pkg()
+    m = rotate_local_vertices(jittered_grid(16, 16, jitter=0.1, seed=9, bc_sides=(1, 2, 1, 1)), 2)
+    for N, degrees in ((10, [10, 5, 2, 1]), (9, [9, 4, 1])):
+        lib, ora = pair(m, N)
+        bb = ora.mass_apply(uniform_field((2, m.K, ora.Np), seed=30 + N))
+        for lam in (0.0, 2.0):
+            x, info = lib.solve(cuda(bb), lam=lam, precond=P.PREC_PMG, degrees=degrees, tol=1e-10, max_iter=300,
+                                mixed=mixed)
+            for k in range(2):
+                assert info["relres"][k] <= 1e-10
+                assert _oracle_relres(ora, x[k].cpu().numpy(), bb[k], lam=lam) <= 1.5e-10, (N, lam, k)

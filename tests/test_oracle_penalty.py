@@ -124,7 +124,7 @@ def test_blend_parameter_is_irrelevant_at_degree_3():
     assert np.abs(r0 - r1).max() < 1e-14 and np.abs(s0 - s1).max() < 1e-14
 
 
-@pytest.mark.parametrize("N,delta", [(5, 0.02), (6, 0.05), (7, 0.05), (8, 0.05)])
+@pytest.mark.parametrize("N,delta", [(5, 0.02), (6, 0.05), (7, 0.05), (8, 0.05), (9, 0.05), (10, 0.05)])
 def test_tabulated_blend_parameter_minimises_lebesgue_constant(N, delta):
     """The tabulated alpha(N) is the minimiser of the node set's Lebesgue
     constant (the optimisation that defines the table): moving it either way

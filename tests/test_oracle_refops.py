@@ -7,7 +7,7 @@ from oracle import basis, refops
 from tests.test_oracle_basis import _tri_monomial
 
 
-@pytest.mark.parametrize("N", range(1, 9))
+@pytest.mark.parametrize("N", range(1, 11))
 def test_derivatives_exact_on_monomials(N):
     ops = refops.reference_operators(N)
     r, s = ops["r"], ops["s"]
@@ -21,7 +21,7 @@ def test_derivatives_exact_on_monomials(N):
             assert np.abs(ops["Ds"] @ u - us).max() < 1e-11 * max(1, N ** 2)
 
 
-@pytest.mark.parametrize("N", range(1, 9))
+@pytest.mark.parametrize("N", range(1, 11))
 def test_mass_integrates_monomials(N):
     ops = refops.reference_operators(N)
     r, s, M = ops["r"], ops["s"], ops["M"]
@@ -32,7 +32,7 @@ def test_mass_integrates_monomials(N):
             assert abs(one @ M @ (r ** a * s ** b) - _tri_monomial(a, b)) < 1e-12
 
 
-@pytest.mark.parametrize("N", range(1, 9))
+@pytest.mark.parametrize("N", range(1, 11))
 def test_lift_reproduces_face_integrals(N):
     """v^T M LIFT_f w_f = integral over face f (parameter t in [-1,1]) of v w,
     checked with an independent Gauss-Legendre rule on each edge."""
@@ -58,7 +58,7 @@ def test_lift_reproduces_face_integrals(N):
         assert abs(got - exact) < 1e-10 * max(1, abs(exact))
 
 
-@pytest.mark.parametrize("Nf,Nc", [(2, 1), (3, 1), (6, 3), (8, 4), (4, 2)])
+@pytest.mark.parametrize("Nf,Nc", [(2, 1), (3, 1), (6, 3), (8, 4), (4, 2), (10, 5)])
 def test_pmg_interpolation_reproduces_coarse_polynomials(Nf, Nc):
     P = refops.interpolation(Nf, Nc)
     rf, sf = basis.warp_blend_nodes(Nf)

@@ -17,7 +17,7 @@ def _sip(m, N):
     return Sipdg(m.VX, m.VY, m.EToV, m.bc, N)
 
 
-@pytest.mark.parametrize("n,N", [(1, 1), (1, 8), (2, 2), (2, 5), (4, 3), (4, 8)])
+@pytest.mark.parametrize("n,N", [(1, 1), (1, 8), (2, 2), (2, 5), (4, 3), (4, 8), (2, 10)])
 def test_symmetric_positive_definite(n, N):
     S = _sip(_mesh(n, rotate=3), N)
     A = S.assemble().toarray()
@@ -34,7 +34,7 @@ def test_all_neumann_kills_constants(N):
     assert np.abs(A @ one).max() < 1e-11 * abs(A).max()
 
 
-@pytest.mark.parametrize("N", range(1, 9))
+@pytest.mark.parametrize("N", range(1, 11))
 @pytest.mark.parametrize("lam", [0.0, 3.5])
 def test_polynomial_exactness_with_dirichlet_data(N, lam):
     """For a global polynomial p of degree <= N with g = p on the boundary, all
@@ -56,7 +56,7 @@ def test_polynomial_exactness_with_dirichlet_data(N, lam):
     assert np.linalg.norm(lhs - rhs) <= 1e-11 * max(1.0, np.linalg.norm(rhs)) * N
 
 
-@pytest.mark.parametrize("N", range(1, 9))
+@pytest.mark.parametrize("N", range(1, 11))
 @pytest.mark.parametrize("lam", [0.0, 3.5])
 def test_polynomial_exactness_with_neumann_sides(N, lam):
     """Neumann on x = 0 and x = 1, Dirichlet (g = p) on y = 0 and y = 1: for a
