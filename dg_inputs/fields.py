@@ -50,3 +50,16 @@ def kovasznay(Re=40.0):
     v = lambda x, y: lam / (2 * np.pi) * np.exp(lam * x) * np.sin(2 * np.pi * y)
     p = lambda x, y: 0.5 * (1.0 - np.exp(2 * lam * x))
     return 1.0 / Re, u, v, p
+
+
+def taylor_vortex(nu):
+    """The decaying Taylor-Green vortex, a time-dependent closed-form
+    Navier-Stokes solution: F(t) = exp(-2 pi^2 nu t),
+    u = -cos(pi x) sin(pi y) F, v = sin(pi x) cos(pi y) F,
+    p = -(cos 2 pi x + cos 2 pi y) F^2 / 4.
+    Returns (u, v, p), callables of (x, y, t)."""
+    F = lambda t: np.exp(-2.0 * np.pi ** 2 * nu * t)
+    u = lambda x, y, t: -np.cos(np.pi * x) * np.sin(np.pi * y) * F(t)
+    v = lambda x, y, t: np.sin(np.pi * x) * np.cos(np.pi * y) * F(t)
+    p = lambda x, y, t: -0.25 * (np.cos(2 * np.pi * x) + np.cos(2 * np.pi * y)) * F(t) ** 2
+    return u, v, p

@@ -249,6 +249,12 @@ typedef struct {
   int vel_iters[2];       /* out: iterations of the last step's velocity solves */
   int pr_iters;           /* out: iterations of the last step's pressure solve */
   float ms;               /* out: device time of the last call */
+  /* Time-dependent boundary data (optional; NULL = steady data in gU, gP).
+   * With gU_hist set, gU and gP are the data at t^{n+1} = (step + 1) dt, and a
+   * call advances exactly one step (nsteps = 1); the caller supplies each
+   * step's data. */
+  const double* gU_hist;  /* [2][2][K][Np]: velocity data at t^n, then at t^{n-1} (unused when step == 0) */
+  const double* gP_n;     /* [K][Np]: pressure data at t^n (required with gU_hist) */
 } dg_ins_state;
 
 /* Advance nsteps macro steps of the algebraic splitting scheme with
@@ -266,9 +272,14 @@ typedef struct {
  * velocity and the pressure-increment boundary tags. G uses central fluxes
  * with p* = gP on pressure-Dirichlet faces and p* = p- on the others; D uses
  * u* = gU on velocity-Dirichlet faces and u* = u- on velocity-Neumann faces
- * (Eq. INS_SD_4_1, INS_SD_4_2). Boundary data are steady; the pressure
- * increment is zero on pressure-Dirichlet faces. Workspace is allocated on the
- * first call and kept with mesh_u. Returns the status of a failing solve. */
+ * (Eq. INS_SD_4_1, INS_SD_4_2). With steady boundary data (gU_hist NULL) the
+ * pressure increment is zero on pressure-Dirichlet faces. With time-dependent
+ * data the advection stages at time t take the velocity data interpolated in
+ * time through t^{n-1}, t^n, t^{n+1} (quadratic; linear between t^n and
+ * t^{n+1} at step 0), the Helmholtz solve and D take gU at t^{n+1}, G P^n takes
+ * gP_n, and the increment takes gP - gP_n on pressure-Dirichlet faces.
+ * Workspace is allocated on the first call and kept with mesh_u. Returns the
+ * status of a failing solve. */
 dg_status dg_ins_step(dg_mesh* mesh_u, dg_mesh* mesh_p, dg_ins_state* state, int nsteps, void* stream);
 
 /* Jacobi-preconditioned CG on A(lambda) x = b that allocates nothing.

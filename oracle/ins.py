@@ -24,10 +24,15 @@ Eq. INS_SD_3 has the opposite, anti-dissipative sign).
 Readings where the paper is silent or inconsistent:
   * BDF2 beta_1 = -1/2 (the printed +1/2 violates sum beta = gamma);
     start-up step: BDF1/EXT1 (gamma = 1, beta_0 = 1, Ubar = U^0);
-  * boundary data are steady (the Kovasznay flow): velocity-Dirichlet faces
-    take u+ = g (advection), u* = g (divergence); pressure-Dirichlet faces take
-    p* = g_p (gradient), and the pressure increment is zero there; on
-    pressure-Neumann faces p* = p-; on velocity-Neumann faces u* = u-;
+  * boundary data: velocity-Dirichlet faces take u+ = g (advection), u* = g
+    (divergence); pressure-Dirichlet faces take p* = g_p (gradient); on
+    pressure-Neumann faces p* = p-; on velocity-Neumann faces u* = u-. Steady
+    data (the Kovasznay flow) make the pressure increment zero on
+    pressure-Dirichlet faces. Time-dependent data g(t), g_p(t) (the Taylor
+    vortex of Section 4.1) enter at the times each stage needs them: the
+    advection stage at time t uses g(t), the Helmholtz solve and the
+    divergence use g(t^{n+1}), G P^n uses g_p(t^n), and the increment takes
+    g_p(t^{n+1}) - g_p(t^n) on pressure-Dirichlet faces;
   * the cubature is the collapsed Gauss rule with ceil((3N+1)/2) points per
     direction on the triangle and Gauss-Legendre with as many points per face
     (exact for the degree-3N advection integrands);
@@ -224,10 +229,14 @@ class InsOracle:
     def step(self, st, dt, nu, Ns, gU, gP, solve=None):
         """One time step of Eq. INS_TD_3 (steps (i)-(iv) of the module header)
         with the subcycled advection of Section 2.3; st = dict(U, Uold, P, n).
-        Returns the new state and the intermediate fields (U^, U^^, dP) for
-        inspection."""
+        gU, gP: steady nodal data, or callables of t returning them
+        (time-dependent data, t^n = n dt). Returns the new state and the
+        intermediate fields (U^, U^^, dP) for inspection."""
         U, Uold, P, n = st["U"], st["Uold"], st["P"], st["n"]
         t = n * dt
+        unsteady = callable(gU)
+        gUt = gU if unsteady else (lambda tt: gU)
+        gPt = gP if unsteady else (lambda tt: gP)
         dts = dt / Ns
         if n == 0:
             gamma, betas = 1.0, [1.0]
@@ -239,19 +248,23 @@ class InsOracle:
             starts = [(U, t, Ns), (Uold, t - dt, 2 * Ns)]
         Uhat = np.zeros_like(U)
         for beta, (U0, t0, nsub) in zip(betas, starts):
-            rhs = lambda tt, y: self.advection(ubar(tt), y, gU)
+            rhs = lambda tt, y: self.advection(ubar(tt), y, gUt(tt))
             Uhat += beta * lserk_integrate(rhs, U0, t0, dts, nsub)
         lam = gamma / (nu * dt)
         Au = self.Su.assemble(lam).tocsc()
-        G = self.weak_grad(P, gP)
+        G = self.weak_grad(P, gPt(t))
+        g1 = gUt(t + dt)
         Uhh = np.zeros_like(U)
         for c in range(2):
-            b = self.Su.mass_apply(Uhat[c]) / (nu * dt) - G[c] / nu - self.Su.dirichlet_lift(gU[c])
+            b = self.Su.mass_apply(Uhat[c]) / (nu * dt) - G[c] / nu - self.Su.dirichlet_lift(g1[c])
             Uhh[c] = (solve or _direct)(Au, b)
         Ap = self.Sp.assemble(0.0).tocsc()
-        bp = -(gamma / dt) * self.weak_div(Uhh, gU)
+        bp = -(gamma / dt) * self.weak_div(Uhh, g1)
+        gdP = gPt(t + dt) - gPt(t) if unsteady else np.zeros_like(P)
+        if unsteady:
+            bp = bp - self.Sp.dirichlet_lift(gdP)
         dP = (solve or _direct)(Ap, bp)
-        Gd = self.to_strong(self.weak_grad(dP, np.zeros_like(dP)))
+        Gd = self.to_strong(self.weak_grad(dP, gdP))
         Unew = Uhh - (dt / gamma) * Gd
         new = dict(U=Unew, Uold=U, P=P + dP, n=n + 1)
         return new, dict(Uhat=Uhat, Uhh=Uhh, dP=dP)

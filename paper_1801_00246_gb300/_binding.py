@@ -43,7 +43,7 @@ class InsState(ctypes.Structure):
                 ("U", ctypes.c_void_p), ("Uold", ctypes.c_void_p), ("P", ctypes.c_void_p),
                 ("gU", ctypes.c_void_p), ("gP", ctypes.c_void_p), ("vel_opts", SolverOpts),
                 ("pr_opts", SolverOpts), ("vel_iters", ctypes.c_int * 2), ("pr_iters", ctypes.c_int),
-                ("ms", ctypes.c_float)]
+                ("ms", ctypes.c_float), ("gU_hist", ctypes.c_void_p), ("gP_n", ctypes.c_void_p)]
 
 
 _lib = None
@@ -295,26 +295,51 @@ class Mesh:
 class InsStepper:
     """Semi-implicit INS time stepper (dg_ins_step) on a velocity-tagged and a
     pressure-tagged mesh of the same triangulation. U, Uold: float64 CUDA
-    [2][K][Np]; P: [K][Np]; gU, gP: steady boundary data as nodal fields."""
+    [2][K][Np]; P: [K][Np]; gU, gP: steady boundary data as nodal fields, or
+    with bc given, time-dependent data: bc(t) -> (gU(t), gP(t)) as CUDA tensors
+    of those shapes, sampled at t^{n+1}, t^n and t^{n-1} each step (t^n = n dt)."""
 
-    def __init__(self, mesh_u, mesh_p, nu, dt, Ns, U, P, gU, gP, vel_opts=None, pr_opts=None, Uold=None):
+    def __init__(self, mesh_u, mesh_p, nu, dt, Ns, U, P, gU=None, gP=None, vel_opts=None, pr_opts=None, Uold=None,
+                 bc=None):
         import torch
         self.mesh_u, self.mesh_p = mesh_u, mesh_p
         self.U = U.contiguous()
         self.Uold = (Uold if Uold is not None else U.clone()).contiguous()
         self.P = P.contiguous()
-        self.gU = gU.contiguous()
-        self.gP = gP.contiguous()
+        self.bc = bc
+        if bc is not None:
+            g1, p1 = bc(0.0)
+            self.gU, self.gP = torch.empty_like(g1).contiguous(), torch.empty_like(p1).contiguous()
+            self.gU_hist = torch.empty((2,) + tuple(g1.shape), dtype=g1.dtype, device=g1.device)
+            self.gP_n = torch.empty_like(p1).contiguous()
+        else:
+            self.gU = gU.contiguous()
+            self.gP = gP.contiguous()
         self.st = InsState()
         self.st.nu, self.st.dt, self.st.Ns, self.st.step = float(nu), float(dt), int(Ns), 0
         for name in ("U", "Uold", "P", "gU", "gP"):
             setattr(self.st, name, getattr(self, name).data_ptr())
+        if bc is not None:
+            self.st.gU_hist, self.st.gP_n = self.gU_hist.data_ptr(), self.gP_n.data_ptr()
         self.st.vel_opts = vel_opts if vel_opts is not None else default_opts(precond=PREC_INVMASS, tol=1e-10)
         self.st.pr_opts = pr_opts if pr_opts is not None else default_opts(precond=PREC_JACOBI, tol=1e-10,
                                                                            max_iter=20000)
         del torch
 
     def step(self, n=1):
-        _check(lib().dg_ins_step(self.mesh_u._h, self.mesh_p._h, ctypes.byref(self.st), int(n), _stream()))
-        return dict(step=self.st.step, vel_iters=list(self.st.vel_iters), pr_iters=self.st.pr_iters,
-                    ms=self.st.ms)
+        if self.bc is None:
+            _check(lib().dg_ins_step(self.mesh_u._h, self.mesh_p._h, ctypes.byref(self.st), int(n), _stream()))
+            return dict(step=self.st.step, vel_iters=list(self.st.vel_iters), pr_iters=self.st.pr_iters,
+                        ms=self.st.ms)
+        ms = 0.0
+        for _ in range(int(n)):
+            k, dt = self.st.step, self.st.dt
+            for dst, t in ((self.gU_hist[0], k * dt), (self.gU_hist[1], (k - 1) * dt)):
+                dst.copy_(self.bc(t)[0])
+            self.gP_n.copy_(self.bc(k * dt)[1])
+            g1, p1 = self.bc((k + 1) * dt)
+            self.gU.copy_(g1)
+            self.gP.copy_(p1)
+            _check(lib().dg_ins_step(self.mesh_u._h, self.mesh_p._h, ctypes.byref(self.st), 1, _stream()))
+            ms += self.st.ms
+        return dict(step=self.st.step, vel_iters=list(self.st.vel_iters), pr_iters=self.st.pr_iters, ms=ms)

@@ -56,6 +56,7 @@ struct InsWorkspace {
   double *X = nullptr, *W = nullptr, *Y = nullptr, *R = nullptr;
   double *Ut0 = nullptr, *Ut1 = nullptr, *res = nullptr, *Uhat = nullptr, *Uhh = nullptr, *bu = nullptr,
          *G = nullptr, *bp = nullptr, *dP = nullptr, *tmp = nullptr;
+  double *gts = nullptr, *zero = nullptr;  // time-dependent data: velocity data at a stage time; zeros
   std::vector<void*> allocs;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
@@ -422,10 +423,11 @@ __global__ void strong_kernel(int Np, int64_t K, int ncomp, const double* __rest
 }
 
 // y = a x + b y (n entries); with x2: y = a x + b y + c x2
+// y = a x + b y + c x2; with b = 0 the old y is not read (it may be uninitialised)
 __global__ void axpby_kernel(int64_t n, double a, const double* __restrict__ x, double b, double* __restrict__ y,
                              double c, const double* __restrict__ x2) {
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-    y[i] = a * x[i] + b * y[i] + (x2 ? c * x2[i] : 0.0);
+    y[i] = a * x[i] + (b != 0.0 ? b * y[i] : 0.0) + (x2 ? c * x2[i] : 0.0);
 }
 
 inline int eg(int64_t n) {
@@ -579,6 +581,9 @@ cudaError_t setup_ins(dg_mesh* m) {
   ICK(al(&w->bp, n1));
   ICK(al(&w->dP, n1));
   ICK(al(&w->tmp, 2 * n1));
+  ICK(al(&w->gts, 2 * n1));
+  ICK(al(&w->zero, n1));
+  ICK(cudaMemset(w->zero, 0, n1 * sizeof(double)));
   ICK(cudaEventCreate(&w->ev0));
   ICK(cudaEventCreate(&w->ev1));
   // degree >= 3: the stage's dense contractions on the tensor cores
@@ -643,10 +648,24 @@ cudaError_t advect_field(const dg_mesh* m, InsWorkspace* w, const dg_ins_state* 
         ca = 1.0 + th;
         cb = -th;
       }
+      const double* g = s->gU;
+      if (s->gU_hist) {  // the velocity data at ts, interpolated through t^{n-1}, t^n, t^{n+1}
+        const double tau = (ts - tn) / s->dt;
+        const double* gn = s->gU_hist;
+        if (s->step == 0) {  // t^n, t^{n+1}: linear
+          axpby_kernel<<<eg(n2), 256, 0, st>>>(n2, tau, s->gU, 0.0, w->gts, 1.0 - tau, gn); note_launch();
+        } else {
+          axpby_kernel<<<eg(n2), 256, 0, st>>>(n2, 0.5 * tau * (tau + 1.0), s->gU, 0.0, w->gts, 1.0 - tau * tau, gn);
+          note_launch();
+          axpby_kernel<<<eg(n2), 256, 0, st>>>(n2, 0.5 * tau * (tau - 1.0), gn + n2, 1.0, w->gts, 0.0, nullptr);
+          note_launch();
+        }
+        g = w->gts;
+      }
       if (w->tensor)
-        ICK(advect_stage_tensor(m, w, s->U, s->Uold, ca, cb, cur, nxt, s->gU, kRkA[stg], kRkB[stg], dts, st));
+        ICK(advect_stage_tensor(m, w, s->U, s->Uold, ca, cb, cur, nxt, g, kRkA[stg], kRkB[stg], dts, st));
       else
-        ICK(launch_advect(m, w, s->U, s->Uold, ca, cb, cur, nxt, s->gU, kRkA[stg], kRkB[stg], dts, st));
+        ICK(launch_advect(m, w, s->U, s->Uold, ca, cb, cur, nxt, g, kRkA[stg], kRkB[stg], dts, st));
       std::swap(cur, nxt);
     }
     t += dts;
@@ -689,7 +708,7 @@ cudaError_t ins_run(dg_mesh* mu, dg_mesh* mp, dg_ins_state* s, int nsteps, cudaS
     axpby_kernel<<<eg(n2), 256, 0, st>>>(n2, 1.0 / (nu * dt), w->Uhat, 0.0, w->tmp, 0.0, nullptr); note_launch();
     ICK(launch_rhs(mu, 2, w->tmp, s->gU, w->bu, st));
     grad_div_kernel<<<unsigned(K), gd_threads, 4 * Np * sizeof(double), st>>>(0, mu->N, K, mu->geo64, mp->conn, w->ops, L,
-                                                                       s->P, s->gP, w->G);
+                                                                       s->P, s->gU_hist ? s->gP_n : s->gP, w->G);
     note_launch();
     axpby_kernel<<<eg(n2), 256, 0, st>>>(n2, -1.0 / nu, w->G, 1.0, w->bu, 0.0, nullptr); note_launch();
     ICK(cudaMemcpyAsync(w->Uhh, s->U, n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -708,7 +727,13 @@ cudaError_t ins_run(dg_mesh* mu, dg_mesh* mp, dg_ins_state* s, int nsteps, cudaS
     note_launch();
     axpby_kernel<<<eg(n1), 256, 0, st>>>(n1, 0.0, w->bp, -gamma / dt, w->bp, 0.0, nullptr); note_launch();
     ICK(cudaMemsetAsync(w->dP, 0, n1 * sizeof(double), st));
-    ICK(cudaMemsetAsync(w->tmp, 0, n1 * sizeof(double), st));
+    if (s->gU_hist) {  // the increment's Dirichlet data gP - gP_n: b -= L(gP - gP_n)
+      axpby_kernel<<<eg(n1), 256, 0, st>>>(n1, 1.0, s->gP, 0.0, w->tmp, -1.0, s->gP_n); note_launch();
+      ICK(launch_rhs(mp, 1, w->zero, w->tmp, w->G, st));
+      axpby_kernel<<<eg(n1), 256, 0, st>>>(n1, 1.0, w->G, 1.0, w->bp, 0.0, nullptr); note_launch();
+    } else {
+      ICK(cudaMemsetAsync(w->tmp, 0, n1 * sizeof(double), st));
+    }
     sv = dg_pcg_solve(mp, &s->pr_opts, 1, 0.0, w->bp, w->dP, &info, st);
     s->pr_iters = info.iters[0];
     if (sv != DG_OK) {
@@ -746,6 +771,10 @@ extern "C" dg_status dg_ins_step(dg_mesh* mu, dg_mesh* mp, dg_ins_state* s, int 
   }
   if (!(s->nu > 0) || !(s->dt > 0) || s->Ns < 1 || s->step < 0 || nsteps < 0) {
     set_error("need nu > 0, dt > 0, Ns >= 1, step >= 0, nsteps >= 0");
+    return DG_ERR_ARG;
+  }
+  if (s->gU_hist && (!s->gP_n || nsteps > 1)) {
+    set_error("time-dependent boundary data (gU_hist) need gP_n and one step per call");
     return DG_ERR_ARG;
   }
   try {
