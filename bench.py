@@ -625,6 +625,42 @@ def run_solve_only(args):
                       "iters": info["iters"][0], "coarse_iters": info["coarse_iters"]}), flush=True)
 
 
+def run_amg_compare(args):
+    """Section 3's preconditioner comparison on the 32768-triangle N=6 workload
+    (128x128 jittered grid): p-multigrid 6->3->1 with algebraic multigrid on the
+    degree-1 level (FP32 levels and FP64), against algebraic multigrid alone on
+    the probed degree-6 matrix. One JSON line per preconditioner: outer
+    iterations, solve time (set-up excluded: a first solve builds the
+    hierarchy), wall time of that first solve, device bytes of the
+    preconditioner per element."""
+    import time
+    import torch
+    import paper_1801_00246_gb300 as P
+    from paper_1801_00246_gb300 import build
+    from dg_inputs import config_mesh, manufactured
+    build.build()
+    m, N = config_mesh("c2_pmg_32768tri_N6")
+    mesh = P.Mesh.from_inputs(m, N)
+    xn, yn = mesh.nodes()
+    uex, fex = manufactured("sin_2pi_x_cos_3pi_y")
+    xh, yh = xn.cpu().numpy(), yn.cpu().numpy()
+    dev = xn.device
+    b = mesh.rhs(torch.from_numpy(fex(xh, yh)).to(dev), torch.from_numpy(uex(xh, yh)).to(dev))
+    cases = (("pmg_amg_mixed", dict(precond=P.PREC_PMG, degrees=[6, 3, 1], coarse_amg=1, mixed=1)),
+             ("pmg_amg_fp64", dict(precond=P.PREC_PMG, degrees=[6, 3, 1], coarse_amg=1, mixed=0)),
+             ("amg", dict(precond=P.PREC_AMG)))
+    for name, kw in cases:
+        opts = P._binding.default_opts(tol=1e-10, max_iter=1000, **kw)
+        t0 = time.time()
+        mesh.solve(b, torch.zeros_like(b), opts=opts)
+        torch.cuda.synchronize()
+        first = time.time() - t0
+        _, info = mesh.solve(b, torch.zeros_like(b), opts=opts)
+        print(json.dumps({"amg_compare": True, "precond": name, "K": mesh.K, "N": N, "iters": info["iters"][0],
+                          "relres": info["relres"][0], "ms": info["ms"], "first_solve_s": first,
+                          "precond_bytes_per_element": info["precond_bytes"] / mesh.K}), flush=True)
+
+
 def run_ins(args):
     """The split INS step on the 64x64 Kovasznay workload alone (see ins_measure)."""
     import paper_1801_00246_gb300 as P
@@ -646,11 +682,13 @@ def main():
     ap.add_argument("--degree", type=int, default=8, help="degree for --apply-only")
     ap.add_argument("--kernel64", default="", help="--apply-only: FP64 kernel (tile, tensor, tensor_pipe, ept, tc64)")
     ap.add_argument("--kernel32", default="", help="--apply-only: FP32 kernel (tile, gemm, tensor, tensor_pipe, ept, tc05)")
-    ap.add_argument("--sweep", action="store_true", help="apply throughput for N=1..8, FP64/FP32, B=1/4/16")
+    ap.add_argument("--sweep", action="store_true", help="apply throughput for N=1..10, FP64/FP32, B=1/4/16")
     ap.add_argument("--solve-only", action="store_true", help="one N=8 pMG-FCG solve in an NVTX range (profiling)")
     ap.add_argument("--graph", type=int, default=1, help="--solve-only: 1 = CUDA-graph solve, 0 = host loop")
     ap.add_argument("--fp64", action="store_true", help="--solve-only: FP64 multigrid levels")
     ap.add_argument("--ins", action="store_true", help="time dg_ins_step on the 8192-triangle Kovasznay case")
+    ap.add_argument("--amg-compare", action="store_true",
+                    help="pMG-AMG against AMG alone on the 32768-triangle N=6 workload")
     ap.add_argument("--sweep-degrees", default="1,2,3,4,5,6,7,8,9,10")
     ap.add_argument("--sweep-batches", default="1,4,16")
     args = ap.parse_args()
@@ -667,6 +705,9 @@ def main():
         return
     if args.ins:
         run_ins(args)
+        return
+    if args.amg_compare:
+        run_amg_compare(args)
         return
     world, rank, local = dist_setup(args)
     if args.impl == "reference":

@@ -105,8 +105,11 @@ enum { DG_KERNEL_AUTO = 0, DG_KERNEL_TILE = 1, DG_KERNEL_GEMM = 2, DG_KERNEL_TEN
 #define DG_NUM_KERNELS 8 /* kernel ids 0..7; dg_autotune's times use this many slots per entry */
 #define DG_MAX_DEGREE 10 /* degrees 1..10 (Section 5.2 studies the kernels up to N = 10) */
 
-/* Preconditioner choices for dg_pcg_solve (Section 3). */
-enum { DG_PREC_NONE = 0, DG_PREC_JACOBI = 1, DG_PREC_INVMASS = 2, DG_PREC_PMG = 3 };
+/* Preconditioner choices for dg_pcg_solve (Section 3). DG_PREC_AMG: one
+ * smoothed-aggregation V-cycle on the probed matrix of the mesh degree itself
+ * (algebraic multigrid alone, the baseline the paper compares pMG-AMG with;
+ * flexible CG, as with DG_PREC_PMG). */
+enum { DG_PREC_NONE = 0, DG_PREC_JACOBI = 1, DG_PREC_INVMASS = 2, DG_PREC_PMG = 3, DG_PREC_AMG = 4 };
 
 typedef struct {
   double tol;          /* stop when ||b - A x||_2 / ||b||_2 <= tol (per right-hand side) */
@@ -136,6 +139,9 @@ typedef struct {
   int total_iters;              /* iterations of the batched loop (max over the batch) */
   float ms;                     /* device time of the solve (CUDA events on the stream) */
   int coarse_iters;             /* coarsest-degree CG iterations summed over the solve */
+  double precond_bytes;         /* device bytes of the preconditioner's own data: the p-multigrid
+                                   levels' and coarse solve's vectors, the algebraic multigrid's
+                                   matrices and vectors (0 for none, Jacobi, inverse mass) */
 } dg_solve_info;
 
 /* Default options: tol 1e-10, max_iter 1000, Jacobi, no multigrid. */

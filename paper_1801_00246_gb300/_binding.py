@@ -7,7 +7,7 @@ import numpy as np
 from . import build as _build
 
 DG_F64, DG_F32, DG_F64_DFMA = 0, 1, 2
-PREC_NONE, PREC_JACOBI, PREC_INVMASS, PREC_PMG = 0, 1, 2, 3
+PREC_NONE, PREC_JACOBI, PREC_INVMASS, PREC_PMG, PREC_AMG = 0, 1, 2, 3, 4
 (KERNEL_AUTO, KERNEL_TILE, KERNEL_GEMM, KERNEL_TENSOR, KERNEL_EPT, KERNEL_TENSOR_PIPE, KERNEL_TC05,
  KERNEL_TC64) = 0, 1, 2, 3, 4, 5, 6, 7
 NUM_KERNELS = 8
@@ -35,7 +35,8 @@ class SolverOpts(ctypes.Structure):
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int * DG_MAX_BATCH), ("relres", ctypes.c_double * DG_MAX_BATCH),
-                ("total_iters", ctypes.c_int), ("ms", ctypes.c_float), ("coarse_iters", ctypes.c_int)]
+                ("total_iters", ctypes.c_int), ("ms", ctypes.c_float), ("coarse_iters", ctypes.c_int),
+                ("precond_bytes", ctypes.c_double)]
 
 
 class InsState(ctypes.Structure):
@@ -288,7 +289,8 @@ class Mesh:
         if check:
             _check(st)
         res = dict(iters=list(info.iters[:B]), relres=list(info.relres[:B]), total_iters=info.total_iters,
-                   ms=info.ms, coarse_iters=info.coarse_iters, status=_STATUS.get(st, st))
+                   ms=info.ms, coarse_iters=info.coarse_iters, precond_bytes=info.precond_bytes,
+                   status=_STATUS.get(st, st))
         return x, res
 
 

@@ -53,6 +53,7 @@ struct Amg {
   int64_t nc = 0;
   double *cb = nullptr, *cx = nullptr;
   std::vector<void*> allocs;
+  size_t bytes = 0;  // device bytes held in allocs
 };
 
 void amg_free(Amg* a) {
@@ -291,6 +292,7 @@ cudaError_t upload(Amg* a, const Csr& h, DevCsr& d) {
   a->allocs.push_back(d.col);
   ACK(cudaMalloc(&d.val, sizeof(double) * std::max<int64_t>(d.nnz, 1)));
   a->allocs.push_back(d.val);
+  a->bytes += sizeof(int64_t) * (h.n + 1) + (sizeof(int32_t) + sizeof(double)) * std::max<int64_t>(d.nnz, 1);
   ACK(cudaMemcpy(d.ptr, h.ptr.data(), sizeof(int64_t) * (h.n + 1), cudaMemcpyHostToDevice));
   if (d.nnz) {
     ACK(cudaMemcpy(d.col, h.col.data(), sizeof(int32_t) * d.nnz, cudaMemcpyHostToDevice));
@@ -431,6 +433,7 @@ cudaError_t amg_build(dg_mesh* m, int degree, double lambda, int B, Amg** out, c
       ACK(cudaMalloc(&a->cx, sizeof(double) * n * B));
       ACK(poison(a->cx, sizeof(double) * n * B, POISON_AMG));
       a->allocs.push_back(a->cx);
+      a->bytes += sizeof(double) * (size_t(n) * n + 2 * size_t(n) * B);
       break;
     }
     std::vector<int64_t> agg;
@@ -475,13 +478,15 @@ cudaError_t amg_build(dg_mesh* m, int degree, double lambda, int B, Amg** out, c
     }
     Csr R = transpose(P);
     Csr Ac = spgemm(R, spgemm(A, P));
-    ACK(upload(a, A, L.A));
+    if (lev == 0) L.A = a->A0;  // the probed matrix, already on the device
+    else ACK(upload(a, A, L.A));
     ACK(upload(a, P, L.P));
     ACK(upload(a, R, L.R));
     std::vector<double> di(A.n);
     for (int64_t i = 0; i < A.n; ++i) di[i] = 1.0 / d[i];
     ACK(cudaMalloc(&L.dinv, sizeof(double) * A.n));
     a->allocs.push_back(L.dinv);
+    a->bytes += sizeof(double) * A.n * (1 + 5 * size_t(B));  // dinv and the five level vectors
     ACK(cudaMemcpy(L.dinv, di.data(), sizeof(double) * A.n, cudaMemcpyHostToDevice));
     for (double** p : {&L.x, &L.b, &L.r, &L.d, &L.t}) {
       ACK(cudaMalloc(p, sizeof(double) * A.n * B));
@@ -568,6 +573,7 @@ cudaError_t amg_vcycle(Amg* a, const double* b, double* x, cudaStream_t st) {
 }
 
 int amg_levels(const Amg* a) { return a ? int(a->L.size()) + 1 : 0; }
+size_t amg_bytes(const Amg* a) { return a ? a->bytes : 0; }
 
 // y = A0 x for the Amg's batch of right-hand sides
 cudaError_t amg_apply_fine(Amg* a, const double* x, double* y, cudaStream_t st) {

@@ -42,6 +42,7 @@ cudaError_t amg_build(dg_mesh* m, int degree, double lambda, int B, Amg** out, c
 cudaError_t amg_vcycle(Amg* a, const double* b, double* x, cudaStream_t st);
 void amg_free(Amg* a);
 int amg_levels(const Amg* a);
+size_t amg_bytes(const Amg* a);  // device bytes of the hierarchy (matrices, vectors, coarse inverse)
 cudaError_t amg_apply_fine(Amg* a, const double* x, double* y, cudaStream_t st);
 void free_ins_workspace(dg_mesh* m);
 

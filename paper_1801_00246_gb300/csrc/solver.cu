@@ -76,6 +76,7 @@ struct Workspace {
   Amg* amg = nullptr;
   std::string amg_key;
   uint64_t amg_gen = 0;  // bumped on every AMG (re)build
+  size_t pmg_bytes = 0;  // device bytes of the p-multigrid levels' and coarse solve's vectors
   double* cz = nullptr;  // coarse preconditioned residual
   // whole-solve CUDA graph
   double *gb = nullptr, *gx = nullptr;  // staged right-hand side and iterate (the graph's fixed addresses)
@@ -599,8 +600,10 @@ cudaError_t setup_workspace(Ctx& c) {
         CK(walloc(w, &v.Ad, nl * c.B));
         CK(walloc(w, &v.dinv, nl));
       }
+      w->pmg_bytes += (o->mixed ? sizeof(float) : sizeof(double)) * nl * (5 * size_t(c.B) + 1);
     }
     const size_t nc = size_t(m->K) * npd(o->degrees[L - 1]) * c.B;
+    w->pmg_bytes += sizeof(double) * nc * 6;
     CK(walloc(w, &w->crhs, nc));
     CK(walloc(w, &w->cx, nc));
     CK(walloc(w, &w->cr, nc));
@@ -918,6 +921,9 @@ cudaError_t precondition(Ctx& c, int& coarse_iters) {
       k_invmass<<<int((nt + 255) / 256), 256, 0, c.st>>>(Np, c.m->K, c.B, c.m->geo64, Minv, c.lambda, w->r, w->z); note_launch();
       break;
     }
+    case DG_PREC_AMG:
+      CK(amg_vcycle(w->amg, w->r, w->z, c.st));
+      break;
     case DG_PREC_PMG:
       if (c.o->mixed) {
         k_convert<float, double><<<egrid(nt), 256, 0, c.st>>>(nt, w->r, w->lv32[0].rhs); note_launch();
@@ -989,7 +995,7 @@ cudaError_t pcg_eager(Ctx& c, const double* b, double* x, int& it, int& coarse_i
   Workspace* w = c.w;
   const dg_solver_opts* o = c.o;
   const int B = c.B;
-  const bool flexible = o->precond == DG_PREC_PMG;
+  const bool flexible = o->precond == DG_PREC_PMG || o->precond == DG_PREC_AMG;
   CK(cudaEventRecord(w->ev0, c.st));
   CK(pcg_start(c, b, x, coarse_iters));
   CK(cudaMemcpyAsync(w->h_scal, w->scal, sizeof(double) * B * kNS, cudaMemcpyDeviceToHost, c.st));
@@ -1062,7 +1068,7 @@ std::string graph_key(const Ctx& c) {
 //   WHILE (active and passes < max_iter) { first half; tail; IF (active) { second half } }
 cudaError_t capture_body(Ctx& c) {
   Workspace* w = c.w;
-  const bool flexible = c.o->precond == DG_PREC_PMG;
+  const bool flexible = c.o->precond == DG_PREC_PMG || c.o->precond == DG_PREC_AMG;
   int unused = 0;
   CK(cudaMemsetAsync(w->gctr, 0, sizeof(unsigned long long) * G_NCTR, c.st));
   CK(pcg_start(c, w->gb, w->gx, unused));
@@ -1172,6 +1178,8 @@ cudaError_t pcg_run(Ctx& c, const double* b, double* x, dg_solve_info* info, dg_
   } else if (o->precond == DG_PREC_PMG) {
     CK(setup_pmg(c, key));
     if (o->coarse_amg) CK(ensure_amg(c, o->degrees[o->nlevels - 1]));
+  } else if (o->precond == DG_PREC_AMG) {
+    CK(ensure_amg(c, c.m->N));
   }
   int it = 0, coarse_iters = 0;
   if (o->graph) CK(pcg_graph(c, b, x, it, coarse_iters));
@@ -1195,6 +1203,8 @@ cudaError_t pcg_run(Ctx& c, const double* b, double* x, dg_solve_info* info, dg_
     info->total_iters = it;
     info->ms = ms;
     info->coarse_iters = coarse_iters;
+    if (o->precond == DG_PREC_PMG) info->precond_bytes = double(w->pmg_bytes + (o->coarse_amg ? amg_bytes(w->amg) : 0));
+    if (o->precond == DG_PREC_AMG) info->precond_bytes = double(amg_bytes(w->amg));
   }
   return cudaSuccess;
 }
@@ -1227,7 +1237,7 @@ dg_status dg_pcg_solve(dg_mesh* m, const dg_solver_opts* o, int B, double lambda
   if (B < 1 || B > DG_MAX_BATCH) { set_error("batch must be in 1..64"); return DG_ERR_ARG; }
   if (!(o->tol > 0.0) || o->max_iter < 0) { set_error("tol must be > 0 and max_iter >= 0"); return DG_ERR_ARG; }
   if (!std::isfinite(lambda) || lambda < 0) { set_error("lambda must be finite and >= 0"); return DG_ERR_ARG; }
-  if (o->precond < DG_PREC_NONE || o->precond > DG_PREC_PMG) { set_error("unknown preconditioner"); return DG_ERR_ARG; }
+  if (o->precond < DG_PREC_NONE || o->precond > DG_PREC_AMG) { set_error("unknown preconditioner"); return DG_ERR_ARG; }
   if (o->precond == DG_PREC_INVMASS && !(lambda > 0)) { set_error("inverse-mass preconditioner needs lambda > 0"); return DG_ERR_ARG; }
   if (o->precond == DG_PREC_PMG) {
     if (o->nlevels < 2 || o->nlevels > 8 || o->degrees[0] != m->N) {
