@@ -54,7 +54,7 @@ constexpr int kSplitDepth = 208;
 constexpr int kABytes = kSl * kT * kKC * 2;  // one data chunk, 8 slices: 64 KB
 constexpr int kBBytes = kSl * kNC * kKC * 2; // one operator block, 8 slices: 24 KB
 constexpr int kASlice = kT * kKC * 2, kBSlice = kNC * kKC * 2;
-constexpr int kSmem = 2 * kABytes + 2 * kBBytes + 4 * kT * 4 + 12 * 8;
+constexpr int kSmem = 2 * kABytes + 2 * kBBytes + 4 * kT * 4 + 12 * 8;  // the tail: 10 mbarriers, slot, flag
 
 __device__ int g_tc64_err;
 
@@ -225,13 +225,17 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
   uint8_t* sA = sm;                        // [2][8 slices][128 rows][32] canonical
   uint8_t* sB = sm + 2 * kABytes;          // [2][8 slices][48 rows][32] canonical
   int* pmax = reinterpret_cast<int*>(sB + 2 * kBBytes);  // [4][kT]
-  // full[2], empty[2], bfull[2], acc_full, acc_empty
+  // full[2], empty[2], bfull[2], acc_full, acc_empty, bempty[2]
   uint64_t* bars = reinterpret_cast<uint64_t*>(pmax + 4 * kT);
-  uint64_t *full = bars, *empty = bars + 2, *bfull = bars + 4, *acc_full = bars + 6, *acc_empty = bars + 7;
-  uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 8);
+  uint64_t *full = bars, *empty = bars + 2, *bfull = bars + 4, *acc_full = bars + 6, *acc_empty = bars + 7,
+           *bempty = bars + 8;
+  uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 10);
   int* abort_flag = reinterpret_cast<int*>(slot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t ntiles = (rows + kT - 1) / kT;
+  // with at most two data chunks per row, both stay in the two buffers for all
+  // output passes of a tile: sliced once per tile instead of once per pass
+  const bool resident = KCH <= 2 && NCH > 1;
   if (tid == 0) {
     for (int i = 0; i < 2; ++i) {
       tc::mbar_init(full + i, kSlicers / 32);  // one arrival per slicing warp
@@ -240,6 +244,7 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
     }
     tc::mbar_init(acc_full, 1);
     tc::mbar_init(acc_empty, kSlicers / 32);
+    for (int i = 0; i < 2; ++i) tc::mbar_init(bempty + i, 1);  // an operator stage's products completed
     *abort_flag = 0;
     tc::mbar_init_fence();
   }
@@ -252,28 +257,31 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
 
   if (warp == kSlicers / 32) {
     // ================= products
-    uint32_t g = 0, pass = 0;
+    uint32_t g = 0, pass = 0, it = 0;
     const uint64_t adesc0 = tc::smem_desc(tc::smem_addr(sA), 128, (kKC / 8) * 128);
     const uint64_t bdesc0 = tc::smem_desc(tc::smem_addr(sB), 128, (kKC / 8) * 128);
-    for (int64_t tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
+    for (int64_t tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x, ++it) {
       for (int nc = 0; nc < NCH; ++nc, ++pass) {
         // the accumulators are free once the previous pass has been drained
         if (pass > 0 && !tc::mbar_wait(acc_empty, (pass - 1) & 1u)) *abort_flag = 1;
         tc::fence_after();
         for (int kc = 0; kc < KCH; ++kc, ++g) {
-          const uint32_t b = g & 1u;
+          const uint32_t bs = g & 1u;                 // operator stage
+          const uint32_t bd = resident ? kc : bs;     // data buffer
           // the operator stage is free once chunk g - 2's products completed
-          if (g >= 2 && !tc::mbar_wait(empty + b, ((g - 2) >> 1) & 1u)) *abort_flag = 1;
+          if (g >= 2 && !tc::mbar_wait(bempty + bs, ((g - 2) >> 1) & 1u)) *abort_flag = 1;
           if (lane == 0) {
-            tc::mbar_expect_tx(bfull + b, kBBytes);
-            tc::bulk_g2s(sB + b * kBBytes, Bops + size_t(nc * KCH + kc) * kBBytes, kBBytes, bfull + b);
+            tc::mbar_expect_tx(bfull + bs, kBBytes);
+            tc::bulk_g2s(sB + bs * kBBytes, Bops + size_t(nc * KCH + kc) * kBBytes, kBBytes, bfull + bs);
           }
           __syncwarp();
-          if (!tc::mbar_wait(full + b, (g >> 1) & 1u)) *abort_flag = 1;
-          if (!tc::mbar_wait(bfull + b, (g >> 1) & 1u)) *abort_flag = 1;
+          // the data chunk: sliced once per chunk, or (resident) once per tile for all passes
+          if (!resident && !tc::mbar_wait(full + bd, (g >> 1) & 1u)) *abort_flag = 1;
+          if (resident && nc == 0 && !tc::mbar_wait(full + bd, it & 1u)) *abort_flag = 1;
+          if (!tc::mbar_wait(bfull + bs, (g >> 1) & 1u)) *abort_flag = 1;
           tc::fence_after();
           if (lane == 0) {
-            const uint64_t ab = adesc0 + ((b * kABytes) >> 4), bb = bdesc0 + ((b * kBBytes) >> 4);
+            const uint64_t ab = adesc0 + ((bd * kABytes) >> 4), bb = bdesc0 + ((bs * kBBytes) >> 4);
             uint32_t started = kc > 0 ? 0xffu : 0u;
 #pragma unroll
             for (int ks = 0; ks < kKC / 16; ++ks)
@@ -286,7 +294,8 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
                              idesc, (started >> s) & 1u);
                   started |= 1u << s;
                 }
-            tc::mma_commit(empty + b);
+            tc::mma_commit(bempty + bs);
+            if (!resident || nc == NCH - 1) tc::mma_commit(empty + bd);  // the data buffer is free
             if (kc == KCH - 1) tc::mma_commit(acc_full);
           }
           __syncwarp();
@@ -298,7 +307,7 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
     const int e = (warp & 3) * 32 + lane;
     const int q = warp >> 2;
     const uint32_t lanebase = uint32_t((warp & 3) * 32) << 16;
-    uint32_t g = 0, pass = 0;
+    uint32_t g = 0, pass = 0, it = 0;
     auto load8 = [&](const double* xr, bool live, int k0, double (&v)[8]) {
       if (live && vec2 && k0 + 8 <= Kd) {
         const double2* p2 = reinterpret_cast<const double2*>(xr + k0);
@@ -313,7 +322,7 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
         for (int t = 0; t < 8; ++t) v[t] = (live && k0 + t < Kd) ? __ldg(xr + k0 + t) : 0.0;
       }
     };
-    for (int64_t tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
+    for (int64_t tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x, ++it) {
       const int64_t row = tile * kT + e;
       const bool live = row < rows;
       const double* xr = X + (live ? row : 0) * ldx;
@@ -356,20 +365,23 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
       }
       for (int nc = 0; nc < NCH; ++nc, ++pass) {
         for (int kc = 0; kc < KCH; ++kc, ++g) {
-          const uint32_t b = g & 1u;
+          if (resident && nc > 0) continue;  // the tile's chunks are still in the buffers
+          const uint32_t b = resident ? uint32_t(kc) : (g & 1u);
           double v[8];
 #pragma unroll
           for (int t = 0; t < 8; ++t) v[t] = vn[t];
           {  // request the next chunk of this row (the next pass starts again at chunk 0)
             const int kn = kc + 1 < KCH ? kc + 1 : 0;
-            if (kc + 1 < KCH || nc + 1 < NCH) load8(xr, live, kn * kKC + 8 * q, vn);
+            if (kc + 1 < KCH || (nc + 1 < NCH && !resident)) load8(xr, live, kn * kKC + 8 * q, vn);
           }
           uint64_t I[8];
           uint32_t sg[8];
 #pragma unroll
           for (int t = 0; t < 8; ++t) I[t] = fixed56(v[t], E, sg[t]);
-          // buffer b is free once chunk g - 2's products completed
-          if (g >= 2 && !tc::mbar_wait(empty + b, ((g - 2) >> 1) & 1u)) *abort_flag = 1;
+          // buffer b is free once the products that read it completed: chunk g - 2's, or
+          // (resident) the previous tile's last pass
+          if (!resident && g >= 2 && !tc::mbar_wait(empty + b, ((g - 2) >> 1) & 1u)) *abort_flag = 1;
+          if (resident && it >= 1 && !tc::mbar_wait(empty + b, (it - 1) & 1u)) *abort_flag = 1;
           uint8_t* dst = sA + b * kABytes + (e >> 3) * 512 + q * 128 + (e & 7) * 16;
 #pragma unroll
           for (int j = 0; j < kSl; ++j) {
@@ -497,52 +509,56 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
 }
 
 // ------------------------------------------------------------------ face columns of Y
-// One thread per (element, face-node entry i = f (N+1) + j): from the element's
-// face data and its neighbour's across face f (FN, written by the gradient
-// product), Y[2Np + i] = 1/2 nr sJ [u], Y[2Np + NFN + i] = 1/2 ns sJ [u],
-// Y[2Np + 2 NFN + i] = -sJ ({n.grad u} + tau [u]), in float-float scaled by
-// the entry's largest input; the row's largest exponent per element
-// (exy, raised atomically) for the output product's slicing.
+// One warp per element, a lane per face-node entry i = f (N+1) + j (two rounds
+// above 32 entries): from the element's face data and its neighbour's across
+// face f (FN, written by the gradient product), Y[2Np + i] = 1/2 nr sJ [u],
+// Y[2Np + NFN + i] = 1/2 ns sJ [u], Y[2Np + 2 NFN + i] = -sJ ({n.grad u} +
+// tau [u]), in float-float scaled by the entry's largest input; the row's
+// largest exponent (exy: raised from the volume columns' value the gradient
+// product wrote) for the output product's slicing, one warp maximum per row.
 __global__ void __launch_bounds__(256) tc64_face_fill(int N, int64_t K, int64_t nE, const double* __restrict__ gx,
                                                       const int32_t* __restrict__ conn,
                                                       const double2* __restrict__ FN, double* __restrict__ Y,
                                                       int ldy, int* __restrict__ exy) {
   const int Np = (N + 1) * (N + 2) / 2, Nfp = N + 1, NFN = 3 * Nfp;
-  const int64_t total = nE * NFN;
   const ff cpen{float((N + 1) * (N + 2)) * 0.5f, 0.f};
-  for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t be = t / NFN;
-    const int i = int(t - be * NFN);
-    const int f = i / Nfp, j = i - f * Nfp;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
+  for (int64_t be = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); be < nE; be += warps) {
     const int64_t el = be % K, boff = be - el;
-    const double* g = gx + 16 * el + 4 + 4 * f;
-    const double2 own = __ldg(FN + t);
-    const int code = __ldg(conn + 3 * el + f);
-    double2 oth = make_double2(0.0, 0.0);
-    if (code >= 0) oth = __ldg(FN + (boff + (code >> 2)) * NFN + (code & 3) * Nfp + (Nfp - 1 - j));
-    const int R = max(max(exp_bound64(own.x), exp_bound64(own.y)), max(exp_bound64(oth.x), exp_bound64(oth.y)));
-    const int Rs = R == -1100 ? 0 : R;
-    const ff um = d2ff(own.x, Rs), dnm = d2ff(own.y, Rs);
-    ff jm{0.f, 0.f}, av{0.f, 0.f};
-    if (code >= 0) {
-      jm = ff_sub(d2ff(oth.x, Rs), um);
-      av = ff_pow2(ff_sub(dnm, d2ff(oth.y, Rs)), 0.5f);
-    } else if (code == -2) {  // Dirichlet
-      jm = ff_pow2(um, -2.0f);
-      av = dnm;
+    int ym = -1100;
+    for (int i = lane; i < NFN; i += 32) {
+      const int f = i / Nfp, j = i - f * Nfp;
+      const double* g = gx + 16 * el + 4 + 4 * f;
+      const double2 own = __ldg(FN + be * NFN + i);
+      const int code = __ldg(conn + 3 * el + f);
+      double2 oth = make_double2(0.0, 0.0);
+      if (code >= 0) oth = __ldg(FN + (boff + (code >> 2)) * NFN + (code & 3) * Nfp + (Nfp - 1 - j));
+      const int R = max(max(exp_bound64(own.x), exp_bound64(own.y)), max(exp_bound64(oth.x), exp_bound64(oth.y)));
+      const int Rs = R == -1100 ? 0 : R;
+      const ff um = d2ff(own.x, Rs), dnm = d2ff(own.y, Rs);
+      ff jm{0.f, 0.f}, av{0.f, 0.f};
+      if (code >= 0) {
+        jm = ff_sub(d2ff(oth.x, Rs), um);
+        av = ff_pow2(ff_sub(dnm, d2ff(oth.y, Rs)), 0.5f);
+      } else if (code == -2) {  // Dirichlet
+        jm = ff_pow2(um, -2.0f);
+        av = dnm;
+      }
+      const ff nr = d2ff(__ldg(g), 0), ns = d2ff(__ldg(g + 1), 0), sJ = d2ff(__ldg(g + 2), 0);
+      const ff tau = ff_mul(cpen, d2ff(__ldg(g + 3), 0));
+      const ff hs = ff_pow2(ff_mul(sJ, jm), 0.5f);
+      const ff a = ff_mul(nr, hs), b = ff_mul(ns, hs);
+      const ff fl = ff_neg(ff_mul(sJ, ff_add(av, ff_mul(tau, jm))));
+      double* y = Y + be * ldy + 2 * Np + i;
+      const double da = ff_to_double(a.h, a.l, Rs), db = ff_to_double(b.h, b.l, Rs), dc = ff_to_double(fl.h, fl.l, Rs);
+      y[0] = da;
+      y[NFN] = db;
+      y[2 * NFN] = dc;
+      ym = max(ym, max(exp_bound64(da), max(exp_bound64(db), exp_bound64(dc))));
     }
-    const ff nr = d2ff(__ldg(g), 0), ns = d2ff(__ldg(g + 1), 0), sJ = d2ff(__ldg(g + 2), 0);
-    const ff tau = ff_mul(cpen, d2ff(__ldg(g + 3), 0));
-    const ff hs = ff_pow2(ff_mul(sJ, jm), 0.5f);
-    const ff a = ff_mul(nr, hs), b = ff_mul(ns, hs);
-    const ff fl = ff_neg(ff_mul(sJ, ff_add(av, ff_mul(tau, jm))));
-    double* y = Y + be * ldy + 2 * Np + i;
-    const double da = ff_to_double(a.h, a.l, Rs), db = ff_to_double(b.h, b.l, Rs), dc = ff_to_double(fl.h, fl.l, Rs);
-    y[0] = da;
-    y[NFN] = db;
-    y[2 * NFN] = dc;
-    const int ym = max(exp_bound64(da), max(exp_bound64(db), exp_bound64(dc)));
-    if (ym > -1100) atomicMax(exy + be, ym);  // the row's bound: the volume columns' (set before) and these
+    ym = __reduce_max_sync(0xffffffffu, ym);
+    if (lane == 0 && ym > -1100) exy[be] = max(exy[be], ym);  // with the volume columns' bound, set before
   }
 }
 
@@ -805,8 +821,7 @@ cudaError_t launch_apply_tc64(dg_mesh* m, int degree, int B, double lambda, cons
     int sms = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    const int64_t total = nE * NFN;
-    const int64_t blocks = std::min<int64_t>((total + 255) / 256, int64_t(sms) * 16);
+    const int64_t blocks = std::min<int64_t>((nE + 7) / 8, int64_t(sms) * 16);  // 8 warps, a warp per element
     tc64_face_fill<<<unsigned(blocks), 256, 0, st>>>(N, m->K, nE, m->geox, m->conn, FN, Y, ldy, split ? exf : exy);
     note_launch();
     e = cudaGetLastError();
