@@ -186,14 +186,17 @@ __device__ __forceinline__ ff horner8(const uint32_t (&acc)[kSl][4], int c) {
 // C1 the epilogue writes the volume columns of Y (wr, ws), the Helmholtz
 // columns lambda J u, and every element's face data FN = (u, n.grad u) at its
 // face nodes (outward normal of the element itself).
+// Y and the face data are column-major with leading dimension ldc (a multiple
+// of 32 rows), so a warp's 32 rows write 256 contiguous bytes per column.
 struct GradOut {
   int N;
   int64_t K;
   const double* gx;  // derived geometry, 16 words per element
-  double* Y;
-  int ldy, helm;
+  double* Y;         // [columns][ldc]
+  int64_t ldc;
+  int helm;
   double lambda;
-  double2* FN;  // [rows][3 (N+1)]
+  double *FNu, *FNd;  // [3 (N+1)][ldc]: u and n.grad u at the element's face nodes
   int* exy;     // [rows]: largest exponent of the row's Y values (for the output product)
   int* exf;     // [rows] or null: set to "none" here when the face columns keep their own exponent
 };
@@ -217,6 +220,7 @@ constexpr int kSlicers = 512;  // threads of warps 0-15
 template <int MODE>
 __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int M, int Kd, int NCH, int KCH,
                                                               const double* __restrict__ X, int64_t ldx, int vec2,
+                                                              int xcol,
                                                               const int* __restrict__ ex_given,
                                                               const uint8_t* __restrict__ Bops,
                                                               const int* __restrict__ ea, double* __restrict__ out,
@@ -309,7 +313,10 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
     const uint32_t lanebase = uint32_t((warp & 3) * 32) << 16;
     uint32_t g = 0, pass = 0, it = 0;
     auto load8 = [&](const double* xr, bool live, int k0, double (&v)[8]) {
-      if (live && vec2 && k0 + 8 <= Kd) {
+      if (xcol) {  // column-major X: element (row, k) at xr[k ldx], xr = X + row
+#pragma unroll
+        for (int t = 0; t < 8; ++t) v[t] = (live && k0 + t < Kd) ? __ldg(xr + int64_t(k0 + t) * ldx) : 0.0;
+      } else if (live && vec2 && k0 + 8 <= Kd) {
         const double2* p2 = reinterpret_cast<const double2*>(xr + k0);
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
@@ -325,7 +332,7 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
     for (int64_t tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x, ++it) {
       const int64_t row = tile * kT + e;
       const bool live = row < rows;
-      const double* xr = X + (live ? row : 0) * ldx;
+      const double* xr = xcol ? X + (live ? row : 0) : X + (live ? row : 0) * ldx;
       // scale exponent of the row: a bound |X[row][k]| < 2^E, given by the producer
       // of X or found here
       int E;
@@ -447,10 +454,11 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
                 const ff grr{gh[0], gh[1]}, grs{gh[2], gh[3]}, gss{gh[4], gh[5]};
                 const ff wr = ff_add(ff_mul(grr, ur), ff_mul(grs, us));
                 const ff ws = ff_add(ff_mul(grs, ur), ff_mul(gss, us));
-                double* yr = go.Y + row * go.ldy;
+                double* yr = go.Y + row;  // column c of this row at yr[c ldc]
+                const int64_t ldc = go.ldc;
                 const double dwr = ff_to_double(wr.h, wr.l, S), dws = ff_to_double(ws.h, ws.l, S);
-                yr[n] = dwr;
-                yr[Np + n] = dws;
+                yr[n * ldc] = dwr;
+                yr[(Np + n) * ldc] = dws;
                 ymax = max(ymax, max(exp_bound64(dwr), exp_bound64(dws)));
                 const double un = __ldg(X + row * ldx + n);
                 const int64_t el = row % go.K;
@@ -460,7 +468,7 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
                   const ff lj = ff_mul(d2ff(go.lambda, 0), d2ff(__ldg(gg), 0));
                   const ff vv = ff_mul(lj, d2ff(un, eu));
                   const double dv = ff_to_double(vv.h, vv.l, eu);
-                  yr[2 * Np + 3 * NFN + n] = dv;
+                  yr[(2 * Np + 3 * NFN + n) * ldc] = dv;
                   ymax = max(ymax, exp_bound64(dv));
                 }
                 // face data at the face nodes this node is (a corner belongs to two faces)
@@ -483,7 +491,9 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
                   if (f >= 0) {
                     const ff nr = d2ff(__ldg(gg + 4 + 4 * f), 0), ns = d2ff(__ldg(gg + 5 + 4 * f), 0);
                     const ff dn = ff_add(ff_mul(nr, ur), ff_mul(ns, us));
-                    go.FN[row * NFN + f * Nfp + j] = make_double2(un, ff_to_double(dn.h, dn.l, S));
+                    const int64_t fi = int64_t(f * Nfp + j) * ldc + row;
+                    go.FNu[fi] = un;
+                    go.FNd[fi] = ff_to_double(dn.h, dn.l, S);
                   }
                 }
               }
@@ -509,56 +519,64 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
 }
 
 // ------------------------------------------------------------------ face columns of Y
-// One warp per element, a lane per face-node entry i = f (N+1) + j (two rounds
-// above 32 entries): from the element's face data and its neighbour's across
-// face f (FN, written by the gradient product), Y[2Np + i] = 1/2 nr sJ [u],
-// Y[2Np + NFN + i] = 1/2 ns sJ [u], Y[2Np + 2 NFN + i] = -sJ ({n.grad u} +
-// tau [u]), in float-float scaled by the entry's largest input; the row's
-// largest exponent (exy: raised from the volume columns' value the gradient
-// product wrote) for the output product's slicing, one warp maximum per row.
+// One thread per element (consecutive threads take consecutive rows, so every
+// access to the column-major face data and Y is coalesced except the
+// neighbour's): for each face f and face node j, entry i = f (N+1) + j, from
+// the element's face data and its neighbour's across face f (FNu, FNd, written
+// by the gradient product), Y[2Np + i] = 1/2 nr sJ [u], Y[2Np + NFN + i] =
+// 1/2 ns sJ [u], Y[2Np + 2 NFN + i] = -sJ ({n.grad u} + tau [u]), in
+// float-float scaled by the entry's largest input; the row's largest exponent
+// (exy: raised from the value the gradient product wrote for the volume
+// columns) for the output product's slicing.
 __global__ void __launch_bounds__(256) tc64_face_fill(int N, int64_t K, int64_t nE, const double* __restrict__ gx,
                                                       const int32_t* __restrict__ conn,
-                                                      const double2* __restrict__ FN, double* __restrict__ Y,
-                                                      int ldy, int* __restrict__ exy) {
+                                                      const double* __restrict__ FNu,
+                                                      const double* __restrict__ FNd, double* __restrict__ Y,
+                                                      int64_t ldc, int* __restrict__ exy) {
   const int Np = (N + 1) * (N + 2) / 2, Nfp = N + 1, NFN = 3 * Nfp;
   const ff cpen{float((N + 1) * (N + 2)) * 0.5f, 0.f};
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
-  for (int64_t be = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); be < nE; be += warps) {
+  for (int64_t be = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; be < nE; be += int64_t(gridDim.x) * blockDim.x) {
     const int64_t el = be % K, boff = be - el;
     int ym = -1100;
-    for (int i = lane; i < NFN; i += 32) {
-      const int f = i / Nfp, j = i - f * Nfp;
+    for (int f = 0; f < 3; ++f) {
       const double* g = gx + 16 * el + 4 + 4 * f;
-      const double2 own = __ldg(FN + be * NFN + i);
-      const int code = __ldg(conn + 3 * el + f);
-      double2 oth = make_double2(0.0, 0.0);
-      if (code >= 0) oth = __ldg(FN + (boff + (code >> 2)) * NFN + (code & 3) * Nfp + (Nfp - 1 - j));
-      const int R = max(max(exp_bound64(own.x), exp_bound64(own.y)), max(exp_bound64(oth.x), exp_bound64(oth.y)));
-      const int Rs = R == -1100 ? 0 : R;
-      const ff um = d2ff(own.x, Rs), dnm = d2ff(own.y, Rs);
-      ff jm{0.f, 0.f}, av{0.f, 0.f};
-      if (code >= 0) {
-        jm = ff_sub(d2ff(oth.x, Rs), um);
-        av = ff_pow2(ff_sub(dnm, d2ff(oth.y, Rs)), 0.5f);
-      } else if (code == -2) {  // Dirichlet
-        jm = ff_pow2(um, -2.0f);
-        av = dnm;
-      }
       const ff nr = d2ff(__ldg(g), 0), ns = d2ff(__ldg(g + 1), 0), sJ = d2ff(__ldg(g + 2), 0);
       const ff tau = ff_mul(cpen, d2ff(__ldg(g + 3), 0));
-      const ff hs = ff_pow2(ff_mul(sJ, jm), 0.5f);
-      const ff a = ff_mul(nr, hs), b = ff_mul(ns, hs);
-      const ff fl = ff_neg(ff_mul(sJ, ff_add(av, ff_mul(tau, jm))));
-      double* y = Y + be * ldy + 2 * Np + i;
-      const double da = ff_to_double(a.h, a.l, Rs), db = ff_to_double(b.h, b.l, Rs), dc = ff_to_double(fl.h, fl.l, Rs);
-      y[0] = da;
-      y[NFN] = db;
-      y[2 * NFN] = dc;
-      ym = max(ym, max(exp_bound64(da), max(exp_bound64(db), exp_bound64(dc))));
+      const int code = __ldg(conn + 3 * el + f);
+      const int64_t nb = code >= 0 ? boff + (code >> 2) : 0;
+      const int fn = code >= 0 ? (code & 3) : 0;
+      for (int j = 0; j < Nfp; ++j) {
+        const int i = f * Nfp + j;
+        const double ou = __ldg(FNu + int64_t(i) * ldc + be), od = __ldg(FNd + int64_t(i) * ldc + be);
+        double pu = 0.0, pd = 0.0;
+        if (code >= 0) {
+          const int64_t pi = int64_t(fn * Nfp + (Nfp - 1 - j)) * ldc + nb;
+          pu = __ldg(FNu + pi);
+          pd = __ldg(FNd + pi);
+        }
+        const int R = max(max(exp_bound64(ou), exp_bound64(od)), max(exp_bound64(pu), exp_bound64(pd)));
+        const int Rs = R == -1100 ? 0 : R;
+        const ff um = d2ff(ou, Rs), dnm = d2ff(od, Rs);
+        ff jm{0.f, 0.f}, av{0.f, 0.f};
+        if (code >= 0) {
+          jm = ff_sub(d2ff(pu, Rs), um);
+          av = ff_pow2(ff_sub(dnm, d2ff(pd, Rs)), 0.5f);
+        } else if (code == -2) {  // Dirichlet
+          jm = ff_pow2(um, -2.0f);
+          av = dnm;
+        }
+        const ff hs = ff_pow2(ff_mul(sJ, jm), 0.5f);
+        const ff a = ff_mul(nr, hs), b = ff_mul(ns, hs);
+        const ff fl = ff_neg(ff_mul(sJ, ff_add(av, ff_mul(tau, jm))));
+        double* y = Y + int64_t(2 * Np + i) * ldc + be;
+        const double da = ff_to_double(a.h, a.l, Rs), db = ff_to_double(b.h, b.l, Rs), dc = ff_to_double(fl.h, fl.l, Rs);
+        y[0] = da;
+        y[int64_t(NFN) * ldc] = db;
+        y[int64_t(2 * NFN) * ldc] = dc;
+        ym = max(ym, max(exp_bound64(da), max(exp_bound64(db), exp_bound64(dc))));
+      }
     }
-    ym = __reduce_max_sync(0xffffffffu, ym);
-    if (lane == 0 && ym > -1100) exy[be] = max(exy[be], ym);  // with the volume columns' bound, set before
+    if (ym > -1100) exy[be] = max(exy[be], ym);  // with the volume columns' bound, set before
   }
 }
 
@@ -629,7 +647,7 @@ void tc64_op_free(Tc64Op* op) {
 namespace {
 template <int MODE>
 cudaError_t gemm_launch(const Tc64Op& op, int64_t rows, const double* X, int64_t ldx, double* out, int64_t ldo,
-                        const int* ex_given, const GradOut& go, cudaStream_t st, int accum = 0) {
+                        const int* ex_given, const GradOut& go, cudaStream_t st, int accum = 0, int xcol = 0) {
   if (rows <= 0) return cudaSuccess;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -649,7 +667,7 @@ cudaError_t gemm_launch(const Tc64Op& op, int64_t rows, const double* X, int64_t
   const int vec2 = (ldx % 2 == 0 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0) ? 1 : 0;
   const int64_t tiles = (rows + kT - 1) / kT;
   const unsigned g = unsigned(std::min<int64_t>(tiles, grid[dev & 63]));
-  tc64_gemm<MODE><<<g, kSlicers + 32, kSmem, st>>>(rows, op.M, op.K, op.NCH, op.KCH, X, ldx, vec2, ex_given,
+  tc64_gemm<MODE><<<g, kSlicers + 32, kSmem, st>>>(rows, op.M, op.K, op.NCH, op.KCH, X, ldx, vec2, xcol, ex_given,
                                                    op.blocks, op.ea, out, ldo, accum, go);
   note_launch();
   return cudaGetLastError();
@@ -758,15 +776,16 @@ const Tc64Apply* t64_ops(dg_mesh* m, int degree, bool build, cudaError_t* err) {
   }
   return &o;
 }
-int t64_ldy(int degree, bool helm) {
+int t64_cols(int degree, bool helm) {  // Y's columns
   const int Np = (degree + 1) * (degree + 2) / 2, NFN = 3 * (degree + 1);
-  return (2 * Np + 3 * NFN + (helm ? Np : 0) + 1) & ~1;  // even: 16-byte rows for paired loads
+  return 2 * Np + 3 * NFN + (helm ? Np : 0);
 }
+int64_t t64_ldc(int64_t nE) { return (nE + 31) & ~int64_t(31); }
 }  // namespace
 
 size_t tc64_scratch_words(int degree, int64_t nE, bool helm) {
   const int NFN = 3 * (degree + 1);
-  return size_t(nE) * t64_ldy(degree, helm) + size_t(nE) * NFN * 2 + 2 * (size_t(nE + 1) / 2) + 2;
+  return size_t(t64_ldc(nE)) * (t64_cols(degree, helm) + 2 * NFN) + 2 * (size_t(nE + 1) / 2) + 2;
 }
 
 cudaError_t ensure_tc64_ops(dg_mesh* m, int degree) {
@@ -794,10 +813,10 @@ cudaError_t launch_apply_tc64(dg_mesh* m, int degree, int B, double lambda, cons
   if (e != cudaSuccess) return e;
   const int N = degree, Np = (N + 1) * (N + 2) / 2, NFN = 3 * (N + 1);
   const bool helm = lambda != 0.0;
-  const int ldy = t64_ldy(N, helm);
   const int64_t nE = int64_t(B) * m->K;
-  // scratch: Y [nE][ldy], the face data FN [nE][NFN] (u, n.grad u), FP64, and the
-  // rows' largest Y exponents; every word read is written first by this call
+  const int64_t ldc = t64_ldc(nE);
+  // scratch: Y [columns][ldc], the face data FNu, FNd [NFN][ldc] (u, n.grad u), FP64,
+  // and the rows' largest Y exponents; every word read is written first by this call
   const size_t words = tc64_scratch_words(N, nE, helm);
   if (!scratch && m->t64_cap < words) {
     cudaFree(m->t64_scratch);
@@ -810,36 +829,38 @@ cudaError_t launch_apply_tc64(dg_mesh* m, int degree, int B, double lambda, cons
     ++m->scratch_gen;
   }
   double* Y = scratch ? scratch : m->t64_scratch;
-  double2* FN = reinterpret_cast<double2*>(Y + size_t(nE) * ldy);
-  int* exy = reinterpret_cast<int*>(FN + size_t(nE) * NFN);
+  double* FNu = Y + size_t(ldc) * t64_cols(N, helm);
+  double* FNd = FNu + size_t(ldc) * NFN;
+  int* exy = reinterpret_cast<int*>(FNd + size_t(ldc) * NFN);
   const bool split = ops->outv.blocks != nullptr;
   int* exf = split ? exy + 2 * (size_t(nE + 1) / 2) : nullptr;  // the face columns' own exponents
-  GradOut go{N, m->K, m->geox, Y, ldy, helm ? 1 : 0, lambda, FN, exy, exf};
+  GradOut go{N, m->K, m->geox, Y, ldc, helm ? 1 : 0, lambda, FNu, FNd, exy, exf};
   e = gemm_launch<1>(ops->grad, nE, u, Np, nullptr, 0, nullptr, go, st);
   if (e != cudaSuccess) return e;
   {
     int sms = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    const int64_t blocks = std::min<int64_t>((nE + 7) / 8, int64_t(sms) * 16);  // 8 warps, a warp per element
-    tc64_face_fill<<<unsigned(blocks), 256, 0, st>>>(N, m->K, nE, m->geox, m->conn, FN, Y, ldy, split ? exf : exy);
+    const int64_t blocks = std::min<int64_t>((nE + 255) / 256, int64_t(sms) * 16);  // a thread per element
+    tc64_face_fill<<<unsigned(blocks), 256, 0, st>>>(N, m->K, nE, m->geox, m->conn, FNu, FNd, Y, ldc,
+                                                     split ? exf : exy);
     note_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   if (split) {  // Au = [Br Bs] Y_v + (face blocks) Y_f (+ M Y_h), the face block with its own exponents
-    e = gemm_launch<0>(ops->outv, nE, Y, ldy, Au, Np, exy, GradOut{}, st);
-    if (e == cudaSuccess) e = gemm_launch<0>(ops->outf, nE, Y + 2 * Np, ldy, Au, Np, exf, GradOut{}, st, 1);
+    e = gemm_launch<0>(ops->outv, nE, Y, ldc, Au, Np, exy, GradOut{}, st, 0, 1);
+    if (e == cudaSuccess) e = gemm_launch<0>(ops->outf, nE, Y + 2 * Np * ldc, ldc, Au, Np, exf, GradOut{}, st, 1, 1);
     if (e != cudaSuccess || !helm) return e;
-    return gemm_launch<0>(ops->mh, nE, Y + 2 * Np + 3 * NFN, ldy, Au, Np, exy, GradOut{}, st, 1);
+    return gemm_launch<0>(ops->mh, nE, Y + (2 * Np + 3 * NFN) * ldc, ldc, Au, Np, exy, GradOut{}, st, 1, 1);
   }
   if (helm && !ops->outh.blocks) {  // [OB | M] is too deep for exact group sums: OB Y, then += M (lambda J u)
     const int KY = 2 * Np + 3 * NFN;
-    e = gemm_launch<0>(ops->out, nE, Y, ldy, Au, Np, exy, GradOut{}, st);
+    e = gemm_launch<0>(ops->out, nE, Y, ldc, Au, Np, exy, GradOut{}, st, 0, 1);
     if (e != cudaSuccess) return e;
-    return gemm_launch<0>(ops->mh, nE, Y + KY, ldy, Au, Np, exy, GradOut{}, st, 1);
+    return gemm_launch<0>(ops->mh, nE, Y + KY * ldc, ldc, Au, Np, exy, GradOut{}, st, 1, 1);
   }
-  return gemm_launch<0>(helm ? ops->outh : ops->out, nE, Y, ldy, Au, Np, exy, GradOut{}, st);
+  return gemm_launch<0>(helm ? ops->outh : ops->out, nE, Y, ldc, Au, Np, exy, GradOut{}, st, 0, 1);
 }
 
 cudaError_t tc64_error(int* flag) {
