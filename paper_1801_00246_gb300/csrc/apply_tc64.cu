@@ -54,7 +54,7 @@ constexpr int kSplitDepth = 208;
 constexpr int kABytes = kSl * kT * kKC * 2;  // one data chunk, 8 slices: 64 KB
 constexpr int kBBytes = kSl * kNC * kKC * 2; // one operator block, 8 slices: 24 KB
 constexpr int kASlice = kT * kKC * 2, kBSlice = kNC * kKC * 2;
-constexpr int kSmem = 2 * kABytes + 2 * kBBytes + 4 * kT * 4 + 12 * 8;  // the tail: 10 mbarriers, slot, flag
+constexpr int kSmem = 2 * kABytes + 2 * kBBytes + 4 * kT * 4 + 12 * 8;  // the tail: 10 mbarriers, slot, 2 flags
 
 __device__ int g_tc64_err;
 
@@ -75,13 +75,6 @@ __device__ __forceinline__ uint64_t fixed56(double v, int E, uint32_t& sgn) {
   if (sh >= 0) return sh < 11 ? (m << sh) : 0ull;
   return sh > -63 ? (m >> (-sh)) : 0ull;
 }
-// BF16 bits of slice j (7 bits of I below bit 56 - 7j) with the sign
-__device__ __forceinline__ uint32_t slice_bits(uint64_t I, int j, uint32_t sgn) {
-  const uint32_t x = uint32_t(I >> (49 - 7 * j)) & 127u;
-  const float f = __uint_as_float(0x4B000000u | x) - 8388608.0f;  // exactly x
-  return (__float_as_uint(f) >> 16) | (sgn << 15);
-}
-
 // exact double of (h + l) 2^sc for a float-float pair with |l| small against h
 __device__ __forceinline__ double ff_to_double(float h, float l, int sc) {
   const float s = __fadd_rn(h, l);
@@ -235,6 +228,7 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
            *bempty = bars + 8;
   uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 10);
   int* abort_flag = reinterpret_cast<int*>(slot + 1);
+  int* tile_abort = abort_flag + 1;  // the slicers' common copy of abort_flag at a tile's start
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t ntiles = (rows + kT - 1) / kT;
   // with at most two data chunks per row, both stay in the two buffers for all
@@ -329,7 +323,12 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
         for (int t = 0; t < 8; ++t) v[t] = (live && k0 + t < Kd) ? __ldg(xr + k0 + t) : 0.0;
       }
     };
-    for (int64_t tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x, ++it) {
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+      // every slicer takes the same decision to stop (they meet at named barriers below)
+      asm volatile("bar.sync 1, %0;\n" ::"r"(kSlicers) : "memory");
+      if (tid == 0) *reinterpret_cast<volatile int*>(tile_abort) = *reinterpret_cast<volatile int*>(abort_flag);
+      asm volatile("bar.sync 1, %0;\n" ::"r"(kSlicers) : "memory");
+      if (*reinterpret_cast<volatile int*>(tile_abort)) break;
       const int64_t row = tile * kT + e;
       const bool live = row < rows;
       const double* xr = xcol ? X + (live ? row : 0) : X + (live ? row : 0) * ldx;
@@ -381,10 +380,19 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
             const int kn = kc + 1 < KCH ? kc + 1 : 0;
             if (kc + 1 < KCH || (nc + 1 < NCH && !resident)) load8(xr, live, kn * kKC + 8 * q, vn);
           }
-          uint64_t I[8];
-          uint32_t sg[8];
+          // each value's 56-bit fixed-point magnitude as two 28-bit halves, and its sign
+          // as the pair (s, c) with fma(2^23 + x, s, c) = +-x exactly for 0 <= x < 2^23
+          uint32_t hi[8], lo[8];
+          float sm[8], sc[8];
 #pragma unroll
-          for (int t = 0; t < 8; ++t) I[t] = fixed56(v[t], E, sg[t]);
+          for (int t = 0; t < 8; ++t) {
+            uint32_t sgn;
+            const uint64_t I = fixed56(v[t], E, sgn);
+            hi[t] = uint32_t(I >> 28);
+            lo[t] = uint32_t(I) & 0xFFFFFFFu;
+            sm[t] = sgn ? -1.0f : 1.0f;
+            sc[t] = sgn ? 8388608.0f : -8388608.0f;
+          }
           // buffer b is free once the products that read it completed: chunk g - 2's, or
           // (resident) the previous tile's last pass
           if (!resident && g >= 2 && !tc::mbar_wait(empty + b, ((g - 2) >> 1) & 1u)) *abort_flag = 1;
@@ -392,11 +400,19 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
           uint8_t* dst = sA + b * kABytes + (e >> 3) * 512 + q * 128 + (e & 7) * 16;
 #pragma unroll
           for (int j = 0; j < kSl; ++j) {
-            uint4 w;
-            w.x = slice_bits(I[0], j, sg[0]) | (slice_bits(I[1], j, sg[1]) << 16);
-            w.y = slice_bits(I[2], j, sg[2]) | (slice_bits(I[3], j, sg[3]) << 16);
-            w.z = slice_bits(I[4], j, sg[4]) | (slice_bits(I[5], j, sg[5]) << 16);
-            w.w = slice_bits(I[6], j, sg[6]) | (slice_bits(I[7], j, sg[7]) << 16);
+            // slice j: 7 bits of the magnitude below bit 56 - 7j, as a signed float,
+            // whose upper 16 bits are its BF16 pattern (at most 8 significant bits)
+            uint32_t fb[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+              const uint32_t x = ((j < 4 ? hi[t] : lo[t]) >> (21 - 7 * (j & 3))) & 127u;
+              fb[t] = __float_as_uint(__fmaf_rn(__uint_as_float(0x4B000000u | x), sm[t], sc[t]));
+            }
+            uint4 w;  // value 2i in the low half of word i, value 2i + 1 in the high half
+            w.x = __byte_perm(fb[0], fb[1], 0x7632);
+            w.y = __byte_perm(fb[2], fb[3], 0x7632);
+            w.z = __byte_perm(fb[4], fb[5], 0x7632);
+            w.w = __byte_perm(fb[6], fb[7], 0x7632);
             *reinterpret_cast<uint4*>(dst + j * kASlice) = w;
           }
           tc::fence_async_smem();
@@ -435,7 +451,8 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
                 // value = 2^{ea + E - 14} sum_s acc_s 2^{-7 s}
                 const ff hl = horner8(acc, c);
                 const double v = ff_to_double(hl.h, hl.l, __ldg(ea + col) + E - 14);
-                out[row * ldo + col] = accum ? out[row * ldo + col] + v : v;
+                if (accum) out[row * ldo + col] += v;  // (the Helmholtz or face block of a split product)
+                else out[row * ldo + col] = v;
               }
             }
           } else {
