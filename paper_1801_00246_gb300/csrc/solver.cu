@@ -296,7 +296,8 @@ __global__ void k_loop_head(const double* __restrict__ scal, int B, unsigned lon
 
 // End of a loop body: count the pass (and the body's kernels), continue while
 // a right-hand side is active and the cap is not reached; `hi` (if has_if)
-// guards the rest of the pass, which runs while any right-hand side is active.
+// guards the rest of the pass (the preconditioner and the next direction),
+// which runs only when another pass follows.
 __global__ void k_loop_tail(const double* __restrict__ scal, int B, unsigned long long* __restrict__ ctr, int slot,
                             int total_slot, int max_iter, unsigned long long kernels, cudaGraphConditionalHandle hw,
                             cudaGraphConditionalHandle hi, int has_if) {
@@ -306,7 +307,7 @@ __global__ void k_loop_tail(const double* __restrict__ scal, int B, unsigned lon
   if (total_slot >= 0) ++ctr[total_slot];
   ctr[G_KERNELS] += kernels;
   cudaGraphSetConditional(hw, (any && it < (unsigned long long)max_iter) ? 1u : 0u);
-  if (has_if) cudaGraphSetConditional(hi, any ? 1u : 0u);
+  if (has_if) cudaGraphSetConditional(hi, (any && it < (unsigned long long)max_iter) ? 1u : 0u);
 }
 
 __global__ void k_count(unsigned long long* __restrict__ ctr, unsigned long long kernels) {
@@ -752,7 +753,7 @@ cudaError_t coarse_pcg_amg(Ctx& c, int degree, const double* rhs, double* x, int
     CK(cudaStreamSynchronize(c.st));
     bool any = false;
     for (int b = 0; b < B; ++b) any = any || w->h_scal[b * kNS + S_ACTIVE] != 0.0;
-    if (!any) break;
+    if (!any || it >= c.o->coarse_max_iter) break;  // no further pass: no preconditioning for it
     CK(half2());
   }
   iters_out = it;
@@ -1014,6 +1015,7 @@ cudaError_t pcg_eager(Ctx& c, const double* b, double* x, int& it, int& coarse_i
       for (int bb = 0; bb < B; ++bb) any = any || w->h_scal[bb * kNS + S_ACTIVE] != 0.0;
       if (!any) break;
     }
+    if (it >= o->max_iter) break;  // no further pass: no preconditioning for it
     CK(pcg_half2(c, flexible, coarse_iters));
   }
   CK(cudaEventRecord(w->ev1, c.st));
