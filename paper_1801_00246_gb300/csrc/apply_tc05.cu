@@ -131,13 +131,15 @@ __device__ __forceinline__ void fix_tail(const float* u, int Np, int64_t e0, int
 }
 
 // -------------------------------------------------------------------------------
-// Face data: FN[be][f][j] = (u, n.grad u) at face node j of face f (counter-clockwise),
-// with the element's own outward normal. One thread per element; the tile's
-// face data go through shared memory to coalesced stores.
+// Face data: FN[f (N+1) + j][be] = (u, n.grad u) at face node j of face f
+// (counter-clockwise), with the element's own outward normal; column-major with
+// leading dimension ldc (a multiple of 32), so that the apply kernel's threads,
+// one element each, read their own entries coalesced. One thread per element;
+// the tile's face data go through shared memory to coalesced stores.
 template <int N>
 __global__ void __launch_bounds__(kTile) tc_face(int64_t K, int64_t nE, const float* __restrict__ gx,
                                                  const float* __restrict__ u, const uint8_t* __restrict__ opsF,
-                                                 float2* __restrict__ FN) {
+                                                 float2* __restrict__ FN, int64_t ldc) {
   using S = Tc<N>;
   constexpr int Np = S::Np, Nfp = S::Nfp, NFN = S::NFN, K1 = S::K1, NF = S::NF;
   extern __shared__ __align__(128) uint8_t sm[];
@@ -259,17 +261,9 @@ __global__ void __launch_bounds__(kTile) tc_face(int64_t K, int64_t nE, const fl
       }
     }
     __syncthreads();
-    {
-      const int n = ne * NFN;  // float2 entries of the tile, contiguous in FN
-      float2* dst = FN + e0 * NFN;
-      if ((n & 1) == 0 && ((e0 * NFN) & 1) == 0) {
-        const float4* s4 = reinterpret_cast<const float4*>(stg);
-        float4* d4 = reinterpret_cast<float4*>(dst);
-        for (int i = tid; i < n / 2; i += kTile) d4[i] = s4[i];
-      } else {
-        for (int i = tid; i < n; i += kTile) dst[i] = stg[i];
-      }
-    }
+    // column by column: a warp writes 32 consecutive elements of one entry
+    for (int i = warp; i < NFN; i += kTile / 32)
+      for (int le = tid & 31; le < ne; le += 32) FN[int64_t(i) * ldc + e0 + le] = stg[le * NFN + i];
     tc::fence_async_smem();
     tc::fence_before();
     __syncthreads();
@@ -317,7 +311,7 @@ __device__ __forceinline__ float absmax(const float (&y)[YN]) {
 // element's own face data (trace, outward normal derivative) and its
 // neighbour's across face f, both read from the face kernel's output.
 template <int N, int I0, int I1, int YN>
-__device__ __forceinline__ void face_quarter(float (&y)[YN], const float2* __restrict__ FN, const float* g,
+__device__ __forceinline__ void face_quarter(float (&y)[YN], const float2* __restrict__ FN, int64_t ldc, const float* g,
                                              const int32_t* __restrict__ conn, int64_t be, int64_t el, int64_t boff,
                                              float cpen) {
   constexpr int Nfp = N + 1, NFN = 3 * Nfp;
@@ -332,14 +326,14 @@ __device__ __forceinline__ void face_quarter(float (&y)[YN], const float2* __res
     sJ[f] = __ldg(g + 6 + 4 * f);
     tau[f] = cpen * __ldg(g + 7 + 4 * f);
     code[f] = __ldg(conn + 3 * el + f);
-    nb[f] = code[f] >= 0 ? FN + (boff + (code[f] >> 2)) * NFN + (code[f] & 3) * Nfp : FN;
+    nb[f] = code[f] >= 0 ? FN + int64_t((code[f] & 3) * Nfp) * ldc + (boff + (code[f] >> 2)) : FN;
   }
   float2 own[I1 - I0], oth[I1 - I0];
 #pragma unroll
   for (int i = I0; i < I1; ++i) {
     const int f = i / Nfp, j = i - f * Nfp;
-    own[i - I0] = __ldg(FN + be * NFN + i);
-    oth[i - I0] = code[f] >= 0 ? __ldg(nb[f] + (Nfp - 1 - j)) : make_float2(0.f, 0.f);
+    own[i - I0] = __ldg(FN + int64_t(i) * ldc + be);
+    oth[i - I0] = code[f] >= 0 ? __ldg(nb[f] + int64_t(Nfp - 1 - j) * ldc) : make_float2(0.f, 0.f);
   }
 #pragma unroll
   for (int i = I0; i < I1; ++i) {
@@ -370,9 +364,9 @@ __device__ __forceinline__ void face_quarter(float (&y)[YN], const float2* __res
 template <int N, bool HELM>
 __global__ void __launch_bounds__(512, 1) tc_apply(int64_t K, int64_t nE, const float* __restrict__ gx,
                                                    const int32_t* __restrict__ conn,
-                                                   const float2* __restrict__ FN, const float* __restrict__ u,
-                                                   const uint8_t* __restrict__ opsA, float lambda,
-                                                   float* __restrict__ out) {
+                                                   const float2* __restrict__ FN, int64_t ldc,
+                                                   const float* __restrict__ u, const uint8_t* __restrict__ opsA,
+                                                   float lambda, float* __restrict__ out) {
   using S = Tc<N>;
   constexpr int Np = S::Np, K1 = S::K1, V0 = S::V0, VB = S::VB, FQ = S::FQ, KQ = S::KQ;
   extern __shared__ __align__(128) uint8_t sm[];
@@ -548,8 +542,8 @@ __global__ void __launch_bounds__(512, 1) tc_apply(int64_t K, int64_t nE, const 
 #pragma unroll
       for (int j = 0; j < FQ; ++j) y[j] = 0.f;
       if (live) {
-        if (qf == 0) face_quarter<N, 0, S::E2>(y, FN, g, conn, be, el, boff, cpen);
-        else face_quarter<N, S::E2, S::NFN>(y, FN, g, conn, be, el, boff, cpen);
+        if (qf == 0) face_quarter<N, 0, S::E2>(y, FN, ldc, g, conn, be, el, boff, cpen);
+        else face_quarter<N, S::E2, S::NFN>(y, FN, ldc, g, conn, be, el, boff, cpen);
       }
       pmax[q * kTile + e] = absmax<FQ>(y);
       named_sync(2);
@@ -790,7 +784,8 @@ cudaError_t launch_n(dg_mesh* m, int B, double lambda, const float* u, float* Au
     ops = &o;
   }
   const int64_t nE = int64_t(B) * m->K;
-  const size_t need = size_t(nE) * 3 * (N + 1);
+  const int64_t ldc = (nE + 31) & ~int64_t(31);
+  const size_t need = size_t(ldc) * 3 * (N + 1);
   if (m->face32_cap < need) {
     cudaFree(m->face32);
     m->face32 = nullptr;
@@ -804,13 +799,13 @@ cudaError_t launch_n(dg_mesh* m, int B, double lambda, const float* u, float* Au
   const int64_t ntiles = (nE + kTile - 1) / kTile;
   const unsigned gf = unsigned(std::min<int64_t>(ntiles, grid_face[dev]));
   const unsigned ga = unsigned(std::min<int64_t>(ntiles, grid_apply[dev]));
-  tc_face<N><<<gf, kTile, S::smF, st>>>(m->K, nE, m->geox32, u, ops->opsF, m->face32);
+  tc_face<N><<<gf, kTile, S::smF, st>>>(m->K, nE, m->geox32, u, ops->opsF, m->face32, ldc);
   note_launch();
   if (lambda != 0.0)
-    tc_apply<N, true><<<ga, 512, S::smA, st>>>(m->K, nE, m->geox32, m->conn, m->face32, u, ops->opsA, float(lambda),
-                                               Au);
+    tc_apply<N, true><<<ga, 512, S::smA, st>>>(m->K, nE, m->geox32, m->conn, m->face32, ldc, u, ops->opsA,
+                                               float(lambda), Au);
   else
-    tc_apply<N, false><<<ga, 512, S::smA, st>>>(m->K, nE, m->geox32, m->conn, m->face32, u, ops->opsA, 0.f, Au);
+    tc_apply<N, false><<<ga, 512, S::smA, st>>>(m->K, nE, m->geox32, m->conn, m->face32, ldc, u, ops->opsA, 0.f, Au);
   note_launch();
   return cudaGetLastError();
 }

@@ -351,9 +351,10 @@ __global__ void k_invmass(int Np, int64_t K, int B, const double* __restrict__ g
                           double lambda, const double* __restrict__ r, double* __restrict__ z) {
   const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (idx >= int64_t(B) * K * Np) return;
-  const int64_t be = idx / Np;
+  const bool small = int64_t(B) * K * Np < (int64_t(1) << 31);  // 32-bit divisions where they fit
+  const int64_t be = small ? int64_t(uint32_t(idx) / uint32_t(Np)) : idx / Np;
   const int i = int(idx - be * Np);
-  const int64_t e = be % K;
+  const int64_t e = B == 1 ? be : (small ? int64_t(uint32_t(be) % uint32_t(K)) : be % K);
   const double* g = geo + 4 * e;
   const double J = 1.0 / (g[0] * g[3] - g[2] * g[1]);
   const double* re = r + be * Np;
@@ -367,19 +368,14 @@ __global__ void k_invmass(int Np, int64_t K, int B, const double* __restrict__ g
 //                       else      d = c0 dinv res, x += d.
 template <typename T>
 __global__ void k_cheb_first(int64_t n, int64_t ntot, const T* __restrict__ dinv, const T* __restrict__ rhs,
-                             T* __restrict__ res, T* __restrict__ d, T* __restrict__ x, T c0, int zero_x) {
+                             const T* __restrict__ Ax, T* __restrict__ res, T* __restrict__ d, T* __restrict__ x,
+                             T c0) {
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < ntot; i += int64_t(gridDim.x) * blockDim.x) {
-    if (zero_x) {
-      const T ri = rhs[i];
-      res[i] = ri;
-      const T di = c0 * dinv[i % n] * ri;
-      d[i] = di;
-      x[i] = di;
-    } else {
-      const T di = c0 * dinv[i % n] * res[i];
-      d[i] = di;
-      x[i] += di;
-    }
+    const T ri = Ax ? rhs[i] - Ax[i] : rhs[i];  // Ax null: x = 0
+    res[i] = ri;
+    const T di = c0 * dinv[i % n] * ri;
+    d[i] = di;
+    x[i] = Ax ? x[i] + di : di;
   }
 }
 
@@ -396,17 +392,19 @@ __global__ void k_cheb_step(int64_t n, int64_t ntot, const T* __restrict__ dinv,
   }
 }
 
-// rc[e][j] = sum_i P[i][j] rf[e][i]  (restriction R = P^T)
+// rc[e][j] = sum_i P[i][j] (res[e][i] - Ad[e][i]) (restriction R = P^T of the
+// residual after the last smoothing step, which nothing else reads)
 template <typename T>
-__global__ void k_restrict(int Npf, int Npc, int64_t nE, const T* __restrict__ P, const T* __restrict__ rf,
-                           T* __restrict__ rc) {
+__global__ void k_sub_restrict(int Npf, int Npc, int64_t nE, const T* __restrict__ P, const T* __restrict__ res,
+                               const T* __restrict__ Ad, T* __restrict__ rc) {
   const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (idx >= nE * Npc) return;
-  const int64_t e = idx / Npc;
+  const int64_t e = nE * Npc < (int64_t(1) << 31) ? int64_t(uint32_t(idx) / uint32_t(Npc)) : idx / Npc;
   const int j = int(idx - e * Npc);
-  const T* re = rf + e * Npf;
+  const T* re = res + e * Npf;
+  const T* ae = Ad + e * Npf;
   T acc = T(0);
-  for (int i = 0; i < Npf; ++i) acc += P[size_t(i) * Npc + j] * re[i];
+  for (int i = 0; i < Npf; ++i) acc += P[size_t(i) * Npc + j] * (re[i] - ae[i]);
   rc[idx] = acc;
 }
 
@@ -416,7 +414,7 @@ __global__ void k_prolong(int Npf, int Npc, int64_t nE, const T* __restrict__ P,
                           T* __restrict__ xf) {
   const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (idx >= nE * Npf) return;
-  const int64_t e = idx / Npf;
+  const int64_t e = nE * Npf < (int64_t(1) << 31) ? int64_t(uint32_t(idx) / uint32_t(Npf)) : idx / Npf;
   const int i = int(idx - e * Npf);
   const T* ce = xc + e * Npc;
   T acc = T(0);
@@ -788,11 +786,10 @@ cudaError_t chebyshev(Ctx& c, int l, bool zero_x) {
   const double lmin = rho / 10.0, lmax = 1.1 * rho;
   const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
   double rk = 1.0 / sigma;
-  if (!zero_x) {
-    CK(launch_apply(c.m, deg, prec_of<T>(), c.B, c.lambda, v.x, v.Ad, c.st));
-    k_sub<T><<<egrid(nt), 256, 0, c.st>>>(nt, v.rhs, v.Ad, v.res); note_launch();
-  }
-  k_cheb_first<T><<<egrid(nt), 256, 0, c.st>>>(n, nt, v.dinv, v.rhs, v.res, v.d, v.x, T(1.0 / theta), zero_x ? 1 : 0); note_launch();
+  if (!zero_x) CK(launch_apply(c.m, deg, prec_of<T>(), c.B, c.lambda, v.x, v.Ad, c.st));
+  // res = rhs (- A x), d = D^{-1} res / theta, x (+)= d
+  k_cheb_first<T><<<egrid(nt), 256, 0, c.st>>>(n, nt, v.dinv, v.rhs, zero_x ? nullptr : v.Ad, v.res, v.d, v.x,
+                                                T(1.0 / theta)); note_launch();
   for (int k = 1; k < c.o->cheb_degree; ++k) {
     CK(launch_apply(c.m, deg, prec_of<T>(), c.B, c.lambda, v.d, v.Ad, c.st));
     const double rnew = 1.0 / (2.0 * sigma - rk);
@@ -829,13 +826,13 @@ cudaError_t vcycle(Ctx& c, int l, int& coarse_iters) {
   // pre-smoothing from x = 0, then res = rhs - A x
   CK(chebyshev<T>(c, l, true));
   CK(launch_apply(c.m, deg, prec_of<T>(), c.B, c.lambda, v.d, v.Ad, c.st));
-  k_sub<T><<<egrid(nt), 256, 0, c.st>>>(nt, v.res, v.Ad, v.res); note_launch();
-  // restrict, recurse, prolong
+  // restrict res - A d, recurse, prolong
   const int degc = c.o->degrees[l + 1];
   const int Npf = npd(deg), Npc = npd(degc);
   const int64_t nE = int64_t(c.m->K) * c.B;
   const T* P = transfer_ptr<T>(c.m, deg, degc);
-  k_restrict<T><<<int((nE * Npc + 255) / 256), 256, 0, c.st>>>(Npf, Npc, nE, P, v.res, lv[l + 1].rhs); note_launch();
+  k_sub_restrict<T><<<int((nE * Npc + 255) / 256), 256, 0, c.st>>>(Npf, Npc, nE, P, v.res, v.Ad, lv[l + 1].rhs);
+  note_launch();
   CK(vcycle<T>(c, l + 1, coarse_iters));
   k_prolong<T><<<int((nE * Npf + 255) / 256), 256, 0, c.st>>>(Npf, Npc, nE, P, lv[l + 1].x, v.x); note_launch();
   // post-smoothing
