@@ -84,9 +84,11 @@ __global__ void __launch_bounds__(128, ept_min_blocks<N, T>()) ept_apply(
   constexpr int oDr = off_of(N), oDs = oDr + Np * Np, oBr = oDs + Np * Np, oBs = oBr + Np * Np,
                 oM = oBs + Np * Np, oMf = oM + Np * Np;
   constexpr T cpen = T((N + 1) * (N + 2)) / T(2);
-  __shared__ T sD[2 * Np * Np];  // Dr, Ds for the neighbour's face rows
-  for (int i = threadIdx.x; i < 2 * Np * Np; i += blockDim.x) sD[i] = cop<T>(oDr + i);
-  __syncthreads();
+  __shared__ T sD[2 * Np * Np];  // Dr, Ds for the neighbour's face rows (degree 1 needs none)
+  if (N > 1) {
+    for (int i = threadIdx.x; i < 2 * Np * Np; i += blockDim.x) sD[i] = cop<T>(oDr + i);
+    __syncthreads();
+  }
   const T* __restrict__ u = ub + size_t(blockIdx.y) * size_t(K) * Np;  // this right-hand side
   T* __restrict__ Au = Aub + size_t(blockIdx.y) * size_t(K) * Np;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < K; e += gridDim.x * blockDim.x) {
@@ -161,6 +163,11 @@ __global__ void __launch_bounds__(128, ept_min_blocks<N, T>()) ept_apply(
     T ur[Np], us[Np];
 #pragma unroll
     for (int i = 0; i < Np; ++i) {
+      if (N == 1 && i > 0) {  // degree 1: a constant gradient
+        ur[i] = ur[0];
+        us[i] = us[0];
+        continue;
+      }
       T a = T(0), b = T(0);
 #pragma unroll
       for (int m = 0; m < Np; ++m) {
@@ -218,18 +225,37 @@ __global__ void __launch_bounds__(128, ept_min_blocks<N, T>()) ept_apply(
           gnr = -(nx[f] * ng[f][0] + ny[f] * ng[f][2]);
           gns = -(nx[f] * ng[f][1] + ny[f] * ng[f][3]);
         }
-#pragma unroll
-        for (int j = 0; j < Nfp; ++j) {
-          const int kn = fnode_rt<N>(fn, Nfp - 1 - j);
-          T a = T(0), b = T(0), up = T(0);
+        if constexpr (N == 1) {
+          // degree 1: the neighbour's gradient is constant (every row of Dr, Ds is
+          // the same), so one row serves both face nodes
+          T a = T(0), b = T(0);
 #pragma unroll
           for (int m = 0; m < Np; ++m) {
-            a += sD[kn * Np + m] * unv[f][m];
-            b += sD[Np * Np + kn * Np + m] * unv[f][m];
-            up = (m == kn) ? unv[f][m] : up;
+            a += cop<T>(oDr + m) * unv[f][m];
+            b += cop<T>(oDs + m) * unv[f][m];
           }
-          jm[j] = up - uv[fnode<N>(f, j)];
-          av[j] = T(0.5) * (dn[f][j] - (gnr * a + gns * b));
+          const T dnp = gnr * a + gns * b;
+#pragma unroll
+          for (int j = 0; j < Nfp; ++j) {
+            const int kn = fnode_rt<N>(fn, Nfp - 1 - j);
+            const T up = kn == 0 ? unv[f][0] : (kn == 1 ? unv[f][1] : unv[f][2]);
+            jm[j] = up - uv[fnode<N>(f, j)];
+            av[j] = T(0.5) * (dn[f][j] - dnp);
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < Nfp; ++j) {
+            const int kn = fnode_rt<N>(fn, Nfp - 1 - j);
+            T a = T(0), b = T(0), up = T(0);
+#pragma unroll
+            for (int m = 0; m < Np; ++m) {
+              a += sD[kn * Np + m] * unv[f][m];
+              b += sD[Np * Np + kn * Np + m] * unv[f][m];
+              up = (m == kn) ? unv[f][m] : up;
+            }
+            jm[j] = up - uv[fnode<N>(f, j)];
+            av[j] = T(0.5) * (dn[f][j] - (gnr * a + gns * b));
+          }
         }
       }
       // face mass along the face, then lift
