@@ -195,6 +195,44 @@ def cpu_oracle_sample(N, n_elems, reps=1, seed=1):
     return ora, times, busy_cores(time.process_time() - c0, sum(times))
 
 
+def cpu_oracle_solve_c1():
+    """The oracle's Jacobi-PCG solve of the 512-triangle N=3 workload (manufactured
+    sin(pi x) sin(pi y), Dirichlet) to 1e-10, matrix-free: wall time in ms,
+    iterations, relative residual."""
+    from dg_inputs import config_mesh, manufactured
+    from oracle.sipdg import Sipdg
+    from oracle.solvers import cg
+    m, N = config_mesh("c1_poisson_512tri_N3")
+    ora = Sipdg(m.VX, m.VY, m.EToV, m.bc, N)
+    uex, fex = manufactured("sin_pi_x_sin_pi_y")
+    b = ora.rhs(fex(ora.x, ora.y), uex(ora.x, ora.y))
+    dinv = 1.0 / ora.diagonal()
+    t0 = time.perf_counter()
+    _, it, rr = cg(ora.apply, b, tol=1e-10, maxit=5000, prec=lambda r: dinv * r)
+    return (time.perf_counter() - t0) * 1e3, int(it), float(rr)
+
+
+def oracle_child():
+    """--oracle-child: the oracle apply sample and the c1 solve in this process
+    (started with the BLAS thread pools limited to one thread by the parent)."""
+    N = 8
+    ora, times, cores = cpu_oracle_sample(N, 1024, reps=2)
+    ms, it, rr = cpu_oracle_solve_c1()
+    print(json.dumps({"apply_gdofs": 1024 * ora.Np / float(np.min(times)) / 1e9, "cores": cores,
+                      "solve_c1_ms": ms}), flush=True)
+
+
+def cpu_oracle_one_core():
+    """The oracle timed in a child process on one core (BLAS threads set to 1)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-child"], capture_output=True,
+                           text=True, env=env, timeout=600)
+        return json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception as ex:  # reported, not fatal: the baseline is context
+        return {"error": str(ex)[:200]}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -423,8 +461,15 @@ def run_ours(args, world, rank, local):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         _, times, cores = cpu_oracle_sample(N, 2048, reps=3)
         cv = 2048 * Np / float(np.min(times)) / 1e9
+        solve_ms, solve_it, solve_rr = cpu_oracle_solve_c1()
+        one = cpu_oracle_one_core()
         line["cpu_baseline"] = {"value": cv, "unit": "GDOF/s", "cores": cores, "kind": "oracle",
-                                "sample": "FP64 oracle Poisson apply on 2048 of the 524288 elements (numpy)"}
+                                "sample": "FP64 oracle Poisson apply on 2048 of the 524288 elements (numpy)",
+                                "nproc": os.cpu_count(),
+                                "value_1core": one.get("apply_gdofs"),
+                                "solve_c1_ms": solve_ms, "solve_c1_iters": solve_it, "solve_c1_relres": solve_rr,
+                                "solve_c1_ms_1core": one.get("solve_c1_ms"),
+                                "solve_c1": "oracle Jacobi-PCG, 512 triangles, N=3, to 1e-10 (matrix-free)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -687,6 +732,7 @@ def main():
     ap.add_argument("--graph", type=int, default=1, help="--solve-only: 1 = CUDA-graph solve, 0 = host loop")
     ap.add_argument("--fp64", action="store_true", help="--solve-only: FP64 multigrid levels")
     ap.add_argument("--ins", action="store_true", help="time dg_ins_step on the 8192-triangle Kovasznay case")
+    ap.add_argument("--oracle-child", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--amg-compare", action="store_true",
                     help="pMG-AMG against AMG alone on the 32768-triangle N=6 workload")
     ap.add_argument("--sweep-degrees", default="1,2,3,4,5,6,7,8,9,10")
@@ -708,6 +754,9 @@ def main():
         return
     if args.amg_compare:
         run_amg_compare(args)
+        return
+    if args.oracle_child:
+        oracle_child()
         return
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
