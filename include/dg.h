@@ -320,6 +320,42 @@ dg_status dg_ins_step(dg_mesh* mesh_u, dg_mesh* mesh_p, dg_ins_state* state, int
 dg_status dg_pcg_jacobi_solve_static(const dg_mesh* mesh, int B, double lambda, double tol, int max_iter,
                                      const double* b, double* x, dg_solve_info* info, void* stream);
 
+/* ---------------------------------------------------------------- tetrahedra
+ * The same SIPDG operator on affine tetrahedra, the three-dimensional extension
+ * the paper names as its next step (Section 6). Readings for three dimensions:
+ * penalty tau = (N+1)(N+3)/3 max(1/h-, 1/h+) with h = |E| / |face| (the
+ * triangle's (N+1)(N+2)/2 is the d = 2 case of (N+1)(N+d)/d); boundary faces as
+ * on triangles; nodes equispaced, (r, s, t) = (-1 + 2i/N, -1 + 2j/N, -1 + 2k/N),
+ * i + j + k <= N, ordered by k, then j, then i; degrees 1..5. Reference
+ * tetrahedron v0 = (-1,-1,-1), v1 = (1,-1,-1), v2 = (-1,1,-1), v3 = (-1,-1,1);
+ * local face f is opposite local vertex 3 - f: (v0,v1,v2), (v0,v1,v3),
+ * (v1,v2,v3), (v0,v2,v3). Fields are device arrays [B][K][Np],
+ * Np = (N+1)(N+2)(N+3)/6. */
+typedef struct dg_tet_mesh dg_tet_mesh;
+
+/* Build the degree-N discretisation. VX, VY, VZ: host [Nv]; EToV: host [K][4]
+ * (positive orientation: det[v1-v0, v2-v0, v3-v0] > 0); bc: host [K][4], tag of
+ * face f (0 interior, 1 Dirichlet, 2 Neumann). Faces are matched by their vertex
+ * triples and face nodes by coordinates; a boundary face without a tag, a
+ * non-positive Jacobian or non-matching face nodes give DG_ERR_MESH. */
+dg_status dg_tet_mesh_setup(int N, int64_t Nv, const double* VX, const double* VY, const double* VZ, int64_t K,
+                            const int32_t* EToV, const int8_t* bc, void* stream, dg_tet_mesh** mesh);
+dg_status dg_tet_mesh_destroy(dg_tet_mesh* mesh);
+dg_status dg_tet_mesh_info(const dg_tet_mesh* mesh, int* N, int64_t* K, int* Np);
+/* Node coordinates into device [K][Np] arrays x, y, z. */
+dg_status dg_tet_mesh_nodes(const dg_tet_mesh* mesh, double* x, double* y, double* z, void* stream);
+/* Au = A(lambda) u for B right-hand sides, FP64 (DG_F64) or FP32 (DG_F32):
+ * one thread block handles four elements, one thread per node. */
+dg_status dg_tet_apply(const dg_tet_mesh* mesh, dg_prec prec, int B, double lambda, const void* u, void* Au,
+                       void* stream);
+/* b = J M f - L(g) (the Dirichlet problem's weak right-hand side, as dg_rhs). */
+dg_status dg_tet_rhs(const dg_tet_mesh* mesh, int B, const double* f, const double* g, double* b, void* stream);
+/* Jacobi-preconditioned CG on A(lambda) x = b in FP64 for B right-hand sides
+ * (x: initial guess in, solution out), host-driven (synchronises the stream each
+ * iteration); workspace kept with the mesh. info as for dg_pcg_solve. */
+dg_status dg_tet_pcg_jacobi_solve(dg_tet_mesh* mesh, int B, double lambda, double tol, int max_iter,
+                                  const double* b, double* x, dg_solve_info* info, void* stream);
+
 /* Host-only: the library's own reference data for degree N (1..10), for
  * inspection without a GPU. r, s: Np; M, Dr, Ds: Np x Np row-major;
  * Mf: (N+1) x (N+1); fmask: 3 x (N+1) local node index of face node j of face

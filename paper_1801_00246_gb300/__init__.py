@@ -7,11 +7,11 @@ library is missing every call raises.
 """
 from ._binding import (DG_F32, DG_F64, KERNEL_AUTO, KERNEL_EPT, KERNEL_GEMM, KERNEL_TENSOR, KERNEL_TENSOR_PIPE, KERNEL_TC05, KERNEL_TC64,
                        KERNEL_TILE,
-                       InsStepper,
+                       InsStepper, TetMesh,
                        PREC_AMG, PREC_INVMASS, PREC_JACOBI, PREC_NONE, PREC_PMG, DgError, Mesh, SolverOpts, default_opts,
                        interpolation_matrix, lib, lib_path, reference_operators)
 
-__all__ = ["Mesh", "InsStepper", "SolverOpts", "default_opts", "DgError", "DG_F64", "DG_F32", "PREC_NONE", "PREC_JACOBI", "PREC_INVMASS",
+__all__ = ["Mesh", "TetMesh", "InsStepper", "SolverOpts", "default_opts", "DgError", "DG_F64", "DG_F32", "PREC_NONE", "PREC_JACOBI", "PREC_INVMASS",
            "PREC_PMG", "PREC_AMG", "KERNEL_AUTO", "KERNEL_TILE", "KERNEL_GEMM", "KERNEL_TENSOR", "KERNEL_EPT",
            "KERNEL_TENSOR_PIPE", "KERNEL_TC05", "KERNEL_TC64",
            "reference_operators", "interpolation_matrix", "lib", "lib_path"]

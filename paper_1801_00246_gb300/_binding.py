@@ -79,6 +79,14 @@ def lib():
         "dg_solver_opts_default": ([ctypes.POINTER(SolverOpts)], None),
         "dg_ins_step": ([vp, vp, ctypes.POINTER(InsState), i32, vp], i32),
         "dg_pcg_jacobi_solve_static": ([vp, i32, dbl, dbl, i32, vp, vp, ctypes.POINTER(SolveInfo), vp], i32),
+        "dg_tet_mesh_setup": ([i32, i64, pd, pd, pd, i64, pi32, ctypes.POINTER(ctypes.c_int8), vp, ctypes.POINTER(vp)],
+                              i32),
+        "dg_tet_mesh_destroy": ([vp], i32),
+        "dg_tet_mesh_info": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i32)], i32),
+        "dg_tet_mesh_nodes": ([vp, vp, vp, vp, vp], i32),
+        "dg_tet_apply": ([vp, i32, i32, dbl, vp, vp, vp], i32),
+        "dg_tet_rhs": ([vp, i32, vp, vp, vp, vp], i32),
+        "dg_tet_pcg_jacobi_solve": ([vp, i32, dbl, dbl, i32, vp, vp, ctypes.POINTER(SolveInfo), vp], i32),
         "dg_reference_operators": ([i32, pd, pd, pd, pd, pd, pd, pi32], i32),
         "dg_interpolation_matrix": ([i32, i32, pd], i32),
         "dg_status_string": ([i32], ctypes.c_char_p),
@@ -292,6 +300,72 @@ class Mesh:
                    ms=info.ms, coarse_iters=info.coarse_iters, precond_bytes=info.precond_bytes,
                    status=_STATUS.get(st, st))
         return x, res
+
+
+class TetMesh:
+    """A degree-N (1..5) discretisation on affine tetrahedra (owns a dg_tet_mesh*):
+    VX, VY, VZ vertex coordinates, EToV [K][4], bc [K][4] face tags."""
+
+    def __init__(self, N, VX, VY, VZ, EToV, bc):
+        self.N = int(N)
+        VX, VY, VZ = (np.ascontiguousarray(v, dtype=np.float64) for v in (VX, VY, VZ))
+        EToV = np.ascontiguousarray(EToV, dtype=np.int32)
+        bc = np.ascontiguousarray(bc, dtype=np.int8)
+        self.K = int(EToV.shape[0])
+        self.Np = (self.N + 1) * (self.N + 2) * (self.N + 3) // 6
+        h = ctypes.c_void_p()
+        _check(lib().dg_tet_mesh_setup(self.N, VX.size, _dptr(VX), _dptr(VY), _dptr(VZ), self.K,
+                                       EToV.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                       bc.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)), None, ctypes.byref(h)))
+        self._h = h
+
+    @classmethod
+    def from_inputs(cls, mesh, N):
+        return cls(N, mesh.VX, mesh.VY, mesh.VZ, mesh.EToV, mesh.bc)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.dg_tet_mesh_destroy(h)
+            self._h = None
+
+    def nodes(self):
+        import torch
+        x, y, z = (torch.empty((self.K, self.Np), dtype=torch.float64, device="cuda") for _ in range(3))
+        _check(lib().dg_tet_mesh_nodes(self._h, _tptr(x), _tptr(y), _tptr(z), _stream()))
+        return x, y, z
+
+    def apply(self, u, lam=0.0, out=None):
+        """A(lam) u; u float64 or float32 CUDA [B][K][Np] or [K][Np] (the dtype picks the precision)."""
+        import torch
+        u = u.contiguous()
+        B = 1 if u.dim() == 2 else u.shape[0]
+        out = torch.empty_like(u) if out is None else out
+        prec = DG_F64 if u.dtype == torch.float64 else DG_F32
+        _check(lib().dg_tet_apply(self._h, prec, B, float(lam), _tptr(u), _tptr(out), _stream()))
+        return out
+
+    def rhs(self, f, g):
+        import torch
+        f, g = f.contiguous(), g.contiguous()
+        B = 1 if f.dim() == 2 else f.shape[0]
+        b = torch.empty_like(f)
+        _check(lib().dg_tet_rhs(self._h, B, _tptr(f), _tptr(g), _tptr(b), _stream()))
+        return b
+
+    def solve(self, b, x=None, lam=0.0, tol=1e-10, max_iter=5000, check=True):
+        """Jacobi-PCG in FP64; returns (x, info)."""
+        import torch
+        b = b.contiguous()
+        x = torch.zeros_like(b) if x is None else x
+        B = 1 if b.dim() == 2 else b.shape[0]
+        info = SolveInfo()
+        st = lib().dg_tet_pcg_jacobi_solve(self._h, B, float(lam), float(tol), int(max_iter), _tptr(b), _tptr(x),
+                                           ctypes.byref(info), _stream())
+        if check:
+            _check(st)
+        return x, dict(iters=list(info.iters[:B]), relres=list(info.relres[:B]), total_iters=info.total_iters,
+                       status=_STATUS.get(st, st))
 
 
 class InsStepper:

@@ -1,0 +1,935 @@
+// SIPDG Poisson / screened-Poisson operator on affine tetrahedra, and its
+// Jacobi-preconditioned CG solve: the three-dimensional extension the paper
+// names as its next step (Section 6), with the bilinear form of
+// Eq. ellipticOp1 on tetrahedra in the factored grouping of Eq. ellipticOp3
+// (volume gradient through Dr/Ds/Dt and the element metric, face jumps and
+// averages with the interior penalty, lift through the face mass):
+//
+//   (A u)_i = J [Br wr + Bs ws + Bt wt]_i             (w_a = sum_b G_ab u_b, u_b = D_b u)
+//           + lambda J [M u]_i
+//           + sum_f sum_j (sum_b nr_b D_b[k_fj][i]) F2_fj  1/2 (n.grad l_i, [u])_f
+//           + sum_{f,j: k_fj = i} F1_fj                     -(l_i, n.{grad u} + tau [u])_f
+//
+// with B_b = D_b^T M, G = (grad r_a . grad r_b), nr_b = n . grad r_b, and at the
+// face nodes F1 = sJ Mf(-{n.grad u} - tau [u]), F2 = 1/2 sJ Mf [u]. Readings
+// for three dimensions: tau = (N+1)(N+3)/3 max(1/h-, 1/h+), h = |E| / |face|
+// (the triangle's (N+1)(N+2)/2 is the d = 2 case of (N+1)(N+d)/d); boundary
+// faces as on triangles (Dirichlet ghost u+ = -u-, grad u+ = grad u-;
+// Neumann: no face terms); equispaced nodes (i, j, k)/N with i + j + k <= N,
+// ordered by k, then j, then i, whose face nodes form the equispaced triangle
+// of each face. Reference tetrahedron v0 = (-1,-1,-1), v1 = (1,-1,-1),
+// v2 = (-1,1,-1), v3 = (-1,-1,1); face f opposite vertex 3 - f: (v0,v1,v2),
+// (v0,v1,v3), (v1,v2,v3), (v0,v2,v3).
+//
+// Reference operators are built on the host from a monomial Vandermonde
+// matrix and Gauss-Jacobi quadrature; a neighbour's face nodes are matched to
+// the element's by their physical coordinates at setup. One thread block
+// handles a few elements, one thread per node.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <stdexcept>
+#include <vector>
+
+#include "dg_internal.h"
+
+namespace dgx {
+namespace tet {
+
+constexpr int kMaxTetN = 5;
+constexpr int kFaceVerts[4][3] = {{0, 1, 2}, {0, 1, 3}, {1, 2, 3}, {0, 2, 3}};
+
+inline int np3(int N) { return (N + 1) * (N + 2) * (N + 3) / 6; }
+inline int nfp3(int N) { return (N + 1) * (N + 2) / 2; }
+
+struct TetRef {
+  int N = 0, Np = 0, Nfp = 0;
+  std::vector<double> r, s, t;
+  std::vector<double> D[3];   // Dr, Ds, Dt (Np x Np, row-major: D[k][m] = d l_m / d r_b at node k)
+  std::vector<double> Bm[3];  // B_b = D_b^T M
+  std::vector<double> M;      // mass
+  std::vector<double> Mf[4];  // face mass on each reference face, per unit reference-face area ratio
+  std::vector<int> fmask[4];  // volume node of face node j
+  double face_area[4] = {};   // reference face areas
+  // Jacobi pieces: S_ab[i][i] (a <= b: rr, rs, rt, ss, st, tt), M[i][i], and per face
+  // node fc_b[f][j] = sum_l Mf[j][l] D_b[k_l][k_j]
+  std::vector<double> dS[6], dM, fc[3][4];
+};
+
+std::vector<int> monomial_exps(int N) {
+  std::vector<int> ex;
+  for (int c = 0; c <= N; ++c)
+    for (int b = 0; b + c <= N; ++b)
+      for (int a = 0; a + b + c <= N; ++a) {
+        ex.push_back(a);
+        ex.push_back(b);
+        ex.push_back(c);
+      }
+  return ex;
+}
+
+double ipow(double x, int k) {
+  double v = 1.0;
+  for (int i = 0; i < k; ++i) v *= x;
+  return v;
+}
+
+// monomial values (deriv = -1) or derivative along axis deriv at (r, s, t)
+void monomial_row(int N, double r, double s, double t, int deriv, double* out) {
+  const std::vector<int> ex = monomial_exps(N);
+  const int n = int(ex.size()) / 3;
+  for (int q = 0; q < n; ++q) {
+    const int a = ex[3 * q], b = ex[3 * q + 1], c = ex[3 * q + 2];
+    double v;
+    if (deriv < 0) v = ipow(r, a) * ipow(s, b) * ipow(t, c);
+    else if (deriv == 0) v = a ? a * ipow(r, a - 1) * ipow(s, b) * ipow(t, c) : 0.0;
+    else if (deriv == 1) v = b ? b * ipow(r, a) * ipow(s, b - 1) * ipow(t, c) : 0.0;
+    else v = c ? c * ipow(r, a) * ipow(s, b) * ipow(t, c - 1) : 0.0;
+    out[q] = v;
+  }
+}
+
+TetRef build_tet(int N) {
+  TetRef R;
+  R.N = N;
+  R.Np = np3(N);
+  R.Nfp = nfp3(N);
+  const int Np = R.Np, Nfp = R.Nfp;
+  for (int k = 0; k <= N; ++k)
+    for (int j = 0; j + k <= N; ++j)
+      for (int i = 0; i + j + k <= N; ++i) {
+        R.r.push_back(-1.0 + 2.0 * i / N);
+        R.s.push_back(-1.0 + 2.0 * j / N);
+        R.t.push_back(-1.0 + 2.0 * k / N);
+      }
+  // nodal basis: l_m = sum_q Vinv[q][m] mono_q
+  std::vector<double> V(size_t(Np) * Np);
+  for (int k = 0; k < Np; ++k) monomial_row(N, R.r[k], R.s[k], R.t[k], -1, &V[size_t(k) * Np]);
+  const std::vector<double> Vinv = invert(Np, V);
+  auto nodal_row = [&](double r, double s, double t, int deriv, double* out) {
+    std::vector<double> m(Np);
+    monomial_row(N, r, s, t, deriv, m.data());
+    for (int c = 0; c < Np; ++c) {
+      double a = 0.0;
+      for (int q = 0; q < Np; ++q) a += m[q] * Vinv[size_t(q) * Np + c];
+      out[c] = a;
+    }
+  };
+  for (int b = 0; b < 3; ++b) {
+    R.D[b].assign(size_t(Np) * Np, 0.0);
+    for (int k = 0; k < Np; ++k) nodal_row(R.r[k], R.s[k], R.t[k], b, &R.D[b][size_t(k) * Np]);
+  }
+  // mass by a collapsed Gauss-Jacobi rule exact to degree 2N + 1
+  std::vector<double> xa, wa, xb, wb, xc, wc;
+  const int nq = N + 1;
+  gauss_jacobi(nq, 0.0, 0.0, xa, wa);
+  gauss_jacobi(nq, 1.0, 0.0, xb, wb);
+  gauss_jacobi(nq, 2.0, 0.0, xc, wc);
+  R.M.assign(size_t(Np) * Np, 0.0);
+  std::vector<double> L(Np);
+  for (int i = 0; i < nq; ++i)
+    for (int j = 0; j < nq; ++j)
+      for (int k = 0; k < nq; ++k) {
+        const double a = xa[i], b = xb[j], c = xc[k], w = wa[i] * wb[j] * wc[k] / 8.0;
+        nodal_row(0.25 * (1 + a) * (1 - b) * (1 - c) - 1, 0.5 * (1 + b) * (1 - c) - 1, c, -1, L.data());
+        for (int p = 0; p < Np; ++p)
+          for (int q = 0; q < Np; ++q) R.M[size_t(p) * Np + q] += w * L[p] * L[q];
+      }
+  for (int b = 0; b < 3; ++b) {  // B_b = D_b^T M
+    R.Bm[b].assign(size_t(Np) * Np, 0.0);
+    for (int i = 0; i < Np; ++i)
+      for (int m = 0; m < Np; ++m) {
+        double a = 0.0;
+        for (int k = 0; k < Np; ++k) a += R.D[b][size_t(k) * Np + i] * R.M[size_t(k) * Np + m];
+        R.Bm[b][size_t(i) * Np + m] = a;
+      }
+  }
+  // faces: the nodes on each face, in volume-node order, and the face mass by a
+  // collapsed triangle rule mapped onto the reference face
+  const double V3[4][3] = {{-1, -1, -1}, {1, -1, -1}, {-1, 1, -1}, {-1, -1, 1}};
+  std::vector<double> ya, wya, yb, wyb;
+  gauss_jacobi(nq, 0.0, 0.0, ya, wya);
+  gauss_jacobi(nq, 1.0, 0.0, yb, wyb);
+  for (int f = 0; f < 4; ++f) {
+    const double* A = V3[kFaceVerts[f][0]];
+    const double* Bv = V3[kFaceVerts[f][1]];
+    const double* C = V3[kFaceVerts[f][2]];
+    double e1[3], e2[3], cr[3];
+    for (int d = 0; d < 3; ++d) {
+      e1[d] = Bv[d] - A[d];
+      e2[d] = C[d] - A[d];
+    }
+    cr[0] = e1[1] * e2[2] - e1[2] * e2[1];
+    cr[1] = e1[2] * e2[0] - e1[0] * e2[2];
+    cr[2] = e1[0] * e2[1] - e1[1] * e2[0];
+    const double area = 0.5 * std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+    R.face_area[f] = area;
+    const double nrm[3] = {cr[0] / (2 * area), cr[1] / (2 * area), cr[2] / (2 * area)};
+    for (int k = 0; k < Np; ++k) {  // a node lies on the face when it is in the face's plane
+      const double d = (R.r[k] - A[0]) * nrm[0] + (R.s[k] - A[1]) * nrm[1] + (R.t[k] - A[2]) * nrm[2];
+      if (std::fabs(d) < 1e-10) R.fmask[f].push_back(k);
+    }
+    if (int(R.fmask[f].size()) != Nfp) throw std::runtime_error("tetrahedron face node count");
+    R.Mf[f].assign(size_t(Nfp) * Nfp, 0.0);
+    std::vector<double> Lv(Np);
+    for (int i = 0; i < nq; ++i)
+      for (int j = 0; j < nq; ++j) {
+        // bi-unit triangle point (p, q) and weight (its area is 2), mapped to the face
+        const double p = 0.5 * (1.0 + ya[i]) * (1.0 - yb[j]) - 1.0, q = yb[j];
+        const double w = wya[i] * wyb[j] * 0.5 * (area / 2.0);  // reference-face area element
+        double x[3];
+        for (int d = 0; d < 3; ++d) x[d] = A[d] + 0.5 * (p + 1.0) * e1[d] + 0.5 * (q + 1.0) * e2[d];
+        nodal_row(x[0], x[1], x[2], -1, Lv.data());
+        for (int a = 0; a < Nfp; ++a)
+          for (int c = 0; c < Nfp; ++c) R.Mf[f][size_t(a) * Nfp + c] += w * Lv[R.fmask[f][a]] * Lv[R.fmask[f][c]];
+      }
+  }
+  // Jacobi pieces
+  const int pa[6] = {0, 0, 0, 1, 1, 2}, pb[6] = {0, 1, 2, 1, 2, 2};
+  for (int q = 0; q < 6; ++q) {
+    R.dS[q].assign(Np, 0.0);
+    for (int i = 0; i < Np; ++i) {  // (D_a^T M D_b)[i][i]
+      double a = 0.0;
+      for (int k = 0; k < Np; ++k)
+        for (int m = 0; m < Np; ++m)
+          a += R.D[pa[q]][size_t(k) * Np + i] * R.M[size_t(k) * Np + m] * R.D[pb[q]][size_t(m) * Np + i];
+      R.dS[q][i] = a;
+    }
+  }
+  R.dM.resize(Np);
+  for (int i = 0; i < Np; ++i) R.dM[i] = R.M[size_t(i) * Np + i];
+  for (int b = 0; b < 3; ++b)
+    for (int f = 0; f < 4; ++f) {
+      R.fc[b][f].assign(Nfp, 0.0);
+      for (int j = 0; j < Nfp; ++j) {
+        double a = 0.0;
+        for (int l = 0; l < Nfp; ++l)
+          a += R.Mf[f][size_t(j) * Nfp + l] * R.D[b][size_t(R.fmask[f][l]) * Np + R.fmask[f][j]];
+        R.fc[b][f][j] = a;
+      }
+    }
+  return R;
+}
+
+// Device copies of one precision's reference data (offsets in one buffer):
+// D[3] (Np^2 each), B[3], M, Mf[4] (Nfp^2 each), dS[6] (Np each), dM (Np), fc[3][4] (Nfp each).
+struct OpsLayout {
+  int D[3], B[3], M, Mf[4], dS[6], dM, fc[3][4], total;
+};
+OpsLayout ops_layout(int Np, int Nfp) {
+  OpsLayout L{};
+  int o = 0;
+  for (int b = 0; b < 3; ++b) L.D[b] = o, o += Np * Np;
+  for (int b = 0; b < 3; ++b) L.B[b] = o, o += Np * Np;
+  L.M = o, o += Np * Np;
+  for (int f = 0; f < 4; ++f) L.Mf[f] = o, o += Nfp * Nfp;
+  for (int q = 0; q < 6; ++q) L.dS[q] = o, o += Np;
+  L.dM = o, o += Np;
+  for (int b = 0; b < 3; ++b)
+    for (int f = 0; f < 4; ++f) L.fc[b][f] = o, o += Nfp;
+  L.total = o;
+  return L;
+}
+
+// Geometry per element, kGeo words: J, G (rr, rs, rt, ss, st, tt), then per face
+// f at 7 + 8 f: n.grad r_b of the element (3), n.grad r_b of the neighbour (3, the
+// element's outward n), sJ (physical over reference face area), tau.
+constexpr int kGeo = 40;
+
+}  // namespace tet
+}  // namespace dgx
+
+struct dg_tet_mesh {
+  int N = 0, Np = 0, Nfp = 0;
+  int64_t K = 0;
+  dgx::tet::TetRef ref;
+  dgx::tet::OpsLayout L{};
+  double* ops64 = nullptr;
+  float* ops32 = nullptr;
+  int* fmask = nullptr;    // [4][Nfp]
+  double* geo64 = nullptr;  // [K][kGeo]
+  float* geo32 = nullptr;
+  int* conn = nullptr;     // [K][4]: neighbour element, or -1 - boundary tag
+  int* mapP = nullptr;     // [K][4][Nfp]: the neighbour's volume node at face node j
+  double* xyz = nullptr;   // [3][K][Np] node coordinates
+  // Jacobi-PCG workspace (grown on demand)
+  double* work = nullptr;
+  size_t work_cap = 0;
+};
+
+namespace dgx {
+namespace tet {
+
+constexpr int kGroup = 64;  // threads per element (Np <= 56 at N = 5)
+constexpr int kGroups = 4;  // elements per block
+
+// A u for B right-hand sides ([B][K][Np]); one element per 64-thread group.
+template <typename T, bool HELM>
+__global__ void __launch_bounds__(kGroup * kGroups) tet_apply(int N, int64_t K, int64_t nE, OpsLayout L,
+                                                              const T* __restrict__ ops, const int* __restrict__ fmask,
+                                                              const T* __restrict__ geo, const int* __restrict__ conn,
+                                                              const int* __restrict__ mapP, T lambda,
+                                                              const T* __restrict__ u, T* __restrict__ Au) {
+  const int Np = (N + 1) * (N + 2) * (N + 3) / 6, Nfp = (N + 1) * (N + 2) / 2;
+  constexpr int NPM = 56, NFM = 21;  // N <= 5
+  __shared__ T su[kGroups][5][NPM];       // own values, then the four neighbours'
+  __shared__ T sw[kGroups][3][NPM];       // w_a = sum_b G_ab D_b u
+  __shared__ T sF1[kGroups][4][NFM], sF2[kGroups][4][NFM];
+  __shared__ T sjm[kGroups][4][NFM], sav[kGroups][4][NFM];
+  const int grp = threadIdx.x / kGroup, t = threadIdx.x % kGroup;
+  const T* D0 = ops + L.D[0];
+  const T* D1 = ops + L.D[1];
+  const T* D2 = ops + L.D[2];
+  for (int64_t base = int64_t(blockIdx.x) * kGroups; base < nE; base += int64_t(gridDim.x) * kGroups) {
+    const int64_t be = base + grp;
+    const bool live = be < nE;
+    const int64_t e = live ? be % K : 0, boff = live ? be - e : 0;
+    const T* g = geo + e * kGeo;
+    if (live) {
+      for (int m = t; m < Np; m += kGroup) su[grp][0][m] = u[be * Np + m];
+      for (int f = 0; f < 4; ++f) {
+        const int c = conn[4 * e + f];
+        if (c >= 0)
+          for (int m = t; m < Np; m += kGroup) su[grp][1 + f][m] = u[(boff + c) * Np + m];
+      }
+    }
+    __syncthreads();
+    if (live && t < Np) {
+      T ub[3] = {T(0), T(0), T(0)};
+      for (int m = 0; m < Np; ++m) {
+        const T um = su[grp][0][m];
+        ub[0] += D0[t * Np + m] * um;
+        ub[1] += D1[t * Np + m] * um;
+        ub[2] += D2[t * Np + m] * um;
+      }
+      const T G[6] = {g[1], g[2], g[3], g[4], g[5], g[6]};  // rr rs rt ss st tt
+      sw[grp][0][t] = G[0] * ub[0] + G[1] * ub[1] + G[2] * ub[2];
+      sw[grp][1][t] = G[1] * ub[0] + G[3] * ub[1] + G[4] * ub[2];
+      sw[grp][2][t] = G[2] * ub[0] + G[4] * ub[1] + G[5] * ub[2];
+    }
+    // face nodes: jumps and averages
+    if (live)
+      for (int idx = t; idx < 4 * Nfp; idx += kGroup) {
+        const int f = idx / Nfp, j = idx - f * Nfp;
+        const int k = fmask[f * Nfp + j];
+        const int c = conn[4 * e + f];
+        const T* gf = g + 7 + 8 * f;
+        T jm = T(0), av = T(0);
+        if (c >= 0 || c == -2) {
+          T db[3] = {T(0), T(0), T(0)};
+          for (int m = 0; m < Np; ++m) {
+            const T um = su[grp][0][m];
+            db[0] += D0[k * Np + m] * um;
+            db[1] += D1[k * Np + m] * um;
+            db[2] += D2[k * Np + m] * um;
+          }
+          const T dnm = gf[0] * db[0] + gf[1] * db[1] + gf[2] * db[2];
+          if (c >= 0) {
+            const int kp = mapP[(e * 4 + f) * Nfp + j];
+            T pb[3] = {T(0), T(0), T(0)};
+            for (int m = 0; m < Np; ++m) {
+              const T um = su[grp][1 + f][m];
+              pb[0] += D0[kp * Np + m] * um;
+              pb[1] += D1[kp * Np + m] * um;
+              pb[2] += D2[kp * Np + m] * um;
+            }
+            const T dnp = gf[3] * pb[0] + gf[4] * pb[1] + gf[5] * pb[2];
+            jm = su[grp][1 + f][kp] - su[grp][0][k];
+            av = T(0.5) * (dnm + dnp);
+          } else {  // Dirichlet ghost: u+ = -u-, grad u+ = grad u-
+            jm = T(-2) * su[grp][0][k];
+            av = dnm;
+          }
+        }
+        sjm[grp][f][j] = jm;
+        sav[grp][f][j] = av;
+      }
+    __syncthreads();
+    if (live)
+      for (int idx = t; idx < 4 * Nfp; idx += kGroup) {
+        const int f = idx / Nfp, j = idx - f * Nfp;
+        const T* gf = g + 7 + 8 * f;
+        const T sJ = gf[6], tau = gf[7];
+        const T* Mf = ops + L.Mf[f];
+        T m1 = T(0), m2 = T(0);
+        for (int l = 0; l < Nfp; ++l) {
+          const T mf = Mf[j * Nfp + l];
+          m1 += mf * (sav[grp][f][l] + tau * sjm[grp][f][l]);
+          m2 += mf * sjm[grp][f][l];
+        }
+        sF1[grp][f][j] = -sJ * m1;
+        sF2[grp][f][j] = T(0.5) * sJ * m2;
+      }
+    __syncthreads();
+    if (live && t < Np) {
+      const T J = g[0];
+      T o = T(0);
+      for (int m = 0; m < Np; ++m)
+        o += ops[L.B[0] + t * Np + m] * sw[grp][0][m] + ops[L.B[1] + t * Np + m] * sw[grp][1][m] +
+             ops[L.B[2] + t * Np + m] * sw[grp][2][m];
+      o *= J;
+      if (HELM) {
+        T a = T(0);
+        for (int m = 0; m < Np; ++m) a += ops[L.M + t * Np + m] * su[grp][0][m];
+        o += lambda * J * a;
+      }
+      for (int f = 0; f < 4; ++f) {
+        const T* gf = g + 7 + 8 * f;
+        for (int j = 0; j < Nfp; ++j) {
+          const int k = fmask[f * Nfp + j];
+          const T F2 = sF2[grp][f][j];
+          o += (gf[0] * D0[k * Np + t] + gf[1] * D1[k * Np + t] + gf[2] * D2[k * Np + t]) * F2;
+          if (k == t) o += sF1[grp][f][j];
+        }
+      }
+      Au[be * Np + t] = o;
+    }
+    __syncthreads();
+  }
+}
+
+// diag(A) per node of one right-hand side ([K][Np], FP64).
+__global__ void tet_diag(int N, int64_t K, OpsLayout L, const double* __restrict__ ops, const int* __restrict__ fmask,
+                         const double* __restrict__ geo, const int* __restrict__ conn, double lambda,
+                         double* __restrict__ diag) {
+  const int Np = (N + 1) * (N + 2) * (N + 3) / 6, Nfp = (N + 1) * (N + 2) / 2;
+  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= K * Np) return;
+  const int64_t e = idx / Np;
+  const int i = int(idx - e * Np);
+  const double* g = geo + e * kGeo;
+  const double J = g[0];
+  const double c[6] = {1, 2, 2, 1, 2, 1};
+  double d = 0.0;
+  for (int q = 0; q < 6; ++q) d += c[q] * g[1 + q] * ops[L.dS[q] + i];
+  d = J * d + lambda * J * ops[L.dM + i];
+  for (int f = 0; f < 4; ++f) {
+    const int cf = conn[4 * e + f];
+    if (!(cf >= 0 || cf == -2)) continue;
+    const double w = cf >= 0 ? 1.0 : 2.0;
+    const double* gf = g + 7 + 8 * f;
+    for (int j = 0; j < Nfp; ++j) {
+      if (fmask[f * Nfp + j] != i) continue;
+      const double a1 = gf[6] * (gf[0] * ops[L.fc[0][f] + j] + gf[1] * ops[L.fc[1][f] + j] + gf[2] * ops[L.fc[2][f] + j]);
+      const double a2 = gf[6] * ops[L.Mf[f] + j * Nfp + j];
+      d += w * (-a1 + gf[7] * a2);
+    }
+  }
+  diag[idx] = d;
+}
+
+// b = J M f - L(g) for B right-hand sides: L(g)_i = sum over Dirichlet faces of
+// (n.grad l_i, g) - 2 tau (l_i, g), g the nodal trace.
+__global__ void tet_rhs(int N, int64_t K, int64_t nE, OpsLayout L, const double* __restrict__ ops,
+                        const int* __restrict__ fmask, const double* __restrict__ geo, const int* __restrict__ conn,
+                        const double* __restrict__ f, const double* __restrict__ gd, double* __restrict__ b) {
+  const int Np = (N + 1) * (N + 2) * (N + 3) / 6, Nfp = (N + 1) * (N + 2) / 2;
+  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= nE * Np) return;
+  const int64_t be = idx / Np;
+  const int i = int(idx - be * Np);
+  const int64_t e = be % K;
+  const double* g = geo + e * kGeo;
+  double o = 0.0;
+  for (int m = 0; m < Np; ++m) o += ops[L.M + i * Np + m] * f[be * Np + m];
+  o *= g[0];
+  for (int fc = 0; fc < 4; ++fc) {
+    if (conn[4 * e + fc] != -2) continue;
+    const double* gf = g + 7 + 8 * fc;
+    for (int j = 0; j < Nfp; ++j) {  // (Mf g)_j, then its two uses
+      double mg = 0.0;
+      for (int l = 0; l < Nfp; ++l) mg += ops[L.Mf[fc] + j * Nfp + l] * gd[be * Np + fmask[fc * Nfp + l]];
+      mg *= gf[6];
+      const int k = fmask[fc * Nfp + j];
+      const double dn = gf[0] * ops[L.D[0] + k * Np + i] + gf[1] * ops[L.D[1] + k * Np + i] +
+                        gf[2] * ops[L.D[2] + k * Np + i];
+      o -= dn * mg;
+      if (k == i) o += 2.0 * gf[7] * mg;
+    }
+  }
+  b[idx] = o;
+}
+
+// --- Jacobi-PCG vector kernels ([B][n] vectors, fixed-order reductions)
+constexpr int kRB = 256;  // reduction blocks per right-hand side
+
+__global__ void k_dot2(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
+                       double* __restrict__ partial) {
+  __shared__ double sh[256];
+  const int rhs = blockIdx.y;
+  const double* x = a + int64_t(rhs) * n;
+  const double* y = b + int64_t(rhs) * n;
+  double s = 0.0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    s += x[i] * y[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[rhs * kRB + blockIdx.x] = sh[0];
+}
+__global__ void k_sum(const double* __restrict__ partial, double* __restrict__ out) {
+  __shared__ double sh[kRB];
+  sh[threadIdx.x] = partial[blockIdx.x * kRB + threadIdx.x];
+  __syncthreads();
+  for (int w = kRB / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = sh[0];
+}
+// y[rhs] = a[rhs] * x[rhs] + y[rhs] (coefficients per right-hand side, device)
+__global__ void k_axpy(int64_t n, int B, const double* __restrict__ coef, int sign, const double* __restrict__ x,
+                       double* __restrict__ y) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n * B; i += int64_t(gridDim.x) * blockDim.x) {
+    const double a = coef[i / n];
+    y[i] += sign * a * x[i];
+  }
+}
+// p = z + beta p
+__global__ void k_xpay(int64_t n, int B, const double* __restrict__ beta, const double* __restrict__ z,
+                       double* __restrict__ p) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n * B; i += int64_t(gridDim.x) * blockDim.x)
+    p[i] = z[i] + beta[i / n] * p[i];
+}
+// z = dinv r (dinv shared by the right-hand sides); r = b - Ax when ax is given
+__global__ void k_jac(int64_t n, int B, const double* __restrict__ dinv, const double* __restrict__ b,
+                      const double* __restrict__ ax, double* __restrict__ r, double* __restrict__ z) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n * B; i += int64_t(gridDim.x) * blockDim.x) {
+    const double ri = ax ? b[i] - ax[i] : r[i];
+    r[i] = ri;
+    z[i] = dinv[i % n] * ri;
+  }
+}
+__global__ void k_recip(int64_t n, double* __restrict__ d) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    d[i] = 1.0 / d[i];
+}
+inline unsigned grid_of(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  return unsigned(std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16)));
+}
+
+}  // namespace tet
+}  // namespace dgx
+
+namespace dgx {
+namespace tet {
+
+dg_status fail(cudaError_t e, const char* what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA;
+}
+
+template <typename T>
+cudaError_t upload(T** dst, const std::vector<T>& v) {
+  cudaError_t e = cudaMalloc(dst, std::max<size_t>(1, v.size()) * sizeof(T));
+  if (e == cudaSuccess && !v.empty()) e = cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+  return e;
+}
+
+}  // namespace tet
+}  // namespace dgx
+
+using namespace dgx;
+using namespace dgx::tet;
+
+namespace {
+template <typename T>
+cudaError_t tet_apply_launch(const dg_tet_mesh* m, int B, double lambda, const T* u, T* Au, cudaStream_t st) {
+  const bool f64 = sizeof(T) == 8;
+  const T* ops = f64 ? reinterpret_cast<const T*>(m->ops64) : reinterpret_cast<const T*>(m->ops32);
+  const T* geo = f64 ? reinterpret_cast<const T*>(m->geo64) : reinterpret_cast<const T*>(m->geo32);
+  const int64_t nE = int64_t(B) * m->K;
+  const unsigned grid = unsigned(std::min<int64_t>((nE + kGroups - 1) / kGroups, 152 * 32));
+  if (lambda != 0.0)
+    tet_apply<T, true><<<grid, kGroup * kGroups, 0, st>>>(m->N, m->K, nE, m->L, ops, m->fmask, geo, m->conn,
+                                                          m->mapP, T(lambda), u, Au);
+  else
+    tet_apply<T, false><<<grid, kGroup * kGroups, 0, st>>>(m->N, m->K, nE, m->L, ops, m->fmask, geo, m->conn,
+                                                           m->mapP, T(0), u, Au);
+  note_launch();
+  return cudaGetLastError();
+}
+}  // namespace
+
+extern "C" {
+
+dg_status dg_tet_mesh_destroy(dg_tet_mesh* m) {
+  if (!m) return DG_OK;
+  for (void* p : {static_cast<void*>(m->ops64), static_cast<void*>(m->ops32), static_cast<void*>(m->fmask),
+                  static_cast<void*>(m->geo64), static_cast<void*>(m->geo32), static_cast<void*>(m->conn),
+                  static_cast<void*>(m->mapP), static_cast<void*>(m->xyz), static_cast<void*>(m->work)})
+    cudaFree(p);
+  delete m;
+  return DG_OK;
+}
+
+dg_status dg_tet_mesh_setup(int N, int64_t Nv, const double* VX, const double* VY, const double* VZ, int64_t K,
+                            const int32_t* EToV, const int8_t* bc, void* stream, dg_tet_mesh** out) {
+  (void)stream;
+  if (!out || !VX || !VY || !VZ || !EToV || !bc) { set_error("NULL argument"); return DG_ERR_ARG; }
+  *out = nullptr;
+  if (N < 1 || N > kMaxTetN) { set_error("tetrahedral degree N must be in 1..5"); return DG_ERR_ARG; }
+  if (K < 1 || Nv < 4 || K * np3(N) >= (int64_t(1) << 31)) { set_error("bad tetrahedral mesh size"); return DG_ERR_ARG; }
+  for (int64_t i = 0; i < 4 * K; ++i)
+    if (EToV[i] < 0 || EToV[i] >= Nv) { set_error("EToV index out of range"); return DG_ERR_MESH; }
+  dg_tet_mesh* m = new dg_tet_mesh();
+  try {
+    m->N = N;
+    m->K = K;
+    m->ref = build_tet(N);
+  } catch (const std::exception& ex) {
+    delete m;
+    set_error(ex.what());
+    return DG_ERR_ARG;
+  }
+  const TetRef& R = m->ref;
+  const int Np = R.Np, Nfp = R.Nfp;
+  m->Np = Np;
+  m->Nfp = Nfp;
+  // element geometry
+  std::vector<double> jinv(size_t(K) * 9), Jd(K), vol(K), nrm(size_t(K) * 12), area(size_t(K) * 4);
+  for (int64_t e = 0; e < K; ++e) {
+    double P[4][3];
+    for (int v = 0; v < 4; ++v) {
+      const int32_t g = EToV[4 * e + v];
+      P[v][0] = VX[g], P[v][1] = VY[g], P[v][2] = VZ[g];
+    }
+    double A[3][3];  // columns x_r, x_s, x_t
+    for (int d = 0; d < 3; ++d)
+      for (int c = 0; c < 3; ++c) A[d][c] = 0.5 * (P[c + 1][d] - P[0][d]);
+    const double det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) -
+                       A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+                       A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+    if (!(det > 0)) {
+      dg_tet_mesh_destroy(m);
+      set_error("tetrahedron with non-positive Jacobian");
+      return DG_ERR_MESH;
+    }
+    // inverse: rows grad r, grad s, grad t
+    double* I = &jinv[size_t(e) * 9];
+    I[0] = (A[1][1] * A[2][2] - A[1][2] * A[2][1]) / det;
+    I[1] = (A[0][2] * A[2][1] - A[0][1] * A[2][2]) / det;
+    I[2] = (A[0][1] * A[1][2] - A[0][2] * A[1][1]) / det;
+    I[3] = (A[1][2] * A[2][0] - A[1][0] * A[2][2]) / det;
+    I[4] = (A[0][0] * A[2][2] - A[0][2] * A[2][0]) / det;
+    I[5] = (A[0][2] * A[1][0] - A[0][0] * A[1][2]) / det;
+    I[6] = (A[1][0] * A[2][1] - A[1][1] * A[2][0]) / det;
+    I[7] = (A[0][1] * A[2][0] - A[0][0] * A[2][1]) / det;
+    I[8] = (A[0][0] * A[1][1] - A[0][1] * A[1][0]) / det;
+    Jd[e] = det;
+    vol[e] = det * 4.0 / 3.0;
+    double cen[3] = {0, 0, 0};
+    for (int v = 0; v < 4; ++v)
+      for (int d = 0; d < 3; ++d) cen[d] += 0.25 * P[v][d];
+    for (int f = 0; f < 4; ++f) {
+      const double* a = P[kFaceVerts[f][0]];
+      const double* b = P[kFaceVerts[f][1]];
+      const double* c = P[kFaceVerts[f][2]];
+      const double u1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, u2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+      double n[3] = {u1[1] * u2[2] - u1[2] * u2[1], u1[2] * u2[0] - u1[0] * u2[2], u1[0] * u2[1] - u1[1] * u2[0]};
+      const double len = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+      for (int d = 0; d < 3; ++d) n[d] /= len;
+      if (n[0] * (a[0] - cen[0]) + n[1] * (a[1] - cen[1]) + n[2] * (a[2] - cen[2]) < 0)
+        for (int d = 0; d < 3; ++d) n[d] = -n[d];
+      for (int d = 0; d < 3; ++d) nrm[size_t(e) * 12 + 3 * f + d] = n[d];
+      area[size_t(e) * 4 + f] = 0.5 * len;
+    }
+  }
+  // face connectivity by the sorted vertex triple
+  std::vector<int> nbE(size_t(K) * 4, -1), nbF(size_t(K) * 4, -1);
+  {
+    std::map<std::array<int32_t, 3>, std::pair<int64_t, int>> open;
+    for (int64_t e = 0; e < K; ++e)
+      for (int f = 0; f < 4; ++f) {
+        std::array<int32_t, 3> key = {EToV[4 * e + kFaceVerts[f][0]], EToV[4 * e + kFaceVerts[f][1]],
+                                      EToV[4 * e + kFaceVerts[f][2]]};
+        std::sort(key.begin(), key.end());
+        auto it = open.find(key);
+        if (it == open.end()) {
+          open[key] = {e, f};
+        } else {
+          const int64_t e2 = it->second.first;
+          const int f2 = it->second.second;
+          nbE[4 * e + f] = int(e2), nbF[4 * e + f] = f2;
+          nbE[4 * e2 + f2] = int(e), nbF[4 * e2 + f2] = f;
+          open.erase(it);
+        }
+      }
+  }
+  std::vector<int> conn(size_t(K) * 4);
+  for (int64_t e = 0; e < K; ++e)
+    for (int f = 0; f < 4; ++f) {
+      if (nbE[4 * e + f] >= 0) {
+        conn[4 * e + f] = nbE[4 * e + f];
+      } else {
+        const int tag = bc[4 * e + f];
+        if (tag != 1 && tag != 2) {
+          dg_tet_mesh_destroy(m);
+          set_error("a face without a neighbour needs boundary tag 1 (Dirichlet) or 2 (Neumann)");
+          return DG_ERR_MESH;
+        }
+        conn[4 * e + f] = -1 - tag;
+      }
+    }
+  // node coordinates and the neighbour's node at each face node
+  std::vector<double> xyz(size_t(3) * K * Np);
+  for (int64_t e = 0; e < K; ++e) {
+    const int32_t* ev = &EToV[4 * e];
+    for (int k = 0; k < Np; ++k) {
+      const double w[3] = {0.5 * (R.r[k] + 1.0), 0.5 * (R.s[k] + 1.0), 0.5 * (R.t[k] + 1.0)};
+      const double* V[3] = {VX, VY, VZ};
+      for (int d = 0; d < 3; ++d) {
+        const double x0 = V[d][ev[0]];
+        xyz[(size_t(d) * K + e) * Np + k] =
+            x0 + w[0] * (V[d][ev[1]] - x0) + w[1] * (V[d][ev[2]] - x0) + w[2] * (V[d][ev[3]] - x0);
+      }
+    }
+  }
+  std::vector<int> mapP(size_t(K) * 4 * Nfp, -1);
+  for (int64_t e = 0; e < K; ++e)
+    for (int f = 0; f < 4; ++f) {
+      const int e2 = nbE[4 * e + f], f2 = nbF[4 * e + f];
+      if (e2 < 0) continue;
+      const double hscale = std::cbrt(vol[e]);
+      for (int j = 0; j < Nfp; ++j) {
+        const int k = R.fmask[f][j];
+        int best = -1;
+        for (int j2 = 0; j2 < Nfp; ++j2) {
+          const int k2 = R.fmask[f2][j2];
+          double d2 = 0.0;
+          for (int d = 0; d < 3; ++d) {
+            const double dx = xyz[(size_t(d) * K + e) * Np + k] - xyz[(size_t(d) * K + e2) * Np + k2];
+            d2 += dx * dx;
+          }
+          if (std::sqrt(d2) < 1e-8 * hscale) best = k2;
+        }
+        if (best < 0) {
+          dg_tet_mesh_destroy(m);
+          set_error("non-conforming tetrahedral faces (face nodes do not match)");
+          return DG_ERR_MESH;
+        }
+        mapP[(size_t(e) * 4 + f) * Nfp + j] = best;
+      }
+    }
+  // per-element geometry words
+  const double cpen = double((N + 1) * (N + 3)) / 3.0;
+  std::vector<double> geo(size_t(K) * kGeo, 0.0);
+  for (int64_t e = 0; e < K; ++e) {
+    double* g = &geo[size_t(e) * kGeo];
+    const double* I = &jinv[size_t(e) * 9];
+    g[0] = Jd[e];
+    const int pa[6] = {0, 0, 0, 1, 1, 2}, pb[6] = {0, 1, 2, 1, 2, 2};
+    for (int q = 0; q < 6; ++q)
+      g[1 + q] = I[3 * pa[q]] * I[3 * pb[q]] + I[3 * pa[q] + 1] * I[3 * pb[q] + 1] + I[3 * pa[q] + 2] * I[3 * pb[q] + 2];
+    for (int f = 0; f < 4; ++f) {
+      double* gf = g + 7 + 8 * f;
+      const double* n = &nrm[size_t(e) * 12 + 3 * f];
+      for (int b = 0; b < 3; ++b) gf[b] = n[0] * I[3 * b] + n[1] * I[3 * b + 1] + n[2] * I[3 * b + 2];
+      const int e2 = nbE[4 * e + f];
+      if (e2 >= 0) {
+        const double* I2 = &jinv[size_t(e2) * 9];
+        for (int b = 0; b < 3; ++b) gf[3 + b] = n[0] * I2[3 * b] + n[1] * I2[3 * b + 1] + n[2] * I2[3 * b + 2];
+      }
+      gf[6] = area[size_t(e) * 4 + f] / R.face_area[f];
+      double ih = area[size_t(e) * 4 + f] / vol[e];
+      if (e2 >= 0) ih = std::max(ih, area[size_t(e2) * 4 + nbF[4 * e + f]] / vol[e2]);
+      gf[7] = cpen * ih;
+    }
+  }
+  // reference data, both precisions
+  m->L = ops_layout(Np, Nfp);
+  std::vector<double> ops(m->L.total, 0.0);
+  for (int b = 0; b < 3; ++b) {
+    std::copy(R.D[b].begin(), R.D[b].end(), ops.begin() + m->L.D[b]);
+    std::copy(R.Bm[b].begin(), R.Bm[b].end(), ops.begin() + m->L.B[b]);
+  }
+  std::copy(R.M.begin(), R.M.end(), ops.begin() + m->L.M);
+  for (int f = 0; f < 4; ++f) std::copy(R.Mf[f].begin(), R.Mf[f].end(), ops.begin() + m->L.Mf[f]);
+  for (int q = 0; q < 6; ++q) std::copy(R.dS[q].begin(), R.dS[q].end(), ops.begin() + m->L.dS[q]);
+  std::copy(R.dM.begin(), R.dM.end(), ops.begin() + m->L.dM);
+  for (int b = 0; b < 3; ++b)
+    for (int f = 0; f < 4; ++f) std::copy(R.fc[b][f].begin(), R.fc[b][f].end(), ops.begin() + m->L.fc[b][f]);
+  std::vector<int> fm(size_t(4) * Nfp);
+  for (int f = 0; f < 4; ++f)
+    for (int j = 0; j < Nfp; ++j) fm[size_t(f) * Nfp + j] = R.fmask[f][j];
+  const std::vector<float> ops32(ops.begin(), ops.end()), geo32(geo.begin(), geo.end());
+  cudaError_t ce = upload(&m->ops64, ops);
+  if (ce == cudaSuccess) ce = upload(&m->ops32, ops32);
+  if (ce == cudaSuccess) ce = upload(&m->fmask, fm);
+  if (ce == cudaSuccess) ce = upload(&m->geo64, geo);
+  if (ce == cudaSuccess) ce = upload(&m->geo32, geo32);
+  if (ce == cudaSuccess) ce = upload(&m->conn, conn);
+  if (ce == cudaSuccess) ce = upload(&m->mapP, mapP);
+  if (ce == cudaSuccess) ce = upload(&m->xyz, xyz);
+  if (ce != cudaSuccess) {
+    dg_tet_mesh_destroy(m);
+    return fail(ce, "dg_tet_mesh_setup");
+  }
+  *out = m;
+  return DG_OK;
+}
+
+dg_status dg_tet_mesh_info(const dg_tet_mesh* m, int* N, int64_t* K, int* Np) {
+  if (!m) { set_error("NULL mesh"); return DG_ERR_ARG; }
+  if (N) *N = m->N;
+  if (K) *K = m->K;
+  if (Np) *Np = m->Np;
+  return DG_OK;
+}
+
+dg_status dg_tet_mesh_nodes(const dg_tet_mesh* m, double* x, double* y, double* z, void* stream) {
+  if (!m || !x || !y || !z) { set_error("NULL argument"); return DG_ERR_ARG; }
+  const size_t n = size_t(m->K) * m->Np * sizeof(double);
+  cudaStream_t st = (cudaStream_t)stream;
+  double* dst[3] = {x, y, z};
+  for (int d = 0; d < 3; ++d) {
+    const cudaError_t e = cudaMemcpyAsync(dst[d], m->xyz + size_t(d) * m->K * m->Np, n, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return fail(e, "dg_tet_mesh_nodes");
+  }
+  return DG_OK;
+}
+
+
+
+dg_status dg_tet_apply(const dg_tet_mesh* m, dg_prec prec, int B, double lambda, const void* u, void* Au,
+                       void* stream) {
+  if (!m || !u || !Au) { set_error("NULL argument"); return DG_ERR_ARG; }
+  if (B < 1 || B > DG_MAX_BATCH) { set_error("batch must be in 1..64"); return DG_ERR_ARG; }
+  if (!std::isfinite(lambda) || lambda < 0) { set_error("lambda must be finite and >= 0"); return DG_ERR_ARG; }
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e;
+  if (prec == DG_F32)
+    e = tet_apply_launch<float>(m, B, lambda, static_cast<const float*>(u), static_cast<float*>(Au), st);
+  else if (prec == DG_F64 || prec == DG_F64_DFMA)
+    e = tet_apply_launch<double>(m, B, lambda, static_cast<const double*>(u), static_cast<double*>(Au), st);
+  else {
+    set_error("unknown precision");
+    return DG_ERR_ARG;
+  }
+  return e == cudaSuccess ? DG_OK : fail(e, "dg_tet_apply");
+}
+
+dg_status dg_tet_rhs(const dg_tet_mesh* m, int B, const double* f, const double* g, double* b, void* stream) {
+  if (!m || !f || !g || !b) { set_error("NULL argument"); return DG_ERR_ARG; }
+  if (B < 1 || B > DG_MAX_BATCH) { set_error("batch must be in 1..64"); return DG_ERR_ARG; }
+  const int64_t nE = int64_t(B) * m->K, n = nE * m->Np;
+  tet_rhs<<<unsigned((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(m->N, m->K, nE, m->L, m->ops64, m->fmask,
+                                                                       m->geo64, m->conn, f, g, b);
+  note_launch();
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? DG_OK : fail(e, "dg_tet_rhs");
+}
+
+dg_status dg_tet_pcg_jacobi_solve(dg_tet_mesh* m, int B, double lambda, double tol, int max_iter, const double* b,
+                                  double* x, dg_solve_info* info, void* stream) {
+  if (!m || !b || !x) { set_error("NULL argument"); return DG_ERR_ARG; }
+  if (B < 1 || B > DG_MAX_BATCH) { set_error("batch must be in 1..64"); return DG_ERR_ARG; }
+  if (!(tol > 0.0) || max_iter < 0) { set_error("tol must be > 0 and max_iter >= 0"); return DG_ERR_ARG; }
+  if (!std::isfinite(lambda) || lambda < 0) { set_error("lambda must be finite and >= 0"); return DG_ERR_ARG; }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = m->K * m->Np;
+  const size_t nt = size_t(n) * B;
+  // workspace: r, z, p, Ap (nt each), dinv (n), partials (B kRB), scalars (4 B)
+  const size_t words = 4 * nt + size_t(n) + size_t(B) * kRB + 4 * size_t(B);
+  if (m->work_cap < words) {
+    cudaFree(m->work);
+    m->work = nullptr;
+    m->work_cap = 0;
+    const cudaError_t e = cudaMalloc(&m->work, words * sizeof(double));
+    if (e != cudaSuccess) return fail(e, "dg_tet_pcg_jacobi_solve");
+    m->work_cap = words;
+  }
+  double *r = m->work, *z = r + nt, *p = z + nt, *Ap = p + nt, *dinv = Ap + nt, *part = dinv + n, *sc = part + size_t(B) * kRB;
+  double* coefd = sc + B;  // B coefficients uploaded per step
+  const dim3 rg(kRB, unsigned(B));
+  const unsigned gv = grid_of(int64_t(nt)), gn = grid_of(n);
+  std::vector<double> hb(B), hrz(B), hd(B), coef(B), active(B, 1.0);
+  auto dot = [&](const double* a, const double* c, double* host) -> cudaError_t {
+    k_dot2<<<rg, 256, 0, st>>>(n, a, c, part); note_launch();
+    k_sum<<<unsigned(B), kRB, 0, st>>>(part, sc); note_launch();
+    cudaError_t e = cudaMemcpyAsync(host, sc, sizeof(double) * B, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e;
+  };
+  auto setc = [&](const std::vector<double>& c) {
+    return cudaMemcpyAsync(coefd, c.data(), sizeof(double) * B, cudaMemcpyHostToDevice, st);
+  };
+#define TCK(expr)                                          \
+  do {                                                     \
+    const cudaError_t e_ = (expr);                         \
+    if (e_ != cudaSuccess) return fail(e_, "dg_tet_pcg_jacobi_solve"); \
+  } while (0)
+  tet_diag<<<unsigned((n + 255) / 256), 256, 0, st>>>(m->N, m->K, m->L, m->ops64, m->fmask, m->geo64, m->conn, lambda,
+                                                      dinv);
+  note_launch();
+  k_recip<<<gn, 256, 0, st>>>(n, dinv); note_launch();
+  TCK(tet_apply_launch<double>(m, B, lambda, x, Ap, st));
+  k_jac<<<gv, 256, 0, st>>>(n, B, dinv, b, Ap, r, z); note_launch();
+  TCK(cudaMemcpyAsync(p, z, nt * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  TCK(dot(b, b, hb.data()));
+  std::vector<double> hrr(B);
+  TCK(dot(r, r, hrr.data()));
+  TCK(dot(r, z, hrz.data()));
+  for (int k = 0; k < B; ++k) {
+    hb[k] = std::sqrt(hb[k]);
+    if (hb[k] == 0.0 || std::sqrt(hrr[k]) <= tol * hb[k]) active[k] = 0.0;
+  }
+  int it = 0;
+  dg_status status = DG_OK;
+  std::vector<int> iters(B, 0);
+  auto any_active = [&]() {
+    for (int k = 0; k < B; ++k)
+      if (active[k] != 0.0) return true;
+    return false;
+  };
+  while (any_active() && it < max_iter) {
+    TCK(tet_apply_launch<double>(m, B, lambda, p, Ap, st));
+    TCK(dot(p, Ap, hd.data()));
+    for (int k = 0; k < B; ++k) {
+      if (active[k] != 0.0 && !(hd[k] > 0.0)) {
+        status = DG_ERR_BREAKDOWN;
+        active[k] = 0.0;
+      }
+      coef[k] = active[k] != 0.0 ? hrz[k] / hd[k] : 0.0;
+    }
+    TCK(setc(coef));
+    k_axpy<<<gv, 256, 0, st>>>(n, B, coefd, 1, p, x); note_launch();
+    k_axpy<<<gv, 256, 0, st>>>(n, B, coefd, -1, Ap, r); note_launch();
+    ++it;
+    TCK(dot(r, r, hrr.data()));
+    for (int k = 0; k < B; ++k)
+      if (active[k] != 0.0) {
+        iters[k] = it;
+        if (std::sqrt(hrr[k]) <= tol * hb[k]) active[k] = 0.0;
+      }
+    if (!any_active() || it >= max_iter) break;
+    k_jac<<<gv, 256, 0, st>>>(n, B, dinv, nullptr, nullptr, r, z); note_launch();
+    std::vector<double> rzn(B);
+    TCK(dot(r, z, rzn.data()));
+    for (int k = 0; k < B; ++k) {
+      coef[k] = (active[k] != 0.0 && hrz[k] != 0.0) ? rzn[k] / hrz[k] : 0.0;
+      hrz[k] = rzn[k];
+    }
+    TCK(setc(coef));
+    k_xpay<<<gv, 256, 0, st>>>(n, B, coefd, z, p); note_launch();
+  }
+#undef TCK
+  if (status == DG_OK && any_active()) status = DG_ERR_NOT_CONVERGED;
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    for (int k = 0; k < B; ++k) {
+      info->iters[k] = iters[k];
+      info->relres[k] = hb[k] > 0.0 ? std::sqrt(hrr[k]) / hb[k] : 0.0;
+    }
+    info->total_iters = it;
+  }
+  return status;
+}
+
+}  // extern "C"

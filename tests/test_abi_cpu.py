@@ -91,6 +91,30 @@ def test_mesh_validation_rejects_bad_meshes_before_any_device_work(P):
     assert ei.value.name == "DG_ERR_ARG"
 
 
+def test_tet_mesh_validation_rejects_before_any_device_work(P):
+    from dg_inputs.tetmesh import jittered_tet_grid
+    m = jittered_tet_grid(1)
+    for N in (0, 6):                       # tetrahedral degrees are 1..5
+        with pytest.raises(P.DgError) as ei:
+            P.TetMesh.from_inputs(m, N)
+        assert ei.value.name == "DG_ERR_ARG"
+    e = m.EToV.copy()
+    e[0, 0] = 999
+    with pytest.raises(P.DgError) as ei:
+        P.TetMesh(2, m.VX, m.VY, m.VZ, e, m.bc)
+    assert ei.value.name == "DG_ERR_MESH"
+    e = m.EToV.copy()
+    e[0, [1, 2]] = e[0, [2, 1]]            # negative Jacobian
+    with pytest.raises(P.DgError) as ei:
+        P.TetMesh(2, m.VX, m.VY, m.VZ, e, m.bc)
+    assert ei.value.name == "DG_ERR_MESH"
+    bad = m.bc.copy()
+    bad[m.bc != 0] = 0                     # boundary face without a tag
+    with pytest.raises(P.DgError) as ei:
+        P.TetMesh(2, m.VX, m.VY, m.VZ, m.EToV, bad)
+    assert ei.value.name == "DG_ERR_MESH"
+
+
 C_CONSUMER = r"""
 #include <stdio.h>
 #include "dg.h"
