@@ -21,7 +21,8 @@ and 16 right-hand sides in one batched solve, and the split INS step on the
 launching stream.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-  python bench.py --sweep     # applies for N = 1..8, FP64/FP32, batch 1/4/16
+  python bench.py --sweep     # applies for N = 1..10, FP64/FP32, batch 1/4/16
+  python bench.py --tet       # tetrahedral applies for N = 1..5 (196,608 tetrahedra)
 
 `--impl reference` times the FP64 CPU oracle (the method written plainly in
 numpy) on a bounded sample of the same workload, on the host cores.
@@ -642,6 +643,52 @@ def run_sweep(args):
         torch.cuda.empty_cache()
 
 
+def run_tet(args):
+    """Tetrahedral apply throughput: 6 n^3 jittered tetrahedra (n = 32:
+    196,608 elements), N = 1..5, Poisson and Helmholtz, FP64 and FP32, B = 1
+    and 4, L2 flushed between launches; one JSON line per case. Algorithmic
+    bytes per element: u read and Au written once (2 B Np words), the geometry
+    (40 words), the connectivity (4 ints) and the neighbour node map (4 Nfp
+    ints)."""
+    import torch
+    import paper_1801_00246_gb300 as P
+    from paper_1801_00246_gb300 import build
+    from dg_inputs import uniform_field
+    from dg_inputs.tetmesh import jittered_tet_grid
+    build.build()
+    pk = peaks()
+    m = jittered_tet_grid(args.tet_n, jitter=0.1, seed=1, bc_sides=(1, 2, 2, 1, 1, 2))
+    flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for N in range(1, 6):
+        mesh = P.TetMesh.from_inputs(m, N)
+        K, Np, Nfp = mesh.K, mesh.Np, (N + 1) * (N + 2) // 2
+        for B in (1, 4):
+            u64 = torch.from_numpy(uniform_field((B, K, Np), seed=1)).cuda()
+            for key, u in (("f64", u64), ("f32", u64.float())):
+                o = torch.empty_like(u)
+                word = u.element_size()
+                for lam in (0.0, 1.0):
+                    ms = []
+                    for it in range(args.warmup + args.steps):
+                        flush_buf.fill_(1.0)
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record()
+                        mesh.apply(u, lam=lam, out=o)
+                        e1.record()
+                        torch.cuda.synchronize()
+                        if it >= args.warmup:
+                            ms.append(e0.elapsed_time(e1))
+                    t = float(np.median(ms)) * 1e-3
+                    nbytes = K * (2 * B * Np * word + 40 * word + 4 * 4 + 4 * Nfp * 4)
+                    print(json.dumps({
+                        "tet": True, "N": N, "Np": Np, "K": K, "B": B, "op": "helmholtz" if lam else "poisson",
+                        "prec": key, "ms": t * 1e3, "gdofs": B * K * Np / t / 1e9,
+                        "hbm_gbs": nbytes / t / 1e9, "hbm_frac": nbytes / t / 1e9 / pk["hbm_gbs"]}), flush=True)
+            del u64
+        del mesh
+        torch.cuda.empty_cache()
+
+
 def run_solve_only(args):
     """One mixed-precision pMG-FCG solve on the N=8 workload inside an NVTX
     range "timed_solve" (after a set-up solve), for per-kernel launch lists."""
@@ -735,6 +782,8 @@ def main():
     ap.add_argument("--oracle-child", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--amg-compare", action="store_true",
                     help="pMG-AMG against AMG alone on the 32768-triangle N=6 workload")
+    ap.add_argument("--tet", action="store_true", help="tetrahedral apply throughput, N = 1..5")
+    ap.add_argument("--tet-n", type=int, default=32, help="--tet: cubes per side (6 n^3 tetrahedra)")
     ap.add_argument("--sweep-degrees", default="1,2,3,4,5,6,7,8,9,10")
     ap.add_argument("--sweep-batches", default="1,4,16")
     args = ap.parse_args()
@@ -745,6 +794,9 @@ def main():
         return
     if args.sweep:
         run_sweep(args)
+        return
+    if args.tet:
+        run_tet(args)
         return
     if args.solve_only:
         run_solve_only(args)

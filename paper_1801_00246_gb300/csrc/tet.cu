@@ -23,10 +23,15 @@
 //
 // Reference operators are built on the host from a monomial Vandermonde
 // matrix and Gauss-Jacobi quadrature; a neighbour's face nodes are matched to
-// the element's by their physical coordinates at setup. One thread block
-// handles a few elements, one thread per node.
+// the element's by their physical coordinates at setup. The apply is two
+// kernels with the reference operators in shared memory: the first forms the
+// reference gradient once per element and writes w_a = G_ab D_b u and the face
+// traces (u, n.grad u); the second takes jumps and averages from the element's
+// and its neighbours' traces, lifts them through the face mass and applies
+// D_b^T to J M w_b plus the lifted jumps, so that no gradient is formed twice.
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -252,141 +257,257 @@ struct dg_tet_mesh {
   double* geo64 = nullptr;  // [K][kGeo]
   float* geo32 = nullptr;
   int* conn = nullptr;     // [K][4]: neighbour element, or -1 - boundary tag
-  int* mapP = nullptr;     // [K][4][Nfp]: the neighbour's volume node at face node j
+  int* mapJ = nullptr;     // [K][4 Nfp]: the neighbour's face-node slot f2 Nfp + j2 at face node (f, j)
+  int* nfs = nullptr;      // [Np][3]: the face-node slots f Nfp + j at volume node i (-1 padded)
   double* xyz = nullptr;   // [3][K][Np] node coordinates
   // Jacobi-PCG workspace (grown on demand)
   double* work = nullptr;
   size_t work_cap = 0;
+  // apply scratch: w ([B K][3][Np]) and face traces ([B K][4 Nfp][2]), grown on demand
+  mutable void* ascr = nullptr;
+  mutable size_t ascr_bytes = 0;
 };
 
 namespace dgx {
 namespace tet {
 
-constexpr int kGroup = 64;  // threads per element (Np <= 56 at N = 5)
-constexpr int kGroups = 4;  // elements per block
+// Compile-time sizes of the degree-N apply: a block of kTetThreads threads
+// handles EB elements, kR per thread in the node stages (each operator entry
+// read from shared memory serves kR elements).
+constexpr int kTetThreads = 256;
+constexpr int kR = 2;
+template <int N>
+struct TetDims {
+  static constexpr int Np = (N + 1) * (N + 2) * (N + 3) / 6;
+  static constexpr int Nfp = (N + 1) * (N + 2) / 2;
+  static constexpr int NF = 4 * Nfp;                  // face nodes of an element
+  static constexpr int GS = kTetThreads / Np;         // element slots in the node stages
+  static constexpr int EB = GS * kR;                  // elements per block iteration
+};
 
-// A u for B right-hand sides ([B][K][Np]); one element per 64-thread group.
-template <typename T, bool HELM>
-__global__ void __launch_bounds__(kGroup * kGroups) tet_apply(int N, int64_t K, int64_t nE, OpsLayout L,
-                                                              const T* __restrict__ ops, const int* __restrict__ fmask,
-                                                              const T* __restrict__ geo, const int* __restrict__ conn,
-                                                              const int* __restrict__ mapP, T lambda,
-                                                              const T* __restrict__ u, T* __restrict__ Au) {
-  const int Np = (N + 1) * (N + 2) * (N + 3) / 6, Nfp = (N + 1) * (N + 2) / 2;
-  constexpr int NPM = 56, NFM = 21;  // N <= 5
-  __shared__ T su[kGroups][5][NPM];       // own values, then the four neighbours'
-  __shared__ T sw[kGroups][3][NPM];       // w_a = sum_b G_ab D_b u
-  __shared__ T sF1[kGroups][4][NFM], sF2[kGroups][4][NFM];
-  __shared__ T sjm[kGroups][4][NFM], sav[kGroups][4][NFM];
-  const int grp = threadIdx.x / kGroup, t = threadIdx.x % kGroup;
-  const T* D0 = ops + L.D[0];
-  const T* D1 = ops + L.D[1];
-  const T* D2 = ops + L.D[2];
-  for (int64_t base = int64_t(blockIdx.x) * kGroups; base < nE; base += int64_t(gridDim.x) * kGroups) {
-    const int64_t be = base + grp;
-    const bool live = be < nE;
-    const int64_t e = live ? be % K : 0, boff = live ? be - e : 0;
-    const T* g = geo + e * kGeo;
-    if (live) {
-      for (int m = t; m < Np; m += kGroup) su[grp][0][m] = u[be * Np + m];
-      for (int f = 0; f < 4; ++f) {
-        const int c = conn[4 * e + f];
-        if (c >= 0)
-          for (int m = t; m < Np; m += kGroup) su[grp][1 + f][m] = u[(boff + c) * Np + m];
-      }
-    }
+// Shared-memory words of each kernel (operators, then per-element buffers).
+template <int N>
+constexpr int tet_grad_words() {
+  using D = TetDims<N>;
+  return 3 * D::Np * D::Np + D::EB * 4 * D::Np;
+}
+template <int N>
+constexpr int tet_lift_words() {
+  using D = TetDims<N>;
+  return 4 * D::Np * D::Np + 4 * D::Nfp * D::Nfp + D::EB * (7 * D::Np + 4 * D::NF);
+}
+
+// First kernel of the apply: per element the reference gradient ub_b = D_b u at
+// every node, then (a) w_a = sum_b G_ab ub_b ([nE][3][Np]) and (b) the face
+// traces (u, n.grad u) at the element's face nodes with its own outward normal
+// ([nE][4 Nfp][2]), which the element and its neighbours read in the second kernel.
+template <typename T, int N>
+__global__ void __launch_bounds__(kTetThreads) tet_grad(int64_t K, int64_t nE, OpsLayout L, const T* __restrict__ ops,
+                                                        const int* __restrict__ fmask, const T* __restrict__ geo,
+                                                        const T* __restrict__ u, T* __restrict__ w,
+                                                        T* __restrict__ tr) {
+  using D = TetDims<N>;
+  constexpr int Np = D::Np, NF = D::NF, EB = D::EB, GS = D::GS;
+  extern __shared__ __align__(16) unsigned char tet_smem[];
+  T* sDT = reinterpret_cast<T*>(tet_smem);  // [3][m][i] = D_b[i][m]
+  T* su = sDT + 3 * Np * Np;                // [EB][Np]
+  T* sub = su + EB * Np;                    // [EB][3][Np]
+  for (int q = threadIdx.x; q < 3 * Np * Np; q += kTetThreads) {
+    const int b = q / (Np * Np), r = q - b * Np * Np, m = r / Np, i = r - m * Np;
+    sDT[q] = ops[L.D[b] + i * Np + m];
+  }
+  const int slot = threadIdx.x / Np, i = threadIdx.x - slot * Np;
+  for (int64_t be0 = int64_t(blockIdx.x) * EB; be0 < nE; be0 += int64_t(gridDim.x) * EB) {
+    const int nv = int(nE - be0 < EB ? nE - be0 : EB);
     __syncthreads();
-    if (live && t < Np) {
-      T ub[3] = {T(0), T(0), T(0)};
+    for (int q = threadIdx.x; q < nv * Np; q += kTetThreads) su[q] = u[be0 * Np + q];
+    __syncthreads();
+    if (slot < GS) {
+      T acc[kR][3];
+#pragma unroll
+      for (int r = 0; r < kR; ++r) acc[r][0] = acc[r][1] = acc[r][2] = T(0);
+#pragma unroll 4
       for (int m = 0; m < Np; ++m) {
-        const T um = su[grp][0][m];
-        ub[0] += D0[t * Np + m] * um;
-        ub[1] += D1[t * Np + m] * um;
-        ub[2] += D2[t * Np + m] * um;
-      }
-      const T G[6] = {g[1], g[2], g[3], g[4], g[5], g[6]};  // rr rs rt ss st tt
-      sw[grp][0][t] = G[0] * ub[0] + G[1] * ub[1] + G[2] * ub[2];
-      sw[grp][1][t] = G[1] * ub[0] + G[3] * ub[1] + G[4] * ub[2];
-      sw[grp][2][t] = G[2] * ub[0] + G[4] * ub[1] + G[5] * ub[2];
-    }
-    // face nodes: jumps and averages
-    if (live)
-      for (int idx = t; idx < 4 * Nfp; idx += kGroup) {
-        const int f = idx / Nfp, j = idx - f * Nfp;
-        const int k = fmask[f * Nfp + j];
-        const int c = conn[4 * e + f];
-        const T* gf = g + 7 + 8 * f;
-        T jm = T(0), av = T(0);
-        if (c >= 0 || c == -2) {
-          T db[3] = {T(0), T(0), T(0)};
-          for (int m = 0; m < Np; ++m) {
-            const T um = su[grp][0][m];
-            db[0] += D0[k * Np + m] * um;
-            db[1] += D1[k * Np + m] * um;
-            db[2] += D2[k * Np + m] * um;
-          }
-          const T dnm = gf[0] * db[0] + gf[1] * db[1] + gf[2] * db[2];
-          if (c >= 0) {
-            const int kp = mapP[(e * 4 + f) * Nfp + j];
-            T pb[3] = {T(0), T(0), T(0)};
-            for (int m = 0; m < Np; ++m) {
-              const T um = su[grp][1 + f][m];
-              pb[0] += D0[kp * Np + m] * um;
-              pb[1] += D1[kp * Np + m] * um;
-              pb[2] += D2[kp * Np + m] * um;
-            }
-            const T dnp = gf[3] * pb[0] + gf[4] * pb[1] + gf[5] * pb[2];
-            jm = su[grp][1 + f][kp] - su[grp][0][k];
-            av = T(0.5) * (dnm + dnp);
-          } else {  // Dirichlet ghost: u+ = -u-, grad u+ = grad u-
-            jm = T(-2) * su[grp][0][k];
-            av = dnm;
-          }
-        }
-        sjm[grp][f][j] = jm;
-        sav[grp][f][j] = av;
-      }
-    __syncthreads();
-    if (live)
-      for (int idx = t; idx < 4 * Nfp; idx += kGroup) {
-        const int f = idx / Nfp, j = idx - f * Nfp;
-        const T* gf = g + 7 + 8 * f;
-        const T sJ = gf[6], tau = gf[7];
-        const T* Mf = ops + L.Mf[f];
-        T m1 = T(0), m2 = T(0);
-        for (int l = 0; l < Nfp; ++l) {
-          const T mf = Mf[j * Nfp + l];
-          m1 += mf * (sav[grp][f][l] + tau * sjm[grp][f][l]);
-          m2 += mf * sjm[grp][f][l];
-        }
-        sF1[grp][f][j] = -sJ * m1;
-        sF2[grp][f][j] = T(0.5) * sJ * m2;
-      }
-    __syncthreads();
-    if (live && t < Np) {
-      const T J = g[0];
-      T o = T(0);
-      for (int m = 0; m < Np; ++m)
-        o += ops[L.B[0] + t * Np + m] * sw[grp][0][m] + ops[L.B[1] + t * Np + m] * sw[grp][1][m] +
-             ops[L.B[2] + t * Np + m] * sw[grp][2][m];
-      o *= J;
-      if (HELM) {
-        T a = T(0);
-        for (int m = 0; m < Np; ++m) a += ops[L.M + t * Np + m] * su[grp][0][m];
-        o += lambda * J * a;
-      }
-      for (int f = 0; f < 4; ++f) {
-        const T* gf = g + 7 + 8 * f;
-        for (int j = 0; j < Nfp; ++j) {
-          const int k = fmask[f * Nfp + j];
-          const T F2 = sF2[grp][f][j];
-          o += (gf[0] * D0[k * Np + t] + gf[1] * D1[k * Np + t] + gf[2] * D2[k * Np + t]) * F2;
-          if (k == t) o += sF1[grp][f][j];
+        const T d0 = sDT[m * Np + i], d1 = sDT[Np * Np + m * Np + i], d2 = sDT[2 * Np * Np + m * Np + i];
+#pragma unroll
+        for (int r = 0; r < kR; ++r) {
+          const T um = su[(slot + GS * r) * Np + m];
+          acc[r][0] += d0 * um;
+          acc[r][1] += d1 * um;
+          acc[r][2] += d2 * um;
         }
       }
-      Au[be * Np + t] = o;
+#pragma unroll
+      for (int r = 0; r < kR; ++r) {
+        const int g = slot + GS * r;
+        if (g >= nv) continue;
+        const int64_t be = be0 + g, e = be % K;
+        const T* G = geo + e * kGeo + 1;  // rr rs rt ss st tt
+        sub[(g * 3 + 0) * Np + i] = acc[r][0];
+        sub[(g * 3 + 1) * Np + i] = acc[r][1];
+        sub[(g * 3 + 2) * Np + i] = acc[r][2];
+        T* wo = w + be * 3 * Np;
+        wo[i] = G[0] * acc[r][0] + G[1] * acc[r][1] + G[2] * acc[r][2];
+        wo[Np + i] = G[1] * acc[r][0] + G[3] * acc[r][1] + G[4] * acc[r][2];
+        wo[2 * Np + i] = G[2] * acc[r][0] + G[4] * acc[r][1] + G[5] * acc[r][2];
+      }
     }
     __syncthreads();
+    for (int q = threadIdx.x; q < nv * NF; q += kTetThreads) {
+      const int g = q / NF, fj = q - g * NF, f = fj / D::Nfp;
+      const int k = fmask[fj];
+      const int64_t e = (be0 + g) % K;
+      const T* nr = geo + e * kGeo + 7 + 8 * f;
+      const T* ub = sub + g * 3 * Np;
+      T* t2 = tr + ((be0 + g) * NF + fj) * 2;
+      t2[0] = su[g * Np + k];
+      t2[1] = nr[0] * ub[k] + nr[1] * ub[Np + k] + nr[2] * ub[2 * Np + k];
+    }
+  }
+}
+
+// Second kernel of the apply: per element the face jumps and averages from the
+// traces (own and neighbour's), the face-mass products F1 = -sJ Mf (avg + tau jump)
+// and F2 = sJ Mf jump / 2, then per node
+//   z_b = J M w_b + y_b,  y_b[k] = sum over the face nodes (f, j) at node k of nr_fb F2_fj,
+//   (A u)_i = sum_b (D_b^T z_b)_i + sum over (f, j) at node i of F1_fj [+ lambda J (M u)_i]
+// (B_b = D_b^T M, so the volume term and the lift of the jump share one product).
+template <typename T, int N, bool HELM>
+__global__ void __launch_bounds__(kTetThreads) tet_lift(int64_t K, int64_t nE, OpsLayout L, const T* __restrict__ ops,
+                                                        const int* __restrict__ nfs, const T* __restrict__ geo,
+                                                        const int* __restrict__ conn, const int* __restrict__ mapJ,
+                                                        T lambda, const T* __restrict__ u, const T* __restrict__ w,
+                                                        const T* __restrict__ tr, T* __restrict__ Au) {
+  using D = TetDims<N>;
+  constexpr int Np = D::Np, Nfp = D::Nfp, NF = D::NF, EB = D::EB, GS = D::GS;
+  extern __shared__ __align__(16) unsigned char tet_smem[];
+  T* sD = reinterpret_cast<T*>(tet_smem);  // [3][m][i] = D_b[m][i]
+  T* sM = sD + 3 * Np * Np;                 // [m][i]
+  T* sMf = sM + Np * Np;                    // [4][l][j]
+  T* su = sMf + 4 * Nfp * Nfp;              // [EB][Np]
+  T* sw = su + EB * Np;                     // [EB][3][Np]
+  T* sz = sw + EB * 3 * Np;                 // [EB][3][Np]
+  T* sJm = sz + EB * 3 * Np;                // [EB][NF]
+  T* sAv = sJm + EB * NF;
+  T* sF1 = sAv + EB * NF;
+  T* sF2 = sF1 + EB * NF;
+  for (int q = threadIdx.x; q < 3 * Np * Np; q += kTetThreads) {
+    const int b = q / (Np * Np);
+    sD[q] = ops[L.D[b] + (q - b * Np * Np)];
+  }
+  for (int q = threadIdx.x; q < Np * Np; q += kTetThreads) sM[q] = ops[L.M + q];
+  for (int q = threadIdx.x; q < 4 * Nfp * Nfp; q += kTetThreads) {
+    const int f = q / (Nfp * Nfp);
+    sMf[q] = ops[L.Mf[f] + (q - f * Nfp * Nfp)];
+  }
+  const int slot = threadIdx.x / Np, i = threadIdx.x - slot * Np;
+  for (int64_t be0 = int64_t(blockIdx.x) * EB; be0 < nE; be0 += int64_t(gridDim.x) * EB) {
+    const int nv = int(nE - be0 < EB ? nE - be0 : EB);
+    __syncthreads();
+    if (HELM)
+      for (int q = threadIdx.x; q < nv * Np; q += kTetThreads) su[q] = u[be0 * Np + q];
+    for (int q = threadIdx.x; q < nv * 3 * Np; q += kTetThreads) sw[q] = w[be0 * 3 * Np + q];
+    for (int q = threadIdx.x; q < nv * NF; q += kTetThreads) {  // jumps and averages
+      const int g = q / NF, fj = q - g * NF, f = fj / Nfp;
+      const int64_t be = be0 + g, e = be % K;
+      const int c = conn[4 * e + f];
+      const T* own = tr + (be * NF + fj) * 2;
+      T jm = T(0), av = T(0);
+      if (c >= 0) {
+        const T* nb = tr + ((be - e + c) * NF + mapJ[e * NF + fj]) * 2;
+        jm = nb[0] - own[0];
+        av = T(0.5) * (own[1] - nb[1]);  // the neighbour's trace carries its own (opposite) normal
+      } else if (c == -2) {              // Dirichlet ghost: u+ = -u-, grad u+ = grad u-
+        jm = T(-2) * own[0];
+        av = own[1];
+      }
+      sJm[g * NF + fj] = jm;
+      sAv[g * NF + fj] = av;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < nv * NF; q += kTetThreads) {  // face-mass products
+      const int g = q / NF, fj = q - g * NF, f = fj / Nfp, j = fj - f * Nfp;
+      const int64_t e = (be0 + g) % K;
+      const T* gf = geo + e * kGeo + 7 + 8 * f;
+      const T sJ = gf[6], tau = gf[7];
+      const T* Mf = sMf + f * Nfp * Nfp;
+      const T* jf = sJm + g * NF + f * Nfp;
+      const T* af = sAv + g * NF + f * Nfp;
+      T m1 = T(0), m2 = T(0);
+#pragma unroll 4
+      for (int l = 0; l < Nfp; ++l) {
+        const T mf = Mf[l * Nfp + j];
+        m1 += mf * (af[l] + tau * jf[l]);
+        m2 += mf * jf[l];
+      }
+      sF1[g * NF + fj] = -sJ * m1;
+      sF2[g * NF + fj] = T(0.5) * sJ * m2;
+    }
+    __syncthreads();
+    T extra[kR] = {};
+    if (slot < GS) {
+      T z[kR][3], h[kR];
+#pragma unroll
+      for (int r = 0; r < kR; ++r) z[r][0] = z[r][1] = z[r][2] = h[r] = T(0);
+#pragma unroll 4
+      for (int m = 0; m < Np; ++m) {
+        const T mv = sM[m * Np + i];
+#pragma unroll
+        for (int r = 0; r < kR; ++r) {
+          const T* wg = sw + (slot + GS * r) * 3 * Np;
+          z[r][0] += mv * wg[m];
+          z[r][1] += mv * wg[Np + m];
+          z[r][2] += mv * wg[2 * Np + m];
+          if (HELM) h[r] += mv * su[(slot + GS * r) * Np + m];
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < kR; ++r) {
+        const int g = slot + GS * r;
+        extra[r] = T(0);
+        if (g >= nv) continue;
+        const int64_t e = (be0 + g) % K;
+        const T* ge = geo + e * kGeo;
+        const T J = ge[0];
+        T y0 = T(0), y1 = T(0), y2 = T(0), f1 = T(0);
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+          const int fj = nfs[i * 3 + s];
+          if (fj < 0) continue;
+          const T* nr = ge + 7 + 8 * (fj / Nfp);
+          const T F2 = sF2[g * NF + fj];
+          y0 += nr[0] * F2;
+          y1 += nr[1] * F2;
+          y2 += nr[2] * F2;
+          f1 += sF1[g * NF + fj];
+        }
+        T* zg = sz + g * 3 * Np;
+        zg[i] = J * z[r][0] + y0;
+        zg[Np + i] = J * z[r][1] + y1;
+        zg[2 * Np + i] = J * z[r][2] + y2;
+        extra[r] = HELM ? f1 + lambda * J * h[r] : f1;
+      }
+    }
+    __syncthreads();
+    if (slot < GS) {
+      T o[kR];
+#pragma unroll
+      for (int r = 0; r < kR; ++r) o[r] = T(0);
+#pragma unroll 4
+      for (int m = 0; m < Np; ++m) {
+        const T d0 = sD[m * Np + i], d1 = sD[Np * Np + m * Np + i], d2 = sD[2 * Np * Np + m * Np + i];
+#pragma unroll
+        for (int r = 0; r < kR; ++r) {
+          const T* zg = sz + (slot + GS * r) * 3 * Np;
+          o[r] += d0 * zg[m] + d1 * zg[Np + m] + d2 * zg[2 * Np + m];
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < kR; ++r) {
+        const int g = slot + GS * r;
+        if (g < nv) Au[(be0 + g) * Np + i] = o[r] + extra[r];
+      }
+    }
   }
 }
 
@@ -539,21 +660,84 @@ using namespace dgx;
 using namespace dgx::tet;
 
 namespace {
+// Per-instantiation launch data: the dynamic shared-memory limit raised once per
+// device, and the resident blocks per SM at the kernel's shared-memory size.
+struct TetKernelInfo {
+  std::atomic<uint64_t> ready{0};
+  std::atomic<int> occ{1};
+};
+
+template <typename Kern>
+cudaError_t tet_prepare(Kern k, size_t smem, TetKernelInfo& info, int dev, int* occ) {
+  const uint64_t bit = uint64_t(1) << (dev & 63);
+  if (!(info.ready.load() & bit)) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    int o = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, kTetThreads, smem);
+    if (e != cudaSuccess) return e;
+    info.occ.store(o > 0 ? o : 1);
+    info.ready.fetch_or(bit);
+  }
+  *occ = info.occ.load();
+  return cudaSuccess;
+}
+
+template <typename T, int N, bool HELM>
+cudaError_t tet_apply_n(const dg_tet_mesh* m, int64_t nE, T lambda, const T* ops, const T* geo, const T* u, T* Au,
+                        T* w, T* tr, cudaStream_t st) {
+  static TetKernelInfo info_g, info_l;
+  const size_t sg = size_t(tet_grad_words<N>()) * sizeof(T), sl = size_t(tet_lift_words<N>()) * sizeof(T);
+  int dev = 0, sms = 0, og = 1, ol = 1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = tet_prepare(tet_grad<T, N>, sg, info_g, dev, &og);
+  if (e == cudaSuccess) e = tet_prepare(tet_lift<T, N, HELM>, sl, info_l, dev, &ol);
+  if (e != cudaSuccess) return e;
+  // one resident wave of blocks, each loading the operators once and striding over element batches
+  const int64_t batches = (nE + TetDims<N>::EB - 1) / TetDims<N>::EB;
+  const unsigned gg = unsigned(std::min<int64_t>(batches, int64_t(sms) * og));
+  const unsigned gl = unsigned(std::min<int64_t>(batches, int64_t(sms) * ol));
+  tet_grad<T, N><<<gg, kTetThreads, sg, st>>>(m->K, nE, m->L, ops, m->fmask, geo, u, w, tr);
+  note_launch();
+  tet_lift<T, N, HELM><<<gl, kTetThreads, sl, st>>>(m->K, nE, m->L, ops, m->nfs, geo, m->conn, m->mapJ, lambda, u, w,
+                                                    tr, Au);
+  note_launch();
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t tet_apply_launch(const dg_tet_mesh* m, int B, double lambda, const T* u, T* Au, cudaStream_t st) {
   const bool f64 = sizeof(T) == 8;
   const T* ops = f64 ? reinterpret_cast<const T*>(m->ops64) : reinterpret_cast<const T*>(m->ops32);
   const T* geo = f64 ? reinterpret_cast<const T*>(m->geo64) : reinterpret_cast<const T*>(m->geo32);
   const int64_t nE = int64_t(B) * m->K;
-  const unsigned grid = unsigned(std::min<int64_t>((nE + kGroups - 1) / kGroups, 152 * 32));
-  if (lambda != 0.0)
-    tet_apply<T, true><<<grid, kGroup * kGroups, 0, st>>>(m->N, m->K, nE, m->L, ops, m->fmask, geo, m->conn,
-                                                          m->mapP, T(lambda), u, Au);
-  else
-    tet_apply<T, false><<<grid, kGroup * kGroups, 0, st>>>(m->N, m->K, nE, m->L, ops, m->fmask, geo, m->conn,
-                                                           m->mapP, T(0), u, Au);
-  note_launch();
-  return cudaGetLastError();
+  const size_t need = size_t(nE) * size_t(3 * m->Np + 8 * m->Nfp) * sizeof(T);
+  if (m->ascr_bytes < need) {
+    cudaFree(m->ascr);
+    m->ascr = nullptr;
+    m->ascr_bytes = 0;
+    const cudaError_t e = cudaMalloc(&m->ascr, need);
+    if (e != cudaSuccess) return e;
+    m->ascr_bytes = need;
+  }
+  T* w = static_cast<T*>(m->ascr);
+  T* tr = w + nE * 3 * m->Np;
+  const T lam = T(lambda);
+  const bool helm = lambda != 0.0;
+  switch (m->N) {
+#define TET_CASE(NN)                                                                           \
+  case NN:                                                                                     \
+    return helm ? tet_apply_n<T, NN, true>(m, nE, lam, ops, geo, u, Au, w, tr, st)             \
+                : tet_apply_n<T, NN, false>(m, nE, lam, ops, geo, u, Au, w, tr, st);
+    TET_CASE(1)
+    TET_CASE(2)
+    TET_CASE(3)
+    TET_CASE(4)
+    TET_CASE(5)
+#undef TET_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
 }
 }  // namespace
 
@@ -563,7 +747,8 @@ dg_status dg_tet_mesh_destroy(dg_tet_mesh* m) {
   if (!m) return DG_OK;
   for (void* p : {static_cast<void*>(m->ops64), static_cast<void*>(m->ops32), static_cast<void*>(m->fmask),
                   static_cast<void*>(m->geo64), static_cast<void*>(m->geo32), static_cast<void*>(m->conn),
-                  static_cast<void*>(m->mapP), static_cast<void*>(m->xyz), static_cast<void*>(m->work)})
+                  static_cast<void*>(m->mapJ), static_cast<void*>(m->nfs), static_cast<void*>(m->xyz),
+                  static_cast<void*>(m->work), m->ascr})
     cudaFree(p);
   delete m;
   return DG_OK;
@@ -691,7 +876,7 @@ dg_status dg_tet_mesh_setup(int N, int64_t Nv, const double* VX, const double* V
       }
     }
   }
-  std::vector<int> mapP(size_t(K) * 4 * Nfp, -1);
+  std::vector<int> mapJ(size_t(K) * 4 * Nfp, -1);
   for (int64_t e = 0; e < K; ++e)
     for (int f = 0; f < 4; ++f) {
       const int e2 = nbE[4 * e + f], f2 = nbF[4 * e + f];
@@ -699,7 +884,7 @@ dg_status dg_tet_mesh_setup(int N, int64_t Nv, const double* VX, const double* V
       const double hscale = std::cbrt(vol[e]);
       for (int j = 0; j < Nfp; ++j) {
         const int k = R.fmask[f][j];
-        int best = -1;
+        int best = -1, bestj = -1;
         for (int j2 = 0; j2 < Nfp; ++j2) {
           const int k2 = R.fmask[f2][j2];
           double d2 = 0.0;
@@ -707,14 +892,14 @@ dg_status dg_tet_mesh_setup(int N, int64_t Nv, const double* VX, const double* V
             const double dx = xyz[(size_t(d) * K + e) * Np + k] - xyz[(size_t(d) * K + e2) * Np + k2];
             d2 += dx * dx;
           }
-          if (std::sqrt(d2) < 1e-8 * hscale) best = k2;
+          if (std::sqrt(d2) < 1e-8 * hscale) best = k2, bestj = j2;
         }
         if (best < 0) {
           dg_tet_mesh_destroy(m);
           set_error("non-conforming tetrahedral faces (face nodes do not match)");
           return DG_ERR_MESH;
         }
-        mapP[(size_t(e) * 4 + f) * Nfp + j] = best;
+        mapJ[(size_t(e) * 4 + f) * Nfp + j] = f2 * Nfp + bestj;
       }
     }
   // per-element geometry words
@@ -755,9 +940,20 @@ dg_status dg_tet_mesh_setup(int N, int64_t Nv, const double* VX, const double* V
   std::copy(R.dM.begin(), R.dM.end(), ops.begin() + m->L.dM);
   for (int b = 0; b < 3; ++b)
     for (int f = 0; f < 4; ++f) std::copy(R.fc[b][f].begin(), R.fc[b][f].end(), ops.begin() + m->L.fc[b][f]);
-  std::vector<int> fm(size_t(4) * Nfp);
+  std::vector<int> fm(size_t(4) * Nfp), nfs(size_t(Np) * 3, -1);
   for (int f = 0; f < 4; ++f)
-    for (int j = 0; j < Nfp; ++j) fm[size_t(f) * Nfp + j] = R.fmask[f][j];
+    for (int j = 0; j < Nfp; ++j) {
+      const int k = R.fmask[f][j];
+      fm[size_t(f) * Nfp + j] = k;
+      int s = 0;
+      while (s < 3 && nfs[size_t(k) * 3 + s] >= 0) ++s;
+      if (s == 3) {  // a node of a tetrahedron lies on at most three faces
+        dg_tet_mesh_destroy(m);
+        set_error("tetrahedron node on more than three faces");
+        return DG_ERR_ARG;
+      }
+      nfs[size_t(k) * 3 + s] = f * Nfp + j;
+    }
   const std::vector<float> ops32(ops.begin(), ops.end()), geo32(geo.begin(), geo.end());
   cudaError_t ce = upload(&m->ops64, ops);
   if (ce == cudaSuccess) ce = upload(&m->ops32, ops32);
@@ -765,7 +961,8 @@ dg_status dg_tet_mesh_setup(int N, int64_t Nv, const double* VX, const double* V
   if (ce == cudaSuccess) ce = upload(&m->geo64, geo);
   if (ce == cudaSuccess) ce = upload(&m->geo32, geo32);
   if (ce == cudaSuccess) ce = upload(&m->conn, conn);
-  if (ce == cudaSuccess) ce = upload(&m->mapP, mapP);
+  if (ce == cudaSuccess) ce = upload(&m->mapJ, mapJ);
+  if (ce == cudaSuccess) ce = upload(&m->nfs, nfs);
   if (ce == cudaSuccess) ce = upload(&m->xyz, xyz);
   if (ce != cudaSuccess) {
     dg_tet_mesh_destroy(m);

@@ -67,11 +67,13 @@ def test_tet_apply_all_neumann_and_all_dirichlet(N):
 
 
 def test_tet_apply_parity_past_one_grid_stride():
-    """20,250 elements (15 cubes a side) at B = 1: more element groups than one
-    pass of the capped grid covers, so the grid-stride loop runs."""
+    """20,250 elements (15 cubes a side) at B = 4: 81,000 element applies, more
+    than one resident wave of blocks covers at N = 2 (batches of 50 elements;
+    at most 8 blocks per SM of 152), so both kernels' block loops run more
+    than once, and the last batch is ragged."""
     m = jittered_tet_grid(15, jitter=0.1, seed=11, bc_sides=MIXED)
     lib, ora = _pair(m, 2)
-    u = uniform_field((m.K, ora.Np), seed=5)
+    u = uniform_field((4, m.K, ora.Np), seed=5)
     assert rel(lib.apply(cuda(u), lam=0.7).cpu().numpy(), ora.apply(u, lam=0.7)) <= TOL64
 
 
