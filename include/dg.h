@@ -344,8 +344,11 @@ dg_status dg_tet_mesh_destroy(dg_tet_mesh* mesh);
 dg_status dg_tet_mesh_info(const dg_tet_mesh* mesh, int* N, int64_t* K, int* Np);
 /* Node coordinates into device [K][Np] arrays x, y, z. */
 dg_status dg_tet_mesh_nodes(const dg_tet_mesh* mesh, double* x, double* y, double* z, void* stream);
-/* Au = A(lambda) u for B right-hand sides, FP64 (DG_F64) or FP32 (DG_F32):
- * one thread block handles four elements, one thread per node. */
+/* Au = A(lambda) u for B right-hand sides, FP64 (DG_F64) or FP32 (DG_F32), in
+ * two kernels (reference gradient and face traces, then lift and output). The
+ * first call at a batch size (and precision) larger than any before allocates
+ * the mesh's apply scratch, (3 Np + 8 Nfp) B K words, Nfp = (N+1)(N+2)/2;
+ * applies on one mesh must not overlap. */
 dg_status dg_tet_apply(const dg_tet_mesh* mesh, dg_prec prec, int B, double lambda, const void* u, void* Au,
                        void* stream);
 /* b = J M f - L(g) (the Dirichlet problem's weak right-hand side, as dg_rhs). */
