@@ -323,6 +323,12 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
         for (int t = 0; t < 8; ++t) v[t] = (live && k0 + t < Kd) ? __ldg(xr + k0 + t) : 0.0;
       }
     };
+    // output product (row exponents given): the last chunk of a tile requests the
+    // next tile's first chunk and exponent (vn, En), so that their latency overlaps
+    // the drain
+    bool have_next = false;
+    int En = 0;
+    double vn[8];  // the next chunk's values (loaded one chunk ahead)
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
       // every slicer takes the same decision to stop (they meet at named barriers below)
       asm volatile("bar.sync 1, %0;\n" ::"r"(kSlicers) : "memory");
@@ -335,9 +341,8 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
       // scale exponent of the row: a bound |X[row][k]| < 2^E, given by the producer
       // of X or found here
       int E;
-      double vn[8];  // the next chunk's values (loaded one chunk ahead)
       if (ex_given) {
-        E = live ? __ldg(ex_given + row) : 0;
+        E = have_next ? En : (live ? __ldg(ex_given + row) : 0);
         if (E == -1100) E = 0;
       } else {
         int em = -1100;
@@ -356,7 +361,8 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
         E = max(max(pmax[e], pmax[kT + e]), max(pmax[2 * kT + e], pmax[3 * kT + e]));
         if (E == -1100) E = 0;
       }
-      load8(xr, live, 8 * q, vn);
+      if (!have_next) load8(xr, live, 8 * q, vn);
+      have_next = false;
       int ymax = -1100;  // MODE 1: largest exponent of the Y columns this thread writes
       float gh[6];  // MODE 1: Grr, Grs, Gss as float-float
       if (MODE == 1) {
@@ -378,7 +384,15 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
           for (int t = 0; t < 8; ++t) v[t] = vn[t];
           {  // request the next chunk of this row (the next pass starts again at chunk 0)
             const int kn = kc + 1 < KCH ? kc + 1 : 0;
-            if (kc + 1 < KCH || (nc + 1 < NCH && !resident)) load8(xr, live, kn * kKC + 8 * q, vn);
+            if (kc + 1 < KCH || (nc + 1 < NCH && !resident)) {
+              load8(xr, live, kn * kKC + 8 * q, vn);
+            } else if (MODE == 0 && ex_given && nc + 1 == NCH && tile + gridDim.x < ntiles) {
+              const int64_t nrow = row + int64_t(gridDim.x) * kT;
+              const bool nlive = nrow < rows;
+              load8(xcol ? X + (nlive ? nrow : 0) : X + (nlive ? nrow : 0) * ldx, nlive, 8 * q, vn);
+              En = nlive ? __ldg(ex_given + nrow) : 0;
+              have_next = true;
+            }
           }
           // each value's 56-bit fixed-point magnitude as two 28-bit halves, and its sign
           // as the pair (s, c) with fma(2^23 + x, s, c) = +-x exactly for 0 <= x < 2^23
