@@ -45,9 +45,9 @@ PMG_DEGREES = [8, 4, 2, 1]
 CHEB = 3           # Chebyshev-Jacobi smoothing degree per pre/post smoothing
 COARSE_PASSES = 1  # degree-1 coarse solve: one AMG-preconditioned CG pass (a scaled AMG V-cycle)
 # DRAM bytes per FP64 apply at N=8 from the latest ncu capture of the current
-# default kernels (tcgen05: gradient product 0.807 GB, face fill 0.938 GB, output
-# product 0.889 GB); None while the kernels differ from that capture
-TENSOR_APPLY_TRAFFIC = 2.634e9
+# default kernels (tcgen05: gradient product 0.807 GB, face fill 0.941 GB, output
+# product 0.888 GB); None while the kernels differ from that capture
+TENSOR_APPLY_TRAFFIC = 2.637e9
 
 
 # apply kernels by DG_KERNEL_* value
@@ -659,10 +659,10 @@ def run_tet(args):
     pk = peaks()
     m = jittered_tet_grid(args.tet_n, jitter=0.1, seed=1, bc_sides=(1, 2, 2, 1, 1, 2))
     flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    for N in range(1, 6):
+    for N in [int(d) for d in args.tet_degrees.split(",")]:
         mesh = P.TetMesh.from_inputs(m, N)
         K, Np, Nfp = mesh.K, mesh.Np, (N + 1) * (N + 2) // 2
-        for B in (1, 4):
+        for B in [int(b) for b in args.tet_batches.split(",")]:
             u64 = torch.from_numpy(uniform_field((B, K, Np), seed=1)).cuda()
             for key, u in (("f64", u64), ("f32", u64.float())):
                 o = torch.empty_like(u)
@@ -784,6 +784,8 @@ def main():
                     help="pMG-AMG against AMG alone on the 32768-triangle N=6 workload")
     ap.add_argument("--tet", action="store_true", help="tetrahedral apply throughput, N = 1..5")
     ap.add_argument("--tet-n", type=int, default=32, help="--tet: cubes per side (6 n^3 tetrahedra)")
+    ap.add_argument("--tet-degrees", default="1,2,3,4,5")
+    ap.add_argument("--tet-batches", default="1,4")
     ap.add_argument("--sweep-degrees", default="1,2,3,4,5,6,7,8,9,10")
     ap.add_argument("--sweep-batches", default="1,4,16")
     args = ap.parse_args()
