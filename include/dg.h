@@ -187,6 +187,21 @@ dg_status dg_helmholtz_apply(const dg_mesh* mesh, dg_prec prec, int B, double la
 dg_status dg_operator_apply(const dg_mesh* mesh, int degree, dg_prec prec, int B, double lambda,
                             const void* u, void* Au, void* stream);
 
+/* dg_operator_apply on fields in HOST memory: u_host, Au_host [B][K][Np]
+ * (page-locked memory lets the copies overlap the apply; pageable memory
+ * works, the copies then serialise). The input is copied to a device buffer
+ * kept with the mesh, the operator applied and the result copied back, all
+ * enqueued behind the caller's earlier work on `stream`; the caller's later
+ * work on `stream` runs after the last copy. With the tcgen05 FP64 kernel (the
+ * FP64 default from degree 3) the copies run on two copy streams of the mesh,
+ * in chunks of rows: a chunk's gradient product starts once its input has
+ * arrived, and a chunk's output copy starts as soon as its output product has
+ * written it. The host buffers must stay valid until `stream` has passed the
+ * call (synchronise it before reading Au_host). Calls on one mesh must not
+ * overlap. Same results as dg_operator_apply on device copies of u. */
+dg_status dg_apply_host(const dg_mesh* mesh, int degree, dg_prec prec, int B, double lambda, const void* u_host,
+                        void* Au_host, void* stream);
+
 /* Kernel selection has no counterpart in the paper, which tunes its kernels
  * per degree by hand (Section 5.2); it changes how the operator of
  * Eq. ellipticOp3 is computed, never what.

@@ -73,6 +73,7 @@ def lib():
         "dg_poisson_apply": ([vp, i32, i32, vp, vp, vp], i32),
         "dg_helmholtz_apply": ([vp, i32, i32, dbl, vp, vp, vp], i32),
         "dg_operator_apply": ([vp, i32, i32, i32, dbl, vp, vp, vp], i32),
+        "dg_apply_host": ([vp, i32, i32, i32, dbl, vp, vp, vp], i32),
         "dg_operator_diagonal": ([vp, i32, i32, dbl, vp, vp], i32),
         "dg_rhs": ([vp, i32, vp, vp, vp, vp], i32),
         "dg_pcg_solve": ([vp, ctypes.POINTER(SolverOpts), i32, dbl, vp, vp, ctypes.POINTER(SolveInfo), vp], i32),
@@ -214,6 +215,22 @@ class Mesh:
             out = torch.empty_like(u)
         _check(lib().dg_operator_apply(self._h, int(degree or 0), prec, B, float(lam), _tptr(u), _tptr(out),
                                        _stream()))
+        return out
+
+    def apply_host(self, u, lam=0.0, degree=0, out=None):
+        """A u for a contiguous CPU tensor u ([B][K][Np] or [K][Np], float64 or
+        float32; page-locked memory overlaps the copies with the apply), result in
+        a CPU tensor (out, page-locked if u is). Enqueued on the current stream;
+        synchronise it before reading the result."""
+        import torch
+        if u.is_cuda or not u.is_contiguous():
+            raise ValueError("u must be a contiguous CPU tensor")
+        prec = {torch.float64: DG_F64, torch.float32: DG_F32}[u.dtype]
+        B = 1 if u.dim() == 2 else u.shape[0]
+        if out is None:
+            out = torch.empty_like(u, pin_memory=u.is_pinned())
+        _check(lib().dg_apply_host(self._h, int(degree or 0), prec, B, float(lam), ctypes.c_void_p(u.data_ptr()),
+                                   ctypes.c_void_p(out.data_ptr()), _stream()))
         return out
 
     def set_kernel(self, degree, prec, helmholtz, kernel):

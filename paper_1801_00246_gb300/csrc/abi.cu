@@ -359,6 +359,7 @@ dg_status dg_mesh_destroy(dg_mesh* m) {
   if (!m) return DG_OK;
   free_workspace(m);
   free_ins_workspace(m);
+  free_host_apply(m);
   cudaFree(m->face32);
   cudaFree(m->oz_scratch);
   cudaFree(m->t64_scratch);

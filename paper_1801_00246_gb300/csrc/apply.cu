@@ -407,6 +407,12 @@ bool kernel_valid(int kernel, int degree, bool f64) {
   }
 }
 
+int selected_kernel(const dg_mesh* m, int degree, dg_prec prec, bool helm) {
+  if (prec == DG_F64_DFMA) return DG_KERNEL_TILE;
+  const int k = m->kern[degree][prec == DG_F32 ? 1 : 0][helm ? 1 : 0];
+  return k == DG_KERNEL_AUTO ? default_kernel(degree, prec == DG_F64) : k;
+}
+
 cudaError_t launch_apply(const dg_mesh* mc, int degree, dg_prec prec, int B, double lambda, const void* u, void* Au,
                          cudaStream_t st, double* c1_scratch) {
   dg_mesh* m = const_cast<dg_mesh*>(mc);

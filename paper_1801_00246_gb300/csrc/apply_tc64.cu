@@ -192,6 +192,7 @@ struct GradOut {
   double *FNu, *FNd;  // [3 (N+1)][ldc]: u and n.grad u at the element's face nodes
   int* exy;     // [rows]: largest exponent of the row's Y values (for the output product)
   int* exf;     // [rows] or null: set to "none" here when the face columns keep their own exponent
+  int64_t row0;  // global index of the launch's first row (Y, FNu, FNd, exy, exf start there)
 };
 
 // out[r][c] = sum_k A[c][k] X[r][k] for r < rows, c < M, k < Kd (A sliced in
@@ -366,7 +367,7 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
       int ymax = -1100;  // MODE 1: largest exponent of the Y columns this thread writes
       float gh[6];  // MODE 1: Grr, Grs, Gss as float-float
       if (MODE == 1) {
-        const int64_t el = (live ? row : 0) % go.K;
+        const int64_t el = ((live ? row : 0) + go.row0) % go.K;
         const double* gg = go.gx + 16 * el;
 #pragma unroll
         for (int t = 0; t < 3; ++t) {
@@ -492,7 +493,7 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
                 yr[(Np + n) * ldc] = dws;
                 ymax = max(ymax, max(exp_bound64(dwr), exp_bound64(dws)));
                 const double un = __ldg(X + row * ldx + n);
-                const int64_t el = row % go.K;
+                const int64_t el = (row + go.row0) % go.K;
                 const double* gg = go.gx + 16 * el;
                 if (go.helm) {
                   const int eu = exp_bound64(un);
@@ -559,14 +560,16 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
 // float-float scaled by the entry's largest input; the row's largest exponent
 // (exy: raised from the value the gradient product wrote for the volume
 // columns) for the output product's slicing.
-__global__ void __launch_bounds__(256) tc64_face_fill(int N, int64_t K, int64_t nE, const double* __restrict__ gx,
+__global__ void __launch_bounds__(256) tc64_face_fill(int N, int64_t K, int64_t r0, int64_t nE,
+                                                      const double* __restrict__ gx,
                                                       const int32_t* __restrict__ conn,
                                                       const double* __restrict__ FNu,
                                                       const double* __restrict__ FNd, double* __restrict__ Y,
                                                       int64_t ldc, int* __restrict__ exy) {
   const int Np = (N + 1) * (N + 2) / 2, Nfp = N + 1, NFN = 3 * Nfp;
   const ff cpen{float((N + 1) * (N + 2)) * 0.5f, 0.f};
-  for (int64_t be = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; be < nE; be += int64_t(gridDim.x) * blockDim.x) {
+  for (int64_t be = r0 + int64_t(blockIdx.x) * blockDim.x + threadIdx.x; be < nE;
+       be += int64_t(gridDim.x) * blockDim.x) {  // rows r0 .. nE - 1
     const int64_t el = be % K, boff = be - el;
     int ym = -1100;
     for (int f = 0; f < 3; ++f) {
@@ -832,8 +835,25 @@ bool tc64_ops_ready(int degree) {
   return t64_ops(nullptr, degree, false, &e) != nullptr;
 }
 
+namespace {
+// The largest forward distance from an element to one of its neighbours (rows),
+// from the host copy of the connectivity; kept with the mesh.
+int64_t t64_reach(dg_mesh* m) {
+  if (m->nb_reach < 0) {
+    int64_t r = 0;
+    for (int64_t e = 0; e < m->K; ++e)
+      for (int f = 0; f < 3; ++f) {
+        const int32_t code = m->conn_h[size_t(3 * e + f)];
+        if (code >= 0) r = std::max<int64_t>(r, int64_t(code >> 2) - e);
+      }
+    m->nb_reach = r;
+  }
+  return m->nb_reach;
+}
+}  // namespace
+
 cudaError_t launch_apply_tc64(dg_mesh* m, int degree, int B, double lambda, const double* u, double* Au,
-                              cudaStream_t st, double* scratch) {
+                              cudaStream_t st, double* scratch, const ApplyChunks* chunks) {
   if (B < 1) return cudaSuccess;
   if (!tc64_supported(degree)) return cudaErrorInvalidValue;
   cudaError_t e;
@@ -865,33 +885,62 @@ cudaError_t launch_apply_tc64(dg_mesh* m, int degree, int B, double lambda, cons
   int* exy = reinterpret_cast<int*>(FNd + size_t(ldc) * NFN);
   const bool split = ops->outv.blocks != nullptr;
   int* exf = split ? exy + 2 * (size_t(nE + 1) / 2) : nullptr;  // the face columns' own exponents
-  GradOut go{N, m->K, m->geox, Y, ldc, helm ? 1 : 0, lambda, FNu, FNd, exy, exf};
-  e = gemm_launch<1>(ops->grad, nE, u, Np, nullptr, 0, nullptr, go, st);
+  const bool chunked = chunks && chunks->n > 0 && chunks->bounds && chunks->bounds[chunks->n] == nE;
+  const int nch = chunked ? chunks->n : 1;
+  const int64_t whole[2] = {0, nE};
+  const int64_t* bnd = chunked ? chunks->bounds : whole;
+  int sms = 0;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  {
-    int sms = 0;
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    const int64_t blocks = std::min<int64_t>((nE + 255) / 256, int64_t(sms) * 16);  // a thread per element
-    tc64_face_fill<<<unsigned(blocks), 256, 0, st>>>(N, m->K, nE, m->geox, m->conn, FNu, FNd, Y, ldc,
+  // a chunk's neighbour phase needs the gradient products of every chunk that
+  // holds one of its rows' neighbours: rows up to (last row + reach)
+  const int64_t reach = nch > 1 ? t64_reach(m) : nE;
+  auto ready_after = [&](int c) {  // the last chunk whose gradient product chunk c's face fill needs
+    const int64_t last = std::min<int64_t>(nE - 1, bnd[c + 1] - 1 + reach);
+    int j = c;
+    while (j + 1 < nch && bnd[j + 1] <= last) ++j;
+    return j;
+  };
+  auto finish = [&](int c) -> cudaError_t {  // face fill and output product of chunk c
+    const int64_t r0 = bnd[c], n = bnd[c + 1] - r0;
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, int64_t(sms) * 16);  // a thread per element
+    tc64_face_fill<<<unsigned(blocks), 256, 0, st>>>(N, m->K, r0, r0 + n, m->geox, m->conn, FNu, FNd, Y, ldc,
                                                      split ? exf : exy);
     note_launch();
-    e = cudaGetLastError();
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    double* out = Au + r0 * Np;
+    const double* Yc = Y + r0;
+    const int* ey = exy + r0;
+    if (split) {  // Au = [Br Bs] Y_v + (face blocks) Y_f (+ M Y_h), the face block with its own exponents
+      err = gemm_launch<0>(ops->outv, n, Yc, ldc, out, Np, ey, GradOut{}, st, 0, 1);
+      if (err == cudaSuccess)
+        err = gemm_launch<0>(ops->outf, n, Yc + 2 * Np * ldc, ldc, out, Np, exf + r0, GradOut{}, st, 1, 1);
+      if (err == cudaSuccess && helm)
+        err = gemm_launch<0>(ops->mh, n, Yc + (2 * Np + 3 * NFN) * ldc, ldc, out, Np, ey, GradOut{}, st, 1, 1);
+    } else if (helm && !ops->outh.blocks) {  // [OB | M] is too deep for exact group sums: OB Y, then += M (lambda J u)
+      const int KY = 2 * Np + 3 * NFN;
+      err = gemm_launch<0>(ops->out, n, Yc, ldc, out, Np, ey, GradOut{}, st, 0, 1);
+      if (err == cudaSuccess) err = gemm_launch<0>(ops->mh, n, Yc + KY * ldc, ldc, out, Np, ey, GradOut{}, st, 1, 1);
+    } else {
+      err = gemm_launch<0>(helm ? ops->outh : ops->out, n, Yc, ldc, out, Np, ey, GradOut{}, st, 0, 1);
+    }
+    if (err != cudaSuccess) return err;
+    if (chunked && chunks->after) err = chunks->after(chunks->ctx, c, r0, r0 + n);
+    return err;
+  };
+  int done = 0;  // chunks whose face fill and output product are issued
+  for (int c = 0; c < nch; ++c) {  // gradient product, element-local
+    const int64_t r0 = bnd[c], r1 = bnd[c + 1];
+    if (chunked && chunks->before && (e = chunks->before(chunks->ctx, c, r0, r1)) != cudaSuccess) return e;
+    GradOut go{N, m->K, m->geox, Y + r0, ldc, helm ? 1 : 0, lambda, FNu + r0, FNd + r0, exy + r0,
+               exf ? exf + r0 : nullptr, r0};
+    e = gemm_launch<1>(ops->grad, r1 - r0, u + r0 * Np, Np, nullptr, 0, nullptr, go, st);
     if (e != cudaSuccess) return e;
+    while (done < nch && ready_after(done) <= c)
+      if ((e = finish(done++)) != cudaSuccess) return e;
   }
-  if (split) {  // Au = [Br Bs] Y_v + (face blocks) Y_f (+ M Y_h), the face block with its own exponents
-    e = gemm_launch<0>(ops->outv, nE, Y, ldc, Au, Np, exy, GradOut{}, st, 0, 1);
-    if (e == cudaSuccess) e = gemm_launch<0>(ops->outf, nE, Y + 2 * Np * ldc, ldc, Au, Np, exf, GradOut{}, st, 1, 1);
-    if (e != cudaSuccess || !helm) return e;
-    return gemm_launch<0>(ops->mh, nE, Y + (2 * Np + 3 * NFN) * ldc, ldc, Au, Np, exy, GradOut{}, st, 1, 1);
-  }
-  if (helm && !ops->outh.blocks) {  // [OB | M] is too deep for exact group sums: OB Y, then += M (lambda J u)
-    const int KY = 2 * Np + 3 * NFN;
-    e = gemm_launch<0>(ops->out, nE, Y, ldc, Au, Np, exy, GradOut{}, st, 0, 1);
-    if (e != cudaSuccess) return e;
-    return gemm_launch<0>(ops->mh, nE, Y + KY * ldc, ldc, Au, Np, exy, GradOut{}, st, 1, 1);
-  }
-  return gemm_launch<0>(helm ? ops->outh : ops->out, nE, Y, ldc, Au, Np, exy, GradOut{}, st, 0, 1);
+  return cudaSuccess;
 }
 
 cudaError_t tc64_error(int* flag) {

@@ -107,10 +107,20 @@ struct dg_mesh {
   double* t64_scratch = nullptr;
   size_t t64_cap = 0;
   uint64_t scratch_gen = 0;  // bumped whenever face32, oz_scratch or t64_scratch is reallocated
+  int64_t nb_reach = -1;     // largest (neighbour - element) index over interior faces (-1: not computed)
   // apply kernel per [degree][0: FP64, 1: FP32][Helmholtz]; DG_KERNEL_AUTO = built-in choice
   int8_t kern[dgx::kMaxN + 1][2][2] = {};
   uint64_t kern_gen = 0;  // bumped whenever the table changes
+  // host-buffer apply (dg_apply_host): device copies of u and Au (grown on demand),
+  // its two copy streams and events (chunk inputs, chunk outputs, start, done)
+  void* hx_u = nullptr;
+  void* hx_out = nullptr;
+  size_t hx_cap = 0;
+  cudaStream_t hx_in = nullptr, hx_outs = nullptr;
+  static constexpr int kHostChunks = 32;
+  cudaEvent_t hx_ev[2 * kHostChunks + 2] = {};
 };
+void free_host_apply(dg_mesh* m);  // host_apply.cu
 
 namespace dgx {
 
@@ -151,11 +161,25 @@ void tc64_op_free(Tc64Op* op);
 cudaError_t tc64_gemm_launch(const Tc64Op& op, int64_t rows, const double* X, int64_t ldx, double* out, int64_t ldo,
                              cudaStream_t st);
 bool tc64_supported(int degree);
+// An apply in chunks of rows (elements x right-hand sides) for callers that move
+// the data in and out while it runs: the first phase (gradient product) reads
+// only each row's own u, the last (output product) writes each row's Au by
+// itself. `before` is enqueued ahead of chunk i's first phase, `after` behind
+// chunk i's last; the neighbour phase between them runs once over all rows.
+struct ApplyChunks {
+  int n = 0;                        // chunks
+  const int64_t* bounds = nullptr;  // chunk c holds rows [bounds[c], bounds[c + 1]); bounds[n] = all rows
+  cudaError_t (*before)(void* ctx, int chunk, int64_t r0, int64_t r1) = nullptr;
+  cudaError_t (*after)(void* ctx, int chunk, int64_t r0, int64_t r1) = nullptr;
+  void* ctx = nullptr;
+};
 // scratch (optional): tc64_scratch_words(degree, B*K, lambda != 0) device words;
 // null uses the scratch kept with the mesh (grown on demand) and builds the
 // degree's tables on first use, a given scratch needs them built already
 cudaError_t launch_apply_tc64(dg_mesh* m, int degree, int B, double lambda, const double* u, double* Au,
-                              cudaStream_t st, double* scratch = nullptr);
+                              cudaStream_t st, double* scratch = nullptr, const ApplyChunks* chunks = nullptr);
+// The apply kernel the mesh's table selects (DG_KERNEL_AUTO resolved).
+int selected_kernel(const dg_mesh* m, int degree, dg_prec prec, bool helm);
 size_t tc64_scratch_words(int degree, int64_t nE, bool helm);
 cudaError_t ensure_tc64_ops(dg_mesh* m, int degree);  // dg_mesh_setup builds the mesh degree's tables
 bool tc64_ops_ready(int degree);                      // built on the current device (no build)
