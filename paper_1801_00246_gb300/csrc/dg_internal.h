@@ -165,7 +165,8 @@ bool tc64_supported(int degree);
 // the data in and out while it runs: the first phase (gradient product) reads
 // only each row's own u, the last (output product) writes each row's Au by
 // itself. `before` is enqueued ahead of chunk i's first phase, `after` behind
-// chunk i's last; the neighbour phase between them runs once over all rows.
+// chunk i's last; chunk i's neighbour phase runs once the first phase of every
+// chunk holding one of its rows' neighbours has been issued.
 struct ApplyChunks {
   int n = 0;                        // chunks
   const int64_t* bounds = nullptr;  // chunk c holds rows [bounds[c], bounds[c + 1]); bounds[n] = all rows

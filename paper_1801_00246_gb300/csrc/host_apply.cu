@@ -3,10 +3,11 @@
 // kernels allow. The tcgen05 FP64 apply (the FP64 default from degree 3) runs
 // in chunks of rows: chunk i's gradient product, which reads only its own
 // elements' u, starts once chunk i has arrived while later chunks are still
-// being copied in; after the neighbour phase over all rows, chunk i's output
-// product writes its rows of Au and their copy out starts while later chunks
-// are still being computed. Every other kernel copies the whole input in,
-// applies and copies the whole result out, in order on the caller's stream.
+// being copied in; chunk i's neighbour phase and output product follow as soon
+// as the gradient products of the chunks holding its neighbours are done, and
+// its copy out starts while later chunks are still being computed. Every other
+// kernel copies the whole input in, applies and copies the whole result out, in
+// order on the caller's stream.
 #include <algorithm>
 #include <cmath>
 #include <new>
