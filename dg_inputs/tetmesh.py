@@ -11,9 +11,8 @@ each ordering (p, q, r) of the three axes, the tetrahedron (000, 000+e_p,
 vertices are swapped where needed so that every element has a positive
 Jacobian. Cubes are visited with i fastest, then j, then k.
 
-Local face f of a tetrahedron is the triangle opposite local vertex 3 - f:
-face 0 = (v0, v1, v2), face 1 = (v0, v1, v3), face 2 = (v1, v2, v3),
-face 3 = (v0, v2, v3). Boundary faces carry the tag of their side
+Local faces of a tetrahedron: face 0 = (v0, v1, v2), face 1 = (v0, v1, v3),
+face 2 = (v1, v2, v3), face 3 = (v0, v2, v3), opposite local vertices 3, 2, 0, 1. Boundary faces carry the tag of their side
 (x0, x1, y0, y1, z0, z1 -> bc_sides[0..5]): 0 = interior, 1 = Dirichlet,
 2 = Neumann.
 """
@@ -92,3 +91,26 @@ def jittered_tet_grid(n, box=(0.0, 1.0, 0.0, 1.0, 0.0, 1.0), jitter=0.1, seed=0,
         e, f = owners[0]
         bc[e, f] = tag
     return TetMesh(X[:, 0].copy(), X[:, 1].copy(), X[:, 2].copy(), EToV, bc)
+
+
+def permute_local_vertices(mesh, seed):
+    """The same mesh with each element's local vertices renumbered by an even
+    permutation p drawn from default_rng(seed) (even permutations keep the
+    orientation; new local vertex i is old local vertex p[i]), and the face tags
+    moved with them: new face f is opposite new vertex OPP[f], which was old
+    vertex p[OPP[f]], whose opposite face was old face FACE_OPP[p[OPP[f]]]."""
+    from itertools import permutations as _perms
+    OPP = (3, 2, 0, 1)        # the local vertex opposite face f
+    FACE_OPP = (2, 3, 1, 0)   # the local face opposite vertex v
+    even = [p for p in _perms(range(4))
+            if sum(1 for i in range(4) for j in range(i + 1, 4) if p[i] > p[j]) % 2 == 0]
+    rng = np.random.default_rng(seed)
+    pick = rng.integers(0, len(even), size=mesh.K)
+    EToV = np.empty_like(mesh.EToV)
+    bc = np.empty_like(mesh.bc)
+    for e in range(mesh.K):
+        p = even[pick[e]]
+        EToV[e] = mesh.EToV[e, list(p)]
+        for f in range(4):
+            bc[e, f] = mesh.bc[e, FACE_OPP[p[OPP[f]]]]
+    return TetMesh(mesh.VX.copy(), mesh.VY.copy(), mesh.VZ.copy(), EToV, bc)

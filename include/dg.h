@@ -343,8 +343,8 @@ dg_status dg_pcg_jacobi_solve_static(const dg_mesh* mesh, int B, double lambda, 
  * on triangles; nodes equispaced, (r, s, t) = (-1 + 2i/N, -1 + 2j/N, -1 + 2k/N),
  * i + j + k <= N, ordered by k, then j, then i; degrees 1..5. Reference
  * tetrahedron v0 = (-1,-1,-1), v1 = (1,-1,-1), v2 = (-1,1,-1), v3 = (-1,-1,1);
- * local face f is opposite local vertex 3 - f: (v0,v1,v2), (v0,v1,v3),
- * (v1,v2,v3), (v0,v2,v3). Fields are device arrays [B][K][Np],
+ * local faces (v0,v1,v2), (v0,v1,v3), (v1,v2,v3), (v0,v2,v3), opposite
+ * v3, v2, v0, v1. Fields are device arrays [B][K][Np],
  * Np = (N+1)(N+2)(N+3)/6. */
 typedef struct dg_tet_mesh dg_tet_mesh;
 

@@ -24,9 +24,9 @@ paper gives none):
     the paper; equispaced nodes are well conditioned at the degrees used
     here, N <= 4).
 Reference tetrahedron: vertices v0 = (-1,-1,-1), v1 = (1,-1,-1),
-v2 = (-1,1,-1), v3 = (-1,-1,1); local face f is opposite vertex 3 - f:
-face 0 = (v0, v1, v2), face 1 = (v0, v1, v3), face 2 = (v1, v2, v3),
-face 3 = (v0, v2, v3).
+v2 = (-1,1,-1), v3 = (-1,-1,1); local faces face 0 = (v0, v1, v2),
+face 1 = (v0, v1, v3), face 2 = (v1, v2, v3), face 3 = (v0, v2, v3), opposite
+vertices v3, v2, v0, v1.
 
 The nodal basis is built from monomials r^a s^b t^c (a + b + c <= N) through
 the nodal Vandermonde matrix, and every integral is taken by quadrature

@@ -18,8 +18,8 @@
 // Neumann: no face terms); equispaced nodes (i, j, k)/N with i + j + k <= N,
 // ordered by k, then j, then i, whose face nodes form the equispaced triangle
 // of each face. Reference tetrahedron v0 = (-1,-1,-1), v1 = (1,-1,-1),
-// v2 = (-1,1,-1), v3 = (-1,-1,1); face f opposite vertex 3 - f: (v0,v1,v2),
-// (v0,v1,v3), (v1,v2,v3), (v0,v2,v3).
+// v2 = (-1,1,-1), v3 = (-1,-1,1); faces (v0,v1,v2), (v0,v1,v3), (v1,v2,v3),
+// (v0,v2,v3), opposite v3, v2, v0, v1.
 //
 // Reference operators are built on the host from a monomial Vandermonde
 // matrix and Gauss-Jacobi quadrature; a neighbour's face nodes are matched to

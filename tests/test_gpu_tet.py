@@ -142,3 +142,35 @@ def test_tet_argument_errors():
         lib.solve(u, tol=0.0)
     with pytest.raises(P.DgError):
         P.TetMesh.from_inputs(m, 6)
+
+
+@pytest.mark.parametrize("N", range(1, 6))
+def test_tet_apply_parity_renumbered_local_vertices(N):
+    """Each element's vertices renumbered by a seeded even permutation: every
+    pairing of local faces and every rotation of a shared face's nodes occurs,
+    so the neighbour face-node matching is exercised in all its cases."""
+    import torch
+    from dg_inputs.tetmesh import permute_local_vertices
+    m = permute_local_vertices(jittered_tet_grid(3, jitter=0.1, seed=9, bc_sides=MIXED), seed=N)
+    lib, ora = _pair(m, N)
+    u = uniform_field((2, m.K, ora.Np), seed=40 + N)
+    ref = ora.apply(u, lam=1.25)
+    assert rel(lib.apply(cuda(u), lam=1.25).cpu().numpy(), ref) <= tol64(N)
+    assert rel(lib.apply(cuda(u, torch.float32), lam=1.25).cpu().numpy(), ref) <= TOL32
+
+
+@pytest.mark.parametrize("N", [2, 4])
+def test_tet_apply_entrywise_against_abs_bound(N):
+    """Node by node: |A u - (A u)_oracle|_i <= tol (|A| |u|)_i, the scale that
+    bounds the rounding of each node's sum whatever the cancellation."""
+    import torch
+    m = jittered_tet_grid(2, jitter=0.1, seed=6, bc_sides=MIXED)
+    lib, ora = _pair(m, N)
+    u = uniform_field((m.K, ora.Np), seed=8)
+    A = ora.assemble(0.0)
+    bound = (abs(A) @ np.abs(u).ravel()).reshape(u.shape)
+    ref = ora.apply(u)
+    got64 = lib.apply(cuda(u)).cpu().numpy()
+    got32 = lib.apply(cuda(u, torch.float32)).cpu().numpy()
+    assert np.all(np.abs(got64 - ref) <= tol64(N) * bound)
+    assert np.all(np.abs(got32 - ref) <= TOL32 * bound)

@@ -103,3 +103,25 @@ def test_tet_h_convergence_rate():
             e = x @ Lq.T - u(X[..., 0], X[..., 1], X[..., 2])
             errs.append(np.sqrt(np.sum(e ** 2 * wq[None] * S.geo.J[:, None])))
         assert np.log2(errs[0] / errs[1]) > rmin, (N, errs)
+
+
+@pytest.mark.parametrize("N", [1, 3])
+def test_tet_operator_invariant_under_local_vertex_renumbering(N):
+    """Renumbering each element's vertices (even permutations, face tags moved
+    with them) renumbers the nodes of the element and nothing else: A u at every
+    physical node is unchanged."""
+    from dg_inputs.tetmesh import permute_local_vertices
+    m = jittered_tet_grid(2, jitter=0.1, seed=3, bc_sides=(1, 2, 2, 1, 1, 2))
+    pm = permute_local_vertices(m, 5)
+    S1 = TetSipdg(m.VX, m.VY, m.VZ, m.EToV, m.bc, N)
+    S2 = TetSipdg(pm.VX, pm.VY, pm.VZ, pm.EToV, pm.bc, N)
+    f = lambda x, y, z: np.sin(x + 2 * y) * np.cos(z) + x * z
+    A1 = S1.apply(f(S1.x, S1.y, S1.z), lam=0.5)
+    A2 = S2.apply(f(S2.x, S2.y, S2.z), lam=0.5)
+    X1 = np.stack([S1.x, S1.y, S1.z], -1)
+    X2 = np.stack([S2.x, S2.y, S2.z], -1)
+    for e in range(S1.K):
+        d = np.linalg.norm(X1[e][:, None, :] - X2[e][None, :, :], axis=-1)
+        perm = d.argmin(axis=1)
+        assert np.all(d[np.arange(S1.Np), perm] < 1e-12)
+        assert np.abs(A1[e] - A2[e][perm]).max() <= 1e-12 * np.abs(A1).max()
