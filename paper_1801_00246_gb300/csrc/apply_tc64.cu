@@ -54,7 +54,9 @@ constexpr int kSplitDepth = 208;
 constexpr int kABytes = kSl * kT * kKC * 2;  // one data chunk, 8 slices: 64 KB
 constexpr int kBBytes = kSl * kNC * kKC * 2; // one operator block, 8 slices: 24 KB
 constexpr int kASlice = kT * kKC * 2, kBSlice = kNC * kKC * 2;
-constexpr int kSmem = 2 * kABytes + 2 * kBBytes + 4 * kT * 4 + 12 * 8;  // the tail: 10 mbarriers, slot, 2 flags
+constexpr int kNodeTab = 72;  // entries of the gradient product's node-to-face table (Np <= 66)
+// the tail: 10 mbarriers, slot, 2 flags, the node-to-face table
+constexpr int kSmem = 2 * kABytes + 2 * kBBytes + 4 * kT * 4 + 12 * 8 + kNodeTab * 4;
 
 __device__ int g_tc64_err;
 
@@ -230,6 +232,9 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
   uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 10);
   int* abort_flag = reinterpret_cast<int*>(slot + 1);
   int* tile_abort = abort_flag + 1;  // the slicers' common copy of abort_flag at a tile's start
+  // MODE 1: per node n the face nodes it is, packed (fa + 1) | ja << 4 | (fb + 1) << 8 | jb << 12
+  // (face f, position j; a corner is on two faces; 0 in the face field: none)
+  int* nodetab = reinterpret_cast<int*>(reinterpret_cast<uint8_t*>(bars) + 12 * 8);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t ntiles = (rows + kT - 1) / kT;
   // with at most two data chunks per row, both stay in the two buffers for all
@@ -248,6 +253,23 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
     tc::mbar_init_fence();
   }
   if (warp == 0) tc::tmem_alloc(slot, 512);
+  if (MODE == 1 && tid < (go.N + 1) * (go.N + 2) / 2 && tid < kNodeTab) {
+    const int N = go.N, n = tid;
+    int rrow = 0;  // n's row of constant s
+    while (n >= (rrow + 1) * (N + 1) - (rrow + 1) * rrow / 2) ++rrow;
+    const int rs0 = rrow * (N + 1) - rrow * (rrow - 1) / 2, len = N + 1 - rrow;
+    int fa = -1, ja = 0, fb = -1, jb = 0;
+    if (rrow == 0) fa = 0, ja = n;  // face 0, j = n
+    if (n == rs0 + len - 1) {       // face 1, j = row
+      if (fa < 0) fa = 1, ja = rrow;
+      else fb = 1, jb = rrow;
+    }
+    if (n == rs0 && fb < 0) {  // face 2, j = N - row
+      if (fa < 0) fa = 2, ja = N - rrow;
+      else fb = 2, jb = N - rrow;
+    }
+    nodetab[n] = (fa + 1) | (ja << 4) | ((fb + 1) << 8) | (jb << 12);
+  }
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
@@ -366,9 +388,9 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
       have_next = false;
       int ymax = -1100;  // MODE 1: largest exponent of the Y columns this thread writes
       float gh[6];  // MODE 1: Grr, Grs, Gss as float-float
+      const double* gg = nullptr;  // MODE 1: the row's element geometry
       if (MODE == 1) {
-        const int64_t el = ((live ? row : 0) + go.row0) % go.K;
-        const double* gg = go.gx + 16 * el;
+        gg = go.gx + 16 * (((live ? row : 0) + go.row0) % go.K);
 #pragma unroll
         for (int t = 0; t < 3; ++t) {
           const ff gf = d2ff(__ldg(gg + 1 + t), 0);
@@ -493,8 +515,6 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
                 yr[(Np + n) * ldc] = dws;
                 ymax = max(ymax, max(exp_bound64(dwr), exp_bound64(dws)));
                 const double un = __ldg(X + row * ldx + n);
-                const int64_t el = (row + go.row0) % go.K;
-                const double* gg = go.gx + 16 * el;
                 if (go.helm) {
                   const int eu = exp_bound64(un);
                   const ff lj = ff_mul(d2ff(go.lambda, 0), d2ff(__ldg(gg), 0));
@@ -504,19 +524,8 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
                   ymax = max(ymax, exp_bound64(dv));
                 }
                 // face data at the face nodes this node is (a corner belongs to two faces)
-                int rrow = 0;
-                while (n >= (rrow + 1) * (N + 1) - (rrow + 1) * rrow / 2) ++rrow;  // n's row of constant s
-                const int rs0 = rrow * (N + 1) - rrow * (rrow - 1) / 2, len = N + 1 - rrow;
-                int fa = -1, ja = 0, fb = -1, jb = 0;
-                if (rrow == 0) fa = 0, ja = n;                         // face 0, j = n
-                if (n == rs0 + len - 1) {                              // face 1, j = row
-                  if (fa < 0) fa = 1, ja = rrow;
-                  else fb = 1, jb = rrow;
-                }
-                if (n == rs0 && fb < 0) {                              // face 2, j = N - row
-                  if (fa < 0) fa = 2, ja = N - rrow;
-                  else fb = 2, jb = N - rrow;
-                }
+                const int nt = nodetab[n];
+                const int fa = (nt & 15) - 1, ja = (nt >> 4) & 15, fb = ((nt >> 8) & 15) - 1, jb = (nt >> 12) & 15;
 #pragma unroll
                 for (int t = 0; t < 2; ++t) {
                   const int f = t == 0 ? fa : fb, j = t == 0 ? ja : jb;
