@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(kTile) tc_face(int64_t K, int64_t nE, const fl
     float* cur = ut + buf * (kTile * Np);
     const int e = tid;
     const bool live = e < ne;
-    const int64_t el = (e0 + e) % K;
+    const int64_t el = e0 + e < K ? e0 + e : (e0 + e) % K;
     // the face normals, loaded while the tile and the products are in flight
     float nrm[6];
 #pragma unroll
@@ -416,7 +416,7 @@ __global__ void __launch_bounds__(512, 1) tc_apply(int64_t K, int64_t nE, const 
     float* cur = ut + buf * (kTile * Np);
     const bool live = e < ne;
     const int64_t be = e0 + e;
-    const int64_t el = be % K;  // element of the mesh (first right-hand side: no division)
+    const int64_t el = be < K ? be : be % K;  // element of the mesh (first right-hand side: no division)
     const int64_t boff = be - el;
     const float* g = gx + 16 * el;
     float s_own = 0.f;  // 2^{-s} of this pair's Y scale, for the epilogue

@@ -579,7 +579,7 @@ __global__ void __launch_bounds__(256) tc64_face_fill(int N, int64_t K, int64_t 
   const ff cpen{float((N + 1) * (N + 2)) * 0.5f, 0.f};
   for (int64_t be = r0 + int64_t(blockIdx.x) * blockDim.x + threadIdx.x; be < nE;
        be += int64_t(gridDim.x) * blockDim.x) {  // rows r0 .. nE - 1
-    const int64_t el = be % K, boff = be - el;
+    const int64_t el = be < K ? be : be % K, boff = be - el;  // first right-hand side: no division
     int ym = -1100;
     for (int f = 0; f < 3; ++f) {
       const double* g = gx + 16 * el + 4 + 4 * f;

@@ -297,6 +297,15 @@ constexpr int tet_lift_words() {
   return 4 * D::Np * D::Np + 4 * D::Nfp * D::Nfp + D::EB * (7 * D::Np + 4 * D::NF);
 }
 
+// The mesh element of batch row g, from the element e0 = be0 mod K of the
+// batch's first row: subtractions only (rows past K wrap to the next
+// right-hand side), no 64-bit division in the per-item loops.
+__device__ __forceinline__ int64_t tet_elem(int64_t e0, int g, int64_t K) {
+  int64_t e = e0 + g;
+  while (e >= K) e -= K;
+  return e;
+}
+
 // First kernel of the apply: per element the reference gradient ub_b = D_b u at
 // every node, then (a) w_a = sum_b G_ab ub_b ([nE][3][Np]) and (b) the face
 // traces (u, n.grad u) at the element's face nodes with its own outward normal
@@ -317,7 +326,9 @@ __global__ void __launch_bounds__(kTetThreads) tet_grad(int64_t K, int64_t nE, O
     sDT[q] = ops[L.D[b] + i * Np + m];
   }
   const int slot = threadIdx.x / Np, i = threadIdx.x - slot * Np;
-  for (int64_t be0 = int64_t(blockIdx.x) * EB; be0 < nE; be0 += int64_t(gridDim.x) * EB) {
+  const int64_t stride = int64_t(gridDim.x) * EB, strideK = stride % K;
+  int64_t e0 = (int64_t(blockIdx.x) * EB) % K;  // be0 mod K, advanced with be0
+  for (int64_t be0 = int64_t(blockIdx.x) * EB; be0 < nE; be0 += stride, e0 = e0 + strideK < K ? e0 + strideK : e0 + strideK - K) {
     const int nv = int(nE - be0 < EB ? nE - be0 : EB);
     __syncthreads();
     for (int q = threadIdx.x; q < nv * Np; q += kTetThreads) su[q] = u[be0 * Np + q];
@@ -341,7 +352,7 @@ __global__ void __launch_bounds__(kTetThreads) tet_grad(int64_t K, int64_t nE, O
       for (int r = 0; r < kR; ++r) {
         const int g = slot + GS * r;
         if (g >= nv) continue;
-        const int64_t be = be0 + g, e = be % K;
+        const int64_t be = be0 + g, e = tet_elem(e0, g, K);
         const T* G = geo + e * kGeo + 1;  // rr rs rt ss st tt
         sub[(g * 3 + 0) * Np + i] = acc[r][0];
         sub[(g * 3 + 1) * Np + i] = acc[r][1];
@@ -356,7 +367,7 @@ __global__ void __launch_bounds__(kTetThreads) tet_grad(int64_t K, int64_t nE, O
     for (int q = threadIdx.x; q < nv * NF; q += kTetThreads) {
       const int g = q / NF, fj = q - g * NF, f = fj / D::Nfp;
       const int k = fmask[fj];
-      const int64_t e = (be0 + g) % K;
+      const int64_t e = tet_elem(e0, g, K);
       const T* nr = geo + e * kGeo + 7 + 8 * f;
       const T* ub = sub + g * 3 * Np;
       T* t2 = tr + ((be0 + g) * NF + fj) * 2;
@@ -401,7 +412,9 @@ __global__ void __launch_bounds__(kTetThreads) tet_lift(int64_t K, int64_t nE, O
     sMf[q] = ops[L.Mf[f] + (q - f * Nfp * Nfp)];
   }
   const int slot = threadIdx.x / Np, i = threadIdx.x - slot * Np;
-  for (int64_t be0 = int64_t(blockIdx.x) * EB; be0 < nE; be0 += int64_t(gridDim.x) * EB) {
+  const int64_t stride = int64_t(gridDim.x) * EB, strideK = stride % K;
+  int64_t e0 = (int64_t(blockIdx.x) * EB) % K;  // be0 mod K, advanced with be0
+  for (int64_t be0 = int64_t(blockIdx.x) * EB; be0 < nE; be0 += stride, e0 = e0 + strideK < K ? e0 + strideK : e0 + strideK - K) {
     const int nv = int(nE - be0 < EB ? nE - be0 : EB);
     __syncthreads();
     if (HELM)
@@ -409,7 +422,7 @@ __global__ void __launch_bounds__(kTetThreads) tet_lift(int64_t K, int64_t nE, O
     for (int q = threadIdx.x; q < nv * 3 * Np; q += kTetThreads) sw[q] = w[be0 * 3 * Np + q];
     for (int q = threadIdx.x; q < nv * NF; q += kTetThreads) {  // jumps and averages
       const int g = q / NF, fj = q - g * NF, f = fj / Nfp;
-      const int64_t be = be0 + g, e = be % K;
+      const int64_t be = be0 + g, e = tet_elem(e0, g, K);
       const int c = conn[4 * e + f];
       const T* own = tr + (be * NF + fj) * 2;
       T jm = T(0), av = T(0);
@@ -427,7 +440,7 @@ __global__ void __launch_bounds__(kTetThreads) tet_lift(int64_t K, int64_t nE, O
     __syncthreads();
     for (int q = threadIdx.x; q < nv * NF; q += kTetThreads) {  // face-mass products
       const int g = q / NF, fj = q - g * NF, f = fj / Nfp, j = fj - f * Nfp;
-      const int64_t e = (be0 + g) % K;
+      const int64_t e = tet_elem(e0, g, K);
       const T* gf = geo + e * kGeo + 7 + 8 * f;
       const T sJ = gf[6], tau = gf[7];
       const T* Mf = sMf + f * Nfp * Nfp;
@@ -466,7 +479,7 @@ __global__ void __launch_bounds__(kTetThreads) tet_lift(int64_t K, int64_t nE, O
         const int g = slot + GS * r;
         extra[r] = T(0);
         if (g >= nv) continue;
-        const int64_t e = (be0 + g) % K;
+        const int64_t e = tet_elem(e0, g, K);
         const T* ge = geo + e * kGeo;
         const T J = ge[0];
         T y0 = T(0), y1 = T(0), y2 = T(0), f1 = T(0);
