@@ -662,7 +662,7 @@ def run_tet(args):
         K, Np, Nfp = mesh.K, mesh.Np, (N + 1) * (N + 2) // 2
         for B in [int(b) for b in args.tet_batches.split(",")]:
             u64 = torch.from_numpy(uniform_field((B, K, Np), seed=1)).cuda()
-            for key, u in (("f64", u64), ("f32", u64.float())):
+            for key, u, pipe in (("f64", u64, False), ("f64", u64, True), ("f32", u64.float(), False)):
                 o = torch.empty_like(u)
                 word = u.element_size()
                 for lam in (0.0, 1.0):
@@ -671,7 +671,7 @@ def run_tet(args):
                         flush_buf.fill_(1.0)
                         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                         e0.record()
-                        mesh.apply(u, lam=lam, out=o)
+                        mesh.apply(u, lam=lam, out=o, fp64_pipe=pipe)
                         e1.record()
                         torch.cuda.synchronize()
                         if it >= args.warmup:
@@ -680,7 +680,8 @@ def run_tet(args):
                     nbytes = K * (2 * B * Np * word + 40 * word + 4 * 4 + 4 * Nfp * 4)
                     print(json.dumps({
                         "tet": True, "N": N, "Np": Np, "K": K, "B": B, "op": "helmholtz" if lam else "poisson",
-                        "prec": key, "ms": t * 1e3, "gdofs": B * K * Np / t / 1e9,
+                        "prec": key, "kernel": "fp64_pipe" if pipe else ("tc64" if key == "f64" else "cuda_cores"),
+                        "ms": t * 1e3, "gdofs": B * K * Np / t / 1e9,
                         "hbm_gbs": nbytes / t / 1e9, "hbm_frac": nbytes / t / 1e9 / pk["hbm_gbs"]}), flush=True)
             del u64
         del mesh

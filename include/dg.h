@@ -359,11 +359,16 @@ dg_status dg_tet_mesh_destroy(dg_tet_mesh* mesh);
 dg_status dg_tet_mesh_info(const dg_tet_mesh* mesh, int* N, int64_t* K, int* Np);
 /* Node coordinates into device [K][Np] arrays x, y, z. */
 dg_status dg_tet_mesh_nodes(const dg_tet_mesh* mesh, double* x, double* y, double* z, void* stream);
-/* Au = A(lambda) u for B right-hand sides, FP64 (DG_F64) or FP32 (DG_F32), in
- * two kernels (reference gradient and face traces, then lift and output). The
+/* Au = A(lambda) u for B right-hand sides. DG_F64: the dense products ([Dr; Ds;
+ * Dt] u, the mass matrix, [Dr^T Ds^T Dt^T]) as exactly sliced FP64 products on
+ * the tcgen05 tensor cores, the pointwise and face stages on CUDA cores in FP64;
+ * DG_F64_DFMA (and DG_F64 at degrees 1 and 2): everything on the FP64 pipe;
+ * DG_F32: FP32. The FP32 and FP64-pipe
+ * forms run in two kernels (reference gradient and face traces, then lift and
+ * output). The
  * first call at a batch size (and precision) larger than any before allocates
- * the mesh's apply scratch, (3 Np + 8 Nfp) B K words, Nfp = (N+1)(N+2)/2;
- * applies on one mesh must not overlap. */
+ * the mesh's apply scratch ((3 Np + 8 Nfp) B K words, Nfp = (N+1)(N+2)/2; about
+ * (11 Np + 16 Nfp) B K doubles for DG_F64); applies on one mesh must not overlap. */
 dg_status dg_tet_apply(const dg_tet_mesh* mesh, dg_prec prec, int B, double lambda, const void* u, void* Au,
                        void* stream);
 /* b = J M f - L(g) (the Dirichlet problem's weak right-hand side, as dg_rhs). */

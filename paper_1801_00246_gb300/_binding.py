@@ -352,13 +352,16 @@ class TetMesh:
         _check(lib().dg_tet_mesh_nodes(self._h, _tptr(x), _tptr(y), _tptr(z), _stream()))
         return x, y, z
 
-    def apply(self, u, lam=0.0, out=None):
-        """A(lam) u; u float64 or float32 CUDA [B][K][Np] or [K][Np] (the dtype picks the precision)."""
+    def apply(self, u, lam=0.0, out=None, fp64_pipe=False):
+        """A(lam) u; u float64 or float32 CUDA [B][K][Np] or [K][Np] (the dtype picks the precision;
+        float64 runs its products on the tensor cores unless fp64_pipe=True)."""
         import torch
         u = u.contiguous()
         B = 1 if u.dim() == 2 else u.shape[0]
         out = torch.empty_like(u) if out is None else out
         prec = DG_F64 if u.dtype == torch.float64 else DG_F32
+        if fp64_pipe and prec == DG_F64:
+            prec = DG_F64_DFMA
         _check(lib().dg_tet_apply(self._h, prec, B, float(lam), _tptr(u), _tptr(out), _stream()))
         return out
 

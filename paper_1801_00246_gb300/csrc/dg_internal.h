@@ -157,9 +157,10 @@ cudaError_t launch_wait_selftest(double seconds, int* gave_up_dev, cudaStream_t 
 struct Tc64Op;
 cudaError_t tc64_op_create(const std::vector<double>& A, int M, int K, Tc64Op* op);
 void tc64_op_free(Tc64Op* op);
-// out[r][c] = sum_k A[c][k] X[r][k] (FP64, exact slicing on the tcgen05 tensor cores)
+// out[r][c] (+)= sum_k A[c][k] X[r][k] (FP64, exact slicing on the tcgen05 tensor cores;
+// accum: add to out instead of overwriting it); X row-major with leading dimension ldx
 cudaError_t tc64_gemm_launch(const Tc64Op& op, int64_t rows, const double* X, int64_t ldx, double* out, int64_t ldo,
-                             cudaStream_t st);
+                             cudaStream_t st, int accum = 0);
 bool tc64_supported(int degree);
 // An apply in chunks of rows (elements x right-hand sides) for callers that move
 // the data in and out while it runs: the first phase (gradient product) reads

@@ -266,6 +266,11 @@ struct dg_tet_mesh {
   // apply scratch: w ([B K][3][Np]) and face traces ([B K][4 Nfp][2]), grown on demand
   mutable void* ascr = nullptr;
   mutable size_t ascr_bytes = 0;
+  // FP64 products on the tensor cores: [Dr; Ds; Dt], M, [Dr^T Ds^T Dt^T] (built at setup),
+  // and their scratch (grown on demand)
+  dgx::Tc64Op t64_grad, t64_mass, t64_out;
+  mutable double* t64scr = nullptr;
+  mutable size_t t64scr_bytes = 0;
 };
 
 namespace dgx {
@@ -524,6 +529,144 @@ __global__ void __launch_bounds__(kTetThreads) tet_lift(int64_t K, int64_t nE, O
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP64 apply with its dense products on the tensor cores (exactly sliced FP64
+// GEMMs, out[r] = A X[r]): UB = [Dr; Ds; Dt] u, MW = M [J w_0; J w_1; J w_2;
+// lambda J u] and Au += [Dr^T Ds^T Dt^T] z, with the pointwise stages between
+// them on CUDA cores:
+//   tet64_point1: W = J G UB (and lambda J u), face traces (u, n.grad u);
+//   tet64_face:   jumps and averages, F1 = -sJ Mf (avg + tau jump), F2 = sJ Mf jump / 2;
+//   tet64_point2: z_b = MW_b + y_b (y_b the lifted F2), Au = sum of F1 at the node
+//                 [+ lambda J M u], which the last product adds D_b^T z_b to.
+// The same operator as tet_grad / tet_lift, with the FP64 products no longer on
+// the FP64 pipe.
+template <int N>
+__global__ void __launch_bounds__(256) tet64_point1(int64_t K, int64_t nE, int R4, double lambda,
+                                                    const int* __restrict__ fmask, const double* __restrict__ geo,
+                                                    const double* __restrict__ u, const double* __restrict__ UB,
+                                                    double* __restrict__ W, double2* __restrict__ tr) {
+  constexpr int Np = (N + 1) * (N + 2) * (N + 3) / 6, Nfp = (N + 1) * (N + 2) / 2, NF = 4 * Nfp;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < nE * Np; q += stride) {
+    const int64_t be = q / Np, e = be < K ? be : be % K;
+    const int i = int(q - be * Np);
+    const double* g = geo + e * kGeo;
+    const double J = g[0];
+    const double* ub = UB + be * 3 * Np;
+    const double a0 = ub[i], a1 = ub[Np + i], a2 = ub[2 * Np + i];
+    double* wo = W + be * R4 * Np;
+    wo[i] = J * (g[1] * a0 + g[2] * a1 + g[3] * a2);
+    wo[Np + i] = J * (g[2] * a0 + g[4] * a1 + g[5] * a2);
+    wo[2 * Np + i] = J * (g[3] * a0 + g[5] * a1 + g[6] * a2);
+    if (R4 == 4) wo[3 * Np + i] = lambda * J * u[q];
+  }
+  for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < nE * NF; q += stride) {
+    const int64_t be = q / NF, e = be < K ? be : be % K;
+    const int fj = int(q - be * NF), k = fmask[fj];
+    const double* nr = geo + e * kGeo + 7 + 8 * (fj / Nfp);
+    const double* ub = UB + be * 3 * Np;
+    tr[q] = make_double2(u[be * Np + k], nr[0] * ub[k] + nr[1] * ub[Np + k] + nr[2] * ub[2 * Np + k]);
+  }
+}
+
+template <int N>
+struct Tet64Face {
+  static constexpr int Nfp = (N + 1) * (N + 2) / 2, NF = 4 * Nfp;
+  static constexpr int EB = 1024 / NF;  // elements per block iteration
+  static constexpr int words = 4 * Nfp * Nfp + 2 * EB * NF;
+};
+
+template <int N>
+__global__ void __launch_bounds__(256) tet64_face(int64_t K, int64_t nE, OpsLayout L, const double* __restrict__ ops,
+                                                  const double* __restrict__ geo, const int* __restrict__ conn,
+                                                  const int* __restrict__ mapJ, const double2* __restrict__ tr,
+                                                  double* __restrict__ F) {
+  using D = Tet64Face<N>;
+  constexpr int Nfp = D::Nfp, NF = D::NF, EB = D::EB;
+  extern __shared__ __align__(16) unsigned char tet_smem[];
+  double* sMf = reinterpret_cast<double*>(tet_smem);  // [4][l][j]
+  double* sJm = sMf + 4 * Nfp * Nfp;                  // [EB][NF]
+  double* sAv = sJm + EB * NF;
+  for (int q = threadIdx.x; q < 4 * Nfp * Nfp; q += blockDim.x) {
+    const int f = q / (Nfp * Nfp);
+    sMf[q] = ops[L.Mf[f] + (q - f * Nfp * Nfp)];
+  }
+  const int64_t stride = int64_t(gridDim.x) * EB, strideK = stride % K;
+  int64_t e0 = (int64_t(blockIdx.x) * EB) % K;  // be0 mod K, advanced with be0
+  for (int64_t be0 = int64_t(blockIdx.x) * EB; be0 < nE;
+       be0 += stride, e0 = e0 + strideK < K ? e0 + strideK : e0 + strideK - K) {
+    const int nv = int(nE - be0 < EB ? nE - be0 : EB);
+    __syncthreads();
+    for (int q = threadIdx.x; q < nv * NF; q += blockDim.x) {  // jumps and averages
+      const int g = q / NF, fj = q - g * NF, f = fj / Nfp;
+      const int64_t be = be0 + g, e = tet_elem(e0, g, K);
+      const int c = conn[4 * e + f];
+      const double2 own = tr[be * NF + fj];
+      double jm = 0.0, av = 0.0;
+      if (c >= 0) {
+        const double2 nb = tr[(be - e + c) * NF + mapJ[e * NF + fj]];
+        jm = nb.x - own.x;
+        av = 0.5 * (own.y - nb.y);  // the neighbour's trace carries its own (opposite) normal
+      } else if (c == -2) {         // Dirichlet ghost: u+ = -u-, grad u+ = grad u-
+        jm = -2.0 * own.x;
+        av = own.y;
+      }
+      sJm[q] = jm;
+      sAv[q] = av;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < nv * NF; q += blockDim.x) {  // face-mass products
+      const int g = q / NF, fj = q - g * NF, f = fj / Nfp, j = fj - f * Nfp;
+      const int64_t be = be0 + g, e = tet_elem(e0, g, K);
+      const double* gf = geo + e * kGeo + 7 + 8 * f;
+      const double sJ = gf[6], tau = gf[7];
+      const double* Mf = sMf + f * Nfp * Nfp;
+      const double* jf = sJm + g * NF + f * Nfp;
+      const double* af = sAv + g * NF + f * Nfp;
+      double m1 = 0.0, m2 = 0.0;
+#pragma unroll 4
+      for (int l = 0; l < Nfp; ++l) {
+        const double mf = Mf[l * Nfp + j];
+        m1 += mf * (af[l] + tau * jf[l]);
+        m2 += mf * jf[l];
+      }
+      F[(be * 2) * NF + fj] = -sJ * m1;
+      F[(be * 2 + 1) * NF + fj] = 0.5 * sJ * m2;
+    }
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(256) tet64_point2(int64_t K, int64_t nE, int R4, const int* __restrict__ nfs,
+                                                    const double* __restrict__ geo, const double* __restrict__ F,
+                                                    double* __restrict__ MW, double* __restrict__ Au) {
+  constexpr int Np = (N + 1) * (N + 2) * (N + 3) / 6, Nfp = (N + 1) * (N + 2) / 2, NF = 4 * Nfp;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < nE * Np; q += stride) {
+    const int64_t be = q / Np, e = be < K ? be : be % K;
+    const int i = int(q - be * Np);
+    const double* ge = geo + e * kGeo;
+    const double* F1 = F + be * 2 * NF;
+    const double* F2 = F1 + NF;
+    double y0 = 0.0, y1 = 0.0, y2 = 0.0, f1 = 0.0;
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      const int fj = nfs[i * 3 + s];
+      if (fj < 0) continue;
+      const double* nr = ge + 7 + 8 * (fj / Nfp);
+      y0 += nr[0] * F2[fj];
+      y1 += nr[1] * F2[fj];
+      y2 += nr[2] * F2[fj];
+      f1 += F1[fj];
+    }
+    double* mw = MW + be * R4 * Np;
+    mw[i] += y0;
+    mw[Np + i] += y1;
+    mw[2 * Np + i] += y2;
+    Au[q] = R4 == 4 ? f1 + mw[3 * Np + i] : f1;
+  }
+}
+
 // diag(A) per node of one right-hand side ([K][Np], FP64).
 __global__ void tet_diag(int N, int64_t K, OpsLayout L, const double* __restrict__ ops, const int* __restrict__ fmask,
                          const double* __restrict__ geo, const int* __restrict__ conn, double lambda,
@@ -718,6 +861,52 @@ cudaError_t tet_apply_n(const dg_tet_mesh* m, int64_t nE, T lambda, const T* ops
   return cudaGetLastError();
 }
 
+template <int N>
+cudaError_t tet64_tc_n(const dg_tet_mesh* m, int64_t nE, double lambda, const double* u, double* Au, cudaStream_t st) {
+  constexpr int Np = (N + 1) * (N + 2) * (N + 3) / 6, NF = 2 * (N + 1) * (N + 2);
+  const int R4 = lambda != 0.0 ? 4 : 3;
+  auto even = [](size_t n) { return (n + 1) & ~size_t(1); };  // keeps the traces 16-byte aligned
+  const size_t nUB = even(size_t(nE) * 3 * Np), nW = even(size_t(nE) * R4 * Np);
+  const size_t words = nUB + 2 * nW + size_t(nE) * NF * 2 + size_t(nE) * 2 * NF;
+  if (m->t64scr_bytes < words * sizeof(double)) {
+    cudaFree(m->t64scr);
+    m->t64scr = nullptr;
+    m->t64scr_bytes = 0;
+    const cudaError_t e = cudaMalloc(&m->t64scr, words * sizeof(double));
+    if (e != cudaSuccess) return e;
+    m->t64scr_bytes = words * sizeof(double);
+  }
+  double* UB = m->t64scr;
+  double* W = UB + nUB;
+  double* MW = W + nW;
+  double2* tr = reinterpret_cast<double2*>(MW + nW);
+  double* F = reinterpret_cast<double*>(tr + size_t(nE) * NF);
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const unsigned gp = unsigned(std::min<int64_t>((nE * Np + 255) / 256, int64_t(sms) * 16));
+  const unsigned gf = unsigned(std::min<int64_t>((nE + Tet64Face<N>::EB - 1) / Tet64Face<N>::EB, int64_t(sms) * 8));
+  e = tc64_gemm_launch(m->t64_grad, nE, u, Np, UB, 3 * Np, st);
+  if (e != cudaSuccess) return e;
+  tet64_point1<N><<<gp, 256, 0, st>>>(m->K, nE, R4, lambda, m->fmask, m->geo64, u, UB, W, tr);
+  note_launch();
+  tet64_face<N><<<gf, 256, Tet64Face<N>::words * sizeof(double), st>>>(m->K, nE, m->L, m->ops64, m->geo64, m->conn,
+                                                                       m->mapJ, tr, F);
+  note_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  e = tc64_gemm_launch(m->t64_mass, nE * R4, W, Np, MW, Np, st);
+  if (e != cudaSuccess) return e;
+  tet64_point2<N><<<gp, 256, 0, st>>>(m->K, nE, R4, m->nfs, m->geo64, F, MW, Au);
+  note_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return tc64_gemm_launch(m->t64_out, nE, MW, int64_t(R4) * Np, Au, Np, st, 1);
+}
+
+// FP64 on the tensor cores (the default) or, with pipe set, on the FP64 pipe.
+cudaError_t tet64_apply(const dg_tet_mesh* m, int B, double lambda, const double* u, double* Au, bool pipe,
+                        cudaStream_t st);
+
 template <typename T>
 cudaError_t tet_apply_launch(const dg_tet_mesh* m, int B, double lambda, const T* u, T* Au, cudaStream_t st) {
   const bool f64 = sizeof(T) == 8;
@@ -752,6 +941,22 @@ cudaError_t tet_apply_launch(const dg_tet_mesh* m, int B, double lambda, const T
       return cudaErrorInvalidValue;
   }
 }
+
+cudaError_t tet64_apply(const dg_tet_mesh* m, int B, double lambda, const double* u, double* Au, bool pipe,
+                        cudaStream_t st) {
+  // at degrees 1 and 2 the products are too small for the tensor cores to pay
+  // (196,608 elements, N = 1: 0.25 ms on the FP64 pipe against 0.54 ms)
+  if (pipe || !m->t64_grad.blocks || m->N <= 2) return tet_apply_launch<double>(m, B, lambda, u, Au, st);
+  const int64_t nE = int64_t(B) * m->K;
+  switch (m->N) {
+    case 1: return tet64_tc_n<1>(m, nE, lambda, u, Au, st);
+    case 2: return tet64_tc_n<2>(m, nE, lambda, u, Au, st);
+    case 3: return tet64_tc_n<3>(m, nE, lambda, u, Au, st);
+    case 4: return tet64_tc_n<4>(m, nE, lambda, u, Au, st);
+    case 5: return tet64_tc_n<5>(m, nE, lambda, u, Au, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
 }  // namespace
 
 extern "C" {
@@ -761,8 +966,11 @@ dg_status dg_tet_mesh_destroy(dg_tet_mesh* m) {
   for (void* p : {static_cast<void*>(m->ops64), static_cast<void*>(m->ops32), static_cast<void*>(m->fmask),
                   static_cast<void*>(m->geo64), static_cast<void*>(m->geo32), static_cast<void*>(m->conn),
                   static_cast<void*>(m->mapJ), static_cast<void*>(m->nfs), static_cast<void*>(m->xyz),
-                  static_cast<void*>(m->work), m->ascr})
+                  static_cast<void*>(m->work), m->ascr, static_cast<void*>(m->t64scr)})
     cudaFree(p);
+  tc64_op_free(&m->t64_grad);
+  tc64_op_free(&m->t64_mass);
+  tc64_op_free(&m->t64_out);
   delete m;
   return DG_OK;
 }
@@ -977,6 +1185,18 @@ dg_status dg_tet_mesh_setup(int N, int64_t Nv, const double* VX, const double* V
   if (ce == cudaSuccess) ce = upload(&m->mapJ, mapJ);
   if (ce == cudaSuccess) ce = upload(&m->nfs, nfs);
   if (ce == cudaSuccess) ce = upload(&m->xyz, xyz);
+  if (ce == cudaSuccess) {  // the FP64 tensor-core operators
+    std::vector<double> A1(size_t(3) * Np * Np), A3(size_t(Np) * 3 * Np);
+    for (int b = 0; b < 3; ++b)
+      for (int i = 0; i < Np; ++i)
+        for (int q = 0; q < Np; ++q) {
+          A1[(size_t(b) * Np + i) * Np + q] = R.D[b][size_t(i) * Np + q];
+          A3[size_t(i) * 3 * Np + size_t(b) * Np + q] = R.D[b][size_t(q) * Np + i];
+        }
+    ce = tc64_op_create(A1, 3 * Np, Np, &m->t64_grad);
+    if (ce == cudaSuccess) ce = tc64_op_create(R.M, Np, Np, &m->t64_mass);
+    if (ce == cudaSuccess) ce = tc64_op_create(A3, Np, 3 * Np, &m->t64_out);
+  }
   if (ce != cudaSuccess) {
     dg_tet_mesh_destroy(m);
     return fail(ce, "dg_tet_mesh_setup");
@@ -1017,7 +1237,7 @@ dg_status dg_tet_apply(const dg_tet_mesh* m, dg_prec prec, int B, double lambda,
   if (prec == DG_F32)
     e = tet_apply_launch<float>(m, B, lambda, static_cast<const float*>(u), static_cast<float*>(Au), st);
   else if (prec == DG_F64 || prec == DG_F64_DFMA)
-    e = tet_apply_launch<double>(m, B, lambda, static_cast<const double*>(u), static_cast<double*>(Au), st);
+    e = tet64_apply(m, B, lambda, static_cast<const double*>(u), static_cast<double*>(Au), prec == DG_F64_DFMA, st);
   else {
     set_error("unknown precision");
     return DG_ERR_ARG;
@@ -1079,7 +1299,7 @@ dg_status dg_tet_pcg_jacobi_solve(dg_tet_mesh* m, int B, double lambda, double t
                                                       dinv);
   note_launch();
   k_recip<<<gn, 256, 0, st>>>(n, dinv); note_launch();
-  TCK(tet_apply_launch<double>(m, B, lambda, x, Ap, st));
+  TCK(tet64_apply(m, B, lambda, x, Ap, false, st));
   k_jac<<<gv, 256, 0, st>>>(n, B, dinv, b, Ap, r, z); note_launch();
   TCK(cudaMemcpyAsync(p, z, nt * sizeof(double), cudaMemcpyDeviceToDevice, st));
   TCK(dot(b, b, hb.data()));
@@ -1099,7 +1319,7 @@ dg_status dg_tet_pcg_jacobi_solve(dg_tet_mesh* m, int B, double lambda, double t
     return false;
   };
   while (any_active() && it < max_iter) {
-    TCK(tet_apply_launch<double>(m, B, lambda, p, Ap, st));
+    TCK(tet64_apply(m, B, lambda, p, Ap, false, st));
     TCK(dot(p, Ap, hd.data()));
     for (int k = 0; k < B; ++k) {
       if (active[k] != 0.0 && !(hd[k] > 0.0)) {

@@ -44,8 +44,10 @@ def test_tet_apply_parity_mixed_boundaries(N, lam):
     lib, ora = _pair(m, N)
     u = uniform_field((2, m.K, ora.Np), seed=20 + N)
     ref = ora.apply(u, lam=lam)
-    got64 = lib.apply(cuda(u), lam=lam).cpu().numpy()
+    got64 = lib.apply(cuda(u), lam=lam).cpu().numpy()             # products on the tensor cores
     assert rel(got64, ref) <= tol64(N)
+    gotp = lib.apply(cuda(u), lam=lam, fp64_pipe=True).cpu().numpy()
+    assert rel(gotp, ref) <= tol64(N)
     got32 = lib.apply(cuda(u, torch.float32), lam=lam).cpu().numpy()
     assert rel(got32, ref) <= TOL32
     # right-hand sides are independent
@@ -74,7 +76,9 @@ def test_tet_apply_parity_past_one_grid_stride():
     m = jittered_tet_grid(15, jitter=0.1, seed=11, bc_sides=MIXED)
     lib, ora = _pair(m, 2)
     u = uniform_field((4, m.K, ora.Np), seed=5)
-    assert rel(lib.apply(cuda(u), lam=0.7).cpu().numpy(), ora.apply(u, lam=0.7)) <= TOL64
+    ref = ora.apply(u, lam=0.7)
+    assert rel(lib.apply(cuda(u), lam=0.7).cpu().numpy(), ref) <= TOL64
+    assert rel(lib.apply(cuda(u), lam=0.7, fp64_pipe=True).cpu().numpy(), ref) <= TOL64
 
 
 @pytest.mark.parametrize("N", [1, 3, 5])
@@ -156,6 +160,7 @@ def test_tet_apply_parity_renumbered_local_vertices(N):
     u = uniform_field((2, m.K, ora.Np), seed=40 + N)
     ref = ora.apply(u, lam=1.25)
     assert rel(lib.apply(cuda(u), lam=1.25).cpu().numpy(), ref) <= tol64(N)
+    assert rel(lib.apply(cuda(u), lam=1.25, fp64_pipe=True).cpu().numpy(), ref) <= tol64(N)
     assert rel(lib.apply(cuda(u, torch.float32), lam=1.25).cpu().numpy(), ref) <= TOL32
 
 
@@ -171,6 +176,8 @@ def test_tet_apply_entrywise_against_abs_bound(N):
     bound = (abs(A) @ np.abs(u).ravel()).reshape(u.shape)
     ref = ora.apply(u)
     got64 = lib.apply(cuda(u)).cpu().numpy()
+    gotp = lib.apply(cuda(u), fp64_pipe=True).cpu().numpy()
     got32 = lib.apply(cuda(u, torch.float32)).cpu().numpy()
     assert np.all(np.abs(got64 - ref) <= tol64(N) * bound)
+    assert np.all(np.abs(gotp - ref) <= tol64(N) * bound)
     assert np.all(np.abs(got32 - ref) <= TOL32 * bound)
