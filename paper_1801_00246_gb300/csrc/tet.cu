@@ -268,7 +268,7 @@ struct dg_tet_mesh {
   mutable size_t ascr_bytes = 0;
   // FP64 products on the tensor cores: [Dr; Ds; Dt], M, [Dr^T Ds^T Dt^T] (built at setup),
   // and their scratch (grown on demand)
-  dgx::Tc64Op t64_grad, t64_mass, t64_out;
+  dgx::Tc64Op t64_grad, t64_mass, t64_out, t64_face[4];
   mutable double* t64scr = nullptr;
   mutable size_t t64scr_bytes = 0;
 };
@@ -531,13 +531,14 @@ __global__ void __launch_bounds__(kTetThreads) tet_lift(int64_t K, int64_t nE, O
 
 // ---------------------------------------------------------------------------
 // FP64 apply with its dense products on the tensor cores (exactly sliced FP64
-// GEMMs, out[r] = A X[r]): UB = [Dr; Ds; Dt] u, MW = M [J w_0; J w_1; J w_2;
-// lambda J u] and Au += [Dr^T Ds^T Dt^T] z, with the pointwise stages between
-// them on CUDA cores:
+// GEMMs, out[r] = A X[r]): UB = [Dr; Ds; Dt] u, FM_f = diag(Mf_f, Mf_f) [avg +
+// tau jump | jump] per local face f, MW = M [J w_0; J w_1; J w_2; lambda J u] and
+// Au += [Dr^T Ds^T Dt^T] z, with the pointwise stages between them on CUDA cores:
 //   tet64_point1: W = J G UB (and lambda J u), face traces (u, n.grad u);
-//   tet64_face:   jumps and averages, F1 = -sJ Mf (avg + tau jump), F2 = sJ Mf jump / 2;
-//   tet64_point2: z_b = MW_b + y_b (y_b the lifted F2), Au = sum of F1 at the node
-//                 [+ lambda J M u], which the last product adds D_b^T z_b to.
+//   tet64_jumps:  jumps and averages from the element's and the neighbours' traces;
+//   tet64_point2: F1 = -sJ FM, F2 = sJ FM / 2; z_b = MW_b + y_b (y_b the lifted F2),
+//                 Au = sum of F1 at the node [+ lambda J M u], which the last
+//                 product adds D_b^T z_b to.
 // The same operator as tet_grad / tet_lift, with the FP64 products no longer on
 // the FP64 pipe.
 template <int N>
@@ -569,76 +570,40 @@ __global__ void __launch_bounds__(256) tet64_point1(int64_t K, int64_t nE, int R
   }
 }
 
+// Per element and face: the rows [avg + tau jump | jump] at the face nodes
+// ([nE][4][2 Nfp]) that the face-mass products take.
 template <int N>
-struct Tet64Face {
-  static constexpr int Nfp = (N + 1) * (N + 2) / 2, NF = 4 * Nfp;
-  static constexpr int EB = 1024 / NF;  // elements per block iteration
-  static constexpr int words = 4 * Nfp * Nfp + 2 * EB * NF;
-};
-
-template <int N>
-__global__ void __launch_bounds__(256) tet64_face(int64_t K, int64_t nE, OpsLayout L, const double* __restrict__ ops,
-                                                  const double* __restrict__ geo, const int* __restrict__ conn,
-                                                  const int* __restrict__ mapJ, const double2* __restrict__ tr,
-                                                  double* __restrict__ F) {
-  using D = Tet64Face<N>;
-  constexpr int Nfp = D::Nfp, NF = D::NF, EB = D::EB;
-  extern __shared__ __align__(16) unsigned char tet_smem[];
-  double* sMf = reinterpret_cast<double*>(tet_smem);  // [4][l][j]
-  double* sJm = sMf + 4 * Nfp * Nfp;                  // [EB][NF]
-  double* sAv = sJm + EB * NF;
-  for (int q = threadIdx.x; q < 4 * Nfp * Nfp; q += blockDim.x) {
-    const int f = q / (Nfp * Nfp);
-    sMf[q] = ops[L.Mf[f] + (q - f * Nfp * Nfp)];
-  }
-  const int64_t stride = int64_t(gridDim.x) * EB, strideK = stride % K;
-  int64_t e0 = (int64_t(blockIdx.x) * EB) % K;  // be0 mod K, advanced with be0
-  for (int64_t be0 = int64_t(blockIdx.x) * EB; be0 < nE;
-       be0 += stride, e0 = e0 + strideK < K ? e0 + strideK : e0 + strideK - K) {
-    const int nv = int(nE - be0 < EB ? nE - be0 : EB);
-    __syncthreads();
-    for (int q = threadIdx.x; q < nv * NF; q += blockDim.x) {  // jumps and averages
-      const int g = q / NF, fj = q - g * NF, f = fj / Nfp;
-      const int64_t be = be0 + g, e = tet_elem(e0, g, K);
-      const int c = conn[4 * e + f];
-      const double2 own = tr[be * NF + fj];
-      double jm = 0.0, av = 0.0;
-      if (c >= 0) {
-        const double2 nb = tr[(be - e + c) * NF + mapJ[e * NF + fj]];
-        jm = nb.x - own.x;
-        av = 0.5 * (own.y - nb.y);  // the neighbour's trace carries its own (opposite) normal
-      } else if (c == -2) {         // Dirichlet ghost: u+ = -u-, grad u+ = grad u-
-        jm = -2.0 * own.x;
-        av = own.y;
-      }
-      sJm[q] = jm;
-      sAv[q] = av;
+__global__ void __launch_bounds__(256) tet64_jumps(int64_t K, int64_t nE, const double* __restrict__ geo,
+                                                   const int* __restrict__ conn, const int* __restrict__ mapJ,
+                                                   const double2* __restrict__ tr, double* __restrict__ XF) {
+  constexpr int Nfp = (N + 1) * (N + 2) / 2, NF = 4 * Nfp;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < nE * NF; q += stride) {
+    const int64_t be = q / NF, e = be < K ? be : be % K;
+    const int fj = int(q - be * NF), f = fj / Nfp, j = fj - f * Nfp;
+    const int c = conn[4 * e + f];
+    const double2 own = tr[q];
+    double jm = 0.0, av = 0.0;
+    if (c >= 0) {
+      const double2 nb = tr[(be - e + c) * NF + mapJ[e * NF + fj]];
+      jm = nb.x - own.x;
+      av = 0.5 * (own.y - nb.y);  // the neighbour's trace carries its own (opposite) normal
+    } else if (c == -2) {         // Dirichlet ghost: u+ = -u-, grad u+ = grad u-
+      jm = -2.0 * own.x;
+      av = own.y;
     }
-    __syncthreads();
-    for (int q = threadIdx.x; q < nv * NF; q += blockDim.x) {  // face-mass products
-      const int g = q / NF, fj = q - g * NF, f = fj / Nfp, j = fj - f * Nfp;
-      const int64_t be = be0 + g, e = tet_elem(e0, g, K);
-      const double* gf = geo + e * kGeo + 7 + 8 * f;
-      const double sJ = gf[6], tau = gf[7];
-      const double* Mf = sMf + f * Nfp * Nfp;
-      const double* jf = sJm + g * NF + f * Nfp;
-      const double* af = sAv + g * NF + f * Nfp;
-      double m1 = 0.0, m2 = 0.0;
-#pragma unroll 4
-      for (int l = 0; l < Nfp; ++l) {
-        const double mf = Mf[l * Nfp + j];
-        m1 += mf * (af[l] + tau * jf[l]);
-        m2 += mf * jf[l];
-      }
-      F[(be * 2) * NF + fj] = -sJ * m1;
-      F[(be * 2 + 1) * NF + fj] = 0.5 * sJ * m2;
-    }
+    const double tau = geo[e * kGeo + 7 + 8 * f + 7];
+    double* x = XF + (be * 4 + f) * 2 * Nfp;
+    x[j] = av + tau * jm;
+    x[Nfp + j] = jm;
   }
 }
 
+// FM ([nE][4][2 Nfp]): the face-mass products Mf [avg + tau jump | jump] per face;
+// F1 = -sJ FM[f][j], F2 = sJ FM[f][Nfp + j] / 2.
 template <int N>
 __global__ void __launch_bounds__(256) tet64_point2(int64_t K, int64_t nE, int R4, const int* __restrict__ nfs,
-                                                    const double* __restrict__ geo, const double* __restrict__ F,
+                                                    const double* __restrict__ geo, const double* __restrict__ FM,
                                                     double* __restrict__ MW, double* __restrict__ Au) {
   constexpr int Np = (N + 1) * (N + 2) * (N + 3) / 6, Nfp = (N + 1) * (N + 2) / 2, NF = 4 * Nfp;
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
@@ -646,18 +611,20 @@ __global__ void __launch_bounds__(256) tet64_point2(int64_t K, int64_t nE, int R
     const int64_t be = q / Np, e = be < K ? be : be % K;
     const int i = int(q - be * Np);
     const double* ge = geo + e * kGeo;
-    const double* F1 = F + be * 2 * NF;
-    const double* F2 = F1 + NF;
+    const double* fm = FM + be * 2 * NF;
     double y0 = 0.0, y1 = 0.0, y2 = 0.0, f1 = 0.0;
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
       const int fj = nfs[i * 3 + s];
       if (fj < 0) continue;
-      const double* nr = ge + 7 + 8 * (fj / Nfp);
-      y0 += nr[0] * F2[fj];
-      y1 += nr[1] * F2[fj];
-      y2 += nr[2] * F2[fj];
-      f1 += F1[fj];
+      const int f = fj / Nfp, j = fj - f * Nfp;
+      const double* gf = ge + 7 + 8 * f;
+      const double sJ = gf[6];
+      const double F2 = 0.5 * sJ * fm[f * 2 * Nfp + Nfp + j];
+      y0 += gf[0] * F2;
+      y1 += gf[1] * F2;
+      y2 += gf[2] * F2;
+      f1 -= sJ * fm[f * 2 * Nfp + j];
     }
     double* mw = MW + be * R4 * Np;
     mw[i] += y0;
@@ -863,11 +830,11 @@ cudaError_t tet_apply_n(const dg_tet_mesh* m, int64_t nE, T lambda, const T* ops
 
 template <int N>
 cudaError_t tet64_tc_n(const dg_tet_mesh* m, int64_t nE, double lambda, const double* u, double* Au, cudaStream_t st) {
-  constexpr int Np = (N + 1) * (N + 2) * (N + 3) / 6, NF = 2 * (N + 1) * (N + 2);
+  constexpr int Np = (N + 1) * (N + 2) * (N + 3) / 6, Nfp = (N + 1) * (N + 2) / 2, NF = 4 * Nfp;
   const int R4 = lambda != 0.0 ? 4 : 3;
   auto even = [](size_t n) { return (n + 1) & ~size_t(1); };  // keeps the traces 16-byte aligned
   const size_t nUB = even(size_t(nE) * 3 * Np), nW = even(size_t(nE) * R4 * Np);
-  const size_t words = nUB + 2 * nW + size_t(nE) * NF * 2 + size_t(nE) * 2 * NF;
+  const size_t words = nUB + 2 * nW + size_t(nE) * NF * 2 + 2 * size_t(nE) * 2 * NF;
   if (m->t64scr_bytes < words * sizeof(double)) {
     cudaFree(m->t64scr);
     m->t64scr = nullptr;
@@ -880,24 +847,26 @@ cudaError_t tet64_tc_n(const dg_tet_mesh* m, int64_t nE, double lambda, const do
   double* W = UB + nUB;
   double* MW = W + nW;
   double2* tr = reinterpret_cast<double2*>(MW + nW);
-  double* F = reinterpret_cast<double*>(tr + size_t(nE) * NF);
+  double* XF = reinterpret_cast<double*>(tr + size_t(nE) * NF);  // [nE][4][2 Nfp]
+  double* FM = XF + size_t(nE) * 2 * NF;
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
   const unsigned gp = unsigned(std::min<int64_t>((nE * Np + 255) / 256, int64_t(sms) * 16));
-  const unsigned gf = unsigned(std::min<int64_t>((nE + Tet64Face<N>::EB - 1) / Tet64Face<N>::EB, int64_t(sms) * 8));
+  const unsigned gf = unsigned(std::min<int64_t>((nE * NF + 255) / 256, int64_t(sms) * 16));
   e = tc64_gemm_launch(m->t64_grad, nE, u, Np, UB, 3 * Np, st);
   if (e != cudaSuccess) return e;
   tet64_point1<N><<<gp, 256, 0, st>>>(m->K, nE, R4, lambda, m->fmask, m->geo64, u, UB, W, tr);
   note_launch();
-  tet64_face<N><<<gf, 256, Tet64Face<N>::words * sizeof(double), st>>>(m->K, nE, m->L, m->ops64, m->geo64, m->conn,
-                                                                       m->mapJ, tr, F);
+  tet64_jumps<N><<<gf, 256, 0, st>>>(m->K, nE, m->geo64, m->conn, m->mapJ, tr, XF);
   note_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  e = tc64_gemm_launch(m->t64_mass, nE * R4, W, Np, MW, Np, st);
+  for (int f = 0; f < 4 && e == cudaSuccess; ++f)  // FM[f] = diag(Mf, Mf) XF[f], the rows of face f
+    e = tc64_gemm_launch(m->t64_face[f], nE, XF + f * 2 * Nfp, 2 * NF, FM + f * 2 * Nfp, 2 * NF, st);
+  if (e == cudaSuccess) e = tc64_gemm_launch(m->t64_mass, nE * R4, W, Np, MW, Np, st);
   if (e != cudaSuccess) return e;
-  tet64_point2<N><<<gp, 256, 0, st>>>(m->K, nE, R4, m->nfs, m->geo64, F, MW, Au);
+  tet64_point2<N><<<gp, 256, 0, st>>>(m->K, nE, R4, m->nfs, m->geo64, FM, MW, Au);
   note_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return tc64_gemm_launch(m->t64_out, nE, MW, int64_t(R4) * Np, Au, Np, st, 1);
@@ -971,6 +940,7 @@ dg_status dg_tet_mesh_destroy(dg_tet_mesh* m) {
   tc64_op_free(&m->t64_grad);
   tc64_op_free(&m->t64_mass);
   tc64_op_free(&m->t64_out);
+  for (dgx::Tc64Op& op : m->t64_face) tc64_op_free(&op);
   delete m;
   return DG_OK;
 }
@@ -1196,6 +1166,15 @@ dg_status dg_tet_mesh_setup(int N, int64_t Nv, const double* VX, const double* V
     ce = tc64_op_create(A1, 3 * Np, Np, &m->t64_grad);
     if (ce == cudaSuccess) ce = tc64_op_create(R.M, Np, Np, &m->t64_mass);
     if (ce == cudaSuccess) ce = tc64_op_create(A3, Np, 3 * Np, &m->t64_out);
+    for (int f = 0; f < 4 && ce == cudaSuccess; ++f) {  // diag(Mf, Mf) of each reference face
+      std::vector<double> A4(size_t(4) * Nfp * Nfp, 0.0);
+      for (int j = 0; j < Nfp; ++j)
+        for (int l = 0; l < Nfp; ++l) {
+          A4[size_t(j) * 2 * Nfp + l] = R.Mf[f][size_t(j) * Nfp + l];
+          A4[size_t(Nfp + j) * 2 * Nfp + Nfp + l] = R.Mf[f][size_t(j) * Nfp + l];
+        }
+      ce = tc64_op_create(A4, 2 * Nfp, 2 * Nfp, &m->t64_face[f]);
+    }
   }
   if (ce != cudaSuccess) {
     dg_tet_mesh_destroy(m);
