@@ -269,6 +269,10 @@ struct dg_tet_mesh {
   // FP64 products on the tensor cores: [Dr; Ds; Dt], M, [Dr^T Ds^T Dt^T] (built at setup),
   // and their scratch (grown on demand)
   dgx::Tc64Op t64_grad, t64_mass, t64_out, t64_face[4];
+  // every reference face's mass is face_ratio[f] times face 0's (the faces list their
+  // nodes in one pattern): one face-mass product over all faces, scaled afterwards
+  bool face_shared = false;
+  double face_ratio[4] = {1.0, 1.0, 1.0, 1.0};
   mutable double* t64scr = nullptr;
   mutable size_t t64scr_bytes = 0;
 };
@@ -599,12 +603,16 @@ __global__ void __launch_bounds__(256) tet64_jumps(int64_t K, int64_t nE, const 
   }
 }
 
-// FM ([nE][4][2 Nfp]): the face-mass products Mf [avg + tau jump | jump] per face;
-// F1 = -sJ FM[f][j], F2 = sJ FM[f][Nfp + j] / 2.
+// FM ([nE][4][2 Nfp]): the face-mass products Mf [avg + tau jump | jump] per face
+// (with face 0's matrix for every face when they share it, fr[f] the area ratio);
+// F1 = -sJ fr[f] FM[f][j], F2 = sJ fr[f] FM[f][Nfp + j] / 2.
+struct FaceRatio {
+  double r[4];
+};
 template <int N>
 __global__ void __launch_bounds__(256) tet64_point2(int64_t K, int64_t nE, int R4, const int* __restrict__ nfs,
                                                     const double* __restrict__ geo, const double* __restrict__ FM,
-                                                    double* __restrict__ MW, double* __restrict__ Au) {
+                                                    FaceRatio fr, double* __restrict__ MW, double* __restrict__ Au) {
   constexpr int Np = (N + 1) * (N + 2) * (N + 3) / 6, Nfp = (N + 1) * (N + 2) / 2, NF = 4 * Nfp;
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < nE * Np; q += stride) {
@@ -619,7 +627,7 @@ __global__ void __launch_bounds__(256) tet64_point2(int64_t K, int64_t nE, int R
       if (fj < 0) continue;
       const int f = fj / Nfp, j = fj - f * Nfp;
       const double* gf = ge + 7 + 8 * f;
-      const double sJ = gf[6];
+      const double sJ = gf[6] * fr.r[f];
       const double F2 = 0.5 * sJ * fm[f * 2 * Nfp + Nfp + j];
       y0 += gf[0] * F2;
       y1 += gf[1] * F2;
@@ -862,11 +870,17 @@ cudaError_t tet64_tc_n(const dg_tet_mesh* m, int64_t nE, double lambda, const do
   tet64_jumps<N><<<gf, 256, 0, st>>>(m->K, nE, m->geo64, m->conn, m->mapJ, tr, XF);
   note_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  for (int f = 0; f < 4 && e == cudaSuccess; ++f)  // FM[f] = diag(Mf, Mf) XF[f], the rows of face f
-    e = tc64_gemm_launch(m->t64_face[f], nE, XF + f * 2 * Nfp, 2 * NF, FM + f * 2 * Nfp, 2 * NF, st);
+  if (m->face_shared) {  // FM = diag(Mf_0, Mf_0) XF over the rows of all faces
+    e = tc64_gemm_launch(m->t64_face[0], nE * 4, XF, 2 * Nfp, FM, 2 * Nfp, st);
+  } else {
+    for (int f = 0; f < 4 && e == cudaSuccess; ++f)  // FM[f] = diag(Mf, Mf) XF[f], the rows of face f
+      e = tc64_gemm_launch(m->t64_face[f], nE, XF + f * 2 * Nfp, 2 * NF, FM + f * 2 * Nfp, 2 * NF, st);
+  }
+  FaceRatio fr;
+  for (int f = 0; f < 4; ++f) fr.r[f] = m->face_shared ? m->face_ratio[f] : 1.0;
   if (e == cudaSuccess) e = tc64_gemm_launch(m->t64_mass, nE * R4, W, Np, MW, Np, st);
   if (e != cudaSuccess) return e;
-  tet64_point2<N><<<gp, 256, 0, st>>>(m->K, nE, R4, m->nfs, m->geo64, FM, MW, Au);
+  tet64_point2<N><<<gp, 256, 0, st>>>(m->K, nE, R4, m->nfs, m->geo64, FM, fr, MW, Au);
   note_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return tc64_gemm_launch(m->t64_out, nE, MW, int64_t(R4) * Np, Au, Np, st, 1);
@@ -1166,7 +1180,17 @@ dg_status dg_tet_mesh_setup(int N, int64_t Nv, const double* VX, const double* V
     ce = tc64_op_create(A1, 3 * Np, Np, &m->t64_grad);
     if (ce == cudaSuccess) ce = tc64_op_create(R.M, Np, Np, &m->t64_mass);
     if (ce == cudaSuccess) ce = tc64_op_create(A3, Np, 3 * Np, &m->t64_out);
-    for (int f = 0; f < 4 && ce == cudaSuccess; ++f) {  // diag(Mf, Mf) of each reference face
+    m->face_shared = true;
+    for (int f = 0; f < 4; ++f) {
+      m->face_ratio[f] = R.face_area[f] / R.face_area[0];
+      double dmax = 0.0, amax = 0.0;
+      for (size_t q = 0; q < R.Mf[f].size(); ++q) {
+        dmax = std::max(dmax, std::fabs(R.Mf[f][q] - m->face_ratio[f] * R.Mf[0][q]));
+        amax = std::max(amax, std::fabs(R.Mf[f][q]));
+      }
+      if (dmax > 1e-13 * amax) m->face_shared = false;
+    }
+    for (int f = 0; f < (m->face_shared ? 1 : 4) && ce == cudaSuccess; ++f) {  // diag(Mf, Mf) per reference face
       std::vector<double> A4(size_t(4) * Nfp * Nfp, 0.0);
       for (int j = 0; j < Nfp; ++j)
         for (int l = 0; l < Nfp; ++l) {
