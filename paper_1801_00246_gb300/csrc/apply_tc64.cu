@@ -718,8 +718,8 @@ cudaError_t gemm_launch(const Tc64Op& op, int64_t rows, const double* X, int64_t
 }  // namespace
 
 cudaError_t tc64_gemm_launch(const Tc64Op& op, int64_t rows, const double* X, int64_t ldx, double* out, int64_t ldo,
-                             cudaStream_t st, int accum) {
-  return gemm_launch<0>(op, rows, X, ldx, out, ldo, nullptr, GradOut{}, st, accum);
+                             cudaStream_t st, int accum, const int* ex) {
+  return gemm_launch<0>(op, rows, X, ldx, out, ldo, ex, GradOut{}, st, accum);
 }
 
 namespace {

@@ -158,9 +158,11 @@ struct Tc64Op;
 cudaError_t tc64_op_create(const std::vector<double>& A, int M, int K, Tc64Op* op);
 void tc64_op_free(Tc64Op* op);
 // out[r][c] (+)= sum_k A[c][k] X[r][k] (FP64, exact slicing on the tcgen05 tensor cores;
-// accum: add to out instead of overwriting it); X row-major with leading dimension ldx
+// accum: add to out instead of overwriting it); X row-major with leading dimension ldx.
+// ex (optional): per row r an exponent E with |X[r][k]| < 2^E for every k (-1100 for a
+// zero row), from the producer of X; without it the product scans each row itself.
 cudaError_t tc64_gemm_launch(const Tc64Op& op, int64_t rows, const double* X, int64_t ldx, double* out, int64_t ldo,
-                             cudaStream_t st, int accum = 0);
+                             cudaStream_t st, int accum = 0, const int* ex = nullptr);
 bool tc64_supported(int degree);
 // An apply in chunks of rows (elements x right-hand sides) for callers that move
 // the data in and out while it runs: the first phase (gradient product) reads
