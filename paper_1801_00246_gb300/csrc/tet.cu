@@ -545,11 +545,27 @@ __global__ void __launch_bounds__(kTetThreads) tet_lift(int64_t K, int64_t nE, O
 //                 product adds D_b^T z_b to.
 // The same operator as tet_grad / tet_lift, with the FP64 products no longer on
 // the FP64 pipe.
+// exponent e with |v| < 2^e (-1100 for zero and subnormals), the row bound the
+// sliced products take
+__device__ __forceinline__ int exp_bound(double v) {
+  const int E = int((__double_as_longlong(v) >> 52) & 0x7ff);
+  return E == 0 ? -1100 : E - 1022;
+}
+
+// The largest exponent over the lanes of the warp that share `key` (lanes of one
+// row), which the lowest of them adds to ex[row] by an atomic maximum; ex starts
+// below every exponent, so each row ends at its exact bound.
+__device__ __forceinline__ void row_exp_max(int* ex, int64_t row, unsigned peers, int v) {
+  const int m = __reduce_max_sync(peers, v);
+  if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicMax(ex + row, m);
+}
+
 template <int N>
 __global__ void __launch_bounds__(256) tet64_point1(int64_t K, int64_t nE, int R4, double lambda,
                                                     const int* __restrict__ fmask, const double* __restrict__ geo,
                                                     const double* __restrict__ u, const double* __restrict__ UB,
-                                                    double* __restrict__ W, double2* __restrict__ tr) {
+                                                    double* __restrict__ W, int* __restrict__ exW,
+                                                    double2* __restrict__ tr) {
   constexpr int Np = (N + 1) * (N + 2) * (N + 3) / 6, Nfp = (N + 1) * (N + 2) / 2, NF = 4 * Nfp;
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < nE * Np; q += stride) {
@@ -560,10 +576,21 @@ __global__ void __launch_bounds__(256) tet64_point1(int64_t K, int64_t nE, int R
     const double* ub = UB + be * 3 * Np;
     const double a0 = ub[i], a1 = ub[Np + i], a2 = ub[2 * Np + i];
     double* wo = W + be * R4 * Np;
-    wo[i] = J * (g[1] * a0 + g[2] * a1 + g[3] * a2);
-    wo[Np + i] = J * (g[2] * a0 + g[4] * a1 + g[5] * a2);
-    wo[2 * Np + i] = J * (g[3] * a0 + g[5] * a1 + g[6] * a2);
-    if (R4 == 4) wo[3 * Np + i] = lambda * J * u[q];
+    const double w0 = J * (g[1] * a0 + g[2] * a1 + g[3] * a2);
+    const double w1 = J * (g[2] * a0 + g[4] * a1 + g[5] * a2);
+    const double w2 = J * (g[3] * a0 + g[5] * a1 + g[6] * a2);
+    wo[i] = w0;
+    wo[Np + i] = w1;
+    wo[2 * Np + i] = w2;
+    const unsigned peers = __match_any_sync(__activemask(), static_cast<unsigned long long>(be));
+    row_exp_max(exW, be * R4, peers, exp_bound(w0));
+    row_exp_max(exW, be * R4 + 1, peers, exp_bound(w1));
+    row_exp_max(exW, be * R4 + 2, peers, exp_bound(w2));
+    if (R4 == 4) {
+      const double w3 = lambda * J * u[q];
+      wo[3 * Np + i] = w3;
+      row_exp_max(exW, be * R4 + 3, peers, exp_bound(w3));
+    }
   }
   for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < nE * NF; q += stride) {
     const int64_t be = q / NF, e = be < K ? be : be % K;
@@ -579,7 +606,8 @@ __global__ void __launch_bounds__(256) tet64_point1(int64_t K, int64_t nE, int R
 template <int N>
 __global__ void __launch_bounds__(256) tet64_jumps(int64_t K, int64_t nE, const double* __restrict__ geo,
                                                    const int* __restrict__ conn, const int* __restrict__ mapJ,
-                                                   const double2* __restrict__ tr, double* __restrict__ XF) {
+                                                   const double2* __restrict__ tr, double* __restrict__ XF,
+                                                   int* __restrict__ exF) {
   constexpr int Nfp = (N + 1) * (N + 2) / 2, NF = 4 * Nfp;
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < nE * NF; q += stride) {
@@ -598,8 +626,12 @@ __global__ void __launch_bounds__(256) tet64_jumps(int64_t K, int64_t nE, const 
     }
     const double tau = geo[e * kGeo + 7 + 8 * f + 7];
     double* x = XF + (be * 4 + f) * 2 * Nfp;
-    x[j] = av + tau * jm;
+    const double v1 = av + tau * jm;
+    x[j] = v1;
     x[Nfp + j] = jm;
+    const int64_t row = be * 4 + f;
+    const unsigned peers = __match_any_sync(__activemask(), static_cast<unsigned long long>(row));
+    row_exp_max(exF, row, peers, max(exp_bound(v1), exp_bound(jm)));
   }
 }
 
@@ -612,7 +644,8 @@ struct FaceRatio {
 template <int N>
 __global__ void __launch_bounds__(256) tet64_point2(int64_t K, int64_t nE, int R4, const int* __restrict__ nfs,
                                                     const double* __restrict__ geo, const double* __restrict__ FM,
-                                                    FaceRatio fr, double* __restrict__ MW, double* __restrict__ Au) {
+                                                    FaceRatio fr, double* __restrict__ MW, int* __restrict__ exZ,
+                                                    double* __restrict__ Au) {
   constexpr int Np = (N + 1) * (N + 2) * (N + 3) / 6, Nfp = (N + 1) * (N + 2) / 2, NF = 4 * Nfp;
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < nE * Np; q += stride) {
@@ -635,10 +668,13 @@ __global__ void __launch_bounds__(256) tet64_point2(int64_t K, int64_t nE, int R
       f1 -= sJ * fm[f * 2 * Nfp + j];
     }
     double* mw = MW + be * R4 * Np;
-    mw[i] += y0;
-    mw[Np + i] += y1;
-    mw[2 * Np + i] += y2;
+    const double z0 = mw[i] + y0, z1 = mw[Np + i] + y1, z2 = mw[2 * Np + i] + y2;
+    mw[i] = z0;
+    mw[Np + i] = z1;
+    mw[2 * Np + i] = z2;
     Au[q] = R4 == 4 ? f1 + mw[3 * Np + i] : f1;
+    const unsigned peers = __match_any_sync(__activemask(), static_cast<unsigned long long>(be));
+    row_exp_max(exZ, be, peers, max(exp_bound(z0), max(exp_bound(z1), exp_bound(z2))));
   }
 }
 
@@ -842,7 +878,8 @@ cudaError_t tet64_tc_n(const dg_tet_mesh* m, int64_t nE, double lambda, const do
   const int R4 = lambda != 0.0 ? 4 : 3;
   auto even = [](size_t n) { return (n + 1) & ~size_t(1); };  // keeps the traces 16-byte aligned
   const size_t nUB = even(size_t(nE) * 3 * Np), nW = even(size_t(nE) * R4 * Np);
-  const size_t words = nUB + 2 * nW + size_t(nE) * NF * 2 + 2 * size_t(nE) * 2 * NF;
+  const size_t nEx = even((size_t(nE) * (R4 + 4 + 1) + 1) / 2);  // row exponents (ints), in doubles
+  const size_t words = nUB + 2 * nW + size_t(nE) * NF * 2 + 2 * size_t(nE) * 2 * NF + nEx;
   if (m->t64scr_bytes < words * sizeof(double)) {
     cudaFree(m->t64scr);
     m->t64scr = nullptr;
@@ -857,33 +894,38 @@ cudaError_t tet64_tc_n(const dg_tet_mesh* m, int64_t nE, double lambda, const do
   double2* tr = reinterpret_cast<double2*>(MW + nW);
   double* XF = reinterpret_cast<double*>(tr + size_t(nE) * NF);  // [nE][4][2 Nfp]
   double* FM = XF + size_t(nE) * 2 * NF;
+  int* exW = reinterpret_cast<int*>(FM + size_t(nE) * 2 * NF);  // [nE R4]
+  int* exF = exW + size_t(nE) * R4;                              // [nE 4]
+  int* exZ = exF + size_t(nE) * 4;                               // [nE]
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
   const unsigned gp = unsigned(std::min<int64_t>((nE * Np + 255) / 256, int64_t(sms) * 16));
   const unsigned gf = unsigned(std::min<int64_t>((nE * NF + 255) / 256, int64_t(sms) * 16));
-  e = tc64_gemm_launch(m->t64_grad, nE, u, Np, UB, 3 * Np, st);
+  // row exponents start below every exponent (0x80808080); the producers raise them
+  e = cudaMemsetAsync(exW, 0x80, size_t(nE) * (R4 + 4 + 1) * sizeof(int), st);
+  if (e == cudaSuccess) e = tc64_gemm_launch(m->t64_grad, nE, u, Np, UB, 3 * Np, st);
   if (e != cudaSuccess) return e;
-  tet64_point1<N><<<gp, 256, 0, st>>>(m->K, nE, R4, lambda, m->fmask, m->geo64, u, UB, W, tr);
+  tet64_point1<N><<<gp, 256, 0, st>>>(m->K, nE, R4, lambda, m->fmask, m->geo64, u, UB, W, exW, tr);
   note_launch();
-  tet64_jumps<N><<<gf, 256, 0, st>>>(m->K, nE, m->geo64, m->conn, m->mapJ, tr, XF);
+  tet64_jumps<N><<<gf, 256, 0, st>>>(m->K, nE, m->geo64, m->conn, m->mapJ, tr, XF, exF);
   note_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (m->face_shared) {  // FM = diag(Mf_0, Mf_0) XF over the rows of all faces
-    e = tc64_gemm_launch(m->t64_face[0], nE * 4, XF, 2 * Nfp, FM, 2 * Nfp, st);
+    e = tc64_gemm_launch(m->t64_face[0], nE * 4, XF, 2 * Nfp, FM, 2 * Nfp, st, 0, exF);
   } else {
     for (int f = 0; f < 4 && e == cudaSuccess; ++f)  // FM[f] = diag(Mf, Mf) XF[f], the rows of face f
       e = tc64_gemm_launch(m->t64_face[f], nE, XF + f * 2 * Nfp, 2 * NF, FM + f * 2 * Nfp, 2 * NF, st);
   }
   FaceRatio fr;
   for (int f = 0; f < 4; ++f) fr.r[f] = m->face_shared ? m->face_ratio[f] : 1.0;
-  if (e == cudaSuccess) e = tc64_gemm_launch(m->t64_mass, nE * R4, W, Np, MW, Np, st);
+  if (e == cudaSuccess) e = tc64_gemm_launch(m->t64_mass, nE * R4, W, Np, MW, Np, st, 0, exW);
   if (e != cudaSuccess) return e;
-  tet64_point2<N><<<gp, 256, 0, st>>>(m->K, nE, R4, m->nfs, m->geo64, FM, fr, MW, Au);
+  tet64_point2<N><<<gp, 256, 0, st>>>(m->K, nE, R4, m->nfs, m->geo64, FM, fr, MW, exZ, Au);
   note_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  return tc64_gemm_launch(m->t64_out, nE, MW, int64_t(R4) * Np, Au, Np, st, 1);
+  return tc64_gemm_launch(m->t64_out, nE, MW, int64_t(R4) * Np, Au, Np, st, 1, exZ);
 }
 
 // FP64 on the tensor cores (the default) or, with pipe set, on the FP64 pipe.
