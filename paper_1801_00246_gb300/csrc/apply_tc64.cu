@@ -55,8 +55,9 @@ constexpr int kABytes = kSl * kT * kKC * 2;  // one data chunk, 8 slices: 64 KB
 constexpr int kBBytes = kSl * kNC * kKC * 2; // one operator block, 8 slices: 24 KB
 constexpr int kASlice = kT * kKC * 2, kBSlice = kNC * kKC * 2;
 constexpr int kNodeTab = 72;  // entries of the gradient product's node-to-face table (Np <= 66)
-// the tail: 10 mbarriers, slot, 2 flags, the node-to-face table
-constexpr int kSmem = 2 * kABytes + 2 * kBBytes + 4 * kT * 4 + 12 * 8 + kNodeTab * 4;
+// the tail: 10 mbarriers, slot, 2 flags, the node-to-face table, the tile's face normals
+// (MODE 1: n.grad r and n.grad s of the three faces as float-float, [3 faces][4][kT])
+constexpr int kSmem = 2 * kABytes + 2 * kBBytes + 4 * kT * 4 + 12 * 8 + kNodeTab * 4 + 12 * kT * 4;
 
 __device__ int g_tc64_err;
 
@@ -235,6 +236,7 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
   // MODE 1: per node n the face nodes it is, packed (fa + 1) | ja << 4 | (fb + 1) << 8 | jb << 12
   // (face f, position j; a corner is on two faces; 0 in the face field: none)
   int* nodetab = reinterpret_cast<int*>(reinterpret_cast<uint8_t*>(bars) + 12 * 8);
+  float* snrm = reinterpret_cast<float*>(nodetab + kNodeTab);  // [f][nr.h, nr.l, ns.h, ns.l][kT]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t ntiles = (rows + kT - 1) / kT;
   // with at most two data chunks per row, both stay in the two buffers for all
@@ -356,6 +358,15 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
       // every slicer takes the same decision to stop (they meet at named barriers below)
       asm volatile("bar.sync 1, %0;\n" ::"r"(kSlicers) : "memory");
       if (tid == 0) *reinterpret_cast<volatile int*>(tile_abort) = *reinterpret_cast<volatile int*>(abort_flag);
+      if (MODE == 1 && q < 3) {  // face q's normal metric of this row, once per tile (read by the drains)
+        const int64_t rw = tile * kT + e;
+        const double* gq = go.gx + 16 * (((rw < rows ? rw : 0) + go.row0) % go.K) + 4 + 4 * q;
+        const ff nr = d2ff(__ldg(gq), 0), ns = d2ff(__ldg(gq + 1), 0);
+        snrm[(q * 4 + 0) * kT + e] = nr.h;
+        snrm[(q * 4 + 1) * kT + e] = nr.l;
+        snrm[(q * 4 + 2) * kT + e] = ns.h;
+        snrm[(q * 4 + 3) * kT + e] = ns.l;
+      }
       asm volatile("bar.sync 1, %0;\n" ::"r"(kSlicers) : "memory");
       if (*reinterpret_cast<volatile int*>(tile_abort)) break;
       const int64_t row = tile * kT + e;
@@ -530,7 +541,8 @@ __global__ void __launch_bounds__(kSlicers + 32, 1) tc64_gemm(int64_t rows, int 
                 for (int t = 0; t < 2; ++t) {
                   const int f = t == 0 ? fa : fb, j = t == 0 ? ja : jb;
                   if (f >= 0) {
-                    const ff nr = d2ff(__ldg(gg + 4 + 4 * f), 0), ns = d2ff(__ldg(gg + 5 + 4 * f), 0);
+                    const ff nr{snrm[(f * 4 + 0) * kT + e], snrm[(f * 4 + 1) * kT + e]};
+                    const ff ns{snrm[(f * 4 + 2) * kT + e], snrm[(f * 4 + 3) * kT + e]};
                     const ff dn = ff_add(ff_mul(nr, ur), ff_mul(ns, us));
                     const int64_t fi = int64_t(f * Nfp + j) * ldc + row;
                     go.FNu[fi] = un;
