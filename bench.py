@@ -45,8 +45,9 @@ PMG_DEGREES = [8, 4, 2, 1]
 CHEB = 3           # Chebyshev-Jacobi smoothing degree per pre/post smoothing
 COARSE_PASSES = 1  # degree-1 coarse solve: one AMG-preconditioned CG pass (a scaled AMG V-cycle)
 # DRAM bytes per FP64 apply at N=8 from the latest ncu capture of the current
-# default kernels; None while the kernels differ from that capture
-TENSOR_APPLY_TRAFFIC = None
+# default kernels (tcgen05: gradient product 0.806 GB, face fill 0.938 GB, output
+# product 0.888 GB); None while the kernels differ from that capture
+TENSOR_APPLY_TRAFFIC = 2.632e9
 
 
 # apply kernels by DG_KERNEL_* value
