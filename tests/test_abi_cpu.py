@@ -152,3 +152,27 @@ def test_header_is_c_and_a_c_program_links_and_runs(P, tmp_path):
     st, r0, s_last, tol, max_iter, name = out.stdout.split(None, 5)
     assert st == "0" and float(r0) == -1.0 and float(s_last) == 1.0   # vertices v0 and v2 of the reference triangle
     assert float(tol) == 1e-10 and int(max_iter) == 1000 and name.strip()
+
+
+def test_new_entry_points_reject_bad_arguments_before_device_work(P):
+    """dg_apply_host and the tetrahedral calls check their arguments on the host:
+    a NULL mesh or pointer is DG_ERR_ARG with no device call."""
+    import ctypes
+    L = P.lib()
+    buf = (ctypes.c_double * 8)()
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    assert L.dg_apply_host(None, 0, P.DG_F64, 1, 0.0, p, p, None) == 1
+    assert L.dg_tet_apply(None, P.DG_F64, 1, 0.0, p, p, None) == 1
+    assert L.dg_tet_rhs(None, 1, p, p, p, None) == 1
+    assert L.dg_tet_pcg_jacobi_solve(None, 1, 0.0, 1e-10, 10, p, p, None, None) == 1
+    assert L.dg_tet_mesh_info(None, None, None, None) == 1
+    assert L.dg_tet_mesh_destroy(None) == 0
+    out = ctypes.c_void_p()
+    VX = (ctypes.c_double * 4)(0, 1, 0, 0)
+    VY = (ctypes.c_double * 4)(0, 0, 1, 0)
+    VZ = (ctypes.c_double * 4)(0, 0, 0, 1)
+    E = (ctypes.c_int32 * 4)(0, 1, 2, 3)
+    bc = (ctypes.c_int8 * 4)(1, 1, 1, 1)
+    assert L.dg_tet_mesh_setup(6, 4, VX, VY, VZ, 1, E, bc, None, ctypes.byref(out)) == 1   # degree 6
+    assert L.dg_tet_mesh_setup(2, 4, VX, VY, VZ, 1, E, None, None, ctypes.byref(out)) == 1  # NULL tags
+    assert not out.value
