@@ -125,3 +125,21 @@ def test_tet_operator_invariant_under_local_vertex_renumbering(N):
         perm = d.argmin(axis=1)
         assert np.all(d[np.arange(S1.Np), perm] < 1e-12)
         assert np.abs(A1[e] - A2[e][perm]).max() <= 1e-12 * np.abs(A1).max()
+
+
+def test_tet_mass_integrates_volume_and_moments():
+    """1^T J M p is the integral of p over the mesh: the unit cube's volume 1 and its
+    first and second moments 1/2 and 1/3 (p = 1, x, y^2)."""
+    S, _ = _sip(2, 2)
+    for p, want in ((np.ones_like(S.x), 1.0), (S.x, 0.5), (S.y ** 2, 1.0 / 3.0)):
+        assert abs(S.mass_apply(p).sum() - want) <= 1e-13
+
+
+def test_tet_helmholtz_is_poisson_plus_lambda_mass():
+    """A(lambda) u = A(0) u + lambda J M u: the screened term enters the element
+    blocks only, at the quadrature that integrates the mass exactly."""
+    S, _ = _sip(2, 3, seed=4)
+    u = np.random.default_rng(2).uniform(-1, 1, (S.K, S.Np))
+    lam = 7.25
+    d = S.apply(u, lam=lam) - S.apply(u)
+    assert np.abs(d - lam * S.mass_apply(u)).max() <= 1e-12 * np.abs(d).max()
