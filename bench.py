@@ -681,7 +681,9 @@ def run_tet(args):
                     nbytes = K * (2 * B * Np * word + 40 * word + 4 * 4 + 4 * Nfp * 4)
                     print(json.dumps({
                         "tet": True, "N": N, "Np": Np, "K": K, "B": B, "op": "helmholtz" if lam else "poisson",
-                        "prec": key, "kernel": "fp64_pipe" if pipe else ("tc64" if key == "f64" else "cuda_cores"),
+                        "prec": key, "kernel": ("fp64_pipe" if pipe or (key == "f64" and N <= 2)
+                                                else ("tc64" if key == "f64" else "cuda_cores")),
+                        "default": not pipe,
                         "ms": t * 1e3, "gdofs": B * K * Np / t / 1e9,
                         "hbm_gbs": nbytes / t / 1e9, "hbm_frac": nbytes / t / 1e9 / pk["hbm_gbs"]}), flush=True)
             del u64
