@@ -143,3 +143,22 @@ def test_tet_helmholtz_is_poisson_plus_lambda_mass():
     lam = 7.25
     d = S.apply(u, lam=lam) - S.apply(u)
     assert np.abs(d - lam * S.mass_apply(u)).max() <= 1e-12 * np.abs(d).max()
+
+
+@pytest.mark.parametrize("N,lost", [(1, 0.1), (2, 0.25), (3, 0.25)])
+def test_tet_penalty_keeps_the_form_coercive_with_margin(N, lost):
+    """The interior penalty has to dominate the consistency terms: with the
+    reading's tau = (N+1)(N+3)/3 max(1/h) the assembled form stays positive
+    definite at half the penalty too, and loses definiteness once the penalty is
+    cut to a quarter (a tenth at N = 1): the constant is of the right size, not
+    merely positive."""
+    S, _ = _sip(2, N)
+    t0 = S.tau.copy()
+
+    def lam_min(scale):
+        S.tau = t0 * scale
+        A = S.assemble().toarray()
+        return np.linalg.eigvalsh(0.5 * (A + A.T)).min()
+
+    assert lam_min(1.0) > 0 and lam_min(0.5) > 0
+    assert lam_min(lost) < 0
