@@ -146,3 +146,22 @@ def test_blend_parameter_at_degree_4_is_near_optimal():
     value lies within 1e-3 of the best constant over [0, 0.3]."""
     best = min(_lebesgue(4, a) for a in np.linspace(0.0, 0.3, 7))
     assert _lebesgue(4, basis.ALPHA_OPT[3]) <= best + 1e-3
+
+
+@pytest.mark.parametrize("N", [1, 2, 4])
+def test_penalty_keeps_the_form_coercive_with_margin(N):
+    """Eq. PenaltyParameter's tau = (N+1)(N+2)/2 max(1/h) keeps the SIPDG form
+    positive definite at half of it too, and the form loses definiteness at a
+    quarter: the constant is of the size coercivity needs, not merely positive."""
+    from dg_inputs import jittered_grid
+    m = jittered_grid(4, 4, jitter=0.1, seed=1)
+    S = Sipdg(m.VX, m.VY, m.EToV, m.bc, N)
+    t0 = S.tau.copy()
+
+    def lam_min(scale):
+        S.tau = t0 * scale
+        A = S.assemble().toarray()
+        return np.linalg.eigvalsh(0.5 * (A + A.T)).min()
+
+    assert lam_min(1.0) > 0 and lam_min(0.5) > 0
+    assert lam_min(0.25) < 0
