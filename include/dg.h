@@ -368,7 +368,8 @@ dg_status dg_tet_mesh_nodes(const dg_tet_mesh* mesh, double* x, double* y, doubl
  * output). The
  * first call at a batch size (and precision) larger than any before allocates
  * the mesh's apply scratch ((3 Np + 8 Nfp) B K words, Nfp = (N+1)(N+2)/2; about
- * (11 Np + 16 Nfp) B K doubles for DG_F64); applies on one mesh must not overlap. */
+ * (11 Np + 24 Nfp + 5) B K doubles for DG_F64 from degree 3); applies on one mesh
+ * must not overlap. */
 dg_status dg_tet_apply(const dg_tet_mesh* mesh, dg_prec prec, int B, double lambda, const void* u, void* Au,
                        void* stream);
 /* b = J M f - L(g) (the Dirichlet problem's weak right-hand side, as dg_rhs). */
